@@ -1,0 +1,120 @@
+"""Pins of the oracle's quadtree and interaction lists (Section 3.1, Fig. 1).
+
+Invariants fixed by the definitions: leaves tile the root box, every split box
+has four children, adjacent leaves differ by at most one level (the level
+restriction of Section 3.1), the balance step adds only forced boxes, the
+hashed list builder equals a pairwise test of the list definitions, and the
+lists are symmetric (U, V) or mutually inverse (W, X).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import source, tables
+from oracle import tree as T
+
+
+def small_trees():
+    out = []
+    for seed, tol, depth, sig in ((3, 1e-3, 4, 0.05), (4, 1e-4, 5, 0.03), (7, 1e-2, 5, 0.01),
+                                  (11, 1e-6, 4, 0.08)):
+        src = W.narrow_gaussians(seed, n=2, sigma=sig, spread=0.35)
+        out.append(T.build_adaptive(0.1, -0.2, 1.5, 6, src, tol, depth, return_info=True))
+    return out
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2, 3])
+def test_uniform_counts(depth):
+    t = T.build_uniform(0, 0, 1, 4, depth)
+    assert t.n_boxes == (4 ** (depth + 1) - 1) // 3
+    assert t.n_leaves == 4 ** depth
+
+
+def test_adaptive_trees_tile_and_balance():
+    for t, info in small_trees():
+        area = float(np.sum(t.h(t.leaves) ** 2))
+        assert abs(area - t.width ** 2) < 1e-12 * t.width ** 2
+        assert T.is_balanced(t)
+        # every box the balance step added is forced: un-splitting it breaks the restriction
+        refined = info["refined"]
+        for b in range(t.n_boxes):
+            ch = t.child[b]
+            if ch[0] < 0 or not np.all(t.is_leaf[ch]):
+                continue
+            key = (int(t.level[ch[0]]), int(t.ix[ch[0]]), int(t.iy[ch[0]]))
+            if key in refined:
+                continue
+            boxes = set(t.index.keys()) - {(int(t.level[c]), int(t.ix[c]), int(t.iy[c])) for c in ch}
+            assert not T.is_balanced(T.Tree(t.cx, t.cy, t.width, t.k, boxes))
+
+
+def test_lists_match_definitions_and_symmetry():
+    for t, _ in small_trees() + [(T.build_uniform(0, 0, 1, 4, 3), None)]:
+        L = T.build_lists(t)
+        B = T.build_lists_bruteforce(t)
+        for name in "UVWX":
+            assert np.array_equal(L[name][0], B[name][0]), name
+            assert np.array_equal(L[name][1], B[name][1]), name
+
+        def pairs(name):
+            p, i = L[name][0], L[name][1]
+            return {(b, int(c)) for b in range(t.n_boxes) for c in i[p[b]:p[b + 1]]}
+        U, V, Wl, X = pairs("U"), pairs("V"), pairs("W"), pairs("X")
+        assert U == {(c, b) for (b, c) in U}
+        assert V == {(c, b) for (b, c) in V}
+        assert Wl == {(c, b) for (b, c) in X}
+        sizes = {n: np.diff(L[n][0]).max(initial=0) for n in "UVWX"}
+        assert sizes["U"] <= 13 and sizes["V"] <= 27 and sizes["W"] <= 20 and sizes["X"] <= 5
+
+
+def test_list_configs_match_geometry():
+    cfg = tables.near_configs()
+    for t, _ in small_trees():
+        L = T.build_lists(t)
+        p, idx, cf = L["U"]
+        for b in range(t.n_boxes):
+            for e in range(p[b], p[b + 1]):
+                s = idx[e]
+                rho, dx, dy = cfg[cf[e]]
+                hb = float(t.h(b))
+                cb, cs = t.centre(b), t.centre(s)
+                assert abs(float(t.h(s)) / hb - rho) < 1e-15
+                assert abs((cs[0] - cb[0]) / hb - dx) < 1e-12 and abs((cs[1] - cb[1]) / hb - dy) < 1e-12
+        for name, geo, scale in (("W", tables.w_configs(), 0.5), ("X", tables.x_configs(), 2.0)):
+            p, idx, cf = L[name]
+            for b in range(t.n_boxes):
+                for e in range(p[b], p[b + 1]):
+                    s = idx[e]
+                    hb = float(t.h(b))
+                    cb, cs = t.centre(b), t.centre(s)
+                    dx, dy = geo[cf[e]]
+                    assert abs(float(t.h(s)) / hb - scale) < 1e-15
+                    assert abs((cs[0] - cb[0]) / hb - dx) < 1e-12 and abs((cs[1] - cb[1]) / hb - dy) < 1e-12
+
+
+def test_refinement_decisions_follow_tail_test():
+    """Every leaf below max_depth passes the tail test; every refined box failed it."""
+    src = W.narrow_gaussians(5, n=3, sigma=0.04)
+    tol, depth, k = 1e-5, 6, 8
+    t, info = T.build_adaptive(0, 0, 1, k, src, tol, depth, return_info=True)
+    X, Y = t.leaf_nodes()
+    vals = source.evaluate_source(src, X, Y).reshape(-1, k, k)
+    tl = T.cheb.tail(vals, k)
+    lv = t.level[t.leaves]
+    refined_leaf = np.array([(int(t.level[b]), int(t.ix[b]), int(t.iy[b])) in info["refined"] for b in t.leaves])
+    assert np.all(tl[(lv < depth) & refined_leaf] <= tol * info["F"])
+    assert info["min_margin"] > 1e-9
+
+
+def test_kinked_source_zero_set_is_the_curve():
+    wl = W.kinked()
+    prm = wl.sources[0].params
+    a, c = prm[0:7], prm[7:14]
+    th = np.linspace(0, 2 * math.pi, 97)
+    r = 0.6 + sum(a[i] * np.cos((i + 2) * th + c[i]) for i in range(7))
+    phi = source.kinked_phi(prm, r * np.cos(th), r * np.sin(th))
+    assert np.max(np.abs(phi)) < 1e-14
+    assert np.all(source.kinked_phi(prm, 0.5 * r * np.cos(th), 0.5 * r * np.sin(th)) > 0)
+    assert np.all(source.kinked_phi(prm, 1.1 * r * np.cos(th), 1.1 * r * np.sin(th)) < 0)
