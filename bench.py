@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Throughput of the volume-potential box FMM on one GB300 (target points per second).
+
+One step = one call of the box code (S2M, M2M, M2L/S2L/L2L, near-field tables,
+L2T, M2T) over the whole tree of the adaptive 20-Gaussian workload (k = 16,
+p = 40, tol 1e-10, depth <= 16), with tree, operators and f resident in HBM.
+Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload adaptive_gauss20|uniform_gauss3|kinked] [--precision fp64|mixed]
+
+--impl reference times the CPU oracle (plain numpy FP64 box code) on bounded
+samples of the same workload on the host cores. Under torchrun every rank runs an
+independent replica of the workload (the path is not sharded: replicas only).
+"""
+from __future__ import annotations
+
+import os
+
+# the CPU oracle legs run single-threaded BLAS; the GPU path does not use host BLAS
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import math  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "volume-FMM target pts/s at 1e-10 rel err: mixed/batched vs plain FP64, 1 GB300"
+UNIT = "target points/s"
+FP64_OVER_BF16 = 1.25 / 2250.0  # nominal dense FP64 / BF16 tensor ratio of GB300
+
+
+def workload(name):
+    if name == "adaptive_gauss20":
+        return W.adaptive_gauss20()
+    if name == "uniform_gauss3":
+        return W.uniform_gauss3()
+    if name == "kinked":
+        return W.kinked()
+    raise SystemExit("unknown workload " + name)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_setup(wl):
+    from oracle import tables
+    from oracle import tree as T
+    src = wl.sources[0]
+    if wl.uniform_depth >= 0:
+        ot = T.build_uniform(wl.cx, wl.cy, wl.width, wl.k, wl.uniform_depth)
+    else:
+        ot = T.build_adaptive(wl.cx, wl.cy, wl.width, wl.k, src, wl.tol, wl.max_depth, wl.min_depth)
+    return ot, T.build_lists(ot), tables.Ops(wl.k, wl.p), ot.sample(src)
+
+
+def oracle_sample_step(ot, L, ops, F, leaves):
+    """One oracle step on a bounded sample: the full upward pass plus the leaf pass for `leaves`."""
+    from oracle import fmm
+    t0 = time.perf_counter()
+    out = fmm.solve(ot, L, ops, F, leaves=leaves)
+    return time.perf_counter() - t0, out
+
+
+def pick_sample(ot, L, ops, F, budget_s, rng):
+    """Leaves for one step of about budget_s seconds (calibrated on a short run)."""
+    n_leaves = ot.n_leaves
+    probe = rng.choice(n_leaves, size=min(8, n_leaves), replace=False)
+    dt, _ = oracle_sample_step(ot, L, ops, F, probe)
+    per = dt / len(probe)
+    m = int(max(1, min(n_leaves, budget_s / max(per, 1e-6))))
+    return np.sort(rng.choice(n_leaves, size=m, replace=False))
+
+
+def run_reference(args, wl):
+    ot, L, ops, F = oracle_setup(wl)
+    rng = np.random.default_rng(7)
+    leaves = pick_sample(ot, L, ops, F, budget_s=max(2.0, 120.0 / max(1, args.steps + args.warmup)), rng=rng)
+    kk = wl.k * wl.k
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, _ = oracle_sample_step(ot, L, ops, F, leaves)
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = len(leaves) * kk / (ms / 1e3)
+    sample = "%d of %d leaves (%d targets) per step, full upward pass included" % (
+        len(leaves), ot.n_leaves, len(leaves) * kk)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "n_leaves": ot.n_leaves, "n_targets": ot.n_leaves * kk, "k": wl.k,
+                       "p": wl.p, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(wl, gpu_u, budget_s=15.0):
+    """Oracle on a bounded sample of the same workload; also the sampled error of the GPU result."""
+    t0 = time.perf_counter()
+    ot, L, ops, F = oracle_setup(wl)
+    setup_s = time.perf_counter() - t0
+    rng = np.random.default_rng(11)
+    leaves = pick_sample(ot, L, ops, F, budget_s, rng)
+    dt, ref = oracle_sample_step(ot, L, ops, F, leaves)
+    kk = wl.k * wl.k
+    errs = None
+    if gpu_u is not None and gpu_u[0].shape[0] == ot.n_leaves * kk:
+        errs = []
+        for q in range(3):
+            got = gpu_u[q].reshape(ot.n_leaves, kk)[leaves]
+            errs.append(float(np.max(np.abs(got - ref[q])) / np.max(np.abs(ref[q]))))
+    return {"value": len(leaves) * kk / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of %d leaves (%d targets), full upward pass included, %.1f s; oracle setup %.1f s untimed"
+                      % (len(leaves), ot.n_leaves, len(leaves) * kk, dt, setup_s)}, errs
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="adaptive_gauss20")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    wl = workload(args.workload)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1610_00823_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_1610_00823_gb300 import build as b
+        b.build()
+    import paper_1610_00823_gb300 as v
+    from paper_1610_00823_gb300.api import volume_potential_profiled, workspace
+
+    src = wl.sources[0]
+    t0 = time.perf_counter()
+    if wl.uniform_depth >= 0:
+        tree = v.tree_build_uniform(wl.cx, wl.cy, wl.width, wl.k, wl.uniform_depth)
+    else:
+        tree = v.tree_build(wl.cx, wl.cy, wl.width, wl.k, src, wl.tol, wl.max_depth, wl.min_depth)
+    torch.cuda.synchronize()
+    t_tree = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    prec = v.MIXED if args.precision == "mixed" else v.FP64
+    ops = v.ops_create(wl.k, wl.p, prec)
+    torch.cuda.synchronize()
+    t_ops = time.perf_counter() - t0
+    f = v.source_sample(tree, src)
+    kk = wl.k * wl.k
+    n_targets = tree.n_leaves * kk
+    out = tuple(torch.empty_like(f) for _ in range(3))
+    ws = workspace(tree, ops, 1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        v.volume_potential(tree, ops, f, out=out, ws=ws)
+    torch.cuda.synchronize()
+
+    step_ms, stage_acc, launches = [], {}, 0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 between timed steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stages, launches = volume_potential_profiled(tree, ops, f, out, ws)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            for kname, val in stages.items():
+                stage_acc[kname] = stage_acc.get(kname, 0.0) + val
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = statistics.mean(step_ms)
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * n_targets / (ms / 1e3)
+    stage_ms = {kname: val / args.steps for kname, val in stage_acc.items()}
+
+    # end to end through the host entry point (pinned buffers, copies inside the timed region)
+    f_host = f.cpu().pin_memory()
+    outs_host = tuple(torch.empty_like(f_host).pin_memory() for _ in range(3))
+    ws_io = workspace(tree, ops, 1, with_io=True)
+    for _ in range(2):
+        v.volume_potential_host(tree, ops, f_host, out_host=outs_host, ws=ws_io)
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        v.volume_potential_host(tree, ops, f_host, out_host=outs_host, ws=ws_io)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = world * n_targets / (statistics.mean(e2e_ms) / 1e3)
+    del ws_io
+
+    peaks, peak_kind = measured_peaks()
+    if args.precision == "fp64":
+        flops = 2.0 * 3 * kk * kk * tree.list_len[0]  # near-field table applies, one launch
+        achieved = flops / (stage_ms["near"] / 1e3) / 1e12
+        peak = peaks["bf16_tflops"] * FP64_OVER_BF16
+        roof = {"kernel": "near_gemm_kernel", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "%s bf16 x nominal FP64/BF16 ratio (1.25/2250)" % peak_kind,
+                "flops_per_launch": flops, "ms_per_launch": stage_ms["near"]}
+    else:
+        flops = 2.0 * 3 * kk * kk * tree.list_len[0]
+        achieved = flops / (stage_ms["near"] / 1e3) / 1e12
+        roof = {"kernel": "near field (split-BF16 tcgen05)", "bound": "tensor", "achieved": achieved,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s (FP64-equivalent)", "frac": achieved / peaks["bf16_tflops"],
+                "traffic": None, "peak_source": peak_kind, "ms_per_launch": stage_ms["near"]}
+
+    cpu = None
+    errs = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        got = [o.cpu().numpy() for o in out]
+        cpu, errs = cpu_baseline(wl, got)
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x6+f64",
+                "data": "synthetic",
+                "config": {"workload": wl.name, "precision": args.precision, "n_leaves": tree.n_leaves,
+                           "n_boxes": tree.n_boxes, "depth": tree.depth, "n_targets": n_targets, "k": wl.k,
+                           "p": wl.p, "tol": wl.tol, "u_list_len": tree.list_len[0],
+                           "l2": "flushed between timed steps (256 MB write outside the events)",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "tree_build_s": t_tree, "ops_create_s": t_ops},
+                "stage_ms": stage_ms,
+                "roofline": roof,
+                "cpu_baseline": cpu,
+                "sampled_rel_err_vs_oracle": errs,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_targets * 8,
+                        "d2h_bytes_per_step": 3 * n_targets * 8, "ms_per_step": statistics.mean(e2e_ms)},
+                "gpu_launches": launches,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * vfmm: adaptive volume-potential box FMM on one GB300 (sm_103a).
+ *
+ * Computes, at every collocation node of every leaf of a level-restricted
+ * quadtree, the volume integral of Section 3 (Eq. volumeint3)
+ *     u(x) = V[f~](x) = -(1/2 pi) int_B log|x - y| f~(y) dy
+ * and its gradient (Section 3.2, Eq. volumeint3x), where B is the root box and
+ * f~ is the piecewise polynomial interpolant of f on the leaves (Section 3.1).
+ *
+ * Conventions shared by every entry point
+ *  - Root box: centre (cx, cy), width W. A box at level l has width W 2^-l and
+ *    integer coordinates (ix, iy) in [0, 2^l)^2. Boxes are numbered in
+ *    canonical order: by level, then by Morton key (bit b of ix -> bit 2b,
+ *    bit b of iy -> bit 2b + 1). Leaves are numbered in the same order.
+ *  - Leaf nodes: tensor first-kind Chebyshev nodes, k per side; node (i, j) of
+ *    a leaf of width h and lower-left corner (lo_x, lo_y) sits at
+ *    x = lo_x + h (i_box + 1/2 + xhat_i), xhat_i = -cos(pi (2i+1) / (2k)) / 2,
+ *    stored x-fastest: flat index j*k + i.
+ *  - Values arrays (f, u, u_x, u_y) are FP64, [nrhs][n_leaves][k*k], leaf-major
+ *    in canonical leaf order, row-major, no padding.
+ *  - Level restriction (Section 3.1): adjacent leaves (corner contact counts)
+ *    differ by at most one level.
+ *  - Refinement (Section 3.1, Section 6.1): a box at level l < max_depth is
+ *    split when the largest |c_mn| with max(m, n) >= k - 2 of its 2-D Chebyshev
+ *    coefficients exceeds tol * F, F = max |f| over the nodes of the uniform
+ *    tree of level min(5, max_depth); boxes above min_depth always split.
+ *  - Pointers named *_dev are CUDA device pointers on the current device;
+ *    everything else is host memory. The caller owns every buffer it passes;
+ *    the library owns the memory behind vfmm_tree and vfmm_ops handles and
+ *    frees it in the matching destroy call.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream). Calls
+ *    that fill device buffers are stream-ordered and return before the work
+ *    completes, unless stated otherwise.
+ *  - Errors: every call returns VFMM_OK (0) or a negative VFMM_ERR_* code and
+ *    never aborts; vfmm_strerror() names the code and vfmm_last_error_detail()
+ *    gives the last failure's message (thread-local).
+ */
+#ifndef VFMM_H
+#define VFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VFMM_OK 0
+#define VFMM_ERR_INVALID_ARG (-1)
+#define VFMM_ERR_OOM (-2)
+#define VFMM_ERR_CUDA (-3)
+#define VFMM_ERR_NOT_BUILT (-4)
+#define VFMM_ERR_TIMEOUT (-5)
+#define VFMM_ERR_WORKSPACE (-6)
+#define VFMM_ERR_INTERNAL (-7)
+
+/* Source kinds; params layouts (host FP64 arrays):
+ *  CONSTANT  : [A]                                         f = A
+ *  GAUSS_SUM : n rows [cx, cy, sigma, A]                   f = sum A exp(-|x-c|^2 / (2 sigma^2))
+ *  KINKED    : [a_2..a_8, c_2..c_8, 5 g rows, 5 h rows]    f = g max(0, phi) + h,
+ *              phi = r_chi(x)^2 - |x|^2, r_chi = 0.6 + chi(|x|) sum_m a_m cos(m theta + c_m),
+ *              chi(rho) = psi((rho - 0.1)/0.2), psi(t) = e^{-1/t} / (e^{-1/t} + e^{-1/(1-t)}),
+ *              g and h Gaussian sums in the GAUSS_SUM row layout (n = 5). */
+#define VFMM_SRC_CONSTANT 0
+#define VFMM_SRC_GAUSS_SUM 1
+#define VFMM_SRC_KINKED 2
+
+/* Arithmetic of the solve. */
+#define VFMM_FP64 0  /* every product and sum in FP64 */
+#define VFMM_MIXED 1 /* near-field table apply as split-BF16 tensor-core products, FP64 elsewhere */
+
+#define VFMM_LIST_U 0 /* leaves: the leaf itself and every adjacent leaf (near field) */
+#define VFMM_LIST_V 1 /* boxes: children of parent's colleagues not adjacent to the box (M2L) */
+#define VFMM_LIST_W 2 /* leaves: children of colleagues not adjacent to the leaf (M2T) */
+#define VFMM_LIST_X 3 /* boxes: leaves c with the box in W(c) (S2L) */
+
+typedef struct vfmm_tree vfmm_tree;
+typedef struct vfmm_ops vfmm_ops;
+
+typedef struct {
+    double cx, cy, width; /* root box */
+    int32_t k;            /* nodes per side, 4 <= k <= 16 */
+    int32_t max_depth;    /* 0 <= max_depth <= 16 */
+    int32_t min_depth;    /* 0 <= min_depth <= max_depth */
+    double tol;           /* refinement tolerance (relative to F) */
+} vfmm_tree_params;
+
+typedef struct {
+    int32_t kind;         /* VFMM_SRC_* */
+    int32_t n;            /* GAUSS_SUM: number of rows; ignored otherwise */
+    const double* params; /* host, layout above */
+} vfmm_source;
+
+typedef struct {
+    int64_t n_boxes, n_leaves;
+    int32_t depth, k;
+    int64_t list_len[4]; /* entries in the U, V, W, X lists */
+    double f_scale;      /* F of the refinement test (0 for uniform trees) */
+    double min_margin;   /* min over refinement decisions of |tail / (tol F) - 1| */
+} vfmm_tree_info_t;
+
+/* Adaptive build (Section 3.1): level-by-level refinement of the root box by the
+ * tail test on f, then the minimal refinement that meets the level restriction,
+ * canonical numbering and the U/V/W/X lists, all on the device.
+ * Synchronises `stream` (box counts are read back per level).
+ * Errors: INVALID_ARG (bad k, depths, width <= 0, tol < 0, unknown source kind),
+ * OOM, CUDA. */
+int vfmm_tree_build(const vfmm_tree_params* prm, const vfmm_source* src, void* stream, vfmm_tree** out);
+
+/* Uniform tree of the given depth (prm->tol and depths ignored). Synchronises. */
+int vfmm_tree_build_uniform(const vfmm_tree_params* prm, int32_t depth, void* stream, vfmm_tree** out);
+
+int vfmm_tree_info(const vfmm_tree* tree, vfmm_tree_info_t* info);
+
+/* Host copies of the box table: level, ix, iy, each [n_boxes] int32. Synchronous. */
+int vfmm_tree_export_boxes(const vfmm_tree* tree, int32_t* level, int32_t* ix, int32_t* iy);
+
+/* Host copy of one list in CSR form: ptr [n_boxes + 1], idx [len], cfg [len] (box
+ * indices ascending within a row). cfg: U -> near configuration 0..32, V -> offset
+ * index 0..39, W and X -> pattern index 0..19 (conventions in the tables section
+ * of the design notes: same-level (dy+1)*3+(dx+1); coarse/fine patterns sorted by
+ * (y, x)). Any output pointer may be NULL. Synchronous. */
+int vfmm_tree_export_list(const vfmm_tree* tree, int32_t which, int32_t* ptr, int32_t* idx, int32_t* cfg);
+
+/* Node coordinates of every leaf, x_dev and y_dev [n_leaves * k * k]. */
+int vfmm_tree_leaf_nodes(const vfmm_tree* tree, double* x_dev, double* y_dev, void* stream);
+
+/* f at every leaf node, f_dev [n_leaves * k * k]. */
+int vfmm_source_sample(const vfmm_tree* tree, const vfmm_source* src, double* f_dev, void* stream);
+
+int vfmm_tree_destroy(vfmm_tree* tree);
+
+/* Unit-scale operators of the box code for (k, p) (Section 3.1, "precomputed
+ * tables ... up to scale"; Section 3.2 for the gradient tables), generated on the
+ * device: 33 near-field tables of the potential and both gradient components,
+ * S2M, S2L (20), M2T geometry (20), L2T, M2M (4), M2L (40), L2L (4).
+ * 4 <= k <= 16, 1 <= p <= 60. Synchronises. Errors: INVALID_ARG, OOM, CUDA. */
+int vfmm_ops_create(int32_t k, int32_t p, int32_t precision, void* stream, vfmm_ops** out);
+
+/* Host copy of one operator table for parity tests (layouts in the binding). */
+#define VFMM_OP_NEAR 0 /* [33][3][k*k][k*k] */
+#define VFMM_OP_S2M 1  /* [p+1][k*k] complex (re, im interleaved) */
+#define VFMM_OP_S2L 2  /* [20][p+1][k*k] complex */
+#define VFMM_OP_M2M 3  /* [4][p+1][p+1] complex */
+#define VFMM_OP_L2L 4  /* [4][p+1][p+1] complex */
+#define VFMM_OP_M2L 5  /* [40][p+1][p+1] complex */
+int vfmm_ops_export(const vfmm_ops* ops, int32_t which, double* host, int64_t n_doubles);
+
+int vfmm_ops_destroy(vfmm_ops* ops);
+
+/* Device workspace the solve needs for this tree, operator set and nrhs
+ * (multipole and local expansions, near-field partial products). with_io != 0
+ * adds room for the device copies vfmm_volume_potential_host stages through. */
+int vfmm_workspace_size(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs, int32_t with_io,
+                        size_t* bytes);
+
+/* The box code (Section 3.1): u, u_x, u_y at every leaf node for nrhs right-hand
+ * sides: upward pass (S2M, M2M), downward pass (M2L over V, S2L over X, L2L),
+ * leaf pass (near-field tables over U with the log(h) scale term, L2T, M2T over W).
+ * Everything runs on `stream`, with no host synchronisation and no allocation.
+ * Errors: INVALID_ARG (k or p of ops differ from the tree's k, nrhs < 1), WORKSPACE
+ * (workspace_bytes below vfmm_workspace_size), CUDA. */
+int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
+                          double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
+                          size_t workspace_bytes, void* stream);
+
+/* Same, from host buffers: copies f to the device, solves, copies u, u_x, u_y back
+ * and synchronises `stream`. Host buffers should be pinned for full copy speed.
+ * The workspace must be sized with with_io = 1. */
+int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_host, int32_t nrhs,
+                               double* u_host, double* ux_host, double* uy_host, void* workspace_dev,
+                               size_t workspace_bytes, void* stream);
+
+/* Stage timers (tracing): the same solve as vfmm_volume_potential with CUDA events
+ * recorded on `stream` between its stages; synchronises `stream` and returns the
+ * elapsed milliseconds of each stage summed over the right-hand sides
+ * (stage_ms[VFMM_N_STAGES]: S2M, M2M, DOWN (M2L + S2L + L2L), NEAR, L2T, LEAF)
+ * and the number of kernels the solve launched (*launches). */
+#define VFMM_N_STAGES 6
+int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
+                                   double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
+                                   size_t workspace_bytes, void* stream, float* stage_ms, int32_t* launches);
+
+const char* vfmm_strerror(int code);
+const char* vfmm_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VFMM_H */

@@ -1,0 +1,205 @@
+"""Torch-facing wrappers over the C ABI (names follow include/vfmm.h without the prefix)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import c_double_p, c_int32_p, call
+
+FP64 = 0
+MIXED = 1
+LISTS = {"U": 0, "V": 1, "W": 2, "X": 3}
+OP_IDS = {"near": 0, "s2m": 1, "s2l": 2, "m2m": 3, "l2l": 4, "m2l": 5}
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _source(src):
+    """(kind, n, params) or an object with those attributes -> (ctypes Source, keep-alive array)."""
+    kind, n, params = (src.kind, src.n, src.params) if hasattr(src, "kind") else src
+    arr = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    s = _lib.Source(int(kind), int(n), arr.ctypes.data_as(c_double_p))
+    return s, arr
+
+
+class Tree:
+    """Device-resident level-restricted quadtree with its interaction lists."""
+
+    def __init__(self, handle, k):
+        self._h = handle
+        self.k = k
+        info = _lib.TreeInfo()
+        call("vfmm_tree_info", self._h, ctypes.byref(info))
+        self.n_boxes = int(info.n_boxes)
+        self.n_leaves = int(info.n_leaves)
+        self.depth = int(info.depth)
+        self.list_len = [int(v) for v in info.list_len]
+        self.f_scale = float(info.f_scale)
+        self.min_margin = float(info.min_margin)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                _lib.load().vfmm_tree_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def export_boxes(self):
+        n = self.n_boxes
+        out = [np.zeros(n, dtype=np.int32) for _ in range(3)]
+        call("vfmm_tree_export_boxes", self._h, *[a.ctypes.data_as(c_int32_p) for a in out])
+        return out
+
+    def export_list(self, name):
+        q = LISTS[name]
+        ptr = np.zeros(self.n_boxes + 1, dtype=np.int32)
+        idx = np.zeros(max(1, self.list_len[q]), dtype=np.int32)
+        cfg = np.zeros(max(1, self.list_len[q]), dtype=np.int32)
+        call("vfmm_tree_export_list", self._h, q, ptr.ctypes.data_as(c_int32_p), idx.ctypes.data_as(c_int32_p),
+             cfg.ctypes.data_as(c_int32_p))
+        n = self.list_len[q]
+        return ptr, idx[:n], cfg[:n]
+
+    def leaf_nodes(self, stream=None):
+        n = self.n_leaves * self.k * self.k
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        call("vfmm_tree_leaf_nodes", self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+             _stream(stream))
+        return x, y
+
+
+def tree_build(cx, cy, width, k, source, tol, max_depth, min_depth=0, stream=None) -> Tree:
+    prm = _lib.TreeParams(cx, cy, width, k, max_depth, min_depth, tol)
+    s, keep = _source(source)
+    h = ctypes.c_void_p()
+    call("vfmm_tree_build", ctypes.byref(prm), ctypes.byref(s), _stream(stream), ctypes.byref(h))
+    del keep
+    return Tree(h, k)
+
+
+def tree_build_uniform(cx, cy, width, k, depth, stream=None) -> Tree:
+    prm = _lib.TreeParams(cx, cy, width, k, depth, depth, 0.0)
+    h = ctypes.c_void_p()
+    call("vfmm_tree_build_uniform", ctypes.byref(prm), int(depth), _stream(stream), ctypes.byref(h))
+    return Tree(h, k)
+
+
+def source_sample(tree: Tree, source, stream=None):
+    s, keep = _source(source)
+    f = torch.empty(tree.n_leaves * tree.k * tree.k, dtype=torch.float64, device="cuda")
+    call("vfmm_source_sample", tree.handle, ctypes.byref(s), ctypes.c_void_p(f.data_ptr()), _stream(stream))
+    del keep
+    return f
+
+
+class Ops:
+    """Device-resident unit-scale operators for (k, p, precision)."""
+
+    def __init__(self, handle, k, p, precision):
+        self._h = handle
+        self.k, self.p, self.precision = k, p, precision
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                _lib.load().vfmm_ops_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def export(self, name):
+        k, p = self.k, self.p
+        kk, P = k * k, p + 1
+        shapes = {"near": (33, 3, kk, kk), "s2m": (P, kk, 2), "s2l": (20, P, kk, 2), "m2m": (4, P, P, 2),
+                  "l2l": (4, P, P, 2), "m2l": (40, P, P, 2)}
+        shp = shapes[name]
+        out = np.zeros(int(np.prod(shp)), dtype=np.float64)
+        call("vfmm_ops_export", self._h, OP_IDS[name], out.ctypes.data_as(c_double_p), out.size)
+        out = out.reshape(shp)
+        if name != "near":
+            out = out[..., 0] + 1j * out[..., 1]
+        return out
+
+
+def ops_create(k, p, precision=FP64, stream=None) -> Ops:
+    h = ctypes.c_void_p()
+    call("vfmm_ops_create", int(k), int(p), int(precision), _stream(stream), ctypes.byref(h))
+    return Ops(h, k, p, precision)
+
+
+def workspace_size(tree: Tree, ops: Ops, nrhs=1, with_io=False) -> int:
+    b = ctypes.c_size_t()
+    call("vfmm_workspace_size", tree.handle, ops.handle, int(nrhs), int(bool(with_io)), ctypes.byref(b))
+    return int(b.value)
+
+
+def workspace(tree: Tree, ops: Ops, nrhs=1, with_io=False):
+    return torch.empty(workspace_size(tree, ops, nrhs, with_io), dtype=torch.uint8, device="cuda")
+
+
+def volume_potential(tree: Tree, ops: Ops, f, out=None, ws=None, stream=None):
+    """u, u_x, u_y at every leaf node. f: cuda float64 [n_leaves*k*k] or [nrhs, n_leaves*k*k]."""
+    n = tree.n_leaves * tree.k * tree.k
+    f = f.contiguous()
+    if f.dtype != torch.float64 or not f.is_cuda or f.numel() % n:
+        raise ValueError("f must be a cuda float64 tensor with a multiple of n_leaves*k*k elements")
+    nrhs = f.numel() // n
+    if out is None:
+        out = tuple(torch.empty_like(f) for _ in range(3))
+    if ws is None:
+        ws = workspace(tree, ops, nrhs)
+    call("vfmm_volume_potential", tree.handle, ops.handle, ctypes.c_void_p(f.data_ptr()), nrhs,
+         ctypes.c_void_p(out[0].data_ptr()), ctypes.c_void_p(out[1].data_ptr()), ctypes.c_void_p(out[2].data_ptr()),
+         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    return out
+
+
+def volume_potential_host(tree: Tree, ops: Ops, f_host, out_host=None, ws=None, stream=None):
+    """Same from host tensors (pinned for full speed); returns host tensors; synchronises."""
+    n = tree.n_leaves * tree.k * tree.k
+    f_host = f_host.contiguous()
+    if f_host.dtype != torch.float64 or f_host.is_cuda or f_host.numel() % n:
+        raise ValueError("f_host must be a host float64 tensor with a multiple of n_leaves*k*k elements")
+    nrhs = f_host.numel() // n
+    if out_host is None:
+        out_host = tuple(torch.empty_like(f_host) for _ in range(3))
+    if ws is None:
+        ws = workspace(tree, ops, nrhs, with_io=True)
+    call("vfmm_volume_potential_host", tree.handle, ops.handle, ctypes.c_void_p(f_host.data_ptr()), nrhs,
+         ctypes.c_void_p(out_host[0].data_ptr()), ctypes.c_void_p(out_host[1].data_ptr()),
+         ctypes.c_void_p(out_host[2].data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream))
+    return out_host
+
+
+STAGES = ("s2m", "m2m", "down", "near", "l2t", "leaf")
+
+
+def volume_potential_profiled(tree: Tree, ops: Ops, f, out, ws, stream=None):
+    """volume_potential with per-stage CUDA-event times; returns (stage_ms dict, kernel launches)."""
+    n = tree.n_leaves * tree.k * tree.k
+    nrhs = f.numel() // n
+    ms = (ctypes.c_float * len(STAGES))()
+    launches = ctypes.c_int32()
+    call("vfmm_volume_potential_profiled", tree.handle, ops.handle, ctypes.c_void_p(f.data_ptr()), nrhs,
+         ctypes.c_void_p(out[0].data_ptr()), ctypes.c_void_p(out[1].data_ptr()), ctypes.c_void_p(out[2].data_ptr()),
+         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream), ms, ctypes.byref(launches))
+    return dict(zip(STAGES, [float(x) for x in ms])), int(launches.value)

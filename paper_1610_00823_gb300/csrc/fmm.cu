@@ -1,0 +1,617 @@
+// The FMM passes of the box code (Section 3.1) in FP64, with the gradient from
+// differentiated tables and expansions (Section 3.2).
+//
+//   S2M      leaf multipoles  a = h^2 Q f                 (gather GEMM, all leaves)
+//   M2M      per level, finest first, one warp per parent box
+//   DOWN     per level from 2 down the tree, one CTA per box:
+//            b = L2L(parent) + sum_V M2L a_c (+ a_0(c) log h) + sum_X (2h)^2 R f_c (+ a_0(c) log h)
+//   NEAR     per near configuration, T_cfg f_src for every U-list entry (gather GEMM into
+//            a per-entry slab of the workspace; one launch for all 33 configurations)
+//   L2T      far-field values from the leaf's local expansion (gather GEMM)
+//   LEAF     one CTA per leaf: u = h^2 sum_U T f - (1/2pi) log(h) sum_U a_0(src) + L2T + sum_W M2T,
+//            gradient = h sum_U T' f + L2T'/h + sum_W M2T'
+//
+// Workspace (caller-owned, from vfmm_workspace_size): multipoles and locals
+// [n_boxes][2(p+1)], near slabs [n_U][3kk], far values [n_leaves][3kk] (+ I/O copies).
+#include <algorithm>
+#include <cmath>
+
+#include "ops.cuh"
+#include "vfmm_internal.cuh"
+
+namespace vfmm {
+
+constexpr double kInv2Pi = 0.15915494309189533577;
+
+// ---------------------------------------------------------------- FP64 gather GEMM tile
+// C_j[r] = scale_j * sum_s A[r][s] B_j[s] for rows r in [row0, row0 + 64), columns j < ncols.
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+struct ColPtrs {
+    const double* b[GBN];
+    double* c[GBN];
+    double scale[GBN];
+};
+
+__device__ inline void gemm_tile_fp64(const double* __restrict__ A, int M, int K, int row0, int ncols,
+                                      const ColPtrs& cp) {
+    __shared__ double As[GBK][GBM + 1];
+    __shared__ double Bs[GBK][GBN + 1];
+    const int t = threadIdx.x;
+    const int tx = t % 16, ty = t / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    const int lr = t / 4, lk = (t % 4) * 4;  // loader: row/column lr, k offset lk
+    for (int k0 = 0; k0 < K; k0 += GBK) {
+        {
+            int r = row0 + lr;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int kk = k0 + lk + q;
+                As[lk + q][lr] = (r < M && kk < K) ? A[(size_t)r * K + kk] : 0.0;
+            }
+            const double* bp = lr < ncols ? cp.b[lr] : nullptr;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int kk = k0 + lk + q;
+                Bs[lk + q][lr] = (bp && kk < K) ? bp[kk] : 0.0;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int c = tx * 4 + j;
+        if (c >= ncols) continue;
+        double* cptr = cp.c[c];
+        double sc = cp.scale[c];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int r = row0 + ty * 4 + i;
+            if (r < M) cptr[r] = sc * acc[i][j];
+        }
+    }
+}
+
+// Near field: one tile = (configuration, range of its U entries); blockIdx.x = row tile.
+__global__ void __launch_bounds__(256) near_gemm_kernel(const int4* __restrict__ tiles, const double* __restrict__ T,
+                                                        int kk, const int32_t* __restrict__ u_by_cfg,
+                                                        const int32_t* __restrict__ lidxU,
+                                                        const int32_t* __restrict__ leaf_of_box,
+                                                        const double* __restrict__ f, double* __restrict__ slab) {
+    __shared__ ColPtrs cp;
+    const int4 tl = tiles[blockIdx.y];  // cfg, begin, end
+    const int ncols = min(GBN, tl.z - tl.y);
+    if (threadIdx.x < GBN) {
+        int j = threadIdx.x;
+        if (j < ncols) {
+            int e = u_by_cfg[tl.y + j];
+            cp.b[j] = f + (size_t)leaf_of_box[lidxU[e]] * kk;
+            cp.c[j] = slab + (size_t)e * 3 * kk;
+        } else {
+            cp.b[j] = nullptr;
+            cp.c[j] = nullptr;
+        }
+        cp.scale[j] = 1.0;
+    }
+    __syncthreads();
+    gemm_tile_fp64(T + (size_t)tl.x * 3 * kk * kk, 3 * kk, kk, blockIdx.x * GBM, ncols, cp);
+}
+
+// S2M: columns are leaves; output row = multipole of the leaf's box, scaled by h^2.
+__global__ void __launch_bounds__(256) s2m_gemm_kernel(const double* __restrict__ S2M, int P2, int kk, int nleaf,
+                                                       const int32_t* __restrict__ box_of_leaf,
+                                                       const int32_t* __restrict__ level, double width,
+                                                       const double* __restrict__ f, double* __restrict__ Mexp) {
+    __shared__ ColPtrs cp;
+    const int col0 = blockIdx.y * GBN;
+    const int ncols = min(GBN, nleaf - col0);
+    if (threadIdx.x < GBN) {
+        int j = threadIdx.x;
+        if (j < ncols) {
+            int leaf = col0 + j;
+            int b = box_of_leaf[leaf];
+            double h = ldexp(width, -level[b]);
+            cp.b[j] = f + (size_t)leaf * kk;
+            cp.c[j] = Mexp + (size_t)b * P2;
+            cp.scale[j] = h * h;
+        } else {
+            cp.b[j] = nullptr;
+            cp.c[j] = nullptr;
+            cp.scale[j] = 0.0;
+        }
+    }
+    __syncthreads();
+    gemm_tile_fp64(S2M, P2, kk, blockIdx.x * GBM, ncols, cp);
+}
+
+// L2T: columns are leaves; input = local expansion of the leaf's box.
+__global__ void __launch_bounds__(256) l2t_gemm_kernel(const double* __restrict__ L2T, int P2, int kk, int nleaf,
+                                                       const int32_t* __restrict__ box_of_leaf,
+                                                       const double* __restrict__ Lexp, double* __restrict__ far) {
+    __shared__ ColPtrs cp;
+    const int col0 = blockIdx.y * GBN;
+    const int ncols = min(GBN, nleaf - col0);
+    if (threadIdx.x < GBN) {
+        int j = threadIdx.x;
+        if (j < ncols) {
+            int leaf = col0 + j;
+            cp.b[j] = Lexp + (size_t)box_of_leaf[leaf] * P2;
+            cp.c[j] = far + (size_t)leaf * 3 * kk;
+        } else {
+            cp.b[j] = nullptr;
+            cp.c[j] = nullptr;
+        }
+        cp.scale[j] = 1.0;
+    }
+    __syncthreads();
+    gemm_tile_fp64(L2T, 3 * kk, P2, blockIdx.x * GBM, ncols, cp);
+}
+
+// ---------------------------------------------------------------- M2M (one warp per box)
+__global__ void m2m_kernel(int begin, int end, int P, const int32_t* __restrict__ child0,
+                           const double* __restrict__ m2m_t, double* __restrict__ Mexp) {
+    extern __shared__ double sm[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int wpb = blockDim.x / 32;
+    const int b = begin + blockIdx.x * wpb + warp;
+    double* a = sm + (size_t)warp * 4 * 2 * P;
+    const bool live = b < end && child0[b] >= 0;
+    if (live) {
+        const int c0 = child0[b];
+        for (int q = lane; q < 4 * 2 * P; q += 32) a[q] = Mexp[(size_t)(c0 + q / (2 * P)) * 2 * P + q % (2 * P)];
+    }
+    __syncwarp();
+    if (!live) return;
+    for (int out = lane; out < P; out += 32) {
+        double re = 0.0, im = 0.0;
+        for (int pos = 0; pos < 4; ++pos) {
+            const double* ac = a + pos * 2 * P;
+            const double* M = m2m_t + (size_t)pos * P * P * 2;
+            for (int n = 0; n <= out; ++n) {
+                double mr = M[((size_t)n * P + out) * 2], mi = M[((size_t)n * P + out) * 2 + 1];
+                double xr = ac[2 * n], xi = ac[2 * n + 1];
+                re = fma(mr, xr, fma(-mi, xi, re));
+                im = fma(mr, xi, fma(mi, xr, im));
+            }
+        }
+        Mexp[(size_t)b * 2 * P + 2 * out] = re;
+        Mexp[(size_t)b * 2 * P + 2 * out + 1] = im;
+    }
+}
+
+// ---------------------------------------------------------------- downward pass (one CTA per box)
+struct DownArgs {
+    int begin, end, P, kk, level;
+    double width;
+    const int32_t* parent;
+    const int32_t* ix;
+    const int32_t* iy;
+    const int32_t *vptr, *vidx, *vcfg;
+    const int32_t *xptr, *xidx, *xcfg;
+    const int32_t* leaf_of_box;
+    const double* l2l_t;
+    const double* m2l_t;
+    const double* s2l_t;
+    const double* Mexp;
+    const double* f;
+    double* Lexp;
+};
+
+__global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
+    __shared__ double src[2 * 256];
+    const int b = d.begin + blockIdx.x;
+    if (b >= d.end) return;
+    const int P = d.P, t = threadIdx.x;
+    const double h = ldexp(d.width, -d.level);
+    const double logh = log(h);
+    double re = 0.0, im = 0.0;
+    if (d.level >= 3) {
+        const int par = d.parent[b];
+        for (int q = t; q < 2 * P; q += blockDim.x) src[q] = d.Lexp[(size_t)par * 2 * P + q];
+        __syncthreads();
+        const int pos = ((d.iy[b] & 1) << 1) | (d.ix[b] & 1);
+        const double* M = d.l2l_t + (size_t)pos * P * P * 2;
+        if (t < P)
+            for (int m = t; m < P; ++m) {  // c_t = sum_{m >= t}
+                double mr = M[((size_t)m * P + t) * 2], mi = M[((size_t)m * P + t) * 2 + 1];
+                double xr = src[2 * m], xi = src[2 * m + 1];
+                re = fma(mr, xr, fma(-mi, xi, re));
+                im = fma(mr, xi, fma(mi, xr, im));
+            }
+        __syncthreads();
+    }
+    for (int e = d.vptr[b]; e < d.vptr[b + 1]; ++e) {
+        const int c = d.vidx[e];
+        for (int q = t; q < 2 * P; q += blockDim.x) src[q] = d.Mexp[(size_t)c * 2 * P + q];
+        __syncthreads();
+        const double* M = d.m2l_t + (size_t)d.vcfg[e] * P * P * 2;
+        if (t < P) {
+            for (int n = 0; n < P; ++n) {
+                double mr = M[((size_t)n * P + t) * 2], mi = M[((size_t)n * P + t) * 2 + 1];
+                double xr = src[2 * n], xi = src[2 * n + 1];
+                re = fma(mr, xr, fma(-mi, xi, re));
+                im = fma(mr, xi, fma(mi, xr, im));
+            }
+            if (t == 0) re += src[0] * logh;
+        }
+        __syncthreads();
+    }
+    for (int e = d.xptr[b]; e < d.xptr[b + 1]; ++e) {
+        const int c = d.xidx[e];
+        const double* fc = d.f + (size_t)d.leaf_of_box[c] * d.kk;
+        for (int q = t; q < d.kk; q += blockDim.x) src[q] = fc[q];
+        __syncthreads();
+        const double* R = d.s2l_t + (size_t)d.xcfg[e] * d.kk * P * 2;
+        if (t < P) {
+            double sr = 0.0, si = 0.0;
+            for (int s = 0; s < d.kk; ++s) {
+                sr = fma(R[((size_t)s * P + t) * 2], src[s], sr);
+                si = fma(R[((size_t)s * P + t) * 2 + 1], src[s], si);
+            }
+            const double hc2 = 4.0 * h * h;
+            re += hc2 * sr;
+            im += hc2 * si;
+            if (t == 0) re += logh * d.Mexp[(size_t)c * 2 * P];
+        }
+        __syncthreads();
+    }
+    if (t < P) {
+        d.Lexp[(size_t)b * 2 * P + 2 * t] = re;
+        d.Lexp[(size_t)b * 2 * P + 2 * t + 1] = im;
+    }
+}
+
+// ---------------------------------------------------------------- leaf pass (one CTA per leaf)
+struct LeafArgs {
+    int nleaf, kk, k, P;
+    double width;
+    const int32_t* box_of_leaf;
+    const int32_t* level;
+    const int32_t *uptr, *uidx;
+    const int32_t *wptr, *widx, *wcfg;
+    const double* xhat;
+    const double* slab;
+    const double* far;
+    const double* Mexp;
+    double* u;
+    double* ux;
+    double* uy;
+};
+
+__global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
+    __shared__ double sa[2 * 64];
+    const int leaf = blockIdx.x;
+    const int t = threadIdx.x;
+    const int kk = a.kk, P = a.P;
+    const bool act = t < kk;
+    const int b = a.box_of_leaf[leaf];
+    const double h = ldexp(a.width, -a.level[b]);
+    double u = 0.0, gx = 0.0, gy = 0.0, mass = 0.0;
+    for (int e = a.uptr[b]; e < a.uptr[b + 1]; ++e) {
+        if (act) {
+            const double* s = a.slab + (size_t)e * 3 * kk;
+            u += s[t];
+            gx += s[kk + t];
+            gy += s[2 * kk + t];
+        }
+        mass += a.Mexp[(size_t)a.uidx[e] * 2 * P];
+    }
+    u = h * h * u - kInv2Pi * log(h) * mass;
+    gx *= h;
+    gy *= h;
+    if (act) {
+        const double* fr = a.far + (size_t)leaf * 3 * kk;
+        u += fr[t];
+        gx += fr[kk + t] / h;
+        gy += fr[2 * kk + t] / h;
+    }
+    const double xt = act ? a.xhat[t % a.k] : 0.0, yt = act ? a.xhat[t / a.k] : 0.0;
+    const double hw = 0.5 * h;
+    for (int e = a.wptr[b]; e < a.wptr[b + 1]; ++e) {
+        const int w = a.widx[e];
+        for (int q = t; q < 2 * P; q += blockDim.x) sa[q] = a.Mexp[(size_t)w * 2 * P + q];
+        __syncthreads();
+        if (act) {
+            int px, py;
+            far_pattern(a.wcfg[e], &px, &py);
+            // zeta = (z - z_w)/h_w = 2 (xhat - D), D = (px, py)/4
+            double zr = 2.0 * (xt - px / 4.0), zi = 2.0 * (yt - py / 4.0);
+            double r2 = zr * zr + zi * zi;
+            double vr = zr / r2, vi = -zi / r2;  // z^-1
+            // S = sum_{n>=1} a_n v^n and S' = sum n a_n v^n by Horner
+            double Sr = 0.0, Si = 0.0, Tr = 0.0, Ti = 0.0;
+            for (int n = P - 1; n >= 1; --n) {
+                double ar = sa[2 * n], ai = sa[2 * n + 1];
+                double nr = Sr + ar, ni = Si + ai;
+                Sr = nr * vr - ni * vi;
+                Si = nr * vi + ni * vr;
+                double mr = Tr + n * ar, mi = Ti + n * ai;
+                Tr = mr * vr - mi * vi;
+                Ti = mr * vi + mi * vr;
+            }
+            const double a0r = sa[0], a0i = sa[1];
+            const double lz = 0.5 * log(r2), th = atan2(zi, zr);
+            // Re Phi = Re(a0 (log h_w + log zeta)) + Re S
+            double phir = a0r * (log(hw) + lz) - a0i * th + Sr;
+            // dPhi/dzeta = v (a0 - S'), Phi' = dPhi/dzeta / h_w
+            double dr = a0r - Tr, di = a0i - Ti;
+            double pr = (vr * dr - vi * di) / hw, pi = (vr * di + vi * dr) / hw;
+            u += -kInv2Pi * phir;
+            gx += -kInv2Pi * pr;
+            gy += kInv2Pi * pi;
+        }
+        __syncthreads();
+    }
+    if (act) {
+        const size_t o = (size_t)leaf * kk + t;
+        a.u[o] = u;
+        a.ux[o] = gx;
+        a.uy[o] = gy;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+struct Workspace {
+    double* Mexp;
+    double* Lexp;
+    double* slab;
+    double* far;
+    double* io;  // f, u, ux, uy copies for the host entry point
+    size_t bytes;
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static size_t layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Workspace* w, char* base) {
+    const size_t P2 = 2 * (size_t)(o.p + 1), kk = (size_t)o.k * o.k;
+    size_t off = 0;
+    auto take = [&](double** p, size_t n) {
+        if (w) *p = (double*)(base + off);
+        off += align256(std::max<size_t>(1, n) * sizeof(double));
+    };
+    double* dummy;
+    take(w ? &w->Mexp : &dummy, (size_t)T.n_boxes * P2);
+    take(w ? &w->Lexp : &dummy, (size_t)T.n_boxes * P2);
+    take(w ? &w->slab : &dummy, (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
+    take(w ? &w->far : &dummy, (size_t)T.n_leaves * 3 * kk);
+    if (io) take(w ? &w->io : &dummy, (size_t)4 * nrhs * T.n_leaves * kk);
+    else if (w) w->io = nullptr;
+    if (w) w->bytes = off;
+    return off;
+}
+
+int build_near_tiles(DeviceTree* T) {
+    std::vector<int4> tiles;
+    for (int c = 0; c < kNearCfg; ++c)
+        for (int64_t b = T->u_cfg_start[c]; b < T->u_cfg_start[c + 1]; b += GBN)
+            tiles.push_back(make_int4(c, (int)b, (int)std::min<int64_t>(b + GBN, T->u_cfg_start[c + 1]), 0));
+    T->n_near_tiles = (int)tiles.size();
+    if (T->near_tiles) cudaFree(T->near_tiles);
+    T->near_tiles = nullptr;
+    VFMM_CUDA(cudaMalloc(&T->near_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int4)));
+    VFMM_CUDA(cudaMemcpy(T->near_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    return VFMM_OK;
+}
+
+// Optional stage timing: events[i] is recorded before stage i (and events[6] at the end).
+struct StageEvents {
+    cudaEvent_t ev[VFMM_N_STAGES + 1];
+    int launches = 0;
+};
+
+static inline void mark(StageEvents* se, int i, cudaStream_t st) {
+    if (se) cudaEventRecord(se->ev[i], st);
+}
+
+static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, double* u, double* ux, double* uy,
+                     const Workspace& w, cudaStream_t st, StageEvents* se = nullptr) {
+    const int P = o.p + 1, P2 = 2 * P, kk = o.k * o.k;
+    const int nleaf = T.n_leaves;
+    int launches = 0;
+    mark(se, 0, st);
+    // S2M
+    {
+        ++launches;
+        dim3 g((P2 + GBM - 1) / GBM, (nleaf + GBN - 1) / GBN);
+        s2m_gemm_kernel<<<g, 256, 0, st>>>(o.s2m, P2, kk, nleaf, T.box_of_leaf, T.level, T.width, f, w.Mexp);
+    }
+    mark(se, 1, st);
+    // M2M, finest parents first (levels >= 2 are the ones the lists read)
+    for (int l = T.depth - 1; l >= 2; --l) {
+        int begin = T.level_start[l], end = T.level_start[l + 1];
+        int wpb = 4;
+        int nb = (end - begin + wpb - 1) / wpb;
+        if (nb > 0) ++launches;
+        if (nb > 0)
+            m2m_kernel<<<nb, 32 * wpb, (size_t)wpb * 4 * P2 * sizeof(double), st>>>(begin, end, P, T.child0, o.m2m_t,
+                                                                                   w.Mexp);
+    }
+    mark(se, 2, st);
+    // downward pass
+    for (int l = 2; l <= T.depth; ++l) {
+        DownArgs d;
+        d.begin = T.level_start[l];
+        d.end = T.level_start[l + 1];
+        d.P = P;
+        d.kk = kk;
+        d.level = l;
+        d.width = T.width;
+        d.parent = T.parent;
+        d.ix = T.ix;
+        d.iy = T.iy;
+        d.vptr = T.lptr[VFMM_LIST_V];
+        d.vidx = T.lidx[VFMM_LIST_V];
+        d.vcfg = T.lcfg[VFMM_LIST_V];
+        d.xptr = T.lptr[VFMM_LIST_X];
+        d.xidx = T.lidx[VFMM_LIST_X];
+        d.xcfg = T.lcfg[VFMM_LIST_X];
+        d.leaf_of_box = T.leaf_of_box;
+        d.l2l_t = o.l2l_t;
+        d.m2l_t = o.m2l_t;
+        d.s2l_t = o.s2l_t;
+        d.Mexp = w.Mexp;
+        d.f = f;
+        d.Lexp = w.Lexp;
+        int n = d.end - d.begin;
+        if (n > 0) {
+            ++launches;
+            down_kernel<<<n, 64, 0, st>>>(d);
+        }
+    }
+    if (T.depth < 2) VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.n_boxes * P2 * sizeof(double), st));
+    else VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.level_start[2] * P2 * sizeof(double), st));
+    mark(se, 3, st);
+    // near field
+    if (T.n_near_tiles > 0) {
+        ++launches;
+        dim3 g((3 * kk + GBM - 1) / GBM, T.n_near_tiles);
+        near_gemm_kernel<<<g, 256, 0, st>>>((const int4*)T.near_tiles, o.near, kk, T.u_by_cfg, T.lidx[VFMM_LIST_U],
+                                            T.leaf_of_box, f, w.slab);
+    }
+    mark(se, 4, st);
+    // far field at the leaves
+    {
+        ++launches;
+        dim3 g((3 * kk + GBM - 1) / GBM, (nleaf + GBN - 1) / GBN);
+        l2t_gemm_kernel<<<g, 256, 0, st>>>(o.l2t, P2, kk, nleaf, T.box_of_leaf, w.Lexp, w.far);
+    }
+    mark(se, 5, st);
+    LeafArgs a;
+    a.nleaf = nleaf;
+    a.kk = kk;
+    a.k = o.k;
+    a.P = P;
+    a.width = T.width;
+    a.box_of_leaf = T.box_of_leaf;
+    a.level = T.level;
+    a.uptr = T.lptr[VFMM_LIST_U];
+    a.uidx = T.lidx[VFMM_LIST_U];
+    a.wptr = T.lptr[VFMM_LIST_W];
+    a.widx = T.lidx[VFMM_LIST_W];
+    a.wcfg = T.lcfg[VFMM_LIST_W];
+    a.xhat = o.xhat;
+    a.slab = w.slab;
+    a.far = w.far;
+    a.Mexp = w.Mexp;
+    a.u = u;
+    a.ux = ux;
+    a.uy = uy;
+    leaf_kernel<<<nleaf, ((kk + 31) / 32) * 32, 0, st>>>(a);
+    ++launches;
+    mark(se, 6, st);
+    VFMM_CUDA(cudaGetLastError());
+    if (se) se->launches += launches;
+    return VFMM_OK;
+}
+
+}  // namespace vfmm
+
+using namespace vfmm;
+
+static int check_solve_args(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs) {
+    if (!tree || !ops) return fail(VFMM_ERR_INVALID_ARG, "null tree or ops");
+    if (tree->t.k != ops->k) return fail(VFMM_ERR_INVALID_ARG, "tree and ops differ in k");
+    if (nrhs < 1) return fail(VFMM_ERR_INVALID_ARG, "nrhs must be >= 1");
+    if (ops->p + 1 > 64) return fail(VFMM_ERR_INVALID_ARG, "p too large for the solve kernels");
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_workspace_size(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs, int32_t with_io,
+                                   size_t* bytes) {
+    VFMM_CHECK(check_solve_args(tree, ops, nrhs));
+    if (!bytes) return fail(VFMM_ERR_INVALID_ARG, "null bytes");
+    *bytes = layout(tree->t, *ops, nrhs, with_io != 0, nullptr, nullptr);
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
+                                     double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
+                                     size_t workspace_bytes, void* stream) {
+    VFMM_CHECK(check_solve_args(tree, ops, nrhs));
+    if (!f_dev || !u_dev || !ux_dev || !uy_dev || !workspace_dev) return fail(VFMM_ERR_INVALID_ARG, "null buffer");
+    Workspace w;
+    size_t need = layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev);
+    if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small");
+    const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
+    for (int r = 0; r < nrhs; ++r)
+        VFMM_CHECK(solve_one(tree->t, *ops, f_dev + r * n, u_dev + r * n, ux_dev + r * n, uy_dev + r * n, w,
+                             (cudaStream_t)stream));
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_host,
+                                          int32_t nrhs, double* u_host, double* ux_host, double* uy_host,
+                                          void* workspace_dev, size_t workspace_bytes, void* stream) {
+    VFMM_CHECK(check_solve_args(tree, ops, nrhs));
+    if (!f_host || !u_host || !ux_host || !uy_host || !workspace_dev) return fail(VFMM_ERR_INVALID_ARG, "null buffer");
+    Workspace w;
+    size_t need = layout(tree->t, *ops, nrhs, true, &w, (char*)workspace_dev);
+    if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small (with_io = 1 required)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k * nrhs;
+    double* f = w.io;
+    double* u = w.io + n;
+    double* ux = w.io + 2 * n;
+    double* uy = w.io + 3 * n;
+    VFMM_CUDA(cudaMemcpyAsync(f, f_host, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    const size_t m = (size_t)tree->t.n_leaves * ops->k * ops->k;
+    for (int r = 0; r < nrhs; ++r)
+        VFMM_CHECK(solve_one(tree->t, *ops, f + r * m, u + r * m, ux + r * m, uy + r * m, w, st));
+    VFMM_CUDA(cudaMemcpyAsync(u_host, u, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    VFMM_CUDA(cudaMemcpyAsync(ux_host, ux, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    VFMM_CUDA(cudaMemcpyAsync(uy_host, uy, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    VFMM_CUDA(cudaStreamSynchronize(st));
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev,
+                                              int32_t nrhs, double* u_dev, double* ux_dev, double* uy_dev,
+                                              void* workspace_dev, size_t workspace_bytes, void* stream,
+                                              float* stage_ms, int32_t* launches) {
+    VFMM_CHECK(check_solve_args(tree, ops, nrhs));
+    if (!f_dev || !u_dev || !ux_dev || !uy_dev || !workspace_dev || !stage_ms || !launches)
+        return fail(VFMM_ERR_INVALID_ARG, "null buffer");
+    Workspace w;
+    size_t need = layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev);
+    if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    StageEvents se;
+    for (int i = 0; i <= VFMM_N_STAGES; ++i) VFMM_CUDA(cudaEventCreate(&se.ev[i]));
+    for (int i = 0; i < VFMM_N_STAGES; ++i) stage_ms[i] = 0.0f;
+    const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
+    int rc = VFMM_OK;
+    for (int r = 0; r < nrhs && rc == VFMM_OK; ++r) {
+        rc = solve_one(tree->t, *ops, f_dev + r * n, u_dev + r * n, ux_dev + r * n, uy_dev + r * n, w, st, &se);
+        if (rc != VFMM_OK) break;
+        cudaError_t e = cudaEventSynchronize(se.ev[VFMM_N_STAGES]);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "cudaEventSynchronize");
+            break;
+        }
+        for (int i = 0; i < VFMM_N_STAGES; ++i) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, se.ev[i], se.ev[i + 1]);
+            stage_ms[i] += ms;
+        }
+    }
+    for (int i = 0; i <= VFMM_N_STAGES; ++i) cudaEventDestroy(se.ev[i]);
+    *launches = se.launches;
+    return rc;
+}

@@ -1,0 +1,876 @@
+// Quadtree build, level restriction and interaction lists on the device (Section 3.1).
+//
+// Build plan (host-driven loop over levels, device work per level):
+//   1. F = max |f| over the nodes of the uniform level-min(5, max_depth) tree.
+//   2. Refinement, level by level: one CTA per candidate box samples f at its k*k
+//      nodes, forms the 2-D Chebyshev coefficients, and flags the box when the
+//      largest trailing coefficient exceeds tol * F. A scan of the flags places the
+//      children; children of a Morton-sorted level are again Morton-sorted.
+//   3. Level restriction, finest level first: every box at level l requires the
+//      level-(l-1) cells adjacent to it; their parents are marked in a bitmap over
+//      the level-(l-2) grid (together with the parents of the existing level-(l-1)
+//      boxes), the bitmap is compacted in Morton order, and level l-1 is rebuilt as
+//      the children of the marked boxes. Every added box is forced, so the result is
+//      the minimal balanced refinement.
+//   4. Canonical numbering (level, Morton), parent/child links, leaf ranks.
+//   5. U/V/W/X lists: one thread per box, neighbour lookups by binary search in the
+//      Morton-sorted key array of a level, a count pass and a fill pass.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "source.cuh"
+#include "vfmm_internal.cuh"
+
+namespace vfmm {
+
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) {
+            reset();
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { reset(); }
+    void reset() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    int alloc(size_t count) {
+        reset();
+        n = count;
+        if (count == 0) return VFMM_OK;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(VFMM_ERR_OOM, "cudaMalloc failed in tree build");
+        }
+        return VFMM_OK;
+    }
+    T* release() {
+        T* q = p;
+        p = nullptr;
+        n = 0;
+        return q;
+    }
+};
+
+// ---------------------------------------------------------------- scan (exclusive, int32)
+constexpr int kScanItems = 1024;
+
+__global__ void scan_blocks_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                   int32_t* __restrict__ sums, int64_t n) {
+    __shared__ int32_t s[256];
+    const int64_t base = (int64_t)blockIdx.x * kScanItems;
+    const int t = threadIdx.x;
+    int32_t v[4];
+    int32_t local = 0;
+    for (int i = 0; i < 4; ++i) {
+        int64_t g = base + t * 4 + i;
+        v[i] = g < n ? in[g] : 0;
+        local += v[i];
+    }
+    s[t] = local;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        int32_t x = t >= off ? s[t - off] : 0;
+        __syncthreads();
+        s[t] += x;
+        __syncthreads();
+    }
+    int32_t run = s[t] - local;
+    for (int i = 0; i < 4; ++i) {
+        int64_t g = base + t * 4 + i;
+        if (g < n) out[g] = run;
+        run += v[i];
+    }
+    if (t == 255) sums[blockIdx.x] = s[255];
+}
+
+__global__ void scan_add_kernel(int32_t* __restrict__ out, const int32_t* __restrict__ offs, int64_t n) {
+    const int64_t base = (int64_t)blockIdx.x * kScanItems;
+    const int32_t o = offs[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanItems; i += blockDim.x) {
+        int64_t g = base + i;
+        if (g < n) out[g] += o;
+    }
+}
+
+// out[i] = sum_{j < i} in[j]; *total = sum of all (host). `in` and `out` may alias.
+static int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* total, cudaStream_t st) {
+    if (n <= 0) {
+        *total = 0;
+        return VFMM_OK;
+    }
+    int64_t nb = (n + kScanItems - 1) / kScanItems;
+    DBuf<int32_t> sums, sums_x;
+    VFMM_CHECK(sums.alloc(nb));
+    scan_blocks_kernel<<<(unsigned)nb, 256, 0, st>>>(in, out, sums.p, n);
+    VFMM_CUDA(cudaGetLastError());
+    if (nb == 1) {
+        int32_t h = 0;
+        VFMM_CUDA(cudaMemcpyAsync(&h, sums.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        VFMM_CUDA(cudaStreamSynchronize(st));
+        *total = h;
+        return VFMM_OK;
+    }
+    VFMM_CHECK(sums_x.alloc(nb));
+    VFMM_CHECK(exclusive_scan(sums.p, sums_x.p, nb, total, st));
+    scan_add_kernel<<<(unsigned)nb, 256, 0, st>>>(out, sums_x.p, n);
+    VFMM_CUDA(cudaGetLastError());
+    return VFMM_OK;
+}
+
+// ---------------------------------------------------------------- leaf geometry
+struct NodeGeom {
+    double lox, loy, width;
+    int k;
+    const double* xhat;  // [k] device
+};
+
+// x = lo + ((i_box + 0.5) + xhat) * h, rounded step by step (no contraction).
+__device__ inline double node_coord(double lo, int ib, double xh, double h) {
+    return __dadd_rn(lo, __dmul_rn(__dadd_rn(__dadd_rn((double)ib, 0.5), xh), h));
+}
+
+// ---------------------------------------------------------------- refinement
+__device__ inline void atomic_max_nonneg(double* addr, double v) {
+    atomicMax((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
+}
+__device__ inline void atomic_min_nonneg(double* addr, double v) {
+    atomicMin((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void fscale_kernel(NodeGeom g, SourceDev src, int level, double* fmax_out) {
+    const int side = 1 << level;
+    const int b = blockIdx.x;
+    const int ix = b % side, iy = b / side;
+    const double h = ldexp(g.width, -level);
+    double m = 0.0;
+    for (int t = threadIdx.x; t < g.k * g.k; t += blockDim.x) {
+        int i = t % g.k, j = t / g.k;
+        double x = node_coord(g.lox, ix, g.xhat[i], h);
+        double y = node_coord(g.loy, iy, g.xhat[j], h);
+        m = fmax(m, fabs(source_eval(src, x, y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(fmax_out, m);
+}
+
+// One CTA per candidate box, blockDim = k*k rounded up to a multiple of 32.
+// C[m*k + i] = (2 - delta_m0)/k T_m(t_i).
+__global__ void refine_kernel(NodeGeom g, SourceDev src, int level, const uint32_t* __restrict__ keys, int n,
+                              const double* __restrict__ C, double thresh, int32_t* __restrict__ flags,
+                              double* __restrict__ min_margin) {
+    __shared__ double V[16 * 16];
+    __shared__ double Tm[16 * 16];
+    __shared__ double red[8];
+    const int b = blockIdx.x;
+    const int k = g.k;
+    const int t = threadIdx.x;
+    const bool active = t < k * k;
+    int ix, iy;
+    morton_decode(keys[b], &ix, &iy);
+    const double h = ldexp(g.width, -level);
+    const int i = t % k, j = t / k;
+    if (active)
+        V[j * k + i] = source_eval(src, node_coord(g.lox, ix, g.xhat[i], h), node_coord(g.loy, iy, g.xhat[j], h));
+    __syncthreads();
+    // Tm[m][i] = sum_q C[m][q] V[q][i], thread (m = j, i)
+    if (active) {
+        double acc = 0.0;
+        for (int q = 0; q < k; ++q) acc += C[j * k + q] * V[q * k + i];
+        Tm[j * k + i] = acc;
+    }
+    __syncthreads();
+    // c[m][nn] = sum_q Tm[m][q] C[nn][q], thread (m = j, nn = i); trailing entries only
+    double tail = 0.0;
+    if (active && (j >= k - 2 || i >= k - 2)) {
+        double acc = 0.0;
+        for (int q = 0; q < k; ++q) acc += Tm[j * k + q] * C[i * k + q];
+        tail = fabs(acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) tail = fmax(tail, __shfl_xor_sync(0xffffffffu, tail, o));
+    const int nw = blockDim.x / 32;
+    if ((t & 31) == 0) red[t >> 5] = tail;
+    __syncthreads();
+    if (t == 0 && b < n) {
+        double mx = 0.0;
+        for (int w = 0; w < nw; ++w) mx = fmax(mx, red[w]);
+        flags[b] = mx > thresh ? 1 : 0;
+        if (thresh > 0.0) atomic_min_nonneg(min_margin, fabs(mx / thresh - 1.0));
+    }
+}
+
+__global__ void fill_kernel(int32_t* a, int64_t n, int32_t v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+__global__ void emit_children_kernel(const uint32_t* __restrict__ keys, const int32_t* __restrict__ flags,
+                                     const int32_t* __restrict__ offs, int n, uint32_t* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flags[i]) return;
+    uint32_t base = keys[i] << 2;
+    int o = offs[i] * 4;
+    for (int c = 0; c < 4; ++c) out[o + c] = base | (uint32_t)c;
+}
+
+__global__ void children_of_kernel(const uint32_t* __restrict__ parents, int n, uint32_t* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t base = parents[i] << 2;
+    for (int c = 0; c < 4; ++c) out[4 * i + c] = base | (uint32_t)c;
+}
+
+// ---------------------------------------------------------------- level restriction
+// Marks in the level-(l-2) bitmap: parents of every level-(l-1) box, and the
+// parents of every level-(l-1) cell adjacent to a level-l box (and of its parent).
+__global__ void balance_mark_kernel(const uint32_t* __restrict__ keys_l, int n_l,
+                                    const uint32_t* __restrict__ keys_lm1, int n_lm1, int l,
+                                    uint32_t* __restrict__ bitmap) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_lm1) {
+        uint32_t pk = keys_lm1[i] >> 2;
+        atomicOr(&bitmap[pk >> 5], 1u << (pk & 31));
+    }
+    if (i < n_l) {
+        int bx, by;
+        morton_decode(keys_l[i], &bx, &by);
+        int px = bx >> 1, py = by >> 1;
+        int side = 1 << (l - 1);
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int qx = px + dx, qy = py + dy;
+                if (qx < 0 || qy < 0 || qx >= side || qy >= side) continue;
+                if ((dx || dy) && !boxes_adjacent(l - 1, qx, qy, l, bx, by)) continue;
+                uint32_t pk = morton_encode((uint32_t)qx, (uint32_t)qy) >> 2;
+                atomicOr(&bitmap[pk >> 5], 1u << (pk & 31));
+            }
+    }
+}
+
+__global__ void popc_kernel(const uint32_t* __restrict__ bm, int64_t nw, int32_t* __restrict__ cnt) {
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < nw) cnt[w] = __popc(bm[w]);
+}
+
+__global__ void bitmap_emit_kernel(const uint32_t* __restrict__ bm, int64_t nw, const int32_t* __restrict__ offs,
+                                   uint32_t* __restrict__ out) {
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    uint32_t bits = bm[w];
+    int pos = offs[w];
+    while (bits) {
+        int b = __ffs(bits) - 1;
+        out[pos++] = (uint32_t)(w * 32 + b);
+        bits &= bits - 1;
+    }
+}
+
+// ---------------------------------------------------------------- finalisation
+__device__ inline int lower_bound_key(const uint32_t* key, int lo, int hi, uint32_t k) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (key[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ inline int find_box(const uint32_t* key, const int32_t* lstart, int depth, int l, int x, int y) {
+    if (l < 0 || l > depth) return -1;
+    int side = 1 << l;
+    if (x < 0 || y < 0 || x >= side || y >= side) return -1;
+    uint32_t k = morton_encode((uint32_t)x, (uint32_t)y);
+    int lo = lstart[l], hi = lstart[l + 1];
+    int p = lower_bound_key(key, lo, hi, k);
+    return (p < hi && key[p] == k) ? p : -1;
+}
+
+__global__ void box_setup_kernel(const uint32_t* __restrict__ key, const int32_t* __restrict__ lstart, int depth,
+                                 int n, int32_t* level, int32_t* ix, int32_t* iy, int32_t* parent, int32_t* child0,
+                                 int32_t* is_leaf) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    int l = 0;
+    while (l < depth && b >= lstart[l + 1]) ++l;
+    int x, y;
+    morton_decode(key[b], &x, &y);
+    level[b] = l;
+    ix[b] = x;
+    iy[b] = y;
+    parent[b] = l > 0 ? find_box(key, lstart, depth, l - 1, x >> 1, y >> 1) : -1;
+    int c = l < depth ? find_box(key, lstart, depth, l + 1, 2 * x, 2 * y) : -1;
+    child0[b] = c;
+    is_leaf[b] = c < 0 ? 1 : 0;
+}
+
+__global__ void leaf_rank_kernel(const int32_t* __restrict__ is_leaf, const int32_t* __restrict__ rank, int n,
+                                 int32_t* __restrict__ leaf_of_box, int32_t* __restrict__ box_of_leaf) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    if (is_leaf[b]) {
+        leaf_of_box[b] = rank[b];
+        box_of_leaf[rank[b]] = b;
+    } else {
+        leaf_of_box[b] = -1;
+    }
+}
+
+// ---------------------------------------------------------------- lists
+struct TreeView {
+    const uint32_t* key;
+    const int32_t* lstart;
+    const int32_t* level;
+    const int32_t* ix;
+    const int32_t* iy;
+    const int32_t* parent;
+    const int32_t* child0;
+    int depth;
+};
+
+struct Entries {
+    int n[4];
+    int idx[4][27];
+    int cfg[4][27];
+    __device__ void add(int list, int box, int c) {
+        idx[list][n[list]] = box;
+        cfg[list][n[list]] = c;
+        ++n[list];
+    }
+};
+
+__device__ inline void collect_lists(const TreeView& T, int b, Entries& E) {
+    E.n[0] = E.n[1] = E.n[2] = E.n[3] = 0;
+    const int l = T.level[b], a = T.ix[b], c = T.iy[b];
+    const bool leaf = T.child0[b] < 0;
+    int dx4, dy4;
+    if (leaf) {
+        E.add(VFMM_LIST_U, b, 4);
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (!dx && !dy) continue;
+                int q = find_box(T.key, T.lstart, T.depth, l, a + dx, c + dy);
+                if (q < 0) continue;
+                if (T.child0[q] < 0) {
+                    E.add(VFMM_LIST_U, q, (dy + 1) * 3 + (dx + 1));
+                } else {
+                    for (int s = 0; s < 4; ++s) {
+                        int ch = T.child0[q] + s;
+                        centre_offset4(l, a, c, l + 1, T.ix[ch], T.iy[ch], &dx4, &dy4);
+                        if (boxes_adjacent(l, a, c, l + 1, T.ix[ch], T.iy[ch]))
+                            E.add(VFMM_LIST_U, ch, 21 + near_pattern_index(dx4, dy4));
+                        else
+                            E.add(VFMM_LIST_W, ch, far_pattern_index(dx4, dy4));
+                    }
+                }
+            }
+        if (l >= 1) {
+            int pa = a >> 1, pc = c >> 1;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (!dx && !dy) continue;
+                    int q = find_box(T.key, T.lstart, T.depth, l - 1, pa + dx, pc + dy);
+                    if (q < 0 || T.child0[q] >= 0) continue;
+                    if (!boxes_adjacent(l, a, c, l - 1, pa + dx, pc + dy)) continue;
+                    centre_offset4(l, a, c, l - 1, pa + dx, pc + dy, &dx4, &dy4);
+                    E.add(VFMM_LIST_U, q, 9 + near_pattern_index(dx4 / 2, dy4 / 2));
+                }
+        }
+    }
+    if (l >= 2) {
+        int pa = a >> 1, pc = c >> 1;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int q = find_box(T.key, T.lstart, T.depth, l - 1, pa + dx, pc + dy);
+                if (q < 0) continue;
+                if (T.child0[q] < 0) {
+                    if ((dx || dy) && !boxes_adjacent(l, a, c, l - 1, pa + dx, pc + dy)) {
+                        centre_offset4(l, a, c, l - 1, pa + dx, pc + dy, &dx4, &dy4);
+                        E.add(VFMM_LIST_X, q, far_pattern_index(dx4 / 2, dy4 / 2));
+                    }
+                    continue;
+                }
+                for (int s = 0; s < 4; ++s) {
+                    int ch = T.child0[q] + s;
+                    if (ch == b || boxes_adjacent(l, a, c, l, T.ix[ch], T.iy[ch])) continue;
+                    E.add(VFMM_LIST_V, ch, v_offset_index(T.ix[ch] - a, T.iy[ch] - c));
+                }
+            }
+    }
+}
+
+__global__ void list_count_kernel(TreeView T, int n, int32_t* __restrict__ cnt) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    Entries E;
+    collect_lists(T, b, E);
+    for (int q = 0; q < 4; ++q) cnt[(int64_t)q * n + b] = E.n[q];
+}
+
+__global__ void list_fill_kernel(TreeView T, int n, const int32_t* __restrict__ off, int32_t* __restrict__ idxU,
+                                 int32_t* __restrict__ cfgU, int32_t* __restrict__ idxV, int32_t* __restrict__ cfgV,
+                                 int32_t* __restrict__ idxW, int32_t* __restrict__ cfgW, int32_t* __restrict__ idxX,
+                                 int32_t* __restrict__ cfgX) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    Entries E;
+    collect_lists(T, b, E);
+    int32_t* idxs[4] = {idxU, idxV, idxW, idxX};
+    int32_t* cfgs[4] = {cfgU, cfgV, cfgW, cfgX};
+    for (int q = 0; q < 4; ++q) {
+        // insertion sort by box index
+        for (int i = 1; i < E.n[q]; ++i) {
+            int vi = E.idx[q][i], vc = E.cfg[q][i], j = i - 1;
+            while (j >= 0 && E.idx[q][j] > vi) {
+                E.idx[q][j + 1] = E.idx[q][j];
+                E.cfg[q][j + 1] = E.cfg[q][j];
+                --j;
+            }
+            E.idx[q][j + 1] = vi;
+            E.cfg[q][j + 1] = vc;
+        }
+        int o = off[(int64_t)q * n + b];
+        for (int i = 0; i < E.n[q]; ++i) {
+            idxs[q][o + i] = E.idx[q][i];
+            cfgs[q][o + i] = E.cfg[q][i];
+        }
+    }
+}
+
+__global__ void ptr_from_offsets_kernel(const int32_t* __restrict__ off, int n, int64_t total, int32_t* __restrict__ ptr) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n) ptr[b] = off[b];
+    if (b == n) ptr[n] = (int32_t)total;
+}
+
+__global__ void shift_kernel(int32_t* a, int64_t n, int32_t s) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] -= s;
+}
+
+__global__ void cfg_flags_kernel(const int32_t* __restrict__ cfg, int64_t n, int ncfg, int32_t* __restrict__ flags) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int c = cfg[e];
+    for (int j = 0; j < ncfg; ++j) flags[(int64_t)j * n + e] = (j == c) ? 1 : 0;
+}
+
+__global__ void cfg_scatter_kernel(const int32_t* __restrict__ cfg, const int32_t* __restrict__ pos, int64_t n,
+                                   int32_t* __restrict__ out) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    out[pos[(int64_t)cfg[e] * n + e]] = (int32_t)e;
+}
+
+__global__ void entry_target_kernel(const int32_t* __restrict__ ptr, int n, int32_t* __restrict__ tgt) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    for (int e = ptr[b]; e < ptr[b + 1]; ++e) tgt[e] = b;
+}
+
+static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- host orchestration
+struct BuildCtx {
+    cudaStream_t st;
+    NodeGeom g;
+    DBuf<double> xhat;
+    DBuf<double> C;
+};
+
+static int upload_node_tables(int k, BuildCtx& B) {
+    std::vector<double> xh(k), C(k * k);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < k; ++i) xh[i] = -std::cos(pi * (2.0 * i + 1.0) / (2.0 * k)) / 2.0;
+    for (int m = 0; m < k; ++m)
+        for (int i = 0; i < k; ++i) {
+            double t = 2.0 * xh[i];
+            double v = std::cos(m * std::acos(std::min(1.0, std::max(-1.0, t))));
+            C[m * k + i] = (m == 0 ? 1.0 : 2.0) / k * v;
+        }
+    VFMM_CHECK(B.xhat.alloc(k));
+    VFMM_CHECK(B.C.alloc(k * k));
+    VFMM_CUDA(cudaMemcpyAsync(B.xhat.p, xh.data(), k * sizeof(double), cudaMemcpyHostToDevice, B.st));
+    VFMM_CUDA(cudaMemcpyAsync(B.C.p, C.data(), k * k * sizeof(double), cudaMemcpyHostToDevice, B.st));
+    return VFMM_OK;
+}
+
+static int compute_lists(DeviceTree* T, cudaStream_t st) {
+    const int n = T->n_boxes;
+    TreeView V{T->key, T->level_start_dev, T->level, T->ix, T->iy, T->parent, T->child0, T->depth};
+    DBuf<int32_t> cnt;
+    VFMM_CHECK(cnt.alloc((size_t)4 * n));
+    list_count_kernel<<<nblk(n, 128), 128, 0, st>>>(V, n, cnt.p);
+    VFMM_CUDA(cudaGetLastError());
+    // one scan over the 4 concatenated count arrays; row q starts at total of rows < q
+    int64_t total = 0;
+    VFMM_CHECK(exclusive_scan(cnt.p, cnt.p, (int64_t)4 * n, &total, st));
+    int32_t starts[5];
+    for (int q = 0; q < 4; ++q)
+        VFMM_CUDA(cudaMemcpyAsync(&starts[q], cnt.p + (int64_t)q * n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    VFMM_CUDA(cudaStreamSynchronize(st));
+    starts[4] = (int32_t)total;
+    DBuf<int32_t> idx[4], cfg[4], ptr[4];
+    for (int q = 0; q < 4; ++q) {
+        T->llen[q] = starts[q + 1] - starts[q];
+        VFMM_CHECK(idx[q].alloc(std::max<int64_t>(1, T->llen[q])));
+        VFMM_CHECK(cfg[q].alloc(std::max<int64_t>(1, T->llen[q])));
+        VFMM_CHECK(ptr[q].alloc(n + 1));
+    }
+    // offsets within each list: subtract the row start
+    for (int q = 0; q < 4; ++q) {
+        shift_kernel<<<nblk(n), 256, 0, st>>>(cnt.p + (int64_t)q * n, n, starts[q]);
+        ptr_from_offsets_kernel<<<nblk(n + 1), 256, 0, st>>>(cnt.p + (int64_t)q * n, n, T->llen[q], ptr[q].p);
+    }
+    list_fill_kernel<<<nblk(n, 128), 128, 0, st>>>(V, n, cnt.p, idx[0].p, cfg[0].p, idx[1].p, cfg[1].p, idx[2].p,
+                                                   cfg[2].p, idx[3].p, cfg[3].p);
+    VFMM_CUDA(cudaGetLastError());
+    for (int q = 0; q < 4; ++q) {
+        T->lidx[q] = idx[q].release();
+        T->lcfg[q] = cfg[q].release();
+        T->lptr[q] = ptr[q].release();
+    }
+    // U entries grouped by configuration, stable (flattened config-major scan)
+    const int64_t nU = T->llen[VFMM_LIST_U];
+    DBuf<int32_t> flags, byc, tgt;
+    VFMM_CHECK(flags.alloc((size_t)kNearCfg * nU));
+    VFMM_CHECK(byc.alloc(std::max<int64_t>(1, nU)));
+    VFMM_CHECK(tgt.alloc(std::max<int64_t>(1, nU)));
+    cfg_flags_kernel<<<nblk(nU), 256, 0, st>>>(T->lcfg[0], nU, kNearCfg, flags.p);
+    VFMM_CUDA(cudaGetLastError());
+    int64_t tot = 0;
+    VFMM_CHECK(exclusive_scan(flags.p, flags.p, (int64_t)kNearCfg * nU, &tot, st));
+    cfg_scatter_kernel<<<nblk(nU), 256, 0, st>>>(T->lcfg[0], flags.p, nU, byc.p);
+    entry_target_kernel<<<nblk(n), 256, 0, st>>>(T->lptr[0], n, tgt.p);
+    VFMM_CUDA(cudaGetLastError());
+    T->u_cfg_start.assign(kNearCfg + 1, 0);
+    for (int c = 0; c < kNearCfg; ++c) {
+        int32_t v = 0;
+        VFMM_CUDA(cudaMemcpyAsync(&v, flags.p + (int64_t)c * nU, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        VFMM_CUDA(cudaStreamSynchronize(st));
+        T->u_cfg_start[c] = v;
+    }
+    T->u_cfg_start[kNearCfg] = nU;
+    T->u_by_cfg = byc.release();
+    T->u_tgt = tgt.release();
+    return build_near_tiles(T);
+}
+
+// Builds the tree. src == nullptr means a uniform tree of depth `uniform_depth`.
+static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_depth, cudaStream_t st,
+                 DeviceTree* T) {
+    const int k = prm->k;
+    BuildCtx B;
+    B.st = st;
+    VFMM_CHECK(upload_node_tables(k, B));
+    B.g = NodeGeom{prm->cx - prm->width / 2.0, prm->cy - prm->width / 2.0, prm->width, k, B.xhat.p};
+    const bool uniform = src == nullptr;
+    const int max_depth = uniform ? uniform_depth : prm->max_depth;
+    const int min_depth = uniform ? uniform_depth : prm->min_depth;
+
+    T->k = k;
+    T->cx = prm->cx;
+    T->cy = prm->cy;
+    T->width = prm->width;
+
+    DBuf<double> scal;  // [0] = F, [1] = min margin
+    VFMM_CHECK(scal.alloc(2));
+    double init[2] = {0.0, INFINITY};
+    VFMM_CUDA(cudaMemcpyAsync(scal.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    double thresh = 0.0;
+    if (!uniform) {
+        int m0 = std::min(5, max_depth);
+        fscale_kernel<<<1u << (2 * m0), 128, 0, st>>>(B.g, *src, m0, scal.p);
+        VFMM_CUDA(cudaGetLastError());
+        VFMM_CUDA(cudaMemcpyAsync(&T->f_scale, scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        VFMM_CUDA(cudaStreamSynchronize(st));
+        thresh = prm->tol * T->f_scale;
+    }
+
+    std::vector<DBuf<uint32_t>> keys(max_depth + 1);
+    std::vector<int64_t> cnt(max_depth + 1, 0);
+    VFMM_CHECK(keys[0].alloc(1));
+    uint32_t zero = 0;
+    VFMM_CUDA(cudaMemcpyAsync(keys[0].p, &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    cnt[0] = 1;
+    int depth = 0;
+    for (int l = 0; l < max_depth; ++l) {
+        const int64_t n = cnt[l];
+        DBuf<int32_t> flags, offs;
+        VFMM_CHECK(flags.alloc(n));
+        VFMM_CHECK(offs.alloc(n));
+        if (l < min_depth) {
+            fill_kernel<<<nblk(n), 256, 0, st>>>(flags.p, n, 1);
+        } else {
+            refine_kernel<<<(unsigned)n, ((k * k + 31) / 32) * 32, 0, st>>>(B.g, *src, l, keys[l].p, (int)n, B.C.p, thresh, flags.p,
+                                                         scal.p + 1);
+        }
+        VFMM_CUDA(cudaGetLastError());
+        int64_t m = 0;
+        VFMM_CHECK(exclusive_scan(flags.p, offs.p, n, &m, st));
+        if (m == 0) break;
+        VFMM_CHECK(keys[l + 1].alloc(4 * m));
+        emit_children_kernel<<<nblk(n), 256, 0, st>>>(keys[l].p, flags.p, offs.p, (int)n, keys[l + 1].p);
+        VFMM_CUDA(cudaGetLastError());
+        cnt[l + 1] = 4 * m;
+        depth = l + 1;
+    }
+    if (!uniform) {
+        double mm = 0;
+        VFMM_CUDA(cudaMemcpyAsync(&mm, scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        VFMM_CUDA(cudaStreamSynchronize(st));
+        T->min_margin = mm;
+    }
+
+    // level restriction, finest level first
+    for (int l = depth; l >= 2; --l) {
+        const int m = l - 2;
+        const int64_t nbits = 1ll << (2 * m);
+        const int64_t nw = std::max<int64_t>(1, nbits / 32);
+        DBuf<uint32_t> bm;
+        DBuf<int32_t> wc;
+        VFMM_CHECK(bm.alloc(nw));
+        VFMM_CHECK(wc.alloc(nw));
+        VFMM_CUDA(cudaMemsetAsync(bm.p, 0, nw * sizeof(uint32_t), st));
+        int64_t nmax = std::max(cnt[l], cnt[l - 1]);
+        balance_mark_kernel<<<nblk(nmax), 256, 0, st>>>(keys[l].p, (int)cnt[l], keys[l - 1].p, (int)cnt[l - 1], l,
+                                                        bm.p);
+        popc_kernel<<<nblk(nw), 256, 0, st>>>(bm.p, nw, wc.p);
+        VFMM_CUDA(cudaGetLastError());
+        int64_t ns = 0;
+        VFMM_CHECK(exclusive_scan(wc.p, wc.p, nw, &ns, st));
+        DBuf<uint32_t> split;
+        VFMM_CHECK(split.alloc(ns));
+        bitmap_emit_kernel<<<nblk(nw), 256, 0, st>>>(bm.p, nw, wc.p, split.p);
+        VFMM_CHECK(keys[l - 1].alloc(4 * ns));
+        children_of_kernel<<<nblk(ns), 256, 0, st>>>(split.p, (int)ns, keys[l - 1].p);
+        VFMM_CUDA(cudaGetLastError());
+        cnt[l - 1] = 4 * ns;
+    }
+
+    // canonical numbering
+    T->depth = depth;
+    T->level_start.assign(depth + 2, 0);
+    for (int l = 0; l <= depth; ++l) T->level_start[l + 1] = T->level_start[l] + (int32_t)cnt[l];
+    const int n = T->level_start[depth + 1];
+    T->n_boxes = n;
+    DBuf<uint32_t> key;
+    DBuf<int32_t> level, ix, iy, parent, child0, isleaf, rank, lob, bol, lsd;
+    VFMM_CHECK(key.alloc(n));
+    VFMM_CHECK(level.alloc(n));
+    VFMM_CHECK(ix.alloc(n));
+    VFMM_CHECK(iy.alloc(n));
+    VFMM_CHECK(parent.alloc(n));
+    VFMM_CHECK(child0.alloc(n));
+    VFMM_CHECK(isleaf.alloc(n));
+    VFMM_CHECK(rank.alloc(n));
+    VFMM_CHECK(lob.alloc(n));
+    VFMM_CHECK(lsd.alloc(depth + 2));
+    for (int l = 0; l <= depth; ++l)
+        VFMM_CUDA(cudaMemcpyAsync(key.p + T->level_start[l], keys[l].p, cnt[l] * sizeof(uint32_t),
+                                  cudaMemcpyDeviceToDevice, st));
+    VFMM_CUDA(cudaMemcpyAsync(lsd.p, T->level_start.data(), (depth + 2) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    box_setup_kernel<<<nblk(n), 256, 0, st>>>(key.p, lsd.p, depth, n, level.p, ix.p, iy.p, parent.p, child0.p,
+                                              isleaf.p);
+    VFMM_CUDA(cudaGetLastError());
+    int64_t nleaf = 0;
+    VFMM_CHECK(exclusive_scan(isleaf.p, rank.p, n, &nleaf, st));
+    VFMM_CHECK(bol.alloc(nleaf));
+    leaf_rank_kernel<<<nblk(n), 256, 0, st>>>(isleaf.p, rank.p, n, lob.p, bol.p);
+    VFMM_CUDA(cudaGetLastError());
+    T->n_leaves = (int32_t)nleaf;
+    T->key = key.release();
+    T->level = level.release();
+    T->ix = ix.release();
+    T->iy = iy.release();
+    T->parent = parent.release();
+    T->child0 = child0.release();
+    T->leaf_of_box = lob.release();
+    T->box_of_leaf = bol.release();
+    T->level_start_dev = lsd.release();
+    VFMM_CHECK(compute_lists(T, st));
+    VFMM_CUDA(cudaStreamSynchronize(st));
+    return VFMM_OK;
+}
+
+void free_tree(DeviceTree* t) {
+    void* ps[] = {t->key, t->level, t->ix, t->iy, t->parent, t->child0, t->leaf_of_box, t->box_of_leaf,
+                  t->level_start_dev, t->u_by_cfg, t->u_tgt, t->near_tiles, t->nonleaf_by_level};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    for (int q = 0; q < 4; ++q) {
+        if (t->lptr[q]) cudaFree(t->lptr[q]);
+        if (t->lidx[q]) cudaFree(t->lidx[q]);
+        if (t->lcfg[q]) cudaFree(t->lcfg[q]);
+    }
+    *t = DeviceTree();
+}
+
+static int check_params(const vfmm_tree_params* prm) {
+    if (!prm) return fail(VFMM_ERR_INVALID_ARG, "null params");
+    if (prm->k < 4 || prm->k > 16) return fail(VFMM_ERR_INVALID_ARG, "k must be in [4, 16]");
+    if (!(prm->width > 0.0) || !std::isfinite(prm->width)) return fail(VFMM_ERR_INVALID_ARG, "width must be > 0");
+    if (!std::isfinite(prm->cx) || !std::isfinite(prm->cy)) return fail(VFMM_ERR_INVALID_ARG, "bad centre");
+    return VFMM_OK;
+}
+
+int make_source(const vfmm_source* s, DBuf<double>& buf, SourceDev* out, cudaStream_t st) {
+    if (!s || !s->params) return fail(VFMM_ERR_INVALID_ARG, "null source");
+    int len = 0;
+    if (s->kind == VFMM_SRC_CONSTANT) len = 1;
+    else if (s->kind == VFMM_SRC_GAUSS_SUM) {
+        if (s->n < 1 || s->n > 4096) return fail(VFMM_ERR_INVALID_ARG, "gauss sum needs 1..4096 rows");
+        len = 4 * s->n;
+    } else if (s->kind == VFMM_SRC_KINKED) len = 54;
+    else return fail(VFMM_ERR_INVALID_ARG, "unknown source kind");
+    VFMM_CHECK(buf.alloc(len));
+    VFMM_CUDA(cudaMemcpyAsync(buf.p, s->params, len * sizeof(double), cudaMemcpyHostToDevice, st));
+    out->kind = s->kind;
+    out->n = s->n;
+    out->params = buf.p;
+    return VFMM_OK;
+}
+
+__global__ void leaf_nodes_kernel(NodeGeom g, const int32_t* __restrict__ box_of_leaf, const int32_t* __restrict__ level,
+                                  const int32_t* __restrict__ ix, const int32_t* __restrict__ iy, int nleaf,
+                                  SourceDev src, int mode, double* __restrict__ out0, double* __restrict__ out1) {
+    const int64_t kk = (int64_t)g.k * g.k;
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)nleaf * kk) return;
+    int leaf = (int)(gid / kk);
+    int t = (int)(gid % kk);
+    int b = box_of_leaf[leaf];
+    int l = level[b];
+    double h = ldexp(g.width, -l);
+    double x = node_coord(g.lox, ix[b], g.xhat[t % g.k], h);
+    double y = node_coord(g.loy, iy[b], g.xhat[t / g.k], h);
+    if (mode == 0) {
+        out0[gid] = x;
+        out1[gid] = y;
+    } else {
+        out0[gid] = source_eval(src, x, y);
+    }
+}
+
+static int leaf_nodes_impl(const DeviceTree* T, const vfmm_source* s, double* o0, double* o1, cudaStream_t st) {
+    BuildCtx B;
+    B.st = st;
+    VFMM_CHECK(upload_node_tables(T->k, B));
+    NodeGeom g{T->cx - T->width / 2.0, T->cy - T->width / 2.0, T->width, T->k, B.xhat.p};
+    SourceDev sd;
+    DBuf<double> pbuf;
+    if (s) VFMM_CHECK(make_source(s, pbuf, &sd, st));
+    int64_t total = (int64_t)T->n_leaves * T->k * T->k;
+    leaf_nodes_kernel<<<nblk(total), 256, 0, st>>>(g, T->box_of_leaf, T->level, T->ix, T->iy, T->n_leaves, sd,
+                                                   s ? 1 : 0, o0, o1);
+    VFMM_CUDA(cudaGetLastError());
+    // temporaries are freed on return; make sure the kernel has consumed them
+    VFMM_CUDA(cudaStreamSynchronize(st));
+    return VFMM_OK;
+}
+
+}  // namespace vfmm
+
+using namespace vfmm;
+
+extern "C" int vfmm_tree_build(const vfmm_tree_params* prm, const vfmm_source* src, void* stream, vfmm_tree** out) {
+    if (!out) return fail(VFMM_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    VFMM_CHECK(check_params(prm));
+    if (prm->max_depth < 0 || prm->max_depth > kMaxDepth || prm->min_depth < 0 || prm->min_depth > prm->max_depth)
+        return fail(VFMM_ERR_INVALID_ARG, "need 0 <= min_depth <= max_depth <= 16");
+    if (!(prm->tol >= 0.0)) return fail(VFMM_ERR_INVALID_ARG, "tol must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBuf<double> pbuf;
+    SourceDev sd;
+    VFMM_CHECK(make_source(src, pbuf, &sd, st));
+    vfmm_tree* t = new vfmm_tree();
+    int r = build(prm, &sd, 0, st, &t->t);
+    if (r != VFMM_OK) {
+        free_tree(&t->t);
+        delete t;
+        return r;
+    }
+    *out = t;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_build_uniform(const vfmm_tree_params* prm, int32_t depth, void* stream, vfmm_tree** out) {
+    if (!out) return fail(VFMM_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    VFMM_CHECK(check_params(prm));
+    if (depth < 0 || depth > 10) return fail(VFMM_ERR_INVALID_ARG, "uniform depth must be in [0, 10]");
+    vfmm_tree* t = new vfmm_tree();
+    int r = build(prm, nullptr, depth, (cudaStream_t)stream, &t->t);
+    if (r != VFMM_OK) {
+        free_tree(&t->t);
+        delete t;
+        return r;
+    }
+    *out = t;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_info(const vfmm_tree* tree, vfmm_tree_info_t* info) {
+    if (!tree || !info) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    const DeviceTree& T = tree->t;
+    info->n_boxes = T.n_boxes;
+    info->n_leaves = T.n_leaves;
+    info->depth = T.depth;
+    info->k = T.k;
+    for (int q = 0; q < 4; ++q) info->list_len[q] = T.llen[q];
+    info->f_scale = T.f_scale;
+    info->min_margin = T.min_margin;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_export_boxes(const vfmm_tree* tree, int32_t* level, int32_t* ix, int32_t* iy) {
+    if (!tree) return fail(VFMM_ERR_INVALID_ARG, "null tree");
+    const DeviceTree& T = tree->t;
+    size_t bytes = (size_t)T.n_boxes * sizeof(int32_t);
+    if (level) VFMM_CUDA(cudaMemcpy(level, T.level, bytes, cudaMemcpyDeviceToHost));
+    if (ix) VFMM_CUDA(cudaMemcpy(ix, T.ix, bytes, cudaMemcpyDeviceToHost));
+    if (iy) VFMM_CUDA(cudaMemcpy(iy, T.iy, bytes, cudaMemcpyDeviceToHost));
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_export_list(const vfmm_tree* tree, int32_t which, int32_t* ptr, int32_t* idx, int32_t* cfg) {
+    if (!tree || which < 0 || which > 3) return fail(VFMM_ERR_INVALID_ARG, "bad tree or list id");
+    const DeviceTree& T = tree->t;
+    if (ptr) VFMM_CUDA(cudaMemcpy(ptr, T.lptr[which], (T.n_boxes + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    size_t bytes = (size_t)T.llen[which] * sizeof(int32_t);
+    if (idx && bytes) VFMM_CUDA(cudaMemcpy(idx, T.lidx[which], bytes, cudaMemcpyDeviceToHost));
+    if (cfg && bytes) VFMM_CUDA(cudaMemcpy(cfg, T.lcfg[which], bytes, cudaMemcpyDeviceToHost));
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_leaf_nodes(const vfmm_tree* tree, double* x_dev, double* y_dev, void* stream) {
+    if (!tree || !x_dev || !y_dev) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    return leaf_nodes_impl(&tree->t, nullptr, x_dev, y_dev, (cudaStream_t)stream);
+}
+
+extern "C" int vfmm_source_sample(const vfmm_tree* tree, const vfmm_source* src, double* f_dev, void* stream) {
+    if (!tree || !src || !f_dev) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    return leaf_nodes_impl(&tree->t, src, f_dev, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int vfmm_tree_destroy(vfmm_tree* tree) {
+    if (!tree) return VFMM_OK;
+    free_tree(&tree->t);
+    delete tree;
+    return VFMM_OK;
+}

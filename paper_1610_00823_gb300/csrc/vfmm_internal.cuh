@@ -1,0 +1,193 @@
+// Internal declarations of the vfmm library (device code for sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "vfmm.h"
+
+namespace vfmm {
+
+constexpr int kMaxDepth = 16;
+constexpr int kNearCfg = 33;  // same level 9 + coarser 12 + finer 12
+constexpr int kVCfg = 40;     // offsets in [-3,3]^2 outside [-1,1]^2
+constexpr int kFarCfg = 20;   // W and X configurations
+
+// ---------------------------------------------------------------- error plumbing
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define VFMM_CUDA(call)                                                  \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return ::vfmm::cuda_fail(_e, #call);      \
+    } while (0)
+
+#define VFMM_CHECK(call)                  \
+    do {                                  \
+        int _r = (call);                  \
+        if (_r != VFMM_OK) return _r;     \
+    } while (0)
+
+// ---------------------------------------------------------------- geometry
+// Morton key of a box: bit b of ix -> bit 2b, bit b of iy -> bit 2b+1.
+__host__ __device__ inline uint32_t morton_encode(uint32_t ix, uint32_t iy) {
+    uint32_t key = 0;
+    for (int b = 0; b < 16; ++b) {
+        key |= ((ix >> b) & 1u) << (2 * b);
+        key |= ((iy >> b) & 1u) << (2 * b + 1);
+    }
+    return key;
+}
+__host__ __device__ inline void morton_decode(uint32_t key, int* ix, int* iy) {
+    uint32_t x = 0, y = 0;
+    for (int b = 0; b < 16; ++b) {
+        x |= ((key >> (2 * b)) & 1u) << b;
+        y |= ((key >> (2 * b + 1)) & 1u) << b;
+    }
+    *ix = (int)x;
+    *iy = (int)y;
+}
+
+// Closed boxes (la, ax, ay) and (lb, bx, by) touch but their interiors are disjoint.
+__host__ __device__ inline bool boxes_adjacent(int la, int ax, int ay, int lb, int bx, int by) {
+    int top = la > lb ? la : lb;
+    long long sa = 1ll << (top - la), sb = 1ll << (top - lb);
+    long long a0 = ax * sa, a1 = a0 + sa, b0 = bx * sb, b1 = b0 + sb;
+    long long c0 = ay * sa, c1 = c0 + sa, d0 = by * sb, d1 = d0 + sb;
+    bool touch = a0 <= b1 && b0 <= a1 && c0 <= d1 && d0 <= c1;
+    bool inter = a0 < b1 && b0 < a1 && c0 < d1 && d0 < c1;
+    return touch && !inter;
+}
+
+// 4 * (centre_c - centre_b) / h_b, exact integers for |level_c - level_b| <= 1.
+__host__ __device__ inline void centre_offset4(int lb, int bx, int by, int lc, int cx, int cy, int* dx4, int* dy4) {
+    // centre in units of h_20 / 2: (2i + 1) << (20 - l)
+    long long pbx = (long long)(2 * bx + 1) << (20 - lb), pby = (long long)(2 * by + 1) << (20 - lb);
+    long long pcx = (long long)(2 * cx + 1) << (20 - lc), pcy = (long long)(2 * cy + 1) << (20 - lc);
+    long long div = 1ll << (20 - lb - 1);
+    *dx4 = (int)((pcx - pbx) / div);
+    *dy4 = (int)((pcy - pby) / div);
+}
+
+// The 12 offsets of the coarse/fine near configurations (in units of 2D resp. 4D)
+// and the 20 of the W/X configurations (4D resp. 2D), each sorted by (y, x).
+__host__ __device__ inline int near_pattern_index(int px, int py) {
+    const int P[12][2] = {{-3, -3}, {-1, -3}, {1, -3}, {3, -3}, {-3, -1}, {3, -1},
+                          {-3, 1},  {3, 1},   {-3, 3}, {-1, 3}, {1, 3},   {3, 3}};
+    for (int i = 0; i < 12; ++i)
+        if (P[i][0] == px && P[i][1] == py) return i;
+    return -1;
+}
+__host__ __device__ inline void near_pattern(int i, int* px, int* py) {
+    const int P[12][2] = {{-3, -3}, {-1, -3}, {1, -3}, {3, -3}, {-3, -1}, {3, -1},
+                          {-3, 1},  {3, 1},   {-3, 3}, {-1, 3}, {1, 3},   {3, 3}};
+    *px = P[i][0];
+    *py = P[i][1];
+}
+__host__ __device__ inline int far_pattern_index(int px, int py) {
+    const int P[20][2] = {{-5, -5}, {-3, -5}, {-1, -5}, {1, -5}, {3, -5}, {5, -5}, {-5, -3},
+                          {5, -3},  {-5, -1}, {5, -1},  {-5, 1}, {5, 1},  {-5, 3}, {5, 3},
+                          {-5, 5},  {-3, 5},  {-1, 5},  {1, 5},  {3, 5},  {5, 5}};
+    for (int i = 0; i < 20; ++i)
+        if (P[i][0] == px && P[i][1] == py) return i;
+    return -1;
+}
+__host__ __device__ inline void far_pattern(int i, int* px, int* py) {
+    const int P[20][2] = {{-5, -5}, {-3, -5}, {-1, -5}, {1, -5}, {3, -5}, {5, -5}, {-5, -3},
+                          {5, -3},  {-5, -1}, {5, -1},  {-5, 1}, {5, 1},  {-5, 3}, {5, 3},
+                          {-5, 5},  {-3, 5},  {-1, 5},  {1, 5},  {3, 5},  {5, 5}};
+    *px = P[i][0];
+    *py = P[i][1];
+}
+// V offsets: row-major over dy, dx in [-3, 3], skipping max(|dx|,|dy|) <= 1.
+__host__ __device__ inline int v_offset_index(int dx, int dy) {
+    int idx = 0;
+    for (int y = -3; y <= 3; ++y)
+        for (int x = -3; x <= 3; ++x) {
+            int ax = x < 0 ? -x : x, ay = y < 0 ? -y : y;
+            if ((ax > ay ? ax : ay) < 2) continue;
+            if (x == dx && y == dy) return idx;
+            ++idx;
+        }
+    return -1;
+}
+__host__ __device__ inline void v_offset(int i, int* dx, int* dy) {
+    int idx = 0;
+    for (int y = -3; y <= 3; ++y)
+        for (int x = -3; x <= 3; ++x) {
+            int ax = x < 0 ? -x : x, ay = y < 0 ? -y : y;
+            if ((ax > ay ? ax : ay) < 2) continue;
+            if (idx == i) {
+                *dx = x;
+                *dy = y;
+                return;
+            }
+            ++idx;
+        }
+}
+// Near configuration geometry: source width / target width and centre offset (target widths).
+__host__ __device__ inline void near_config_geometry(int cfg, double* rho, double* dx, double* dy) {
+    if (cfg < 9) {
+        *rho = 1.0;
+        *dx = (double)(cfg % 3 - 1);
+        *dy = (double)(cfg / 3 - 1);
+    } else if (cfg < 21) {
+        int px, py;
+        near_pattern(cfg - 9, &px, &py);
+        *rho = 2.0;
+        *dx = px / 2.0;
+        *dy = py / 2.0;
+    } else {
+        int px, py;
+        near_pattern(cfg - 21, &px, &py);
+        *rho = 0.5;
+        *dx = px / 4.0;
+        *dy = py / 4.0;
+    }
+}
+
+// ---------------------------------------------------------------- tree handle
+struct DeviceTree {
+    // box table, canonical order
+    int32_t n_boxes = 0, n_leaves = 0, depth = 0, k = 0;
+    double cx = 0, cy = 0, width = 0;
+    double f_scale = 0, min_margin = 0;
+    std::vector<int32_t> level_start;  // host copy, depth + 2 entries
+    uint32_t* key = nullptr;           // Morton key per box
+    int32_t* level = nullptr;
+    int32_t* ix = nullptr;
+    int32_t* iy = nullptr;
+    int32_t* parent = nullptr;
+    int32_t* child0 = nullptr;  // first of the 4 consecutive children, -1 for leaves
+    int32_t* leaf_of_box = nullptr;  // leaf rank or -1
+    int32_t* box_of_leaf = nullptr;
+    int32_t* level_start_dev = nullptr;
+    // lists (CSR by box)
+    int32_t* lptr[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t* lidx[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t* lcfg[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t llen[4] = {0, 0, 0, 0};
+    // U entries grouped by near configuration (stable within a configuration)
+    int32_t* u_by_cfg = nullptr;       // [llen[U]] U-entry indices
+    int32_t* u_tgt = nullptr;          // [llen[U]] target leaf box of each U entry
+    std::vector<int64_t> u_cfg_start;  // host, 34 entries
+    // GEMM tile schedule for the near field: per tile (cfg, first column)
+    int32_t* near_tiles = nullptr;
+    int32_t n_near_tiles = 0;
+    int32_t* nonleaf_by_level = nullptr;   // non-leaf boxes grouped by level
+    std::vector<int32_t> nonleaf_start;    // host, depth + 2
+};
+
+void free_tree(DeviceTree* t);
+int build_near_tiles(DeviceTree* t);
+
+}  // namespace vfmm
+
+struct vfmm_tree {
+    vfmm::DeviceTree t;
+};
