@@ -48,6 +48,9 @@ def workload(name):
         return W.uniform_gauss3()
     if name == "kinked":
         return W.kinked()
+    if name.startswith("uniform_d") and "_k" in name:  # uniform_d<depth>_k<k>: 3 Gaussians, p = 2.5 k
+        d, k = name[len("uniform_d"):].split("_k")
+        return W.uniform_gauss3(depth=int(d), k=int(k), p=int(2.5 * int(k)))
     raise SystemExit("unknown workload " + name)
 
 
