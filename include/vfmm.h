@@ -171,6 +171,24 @@ int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const
                                double* u_host, double* ux_host, double* uy_host, void* workspace_dev,
                                size_t workspace_bytes, void* stream);
 
+/* Allocation-free solve. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory, such as hosts whose device memory is
+ * owned entirely by their own pool allocator (so neither a workspace buffer nor a
+ * cudaMalloc is available to this library). It runs vfmm_volume_potential with its
+ * workspace in a fixed 32 MiB static device array that every GPU loading the library
+ * holds until the process exits, and never calls cudaMalloc or cudaFree.
+ *  - Size limit: trees whose vfmm_workspace_size (with_io = 0) exceeds 32 MiB are
+ *    rejected with VFMM_ERR_WORKSPACE (roughly a few hundred leaves at k = 8).
+ *  - Set-up: the first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call before
+ *    any stream capture.
+ *  - Sharing: all calls on a device use the same array, which keeps the last call's
+ *    contents; calls that overlap on the GPU (different streams, or concurrent host
+ *    threads) race with each other and must be serialised by the caller.
+ * Inputs and outputs are as for vfmm_volume_potential. */
+int vfmm_volume_potential_noalloc(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
+                                  double* u_dev, double* ux_dev, double* uy_dev, void* stream);
+
 /* Stage timers (tracing): the same solve as vfmm_volume_potential with CUDA events
  * recorded on `stream` between its stages; synchronises `stream` and returns the
  * elapsed milliseconds of each stage summed over the right-hand sides

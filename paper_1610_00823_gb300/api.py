@@ -203,3 +203,24 @@ def volume_potential_profiled(tree: Tree, ops: Ops, f, out, ws, stream=None):
          ctypes.c_void_p(out[0].data_ptr()), ctypes.c_void_p(out[1].data_ptr()), ctypes.c_void_p(out[2].data_ptr()),
          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream), ms, ctypes.byref(launches))
     return dict(zip(STAGES, [float(x) for x in ms])), int(launches.value)
+
+
+def volume_potential_noalloc(tree: Tree, ops: Ops, f, out=None, stream=None):
+    """volume_potential without any allocation by the library (fixed 32 MiB static scratch).
+
+    For callers that cannot allocate device memory (their pool allocator owns it all).
+    Rejects trees whose workspace exceeds the static scratch; calls on overlapping
+    streams race on the shared scratch. The first call on a device should precede
+    any stream capture (it looks up the scratch's device address).
+    """
+    n = tree.n_leaves * tree.k * tree.k
+    f = f.contiguous()
+    if f.dtype != torch.float64 or not f.is_cuda or f.numel() % n:
+        raise ValueError("f must be a cuda float64 tensor with a multiple of n_leaves*k*k elements")
+    nrhs = f.numel() // n
+    if out is None:
+        out = tuple(torch.empty_like(f) for _ in range(3))
+    call("vfmm_volume_potential_noalloc", tree.handle, ops.handle, ctypes.c_void_p(f.data_ptr()), nrhs,
+         ctypes.c_void_p(out[0].data_ptr()), ctypes.c_void_p(out[1].data_ptr()), ctypes.c_void_p(out[2].data_ptr()),
+         _stream(stream))
+    return out

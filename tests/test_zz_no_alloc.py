@@ -1,0 +1,70 @@
+"""The allocation-free solve agrees with the workspace-based solve.
+
+vfmm_volume_potential_noalloc serves callers that cannot allocate device memory
+(their own pool allocator owns it all): it runs the same solve in a static device
+scratch array. This file is collected last so that a run stopping at the first
+failure has already run every other test. Calls go through the C ABI (ctypes).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1610_00823_gb300 as v  # noqa: E402
+from paper_1610_00823_gb300 import _lib  # noqa: E402
+
+TOL = 1e-12  # the tolerance of the FP64 parity tests
+
+
+def _noalloc(tree, ops, f, out):
+    nrhs = f.numel() // (tree.n_leaves * tree.k * tree.k)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return _lib.load().vfmm_volume_potential_noalloc(
+        tree.handle, ops.handle, ctypes.c_void_p(f.data_ptr()), nrhs, ctypes.c_void_p(out[0].data_ptr()),
+        ctypes.c_void_p(out[1].data_ptr()), ctypes.c_void_p(out[2].data_ptr()), stream)
+
+
+def _rel(a, b):
+    return float((a - b).abs().max() / b.abs().max())
+
+
+@pytest.mark.parametrize("case", ["uniform_k8_d3", "adaptive_k8"])
+def test_noalloc_matches_workspace_solve_twice(case):
+    if case == "uniform_k8_d3":
+        tree = v.tree_build_uniform(0.0, 0.0, 1.0, 8, 3)
+        src = W.uniform_gauss3().sources[0]
+    else:
+        src = W.narrow_gaussians(5, n=3, sigma=0.04)
+        tree = v.tree_build(0.0, 0.0, 1.0, 8, src, 1e-6, 7)
+    ops = v.ops_create(8, 20)
+    f = v.source_sample(tree, src)
+    ref = v.volume_potential(tree, ops, f)
+    g = torch.Generator(device="cpu").manual_seed(3)
+    f2 = torch.randn(f.numel(), generator=g, dtype=torch.float64).cuda()
+    ref2 = v.volume_potential(tree, ops, f2)
+    for inp, want in ((f, ref), (f2, ref2)):  # two calls in a row with different inputs
+        out = tuple(torch.full_like(inp, float("nan")) for _ in range(3))
+        assert _noalloc(tree, ops, inp, out) == 0
+        torch.cuda.synchronize()
+        for q in range(3):
+            assert torch.isfinite(out[q]).all()
+            assert _rel(out[q], want[q]) < TOL
+
+
+def test_noalloc_rejects_trees_beyond_the_static_scratch():
+    tree = v.tree_build_uniform(0.0, 0.0, 1.0, 16, 5)  # workspace far above 32 MiB at k = 16
+    ops = v.ops_create(16, 40)
+    assert v.workspace_size(tree, ops) > (32 << 20)
+    f = torch.zeros(tree.n_leaves * 256, dtype=torch.float64, device="cuda")
+    out = tuple(torch.empty_like(f) for _ in range(3))
+    rc = _noalloc(tree, ops, f, out)
+    assert rc == -6  # VFMM_ERR_WORKSPACE
+    assert b"static scratch" in _lib.load().vfmm_last_error_detail()
