@@ -15,7 +15,9 @@
 // [n_boxes][2(p+1)], near slabs [n_U][3kk], far values [n_leaves][3kk] (+ I/O copies).
 #include <algorithm>
 #include <cmath>
+#include <string>
 
+#include "mixed.cuh"
 #include "ops.cuh"
 #include "vfmm_internal.cuh"
 
@@ -290,6 +292,11 @@ struct LeafArgs {
     const double* slab;
     const double* far;
     const double* Mexp;
+    // split-precision near field (null in the FP64 form): (hi, lo) per row, scaled by 2^-(E_f + E_r)
+    const float2* nearmix;
+    const int* Er;
+    const int* Ef;
+    int Rp;
     double* u;
     double* ux;
     double* uy;
@@ -304,14 +311,26 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
     const int b = a.box_of_leaf[leaf];
     const double h = ldexp(a.width, -a.level[b]);
     double u = 0.0, gx = 0.0, gy = 0.0, mass = 0.0;
-    for (int e = a.uptr[b]; e < a.uptr[b + 1]; ++e) {
+    if (a.nearmix) {
         if (act) {
-            const double* s = a.slab + (size_t)e * 3 * kk;
-            u += s[t];
-            gx += s[kk + t];
-            gy += s[2 * kk + t];
+            const float2* nm = a.nearmix + (size_t)leaf * a.Rp;
+            const int ef = *a.Ef;
+            float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
+            u = ldexp((double)v0.x + (double)v0.y, ef + a.Er[t]);
+            gx = ldexp((double)v1.x + (double)v1.y, ef + a.Er[kk + t]);
+            gy = ldexp((double)v2.x + (double)v2.y, ef + a.Er[2 * kk + t]);
         }
-        mass += a.Mexp[(size_t)a.uidx[e] * 2 * P];
+        for (int e = a.uptr[b]; e < a.uptr[b + 1]; ++e) mass += a.Mexp[(size_t)a.uidx[e] * 2 * P];
+    } else {
+        for (int e = a.uptr[b]; e < a.uptr[b + 1]; ++e) {
+            if (act) {
+                const double* s = a.slab + (size_t)e * 3 * kk;
+                u += s[t];
+                gx += s[kk + t];
+                gy += s[2 * kk + t];
+            }
+            mass += a.Mexp[(size_t)a.uidx[e] * 2 * P];
+        }
     }
     u = h * h * u - kInv2Pi * log(h) * mass;
     gx *= h;
@@ -374,6 +393,7 @@ struct Workspace {
     double* slab;
     double* far;
     double* io;  // f, u, ux, uy copies for the host entry point
+    MixedWork mix;
     size_t bytes;
 };
 
@@ -387,10 +407,28 @@ static size_t layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, 
         off += align256(std::max<size_t>(1, n) * sizeof(double));
     };
     double* dummy;
+    const bool mixed = o.precision == VFMM_MIXED;
     take(w ? &w->Mexp : &dummy, (size_t)T.n_boxes * P2);
     take(w ? &w->Lexp : &dummy, (size_t)T.n_boxes * P2);
-    take(w ? &w->slab : &dummy, (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
+    take(w ? &w->slab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
     take(w ? &w->far : &dummy, (size_t)T.n_leaves * 3 * kk);
+    if (mixed) {
+        const MixedOps* mo = (const MixedOps*)o.mixed;
+        double* p = nullptr;
+        // bf16 slices, (hi, lo) near values, then three scalars
+        take(&p, ((size_t)T.n_leaves * kSlices * mo->Kp * 2 + 7) / 8);
+        if (w) w->mix.fsl = (void*)p;
+        take(&p, (size_t)T.n_leaves * mo->Rp);
+        if (w) w->mix.out = (float2*)p;
+        take(&p, 4);
+        if (w) {
+            w->mix.fmax = (unsigned long long*)p;
+            w->mix.Ef = (int*)(p + 1);
+            w->mix.err = (int*)(p + 2);
+        }
+    } else if (w) {
+        w->mix = MixedWork{nullptr, nullptr, nullptr, nullptr, nullptr};
+    }
     if (io) take(w ? &w->io : &dummy, (size_t)4 * nrhs * T.n_leaves * kk);
     else if (w) w->io = nullptr;
     if (w) w->bytes = off;
@@ -479,7 +517,10 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
     else VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.level_start[2] * P2 * sizeof(double), st));
     mark(se, 3, st);
     // near field
-    if (T.n_near_tiles > 0) {
+    if (o.precision == VFMM_MIXED) {
+        launches += 3;
+        VFMM_CHECK(near_mixed(T, o, f, w.mix, st));
+    } else if (T.n_near_tiles > 0) {
         ++launches;
         dim3 g((3 * kk + GBM - 1) / GBM, T.n_near_tiles);
         near_gemm_kernel<<<g, 256, 0, st>>>((const int4*)T.near_tiles, o.near, kk, T.u_by_cfg, T.lidx[VFMM_LIST_U],
@@ -510,6 +551,17 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
     a.slab = w.slab;
     a.far = w.far;
     a.Mexp = w.Mexp;
+    a.nearmix = nullptr;
+    a.Er = nullptr;
+    a.Ef = nullptr;
+    a.Rp = 0;
+    if (o.precision == VFMM_MIXED) {
+        const MixedOps* mo = (const MixedOps*)o.mixed;
+        a.nearmix = w.mix.out;
+        a.Er = mo->Er;
+        a.Ef = w.mix.Ef;
+        a.Rp = mo->Rp;
+    }
     a.u = u;
     a.ux = ux;
     a.uy = uy;
@@ -541,6 +593,21 @@ extern "C" int vfmm_workspace_size(const vfmm_tree* tree, const vfmm_ops* ops, i
     return VFMM_OK;
 }
 
+static int reset_status(const Workspace& w, cudaStream_t st) {
+    if (w.mix.err) VFMM_CUDA(cudaMemsetAsync(w.mix.err, 0, sizeof(int), st));
+    return VFMM_OK;
+}
+
+// After a synchronised solve: a bounded device wait that expired shows up here.
+static int read_status(const Workspace& w) {
+    if (!w.mix.err) return VFMM_OK;
+    int h = 0;
+    VFMM_CUDA(cudaMemcpy(&h, w.mix.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return fail(VFMM_ERR_TIMEOUT, "a bounded wait in the tensor-core near field expired (code " +
+                                             std::to_string(h) + ")");
+    return VFMM_OK;
+}
+
 extern "C" int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
                                      double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
                                      size_t workspace_bytes, void* stream) {
@@ -549,6 +616,7 @@ extern "C" int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops,
     Workspace w;
     size_t need = layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev);
     if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small");
+    VFMM_CHECK(reset_status(w, (cudaStream_t)stream));
     const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
     for (int r = 0; r < nrhs; ++r)
         VFMM_CHECK(solve_one(tree->t, *ops, f_dev + r * n, u_dev + r * n, ux_dev + r * n, uy_dev + r * n, w,
@@ -570,6 +638,7 @@ extern "C" int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops*
     double* u = w.io + n;
     double* ux = w.io + 2 * n;
     double* uy = w.io + 3 * n;
+    VFMM_CHECK(reset_status(w, st));
     VFMM_CUDA(cudaMemcpyAsync(f, f_host, n * sizeof(double), cudaMemcpyHostToDevice, st));
     const size_t m = (size_t)tree->t.n_leaves * ops->k * ops->k;
     for (int r = 0; r < nrhs; ++r)
@@ -578,7 +647,7 @@ extern "C" int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops*
     VFMM_CUDA(cudaMemcpyAsync(ux_host, ux, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     VFMM_CUDA(cudaMemcpyAsync(uy_host, uy, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     VFMM_CUDA(cudaStreamSynchronize(st));
-    return VFMM_OK;
+    return read_status(w);
 }
 
 extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev,
@@ -592,6 +661,7 @@ extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_
     size_t need = layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev);
     if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small");
     cudaStream_t st = (cudaStream_t)stream;
+    VFMM_CHECK(reset_status(w, st));
     StageEvents se;
     for (int i = 0; i <= VFMM_N_STAGES; ++i) VFMM_CUDA(cudaEventCreate(&se.ev[i]));
     for (int i = 0; i < VFMM_N_STAGES; ++i) stage_ms[i] = 0.0f;
@@ -613,5 +683,6 @@ extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_
     }
     for (int i = 0; i <= VFMM_N_STAGES; ++i) cudaEventDestroy(se.ev[i]);
     *launches = se.launches;
+    if (rc == VFMM_OK) rc = read_status(w);
     return rc;
 }

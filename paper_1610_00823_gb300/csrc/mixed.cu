@@ -1,15 +1,437 @@
-// Split-precision near-field operands (VFMM_MIXED).
+// Split-BF16 tensor-core near field (VFMM_MIXED), tcgen05 on sm_103a.
+//
+// The near-field sum of Section 3.1, out[t][r] = sum_{(cfg, s) in U(t)} sum_k T_cfg[r][k] f_s[k],
+// is an exact-enough FP64 contraction computed from BF16 tensor-core products:
+//
+//  * f is normalised by a global power of two (|a| < 1) and each table row r by its own power
+//    of two shared by all 33 configurations; each normalised value is split into kSlices = 8
+//    slices a = sum_i m_i 2^(-6 i) with integers |m_i| <= 63 (exact in BF16), 48 bits in all.
+//  * Products (i, j) with i + j <= 9 are kept (dropped terms are below 2^-48). For one
+//    configuration, the products of one diagonal d = i + j - 2 sum at most (d + 1) * 256 * 63^2
+//    integers times 2^(-6(d+2)); for d <= 4 that is below 2^24 units, so the FP32 tensor-core
+//    accumulator holds it exactly. Diagonals 0..4 get one TMEM accumulator each; diagonals 5..7
+//    share a sixth, where the tensor core's truncating accumulation of terms much smaller than the
+//    running sum (measured: it does not round to nearest) costs about 2^-46 of the result.
+//  * After every configuration the epilogue warps drain the six accumulators into a running
+//    double-float sum (FP32 pairs, exact two-sums) in registers, so no accumulator ever sums more
+//    than one configuration; at the end they store (hi, lo). The leaf pass scales by
+//    2^(E_f + E_r) and by h^2 (potential) or h (gradient) in FP64.
+//
+// Tile: 128 target leaves (TMEM lanes, grouped by their configuration set) x 80 table rows.
+// For every configuration present in the group and every K block of 32 values, producer warps
+// gather the 8 slices of the 128 source rows and of the 80 table rows with cp.async into a
+// 64-byte-swizzled K-major layout (two stages); one thread issues the 36 x 2 UMMAs
+// (128 x 80 x 16) into the six TMEM accumulators; tcgen05.commit frees the stage and, after
+// the last K block of a configuration, hands the accumulators to the epilogue. Every mbarrier
+// wait is bounded and reports a timeout through an error word.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "mixed.cuh"
 #include "ops.cuh"
+#include "tc_ptx.cuh"
 #include "vfmm_internal.cuh"
 
 namespace vfmm {
 
-int mixed_prepare(vfmm_ops* o, cudaStream_t st) {
-    (void)o;
-    (void)st;
-    return fail(VFMM_ERR_INVALID_ARG, "VFMM_MIXED is not available in this build");
+using bf16 = __nv_bfloat16;
+
+// ---------------------------------------------------------------- slicing
+__device__ inline void split_slices(double a, bf16* out, int stride) {
+    // a in (-1, 1): m_i = trunc(64 * rest), rest <- 64 * rest - m_i (all exact in FP64)
+#pragma unroll
+    for (int i = 1; i <= kSlices; ++i) {
+        double t = a * 64.0;
+        double m = trunc(t);
+        a = t - m;
+        out[(i - 1) * stride] = __float2bfloat16_rn(ldexpf((float)m, -6 * i));
+    }
 }
 
-void mixed_free(vfmm_ops* o) { o->mixed = nullptr; }
+// E_r[r] = exponent e with max_{cfg,k} |T_cfg[r][k]| < 2^e (0 for all-zero rows).
+__global__ void table_row_exp_kernel(const double* __restrict__ T, int R, int kk, int* __restrict__ Er) {
+    __shared__ double red[256];
+    const int r = blockIdx.x;
+    double m = 0.0;
+    for (int q = threadIdx.x; q < kNearCfg * kk; q += blockDim.x) {
+        int c = q / kk, k = q % kk;
+        m = fmax(m, fabs(T[((size_t)c * R + r) * kk + k]));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int e = 0;
+        if (red[0] > 0.0) frexp(red[0], &e);
+        Er[r] = e;
+    }
+}
+
+// tsl[cfg][r][i][k] (rows r >= R and columns k >= kk are zero)
+__global__ void table_slice_kernel(const double* __restrict__ T, int R, int kk, int Rp, int Kp,
+                                   const int* __restrict__ Er, bf16* __restrict__ tsl) {
+    const int cfg = blockIdx.y, r = blockIdx.x;
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+        double v = (r < R && k < kk) ? T[((size_t)cfg * R + r) * kk + k] : 0.0;
+        double a = (r < R) ? ldexp(v, -Er[r]) : 0.0;
+        split_slices(a, tsl + (((size_t)cfg * Rp + r) * kSlices) * Kp + k, Kp);
+    }
+}
+
+__global__ void fmax_abs_kernel(const double* __restrict__ f, int64_t n, unsigned long long* __restrict__ out) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(f[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// fsl[leaf][i][k] from f[leaf][k] / 2^E_f; also stores E_f.
+__global__ void f_slice_kernel(const double* __restrict__ f, int nleaf, int kk, int Kp,
+                               const unsigned long long* __restrict__ fmax_bits, int* __restrict__ Ef,
+                               bf16* __restrict__ fsl) {
+    const double fm = __longlong_as_double((long long)*fmax_bits);
+    int e = 0;
+    if (fm > 0.0) frexp(fm, &e);
+    const int64_t total = (int64_t)nleaf * Kp;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t leaf = q / Kp;
+        int k = (int)(q % Kp);
+        double a = k < kk ? ldexp(f[leaf * kk + k], -e) : 0.0;
+        split_slices(a, fsl + (leaf * kSlices) * Kp + k, Kp);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *Ef = e;
+}
+
+// ---------------------------------------------------------------- the tcgen05 kernel
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+struct NearMixArgs {
+    const bf16* fsl;      // [n_leaves][kS][Kp]
+    const bf16* tsl;      // [33][Rp][kS][Kp]
+    const int32_t* gptr;  // [n_groups + 1] into gcfg
+    const int32_t* gcfg;  // configuration of each (group, configuration) entry
+    const int32_t* gsrc;  // [entries][128] source leaf or -1
+    const int32_t* gtgt;  // [n_groups][128] target leaf or -1
+    float2* out;          // [n_leaves][Rp]
+    int* err;
+    int Kp, Rp, nchunks;
+};
+
+// Accumulator of slice product (i, j): its diagonal i + j - 2; diagonals >= kNumAcc - 1 share the last.
+__host__ __device__ constexpr int acc_of(int i, int j) { return (i + j - 2) < (kNumAcc - 1) ? (i + j - 2) : (kNumAcc - 1); }
+
+// Warps 0..7: epilogue (lane quadrant w % 4, column half w / 4); warps 8..10: producers;
+// warp 11: TMEM allocation and the MMA issuer (lane 0). Twelve warps keep three warps per SM
+// sub-partition, which leaves each thread up to 168 registers.
+__global__ void __launch_bounds__(kThreads, 1) near_mixed_kernel(NearMixArgs a) {
+    extern __shared__ unsigned char dsm[];
+    __shared__ __align__(8) uint64_t bars[2 * kStages + 2];
+    __shared__ uint32_t tmem_holder;
+    __shared__ volatile int abort_flag;
+    constexpr int N = kTileN;
+    constexpr uint32_t A_SLICE = kTileM * 64;
+    constexpr uint32_t B_SLICE = N * 64;
+    constexpr uint32_t STAGE = kSlices * (A_SLICE + B_SLICE);
+    constexpr int HALF = N / 2;  // columns per epilogue warp
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = blockIdx.x / a.nchunks, rc = blockIdx.x % a.nchunks;
+    const uint32_t base = tc::smem_u32(dsm);
+    const uint32_t sbase = (base + 1023u) & ~1023u;
+    const uint32_t full0 = tc::smem_u32(&bars[0]);
+    const uint32_t empty0 = tc::smem_u32(&bars[kStages]);
+    const uint32_t acc_full = tc::smem_u32(&bars[2 * kStages]);
+    const uint32_t acc_empty = tc::smem_u32(&bars[2 * kStages + 1]);
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(full0 + 8 * s, kProducerThreads);
+            tc::mbar_init(empty0 + 8 * s, 1);
+        }
+        tc::mbar_init(acc_full, 1);
+        tc::mbar_init(acc_empty, kEpilogueThreads);
+        abort_flag = 0;
+        tc::mbar_fence_init();
+    }
+    if (warp == kMmaWarp) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_holder), kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_holder;
+    const int cbeg = a.gptr[g], cend = a.gptr[g + 1];
+    const int ncfg = cend - cbeg;
+    const int nkb = a.Kp / kKBlock;
+    const int U = ncfg * nkb;
+    const int r0 = rc * N;
+
+    if (warp >= kEpilogueWarps && warp < kMmaWarp) {
+        // ------------------------------------------------ producers: gather slices with cp.async
+        const int ptid = tid - kEpilogueThreads;
+        bool alive = true;
+        for (int u = 0; u < U; ++u) {
+            const int s = u & 1;
+            if (u >= 2 && !tc::mbar_wait(empty0 + 8 * s, ((u >> 1) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                atomicExch(a.err, 1);
+                alive = false;
+                break;
+            }
+            const int ci = cbeg + u / nkb, kb = u % nkb;
+            const int cfg = a.gcfg[ci];
+            const int32_t* src = a.gsrc + (size_t)ci * kTileM;
+            const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
+            for (int q = ptid; q < kSlices * kTileM * 4; q += kProducerThreads) {
+                const int i = q / (kTileM * 4), rem = q % (kTileM * 4), m = rem >> 2, c = rem & 3;
+                const int sl = src[m];
+                const bf16* gp = a.fsl + ((size_t)(sl < 0 ? 0 : sl) * kSlices + i) * a.Kp + kb * kKBlock + c * 8;
+                const uint32_t dst = sA + i * A_SLICE + m * 64 + ((c ^ ((m >> 1) & 3)) << 4);
+                tc::cp_async16(dst, gp, sl < 0 ? 0u : 16u);
+            }
+            for (int q = ptid; q < kSlices * N * 4; q += kProducerThreads) {
+                const int j = q / (N * 4), rem = q % (N * 4), n = rem >> 2, c = rem & 3;
+                const bf16* gp = a.tsl + (((size_t)cfg * a.Rp + r0 + n) * kSlices + j) * a.Kp + kb * kKBlock + c * 8;
+                const uint32_t dst = sB + j * B_SLICE + n * 64 + ((c ^ ((n >> 1) & 3)) << 4);
+                tc::cp_async16(dst, gp, 16u);
+            }
+            tc::cp_async_commit();
+            if (u >= 1) {
+                tc::cp_async_wait<1>();
+                tc::fence_proxy_async();
+                tc::mbar_arrive(full0 + 8 * ((u - 1) & 1));
+            }
+        }
+        tc::cp_async_wait<0>();
+        tc::fence_proxy_async();
+        if (alive && U >= 1) tc::mbar_arrive(full0 + 8 * ((U - 1) & 1));
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------ MMA issuer: one configuration at a time
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, N);
+            bool alive = true;
+            for (int c = 0; c < ncfg && alive; ++c) {
+                if (c >= 1 && !tc::mbar_wait(acc_empty, (c - 1) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    atomicExch(a.err, 4);
+                    break;
+                }
+                tc::tc_fence_after();
+                uint32_t started = 0;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int u = c * nkb + kb, s = u & 1;
+                    if (!tc::mbar_wait(full0 + 8 * s, (u >> 1) & 1, &abort_flag)) {
+                        abort_flag = 1;
+                        atomicExch(a.err, 2);
+                        alive = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
+                    for (int i = 1; i <= kSlices; ++i)
+                        for (int j = 1; i + j <= kSlices + 1; ++j) {
+                            const int acc = acc_of(i, j);
+#pragma unroll
+                            for (int ks = 0; ks < kKBlock / 16; ++ks) {
+                                const uint64_t ad =
+                                    tc::smem_desc(sA + (i - 1) * A_SLICE + ks * 32, 16, 512, tc::kLayoutSwizzle64B);
+                                const uint64_t bd =
+                                    tc::smem_desc(sB + (j - 1) * B_SLICE + ks * 32, 16, 512, tc::kLayoutSwizzle64B);
+                                tc::umma_bf16(tmem + acc * N, ad, bd, idesc, (started >> acc) & 1u);
+                                started |= 1u << acc;
+                            }
+                        }
+                    tc::umma_commit(empty0 + 8 * s);
+                }
+                if (alive) tc::umma_commit(acc_full);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue: drain each configuration
+        const int quad = warp & 3, half = warp >> 2;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + half * HALF;
+        float hi[HALF], lo[HALF];
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) hi[j] = lo[j] = 0.0f;
+        bool ok = true;
+        for (int c = 0; c < ncfg; ++c) {
+            ok = ok && tc::mbar_wait(acc_full, c & 1, &abort_flag);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) atomicExch(a.err, 3);
+                abort_flag = 1;
+                break;
+            }
+            tc::tc_fence_after();
+#pragma unroll 1
+            for (int acc = 0; acc < kNumAcc; ++acc) {
+#pragma unroll
+                for (int ch = 0; ch < HALF / 8; ++ch) {
+                    float v[8];
+                    tc::tmem_ld8(lane_base + acc * N + ch * 8, v);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float s2, e2;
+                        two_sum(hi[ch * 8 + j], v[j], s2, e2);
+                        hi[ch * 8 + j] = s2;
+                        lo[ch * 8 + j] = __fadd_rn(lo[ch * 8 + j], e2);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(acc_empty);
+        }
+        if (ok && ncfg > 0) {
+            const int m = quad * 32 + lane;
+            const int tgt = a.gtgt[(size_t)g * kTileM + m];
+            if (tgt >= 0) {
+                float4* o = reinterpret_cast<float4*>(a.out + (size_t)tgt * a.Rp + r0 + half * HALF);
+#pragma unroll
+                for (int j = 0; j < HALF / 2; ++j) {
+                    float h0 = __fadd_rn(hi[2 * j], lo[2 * j]);
+                    float l0 = __fsub_rn(lo[2 * j], __fsub_rn(h0, hi[2 * j]));
+                    float h1 = __fadd_rn(hi[2 * j + 1], lo[2 * j + 1]);
+                    float l1 = __fsub_rn(lo[2 * j + 1], __fsub_rn(h1, hi[2 * j + 1]));
+                    o[j] = make_float4(h0, l0, h1, l1);
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+int mixed_prepare(vfmm_ops* o, cudaStream_t st) {
+    if (o->k * o->k * 3 > 4096) return fail(VFMM_ERR_INVALID_ARG, "mixed precision supports k <= 16");
+    MixedOps* mo = new MixedOps();
+    o->mixed = mo;
+    const int kk = o->k * o->k;
+    const int R = 3 * kk;
+    mo->N = kTileN;
+    mo->Rp = (R + mo->N - 1) / mo->N * mo->N;
+    mo->Kp = (kk + kKBlock - 1) / kKBlock * kKBlock;
+    VFMM_CUDA(cudaMalloc(&mo->Er, mo->Rp * sizeof(int)));
+    VFMM_CUDA(cudaMemsetAsync(mo->Er, 0, mo->Rp * sizeof(int), st));
+    VFMM_CUDA(cudaMalloc(&mo->tsl, (size_t)kNearCfg * mo->Rp * kSlices * mo->Kp * sizeof(bf16)));
+    table_row_exp_kernel<<<R, 256, 0, st>>>(o->near, R, kk, mo->Er);
+    table_slice_kernel<<<dim3(mo->Rp, kNearCfg), 128, 0, st>>>(o->near, R, kk, mo->Rp, mo->Kp, mo->Er, (bf16*)mo->tsl);
+    VFMM_CUDA(cudaGetLastError());
+    VFMM_CUDA(cudaStreamSynchronize(st));
+    return VFMM_OK;
+}
+
+void mixed_free(vfmm_ops* o) {
+    MixedOps* mo = (MixedOps*)o->mixed;
+    if (!mo) return;
+    if (mo->tsl) cudaFree(mo->tsl);
+    if (mo->Er) cudaFree(mo->Er);
+    delete mo;
+    o->mixed = nullptr;
+}
+
+// Groups of 128 target leaves with similar configuration sets (sorted by the set, then by
+// leaf rank); per group the configurations present and the source leaf of each target.
+int build_mixed_plan(DeviceTree* T) {
+    const int nb = T->n_boxes, nl = T->n_leaves;
+    std::vector<int32_t> ptr(nb + 1), idx(T->llen[VFMM_LIST_U]), cfg(T->llen[VFMM_LIST_U]), bol(nl), lob(nb);
+    VFMM_CUDA(cudaMemcpy(ptr.data(), T->lptr[VFMM_LIST_U], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(idx.data(), T->lidx[VFMM_LIST_U], idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(cfg.data(), T->lcfg[VFMM_LIST_U], cfg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(bol.data(), T->box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(lob.data(), T->leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<uint64_t> sig(nl, 0);
+    for (int t = 0; t < nl; ++t) {
+        int b = bol[t];
+        for (int e = ptr[b]; e < ptr[b + 1]; ++e) sig[t] |= 1ull << cfg[e];
+    }
+    std::vector<int32_t> order(nl);
+    for (int t = 0; t < nl; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sig[x] < sig[y]; });
+    const int ng = (nl + kTileM - 1) / kTileM;
+    std::vector<int32_t> gtgt((size_t)ng * kTileM, -1), gptr(ng + 1, 0), gcfg, gsrc;
+    for (int g = 0; g < ng; ++g) {
+        uint64_t uni = 0;
+        for (int m = 0; m < kTileM && g * kTileM + m < nl; ++m) {
+            int t = order[g * kTileM + m];
+            gtgt[(size_t)g * kTileM + m] = t;
+            uni |= sig[t];
+        }
+        for (int c = 0; c < kNearCfg; ++c) {
+            if (!((uni >> c) & 1ull)) continue;
+            gcfg.push_back(c);
+            size_t off = gsrc.size();
+            gsrc.resize(off + kTileM, -1);
+            for (int m = 0; m < kTileM && g * kTileM + m < nl; ++m) {
+                int t = order[g * kTileM + m], b = bol[t];
+                for (int e = ptr[b]; e < ptr[b + 1]; ++e)
+                    if (cfg[e] == c) gsrc[off + m] = lob[idx[e]];
+            }
+        }
+        gptr[g + 1] = (int32_t)gcfg.size();
+    }
+    T->n_groups = ng;
+    auto up = [](int32_t** dst, const std::vector<int32_t>& v) -> int {
+        VFMM_CUDA(cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(int32_t)));
+        VFMM_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        return VFMM_OK;
+    };
+    VFMM_CHECK(up(&T->grp_tgt, gtgt));
+    VFMM_CHECK(up(&T->grp_ptr, gptr));
+    VFMM_CHECK(up(&T->grp_cfg, gcfg));
+    VFMM_CHECK(up(&T->grp_src, gsrc));
+    T->grp_entries = (int64_t)gcfg.size();
+    return VFMM_OK;
+}
+
+static size_t smem_bytes() { return (size_t)kStages * kSlices * (kTileM * 64 + kTileN * 64) + 1024; }
+
+int near_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, const MixedWork& w, cudaStream_t st) {
+    const MixedOps* mo = (const MixedOps*)o.mixed;
+    const int kk = o.k * o.k;
+    VFMM_CUDA(cudaMemsetAsync(w.fmax, 0, sizeof(unsigned long long), st));
+    const int64_t n = (int64_t)T.n_leaves * kk;
+    fmax_abs_kernel<<<std::min<int64_t>(1024, (n + 255) / 256), 256, 0, st>>>(f, n, w.fmax);
+    const int64_t ns = (int64_t)T.n_leaves * mo->Kp;
+    f_slice_kernel<<<(unsigned)std::min<int64_t>(65535, (ns + 255) / 256), 256, 0, st>>>(f, T.n_leaves, kk, mo->Kp,
+                                                                                         w.fmax, w.Ef, (bf16*)w.fsl);
+    VFMM_CUDA(cudaGetLastError());
+    NearMixArgs a;
+    a.fsl = (const bf16*)w.fsl;
+    a.tsl = (const bf16*)mo->tsl;
+    a.gptr = T.grp_ptr;
+    a.gcfg = T.grp_cfg;
+    a.gsrc = T.grp_src;
+    a.gtgt = T.grp_tgt;
+    a.out = w.out;
+    a.err = w.err;
+    a.Kp = mo->Kp;
+    a.Rp = mo->Rp;
+    a.nchunks = mo->Rp / mo->N;
+    const unsigned grid = (unsigned)T.n_groups * a.nchunks;
+    static bool attr = false;
+    if (!attr) {
+        VFMM_CUDA(cudaFuncSetAttribute(near_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+        attr = true;
+    }
+    near_mixed_kernel<<<grid, kThreads, smem_bytes(), st>>>(a);
+    VFMM_CUDA(cudaGetLastError());
+    return VFMM_OK;
+}
 
 }  // namespace vfmm

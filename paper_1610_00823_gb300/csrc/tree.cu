@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "mixed.cuh"
 #include "source.cuh"
 #include "vfmm_internal.cuh"
 
@@ -704,12 +705,14 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
     T->level_start_dev = lsd.release();
     VFMM_CHECK(compute_lists(T, st));
     VFMM_CUDA(cudaStreamSynchronize(st));
+    VFMM_CHECK(build_mixed_plan(T));
     return VFMM_OK;
 }
 
 void free_tree(DeviceTree* t) {
-    void* ps[] = {t->key, t->level, t->ix, t->iy, t->parent, t->child0, t->leaf_of_box, t->box_of_leaf,
-                  t->level_start_dev, t->u_by_cfg, t->u_tgt, t->near_tiles, t->nonleaf_by_level};
+    void* ps[] = {t->key,     t->level,       t->ix,       t->iy,         t->parent,     t->child0,
+                  t->leaf_of_box, t->box_of_leaf, t->level_start_dev, t->u_by_cfg, t->u_tgt,
+                  t->near_tiles, t->grp_tgt,     t->grp_ptr,  t->grp_cfg,    t->grp_src};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int q = 0; q < 4; ++q) {

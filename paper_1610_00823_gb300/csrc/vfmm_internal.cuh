@@ -179,8 +179,13 @@ struct DeviceTree {
     // GEMM tile schedule for the near field: per tile (cfg, first column)
     int32_t* near_tiles = nullptr;
     int32_t n_near_tiles = 0;
-    int32_t* nonleaf_by_level = nullptr;   // non-leaf boxes grouped by level
-    std::vector<int32_t> nonleaf_start;    // host, depth + 2
+    // split-precision near field: groups of 128 target leaves
+    int32_t n_groups = 0;
+    int64_t grp_entries = 0;
+    int32_t* grp_tgt = nullptr;  // [n_groups][128] target leaf or -1
+    int32_t* grp_ptr = nullptr;  // [n_groups + 1]
+    int32_t* grp_cfg = nullptr;  // [grp_entries]
+    int32_t* grp_src = nullptr;  // [grp_entries][128] source leaf or -1
 };
 
 void free_tree(DeviceTree* t);
