@@ -25,6 +25,35 @@ namespace vfmm {
 
 constexpr double kInv2Pi = 0.15915494309189533577;
 
+// 2^e as a double, built from its exponent bits (exact, no libm call).
+__device__ __forceinline__ double pow2(int e) {
+    e = max(-1022, min(1023, e));
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// Re of local coefficient 0 contributed by the V list of each box (one warp per box, one lane per
+// V entry): sum_c Re(row 0 of M2L_c . a_c) + a_0(c) log h. FP64; the other coefficients come
+// from the split-precision M2L.
+__global__ void m2l_c0_kernel(int begin, int end, int P, double width, const int32_t* __restrict__ level,
+                              const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
+                              const int32_t* __restrict__ vcfg, const double* __restrict__ m2l_t,
+                              const double* __restrict__ Mexp, double* __restrict__ c0) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int b = begin + warp;
+    if (b >= end) return;
+    const double logh = log(ldexp(width, -level[b]));
+    double acc = 0.0;
+    for (int e = vptr[b] + lane; e < vptr[b + 1]; e += 32) {
+        const double* a = Mexp + (size_t)vidx[e] * 2 * P;
+        const double* M = m2l_t + (size_t)vcfg[e] * P * P * 2;
+        double re = a[0] * logh;
+        for (int n = 0; n < P; ++n) re += M[(size_t)n * P * 2] * a[2 * n] - M[(size_t)n * P * 2 + 1] * a[2 * n + 1];
+        acc += re;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) c0[b] = acc;
+}
+
 // ---------------------------------------------------------------- FP64 gather GEMM tile
 // C_j[r] = scale_j * sum_s A[r][s] B_j[s] for rows r in [row0, row0 + 64), columns j < ncols.
 constexpr int GBM = 64, GBN = 64, GBK = 16;
@@ -214,6 +243,11 @@ struct DownArgs {
     const double* Mexp;
     const double* f;
     double* Lexp;
+    // split-precision M2L rows 2..2p+1 (null in the FP64 form): (hi, lo) scaled by 2^-E[level][r]
+    const float2* m2l_out;
+    const int* m2l_E;
+    const double* m2l_c0;  // Re of local coefficient 0 from the V list, with the log(h) term
+    int Rx;
 };
 
 __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
@@ -239,7 +273,7 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
             }
         __syncthreads();
     }
-    for (int e = d.vptr[b]; e < d.vptr[b + 1]; ++e) {
+    for (int e = d.m2l_out ? d.vptr[b + 1] : d.vptr[b]; e < d.vptr[b + 1]; ++e) {
         const int c = d.vidx[e];
         for (int q = t; q < 2 * P; q += blockDim.x) src[q] = d.Mexp[(size_t)c * 2 * P + q];
         __syncthreads();
@@ -274,6 +308,16 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
         }
         __syncthreads();
     }
+    if (d.m2l_out && t < P && d.vptr[b + 1] > d.vptr[b]) {
+        if (t == 0) {
+            re += d.m2l_c0[b];
+        } else {
+            const float2 vr = d.m2l_out[(size_t)b * d.Rx + 2 * (t - 1)];
+            const float2 vi = d.m2l_out[(size_t)b * d.Rx + 2 * (t - 1) + 1];
+            re += ((double)vr.x + (double)vr.y) * pow2(d.m2l_E[(size_t)d.level * d.Rx + 2 * (t - 1)]);
+            im += ((double)vi.x + (double)vi.y) * pow2(d.m2l_E[(size_t)d.level * d.Rx + 2 * (t - 1) + 1]);
+        }
+    }
     if (t < P) {
         d.Lexp[(size_t)b * 2 * P + 2 * t] = re;
         d.Lexp[(size_t)b * 2 * P + 2 * t + 1] = im;
@@ -297,6 +341,11 @@ struct LeafArgs {
     const int* Er;
     const int* Ef;
     int Rp;
+    // split-precision leaf far field (null in the FP64 form): (hi, lo) scaled by 2^-(E_t + E_r)
+    const float2* farmix;
+    const int* farE;
+    const int* Et;
+    const double* Lexp;
     double* u;
     double* ux;
     double* uy;
@@ -312,15 +361,39 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
     const double h = ldexp(a.width, -a.level[b]);
     double u = 0.0, gx = 0.0, gy = 0.0, mass = 0.0;
     if (a.nearmix) {
+        __shared__ double sc[2];
+        if (t < 32) {
+            // per-leaf scalars: U-list mass (log(h) term), local coefficient 0, W-list a_0 log(h_w)
+            double m = 0.0, w0 = 0.0;
+            for (int e = a.uptr[b] + t; e < a.uptr[b + 1]; e += 32) m += a.Mexp[(size_t)a.uidx[e] * 2 * P];
+            for (int e = a.wptr[b] + t; e < a.wptr[b + 1]; e += 32) w0 += a.Mexp[(size_t)a.widx[e] * 2 * P];
+            for (int o = 16; o > 0; o >>= 1) {
+                m += __shfl_xor_sync(0xffffffffu, m, o);
+                w0 += __shfl_xor_sync(0xffffffffu, w0, o);
+            }
+            if (t == 0) {
+                const double logh = log(h);
+                sc[0] = -kInv2Pi * logh * m;
+                sc[1] = -kInv2Pi * (a.Lexp[(size_t)b * 2 * P] + w0 * (logh - 0.6931471805599453));
+            }
+        }
+        __syncthreads();
         if (act) {
             const float2* nm = a.nearmix + (size_t)leaf * a.Rp;
-            const int ef = *a.Ef;
+            const float2* fm = a.farmix + (size_t)leaf * a.Rp;
+            const int ef = *a.Ef, et = a.Et[leaf];
+            const double hh = h * h, ih = 1.0 / h;
             float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
-            u = ldexp((double)v0.x + (double)v0.y, ef + a.Er[t]);
-            gx = ldexp((double)v1.x + (double)v1.y, ef + a.Er[kk + t]);
-            gy = ldexp((double)v2.x + (double)v2.y, ef + a.Er[2 * kk + t]);
+            float2 w0 = fm[t], w1 = fm[kk + t], w2 = fm[2 * kk + t];
+            const size_t o = (size_t)leaf * kk + t;
+            a.u[o] = hh * ((double)v0.x + (double)v0.y) * pow2(ef + a.Er[t]) + sc[0] + sc[1] +
+                     ((double)w0.x + (double)w0.y) * pow2(et + a.farE[t]);
+            a.ux[o] = h * ((double)v1.x + (double)v1.y) * pow2(ef + a.Er[kk + t]) +
+                      ih * ((double)w1.x + (double)w1.y) * pow2(et + a.farE[kk + t]);
+            a.uy[o] = h * ((double)v2.x + (double)v2.y) * pow2(ef + a.Er[2 * kk + t]) +
+                      ih * ((double)w2.x + (double)w2.y) * pow2(et + a.farE[2 * kk + t]);
         }
-        for (int e = a.uptr[b]; e < a.uptr[b + 1]; ++e) mass += a.Mexp[(size_t)a.uidx[e] * 2 * P];
+        return;
     } else {
         for (int e = a.uptr[b]; e < a.uptr[b + 1]; ++e) {
             if (act) {
@@ -335,6 +408,7 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
     u = h * h * u - kInv2Pi * log(h) * mass;
     gx *= h;
     gy *= h;
+    const double hw = 0.5 * h;
     if (act) {
         const double* fr = a.far + (size_t)leaf * 3 * kk;
         u += fr[t];
@@ -342,7 +416,6 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
         gy += fr[2 * kk + t] / h;
     }
     const double xt = act ? a.xhat[t % a.k] : 0.0, yt = act ? a.xhat[t / a.k] : 0.0;
-    const double hw = 0.5 * h;
     for (int e = a.wptr[b]; e < a.wptr[b + 1]; ++e) {
         const int w = a.widx[e];
         for (int q = t; q < 2 * P; q += blockDim.x) sa[q] = a.Mexp[(size_t)w * 2 * P + q];
@@ -411,7 +484,7 @@ static size_t layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, 
     take(w ? &w->Mexp : &dummy, (size_t)T.n_boxes * P2);
     take(w ? &w->Lexp : &dummy, (size_t)T.n_boxes * P2);
     take(w ? &w->slab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
-    take(w ? &w->far : &dummy, (size_t)T.n_leaves * 3 * kk);
+    take(w ? &w->far : &dummy, mixed ? 1 : (size_t)T.n_leaves * 3 * kk);
     if (mixed) {
         const MixedOps* mo = (const MixedOps*)o.mixed;
         double* p = nullptr;
@@ -426,8 +499,29 @@ static size_t layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, 
             w->mix.Ef = (int*)(p + 1);
             w->mix.err = (int*)(p + 2);
         }
+        const size_t nlev = (size_t)T.depth + 1;
+        take(&p, (size_t)T.n_leaves * mo->Rx);
+        if (w) w->mix.s2m_out = (float2*)p;
+        take(&p, nlev * mo->Kx);
+        if (w) w->mix.gexp = (unsigned long long*)p;
+        take(&p, ((size_t)T.n_boxes * kSlices * mo->Kx * 2 + 7) / 8);
+        if (w) w->mix.msl = (void*)p;
+        take(&p, (nlev * kVCfg * mo->Rx * kSlices * mo->Kx * 2 + 7) / 8);
+        if (w) w->mix.m2l_sl = (void*)p;
+        take(&p, (nlev * mo->Rx + 1) / 2);
+        if (w) w->mix.m2l_E = (int*)p;
+        take(&p, (size_t)T.n_boxes * mo->Rx);
+        if (w) w->mix.m2l_out = (float2*)p;
+        take(&p, (size_t)T.n_boxes);
+        if (w) w->mix.m2l_c0 = p;
+        take(&p, ((size_t)T.n_far_slots * kSlices * mo->Kx * 2 + 7) / 8);
+        if (w) w->mix.aprep = (void*)p;
+        take(&p, ((size_t)T.n_leaves + 1) / 2);
+        if (w) w->mix.Et = (int*)p;
+        take(&p, (size_t)T.n_leaves * mo->Rp);
+        if (w) w->mix.far_out = (float2*)p;
     } else if (w) {
-        w->mix = MixedWork{nullptr, nullptr, nullptr, nullptr, nullptr};
+        w->mix = MixedWork();
     }
     if (io) take(w ? &w->io : &dummy, (size_t)4 * nrhs * T.n_leaves * kk);
     else if (w) w->io = nullptr;
@@ -448,65 +542,102 @@ int build_near_tiles(DeviceTree* T) {
     return VFMM_OK;
 }
 
-// Optional stage timing: events[i] is recorded before stage i (and events[6] at the end).
+// Optional stage timing: a start and a stop event around every stage.
 struct StageEvents {
-    cudaEvent_t ev[VFMM_N_STAGES + 1];
+    cudaEvent_t ev[2 * VFMM_N_STAGES];
     int launches = 0;
 };
 
-static inline void mark(StageEvents* se, int i, cudaStream_t st) {
-    if (se) cudaEventRecord(se->ev[i], st);
+enum { ST_S2M = 0, ST_M2M = 1, ST_DOWN = 2, ST_NEAR = 3, ST_L2T = 4, ST_LEAF = 5 };
+
+static inline void mark(StageEvents* se, int stage, bool stop, cudaStream_t st) {
+    if (se) cudaEventRecord(se->ev[2 * stage + (stop ? 1 : 0)], st);
+}
+
+static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, const double* f, const Workspace& w,
+                           int l) {
+    const MixedOps* mo = (const MixedOps*)o.mixed;
+    d.begin = T.level_start[l];
+    d.end = T.level_start[l + 1];
+    d.P = o.p + 1;
+    d.kk = o.k * o.k;
+    d.level = l;
+    d.width = T.width;
+    d.parent = T.parent;
+    d.ix = T.ix;
+    d.iy = T.iy;
+    d.vptr = T.lptr[VFMM_LIST_V];
+    d.vidx = T.lidx[VFMM_LIST_V];
+    d.vcfg = T.lcfg[VFMM_LIST_V];
+    d.xptr = T.lptr[VFMM_LIST_X];
+    d.xidx = T.lidx[VFMM_LIST_X];
+    d.xcfg = T.lcfg[VFMM_LIST_X];
+    d.leaf_of_box = T.leaf_of_box;
+    d.l2l_t = o.l2l_t;
+    d.m2l_t = o.m2l_t;
+    d.s2l_t = o.s2l_t;
+    d.Mexp = w.Mexp;
+    d.f = f;
+    d.Lexp = w.Lexp;
+    d.m2l_out = mo ? w.mix.m2l_out : nullptr;
+    d.m2l_E = mo ? w.mix.m2l_E : nullptr;
+    d.m2l_c0 = mo ? w.mix.m2l_c0 : nullptr;
+    d.Rx = mo ? mo->Rx : 0;
 }
 
 static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, double* u, double* ux, double* uy,
                      const Workspace& w, cudaStream_t st, StageEvents* se = nullptr) {
     const int P = o.p + 1, P2 = 2 * P, kk = o.k * o.k;
     const int nleaf = T.n_leaves;
+    const bool mixed = o.precision == VFMM_MIXED;
+    const MixedOps* mo = (const MixedOps*)o.mixed;
     int launches = 0;
-    mark(se, 0, st);
+    if (mixed) {
+        // near field first: its f slices also feed S2M
+        mark(se, ST_NEAR, false, st);
+        VFMM_CHECK(near_mixed(T, o, f, w.mix, st));
+        launches += 3;
+        mark(se, ST_NEAR, true, st);
+    }
     // S2M
-    {
+    mark(se, ST_S2M, false, st);
+    if (mixed) {
+        VFMM_CHECK(s2m_mixed(T, o, f, w.Mexp, w.mix, st));
+        launches += 2;
+    } else {
         ++launches;
         dim3 g((P2 + GBM - 1) / GBM, (nleaf + GBN - 1) / GBN);
         s2m_gemm_kernel<<<g, 256, 0, st>>>(o.s2m, P2, kk, nleaf, T.box_of_leaf, T.level, T.width, f, w.Mexp);
     }
-    mark(se, 1, st);
+    mark(se, ST_S2M, true, st);
     // M2M, finest parents first (levels >= 2 are the ones the lists read)
+    mark(se, ST_M2M, false, st);
     for (int l = T.depth - 1; l >= 2; --l) {
         int begin = T.level_start[l], end = T.level_start[l + 1];
         int wpb = 4;
         int nb = (end - begin + wpb - 1) / wpb;
-        if (nb > 0) ++launches;
-        if (nb > 0)
+        if (nb > 0) {
+            ++launches;
             m2m_kernel<<<nb, 32 * wpb, (size_t)wpb * 4 * P2 * sizeof(double), st>>>(begin, end, P, T.child0, o.m2m_t,
                                                                                    w.Mexp);
+        }
     }
-    mark(se, 2, st);
+    mark(se, ST_M2M, true, st);
     // downward pass
+    mark(se, ST_DOWN, false, st);
+    if (mixed && T.depth >= 2) {
+        VFMM_CHECK(m2l_mixed(T, o, w.Mexp, w.mix, st));
+        launches += T.depth + 4;
+        const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
+        const int warps = end - begin;
+        m2l_c0_kernel<<<(warps + 7) / 8, 256, 0, st>>>(begin, end, P, T.width, T.level, T.lptr[VFMM_LIST_V],
+                                                      T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V], o.m2l_t, w.Mexp,
+                                                      w.mix.m2l_c0);
+        ++launches;
+    }
     for (int l = 2; l <= T.depth; ++l) {
         DownArgs d;
-        d.begin = T.level_start[l];
-        d.end = T.level_start[l + 1];
-        d.P = P;
-        d.kk = kk;
-        d.level = l;
-        d.width = T.width;
-        d.parent = T.parent;
-        d.ix = T.ix;
-        d.iy = T.iy;
-        d.vptr = T.lptr[VFMM_LIST_V];
-        d.vidx = T.lidx[VFMM_LIST_V];
-        d.vcfg = T.lcfg[VFMM_LIST_V];
-        d.xptr = T.lptr[VFMM_LIST_X];
-        d.xidx = T.lidx[VFMM_LIST_X];
-        d.xcfg = T.lcfg[VFMM_LIST_X];
-        d.leaf_of_box = T.leaf_of_box;
-        d.l2l_t = o.l2l_t;
-        d.m2l_t = o.m2l_t;
-        d.s2l_t = o.s2l_t;
-        d.Mexp = w.Mexp;
-        d.f = f;
-        d.Lexp = w.Lexp;
+        fill_down_args(d, T, o, f, w, l);
         int n = d.end - d.begin;
         if (n > 0) {
             ++launches;
@@ -515,25 +646,29 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
     }
     if (T.depth < 2) VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.n_boxes * P2 * sizeof(double), st));
     else VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.level_start[2] * P2 * sizeof(double), st));
-    mark(se, 3, st);
-    // near field
-    if (o.precision == VFMM_MIXED) {
-        launches += 3;
-        VFMM_CHECK(near_mixed(T, o, f, w.mix, st));
-    } else if (T.n_near_tiles > 0) {
-        ++launches;
-        dim3 g((3 * kk + GBM - 1) / GBM, T.n_near_tiles);
-        near_gemm_kernel<<<g, 256, 0, st>>>((const int4*)T.near_tiles, o.near, kk, T.u_by_cfg, T.lidx[VFMM_LIST_U],
-                                            T.leaf_of_box, f, w.slab);
+    mark(se, ST_DOWN, true, st);
+    if (!mixed) {
+        mark(se, ST_NEAR, false, st);
+        if (T.n_near_tiles > 0) {
+            ++launches;
+            dim3 g((3 * kk + GBM - 1) / GBM, T.n_near_tiles);
+            near_gemm_kernel<<<g, 256, 0, st>>>((const int4*)T.near_tiles, o.near, kk, T.u_by_cfg,
+                                                T.lidx[VFMM_LIST_U], T.leaf_of_box, f, w.slab);
+        }
+        mark(se, ST_NEAR, true, st);
     }
-    mark(se, 4, st);
     // far field at the leaves
-    {
+    mark(se, ST_L2T, false, st);
+    if (mixed) {
+        VFMM_CHECK(far_leaf_mixed(T, o, w.Mexp, w.Lexp, w.mix, st));
+        launches += 2;
+    } else {
         ++launches;
         dim3 g((3 * kk + GBM - 1) / GBM, (nleaf + GBN - 1) / GBN);
         l2t_gemm_kernel<<<g, 256, 0, st>>>(o.l2t, P2, kk, nleaf, T.box_of_leaf, w.Lexp, w.far);
     }
-    mark(se, 5, st);
+    mark(se, ST_L2T, true, st);
+    mark(se, ST_LEAF, false, st);
     LeafArgs a;
     a.nleaf = nleaf;
     a.kk = kk;
@@ -555,19 +690,25 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
     a.Er = nullptr;
     a.Ef = nullptr;
     a.Rp = 0;
-    if (o.precision == VFMM_MIXED) {
-        const MixedOps* mo = (const MixedOps*)o.mixed;
+    a.farmix = nullptr;
+    a.farE = nullptr;
+    a.Et = nullptr;
+    a.Lexp = w.Lexp;
+    if (mixed) {
         a.nearmix = w.mix.out;
         a.Er = mo->Er;
         a.Ef = w.mix.Ef;
         a.Rp = mo->Rp;
+        a.farmix = w.mix.far_out;
+        a.farE = mo->far_E;
+        a.Et = w.mix.Et;
     }
     a.u = u;
     a.ux = ux;
     a.uy = uy;
     leaf_kernel<<<nleaf, ((kk + 31) / 32) * 32, 0, st>>>(a);
     ++launches;
-    mark(se, 6, st);
+    mark(se, ST_LEAF, true, st);
     VFMM_CUDA(cudaGetLastError());
     if (se) se->launches += launches;
     return VFMM_OK;
@@ -663,25 +804,25 @@ extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_
     cudaStream_t st = (cudaStream_t)stream;
     VFMM_CHECK(reset_status(w, st));
     StageEvents se;
-    for (int i = 0; i <= VFMM_N_STAGES; ++i) VFMM_CUDA(cudaEventCreate(&se.ev[i]));
+    for (int i = 0; i < 2 * VFMM_N_STAGES; ++i) VFMM_CUDA(cudaEventCreate(&se.ev[i]));
     for (int i = 0; i < VFMM_N_STAGES; ++i) stage_ms[i] = 0.0f;
     const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
     int rc = VFMM_OK;
     for (int r = 0; r < nrhs && rc == VFMM_OK; ++r) {
         rc = solve_one(tree->t, *ops, f_dev + r * n, u_dev + r * n, ux_dev + r * n, uy_dev + r * n, w, st, &se);
         if (rc != VFMM_OK) break;
-        cudaError_t e = cudaEventSynchronize(se.ev[VFMM_N_STAGES]);
+        cudaError_t e = cudaEventSynchronize(se.ev[2 * ST_LEAF + 1]);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "cudaEventSynchronize");
             break;
         }
         for (int i = 0; i < VFMM_N_STAGES; ++i) {
             float ms = 0.0f;
-            cudaEventElapsedTime(&ms, se.ev[i], se.ev[i + 1]);
+            cudaEventElapsedTime(&ms, se.ev[2 * i], se.ev[2 * i + 1]);
             stage_ms[i] += ms;
         }
     }
-    for (int i = 0; i <= VFMM_N_STAGES; ++i) cudaEventDestroy(se.ev[i]);
+    for (int i = 0; i < 2 * VFMM_N_STAGES; ++i) cudaEventDestroy(se.ev[i]);
     *launches = se.launches;
     if (rc == VFMM_OK) rc = read_status(w);
     return rc;

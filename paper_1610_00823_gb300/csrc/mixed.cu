@@ -116,14 +116,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-struct NearMixArgs {
-    const bf16* fsl;      // [n_leaves][kS][Kp]
-    const bf16* tsl;      // [33][Rp][kS][Kp]
+struct SplitArgs {
+    const bf16* asl;      // A rows: row r, slice i at asl + (r * kSlices + i) * Kp
+    const bf16* bsl;      // tables: [n_tables][Rp][kSlices][Kp]
     const int32_t* gptr;  // [n_groups + 1] into gcfg
-    const int32_t* gcfg;  // configuration of each (group, configuration) entry
-    const int32_t* gsrc;  // [entries][128] source leaf or -1
-    const int32_t* gtgt;  // [n_groups][128] target leaf or -1
-    float2* out;          // [n_leaves][Rp]
+    const int32_t* gcfg;  // table of each (group, table) entry
+    const int32_t* gsrc;  // [entries][128] A row or -1
+    const int32_t* gtgt;  // [n_groups][128] output row or -1
+    float2* out;          // [n_out_rows][Rp]
     int* err;
     int Kp, Rp, nchunks;
 };
@@ -134,7 +134,7 @@ __host__ __device__ constexpr int acc_of(int i, int j) { return (i + j - 2) < (k
 // Warps 0..7: epilogue (lane quadrant w % 4, column half w / 4); warps 8..10: producers;
 // warp 11: TMEM allocation and the MMA issuer (lane 0). Twelve warps keep three warps per SM
 // sub-partition, which leaves each thread up to 168 registers.
-__global__ void __launch_bounds__(kThreads, 1) near_mixed_kernel(NearMixArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
     extern __shared__ unsigned char dsm[];
     __shared__ __align__(8) uint64_t bars[2 * kStages + 2];
     __shared__ uint32_t tmem_holder;
@@ -195,13 +195,13 @@ __global__ void __launch_bounds__(kThreads, 1) near_mixed_kernel(NearMixArgs a) 
             for (int q = ptid; q < kSlices * kTileM * 4; q += kProducerThreads) {
                 const int i = q / (kTileM * 4), rem = q % (kTileM * 4), m = rem >> 2, c = rem & 3;
                 const int sl = src[m];
-                const bf16* gp = a.fsl + ((size_t)(sl < 0 ? 0 : sl) * kSlices + i) * a.Kp + kb * kKBlock + c * 8;
+                const bf16* gp = a.asl + ((size_t)(sl < 0 ? 0 : sl) * kSlices + i) * a.Kp + kb * kKBlock + c * 8;
                 const uint32_t dst = sA + i * A_SLICE + m * 64 + ((c ^ ((m >> 1) & 3)) << 4);
                 tc::cp_async16(dst, gp, sl < 0 ? 0u : 16u);
             }
             for (int q = ptid; q < kSlices * N * 4; q += kProducerThreads) {
                 const int j = q / (N * 4), rem = q % (N * 4), n = rem >> 2, c = rem & 3;
-                const bf16* gp = a.tsl + (((size_t)cfg * a.Rp + r0 + n) * kSlices + j) * a.Kp + kb * kKBlock + c * 8;
+                const bf16* gp = a.bsl + (((size_t)cfg * a.Rp + r0 + n) * kSlices + j) * a.Kp + kb * kKBlock + c * 8;
                 const uint32_t dst = sB + j * B_SLICE + n * 64 + ((c ^ ((n >> 1) & 3)) << 4);
                 tc::cp_async16(dst, gp, 16u);
             }
@@ -333,20 +333,101 @@ int mixed_prepare(vfmm_ops* o, cudaStream_t st) {
     table_slice_kernel<<<dim3(mo->Rp, kNearCfg), 128, 0, st>>>(o->near, R, kk, mo->Rp, mo->Kp, mo->Er, (bf16*)mo->tsl);
     VFMM_CUDA(cudaGetLastError());
     VFMM_CUDA(cudaStreamSynchronize(st));
-    return VFMM_OK;
+    return far_prepare(o, st);
 }
 
 void mixed_free(vfmm_ops* o) {
     MixedOps* mo = (MixedOps*)o->mixed;
     if (!mo) return;
+    far_free(mo);
     if (mo->tsl) cudaFree(mo->tsl);
     if (mo->Er) cudaFree(mo->Er);
     delete mo;
     o->mixed = nullptr;
 }
 
-// Groups of 128 target leaves with similar configuration sets (sorted by the set, then by
-// leaf rank); per group the configurations present and the source leaf of each target.
+// Groups of 128 targets sorted by `key`; per group the tables present and, per table, the A row
+// of each target (-1 when the target has no entry for that table).
+int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
+                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, SplitPlan* P) {
+    const int nt = (int)tgt_id.size();
+    std::vector<int32_t> order(nt);
+    for (int t = 0; t < nt; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key[x] < key[y]; });
+    const int ng = (nt + kTileM - 1) / kTileM;
+    std::vector<int32_t> gtgt((size_t)std::max(ng, 1) * kTileM, -1), gptr(ng + 1, 0), gcfg, gsrc;
+    std::vector<int32_t> slot(n_tables, -1);
+    std::vector<char> present(n_tables, 0);
+    for (int g = 0; g < ng; ++g) {
+        std::fill(present.begin(), present.end(), 0);
+        const int m_end = std::min(kTileM, nt - g * kTileM);
+        for (int m = 0; m < m_end; ++m) {
+            int t = order[g * kTileM + m];
+            gtgt[(size_t)g * kTileM + m] = tgt_id[t];
+            for (auto& it : items[t]) present[it.first] = 1;
+        }
+        for (int c = 0; c < n_tables; ++c) {
+            if (!present[c]) continue;
+            slot[c] = (int32_t)gcfg.size();
+            gcfg.push_back(c);
+            gsrc.resize(gsrc.size() + kTileM, -1);
+        }
+        for (int m = 0; m < m_end; ++m) {
+            int t = order[g * kTileM + m];
+            for (auto& it : items[t]) gsrc[(size_t)slot[it.first] * kTileM + m] = it.second;
+        }
+        gptr[g + 1] = (int32_t)gcfg.size();
+    }
+    P->n_groups = ng;
+    P->entries = (int64_t)gcfg.size();
+    auto up = [](int32_t** dst, const std::vector<int32_t>& v) -> int {
+        VFMM_CUDA(cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(int32_t)));
+        if (!v.empty()) VFMM_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        return VFMM_OK;
+    };
+    VFMM_CHECK(up(&P->tgt, gtgt));
+    VFMM_CHECK(up(&P->ptr, gptr));
+    VFMM_CHECK(up(&P->cfg, gcfg));
+    VFMM_CHECK(up(&P->src, gsrc));
+    return VFMM_OK;
+}
+
+void free_split_plan(SplitPlan* P) {
+    int32_t* ps[] = {P->tgt, P->ptr, P->cfg, P->src};
+    for (int32_t* p : ps)
+        if (p) cudaFree(p);
+    *P = SplitPlan();
+}
+
+static size_t smem_bytes() { return (size_t)kStages * kSlices * (kTileM * 64 + kTileN * 64) + 1024; }
+
+int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int Rp, float2* out, int* err,
+               cudaStream_t st) {
+    if (P.n_groups == 0) return VFMM_OK;
+    if (Kp % kKBlock || Rp % kTileN) return fail(VFMM_ERR_INTERNAL, "split GEMM shape not tiled");
+    static bool attr = false;
+    if (!attr) {
+        VFMM_CUDA(cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+        attr = true;
+    }
+    SplitArgs a;
+    a.asl = (const bf16*)asl;
+    a.bsl = (const bf16*)bsl;
+    a.gptr = P.ptr;
+    a.gcfg = P.cfg;
+    a.gsrc = P.src;
+    a.gtgt = P.tgt;
+    a.out = out;
+    a.err = err;
+    a.Kp = Kp;
+    a.Rp = Rp;
+    a.nchunks = Rp / kTileN;
+    split_gemm_kernel<<<(unsigned)P.n_groups * a.nchunks, kThreads, smem_bytes(), st>>>(a);
+    VFMM_CUDA(cudaGetLastError());
+    return VFMM_OK;
+}
+
+// Near field: targets are leaves; tables are the 33 configurations; A rows are leaves.
 int build_mixed_plan(DeviceTree* T) {
     const int nb = T->n_boxes, nl = T->n_leaves;
     std::vector<int32_t> ptr(nb + 1), idx(T->llen[VFMM_LIST_U]), cfg(T->llen[VFMM_LIST_U]), bol(nl), lob(nb);
@@ -355,51 +436,22 @@ int build_mixed_plan(DeviceTree* T) {
     VFMM_CUDA(cudaMemcpy(cfg.data(), T->lcfg[VFMM_LIST_U], cfg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
     VFMM_CUDA(cudaMemcpy(bol.data(), T->box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
     VFMM_CUDA(cudaMemcpy(lob.data(), T->leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    std::vector<uint64_t> sig(nl, 0);
+    std::vector<int32_t> tgt(nl);
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> items(nl);
+    std::vector<std::pair<uint64_t, uint64_t>> key(nl);
     for (int t = 0; t < nl; ++t) {
+        tgt[t] = t;
         int b = bol[t];
-        for (int e = ptr[b]; e < ptr[b + 1]; ++e) sig[t] |= 1ull << cfg[e];
-    }
-    std::vector<int32_t> order(nl);
-    for (int t = 0; t < nl; ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sig[x] < sig[y]; });
-    const int ng = (nl + kTileM - 1) / kTileM;
-    std::vector<int32_t> gtgt((size_t)ng * kTileM, -1), gptr(ng + 1, 0), gcfg, gsrc;
-    for (int g = 0; g < ng; ++g) {
-        uint64_t uni = 0;
-        for (int m = 0; m < kTileM && g * kTileM + m < nl; ++m) {
-            int t = order[g * kTileM + m];
-            gtgt[(size_t)g * kTileM + m] = t;
-            uni |= sig[t];
+        uint64_t sig = 0;
+        for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
+            items[t].push_back({cfg[e], lob[idx[e]]});
+            sig |= 1ull << cfg[e];
         }
-        for (int c = 0; c < kNearCfg; ++c) {
-            if (!((uni >> c) & 1ull)) continue;
-            gcfg.push_back(c);
-            size_t off = gsrc.size();
-            gsrc.resize(off + kTileM, -1);
-            for (int m = 0; m < kTileM && g * kTileM + m < nl; ++m) {
-                int t = order[g * kTileM + m], b = bol[t];
-                for (int e = ptr[b]; e < ptr[b + 1]; ++e)
-                    if (cfg[e] == c) gsrc[off + m] = lob[idx[e]];
-            }
-        }
-        gptr[g + 1] = (int32_t)gcfg.size();
+        key[t] = {sig, (uint64_t)t};
     }
-    T->n_groups = ng;
-    auto up = [](int32_t** dst, const std::vector<int32_t>& v) -> int {
-        VFMM_CUDA(cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(int32_t)));
-        VFMM_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        return VFMM_OK;
-    };
-    VFMM_CHECK(up(&T->grp_tgt, gtgt));
-    VFMM_CHECK(up(&T->grp_ptr, gptr));
-    VFMM_CHECK(up(&T->grp_cfg, gcfg));
-    VFMM_CHECK(up(&T->grp_src, gsrc));
-    T->grp_entries = (int64_t)gcfg.size();
-    return VFMM_OK;
+    VFMM_CHECK(build_split_plan(tgt, items, key, kNearCfg, &T->plan_near));
+    return build_far_plans(T);
 }
-
-static size_t smem_bytes() { return (size_t)kStages * kSlices * (kTileM * 64 + kTileN * 64) + 1024; }
 
 int near_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
@@ -411,27 +463,7 @@ int near_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, const Mi
     f_slice_kernel<<<(unsigned)std::min<int64_t>(65535, (ns + 255) / 256), 256, 0, st>>>(f, T.n_leaves, kk, mo->Kp,
                                                                                          w.fmax, w.Ef, (bf16*)w.fsl);
     VFMM_CUDA(cudaGetLastError());
-    NearMixArgs a;
-    a.fsl = (const bf16*)w.fsl;
-    a.tsl = (const bf16*)mo->tsl;
-    a.gptr = T.grp_ptr;
-    a.gcfg = T.grp_cfg;
-    a.gsrc = T.grp_src;
-    a.gtgt = T.grp_tgt;
-    a.out = w.out;
-    a.err = w.err;
-    a.Kp = mo->Kp;
-    a.Rp = mo->Rp;
-    a.nchunks = mo->Rp / mo->N;
-    const unsigned grid = (unsigned)T.n_groups * a.nchunks;
-    static bool attr = false;
-    if (!attr) {
-        VFMM_CUDA(cudaFuncSetAttribute(near_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
-        attr = true;
-    }
-    near_mixed_kernel<<<grid, kThreads, smem_bytes(), st>>>(a);
-    VFMM_CUDA(cudaGetLastError());
-    return VFMM_OK;
+    return split_gemm(T.plan_near, w.fsl, mo->tsl, mo->Kp, mo->Rp, w.out, w.err, st);
 }
 
 }  // namespace vfmm

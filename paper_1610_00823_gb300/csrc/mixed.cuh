@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+#include <vector>
+
 #include "ops.cuh"
 #include "vfmm_internal.cuh"
 
@@ -29,17 +32,51 @@ struct MixedOps {
     int Kp = 0;     // k^2 rounded up to kKBlock
     void* tsl = nullptr;  // bf16 [33][Rp][kSlices][Kp]
     int* Er = nullptr;    // [Rp] row exponents
+    // far field: expansion coefficients as reals (Re, Im of 0..p), Kx = 2(p+1) padded
+    int Kx = 0;           // 2(p+1) rounded up to kKBlock
+    int Rx = 0;           // 2p rounded up to kTileN (rows of S2M and M2L without coefficient 0)
+    void* s2m_sl = nullptr;   // bf16 [1][Rx][kSlices][Kp]: S2M rows 2..2p+1
+    int* s2m_E = nullptr;     // [Rx]
+    double* m2l_real = nullptr;  // [40][Rx][Kx] FP64: M2L rows 2..2p+1, input columns 0..2p+1
+    void* far_sl = nullptr;   // bf16 [21][Rp][kSlices][Kx]: L2T (0) and M2T per W configuration
+    int* far_E = nullptr;     // [Rp]
 };
 
 struct MixedWork {
-    void* fsl;                  // bf16 [n_leaves][kSlices][Kp]
-    float2* out;                // [n_leaves][Rp] (hi, lo), scaled by 2^-(E_f + E_r)
-    unsigned long long* fmax;   // max |f| (bits)
-    int* Ef;                    // exponent of f
-    int* err;                   // non-zero after a bounded wait expired
+    void* fsl = nullptr;                  // bf16 [n_leaves][kSlices][Kp]
+    float2* out = nullptr;                // [n_leaves][Rp] (hi, lo), scaled by 2^-(E_f + E_r)
+    unsigned long long* fmax = nullptr;   // max |f| (bits)
+    int* Ef = nullptr;                    // exponent of f
+    int* err = nullptr;                   // non-zero after a bounded wait expired
+    // far field
+    float2* s2m_out = nullptr;            // [n_leaves][Rx]
+    unsigned long long* gexp = nullptr;   // [depth + 1][Kx] max |multipole coefficient| per level (bits)
+    void* msl = nullptr;                  // bf16 [n_boxes][kSlices][Kx]
+    void* m2l_sl = nullptr;               // bf16 [(depth + 1) * 40][Rx][kSlices][Kx]
+    int* m2l_E = nullptr;                 // [(depth + 1)][Rx]
+    float2* m2l_out = nullptr;            // [n_boxes][Rx]
+    double* m2l_c0 = nullptr;             // [n_boxes] Re local coefficient 0 from the V list
+    void* aprep = nullptr;                // bf16 [n_far_slots][kSlices][Kx]
+    int* Et = nullptr;                    // [n_leaves]
+    float2* far_out = nullptr;            // [n_leaves][Rp]
 };
 
+int build_split_plan(const std::vector<int32_t>& tgt_id,
+                     const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
+                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, SplitPlan* P);
+int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int Rp, float2* out, int* err,
+               cudaStream_t st);
 int build_mixed_plan(DeviceTree* T);
+int build_far_plans(DeviceTree* T);
 int near_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, const MixedWork& w, cudaStream_t st);
+int far_prepare(vfmm_ops* o, cudaStream_t st);
+void far_free(MixedOps* mo);
+size_t far_workspace_doubles(const DeviceTree& T, const vfmm_ops& o);
+// Stages of the split-precision far field (see mixed_far.cu).
+int s2m_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, double* Mexp, const MixedWork& w,
+              cudaStream_t st);
+int m2l_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const MixedWork& w, cudaStream_t st);
+int far_leaf_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const double* Lexp,
+                   const MixedWork& w, cudaStream_t st);
 
 }  // namespace vfmm

@@ -1,0 +1,407 @@
+// Split-BF16 far field (VFMM_MIXED): S2M, M2L and the leaf evaluation of local and W-list
+// multipole expansions (L2T + M2T), all as target-major split contractions on the tensor
+// cores (see mixed.cu for the arithmetic), with FP64 kept for the log(h) terms, the
+// coefficient-0 terms, M2M, L2L, S2L and the final per-target sums.
+//
+// Normalisation (each product must be exact per diagonal, so every A row and every table row
+// carries a power-of-two scale):
+//  * S2M: A = f slices (global exponent, shared with the near field); table rows = S2M rows of
+//    coefficients 1..p (row exponents). Coefficient 0 (the mass) is an FP64 dot product.
+//  * M2L: A = multipole coefficients of a level divided by 2^g(l, k), g = exponent of the
+//    level's largest |coefficient k| (k runs over the real and imaginary parts); the table
+//    columns are multiplied by 2^g(l, k), so there is one table set per level, normalised per
+//    (level, output row). All levels go in one launch (table index = level * 40 + offset).
+//    Output coefficient 0 and the log(h) term are added in FP64 by the downward kernel.
+//  * Leaf: A = the leaf's own local coefficients 1..p and the multipoles of its W boxes, all
+//    divided by 2^E_t, E_t the exponent of the leaf's largest such value; tables: L2T and the
+//    20 M2T configurations (factor h / h_w = 2 folded into the gradient rows), row exponents.
+//    The local coefficient 0 and a_0 log(h_w) are added in FP64 by the leaf kernel.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "mixed.cuh"
+#include "ops.cuh"
+#include "vfmm_internal.cuh"
+
+namespace vfmm {
+
+using bf16 = __nv_bfloat16;
+
+__device__ inline void split_into(double a, bf16* out, int stride) {
+#pragma unroll
+    for (int i = 1; i <= kSlices; ++i) {
+        double t = a * 64.0;
+        double m = trunc(t);
+        a = t - m;
+        out[(i - 1) * stride] = __float2bfloat16_rn(ldexpf((float)m, -6 * i));
+    }
+}
+
+__device__ inline int exp_of(double m) {
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);
+    return e;
+}
+
+// ---------------------------------------------------------------- operator tables
+// E[r] = exponent of max_{c,k} |M[c][r][k]|
+__global__ void rows_exp_kernel(const double* __restrict__ M, int nc, int R, int K, int* __restrict__ E) {
+    __shared__ double red[256];
+    const int r = blockIdx.x;
+    double m = 0.0;
+    for (int q = threadIdx.x; q < nc * K; q += blockDim.x) m = fmax(m, fabs(M[((size_t)(q / K) * R + r) * K + q % K]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) E[r] = exp_of(red[0]);
+}
+
+// out[c][r][i][k] = slice i of M[c][r][k] / 2^E[r]; rows >= R and columns >= K are zero.
+__global__ void rows_slice_kernel(const double* __restrict__ M, int R, int K, int Rp, int Kp,
+                                  const int* __restrict__ E, bf16* __restrict__ out) {
+    const int r = blockIdx.x, c = blockIdx.y;
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+        double v = (r < R && k < K) ? M[((size_t)c * R + r) * K + k] : 0.0;
+        double a = r < R ? ldexp(v, -E[r]) : 0.0;
+        split_into(a, out + (((size_t)c * Rp + r) * kSlices) * Kp + k, Kp);
+    }
+}
+
+static int slice_table(const std::vector<double>& M, int nc, int R, int K, int Rp, int Kp, void** out, int** E,
+                       cudaStream_t st) {
+    double* dM = nullptr;
+    VFMM_CUDA(cudaMalloc(&dM, M.size() * sizeof(double)));
+    VFMM_CUDA(cudaMemcpyAsync(dM, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    VFMM_CUDA(cudaMalloc(E, Rp * sizeof(int)));
+    VFMM_CUDA(cudaMemsetAsync(*E, 0, Rp * sizeof(int), st));
+    VFMM_CUDA(cudaMalloc(out, (size_t)nc * Rp * kSlices * Kp * sizeof(bf16)));
+    rows_exp_kernel<<<R, 256, 0, st>>>(dM, nc, R, K, *E);
+    rows_slice_kernel<<<dim3(Rp, nc), 128, 0, st>>>(dM, R, K, Rp, Kp, *E, (bf16*)*out);
+    VFMM_CUDA(cudaGetLastError());
+    VFMM_CUDA(cudaStreamSynchronize(st));
+    cudaFree(dM);
+    return VFMM_OK;
+}
+
+int far_prepare(vfmm_ops* o, cudaStream_t st) {
+    MixedOps* mo = (MixedOps*)o->mixed;
+    const int k = o->k, kk = k * k, p = o->p, P = p + 1;
+    const int R = 3 * kk;
+    mo->Kx = (2 * P + kKBlock - 1) / kKBlock * kKBlock;
+    mo->Rx = (2 * p + kTileN - 1) / kTileN * kTileN;
+    const double inv2pi = 1.0 / (2.0 * 3.14159265358979323846);
+    // S2M rows 2..2p+1 (coefficients 1..p)
+    std::vector<double> s2m((size_t)2 * P * kk);
+    VFMM_CUDA(cudaMemcpy(s2m.data(), o->s2m, s2m.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> S((size_t)2 * p * kk);
+    std::copy(s2m.begin() + 2 * kk, s2m.end(), S.begin());
+    VFMM_CHECK(slice_table(S, 1, 2 * p, kk, mo->Rx, mo->Kp, &mo->s2m_sl, &mo->s2m_E, st));
+    // M2L as real matrices: rows 2..2p+1, columns 0..2p+1
+    std::vector<double> mt((size_t)kVCfg * P * P * 2);
+    VFMM_CUDA(cudaMemcpy(mt.data(), o->m2l_t, mt.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> MR((size_t)kVCfg * mo->Rx * mo->Kx, 0.0);
+    for (int c = 0; c < kVCfg; ++c)
+        for (int l = 1; l <= p; ++l)
+            for (int n = 0; n <= p; ++n) {
+                double re = mt[(((size_t)c * P + n) * P + l) * 2], im = mt[(((size_t)c * P + n) * P + l) * 2 + 1];
+                size_t rr = (size_t)c * mo->Rx + 2 * (l - 1);
+                MR[rr * mo->Kx + 2 * n] = re;
+                MR[rr * mo->Kx + 2 * n + 1] = -im;
+                MR[(rr + 1) * mo->Kx + 2 * n] = im;
+                MR[(rr + 1) * mo->Kx + 2 * n + 1] = re;
+            }
+    VFMM_CUDA(cudaMalloc(&mo->m2l_real, MR.size() * sizeof(double)));
+    VFMM_CUDA(cudaMemcpy(mo->m2l_real, MR.data(), MR.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // leaf tables: 0 = L2T without coefficient 0, 1 + c = M2T of W configuration c
+    std::vector<double> l2t((size_t)R * 2 * P), xh(k);
+    VFMM_CUDA(cudaMemcpy(l2t.data(), o->l2t, l2t.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(xh.data(), o->xhat, k * sizeof(double), cudaMemcpyDeviceToHost));
+    const int KX = 2 * P;
+    std::vector<double> F((size_t)(1 + kFarCfg) * R * KX, 0.0);
+    for (int r = 0; r < R; ++r)
+        for (int q = 2; q < KX; ++q) F[(size_t)r * KX + q] = l2t[(size_t)r * KX + q];
+    typedef std::complex<double> cd;
+    for (int c = 0; c < kFarCfg; ++c) {
+        int px, py;
+        far_pattern(c, &px, &py);
+        double* Fc = F.data() + (size_t)(1 + c) * R * KX;
+        for (int t = 0; t < kk; ++t) {
+            cd zeta(2.0 * (xh[t % k] - px / 4.0), 2.0 * (xh[t / k] - py / 4.0));
+            cd zi = 1.0 / zeta;
+            // potential row: -(1/2pi) Re(a_0 log zeta + sum_n a_n zeta^-n)
+            Fc[(size_t)t * KX + 0] = -inv2pi * std::log(std::abs(zeta));
+            Fc[(size_t)t * KX + 1] = inv2pi * std::arg(zeta);
+            cd zp = 1.0;
+            for (int n = 1; n <= p; ++n) {
+                zp *= zi;
+                Fc[(size_t)t * KX + 2 * n] = -inv2pi * zp.real();
+                Fc[(size_t)t * KX + 2 * n + 1] = inv2pi * zp.imag();
+            }
+            // gradient rows (times h): 2 sum_n c_n a_n, c_0 = 1/zeta, c_n = -n zeta^(-n-1)
+            cd zq = zi;  // zeta^(-n-1) at step n
+            for (int n = 0; n <= p; ++n) {
+                cd cn = n == 0 ? zi : -(double)n * zq;
+                Fc[(size_t)(kk + t) * KX + 2 * n] = -2.0 * inv2pi * cn.real();
+                Fc[(size_t)(kk + t) * KX + 2 * n + 1] = 2.0 * inv2pi * cn.imag();
+                Fc[(size_t)(2 * kk + t) * KX + 2 * n] = 2.0 * inv2pi * cn.imag();
+                Fc[(size_t)(2 * kk + t) * KX + 2 * n + 1] = 2.0 * inv2pi * cn.real();
+                zq *= zi;
+            }
+        }
+    }
+    VFMM_CHECK(slice_table(F, 1 + kFarCfg, R, KX, mo->Rp, mo->Kx, &mo->far_sl, &mo->far_E, st));
+    return VFMM_OK;
+}
+
+void far_free(MixedOps* mo) {
+    void* ps[] = {mo->s2m_sl, mo->s2m_E, mo->m2l_real, mo->far_sl, mo->far_E};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+}
+
+// ---------------------------------------------------------------- schedules
+int build_far_plans(DeviceTree* T) {
+    const int nb = T->n_boxes, nl = T->n_leaves;
+    std::vector<int32_t> bol(nl), lob(nb), lev(nb);
+    VFMM_CUDA(cudaMemcpy(bol.data(), T->box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(lob.data(), T->leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(lev.data(), T->level, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    auto fetch = [&](int q, std::vector<int32_t>& ptr, std::vector<int32_t>& idx, std::vector<int32_t>& cfg) -> int {
+        ptr.resize(nb + 1);
+        idx.resize(T->llen[q]);
+        cfg.resize(T->llen[q]);
+        VFMM_CUDA(cudaMemcpy(ptr.data(), T->lptr[q], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (T->llen[q]) {
+            VFMM_CUDA(cudaMemcpy(idx.data(), T->lidx[q], idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            VFMM_CUDA(cudaMemcpy(cfg.data(), T->lcfg[q], cfg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+        return VFMM_OK;
+    };
+    // S2M: every leaf, one table, A row = the leaf
+    {
+        std::vector<int32_t> tgt(nl);
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> items(nl);
+        std::vector<std::pair<uint64_t, uint64_t>> key(nl);
+        for (int t = 0; t < nl; ++t) {
+            tgt[t] = t;
+            items[t].push_back({0, t});
+            key[t] = {0, (uint64_t)t};
+        }
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1, &T->plan_s2m));
+    }
+    // M2L: boxes with a V list, tables level * 40 + offset, A row = source box
+    {
+        std::vector<int32_t> ptr, idx, cfg;
+        VFMM_CHECK(fetch(VFMM_LIST_V, ptr, idx, cfg));
+        std::vector<int32_t> tgt;
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> items;
+        std::vector<std::pair<uint64_t, uint64_t>> key;
+        for (int b = 0; b < nb; ++b) {
+            if (ptr[b + 1] == ptr[b]) continue;
+            tgt.push_back(b);
+            items.emplace_back();
+            uint64_t sig = 0;
+            for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
+                items.back().push_back({lev[b] * kVCfg + cfg[e], idx[e]});
+                sig |= 1ull << cfg[e];
+            }
+            key.push_back({(uint64_t)lev[b], sig});
+        }
+        VFMM_CHECK(build_split_plan(tgt, items, key, (T->depth + 1) * kVCfg, &T->plan_m2l));
+    }
+    // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
+    {
+        std::vector<int32_t> ptr, idx, cfg;
+        VFMM_CHECK(fetch(VFMM_LIST_W, ptr, idx, cfg));
+        std::vector<int32_t> tgt(nl), slot(nl + 1, 0);
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> items(nl);
+        std::vector<std::pair<uint64_t, uint64_t>> key(nl);
+        for (int t = 0; t < nl; ++t) {
+            int b = bol[t];
+            slot[t + 1] = slot[t] + 1 + (ptr[b + 1] - ptr[b]);
+        }
+        for (int t = 0; t < nl; ++t) {
+            int b = bol[t];
+            tgt[t] = t;
+            items[t].push_back({0, slot[t]});
+            uint64_t sig = 0;
+            for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
+                items[t].push_back({1 + cfg[e], slot[t] + 1 + (e - ptr[b])});
+                sig |= 1ull << cfg[e];
+            }
+            key[t] = {sig, (uint64_t)t};
+        }
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1 + kFarCfg, &T->plan_far));
+        T->n_far_slots = slot[nl];
+        VFMM_CUDA(cudaMalloc(&T->far_slot, (nl + 1) * sizeof(int32_t)));
+        VFMM_CUDA(cudaMemcpy(T->far_slot, slot.data(), (nl + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    return VFMM_OK;
+}
+
+// ---------------------------------------------------------------- S2M
+__global__ void s2m_finish_kernel(int nleaf, int kk, int p, int Rx, const int32_t* __restrict__ box_of_leaf,
+                                  const int32_t* __restrict__ level, double width, const double* __restrict__ f,
+                                  const double* __restrict__ s2m, const float2* __restrict__ out,
+                                  const int* __restrict__ E, const int* __restrict__ Ef, double* __restrict__ Mexp) {
+    const int leaf = blockIdx.x;
+    const int b = box_of_leaf[leaf];
+    const double h = ldexp(width, -level[b]);
+    const int P2 = 2 * (p + 1);
+    double* M = Mexp + (size_t)b * P2;
+    if (threadIdx.x < 32) {
+        double m = 0.0;
+        for (int s = threadIdx.x; s < kk; s += 32) m += s2m[s] * f[(size_t)leaf * kk + s];
+        for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+        if (threadIdx.x == 0) {
+            M[0] = h * h * m;
+            M[1] = 0.0;
+        }
+    }
+    const int ef = *Ef;
+    for (int r = threadIdx.x; r < 2 * p; r += blockDim.x) {
+        float2 v = out[(size_t)leaf * Rx + r];
+        M[2 + r] = h * h * ldexp((double)v.x + (double)v.y, ef + E[r]);
+    }
+}
+
+int s2m_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, double* Mexp, const MixedWork& w,
+              cudaStream_t st) {
+    const MixedOps* mo = (const MixedOps*)o.mixed;
+    VFMM_CHECK(split_gemm(T.plan_s2m, w.fsl, mo->s2m_sl, mo->Kp, mo->Rx, w.s2m_out, w.err, st));
+    s2m_finish_kernel<<<T.n_leaves, 128, 0, st>>>(T.n_leaves, o.k * o.k, o.p, mo->Rx, T.box_of_leaf, T.level, T.width,
+                                                  f, o.s2m, w.s2m_out, mo->s2m_E, w.Ef, Mexp);
+    VFMM_CUDA(cudaGetLastError());
+    return VFMM_OK;
+}
+
+// ---------------------------------------------------------------- M2L
+// Max |coefficient k| over the boxes of one level: thread k scans a chunk of 256 boxes, then
+// one atomic per (block, k).
+__global__ void level_max_kernel(int lvl, int begin, int end, int P2, const double* __restrict__ Mexp,
+                                 unsigned long long* __restrict__ gexp, int Kx) {
+    const int k = threadIdx.x;
+    if (k >= P2) return;
+    const int b0 = begin + blockIdx.x * 256, b1 = min(end, b0 + 256);
+    double m = 0.0;
+    for (int b = b0; b < b1; ++b) m = fmax(m, fabs(Mexp[(size_t)b * P2 + k]));
+    if (m > 0.0) atomicMax(&gexp[(size_t)lvl * Kx + k], (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void multipole_slice_kernel(const int32_t* __restrict__ level, int begin, int end, int P2, int Kx,
+                                       const double* __restrict__ Mexp, const unsigned long long* __restrict__ gexp,
+                                       bf16* __restrict__ msl) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t total = (int64_t)(end - begin) * Kx;
+    if (q >= total) return;
+    int b = begin + (int)(q / Kx), k = (int)(q % Kx);
+    double a = 0.0;
+    if (k < P2) {
+        int g = exp_of(__longlong_as_double((long long)gexp[(size_t)level[b] * Kx + k]));
+        a = ldexp(Mexp[(size_t)b * P2 + k], -g);
+    }
+    split_into(a, msl + ((size_t)b * kSlices) * Kx + k, Kx);
+}
+
+// E[l][r] = exponent of max_{c,k} |MR[c][r][k]| 2^g(l,k)
+__global__ void m2l_level_exp_kernel(const double* __restrict__ MR, int Rx, int Kx,
+                                     const unsigned long long* __restrict__ gexp, int lmin, int* __restrict__ E) {
+    __shared__ double red[256];
+    const int r = blockIdx.x, l = lmin + blockIdx.y;
+    double m = 0.0;
+    for (int q = threadIdx.x; q < kVCfg * Kx; q += blockDim.x) {
+        int c = q / Kx, k = q % Kx;
+        double gk = __longlong_as_double((long long)gexp[(size_t)l * Kx + k]);
+        if (gk > 0.0) m = fmax(m, ldexp(fabs(MR[((size_t)c * Rx + r) * Kx + k]), exp_of(gk)));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) E[(size_t)l * Rx + r] = exp_of(red[0]);
+}
+
+__global__ void m2l_level_slice_kernel(const double* __restrict__ MR, int Rx, int Kx,
+                                       const unsigned long long* __restrict__ gexp, const int* __restrict__ E,
+                                       int lmin, bf16* __restrict__ out) {
+    const int r = blockIdx.x, c = blockIdx.y, l = lmin + blockIdx.z;
+    for (int k = threadIdx.x; k < Kx; k += blockDim.x) {
+        double gk = __longlong_as_double((long long)gexp[(size_t)l * Kx + k]);
+        double a = 0.0;
+        if (gk > 0.0) a = ldexp(MR[((size_t)c * Rx + r) * Kx + k], exp_of(gk) - E[(size_t)l * Rx + r]);
+        split_into(a, out + (((size_t)(l * kVCfg + c) * Rx + r) * kSlices) * Kx + k, Kx);
+    }
+}
+
+int m2l_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const MixedWork& w, cudaStream_t st) {
+    const MixedOps* mo = (const MixedOps*)o.mixed;
+    if (T.depth < 2 || T.plan_m2l.n_groups == 0) return VFMM_OK;
+    const int P2 = 2 * (o.p + 1);
+    const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
+    VFMM_CUDA(cudaMemsetAsync(w.gexp, 0, (size_t)(T.depth + 1) * mo->Kx * sizeof(unsigned long long), st));
+    for (int l = 2; l <= T.depth; ++l) {
+        const int lb = T.level_start[l], le = T.level_start[l + 1];
+        if (le > lb) level_max_kernel<<<(le - lb + 255) / 256, 128, 0, st>>>(l, lb, le, P2, Mexp, w.gexp, mo->Kx);
+    }
+    int64_t n2 = (int64_t)(end - begin) * mo->Kx;
+    multipole_slice_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(T.level, begin, end, P2, mo->Kx, Mexp,
+                                                                          w.gexp, (bf16*)w.msl);
+    const int nlev = T.depth - 1;  // levels 2..depth
+    m2l_level_exp_kernel<<<dim3(mo->Rx, nlev), 256, 0, st>>>(mo->m2l_real, mo->Rx, mo->Kx, w.gexp, 2, w.m2l_E);
+    m2l_level_slice_kernel<<<dim3(mo->Rx, kVCfg, nlev), 128, 0, st>>>(mo->m2l_real, mo->Rx, mo->Kx, w.gexp, w.m2l_E, 2,
+                                                                      (bf16*)w.m2l_sl);
+    VFMM_CUDA(cudaGetLastError());
+    return split_gemm(T.plan_m2l, w.msl, w.m2l_sl, mo->Kx, mo->Rx, w.m2l_out, w.err, st);
+}
+
+// ---------------------------------------------------------------- leaf far field
+// One CTA per leaf: operand rows (own local without coefficient 0, W multipoles) scaled by 2^-E_t.
+__global__ void far_operand_kernel(int nleaf, int P2, int Kx, const int32_t* __restrict__ box_of_leaf,
+                                   const int32_t* __restrict__ far_slot, const int32_t* __restrict__ wptr,
+                                   const int32_t* __restrict__ widx, const double* __restrict__ Mexp,
+                                   const double* __restrict__ Lexp, int* __restrict__ Et, bf16* __restrict__ aprep) {
+    __shared__ double red[128];
+    const int leaf = blockIdx.x;
+    const int b = box_of_leaf[leaf];
+    const int s0 = far_slot[leaf], ns = far_slot[leaf + 1] - s0;
+    auto value = [&](int j, int k) -> double {
+        if (k >= P2) return 0.0;
+        if (j == 0) return k >= 2 ? Lexp[(size_t)b * P2 + k] : 0.0;
+        return Mexp[(size_t)widx[wptr[b] + j - 1] * P2 + k];
+    };
+    double m = 0.0;
+    for (int q = threadIdx.x; q < ns * P2; q += blockDim.x) m = fmax(m, fabs(value(q / P2, q % P2)));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    const int e = exp_of(red[0]);
+    if (threadIdx.x == 0) Et[leaf] = e;
+    for (int q = threadIdx.x; q < ns * Kx; q += blockDim.x) {
+        int j = q / Kx, k = q % Kx;
+        split_into(ldexp(value(j, k), -e), aprep + ((size_t)(s0 + j) * kSlices) * Kx + k, Kx);
+    }
+}
+
+int far_leaf_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const double* Lexp,
+                   const MixedWork& w, cudaStream_t st) {
+    const MixedOps* mo = (const MixedOps*)o.mixed;
+    far_operand_kernel<<<T.n_leaves, 128, 0, st>>>(T.n_leaves, 2 * (o.p + 1), mo->Kx, T.box_of_leaf, T.far_slot,
+                                                   T.lptr[VFMM_LIST_W], T.lidx[VFMM_LIST_W], Mexp, Lexp, w.Et,
+                                                   (bf16*)w.aprep);
+    VFMM_CUDA(cudaGetLastError());
+    return split_gemm(T.plan_far, w.aprep, mo->far_sl, mo->Kx, mo->Rp, w.far_out, w.err, st);
+}
+
+}  // namespace vfmm

@@ -710,9 +710,13 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
 }
 
 void free_tree(DeviceTree* t) {
-    void* ps[] = {t->key,     t->level,       t->ix,       t->iy,         t->parent,     t->child0,
-                  t->leaf_of_box, t->box_of_leaf, t->level_start_dev, t->u_by_cfg, t->u_tgt,
-                  t->near_tiles, t->grp_tgt,     t->grp_ptr,  t->grp_cfg,    t->grp_src};
+    void* ps[] = {t->key,         t->level,       t->ix,       t->iy,           t->parent,     t->child0,
+                  t->leaf_of_box, t->box_of_leaf, t->level_start_dev, t->u_by_cfg, t->u_tgt, t->near_tiles,
+                  t->far_slot};
+    free_split_plan(&t->plan_near);
+    free_split_plan(&t->plan_s2m);
+    free_split_plan(&t->plan_m2l);
+    free_split_plan(&t->plan_far);
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int q = 0; q < 4; ++q) {

@@ -152,6 +152,17 @@ __host__ __device__ inline void near_config_geometry(int cfg, double* rho, doubl
 }
 
 // ---------------------------------------------------------------- tree handle
+// Schedule of one split-precision contraction: groups of 128 targets, the tables present
+// in each group and the A row of every target for every table (-1: none).
+struct SplitPlan {
+    int32_t n_groups = 0;
+    int64_t entries = 0;
+    int32_t* tgt = nullptr;  // [n_groups][128] output row or -1
+    int32_t* ptr = nullptr;  // [n_groups + 1]
+    int32_t* cfg = nullptr;  // [entries] table index
+    int32_t* src = nullptr;  // [entries][128] A row or -1
+};
+
 struct DeviceTree {
     // box table, canonical order
     int32_t n_boxes = 0, n_leaves = 0, depth = 0, k = 0;
@@ -179,16 +190,17 @@ struct DeviceTree {
     // GEMM tile schedule for the near field: per tile (cfg, first column)
     int32_t* near_tiles = nullptr;
     int32_t n_near_tiles = 0;
-    // split-precision near field: groups of 128 target leaves
-    int32_t n_groups = 0;
-    int64_t grp_entries = 0;
-    int32_t* grp_tgt = nullptr;  // [n_groups][128] target leaf or -1
-    int32_t* grp_ptr = nullptr;  // [n_groups + 1]
-    int32_t* grp_cfg = nullptr;  // [grp_entries]
-    int32_t* grp_src = nullptr;  // [grp_entries][128] source leaf or -1
+    // split-precision schedules (VFMM_MIXED)
+    SplitPlan plan_near;  // U list: targets leaves, tables 33 configurations, A rows leaves
+    SplitPlan plan_s2m;   // targets leaves, one table, A rows leaves
+    SplitPlan plan_m2l;   // V list: targets boxes, tables level * 40 + offset, A rows boxes
+    SplitPlan plan_far;   // L2T + W list: targets leaves, tables 0 (L2T) and 1 + W configuration
+    int32_t* far_slot = nullptr;  // [n_leaves + 1] first A row of each leaf in the far operand
+    int64_t n_far_slots = 0;
 };
 
 void free_tree(DeviceTree* t);
+void free_split_plan(SplitPlan* p);
 int build_near_tiles(DeviceTree* t);
 
 }  // namespace vfmm
