@@ -520,6 +520,9 @@ static size_t layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, 
         if (w) w->mix.Et = (int*)p;
         take(&p, (size_t)T.n_leaves * mo->Rp);
         if (w) w->mix.far_out = (float2*)p;
+        const size_t np = split_part_elems(T, o);
+        take(&p, std::max<size_t>(np, 1));
+        if (w) w->mix.part = np ? (float2*)p : nullptr;
     } else if (w) {
         w->mix = MixedWork();
     }

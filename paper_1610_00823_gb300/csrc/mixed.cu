@@ -40,6 +40,12 @@ namespace vfmm {
 using bf16 = __nv_bfloat16;
 
 // ---------------------------------------------------------------- slicing
+// Operand layout: [row][K block of 32][slice][32 values]; one row's slices of one K block are 512
+// contiguous bytes (one warp-wide cp.async). Offset of (row, slice 0, k):
+__device__ __forceinline__ size_t slice_off(size_t row, int Kp, int k) {
+    return ((row * (Kp / kKBlock) + k / kKBlock) * kSlices) * kKBlock + (k % kKBlock);
+}
+
 __device__ inline void split_slices(double a, bf16* out, int stride) {
     // a in (-1, 1): m_i = trunc(64 * rest), rest <- 64 * rest - m_i (all exact in FP64)
 #pragma unroll
@@ -80,7 +86,7 @@ __global__ void table_slice_kernel(const double* __restrict__ T, int R, int kk, 
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
         double v = (r < R && k < kk) ? T[((size_t)cfg * R + r) * kk + k] : 0.0;
         double a = (r < R) ? ldexp(v, -Er[r]) : 0.0;
-        split_slices(a, tsl + (((size_t)cfg * Rp + r) * kSlices) * Kp + k, Kp);
+        split_slices(a, tsl + slice_off((size_t)cfg * Rp + r, Kp, k), kKBlock);
     }
 }
 
@@ -104,12 +110,17 @@ __global__ void f_slice_kernel(const double* __restrict__ f, int nleaf, int kk, 
         int64_t leaf = q / Kp;
         int k = (int)(q % Kp);
         double a = k < kk ? ldexp(f[leaf * kk + k], -e) : 0.0;
-        split_slices(a, fsl + (leaf * kSlices) * Kp + k, Kp);
+        split_slices(a, fsl + slice_off(leaf, Kp, k), kKBlock);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *Ef = e;
 }
 
 // ---------------------------------------------------------------- the tcgen05 kernel
+// Barrier among `count` threads (a multiple of 32) that use the same id; id 0 is __syncthreads.
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     float bb = __fsub_rn(s, a);
@@ -123,13 +134,39 @@ struct SplitArgs {
     const int32_t* gcfg;  // table of each (group, table) entry
     const int32_t* gsrc;  // [entries][128] A row or -1
     const int32_t* gtgt;  // [n_groups][128] output row or -1
-    float2* out;          // [n_out_rows][Rp]
+    float2* out;          // [n_out_rows][Rp], or partial sums [split][n_out_rows][Rp] when split > 1
     int* err;
     int Kp, Rp, nchunks;
+    int split;            // CTAs sharing one group's tables (split-K over tables)
+    size_t part_stride;   // n_out_rows * Rp
 };
 
 // Accumulator of slice product (i, j): its diagonal i + j - 2; diagonals >= kNumAcc - 1 share the last.
 __host__ __device__ constexpr int acc_of(int i, int j) { return (i + j - 2) < (kNumAcc - 1) ? (i + j - 2) : (kNumAcc - 1); }
+
+// All slice products of one K block: accumulator acc_of(i, j); on the first K block of a
+// configuration the first product into each accumulator overwrites it.
+template <bool kFirst>
+__device__ __forceinline__ void issue_unit(uint32_t tmem, uint64_t ad0, uint64_t bd0) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, kTileN);
+    constexpr uint32_t A_SLICE = kTileM * 64, B_SLICE = kTileN * 64;
+#pragma unroll
+    for (int i = 1; i <= kSlices; ++i)
+#pragma unroll
+        for (int j = 1; j <= kSlices; ++j) {
+            if (i + j > kSlices + 1) continue;
+            const int acc = acc_of(i, j);
+            // first product of accumulator acc in (i, j) order: i == 1 for acc < kNumAcc - 1, else (1, kNumAcc)
+            const bool first_of_acc = (acc < kNumAcc - 1) ? (i == 1) : (i == 1 && j == kNumAcc);
+#pragma unroll
+            for (int ks = 0; ks < kKBlock / 16; ++ks) {
+                const uint64_t ad = ad0 + (((i - 1) * A_SLICE + ks * 32) >> 4);
+                const uint64_t bd = bd0 + (((j - 1) * B_SLICE + ks * 32) >> 4);
+                const uint32_t accum = (kFirst && first_of_acc && ks == 0) ? 0u : 1u;
+                tc::umma_bf16(tmem + acc * kTileN, ad, bd, idesc, accum);
+            }
+        }
+}
 
 // Warps 0..7: epilogue (lane quadrant w % 4, column half w / 4); warps 8..10: producers;
 // warp 11: TMEM allocation and the MMA issuer (lane 0). Twelve warps keep three warps per SM
@@ -139,13 +176,16 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
     __shared__ __align__(8) uint64_t bars[2 * kStages + 2];
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_flag;
+    __shared__ int32_t s_src[kTileM];
+    __shared__ volatile int p_abort;  // written by producers only, read after a producer barrier
     constexpr int N = kTileN;
     constexpr uint32_t A_SLICE = kTileM * 64;
     constexpr uint32_t B_SLICE = N * 64;
     constexpr uint32_t STAGE = kSlices * (A_SLICE + B_SLICE);
     constexpr int HALF = N / 2;  // columns per epilogue warp
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = blockIdx.x / a.nchunks, rc = blockIdx.x % a.nchunks;
+    const int q = blockIdx.x / a.nchunks, rc = blockIdx.x % a.nchunks;
+    const int g = q / a.split, sp = q % a.split;
     const uint32_t base = tc::smem_u32(dsm);
     const uint32_t sbase = (base + 1023u) & ~1023u;
     const uint32_t full0 = tc::smem_u32(&bars[0]);
@@ -160,6 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
         tc::mbar_init(acc_full, 1);
         tc::mbar_init(acc_empty, kEpilogueThreads);
         abort_flag = 0;
+        p_abort = 0;
         tc::mbar_fence_init();
     }
     if (warp == kMmaWarp) {
@@ -170,7 +211,9 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = tmem_holder;
-    const int cbeg = a.gptr[g], cend = a.gptr[g + 1];
+    const int gbeg = a.gptr[g], gcnt = a.gptr[g + 1] - gbeg;
+    const int cbeg = gbeg + (int)(((long long)gcnt * sp) / a.split);
+    const int cend = gbeg + (int)(((long long)gcnt * (sp + 1)) / a.split);
     const int ncfg = cend - cbeg;
     const int nkb = a.Kp / kKBlock;
     const int U = ncfg * nkb;
@@ -182,7 +225,11 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
         bool alive = true;
         for (int u = 0; u < U; ++u) {
             const int s = u & 1;
-            if (u >= 2 && !tc::mbar_wait(empty0 + 8 * s, ((u >> 1) - 1) & 1, &abort_flag)) {
+            if (u >= 2 && !tc::mbar_wait(empty0 + 8 * s, ((u >> 1) - 1) & 1, &abort_flag)) p_abort = 1;
+            // every producer passes this barrier once per unit, so the exit decision below is uniform
+            // and nobody rewrites s_src while another producer still reads it
+            named_bar_sync(1, kProducerThreads);
+            if (p_abort) {
                 abort_flag = 1;
                 atomicExch(a.err, 1);
                 alive = false;
@@ -190,19 +237,24 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
             }
             const int ci = cbeg + u / nkb, kb = u % nkb;
             const int cfg = a.gcfg[ci];
-            const int32_t* src = a.gsrc + (size_t)ci * kTileM;
-            const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
-            for (int q = ptid; q < kSlices * kTileM * 4; q += kProducerThreads) {
-                const int i = q / (kTileM * 4), rem = q % (kTileM * 4), m = rem >> 2, c = rem & 3;
-                const int sl = src[m];
-                const bf16* gp = a.asl + ((size_t)(sl < 0 ? 0 : sl) * kSlices + i) * a.Kp + kb * kKBlock + c * 8;
-                const uint32_t dst = sA + i * A_SLICE + m * 64 + ((c ^ ((m >> 1) & 3)) << 4);
-                tc::cp_async16(dst, gp, sl < 0 ? 0u : 16u);
+            if (kb == 0) {
+                // gather rows of this table for the 128 targets, once per table
+                for (int m = ptid; m < kTileM; m += kProducerThreads) s_src[m] = a.gsrc[(size_t)ci * kTileM + m];
+                named_bar_sync(1, kProducerThreads);
             }
-            for (int q = ptid; q < kSlices * N * 4; q += kProducerThreads) {
-                const int j = q / (N * 4), rem = q % (N * 4), n = rem >> 2, c = rem & 3;
-                const bf16* gp = a.bsl + (((size_t)cfg * a.Rp + r0 + n) * kSlices + j) * a.Kp + kb * kKBlock + c * 8;
-                const uint32_t dst = sB + j * B_SLICE + n * 64 + ((c ^ ((n >> 1) & 3)) << 4);
+            const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
+            // one warp instruction per row: lane = slice * 4 + 16-byte chunk (512 contiguous bytes)
+            const int pw = ptid >> 5, sl_i = (ptid & 31) >> 2, ch = ptid & 3;
+            for (int m = pw; m < kTileM; m += kProducerThreads / 32) {
+                const int src = s_src[m];
+                const bf16* gp = a.asl + (((size_t)(src < 0 ? 0 : src) * nkb + kb) * kSlices + sl_i) * kKBlock + ch * 8;
+                const uint32_t dst = sA + sl_i * A_SLICE + m * 64 + ((ch ^ ((m >> 1) & 3)) << 4);
+                tc::cp_async16(dst, gp, src < 0 ? 0u : 16u);
+            }
+            const bf16* bbase = a.bsl + ((size_t)cfg * a.Rp + r0) * nkb * kSlices * kKBlock;
+            for (int n = pw; n < N; n += kProducerThreads / 32) {
+                const bf16* gp = bbase + (((size_t)n * nkb + kb) * kSlices + sl_i) * kKBlock + ch * 8;
+                const uint32_t dst = sB + sl_i * B_SLICE + n * 64 + ((ch ^ ((n >> 1) & 3)) << 4);
                 tc::cp_async16(dst, gp, 16u);
             }
             tc::cp_async_commit();
@@ -218,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------ MMA issuer: one configuration at a time
         if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, N);
+            const uint64_t adesc_base = tc::smem_desc(sbase, 16, 512, tc::kLayoutSwizzle64B);
             bool alive = true;
             for (int c = 0; c < ncfg && alive; ++c) {
                 if (c >= 1 && !tc::mbar_wait(acc_empty, (c - 1) & 1, &abort_flag)) {
@@ -227,7 +279,6 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
                     break;
                 }
                 tc::tc_fence_after();
-                uint32_t started = 0;
                 for (int kb = 0; kb < nkb; ++kb) {
                     const int u = c * nkb + kb, s = u & 1;
                     if (!tc::mbar_wait(full0 + 8 * s, (u >> 1) & 1, &abort_flag)) {
@@ -237,20 +288,12 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
                         break;
                     }
                     tc::tc_fence_after();
-                    const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
-                    for (int i = 1; i <= kSlices; ++i)
-                        for (int j = 1; i + j <= kSlices + 1; ++j) {
-                            const int acc = acc_of(i, j);
-#pragma unroll
-                            for (int ks = 0; ks < kKBlock / 16; ++ks) {
-                                const uint64_t ad =
-                                    tc::smem_desc(sA + (i - 1) * A_SLICE + ks * 32, 16, 512, tc::kLayoutSwizzle64B);
-                                const uint64_t bd =
-                                    tc::smem_desc(sB + (j - 1) * B_SLICE + ks * 32, 16, 512, tc::kLayoutSwizzle64B);
-                                tc::umma_bf16(tmem + acc * N, ad, bd, idesc, (started >> acc) & 1u);
-                                started |= 1u << acc;
-                            }
-                        }
+                    // descriptors differ only in the 14-bit start-address field (address >> 4), so
+                    // offsets within the stage are added to a base descriptor
+                    const uint64_t ad0 = adesc_base + ((s * STAGE) >> 4);
+                    const uint64_t bd0 = adesc_base + ((s * STAGE + kSlices * A_SLICE) >> 4);
+                    if (kb == 0) issue_unit<true>(tmem, ad0, bd0);
+                    else issue_unit<false>(tmem, ad0, bd0);
                     tc::umma_commit(empty0 + 8 * s);
                 }
                 if (alive) tc::umma_commit(acc_full);
@@ -292,11 +335,12 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
             tc::tc_fence_before();
             tc::mbar_arrive(acc_empty);
         }
-        if (ok && ncfg > 0) {
+        if (ok) {
             const int m = quad * 32 + lane;
             const int tgt = a.gtgt[(size_t)g * kTileM + m];
             if (tgt >= 0) {
-                float4* o = reinterpret_cast<float4*>(a.out + (size_t)tgt * a.Rp + r0 + half * HALF);
+                float2* outp = a.split > 1 ? a.out + (size_t)sp * a.part_stride : a.out;
+                float4* o = reinterpret_cast<float4*>(outp + (size_t)tgt * a.Rp + r0 + half * HALF);
 #pragma unroll
                 for (int j = 0; j < HALF / 2; ++j) {
                     float h0 = __fadd_rn(hi[2 * j], lo[2 * j]);
@@ -349,7 +393,7 @@ void mixed_free(vfmm_ops* o) {
 // Groups of 128 targets sorted by `key`; per group the tables present and, per table, the A row
 // of each target (-1 when the target has no entry for that table).
 int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
-                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, SplitPlan* P) {
+                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, SplitPlan* P) {
     const int nt = (int)tgt_id.size();
     std::vector<int32_t> order(nt);
     for (int t = 0; t < nt; ++t) order[t] = t;
@@ -380,6 +424,16 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
     }
     P->n_groups = ng;
     P->entries = (int64_t)gcfg.size();
+    {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t ctas = (int64_t)std::max(ng, 1) * n_chunks;
+        const int64_t avg_cfg = ng ? (P->entries + ng - 1) / ng : 1;
+        int split = 1;
+        while (ctas * split < 2 * sms && avg_cfg / (split * 2) >= 2) split *= 2;
+        P->split = split;
+    }
     auto up = [](int32_t** dst, const std::vector<int32_t>& v) -> int {
         VFMM_CUDA(cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(int32_t)));
         if (!v.empty()) VFMM_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -401,8 +455,29 @@ void free_split_plan(SplitPlan* P) {
 
 static size_t smem_bytes() { return (size_t)kStages * kSlices * (kTileM * 64 + kTileN * 64) + 1024; }
 
+// out[row][r] = sum over the partial sums (double-float, exact two-sums).
+__global__ void split_reduce_kernel(const float2* __restrict__ part, size_t stride, int split, const int32_t* __restrict__ tgt,
+                                    int n_tgt, int Rp, float2* __restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n_tgt * Rp) return;
+    const int t = tgt[q / Rp];
+    if (t < 0) return;
+    const size_t o = (size_t)t * Rp + q % Rp;
+    float hi = 0.0f, lo = 0.0f;
+    for (int s = 0; s < split; ++s) {
+        float2 v = part[(size_t)s * stride + o];
+        float s1, e1, s2, e2;
+        two_sum(hi, v.x, s1, e1);
+        two_sum(s1, v.y, s2, e2);
+        hi = s2;
+        lo = __fadd_rn(lo, __fadd_rn(e1, e2));
+    }
+    float h = __fadd_rn(hi, lo);
+    out[o] = make_float2(h, __fsub_rn(lo, __fsub_rn(h, hi)));
+}
+
 int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int Rp, float2* out, int* err,
-               cudaStream_t st) {
+               float2* part, size_t n_out_rows, cudaStream_t st) {
     if (P.n_groups == 0) return VFMM_OK;
     if (Kp % kKBlock || Rp % kTileN) return fail(VFMM_ERR_INTERNAL, "split GEMM shape not tiled");
     static bool attr = false;
@@ -417,13 +492,21 @@ int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int
     a.gcfg = P.cfg;
     a.gsrc = P.src;
     a.gtgt = P.tgt;
-    a.out = out;
     a.err = err;
     a.Kp = Kp;
     a.Rp = Rp;
     a.nchunks = Rp / kTileN;
-    split_gemm_kernel<<<(unsigned)P.n_groups * a.nchunks, kThreads, smem_bytes(), st>>>(a);
+    a.split = part ? P.split : 1;
+    a.part_stride = n_out_rows * (size_t)Rp;
+    a.out = a.split > 1 ? part : out;
+    split_gemm_kernel<<<(unsigned)P.n_groups * a.split * a.nchunks, kThreads, smem_bytes(), st>>>(a);
     VFMM_CUDA(cudaGetLastError());
+    if (a.split > 1) {
+        const int64_t n = (int64_t)P.n_groups * kTileM * Rp;
+        split_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, a.part_stride, a.split, P.tgt,
+                                                                          P.n_groups * kTileM, Rp, out);
+        VFMM_CUDA(cudaGetLastError());
+    }
     return VFMM_OK;
 }
 
@@ -449,7 +532,8 @@ int build_mixed_plan(DeviceTree* T) {
         }
         key[t] = {sig, (uint64_t)t};
     }
-    VFMM_CHECK(build_split_plan(tgt, items, key, kNearCfg, &T->plan_near));
+    const int R = 3 * T->k * T->k;
+    VFMM_CHECK(build_split_plan(tgt, items, key, kNearCfg, (R + kTileN - 1) / kTileN, &T->plan_near));
     return build_far_plans(T);
 }
 
@@ -463,7 +547,7 @@ int near_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, const Mi
     f_slice_kernel<<<(unsigned)std::min<int64_t>(65535, (ns + 255) / 256), 256, 0, st>>>(f, T.n_leaves, kk, mo->Kp,
                                                                                          w.fmax, w.Ef, (bf16*)w.fsl);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(T.plan_near, w.fsl, mo->tsl, mo->Kp, mo->Rp, w.out, w.err, st);
+    return split_gemm(T.plan_near, w.fsl, mo->tsl, mo->Kp, mo->Rp, w.out, w.err, w.part, T.n_leaves, st);
 }
 
 }  // namespace vfmm

@@ -59,13 +59,15 @@ struct MixedWork {
     void* aprep = nullptr;                // bf16 [n_far_slots][kSlices][Kx]
     int* Et = nullptr;                    // [n_leaves]
     float2* far_out = nullptr;            // [n_leaves][Rp]
+    float2* part = nullptr;               // partial sums of split contractions (largest plan)
 };
 
 int build_split_plan(const std::vector<int32_t>& tgt_id,
                      const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
-                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, SplitPlan* P);
+                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, SplitPlan* P);
 int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int Rp, float2* out, int* err,
-               cudaStream_t st);
+               float2* part, size_t n_out_rows, cudaStream_t st);
+size_t split_part_elems(const DeviceTree& T, const vfmm_ops& o);
 int build_mixed_plan(DeviceTree* T);
 int build_far_plans(DeviceTree* T);
 int near_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, const MixedWork& w, cudaStream_t st);

@@ -31,6 +31,10 @@ namespace vfmm {
 
 using bf16 = __nv_bfloat16;
 
+__device__ __forceinline__ size_t slice_at(size_t row, int Kp, int k) {
+    return ((row * (Kp / kKBlock) + k / kKBlock) * kSlices) * kKBlock + (k % kKBlock);
+}
+
 __device__ inline void split_into(double a, bf16* out, int stride) {
 #pragma unroll
     for (int i = 1; i <= kSlices; ++i) {
@@ -70,7 +74,7 @@ __global__ void rows_slice_kernel(const double* __restrict__ M, int R, int K, in
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
         double v = (r < R && k < K) ? M[((size_t)c * R + r) * K + k] : 0.0;
         double a = r < R ? ldexp(v, -E[r]) : 0.0;
-        split_into(a, out + (((size_t)c * Rp + r) * kSlices) * Kp + k, Kp);
+        split_into(a, out + slice_at((size_t)c * Rp + r, Kp, k), kKBlock);
     }
 }
 
@@ -194,7 +198,7 @@ int build_far_plans(DeviceTree* T) {
             items[t].push_back({0, t});
             key[t] = {0, (uint64_t)t};
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1, &T->plan_s2m));
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, &T->plan_s2m));
     }
     // M2L: boxes with a V list, tables level * 40 + offset, A row = source box
     {
@@ -214,7 +218,7 @@ int build_far_plans(DeviceTree* T) {
             }
             key.push_back({(uint64_t)lev[b], sig});
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, (T->depth + 1) * kVCfg, &T->plan_m2l));
+        VFMM_CHECK(build_split_plan(tgt, items, key, (T->depth + 1) * kVCfg, 1, &T->plan_m2l));
     }
     // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
     {
@@ -238,12 +242,22 @@ int build_far_plans(DeviceTree* T) {
             }
             key[t] = {sig, (uint64_t)t};
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1 + kFarCfg, &T->plan_far));
+        const int R = 3 * T->k * T->k;
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1 + kFarCfg, (R + kTileN - 1) / kTileN, &T->plan_far));
         T->n_far_slots = slot[nl];
         VFMM_CUDA(cudaMalloc(&T->far_slot, (nl + 1) * sizeof(int32_t)));
         VFMM_CUDA(cudaMemcpy(T->far_slot, slot.data(), (nl + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
     return VFMM_OK;
+}
+
+// Largest partial-sum buffer any split contraction of this tree needs (float2 elements).
+size_t split_part_elems(const DeviceTree& T, const vfmm_ops& o) {
+    const MixedOps* mo = (const MixedOps*)o.mixed;
+    size_t a = T.plan_near.split > 1 ? (size_t)T.plan_near.split * T.n_leaves * mo->Rp : 0;
+    size_t b = T.plan_m2l.split > 1 ? (size_t)T.plan_m2l.split * T.n_boxes * mo->Rx : 0;
+    size_t c = T.plan_far.split > 1 ? (size_t)T.plan_far.split * T.n_leaves * mo->Rp : 0;
+    return std::max(a, std::max(b, c));
 }
 
 // ---------------------------------------------------------------- S2M
@@ -275,7 +289,7 @@ __global__ void s2m_finish_kernel(int nleaf, int kk, int p, int Rx, const int32_
 int s2m_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, double* Mexp, const MixedWork& w,
               cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    VFMM_CHECK(split_gemm(T.plan_s2m, w.fsl, mo->s2m_sl, mo->Kp, mo->Rx, w.s2m_out, w.err, st));
+    VFMM_CHECK(split_gemm(T.plan_s2m, w.fsl, mo->s2m_sl, mo->Kp, mo->Rx, w.s2m_out, w.err, nullptr, 0, st));
     s2m_finish_kernel<<<T.n_leaves, 128, 0, st>>>(T.n_leaves, o.k * o.k, o.p, mo->Rx, T.box_of_leaf, T.level, T.width,
                                                   f, o.s2m, w.s2m_out, mo->s2m_E, w.Ef, Mexp);
     VFMM_CUDA(cudaGetLastError());
@@ -307,7 +321,7 @@ __global__ void multipole_slice_kernel(const int32_t* __restrict__ level, int be
         int g = exp_of(__longlong_as_double((long long)gexp[(size_t)level[b] * Kx + k]));
         a = ldexp(Mexp[(size_t)b * P2 + k], -g);
     }
-    split_into(a, msl + ((size_t)b * kSlices) * Kx + k, Kx);
+    split_into(a, msl + slice_at(b, Kx, k), kKBlock);
 }
 
 // E[l][r] = exponent of max_{c,k} |MR[c][r][k]| 2^g(l,k)
@@ -338,7 +352,7 @@ __global__ void m2l_level_slice_kernel(const double* __restrict__ MR, int Rx, in
         double gk = __longlong_as_double((long long)gexp[(size_t)l * Kx + k]);
         double a = 0.0;
         if (gk > 0.0) a = ldexp(MR[((size_t)c * Rx + r) * Kx + k], exp_of(gk) - E[(size_t)l * Rx + r]);
-        split_into(a, out + (((size_t)(l * kVCfg + c) * Rx + r) * kSlices) * Kx + k, Kx);
+        split_into(a, out + slice_at((size_t)(l * kVCfg + c) * Rx + r, Kx, k), kKBlock);
     }
 }
 
@@ -360,7 +374,7 @@ int m2l_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const 
     m2l_level_slice_kernel<<<dim3(mo->Rx, kVCfg, nlev), 128, 0, st>>>(mo->m2l_real, mo->Rx, mo->Kx, w.gexp, w.m2l_E, 2,
                                                                       (bf16*)w.m2l_sl);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(T.plan_m2l, w.msl, w.m2l_sl, mo->Kx, mo->Rx, w.m2l_out, w.err, st);
+    return split_gemm(T.plan_m2l, w.msl, w.m2l_sl, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, T.n_boxes, st);
 }
 
 // ---------------------------------------------------------------- leaf far field
@@ -390,7 +404,7 @@ __global__ void far_operand_kernel(int nleaf, int P2, int Kx, const int32_t* __r
     if (threadIdx.x == 0) Et[leaf] = e;
     for (int q = threadIdx.x; q < ns * Kx; q += blockDim.x) {
         int j = q / Kx, k = q % Kx;
-        split_into(ldexp(value(j, k), -e), aprep + ((size_t)(s0 + j) * kSlices) * Kx + k, Kx);
+        split_into(ldexp(value(j, k), -e), aprep + slice_at(s0 + j, Kx, k), kKBlock);
     }
 }
 
@@ -401,7 +415,7 @@ int far_leaf_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, c
                                                    T.lptr[VFMM_LIST_W], T.lidx[VFMM_LIST_W], Mexp, Lexp, w.Et,
                                                    (bf16*)w.aprep);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(T.plan_far, w.aprep, mo->far_sl, mo->Kx, mo->Rp, w.far_out, w.err, st);
+    return split_gemm(T.plan_far, w.aprep, mo->far_sl, mo->Kx, mo->Rp, w.far_out, w.err, w.part, T.n_leaves, st);
 }
 
 }  // namespace vfmm

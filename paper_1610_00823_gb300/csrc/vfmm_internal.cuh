@@ -161,6 +161,7 @@ struct SplitPlan {
     int32_t* ptr = nullptr;  // [n_groups + 1]
     int32_t* cfg = nullptr;  // [entries] table index
     int32_t* src = nullptr;  // [entries][128] A row or -1
+    int32_t split = 1;       // CTAs per group (each takes a share of the group's tables)
 };
 
 struct DeviceTree {
