@@ -37,7 +37,10 @@ __device__ __forceinline__ double pow2(int e) {
 __global__ void m2l_c0_kernel(int begin, int end, int P, double width, const int32_t* __restrict__ level,
                               const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
                               const int32_t* __restrict__ vcfg, const double* __restrict__ m2l_t,
-                              const double* __restrict__ Mexp, double* __restrict__ c0) {
+                              const double* __restrict__ Mexp, double* __restrict__ c0,
+                              const int32_t* __restrict__ xptr, const int32_t* __restrict__ xidx,
+                              const int32_t* __restrict__ xcfg, const int32_t* __restrict__ leaf_of_box,
+                              const double* __restrict__ s2l_r0, const double* __restrict__ f, int kk) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     const int b = begin + warp;
     if (b >= end) return;
@@ -49,6 +52,16 @@ __global__ void m2l_c0_kernel(int begin, int end, int P, double width, const int
         double re = a[0] * logh;
         for (int n = 0; n < P; ++n) re += M[(size_t)n * P * 2] * a[2 * n] - M[(size_t)n * P * 2 + 1] * a[2 * n + 1];
         acc += re;
+    }
+    // X list: (2h)^2 [Re(S2L row 0) . f_c + log(h) W . f_c], with W . f_c = a_0(c) / (2h)^2
+    const double h = ldexp(width, -level[b]);
+    for (int e = xptr[b]; e < xptr[b + 1]; ++e) {
+        const double* fc = f + (size_t)leaf_of_box[xidx[e]] * kk;
+        const double* r0 = s2l_r0 + (size_t)xcfg[e] * kk;
+        double part = 0.0;
+        for (int s = lane; s < kk; s += 32) part += r0[s] * fc[s];
+        acc += 4.0 * h * h * part;
+        if (lane == 0) acc += logh * Mexp[(size_t)xidx[e] * 2 * P];
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) c0[b] = acc;
@@ -246,7 +259,10 @@ struct DownArgs {
     // split-precision M2L rows 2..2p+1 (null in the FP64 form): (hi, lo) scaled by 2^-E[level][r]
     const float2* m2l_out;
     const int* m2l_E;
-    const double* m2l_c0;  // Re of local coefficient 0 from the V list, with the log(h) term
+    const double* m2l_c0;  // Re of local coefficient 0 from the V and X lists, with the log(h) terms
+    const float2* s2l_out; // split-precision S2L rows 2..2p+1, scaled by 2^-(E_f + E_r)
+    const int* s2l_E;
+    const int* Ef;
     int Rx;
 };
 
@@ -289,7 +305,7 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
         }
         __syncthreads();
     }
-    for (int e = d.xptr[b]; e < d.xptr[b + 1]; ++e) {
+    for (int e = d.m2l_out ? d.xptr[b + 1] : d.xptr[b]; e < d.xptr[b + 1]; ++e) {
         const int c = d.xidx[e];
         const double* fc = d.f + (size_t)d.leaf_of_box[c] * d.kk;
         for (int q = t; q < d.kk; q += blockDim.x) src[q] = fc[q];
@@ -308,10 +324,17 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
         }
         __syncthreads();
     }
-    if (d.m2l_out && t < P && d.vptr[b + 1] > d.vptr[b]) {
+    if (d.m2l_out && t >= 1 && t < P && d.xptr[b + 1] > d.xptr[b]) {
+        const float2 vr = d.s2l_out[(size_t)b * d.Rx + 2 * (t - 1)];
+        const float2 vi = d.s2l_out[(size_t)b * d.Rx + 2 * (t - 1) + 1];
+        const double sc = 4.0 * h * h * pow2(*d.Ef);
+        re += sc * ((double)vr.x + (double)vr.y) * pow2(d.s2l_E[2 * (t - 1)]);
+        im += sc * ((double)vi.x + (double)vi.y) * pow2(d.s2l_E[2 * (t - 1) + 1]);
+    }
+    if (d.m2l_out && t < P && (d.vptr[b + 1] > d.vptr[b] || d.xptr[b + 1] > d.xptr[b])) {
         if (t == 0) {
             re += d.m2l_c0[b];
-        } else {
+        } else if (d.vptr[b + 1] > d.vptr[b]) {
             const float2 vr = d.m2l_out[(size_t)b * d.Rx + 2 * (t - 1)];
             const float2 vi = d.m2l_out[(size_t)b * d.Rx + 2 * (t - 1) + 1];
             re += ((double)vr.x + (double)vr.y) * pow2(d.m2l_E[(size_t)d.level * d.Rx + 2 * (t - 1)]);
@@ -514,6 +537,8 @@ static size_t layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, 
         if (w) w->mix.m2l_out = (float2*)p;
         take(&p, (size_t)T.n_boxes);
         if (w) w->mix.m2l_c0 = p;
+        take(&p, (size_t)T.n_boxes * mo->Rx);
+        if (w) w->mix.s2l_out = (float2*)p;
         take(&p, ((size_t)T.n_far_slots * kSlices * mo->Kx * 2 + 7) / 8);
         if (w) w->mix.aprep = (void*)p;
         take(&p, ((size_t)T.n_leaves + 1) / 2);
@@ -585,6 +610,9 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     d.m2l_out = mo ? w.mix.m2l_out : nullptr;
     d.m2l_E = mo ? w.mix.m2l_E : nullptr;
     d.m2l_c0 = mo ? w.mix.m2l_c0 : nullptr;
+    d.s2l_out = mo ? w.mix.s2l_out : nullptr;
+    d.s2l_E = mo ? mo->s2l_E : nullptr;
+    d.Ef = mo ? w.mix.Ef : nullptr;
     d.Rx = mo ? mo->Rx : 0;
 }
 
@@ -633,10 +661,12 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
         launches += T.depth + 4;
         const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
         const int warps = end - begin;
-        m2l_c0_kernel<<<(warps + 7) / 8, 256, 0, st>>>(begin, end, P, T.width, T.level, T.lptr[VFMM_LIST_V],
-                                                      T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V], o.m2l_t, w.Mexp,
-                                                      w.mix.m2l_c0);
-        ++launches;
+        m2l_c0_kernel<<<(warps + 7) / 8, 256, 0, st>>>(
+            begin, end, P, T.width, T.level, T.lptr[VFMM_LIST_V], T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V], o.m2l_t,
+            w.Mexp, w.mix.m2l_c0, T.lptr[VFMM_LIST_X], T.lidx[VFMM_LIST_X], T.lcfg[VFMM_LIST_X], T.leaf_of_box,
+            mo->s2l_r0, f, kk);
+        VFMM_CHECK(s2l_mixed(T, o, w.mix, st));
+        launches += 2;
     }
     for (int l = 2; l <= T.depth; ++l) {
         DownArgs d;

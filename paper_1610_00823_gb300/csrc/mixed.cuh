@@ -40,6 +40,9 @@ struct MixedOps {
     double* m2l_real = nullptr;  // [40][Rx][Kx] FP64: M2L rows 2..2p+1, input columns 0..2p+1
     void* far_sl = nullptr;   // bf16 [21][Rp][kSlices][Kx]: L2T (0) and M2T per W configuration
     int* far_E = nullptr;     // [Rp]
+    void* s2l_sl = nullptr;   // bf16 [20][Rx][kSlices][Kp]: S2L rows of coefficients 1..p
+    int* s2l_E = nullptr;     // [Rx]
+    double* s2l_r0 = nullptr; // [20][kk] FP64: Re of S2L row 0
 };
 
 struct MixedWork {
@@ -55,7 +58,8 @@ struct MixedWork {
     void* m2l_sl = nullptr;               // bf16 [(depth + 1) * 40][Rx][kSlices][Kx]
     int* m2l_E = nullptr;                 // [(depth + 1)][Rx]
     float2* m2l_out = nullptr;            // [n_boxes][Rx]
-    double* m2l_c0 = nullptr;             // [n_boxes] Re local coefficient 0 from the V list
+    double* m2l_c0 = nullptr;             // [n_boxes] Re local coefficient 0 from the V and X lists
+    float2* s2l_out = nullptr;            // [n_boxes][Rx]
     void* aprep = nullptr;                // bf16 [n_far_slots][kSlices][Kx]
     int* Et = nullptr;                    // [n_leaves]
     float2* far_out = nullptr;            // [n_leaves][Rp]
@@ -78,6 +82,7 @@ size_t far_workspace_doubles(const DeviceTree& T, const vfmm_ops& o);
 int s2m_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, double* Mexp, const MixedWork& w,
               cudaStream_t st);
 int m2l_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const MixedWork& w, cudaStream_t st);
+int s2l_mixed(const DeviceTree& T, const vfmm_ops& o, const MixedWork& w, cudaStream_t st);
 int far_leaf_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const double* Lexp,
                    const MixedWork& w, cudaStream_t st);
 

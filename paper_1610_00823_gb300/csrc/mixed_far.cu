@@ -161,11 +161,26 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
         }
     }
     VFMM_CHECK(slice_table(F, 1 + kFarCfg, R, KX, mo->Rp, mo->Kx, &mo->far_sl, &mo->far_E, st));
+    // S2L: rows 2..2p+1 (Re, Im of coefficients 1..p) over the k*k source values; row 0 kept in FP64
+    std::vector<double> st_((size_t)kFarCfg * kk * P * 2);
+    VFMM_CUDA(cudaMemcpy(st_.data(), o->s2l_t, st_.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> XL((size_t)kFarCfg * 2 * p * kk), X0((size_t)kFarCfg * kk);
+    for (int c = 0; c < kFarCfg; ++c)
+        for (int s = 0; s < kk; ++s) {
+            X0[(size_t)c * kk + s] = st_[(((size_t)c * kk + s) * P + 0) * 2];
+            for (int l = 1; l <= p; ++l) {
+                XL[((size_t)c * 2 * p + 2 * (l - 1)) * kk + s] = st_[(((size_t)c * kk + s) * P + l) * 2];
+                XL[((size_t)c * 2 * p + 2 * (l - 1) + 1) * kk + s] = st_[(((size_t)c * kk + s) * P + l) * 2 + 1];
+            }
+        }
+    VFMM_CHECK(slice_table(XL, kFarCfg, 2 * p, kk, mo->Rx, mo->Kp, &mo->s2l_sl, &mo->s2l_E, st));
+    VFMM_CUDA(cudaMalloc(&mo->s2l_r0, X0.size() * sizeof(double)));
+    VFMM_CUDA(cudaMemcpy(mo->s2l_r0, X0.data(), X0.size() * sizeof(double), cudaMemcpyHostToDevice));
     return VFMM_OK;
 }
 
 void far_free(MixedOps* mo) {
-    void* ps[] = {mo->s2m_sl, mo->s2m_E, mo->m2l_real, mo->far_sl, mo->far_E};
+    void* ps[] = {mo->s2m_sl, mo->s2m_E, mo->m2l_real, mo->far_sl, mo->far_E, mo->s2l_sl, mo->s2l_E, mo->s2l_r0};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
@@ -220,6 +235,26 @@ int build_far_plans(DeviceTree* T) {
         }
         VFMM_CHECK(build_split_plan(tgt, items, key, (T->depth + 1) * kVCfg, 1, &T->plan_m2l));
     }
+    // S2L: boxes with an X list, tables 20 configurations, A row = source leaf
+    {
+        std::vector<int32_t> ptr, idx, cfg;
+        VFMM_CHECK(fetch(VFMM_LIST_X, ptr, idx, cfg));
+        std::vector<int32_t> tgt;
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> items;
+        std::vector<std::pair<uint64_t, uint64_t>> key;
+        for (int b = 0; b < nb; ++b) {
+            if (ptr[b + 1] == ptr[b]) continue;
+            tgt.push_back(b);
+            items.emplace_back();
+            uint64_t sig = 0;
+            for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
+                items.back().push_back({cfg[e], lob[idx[e]]});
+                sig |= 1ull << cfg[e];
+            }
+            key.push_back({sig, (uint64_t)b});
+        }
+        VFMM_CHECK(build_split_plan(tgt, items, key, kFarCfg, 1, &T->plan_s2l));
+    }
     // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
     {
         std::vector<int32_t> ptr, idx, cfg;
@@ -257,7 +292,8 @@ size_t split_part_elems(const DeviceTree& T, const vfmm_ops& o) {
     size_t a = T.plan_near.split > 1 ? (size_t)T.plan_near.split * T.n_leaves * mo->Rp : 0;
     size_t b = T.plan_m2l.split > 1 ? (size_t)T.plan_m2l.split * T.n_boxes * mo->Rx : 0;
     size_t c = T.plan_far.split > 1 ? (size_t)T.plan_far.split * T.n_leaves * mo->Rp : 0;
-    return std::max(a, std::max(b, c));
+    size_t d = T.plan_s2l.split > 1 ? (size_t)T.plan_s2l.split * T.n_boxes * mo->Rx : 0;
+    return std::max(std::max(a, d), std::max(b, c));
 }
 
 // ---------------------------------------------------------------- S2M
@@ -375,6 +411,12 @@ int m2l_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const 
                                                                       (bf16*)w.m2l_sl);
     VFMM_CUDA(cudaGetLastError());
     return split_gemm(T.plan_m2l, w.msl, w.m2l_sl, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, T.n_boxes, st);
+}
+
+// ---------------------------------------------------------------- S2L
+int s2l_mixed(const DeviceTree& T, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
+    const MixedOps* mo = (const MixedOps*)o.mixed;
+    return split_gemm(T.plan_s2l, w.fsl, mo->s2l_sl, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part, T.n_boxes, st);
 }
 
 // ---------------------------------------------------------------- leaf far field

@@ -717,6 +717,7 @@ void free_tree(DeviceTree* t) {
     free_split_plan(&t->plan_s2m);
     free_split_plan(&t->plan_m2l);
     free_split_plan(&t->plan_far);
+    free_split_plan(&t->plan_s2l);
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int q = 0; q < 4; ++q) {

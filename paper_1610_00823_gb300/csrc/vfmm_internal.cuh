@@ -196,6 +196,7 @@ struct DeviceTree {
     SplitPlan plan_s2m;   // targets leaves, one table, A rows leaves
     SplitPlan plan_m2l;   // V list: targets boxes, tables level * 40 + offset, A rows boxes
     SplitPlan plan_far;   // L2T + W list: targets leaves, tables 0 (L2T) and 1 + W configuration
+    SplitPlan plan_s2l;   // X list: targets boxes, tables 20 configurations, A rows leaves
     int32_t* far_slot = nullptr;  // [n_leaves + 1] first A row of each leaf in the far operand
     int64_t n_far_slots = 0;
 };
