@@ -189,6 +189,28 @@ int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const
 int vfmm_volume_potential_noalloc(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
                                   double* u_dev, double* ux_dev, double* uy_dev, void* stream);
 
+/* CUDA-graph form of vfmm_volume_potential for repeated solves with the same buffers: the
+ * solve (all its kernels, copies and memsets) is captured once on `stream` into an executable
+ * graph; each launch replays it, reading f_dev and writing u_dev, ux_dev, uy_dev, using the
+ * workspace given at creation. The buffers must stay allocated for the graph's lifetime.
+ * Creation runs one ordinary solve first (so one-time kernel attributes are set outside the
+ * capture), then captures; it synchronises `stream`. Errors as vfmm_volume_potential. */
+typedef struct vfmm_graph vfmm_graph;
+int vfmm_graph_create(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs, double* u_dev,
+                      double* ux_dev, double* uy_dev, void* workspace_dev, size_t workspace_bytes, void* stream,
+                      vfmm_graph** out);
+int vfmm_graph_launch(const vfmm_graph* graph, void* stream);
+int vfmm_graph_destroy(vfmm_graph* graph);
+
+/* Work accounting for roofline reports: out[VFMM_N_WORK] =
+ * [0] BF16 tensor-core FLOPs the near-field contraction issues per solve (VFMM_MIXED: every
+ *     slice product of every tile, zero-padded rows included; 0 for VFMM_FP64),
+ * [1] the same for M2L, [2] for the leaf far field (L2T + M2T), [3] for S2L, [4] for S2M,
+ * [5] FP64-equivalent FLOPs of the near field, 2 * 3k^2 * k^2 per U-list entry,
+ * [6] number of U-list entries, [7] reserved (0). Host-only; no device work. */
+#define VFMM_N_WORK 8
+int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, double* out);
+
 /* Stage timers (tracing): the same solve as vfmm_volume_potential with CUDA events
  * recorded on `stream` between its stages; synchronises `stream` and returns the
  * elapsed milliseconds of each stage summed over the right-hand sides

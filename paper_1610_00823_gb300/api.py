@@ -224,3 +224,39 @@ def volume_potential_noalloc(tree: Tree, ops: Ops, f, out=None, stream=None):
          ctypes.c_void_p(out[0].data_ptr()), ctypes.c_void_p(out[1].data_ptr()), ctypes.c_void_p(out[2].data_ptr()),
          _stream(stream))
     return out
+
+
+WORK = ("near_tc_flops", "m2l_tc_flops", "far_tc_flops", "s2l_tc_flops", "s2m_tc_flops", "near_fp64eq_flops",
+        "u_entries", "reserved")
+
+
+def solve_work(tree: Tree, ops: Ops):
+    """Work counts of one solve (host-side accounting for roofline reports)."""
+    out = np.zeros(len(WORK), dtype=np.float64)
+    call("vfmm_solve_work", tree.handle, ops.handle, out.ctypes.data_as(c_double_p))
+    return dict(zip(WORK, out.tolist()))
+
+
+class SolveGraph:
+    """Captured solve (CUDA graph) for repeated calls with the same f/u buffers and workspace."""
+
+    def __init__(self, tree: Tree, ops: Ops, f, out, ws, stream):
+        n = tree.n_leaves * tree.k * tree.k
+        self._keep = (tree, ops, f, out, ws)
+        self._h = ctypes.c_void_p()
+        call("vfmm_graph_create", tree.handle, ops.handle, ctypes.c_void_p(f.data_ptr()), f.numel() // n,
+             ctypes.c_void_p(out[0].data_ptr()), ctypes.c_void_p(out[1].data_ptr()),
+             ctypes.c_void_p(out[2].data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream),
+             ctypes.byref(self._h))
+
+    def launch(self, stream=None):
+        call("vfmm_graph_launch", self._h, _stream(stream))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                _lib.load().vfmm_graph_destroy(h)
+            except Exception:
+                pass
+            self._h = None

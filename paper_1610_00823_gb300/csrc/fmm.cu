@@ -208,36 +208,63 @@ __global__ void __launch_bounds__(256) l2t_gemm_kernel(const double* __restrict_
     gemm_tile_fp64(L2T, 3 * kk, P2, blockIdx.x * GBM, ncols, cp);
 }
 
-// ---------------------------------------------------------------- M2M (one warp per box)
-__global__ void m2m_kernel(int begin, int end, int P, const int32_t* __restrict__ child0,
-                           const double* __restrict__ m2m_t, double* __restrict__ Mexp) {
-    extern __shared__ double sm[];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int wpb = blockDim.x / 32;
-    const int b = begin + blockIdx.x * wpb + warp;
-    double* a = sm + (size_t)warp * 4 * 2 * P;
-    const bool live = b < end && child0[b] >= 0;
-    if (live) {
-        const int c0 = child0[b];
-        for (int q = lane; q < 4 * 2 * P; q += 32) a[q] = Mexp[(size_t)(c0 + q / (2 * P)) * 2 * P + q % (2 * P)];
-    }
-    __syncwarp();
-    if (!live) return;
-    for (int out = lane; out < P; out += 32) {
-        double re = 0.0, im = 0.0;
-        for (int pos = 0; pos < 4; ++pos) {
-            const double* ac = a + pos * 2 * P;
-            const double* M = m2m_t + (size_t)pos * P * P * 2;
-            for (int n = 0; n <= out; ++n) {
-                double mr = M[((size_t)n * P + out) * 2], mi = M[((size_t)n * P + out) * 2 + 1];
-                double xr = ac[2 * n], xi = ac[2 * n + 1];
-                re = fma(mr, xr, fma(-mi, xi, re));
-                im = fma(mr, xi, fma(mi, xr, im));
+// ---------------------------------------------------------------- M2M and L2L (one CTA per non-leaf box)
+// The translations are triangular: M2M output l of the parent takes child coefficients n <= l,
+// L2L output m of a child takes parent coefficients l >= m. A thread owns one child position and
+// the output pair (j, P-1-j), so every thread does P + 1 complex multiply-adds and no zero
+// entry is read. mode 0 (M2M): in = the 4 consecutive child multipoles, out = parent multipole.
+// mode 1 (L2L): in = parent local, out = the 4 child locals (written, later added to by the
+// downward pass). Tables [pos][in][out] complex.
+__global__ void __launch_bounds__(128) translate_kernel(int mode, const int32_t* __restrict__ boxes, int nbox,
+                                                        const int32_t* __restrict__ child0, int P,
+                                                        const double2* __restrict__ tab, double2* __restrict__ ex) {
+    extern __shared__ double2 sx[];  // [4P] in, [4P] per-position results
+    const int bi = blockIdx.x;
+    if (bi >= nbox) return;
+    const int b = boxes[bi], c0 = child0[b];
+    double2* s_in = sx;
+    double2* s_out = sx + 4 * P;
+    const int nin = mode == 0 ? 4 * P : P;
+    const double2* src = ex + (size_t)(mode == 0 ? c0 : b) * P;
+    for (int q = threadIdx.x; q < nin; q += blockDim.x) s_in[q] = src[q];
+    __syncthreads();
+    const int npair = (P + 1) / 2;
+    for (int task = threadIdx.x; task < 4 * npair; task += blockDim.x) {
+        const int pos = task / npair, j = task - pos * npair;
+        const double2* M = tab + (size_t)pos * P * P;
+        const double2* x = mode == 0 ? s_in + pos * P : s_in;
+        for (int half = 0; half < 2; ++half) {
+            const int o = half == 0 ? j : P - 1 - j;
+            if (half == 1 && o == j) break;
+            const int n0 = mode == 0 ? 0 : o, n1 = mode == 0 ? o : P - 1;
+            double re = 0.0, im = 0.0;
+            for (int n = n0; n <= n1; ++n) {
+                const double2 m = M[(size_t)n * P + o], v = x[n];
+                re = fma(m.x, v.x, fma(-m.y, v.y, re));
+                im = fma(m.x, v.y, fma(m.y, v.x, im));
             }
+            s_out[pos * P + o] = make_double2(re, im);
         }
-        Mexp[(size_t)b * 2 * P + 2 * out] = re;
-        Mexp[(size_t)b * 2 * P + 2 * out + 1] = im;
     }
+    __syncthreads();
+    if (mode == 0) {
+        for (int o = threadIdx.x; o < P; o += blockDim.x) {
+            const double2 a0 = s_out[o], a1 = s_out[P + o], a2 = s_out[2 * P + o], a3 = s_out[3 * P + o];
+            ex[(size_t)b * P + o] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+        }
+    } else {
+        for (int q = threadIdx.x; q < 4 * P; q += blockDim.x) ex[(size_t)c0 * P + q] = s_out[q];
+    }
+}
+
+static void launch_translate(int mode, const DeviceTree& T, int level, int P, const double* tab, double* ex,
+                             cudaStream_t st) {
+    const int nbox = T.nonleaf_start[level + 1] - T.nonleaf_start[level];
+    if (nbox <= 0) return;
+    const int threads = std::min(128, ((4 * ((P + 1) / 2) + 31) / 32) * 32);
+    translate_kernel<<<nbox, threads, (size_t)8 * P * sizeof(double2), st>>>(
+        mode, T.nonleaf + T.nonleaf_start[level], nbox, T.child0, P, reinterpret_cast<const double2*>(tab),
+        reinterpret_cast<double2*>(ex));
 }
 
 // ---------------------------------------------------------------- downward pass (one CTA per box)
@@ -258,7 +285,8 @@ struct DownArgs {
     double* Lexp;
     // split-precision M2L rows 2..2p+1 (null in the FP64 form): (hi, lo) scaled by 2^-E[level][r]
     const float2* m2l_out;
-    const int* m2l_E;
+    const int* m2l_E;   // [Rx] row exponents of the M2L tables
+    const int* m2l_G;   // [depth + 1] level exponents of the multipole operand
     const double* m2l_c0;  // Re of local coefficient 0 from the V and X lists, with the log(h) terms
     const float2* s2l_out; // split-precision S2L rows 2..2p+1, scaled by 2^-(E_f + E_r)
     const int* s2l_E;
@@ -274,20 +302,10 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
     const double h = ldexp(d.width, -d.level);
     const double logh = log(h);
     double re = 0.0, im = 0.0;
-    if (d.level >= 3) {
-        const int par = d.parent[b];
-        for (int q = t; q < 2 * P; q += blockDim.x) src[q] = d.Lexp[(size_t)par * 2 * P + q];
-        __syncthreads();
-        const int pos = ((d.iy[b] & 1) << 1) | (d.ix[b] & 1);
-        const double* M = d.l2l_t + (size_t)pos * P * P * 2;
-        if (t < P)
-            for (int m = t; m < P; ++m) {  // c_t = sum_{m >= t}
-                double mr = M[((size_t)m * P + t) * 2], mi = M[((size_t)m * P + t) * 2 + 1];
-                double xr = src[2 * m], xi = src[2 * m + 1];
-                re = fma(mr, xr, fma(-mi, xi, re));
-                im = fma(mr, xi, fma(mi, xr, im));
-            }
-        __syncthreads();
+    if (d.level >= 3 && t < P) {
+        // L2L from the parent, written by translate_kernel just before this launch
+        re = d.Lexp[(size_t)b * 2 * P + 2 * t];
+        im = d.Lexp[(size_t)b * 2 * P + 2 * t + 1];
     }
     for (int e = d.m2l_out ? d.vptr[b + 1] : d.vptr[b]; e < d.vptr[b + 1]; ++e) {
         const int c = d.vidx[e];
@@ -337,8 +355,9 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
         } else if (d.vptr[b + 1] > d.vptr[b]) {
             const float2 vr = d.m2l_out[(size_t)b * d.Rx + 2 * (t - 1)];
             const float2 vi = d.m2l_out[(size_t)b * d.Rx + 2 * (t - 1) + 1];
-            re += ((double)vr.x + (double)vr.y) * pow2(d.m2l_E[(size_t)d.level * d.Rx + 2 * (t - 1)]);
-            im += ((double)vi.x + (double)vi.y) * pow2(d.m2l_E[(size_t)d.level * d.Rx + 2 * (t - 1) + 1]);
+            const int g = d.m2l_G[d.level];
+            re += ((double)vr.x + (double)vr.y) * pow2(g + d.m2l_E[2 * (t - 1)]);
+            im += ((double)vi.x + (double)vi.y) * pow2(g + d.m2l_E[2 * (t - 1) + 1]);
         }
     }
     if (t < P) {
@@ -525,14 +544,10 @@ static size_t layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, 
         const size_t nlev = (size_t)T.depth + 1;
         take(&p, (size_t)T.n_leaves * mo->Rx);
         if (w) w->mix.s2m_out = (float2*)p;
-        take(&p, nlev * mo->Kx);
-        if (w) w->mix.gexp = (unsigned long long*)p;
+        take(&p, (nlev + 1) / 2);
+        if (w) w->mix.glev = (int*)p;
         take(&p, ((size_t)T.n_boxes * kSlices * mo->Kx * 2 + 7) / 8);
         if (w) w->mix.msl = (void*)p;
-        take(&p, (nlev * kVCfg * mo->Rx * kSlices * mo->Kx * 2 + 7) / 8);
-        if (w) w->mix.m2l_sl = (void*)p;
-        take(&p, (nlev * mo->Rx + 1) / 2);
-        if (w) w->mix.m2l_E = (int*)p;
         take(&p, (size_t)T.n_boxes * mo->Rx);
         if (w) w->mix.m2l_out = (float2*)p;
         take(&p, (size_t)T.n_boxes);
@@ -608,7 +623,8 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     d.f = f;
     d.Lexp = w.Lexp;
     d.m2l_out = mo ? w.mix.m2l_out : nullptr;
-    d.m2l_E = mo ? w.mix.m2l_E : nullptr;
+    d.m2l_E = mo ? mo->m2l_E : nullptr;
+    d.m2l_G = mo ? w.mix.glev : nullptr;
     d.m2l_c0 = mo ? w.mix.m2l_c0 : nullptr;
     d.s2l_out = mo ? w.mix.s2l_out : nullptr;
     d.s2l_E = mo ? mo->s2l_E : nullptr;
@@ -644,14 +660,8 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
     // M2M, finest parents first (levels >= 2 are the ones the lists read)
     mark(se, ST_M2M, false, st);
     for (int l = T.depth - 1; l >= 2; --l) {
-        int begin = T.level_start[l], end = T.level_start[l + 1];
-        int wpb = 4;
-        int nb = (end - begin + wpb - 1) / wpb;
-        if (nb > 0) {
-            ++launches;
-            m2m_kernel<<<nb, 32 * wpb, (size_t)wpb * 4 * P2 * sizeof(double), st>>>(begin, end, P, T.child0, o.m2m_t,
-                                                                                   w.Mexp);
-        }
+        if (T.nonleaf_start[l + 1] > T.nonleaf_start[l]) ++launches;
+        launch_translate(0, T, l, P, o.m2m_t, w.Mexp, st);
     }
     mark(se, ST_M2M, true, st);
     // downward pass
@@ -672,10 +682,14 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
         DownArgs d;
         fill_down_args(d, T, o, f, w, l);
         int n = d.end - d.begin;
-        if (n > 0) {
+        if (n <= 0) continue;
+        if (l >= 3) {
+            // L2L for every box of level l (children of the non-leaf boxes of level l - 1)
+            launch_translate(1, T, l - 1, P, o.l2l_t, w.Lexp, st);
             ++launches;
-            down_kernel<<<n, 64, 0, st>>>(d);
         }
+        ++launches;
+        down_kernel<<<n, 64, 0, st>>>(d);
     }
     if (T.depth < 2) VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.n_boxes * P2 * sizeof(double), st));
     else VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.level_start[2] * P2 * sizeof(double), st));
@@ -859,4 +873,57 @@ extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_
     *launches = se.launches;
     if (rc == VFMM_OK) rc = read_status(w);
     return rc;
+}
+
+struct vfmm_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" int vfmm_graph_create(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
+                                 double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
+                                 size_t workspace_bytes, void* stream, vfmm_graph** out) {
+    if (!out) return fail(VFMM_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (st == nullptr) return fail(VFMM_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    VFMM_CHECK(vfmm_volume_potential(tree, ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, workspace_dev, workspace_bytes,
+                                     stream));
+    VFMM_CUDA(cudaStreamSynchronize(st));
+    vfmm_graph* g = new vfmm_graph();
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    int rc = vfmm_volume_potential(tree, ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, workspace_dev, workspace_bytes,
+                                   stream);
+    e = cudaStreamEndCapture(st, &g->graph);
+    if (rc != VFMM_OK || e != cudaSuccess) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return rc != VFMM_OK ? rc : cuda_fail(e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g->graph);
+        delete g;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    *out = g;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_graph_launch(const vfmm_graph* g, void* stream) {
+    if (!g) return fail(VFMM_ERR_INVALID_ARG, "null graph");
+    VFMM_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_graph_destroy(vfmm_graph* g) {
+    if (!g) return VFMM_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return VFMM_OK;
 }

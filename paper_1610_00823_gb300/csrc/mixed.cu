@@ -46,17 +46,6 @@ __device__ __forceinline__ size_t slice_off(size_t row, int Kp, int k) {
     return ((row * (Kp / kKBlock) + k / kKBlock) * kSlices) * kKBlock + (k % kKBlock);
 }
 
-__device__ inline void split_slices(double a, bf16* out, int stride) {
-    // a in (-1, 1): m_i = trunc(64 * rest), rest <- 64 * rest - m_i (all exact in FP64)
-#pragma unroll
-    for (int i = 1; i <= kSlices; ++i) {
-        double t = a * 64.0;
-        double m = trunc(t);
-        a = t - m;
-        out[(i - 1) * stride] = __float2bfloat16_rn(ldexpf((float)m, -6 * i));
-    }
-}
-
 // E_r[r] = exponent e with max_{cfg,k} |T_cfg[r][k]| < 2^e (0 for all-zero rows).
 __global__ void table_row_exp_kernel(const double* __restrict__ T, int R, int kk, int* __restrict__ Er) {
     __shared__ double red[256];
@@ -85,8 +74,7 @@ __global__ void table_slice_kernel(const double* __restrict__ T, int R, int kk, 
     const int cfg = blockIdx.y, r = blockIdx.x;
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
         double v = (r < R && k < kk) ? T[((size_t)cfg * R + r) * kk + k] : 0.0;
-        double a = (r < R) ? ldexp(v, -Er[r]) : 0.0;
-        split_slices(a, tsl + slice_off((size_t)cfg * Rp + r, Kp, k), kKBlock);
+        slice_fixed(v, r < R ? Er[r] : 0, tsl + slice_off((size_t)cfg * Rp + r, Kp, k), kKBlock);
     }
 }
 
@@ -109,8 +97,7 @@ __global__ void f_slice_kernel(const double* __restrict__ f, int nleaf, int kk, 
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         int64_t leaf = q / Kp;
         int k = (int)(q % Kp);
-        double a = k < kk ? ldexp(f[leaf * kk + k], -e) : 0.0;
-        split_slices(a, fsl + slice_off(leaf, Kp, k), kKBlock);
+        slice_fixed(k < kk ? f[leaf * kk + k] : 0.0, e, fsl + slice_off(leaf, Kp, k), kKBlock);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *Ef = e;
 }
@@ -243,16 +230,21 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
                 named_bar_sync(1, kProducerThreads);
             }
             const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
-            // one warp instruction per row: lane = slice * 4 + 16-byte chunk (512 contiguous bytes)
-            const int pw = ptid >> 5, sl_i = (ptid & 31) >> 2, ch = ptid & 3;
-            for (int m = pw; m < kTileM; m += kProducerThreads / 32) {
+            // a warp instruction covers 8 rows x 64 bytes of one slice: 512 contiguous bytes of shared
+            // memory (no bank conflicts) from eight 64-byte pieces of global memory
+            const int lrow = (ptid & 31) >> 2, ch = ptid & 3, pw = ptid >> 5;
+#pragma unroll 4
+            for (int q = pw; q < kSlices * (kTileM / 8); q += kProducerThreads / 32) {
+                const int sl_i = q / (kTileM / 8), m = (q % (kTileM / 8)) * 8 + lrow;
                 const int src = s_src[m];
                 const bf16* gp = a.asl + (((size_t)(src < 0 ? 0 : src) * nkb + kb) * kSlices + sl_i) * kKBlock + ch * 8;
                 const uint32_t dst = sA + sl_i * A_SLICE + m * 64 + ((ch ^ ((m >> 1) & 3)) << 4);
                 tc::cp_async16(dst, gp, src < 0 ? 0u : 16u);
             }
             const bf16* bbase = a.bsl + ((size_t)cfg * a.Rp + r0) * nkb * kSlices * kKBlock;
-            for (int n = pw; n < N; n += kProducerThreads / 32) {
+#pragma unroll 4
+            for (int q = pw; q < kSlices * (N / 8); q += kProducerThreads / 32) {
+                const int sl_i = q / (N / 8), n = (q % (N / 8)) * 8 + lrow;
                 const bf16* gp = bbase + (((size_t)n * nkb + kb) * kSlices + sl_i) * kKBlock + ch * 8;
                 const uint32_t dst = sB + sl_i * B_SLICE + n * 64 + ((ch ^ ((n >> 1) & 3)) << 4);
                 tc::cp_async16(dst, gp, 16u);

@@ -1,6 +1,7 @@
 // Split-BF16 near field: constants and device buffers.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,6 +27,26 @@ constexpr int kMmaWarp = kEpilogueWarps + kProducerThreads / 32;  // 11
 constexpr int kThreads = 32 * (kMmaWarp + 1);                     // 384: 3 warps per SM sub-partition
 static_assert(kNumAcc * kTileN <= kTmemCols, "TMEM budget");
 
+// Splits v / 2^E (|v| < 2^E) into kSlices signed base-64 digits, out[(i - 1) * stride] =
+// sign(v) d_i 2^(-6 i), d_i = floor(|v| 2^(6 i - E)) mod 64: the digits that repeated
+// t <- 64 t, d <- trunc(t), t <- t - d give in exact arithmetic, taken here from the bits of v
+// with integer operations (v's significand shifted to 48 fractional bits).
+__device__ __forceinline__ void slice_fixed(double v, int E, __nv_bfloat16* out, int stride) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    int ev = (int)((bits >> 52) & 0x7FF);
+    unsigned long long mant = bits & ((1ull << 52) - 1);
+    if (ev) mant |= 1ull << 52;
+    else ev = 1;
+    const int shift = 1027 - ev + E;  // |v| 2^(48 - E) = mant 2^-(1027 - ev + E); > 0 when |v| < 2^E
+    const unsigned long long q = shift >= 64 ? 0ull : mant >> (shift < 0 ? 0 : shift);
+    const bool neg = (bits >> 63) != 0;
+#pragma unroll
+    for (int i = 1; i <= kSlices; ++i) {
+        const float s = (float)((q >> (48 - 6 * i)) & 63ull) * __int_as_float((127 - 6 * i) << 23);
+        out[(i - 1) * stride] = __float2bfloat16_rn(neg ? -s : s);
+    }
+}
+
 struct MixedOps {
     int N = kTileN; // table rows per tile
     int Rp = 0;     // 3k^2 rounded up to N
@@ -37,7 +58,10 @@ struct MixedOps {
     int Rx = 0;           // 2p rounded up to kTileN (rows of S2M and M2L without coefficient 0)
     void* s2m_sl = nullptr;   // bf16 [1][Rx][kSlices][Kp]: S2M rows 2..2p+1
     int* s2m_E = nullptr;     // [Rx]
-    double* m2l_real = nullptr;  // [40][Rx][Kx] FP64: M2L rows 2..2p+1, input columns 0..2p+1
+    // M2L rows 2..2p+1 over input columns 0..2p+1, column k scaled by 2^-floor(k/4) (the decay
+    // bound of multipole coefficient k/2), then per row by 2^-m2l_E[r]
+    void* m2l_sl = nullptr;   // bf16 [40][Rx][kSlices][Kx]
+    int* m2l_E = nullptr;     // [Rx]
     void* far_sl = nullptr;   // bf16 [21][Rp][kSlices][Kx]: L2T (0) and M2T per W configuration
     int* far_E = nullptr;     // [Rp]
     void* s2l_sl = nullptr;   // bf16 [20][Rx][kSlices][Kp]: S2L rows of coefficients 1..p
@@ -53,10 +77,8 @@ struct MixedWork {
     int* err = nullptr;                   // non-zero after a bounded wait expired
     // far field
     float2* s2m_out = nullptr;            // [n_leaves][Rx]
-    unsigned long long* gexp = nullptr;   // [depth + 1][Kx] max |multipole coefficient| per level (bits)
+    int* glev = nullptr;                  // [depth + 1] G(l): |coefficient k| 2^floor(k/4) < 2^G(l) on level l
     void* msl = nullptr;                  // bf16 [n_boxes][kSlices][Kx]
-    void* m2l_sl = nullptr;               // bf16 [(depth + 1) * 40][Rx][kSlices][Kx]
-    int* m2l_E = nullptr;                 // [(depth + 1)][Rx]
     float2* m2l_out = nullptr;            // [n_boxes][Rx]
     double* m2l_c0 = nullptr;             // [n_boxes] Re local coefficient 0 from the V and X lists
     float2* s2l_out = nullptr;            // [n_boxes][Rx]

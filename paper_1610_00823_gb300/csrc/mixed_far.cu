@@ -7,11 +7,12 @@
 // carries a power-of-two scale):
 //  * S2M: A = f slices (global exponent, shared with the near field); table rows = S2M rows of
 //    coefficients 1..p (row exponents). Coefficient 0 (the mass) is an FP64 dot product.
-//  * M2L: A = multipole coefficients of a level divided by 2^g(l, k), g = exponent of the
-//    level's largest |coefficient k| (k runs over the real and imaginary parts); the table
-//    columns are multiplied by 2^g(l, k), so there is one table set per level, normalised per
-//    (level, output row). All levels go in one launch (table index = level * 40 + offset).
-//    Output coefficient 0 and the log(h) term are added in FP64 by the downward kernel.
+//  * M2L: A = multipole coefficient k (k runs over real and imaginary parts of a_0..a_p) times
+//    2^(floor(k/4) - G(l)): 2^-floor(n/2), n = k/2, bounds the decay of scaled coefficient n, and
+//    G(l) is the level's exponent, so every level shares one table set (columns times
+//    2^-floor(k/4), rows normalised once) and all levels go in one launch. Output row r is
+//    scaled back by 2^(G(l) + E_r). Output coefficient 0 and the log(h) term are added in FP64
+//    by the downward kernel.
 //  * Leaf: A = the leaf's own local coefficients 1..p and the multipoles of its W boxes, all
 //    divided by 2^E_t, E_t the exponent of the leaf's largest such value; tables: L2T and the
 //    20 M2T configurations (factor h / h_w = 2 folded into the gradient rows), row exponents.
@@ -19,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -33,16 +35,6 @@ using bf16 = __nv_bfloat16;
 
 __device__ __forceinline__ size_t slice_at(size_t row, int Kp, int k) {
     return ((row * (Kp / kKBlock) + k / kKBlock) * kSlices) * kKBlock + (k % kKBlock);
-}
-
-__device__ inline void split_into(double a, bf16* out, int stride) {
-#pragma unroll
-    for (int i = 1; i <= kSlices; ++i) {
-        double t = a * 64.0;
-        double m = trunc(t);
-        a = t - m;
-        out[(i - 1) * stride] = __float2bfloat16_rn(ldexpf((float)m, -6 * i));
-    }
 }
 
 __device__ inline int exp_of(double m) {
@@ -73,8 +65,7 @@ __global__ void rows_slice_kernel(const double* __restrict__ M, int R, int K, in
     const int r = blockIdx.x, c = blockIdx.y;
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
         double v = (r < R && k < K) ? M[((size_t)c * R + r) * K + k] : 0.0;
-        double a = r < R ? ldexp(v, -E[r]) : 0.0;
-        split_into(a, out + slice_at((size_t)c * Rp + r, Kp, k), kKBlock);
+        slice_fixed(v, r < R ? E[r] : 0, out + slice_at((size_t)c * Rp + r, Kp, k), kKBlock);
     }
 }
 
@@ -121,8 +112,11 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
                 MR[(rr + 1) * mo->Kx + 2 * n] = im;
                 MR[(rr + 1) * mo->Kx + 2 * n + 1] = re;
             }
-    VFMM_CUDA(cudaMalloc(&mo->m2l_real, MR.size() * sizeof(double)));
-    VFMM_CUDA(cudaMemcpy(mo->m2l_real, MR.data(), MR.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // |a~_n| <= mass (1/sqrt 2)^n for a box's scaled multipole coefficients, so column k (coefficient
+    // n = k / 2) carries the bound 2^-floor(n/2); the operand is divided by it and the table times it
+    for (size_t r = 0; r < (size_t)kVCfg * mo->Rx; ++r)
+        for (int q = 0; q < mo->Kx; ++q) MR[r * mo->Kx + q] = std::ldexp(MR[r * mo->Kx + q], -(q >> 2));
+    VFMM_CHECK(slice_table(MR, kVCfg, mo->Rx, mo->Kx, mo->Rx, mo->Kx, &mo->m2l_sl, &mo->m2l_E, st));
     // leaf tables: 0 = L2T without coefficient 0, 1 + c = M2T of W configuration c
     std::vector<double> l2t((size_t)R * 2 * P), xh(k);
     VFMM_CUDA(cudaMemcpy(l2t.data(), o->l2t, l2t.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -180,7 +174,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
 }
 
 void far_free(MixedOps* mo) {
-    void* ps[] = {mo->s2m_sl, mo->s2m_E, mo->m2l_real, mo->far_sl, mo->far_E, mo->s2l_sl, mo->s2l_E, mo->s2l_r0};
+    void* ps[] = {mo->s2m_sl, mo->s2m_E, mo->m2l_sl, mo->m2l_E, mo->far_sl, mo->far_E, mo->s2l_sl, mo->s2l_E, mo->s2l_r0};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
@@ -215,7 +209,7 @@ int build_far_plans(DeviceTree* T) {
         }
         VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, &T->plan_s2m));
     }
-    // M2L: boxes with a V list, tables level * 40 + offset, A row = source box
+    // M2L: boxes with a V list, tables = the 40 offsets, A row = source box
     {
         std::vector<int32_t> ptr, idx, cfg;
         VFMM_CHECK(fetch(VFMM_LIST_V, ptr, idx, cfg));
@@ -228,12 +222,12 @@ int build_far_plans(DeviceTree* T) {
             items.emplace_back();
             uint64_t sig = 0;
             for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
-                items.back().push_back({lev[b] * kVCfg + cfg[e], idx[e]});
+                items.back().push_back({cfg[e], idx[e]});
                 sig |= 1ull << cfg[e];
             }
-            key.push_back({(uint64_t)lev[b], sig});
+            key.push_back({sig, (uint64_t)b});
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, (T->depth + 1) * kVCfg, 1, &T->plan_m2l));
+        VFMM_CHECK(build_split_plan(tgt, items, key, kVCfg, 1, &T->plan_m2l));
     }
     // S2L: boxes with an X list, tables 20 configurations, A row = source leaf
     {
@@ -333,63 +327,36 @@ int s2m_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, double* M
 }
 
 // ---------------------------------------------------------------- M2L
-// Max |coefficient k| over the boxes of one level: thread k scans a chunk of 256 boxes, then
-// one atomic per (block, k).
-__global__ void level_max_kernel(int lvl, int begin, int end, int P2, const double* __restrict__ Mexp,
-                                 unsigned long long* __restrict__ gexp, int Kx) {
-    const int k = threadIdx.x;
-    if (k >= P2) return;
-    const int b0 = begin + blockIdx.x * 256, b1 = min(end, b0 + 256);
-    double m = 0.0;
-    for (int b = b0; b < b1; ++b) m = fmax(m, fabs(Mexp[(size_t)b * P2 + k]));
-    if (m > 0.0) atomicMax(&gexp[(size_t)lvl * Kx + k], (unsigned long long)__double_as_longlong(m));
+// G(l) = max over the level's boxes and coefficients k of the binary exponent of |a_k| 2^floor(k/4)
+// (frexp convention, from the bits: integer work only), so that |a_k| 2^floor(k/4) < 2^G(l).
+constexpr int kLevelChunk = 64;  // boxes per CTA
+__global__ void level_exp_kernel(const int32_t* __restrict__ level, int begin, int end, int P2,
+                                 const double* __restrict__ Mexp, int* __restrict__ G) {
+    __shared__ int sG[32];
+    if (threadIdx.x < 32) sG[threadIdx.x] = INT_MIN;
+    __syncthreads();
+    const int b0 = begin + blockIdx.x * kLevelChunk, b1 = min(end, b0 + kLevelChunk);
+    for (int q = threadIdx.x; q < (b1 - b0) * P2; q += blockDim.x) {
+        const int b = b0 + q / P2, k = q % P2;
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(Mexp[(size_t)b * P2 + k]);
+        if ((bits << 1) == 0) continue;  // +-0
+        int ev = (int)((bits >> 52) & 0x7FF);
+        if (ev == 0) ev = 1;
+        atomicMax(&sG[level[b] & 31], ev - 1022 + (k >> 2));
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && sG[threadIdx.x] != INT_MIN) atomicMax(&G[threadIdx.x], sG[threadIdx.x]);
 }
 
 __global__ void multipole_slice_kernel(const int32_t* __restrict__ level, int begin, int end, int P2, int Kx,
-                                       const double* __restrict__ Mexp, const unsigned long long* __restrict__ gexp,
+                                       const double* __restrict__ Mexp, const int* __restrict__ G,
                                        bf16* __restrict__ msl) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t total = (int64_t)(end - begin) * Kx;
     if (q >= total) return;
     int b = begin + (int)(q / Kx), k = (int)(q % Kx);
-    double a = 0.0;
-    if (k < P2) {
-        int g = exp_of(__longlong_as_double((long long)gexp[(size_t)level[b] * Kx + k]));
-        a = ldexp(Mexp[(size_t)b * P2 + k], -g);
-    }
-    split_into(a, msl + slice_at(b, Kx, k), kKBlock);
-}
-
-// E[l][r] = exponent of max_{c,k} |MR[c][r][k]| 2^g(l,k)
-__global__ void m2l_level_exp_kernel(const double* __restrict__ MR, int Rx, int Kx,
-                                     const unsigned long long* __restrict__ gexp, int lmin, int* __restrict__ E) {
-    __shared__ double red[256];
-    const int r = blockIdx.x, l = lmin + blockIdx.y;
-    double m = 0.0;
-    for (int q = threadIdx.x; q < kVCfg * Kx; q += blockDim.x) {
-        int c = q / Kx, k = q % Kx;
-        double gk = __longlong_as_double((long long)gexp[(size_t)l * Kx + k]);
-        if (gk > 0.0) m = fmax(m, ldexp(fabs(MR[((size_t)c * Rx + r) * Kx + k]), exp_of(gk)));
-    }
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) E[(size_t)l * Rx + r] = exp_of(red[0]);
-}
-
-__global__ void m2l_level_slice_kernel(const double* __restrict__ MR, int Rx, int Kx,
-                                       const unsigned long long* __restrict__ gexp, const int* __restrict__ E,
-                                       int lmin, bf16* __restrict__ out) {
-    const int r = blockIdx.x, c = blockIdx.y, l = lmin + blockIdx.z;
-    for (int k = threadIdx.x; k < Kx; k += blockDim.x) {
-        double gk = __longlong_as_double((long long)gexp[(size_t)l * Kx + k]);
-        double a = 0.0;
-        if (gk > 0.0) a = ldexp(MR[((size_t)c * Rx + r) * Kx + k], exp_of(gk) - E[(size_t)l * Rx + r]);
-        split_into(a, out + slice_at((size_t)(l * kVCfg + c) * Rx + r, Kx, k), kKBlock);
-    }
+    const double a = k < P2 ? Mexp[(size_t)b * P2 + k] : 0.0;
+    slice_fixed(a, G[level[b]] - (k >> 2), msl + slice_at(b, Kx, k), kKBlock);
 }
 
 int m2l_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const MixedWork& w, cudaStream_t st) {
@@ -397,20 +364,15 @@ int m2l_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const 
     if (T.depth < 2 || T.plan_m2l.n_groups == 0) return VFMM_OK;
     const int P2 = 2 * (o.p + 1);
     const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
-    VFMM_CUDA(cudaMemsetAsync(w.gexp, 0, (size_t)(T.depth + 1) * mo->Kx * sizeof(unsigned long long), st));
-    for (int l = 2; l <= T.depth; ++l) {
-        const int lb = T.level_start[l], le = T.level_start[l + 1];
-        if (le > lb) level_max_kernel<<<(le - lb + 255) / 256, 128, 0, st>>>(l, lb, le, P2, Mexp, w.gexp, mo->Kx);
-    }
+    // 0x80 bytes: a very negative start value (levels whose multipoles are all zero keep it)
+    VFMM_CUDA(cudaMemsetAsync(w.glev, 0x80, (size_t)(T.depth + 1) * sizeof(int), st));
+    level_exp_kernel<<<(end - begin + kLevelChunk - 1) / kLevelChunk, 256, 0, st>>>(T.level, begin, end, P2, Mexp,
+                                                                                  w.glev);
     int64_t n2 = (int64_t)(end - begin) * mo->Kx;
     multipole_slice_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(T.level, begin, end, P2, mo->Kx, Mexp,
-                                                                          w.gexp, (bf16*)w.msl);
-    const int nlev = T.depth - 1;  // levels 2..depth
-    m2l_level_exp_kernel<<<dim3(mo->Rx, nlev), 256, 0, st>>>(mo->m2l_real, mo->Rx, mo->Kx, w.gexp, 2, w.m2l_E);
-    m2l_level_slice_kernel<<<dim3(mo->Rx, kVCfg, nlev), 128, 0, st>>>(mo->m2l_real, mo->Rx, mo->Kx, w.gexp, w.m2l_E, 2,
-                                                                      (bf16*)w.m2l_sl);
+                                                                          w.glev, (bf16*)w.msl);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(T.plan_m2l, w.msl, w.m2l_sl, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, T.n_boxes, st);
+    return split_gemm(T.plan_m2l, w.msl, mo->m2l_sl, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, T.n_boxes, st);
 }
 
 // ---------------------------------------------------------------- S2L
@@ -446,7 +408,7 @@ __global__ void far_operand_kernel(int nleaf, int P2, int Kx, const int32_t* __r
     if (threadIdx.x == 0) Et[leaf] = e;
     for (int q = threadIdx.x; q < ns * Kx; q += blockDim.x) {
         int j = q / Kx, k = q % Kx;
-        split_into(ldexp(value(j, k), -e), aprep + slice_at(s0 + j, Kx, k), kKBlock);
+        slice_fixed(value(j, k), e, aprep + slice_at(s0 + j, Kx, k), kKBlock);
     }
 }
 
@@ -461,3 +423,29 @@ int far_leaf_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, c
 }
 
 }  // namespace vfmm
+
+using namespace vfmm;
+
+extern "C" int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, double* out) {
+    if (!tree || !ops || !out) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    const DeviceTree& T = tree->t;
+    for (int i = 0; i < VFMM_N_WORK; ++i) out[i] = 0.0;
+    const double kk = (double)ops->k * ops->k;
+    out[5] = 2.0 * 3.0 * kk * kk * (double)T.llen[VFMM_LIST_U];
+    out[6] = (double)T.llen[VFMM_LIST_U];
+    const MixedOps* mo = (const MixedOps*)ops->mixed;
+    if (ops->precision != VFMM_MIXED || !mo) return VFMM_OK;
+    int np = 0;
+    for (int i = 1; i <= kSlices; ++i)
+        for (int j = 1; i + j <= kSlices + 1; ++j) ++np;
+    // per table of a tile and per K value: np products of 128 x kTileN MACs
+    auto tc = [&](const SplitPlan& P, int Kp, int Rp) {
+        return 2.0 * (double)P.entries * (Rp / kTileN) * (double)Kp * np * kTileM * kTileN;
+    };
+    out[0] = tc(T.plan_near, mo->Kp, mo->Rp);
+    out[1] = tc(T.plan_m2l, mo->Kx, mo->Rx);
+    out[2] = tc(T.plan_far, mo->Kx, mo->Rp);
+    out[3] = tc(T.plan_s2l, mo->Kp, mo->Rx);
+    out[4] = tc(T.plan_s2m, mo->Kp, mo->Rx);
+    return VFMM_OK;
+}

@@ -43,8 +43,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const v
 }
 
 // ---------------------------------------------------------------- cp.async (16 B, L2 only)
+// No memory clobber: the destination is read only after cp.async.wait_group plus a barrier (both
+// clobber memory), and leaving it out lets the compiler batch the address loads of many copies.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>

@@ -705,6 +705,22 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
     T->level_start_dev = lsd.release();
     VFMM_CHECK(compute_lists(T, st));
     VFMM_CUDA(cudaStreamSynchronize(st));
+    {
+        // non-leaf boxes per level (for the per-level M2M and L2L GEMMs)
+        std::vector<int32_t> c0(n);
+        VFMM_CUDA(cudaMemcpy(c0.data(), T->child0, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        std::vector<int32_t> nl;
+        T->nonleaf_start.assign(depth + 2, 0);
+        for (int l = 0; l <= depth; ++l) {
+            T->nonleaf_start[l] = (int32_t)nl.size();
+            for (int b = T->level_start[l]; b < T->level_start[l + 1]; ++b)
+                if (c0[b] >= 0) nl.push_back(b);
+        }
+        T->nonleaf_start[depth + 1] = (int32_t)nl.size();
+        VFMM_CUDA(cudaMalloc(&T->nonleaf, std::max<size_t>(1, nl.size()) * sizeof(int32_t)));
+        if (!nl.empty())
+            VFMM_CUDA(cudaMemcpy(T->nonleaf, nl.data(), nl.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     VFMM_CHECK(build_mixed_plan(T));
     return VFMM_OK;
 }
@@ -712,7 +728,7 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
 void free_tree(DeviceTree* t) {
     void* ps[] = {t->key,         t->level,       t->ix,       t->iy,           t->parent,     t->child0,
                   t->leaf_of_box, t->box_of_leaf, t->level_start_dev, t->u_by_cfg, t->u_tgt, t->near_tiles,
-                  t->far_slot};
+                  t->far_slot,    t->nonleaf};
     free_split_plan(&t->plan_near);
     free_split_plan(&t->plan_s2m);
     free_split_plan(&t->plan_m2l);

@@ -197,6 +197,8 @@ struct DeviceTree {
     SplitPlan plan_m2l;   // V list: targets boxes, tables level * 40 + offset, A rows boxes
     SplitPlan plan_far;   // L2T + W list: targets leaves, tables 0 (L2T) and 1 + W configuration
     SplitPlan plan_s2l;   // X list: targets boxes, tables 20 configurations, A rows leaves
+    int32_t* nonleaf = nullptr;           // non-leaf boxes in canonical order (grouped by level)
+    std::vector<int32_t> nonleaf_start;   // host, depth + 2: first entry of each level
     int32_t* far_slot = nullptr;  // [n_leaves + 1] first A row of each leaf in the far operand
     int64_t n_far_slots = 0;
 };

@@ -1,0 +1,82 @@
+"""Full-size parity on the benchmark workloads, in the launch configuration the benchmark times
+(a CUDA-graph replay of the whole solve on a side stream).
+
+* FP64 and split-BF16 (mixed) results against the oracle on sampled leaves: the deepest and
+  the shallowest leaves, the leaf holding max |f|, and a seeded random set.
+* The mixed result against the FP64 result on every target.
+
+Bar: 1e-10 relative L-infinity (u, u_x, u_y), the method's accuracy target; FP64 is held to
+1e-12. Normalisation: the largest |value| of the oracle over the sampled leaves.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fmm
+from oracle import tree as T
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1610_00823_gb300 as v  # noqa: E402
+from paper_1610_00823_gb300.api import SolveGraph, workspace  # noqa: E402
+
+TOL = {"fp64": 1e-12, "mixed": 1e-10}
+WORKLOADS = {"adaptive_gauss20": W.adaptive_gauss20, "kinked": W.kinked}
+_cache = {}
+
+
+def _oracle(name):
+    if name not in _cache:
+        wl = WORKLOADS[name]()
+        src = wl.sources[0]
+        ot = T.build_adaptive(wl.cx, wl.cy, wl.width, wl.k, src, wl.tol, wl.max_depth, wl.min_depth)
+        _cache[name] = (wl, ot, T.build_lists(ot), ot.sample(src))
+    return _cache[name]
+
+
+def _graph_solve(gt, ops, f):
+    stream = torch.cuda.Stream()
+    out = tuple(torch.full_like(f, float("nan")) for _ in range(3))
+    ws = workspace(gt, ops, 1)
+    g = SolveGraph(gt, ops, f, out, ws, stream)
+    g.launch(stream)
+    stream.synchronize()
+    return [o.cpu().numpy() for o in out]
+
+
+def _sample_leaves(ot, F, n_random):
+    lev = ot.level[ot.leaves]
+    rng = np.random.default_rng(5)
+    pick = set(rng.choice(ot.n_leaves, size=min(n_random, ot.n_leaves), replace=False).tolist())
+    pick.add(int(np.argmax(np.max(np.abs(F), axis=1))))
+    pick.add(int(np.argmax(lev)))
+    pick.add(int(np.argmin(lev)))
+    return np.array(sorted(pick))
+
+
+@pytest.mark.parametrize("name,n_random", [("adaptive_gauss20", 40), ("kinked", 12)])
+def test_full_size_sampled_parity(name, n_random, oracle_ops):
+    wl, ot, L, F = _oracle(name)
+    src = wl.sources[0]
+    gt = v.tree_build(wl.cx, wl.cy, wl.width, wl.k, src, wl.tol, wl.max_depth, wl.min_depth)
+    assert gt.n_leaves == ot.n_leaves and gt.n_boxes == ot.level.shape[0]
+    f = v.source_sample(gt, src)
+    kk = wl.k * wl.k
+    leaves = _sample_leaves(ot, F, n_random)
+    ref = fmm.solve(ot, L, oracle_ops(wl.k, wl.p), F, leaves=leaves)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        ops = v.ops_create(wl.k, wl.p, v.MIXED if prec == "mixed" else v.FP64)
+        res[prec] = _graph_solve(gt, ops, f)
+        for q in range(3):
+            got = res[prec][q].reshape(ot.n_leaves, kk)[leaves]
+            err = float(np.max(np.abs(got - ref[q])) / np.max(np.abs(ref[q])))
+            assert err < TOL[prec], (name, prec, q, err)
+    for q in range(3):
+        a, b = res["mixed"][q], res["fp64"][q]
+        err = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        assert err < TOL["mixed"], (name, "mixed vs fp64", q, err)

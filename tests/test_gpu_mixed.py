@@ -56,3 +56,26 @@ def test_mixed_matches_fp64_and_oracle(name, mk, k, p, tol, depth, oracle_ops):
         got = out[q].cpu().numpy().reshape(ref[q].shape)
         assert rel(got, u64[q].cpu().numpy().reshape(ref[q].shape)) < TOL, (name, q)
         assert rel(got, ref[q]) < TOL, (name, q, rel(got, ref[q]))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_equals_direct_call(precision):
+    from paper_1610_00823_gb300.api import SolveGraph
+    src = W.narrow_gaussians(5, n=3, sigma=0.04)
+    gt = v.tree_build(0.0, 0.0, 1.0, 8, src, 1e-6, 7)
+    ops = v.ops_create(8, 20, v.MIXED if precision == "mixed" else v.FP64)
+    f = v.source_sample(gt, src)
+    ref = v.volume_potential(gt, ops, f)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    out = tuple(torch.full_like(f, float("nan")) for _ in range(3))
+    ws = workspace(gt, ops, 1)
+    g = SolveGraph(gt, ops, f, out, ws, stream)
+    for _ in range(2):
+        for q in range(3):
+            out[q].fill_(float("nan"))
+        torch.cuda.synchronize()
+        g.launch(stream)
+        stream.synchronize()
+        for q in range(3):
+            assert torch.equal(out[q], ref[q])
