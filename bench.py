@@ -92,6 +92,12 @@ class ClockSampler:
                 out, _ = self.proc.communicate()
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
 
+    def start(self):
+        return self.__enter__()
+
+    def stop(self):
+        self.__exit__(None, None, None)
+
     def summary(self):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -166,7 +172,8 @@ def run_reference(args, wl):
 
 
 def cpu_baseline(wl, gpu_u, budget_s=15.0):
-    """Oracle on a bounded sample of the same workload; also the sampled error of the GPU result."""
+    """Oracle on a bounded sample of the same workload; also the sampled error of each GPU result
+    (gpu_u: {form: (u, u_x, u_y)})."""
     t0 = time.perf_counter()
     ot, L, ops, F = oracle_setup(wl)
     setup_s = time.perf_counter() - t0
@@ -175,11 +182,15 @@ def cpu_baseline(wl, gpu_u, budget_s=15.0):
     dt, ref = oracle_sample_step(ot, L, ops, F, leaves)
     kk = wl.k * wl.k
     errs = None
-    if gpu_u is not None and gpu_u[0].shape[0] == ot.n_leaves * kk:
-        errs = []
-        for q in range(3):
-            got = gpu_u[q].reshape(ot.n_leaves, kk)[leaves]
-            errs.append(float(np.max(np.abs(got - ref[q])) / np.max(np.abs(ref[q]))))
+    if gpu_u:
+        errs = {}
+        for form, res in gpu_u.items():
+            if res[0].shape[0] != ot.n_leaves * kk:
+                continue
+            errs[form] = {}
+            for q, nm in enumerate(("u", "u_x", "u_y")):
+                got = res[q].reshape(ot.n_leaves, kk)[leaves]
+                errs[form][nm] = float(np.max(np.abs(got - ref[q])) / np.max(np.abs(ref[q])))
     return {"value": len(leaves) * kk / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d of %d leaves (%d targets), full upward pass included, %.1f s; oracle setup %.1f s untimed"
                       % (len(leaves), ot.n_leaves, len(leaves) * kk, dt, setup_s)}, errs
@@ -193,7 +204,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="adaptive_gauss20")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="with --precision mixed, skip timing the plain FP64 form on the same tree")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of CUDA-graph replays")
     args = ap.parse_args()
@@ -240,30 +253,33 @@ def main():
     f = v.source_sample(tree, src)
     kk = wl.k * wl.k
     n_targets = tree.n_leaves * kk
-    out = tuple(torch.empty_like(f) for _ in range(3))
-    ws = workspace(tree, ops, 1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    # the solve is captured once into a CUDA graph; every timed step replays it
-    graph = SolveGraph(tree, ops, f, out, ws, stream) if not args.no_graph else None
 
-    def step():
-        if graph is not None:
-            graph.launch(stream)
-        else:
-            v.volume_potential(tree, ops, f, out=out, ws=ws, stream=stream)
+    def time_form(ops_, steps, clk=None):
+        """Warm-up, then `steps` timed solves (CUDA-graph replays unless --no-graph), L2 flushed between."""
+        out_ = tuple(torch.empty_like(f) for _ in range(3))
+        ws_ = workspace(tree, ops_, 1)
+        # the solve is captured once into a CUDA graph; every timed step replays it
+        graph_ = SolveGraph(tree, ops_, f, out_, ws_, stream) if not args.no_graph else None
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+        def step():
+            if graph_ is not None:
+                graph_.launch(stream)
+            else:
+                v.volume_potential(tree, ops_, f, out=out_, ws=ws_, stream=stream)
 
-    step_ms = []
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        times = []
+        if clk is not None:
+            clk.start()
+        for _ in range(steps):
             flush.fill_(1.0)  # evict L2 between timed steps (outside the events)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -271,11 +287,17 @@ def main():
             step()
             e1.record(stream)
             e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
+            times.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
+        if clk is not None:
+            clk.stop()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        return times, out_, ws_, graph_
+
+    clk = ClockSampler(local)
+    step_ms, out, ws, graph = time_form(ops, args.steps, clk)
     # stage times (CUDA events between stages on the same stream) from separate profiled solves
     stage_acc, launches, n_prof = {}, 0, 3
     for _ in range(n_prof):
@@ -328,10 +350,32 @@ def main():
                 "fp64_equivalent_tflops": work["near_fp64eq_flops"] / (stage_ms["near"] / 1e3) / 1e12,
                 "note": "near stage time includes the f max and slicing kernels"}
 
+    # the plain FP64 form on the same tree and source, timed the same way (the metric's denominator)
+    fp64_form, out64 = None, None
+    if args.precision == "mixed" and not args.no_fp64_compare:
+        t0 = time.perf_counter()
+        ops64 = v.ops_create(wl.k, wl.p, v.FP64)
+        torch.cuda.synchronize()
+        t_ops64 = time.perf_counter() - t0
+        ms64_list, out64, ws64, _g64 = time_form(ops64, max(3, min(args.steps, 10)))
+        ms64 = statistics.mean(ms64_list)
+        if dist is not None:
+            tt = torch.tensor([ms64], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms64 = float(tt.item())
+        d = [torch.max(torch.abs(out[q] - out64[q])).item() / torch.max(torch.abs(out64[q])).item()
+             for q in range(3)]
+        fp64_form = {"value": world * n_targets / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                     "steps": len(ms64_list), "ops_create_s": t_ops64,
+                     "mixed_over_fp64_speedup": ms64 / ms, "rel_diff_mixed_vs_fp64_all_targets": d}
+        del ws64, _g64
+
     cpu = None
     errs = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        got = [o.cpu().numpy() for o in out]
+        got = {args.precision: [o.cpu().numpy() for o in out]}
+        if out64 is not None:
+            got["fp64"] = [o.cpu().numpy() for o in out64]
         cpu, errs = cpu_baseline(wl, got)
 
     if rank == 0:
@@ -351,6 +395,7 @@ def main():
                 "roofline": roof,
                 "cpu_baseline": cpu,
                 "sampled_rel_err_vs_oracle": errs,
+                "fp64_form": fp64_form,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_targets * 8,
                         "d2h_bytes_per_step": 3 * n_targets * 8, "ms_per_step": statistics.mean(e2e_ms)},
                 "gpu_launches": launches,
