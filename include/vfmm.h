@@ -150,14 +150,21 @@ int vfmm_ops_destroy(vfmm_ops* ops);
 
 /* Device workspace the solve needs for this tree, operator set and nrhs
  * (multipole and local expansions, near-field partial products). with_io != 0
- * adds room for the device copies vfmm_volume_potential_host stages through. */
+ * adds room for the device copies vfmm_volume_potential_host stages through.
+ * VFMM_MIXED with nrhs > 1 builds (once per tree and nrhs, host-side, cached in the
+ * tree under a lock) the contraction schedules with the right-hand sides folded in. */
 int vfmm_workspace_size(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs, int32_t with_io,
                         size_t* bytes);
 
 /* The box code (Section 3.1): u, u_x, u_y at every leaf node for nrhs right-hand
  * sides: upward pass (S2M, M2M), downward pass (M2L over V, S2L over X, L2L),
  * leaf pass (near-field tables over U with the log(h) scale term, L2T, M2T over W).
- * Everything runs on `stream`, with no host synchronisation and no allocation.
+ * Layout: f, u, u_x, u_y are [nrhs][n_leaves][k*k] doubles (canonical leaf order, x-fastest
+ * nodes). VFMM_FP64 solves the right-hand sides one after another; VFMM_MIXED folds them
+ * into one solve whose tensor-core contractions carry nrhs rows per leaf or box (no
+ * counterpart in the paper, which solves one right-hand side at a time).
+ * Everything runs on `stream`, with no host synchronisation and no allocation (the first
+ * VFMM_MIXED call for a new nrhs builds its schedules on the host, see vfmm_workspace_size).
  * Errors: INVALID_ARG (k or p of ops differ from the tree's k, nrhs < 1), WORKSPACE
  * (workspace_bytes below vfmm_workspace_size), CUDA. */
 int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
@@ -202,14 +209,14 @@ int vfmm_graph_create(const vfmm_tree* tree, const vfmm_ops* ops, const double* 
 int vfmm_graph_launch(const vfmm_graph* graph, void* stream);
 int vfmm_graph_destroy(vfmm_graph* graph);
 
-/* Work accounting for roofline reports: out[VFMM_N_WORK] =
- * [0] BF16 tensor-core FLOPs the near-field contraction issues per solve (VFMM_MIXED: every
+/* Work accounting for roofline reports, for a call with nrhs right-hand sides: out[VFMM_N_WORK] =
+ * [0] BF16 tensor-core FLOPs the near-field contraction issues per call (VFMM_MIXED: every
  *     slice product of every tile, zero-padded rows included; 0 for VFMM_FP64),
  * [1] the same for M2L, [2] for the leaf far field (L2T + M2T), [3] for S2L, [4] for S2M,
- * [5] FP64-equivalent FLOPs of the near field, 2 * 3k^2 * k^2 per U-list entry,
+ * [5] FP64-equivalent FLOPs of the near field, 2 * 3k^2 * k^2 per U-list entry and right-hand side,
  * [6] number of U-list entries, [7] reserved (0). Host-only; no device work. */
 #define VFMM_N_WORK 8
-int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, double* out);
+int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs, double* out);
 
 /* Stage timers (tracing): the same solve as vfmm_volume_potential with CUDA events
  * recorded on `stream` between its stages; synchronises `stream` and returns the

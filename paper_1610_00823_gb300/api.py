@@ -230,10 +230,10 @@ WORK = ("near_tc_flops", "m2l_tc_flops", "far_tc_flops", "s2l_tc_flops", "s2m_tc
         "u_entries", "reserved")
 
 
-def solve_work(tree: Tree, ops: Ops):
-    """Work counts of one solve (host-side accounting for roofline reports)."""
+def solve_work(tree: Tree, ops: Ops, nrhs: int = 1):
+    """Work counts of one call with nrhs right-hand sides (host-side accounting for roofline reports)."""
     out = np.zeros(len(WORK), dtype=np.float64)
-    call("vfmm_solve_work", tree.handle, ops.handle, out.ctypes.data_as(c_double_p))
+    call("vfmm_solve_work", tree.handle, ops.handle, int(nrhs), out.ctypes.data_as(c_double_p))
     return dict(zip(WORK, out.tolist()))
 
 

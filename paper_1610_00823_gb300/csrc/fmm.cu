@@ -31,23 +31,25 @@ __device__ __forceinline__ double pow2(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// Re of local coefficient 0 contributed by the V list of each box (one warp per box, one lane per
-// V entry): sum_c Re(row 0 of M2L_c . a_c) + a_0(c) log h. FP64; the other coefficients come
-// from the split-precision M2L.
-__global__ void m2l_c0_kernel(int begin, int end, int P, double width, const int32_t* __restrict__ level,
+// Re of local coefficient 0 from the V and X lists of each virtual box (box, r), one warp per
+// virtual box: sum over V of Re(row 0 of M2L_c . a_c) + a_0(c) log h, and over X of
+// (2h)^2 Re(S2L row 0) . f_c + a_0(c) log h. FP64; the other coefficients come from the
+// split-precision M2L and S2L.
+__global__ void m2l_c0_kernel(int begin, int end, int R, int P, double width, const int32_t* __restrict__ level,
                               const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
                               const int32_t* __restrict__ vcfg, const double* __restrict__ m2l_t,
                               const double* __restrict__ Mexp, double* __restrict__ c0,
                               const int32_t* __restrict__ xptr, const int32_t* __restrict__ xidx,
                               const int32_t* __restrict__ xcfg, const int32_t* __restrict__ leaf_of_box,
-                              const double* __restrict__ s2l_r0, const double* __restrict__ f, int kk) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int b = begin + warp;
-    if (b >= end) return;
+                              const double* __restrict__ s2l_r0, const double* __restrict__ f, int nleaf, int kk) {
+    const int64_t vw = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (vw >= (int64_t)(end - begin) * R) return;
+    const int b = begin + (int)(vw / R), r = (int)(vw % R);
     const double logh = log(ldexp(width, -level[b]));
     double acc = 0.0;
     for (int e = vptr[b] + lane; e < vptr[b + 1]; e += 32) {
-        const double* a = Mexp + (size_t)vidx[e] * 2 * P;
+        const double* a = Mexp + ((size_t)vidx[e] * R + r) * 2 * P;
         const double* M = m2l_t + (size_t)vcfg[e] * P * P * 2;
         double re = a[0] * logh;
         for (int n = 0; n < P; ++n) re += M[(size_t)n * P * 2] * a[2 * n] - M[(size_t)n * P * 2 + 1] * a[2 * n + 1];
@@ -56,15 +58,15 @@ __global__ void m2l_c0_kernel(int begin, int end, int P, double width, const int
     // X list: (2h)^2 [Re(S2L row 0) . f_c + log(h) W . f_c], with W . f_c = a_0(c) / (2h)^2
     const double h = ldexp(width, -level[b]);
     for (int e = xptr[b]; e < xptr[b + 1]; ++e) {
-        const double* fc = f + (size_t)leaf_of_box[xidx[e]] * kk;
+        const double* fc = f + ((size_t)r * nleaf + leaf_of_box[xidx[e]]) * kk;
         const double* r0 = s2l_r0 + (size_t)xcfg[e] * kk;
         double part = 0.0;
         for (int s = lane; s < kk; s += 32) part += r0[s] * fc[s];
         acc += 4.0 * h * h * part;
-        if (lane == 0) acc += logh * Mexp[(size_t)xidx[e] * 2 * P];
+        if (lane == 0) acc += logh * Mexp[((size_t)xidx[e] * R + r) * 2 * P];
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) c0[b] = acc;
+    if (lane == 0) c0[(size_t)b * R + r] = acc;
 }
 
 // ---------------------------------------------------------------- FP64 gather GEMM tile
@@ -215,18 +217,21 @@ __global__ void __launch_bounds__(256) l2t_gemm_kernel(const double* __restrict_
 // entry is read. mode 0 (M2M): in = the 4 consecutive child multipoles, out = parent multipole.
 // mode 1 (L2L): in = parent local, out = the 4 child locals (written, later added to by the
 // downward pass). Tables [pos][in][out] complex.
-__global__ void __launch_bounds__(128) translate_kernel(int mode, const int32_t* __restrict__ boxes, int nbox,
+__global__ void __launch_bounds__(128) translate_kernel(int mode, const int32_t* __restrict__ boxes, int nbox, int R,
                                                         const int32_t* __restrict__ child0, int P,
                                                         const double2* __restrict__ tab, double2* __restrict__ ex) {
     extern __shared__ double2 sx[];  // [4P] in, [4P] per-position results
-    const int bi = blockIdx.x;
+    const int bi = blockIdx.x / R, r = blockIdx.x - bi * R;  // virtual box (box, right-hand side)
     if (bi >= nbox) return;
     const int b = boxes[bi], c0 = child0[b];
     double2* s_in = sx;
     double2* s_out = sx + 4 * P;
-    const int nin = mode == 0 ? 4 * P : P;
-    const double2* src = ex + (size_t)(mode == 0 ? c0 : b) * P;
-    for (int q = threadIdx.x; q < nin; q += blockDim.x) s_in[q] = src[q];
+    if (mode == 0) {
+        for (int q = threadIdx.x; q < 4 * P; q += blockDim.x)
+            s_in[q] = ex[((size_t)(c0 + q / P) * R + r) * P + q % P];
+    } else {
+        for (int q = threadIdx.x; q < P; q += blockDim.x) s_in[q] = ex[((size_t)b * R + r) * P + q];
+    }
     __syncthreads();
     const int npair = (P + 1) / 2;
     for (int task = threadIdx.x; task < 4 * npair; task += blockDim.x) {
@@ -250,26 +255,28 @@ __global__ void __launch_bounds__(128) translate_kernel(int mode, const int32_t*
     if (mode == 0) {
         for (int o = threadIdx.x; o < P; o += blockDim.x) {
             const double2 a0 = s_out[o], a1 = s_out[P + o], a2 = s_out[2 * P + o], a3 = s_out[3 * P + o];
-            ex[(size_t)b * P + o] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+            ex[((size_t)b * R + r) * P + o] =
+                make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
         }
     } else {
-        for (int q = threadIdx.x; q < 4 * P; q += blockDim.x) ex[(size_t)c0 * P + q] = s_out[q];
+        for (int q = threadIdx.x; q < 4 * P; q += blockDim.x) ex[((size_t)(c0 + q / P) * R + r) * P + q % P] = s_out[q];
     }
 }
 
-static void launch_translate(int mode, const DeviceTree& T, int level, int P, const double* tab, double* ex,
+static void launch_translate(int mode, const DeviceTree& T, int level, int R, int P, const double* tab, double* ex,
                              cudaStream_t st) {
     const int nbox = T.nonleaf_start[level + 1] - T.nonleaf_start[level];
     if (nbox <= 0) return;
     const int threads = std::min(128, ((4 * ((P + 1) / 2) + 31) / 32) * 32);
-    translate_kernel<<<nbox, threads, (size_t)8 * P * sizeof(double2), st>>>(
-        mode, T.nonleaf + T.nonleaf_start[level], nbox, T.child0, P, reinterpret_cast<const double2*>(tab),
+    translate_kernel<<<(unsigned)nbox * R, threads, (size_t)8 * P * sizeof(double2), st>>>(
+        mode, T.nonleaf + T.nonleaf_start[level], nbox, R, T.child0, P, reinterpret_cast<const double2*>(tab),
         reinterpret_cast<double2*>(ex));
 }
 
 // ---------------------------------------------------------------- downward pass (one CTA per box)
 struct DownArgs {
     int begin, end, P, kk, level;
+    int R, nleaf;  // right-hand sides folded into the box rows (virtual box = box * R + r); leaves
     double width;
     const int32_t* parent;
     const int32_t* ix;
@@ -296,20 +303,22 @@ struct DownArgs {
 
 __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
     __shared__ double src[2 * 256];
-    const int b = d.begin + blockIdx.x;
+    const int R = d.R;
+    const int b = d.begin + blockIdx.x / R, r = blockIdx.x % R;
     if (b >= d.end) return;
+    const size_t vb = (size_t)b * R + r;
     const int P = d.P, t = threadIdx.x;
     const double h = ldexp(d.width, -d.level);
     const double logh = log(h);
     double re = 0.0, im = 0.0;
     if (d.level >= 3 && t < P) {
         // L2L from the parent, written by translate_kernel just before this launch
-        re = d.Lexp[(size_t)b * 2 * P + 2 * t];
-        im = d.Lexp[(size_t)b * 2 * P + 2 * t + 1];
+        re = d.Lexp[vb * 2 * P + 2 * t];
+        im = d.Lexp[vb * 2 * P + 2 * t + 1];
     }
     for (int e = d.m2l_out ? d.vptr[b + 1] : d.vptr[b]; e < d.vptr[b + 1]; ++e) {
         const int c = d.vidx[e];
-        for (int q = t; q < 2 * P; q += blockDim.x) src[q] = d.Mexp[(size_t)c * 2 * P + q];
+        for (int q = t; q < 2 * P; q += blockDim.x) src[q] = d.Mexp[((size_t)c * R + r) * 2 * P + q];
         __syncthreads();
         const double* M = d.m2l_t + (size_t)d.vcfg[e] * P * P * 2;
         if (t < P) {
@@ -325,50 +334,51 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
     }
     for (int e = d.m2l_out ? d.xptr[b + 1] : d.xptr[b]; e < d.xptr[b + 1]; ++e) {
         const int c = d.xidx[e];
-        const double* fc = d.f + (size_t)d.leaf_of_box[c] * d.kk;
+        const double* fc = d.f + ((size_t)r * d.nleaf + d.leaf_of_box[c]) * d.kk;
         for (int q = t; q < d.kk; q += blockDim.x) src[q] = fc[q];
         __syncthreads();
-        const double* R = d.s2l_t + (size_t)d.xcfg[e] * d.kk * P * 2;
+        const double* X = d.s2l_t + (size_t)d.xcfg[e] * d.kk * P * 2;
         if (t < P) {
             double sr = 0.0, si = 0.0;
             for (int s = 0; s < d.kk; ++s) {
-                sr = fma(R[((size_t)s * P + t) * 2], src[s], sr);
-                si = fma(R[((size_t)s * P + t) * 2 + 1], src[s], si);
+                sr = fma(X[((size_t)s * P + t) * 2], src[s], sr);
+                si = fma(X[((size_t)s * P + t) * 2 + 1], src[s], si);
             }
             const double hc2 = 4.0 * h * h;
             re += hc2 * sr;
             im += hc2 * si;
-            if (t == 0) re += logh * d.Mexp[(size_t)c * 2 * P];
+            if (t == 0) re += logh * d.Mexp[((size_t)c * R + r) * 2 * P];
         }
         __syncthreads();
     }
     if (d.m2l_out && t >= 1 && t < P && d.xptr[b + 1] > d.xptr[b]) {
-        const float2 vr = d.s2l_out[(size_t)b * d.Rx + 2 * (t - 1)];
-        const float2 vi = d.s2l_out[(size_t)b * d.Rx + 2 * (t - 1) + 1];
-        const double sc = 4.0 * h * h * pow2(*d.Ef);
+        const float2 vr = d.s2l_out[vb * d.Rx + 2 * (t - 1)];
+        const float2 vi = d.s2l_out[vb * d.Rx + 2 * (t - 1) + 1];
+        const double sc = 4.0 * h * h * pow2(d.Ef[r]);
         re += sc * ((double)vr.x + (double)vr.y) * pow2(d.s2l_E[2 * (t - 1)]);
         im += sc * ((double)vi.x + (double)vi.y) * pow2(d.s2l_E[2 * (t - 1) + 1]);
     }
     if (d.m2l_out && t < P && (d.vptr[b + 1] > d.vptr[b] || d.xptr[b + 1] > d.xptr[b])) {
         if (t == 0) {
-            re += d.m2l_c0[b];
+            re += d.m2l_c0[vb];
         } else if (d.vptr[b + 1] > d.vptr[b]) {
-            const float2 vr = d.m2l_out[(size_t)b * d.Rx + 2 * (t - 1)];
-            const float2 vi = d.m2l_out[(size_t)b * d.Rx + 2 * (t - 1) + 1];
-            const int g = d.m2l_G[d.level];
+            const float2 vr = d.m2l_out[vb * d.Rx + 2 * (t - 1)];
+            const float2 vi = d.m2l_out[vb * d.Rx + 2 * (t - 1) + 1];
+            const int g = d.m2l_G[(size_t)d.level * R + r];
             re += ((double)vr.x + (double)vr.y) * pow2(g + d.m2l_E[2 * (t - 1)]);
             im += ((double)vi.x + (double)vi.y) * pow2(g + d.m2l_E[2 * (t - 1) + 1]);
         }
     }
     if (t < P) {
-        d.Lexp[(size_t)b * 2 * P + 2 * t] = re;
-        d.Lexp[(size_t)b * 2 * P + 2 * t + 1] = im;
+        d.Lexp[vb * 2 * P + 2 * t] = re;
+        d.Lexp[vb * 2 * P + 2 * t + 1] = im;
     }
 }
 
 // ---------------------------------------------------------------- leaf pass (one CTA per leaf)
 struct LeafArgs {
     int nleaf, kk, k, P;
+    int R;  // right-hand sides folded into the leaf rows (mixed form; 1 in the FP64 form)
     double width;
     const int32_t* box_of_leaf;
     const int32_t* level;
@@ -395,7 +405,8 @@ struct LeafArgs {
 
 __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
     __shared__ double sa[2 * 64];
-    const int leaf = blockIdx.x;
+    const int vl = blockIdx.x, R = a.R;
+    const int leaf = vl / R, r = vl - leaf * R;
     const int t = threadIdx.x;
     const int kk = a.kk, P = a.P;
     const bool act = t < kk;
@@ -407,8 +418,8 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
         if (t < 32) {
             // per-leaf scalars: U-list mass (log(h) term), local coefficient 0, W-list a_0 log(h_w)
             double m = 0.0, w0 = 0.0;
-            for (int e = a.uptr[b] + t; e < a.uptr[b + 1]; e += 32) m += a.Mexp[(size_t)a.uidx[e] * 2 * P];
-            for (int e = a.wptr[b] + t; e < a.wptr[b + 1]; e += 32) w0 += a.Mexp[(size_t)a.widx[e] * 2 * P];
+            for (int e = a.uptr[b] + t; e < a.uptr[b + 1]; e += 32) m += a.Mexp[((size_t)a.uidx[e] * R + r) * 2 * P];
+            for (int e = a.wptr[b] + t; e < a.wptr[b + 1]; e += 32) w0 += a.Mexp[((size_t)a.widx[e] * R + r) * 2 * P];
             for (int o = 16; o > 0; o >>= 1) {
                 m += __shfl_xor_sync(0xffffffffu, m, o);
                 w0 += __shfl_xor_sync(0xffffffffu, w0, o);
@@ -416,18 +427,18 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
             if (t == 0) {
                 const double logh = log(h);
                 sc[0] = -kInv2Pi * logh * m;
-                sc[1] = -kInv2Pi * (a.Lexp[(size_t)b * 2 * P] + w0 * (logh - 0.6931471805599453));
+                sc[1] = -kInv2Pi * (a.Lexp[((size_t)b * R + r) * 2 * P] + w0 * (logh - 0.6931471805599453));
             }
         }
         __syncthreads();
         if (act) {
-            const float2* nm = a.nearmix + (size_t)leaf * a.Rp;
-            const float2* fm = a.farmix + (size_t)leaf * a.Rp;
-            const int ef = *a.Ef, et = a.Et[leaf];
+            const float2* nm = a.nearmix + (size_t)vl * a.Rp;
+            const float2* fm = a.farmix + (size_t)vl * a.Rp;
+            const int ef = a.Ef[r], et = a.Et[vl];
             const double hh = h * h, ih = 1.0 / h;
             float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
             float2 w0 = fm[t], w1 = fm[kk + t], w2 = fm[2 * kk + t];
-            const size_t o = (size_t)leaf * kk + t;
+            const size_t o = ((size_t)r * a.nleaf + leaf) * kk + t;
             a.u[o] = hh * ((double)v0.x + (double)v0.y) * pow2(ef + a.Er[t]) + sc[0] + sc[1] +
                      ((double)w0.x + (double)w0.y) * pow2(et + a.farE[t]);
             a.ux[o] = h * ((double)v1.x + (double)v1.y) * pow2(ef + a.Er[kk + t]) +
@@ -503,6 +514,7 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
 
 // ---------------------------------------------------------------- host side
 struct Workspace {
+    const PlanSet* ps;  // split-contraction plans for the folded right-hand sides (mixed form)
     double* Mexp;
     double* Lexp;
     double* slab;
@@ -514,7 +526,10 @@ struct Workspace {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-static size_t layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Workspace* w, char* base) {
+// Workspace carving. The mixed form folds all nrhs right-hand sides into one solve (every
+// per-box and per-leaf buffer has nrhs rows per box); the FP64 form solves them one at a time.
+static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Workspace* w, char* base,
+                  size_t* bytes) {
     const size_t P2 = 2 * (size_t)(o.p + 1), kk = (size_t)o.k * o.k;
     size_t off = 0;
     auto take = [&](double** p, size_t n) {
@@ -523,53 +538,61 @@ static size_t layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, 
     };
     double* dummy;
     const bool mixed = o.precision == VFMM_MIXED;
-    take(w ? &w->Mexp : &dummy, (size_t)T.n_boxes * P2);
-    take(w ? &w->Lexp : &dummy, (size_t)T.n_boxes * P2);
+    const size_t R = mixed ? (size_t)nrhs : 1;
+    take(w ? &w->Mexp : &dummy, (size_t)T.n_boxes * R * P2);
+    take(w ? &w->Lexp : &dummy, (size_t)T.n_boxes * R * P2);
     take(w ? &w->slab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
     take(w ? &w->far : &dummy, mixed ? 1 : (size_t)T.n_leaves * 3 * kk);
     if (mixed) {
         const MixedOps* mo = (const MixedOps*)o.mixed;
+        const PlanSet* PS = nullptr;
+        VFMM_CHECK(plans_for(T, (int)R, &PS));
+        if (w) w->ps = PS;
+        const size_t nl = (size_t)T.n_leaves * R, nb = (size_t)T.n_boxes * R;
         double* p = nullptr;
-        // bf16 slices, (hi, lo) near values, then three scalars
-        take(&p, ((size_t)T.n_leaves * kSlices * mo->Kp * 2 + 7) / 8);
+        take(&p, (nl * kSlices * mo->Kp * 2 + 7) / 8);
         if (w) w->mix.fsl = (void*)p;
-        take(&p, (size_t)T.n_leaves * mo->Rp);
+        take(&p, nl * mo->Rp);
         if (w) w->mix.out = (float2*)p;
-        take(&p, 4);
-        if (w) {
-            w->mix.fmax = (unsigned long long*)p;
-            w->mix.Ef = (int*)(p + 1);
-            w->mix.err = (int*)(p + 2);
-        }
+        take(&p, R);
+        if (w) w->mix.fmax = (unsigned long long*)p;
+        take(&p, (R + 1) / 2);
+        if (w) w->mix.Ef = (int*)p;
+        take(&p, 1);
+        if (w) w->mix.err = (int*)p;
         const size_t nlev = (size_t)T.depth + 1;
-        take(&p, (size_t)T.n_leaves * mo->Rx);
+        take(&p, nl * mo->Rx);
         if (w) w->mix.s2m_out = (float2*)p;
-        take(&p, (nlev + 1) / 2);
+        take(&p, (nb + 1) / 2);
+        if (w) w->mix.bexp = (int*)p;
+        take(&p, (nlev * R + 1) / 2);
         if (w) w->mix.glev = (int*)p;
-        take(&p, ((size_t)T.n_boxes * kSlices * mo->Kx * 2 + 7) / 8);
+        take(&p, (nb * kSlices * mo->Kx * 2 + 7) / 8);
         if (w) w->mix.msl = (void*)p;
-        take(&p, (size_t)T.n_boxes * mo->Rx);
+        take(&p, nb * mo->Rx);
         if (w) w->mix.m2l_out = (float2*)p;
-        take(&p, (size_t)T.n_boxes);
+        take(&p, nb);
         if (w) w->mix.m2l_c0 = p;
-        take(&p, (size_t)T.n_boxes * mo->Rx);
+        take(&p, nb * mo->Rx);
         if (w) w->mix.s2l_out = (float2*)p;
-        take(&p, ((size_t)T.n_far_slots * kSlices * mo->Kx * 2 + 7) / 8);
+        take(&p, ((size_t)T.n_far_slots * R * kSlices * mo->Kx * 2 + 7) / 8);
         if (w) w->mix.aprep = (void*)p;
-        take(&p, ((size_t)T.n_leaves + 1) / 2);
+        take(&p, (nl + 1) / 2);
         if (w) w->mix.Et = (int*)p;
-        take(&p, (size_t)T.n_leaves * mo->Rp);
+        take(&p, nl * mo->Rp);
         if (w) w->mix.far_out = (float2*)p;
-        const size_t np = split_part_elems(T, o);
+        const size_t np = split_part_elems(T, *PS, o);
         take(&p, std::max<size_t>(np, 1));
         if (w) w->mix.part = np ? (float2*)p : nullptr;
     } else if (w) {
         w->mix = MixedWork();
+        w->ps = &T.plans;
     }
     if (io) take(w ? &w->io : &dummy, (size_t)4 * nrhs * T.n_leaves * kk);
     else if (w) w->io = nullptr;
     if (w) w->bytes = off;
-    return off;
+    *bytes = off;
+    return VFMM_OK;
 }
 
 int build_near_tiles(DeviceTree* T) {
@@ -598,8 +621,10 @@ static inline void mark(StageEvents* se, int stage, bool stop, cudaStream_t st) 
 }
 
 static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, const double* f, const Workspace& w,
-                           int l) {
+                           int l, int R) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
+    d.R = R;
+    d.nleaf = T.n_leaves;
     d.begin = T.level_start[l];
     d.end = T.level_start[l + 1];
     d.P = o.p + 1;
@@ -632,25 +657,29 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     d.Rx = mo ? mo->Rx : 0;
 }
 
-static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, double* u, double* ux, double* uy,
-                     const Workspace& w, cudaStream_t st, StageEvents* se = nullptr) {
+// One solve of R right-hand sides (f: [R][n_leaves][k^2]). The mixed form folds them into the
+// rows of every contraction (PS holds plans for R); the FP64 form takes R = 1.
+static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* u,
+                     double* ux, double* uy, const Workspace& w, cudaStream_t st, StageEvents* se = nullptr) {
     const int P = o.p + 1, P2 = 2 * P, kk = o.k * o.k;
     const int nleaf = T.n_leaves;
     const bool mixed = o.precision == VFMM_MIXED;
+    const int R = PS.R;
+    if (!mixed && R != 1) return fail(VFMM_ERR_INTERNAL, "the FP64 form solves one right-hand side at a time");
     const MixedOps* mo = (const MixedOps*)o.mixed;
     int launches = 0;
     if (mixed) {
         // near field first: its f slices also feed S2M
         mark(se, ST_NEAR, false, st);
-        VFMM_CHECK(near_mixed(T, o, f, w.mix, st));
-        launches += 3;
+        VFMM_CHECK(near_mixed(T, PS, o, f, w.mix, st));
+        launches += 3 + (PS.near.split > 1 && PS.near.n_groups > 0);
         mark(se, ST_NEAR, true, st);
     }
     // S2M
     mark(se, ST_S2M, false, st);
     if (mixed) {
-        VFMM_CHECK(s2m_mixed(T, o, f, w.Mexp, w.mix, st));
-        launches += 2;
+        VFMM_CHECK(s2m_mixed(T, PS, o, f, w.Mexp, w.mix, st));
+        launches += 1 + (PS.s2m.n_groups > 0);
     } else {
         ++launches;
         dim3 g((P2 + GBM - 1) / GBM, (nleaf + GBN - 1) / GBN);
@@ -661,38 +690,38 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
     mark(se, ST_M2M, false, st);
     for (int l = T.depth - 1; l >= 2; --l) {
         if (T.nonleaf_start[l + 1] > T.nonleaf_start[l]) ++launches;
-        launch_translate(0, T, l, P, o.m2m_t, w.Mexp, st);
+        launch_translate(0, T, l, R, P, o.m2m_t, w.Mexp, st);
     }
     mark(se, ST_M2M, true, st);
     // downward pass
     mark(se, ST_DOWN, false, st);
     if (mixed && T.depth >= 2) {
-        VFMM_CHECK(m2l_mixed(T, o, w.Mexp, w.mix, st));
-        launches += T.depth + 4;
+        VFMM_CHECK(m2l_mixed(T, PS, o, w.Mexp, w.mix, st));
+        if (PS.m2l.n_groups > 0) launches += 4 + (PS.m2l.split > 1);
         const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
-        const int warps = end - begin;
-        m2l_c0_kernel<<<(warps + 7) / 8, 256, 0, st>>>(
-            begin, end, P, T.width, T.level, T.lptr[VFMM_LIST_V], T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V], o.m2l_t,
-            w.Mexp, w.mix.m2l_c0, T.lptr[VFMM_LIST_X], T.lidx[VFMM_LIST_X], T.lcfg[VFMM_LIST_X], T.leaf_of_box,
-            mo->s2l_r0, f, kk);
-        VFMM_CHECK(s2l_mixed(T, o, w.mix, st));
-        launches += 2;
+        const int64_t warps = (int64_t)(end - begin) * R;
+        m2l_c0_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(
+            begin, end, R, P, T.width, T.level, T.lptr[VFMM_LIST_V], T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V],
+            o.m2l_t, w.Mexp, w.mix.m2l_c0, T.lptr[VFMM_LIST_X], T.lidx[VFMM_LIST_X], T.lcfg[VFMM_LIST_X],
+            T.leaf_of_box, mo->s2l_r0, f, nleaf, kk);
+        VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, st));
+        launches += 1 + (PS.s2l.n_groups > 0) + (PS.s2l.n_groups > 0 && PS.s2l.split > 1);
     }
     for (int l = 2; l <= T.depth; ++l) {
         DownArgs d;
-        fill_down_args(d, T, o, f, w, l);
+        fill_down_args(d, T, o, f, w, l, R);
         int n = d.end - d.begin;
         if (n <= 0) continue;
         if (l >= 3) {
             // L2L for every box of level l (children of the non-leaf boxes of level l - 1)
-            launch_translate(1, T, l - 1, P, o.l2l_t, w.Lexp, st);
+            launch_translate(1, T, l - 1, R, P, o.l2l_t, w.Lexp, st);
             ++launches;
         }
         ++launches;
-        down_kernel<<<n, 64, 0, st>>>(d);
+        down_kernel<<<(unsigned)n * R, 64, 0, st>>>(d);
     }
-    if (T.depth < 2) VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.n_boxes * P2 * sizeof(double), st));
-    else VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.level_start[2] * P2 * sizeof(double), st));
+    if (T.depth < 2) VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.n_boxes * R * P2 * sizeof(double), st));
+    else VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.level_start[2] * R * P2 * sizeof(double), st));
     mark(se, ST_DOWN, true, st);
     if (!mixed) {
         mark(se, ST_NEAR, false, st);
@@ -707,8 +736,8 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
     // far field at the leaves
     mark(se, ST_L2T, false, st);
     if (mixed) {
-        VFMM_CHECK(far_leaf_mixed(T, o, w.Mexp, w.Lexp, w.mix, st));
-        launches += 2;
+        VFMM_CHECK(far_leaf_mixed(T, PS, o, w.Mexp, w.Lexp, w.mix, st));
+        launches += 1 + (PS.far.n_groups > 0) + (PS.far.n_groups > 0 && PS.far.split > 1);
     } else {
         ++launches;
         dim3 g((3 * kk + GBM - 1) / GBM, (nleaf + GBN - 1) / GBN);
@@ -718,6 +747,7 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
     mark(se, ST_LEAF, false, st);
     LeafArgs a;
     a.nleaf = nleaf;
+    a.R = R;
     a.kk = kk;
     a.k = o.k;
     a.P = P;
@@ -753,7 +783,7 @@ static int solve_one(const DeviceTree& T, const vfmm_ops& o, const double* f, do
     a.u = u;
     a.ux = ux;
     a.uy = uy;
-    leaf_kernel<<<nleaf, ((kk + 31) / 32) * 32, 0, st>>>(a);
+    leaf_kernel<<<(unsigned)nleaf * R, ((kk + 31) / 32) * 32, 0, st>>>(a);
     ++launches;
     mark(se, ST_LEAF, true, st);
     VFMM_CUDA(cudaGetLastError());
@@ -777,7 +807,15 @@ extern "C" int vfmm_workspace_size(const vfmm_tree* tree, const vfmm_ops* ops, i
                                    size_t* bytes) {
     VFMM_CHECK(check_solve_args(tree, ops, nrhs));
     if (!bytes) return fail(VFMM_ERR_INVALID_ARG, "null bytes");
-    *bytes = layout(tree->t, *ops, nrhs, with_io != 0, nullptr, nullptr);
+    return layout(tree->t, *ops, nrhs, with_io != 0, nullptr, nullptr, bytes);
+}
+
+// All right-hand sides: one folded solve in the mixed form, one solve per right-hand side in FP64.
+static int solve_all(const DeviceTree& T, const vfmm_ops& o, const double* f, int nrhs, double* u, double* ux,
+                     double* uy, const Workspace& w, cudaStream_t st, StageEvents* se = nullptr) {
+    if (o.precision == VFMM_MIXED) return solve_one(T, *w.ps, o, f, u, ux, uy, w, st, se);
+    const size_t n = (size_t)T.n_leaves * o.k * o.k;
+    for (int r = 0; r < nrhs; ++r) VFMM_CHECK(solve_one(T, T.plans, o, f + r * n, u + r * n, ux + r * n, uy + r * n, w, st, se));
     return VFMM_OK;
 }
 
@@ -802,14 +840,11 @@ extern "C" int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops,
     VFMM_CHECK(check_solve_args(tree, ops, nrhs));
     if (!f_dev || !u_dev || !ux_dev || !uy_dev || !workspace_dev) return fail(VFMM_ERR_INVALID_ARG, "null buffer");
     Workspace w;
-    size_t need = layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev);
+    size_t need = 0;
+    VFMM_CHECK(layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev, &need));
     if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small");
     VFMM_CHECK(reset_status(w, (cudaStream_t)stream));
-    const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
-    for (int r = 0; r < nrhs; ++r)
-        VFMM_CHECK(solve_one(tree->t, *ops, f_dev + r * n, u_dev + r * n, ux_dev + r * n, uy_dev + r * n, w,
-                             (cudaStream_t)stream));
-    return VFMM_OK;
+    return solve_all(tree->t, *ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, w, (cudaStream_t)stream);
 }
 
 extern "C" int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_host,
@@ -818,7 +853,8 @@ extern "C" int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops*
     VFMM_CHECK(check_solve_args(tree, ops, nrhs));
     if (!f_host || !u_host || !ux_host || !uy_host || !workspace_dev) return fail(VFMM_ERR_INVALID_ARG, "null buffer");
     Workspace w;
-    size_t need = layout(tree->t, *ops, nrhs, true, &w, (char*)workspace_dev);
+    size_t need = 0;
+    VFMM_CHECK(layout(tree->t, *ops, nrhs, true, &w, (char*)workspace_dev, &need));
     if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small (with_io = 1 required)");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k * nrhs;
@@ -828,9 +864,7 @@ extern "C" int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops*
     double* uy = w.io + 3 * n;
     VFMM_CHECK(reset_status(w, st));
     VFMM_CUDA(cudaMemcpyAsync(f, f_host, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    const size_t m = (size_t)tree->t.n_leaves * ops->k * ops->k;
-    for (int r = 0; r < nrhs; ++r)
-        VFMM_CHECK(solve_one(tree->t, *ops, f + r * m, u + r * m, ux + r * m, uy + r * m, w, st));
+    VFMM_CHECK(solve_all(tree->t, *ops, f, nrhs, u, ux, uy, w, st));
     VFMM_CUDA(cudaMemcpyAsync(u_host, u, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     VFMM_CUDA(cudaMemcpyAsync(ux_host, ux, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     VFMM_CUDA(cudaMemcpyAsync(uy_host, uy, n * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -846,7 +880,8 @@ extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_
     if (!f_dev || !u_dev || !ux_dev || !uy_dev || !workspace_dev || !stage_ms || !launches)
         return fail(VFMM_ERR_INVALID_ARG, "null buffer");
     Workspace w;
-    size_t need = layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev);
+    size_t need = 0;
+    VFMM_CHECK(layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev, &need));
     if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small");
     cudaStream_t st = (cudaStream_t)stream;
     VFMM_CHECK(reset_status(w, st));
@@ -854,9 +889,12 @@ extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_
     for (int i = 0; i < 2 * VFMM_N_STAGES; ++i) VFMM_CUDA(cudaEventCreate(&se.ev[i]));
     for (int i = 0; i < VFMM_N_STAGES; ++i) stage_ms[i] = 0.0f;
     const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
+    const bool folded = ops->precision == VFMM_MIXED;
     int rc = VFMM_OK;
-    for (int r = 0; r < nrhs && rc == VFMM_OK; ++r) {
-        rc = solve_one(tree->t, *ops, f_dev + r * n, u_dev + r * n, ux_dev + r * n, uy_dev + r * n, w, st, &se);
+    for (int r = 0; r < (folded ? 1 : nrhs) && rc == VFMM_OK; ++r) {
+        rc = folded ? solve_one(tree->t, *w.ps, *ops, f_dev, u_dev, ux_dev, uy_dev, w, st, &se)
+                    : solve_one(tree->t, tree->t.plans, *ops, f_dev + r * n, u_dev + r * n, ux_dev + r * n,
+                                uy_dev + r * n, w, st, &se);
         if (rc != VFMM_OK) break;
         cudaError_t e = cudaEventSynchronize(se.ev[2 * ST_LEAF + 1]);
         if (e != cudaSuccess) {

@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -78,28 +79,31 @@ __global__ void table_slice_kernel(const double* __restrict__ T, int R, int kk, 
     }
 }
 
+// out[r] = max |f| of right-hand side r (bits of the double; grid.y = r).
 __global__ void fmax_abs_kernel(const double* __restrict__ f, int64_t n, unsigned long long* __restrict__ out) {
+    const double* fr = f + (size_t)blockIdx.y * n;
     double m = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, fabs(f[i]));
+        m = fmax(m, fabs(fr[i]));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(m));
 }
 
-// fsl[leaf][i][k] from f[leaf][k] / 2^E_f; also stores E_f.
-__global__ void f_slice_kernel(const double* __restrict__ f, int nleaf, int kk, int Kp,
+// fsl[leaf * R + r][i][k] from f_r[leaf][k] / 2^E_f[r]; also stores E_f[r].
+__global__ void f_slice_kernel(const double* __restrict__ f, int nleaf, int kk, int Kp, int R,
                                const unsigned long long* __restrict__ fmax_bits, int* __restrict__ Ef,
                                bf16* __restrict__ fsl) {
-    const double fm = __longlong_as_double((long long)*fmax_bits);
-    int e = 0;
-    if (fm > 0.0) frexp(fm, &e);
-    const int64_t total = (int64_t)nleaf * Kp;
+    const int64_t total = (int64_t)nleaf * R * Kp;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t leaf = q / Kp;
-        int k = (int)(q % Kp);
-        slice_fixed(k < kk ? f[leaf * kk + k] : 0.0, e, fsl + slice_off(leaf, Kp, k), kKBlock);
+        const int64_t row = q / Kp;
+        const int k = (int)(q % Kp);
+        const int r = (int)(row % R);
+        const int64_t leaf = row / R;
+        const int e = exp_bound(__longlong_as_double((long long)fmax_bits[r]));
+        const double v = k < kk ? f[((size_t)r * nleaf + leaf) * kk + k] : 0.0;
+        slice_fixed(v, e, fsl + slice_off(row, Kp, k), kKBlock);
+        if (leaf == 0 && k == 0) Ef[r] = e;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *Ef = e;
 }
 
 // ---------------------------------------------------------------- the tcgen05 kernel
@@ -385,21 +389,27 @@ void mixed_free(vfmm_ops* o) {
 // Groups of 128 targets sorted by `key`; per group the tables present and, per table, the A row
 // of each target (-1 when the target has no entry for that table).
 int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
-                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, SplitPlan* P) {
-    const int nt = (int)tgt_id.size();
-    std::vector<int32_t> order(nt);
-    for (int t = 0; t < nt; ++t) order[t] = t;
+                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
+                     SplitPlan* P) {
+    // Targets sorted by key; target t stands for the R consecutive virtual targets t * R + r, whose
+    // A rows are src * R + r: the right-hand sides of one target share its set of tables.
+    const int nt0 = (int)tgt_id.size();
+    std::vector<int32_t> order(nt0);
+    for (int t = 0; t < nt0; ++t) order[t] = t;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key[x] < key[y]; });
-    const int ng = (nt + kTileM - 1) / kTileM;
+    const int64_t nt = (int64_t)nt0 * R;
+    if (nt > (int64_t)INT32_MAX / 2) return fail(VFMM_ERR_INVALID_ARG, "too many rows for one split contraction");
+    const int ng = (int)((nt + kTileM - 1) / kTileM);
     std::vector<int32_t> gtgt((size_t)std::max(ng, 1) * kTileM, -1), gptr(ng + 1, 0), gcfg, gsrc;
     std::vector<int32_t> slot(n_tables, -1);
     std::vector<char> present(n_tables, 0);
     for (int g = 0; g < ng; ++g) {
         std::fill(present.begin(), present.end(), 0);
-        const int m_end = std::min(kTileM, nt - g * kTileM);
+        const int m_end = (int)std::min<int64_t>(kTileM, nt - (int64_t)g * kTileM);
         for (int m = 0; m < m_end; ++m) {
-            int t = order[g * kTileM + m];
-            gtgt[(size_t)g * kTileM + m] = tgt_id[t];
+            const int64_t v = (int64_t)g * kTileM + m;
+            const int t = order[v / R], r = (int)(v % R);
+            gtgt[(size_t)g * kTileM + m] = tgt_id[t] * R + r;
             for (auto& it : items[t]) present[it.first] = 1;
         }
         for (int c = 0; c < n_tables; ++c) {
@@ -409,8 +419,9 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
             gsrc.resize(gsrc.size() + kTileM, -1);
         }
         for (int m = 0; m < m_end; ++m) {
-            int t = order[g * kTileM + m];
-            for (auto& it : items[t]) gsrc[(size_t)slot[it.first] * kTileM + m] = it.second;
+            const int64_t v = (int64_t)g * kTileM + m;
+            const int t = order[v / R], r = (int)(v % R);
+            for (auto& it : items[t]) gsrc[(size_t)slot[it.first] * kTileM + m] = it.second * R + r;
         }
         gptr[g + 1] = (int32_t)gcfg.size();
     }
@@ -443,6 +454,14 @@ void free_split_plan(SplitPlan* P) {
     for (int32_t* p : ps)
         if (p) cudaFree(p);
     *P = SplitPlan();
+}
+
+void free_plan_set(PlanSet* ps) {
+    free_split_plan(&ps->near);
+    free_split_plan(&ps->s2m);
+    free_split_plan(&ps->m2l);
+    free_split_plan(&ps->far);
+    free_split_plan(&ps->s2l);
 }
 
 static size_t smem_bytes() { return (size_t)kStages * kSlices * (kTileM * 64 + kTileN * 64) + 1024; }
@@ -503,14 +522,15 @@ int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int
 }
 
 // Near field: targets are leaves; tables are the 33 configurations; A rows are leaves.
-int build_mixed_plan(DeviceTree* T) {
-    const int nb = T->n_boxes, nl = T->n_leaves;
-    std::vector<int32_t> ptr(nb + 1), idx(T->llen[VFMM_LIST_U]), cfg(T->llen[VFMM_LIST_U]), bol(nl), lob(nb);
-    VFMM_CUDA(cudaMemcpy(ptr.data(), T->lptr[VFMM_LIST_U], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(idx.data(), T->lidx[VFMM_LIST_U], idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(cfg.data(), T->lcfg[VFMM_LIST_U], cfg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(bol.data(), T->box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(lob.data(), T->leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+static int build_plans(const DeviceTree& T, int R, PlanSet* PS) {
+    PS->R = R;
+    const int nb = T.n_boxes, nl = T.n_leaves;
+    std::vector<int32_t> ptr(nb + 1), idx(T.llen[VFMM_LIST_U]), cfg(T.llen[VFMM_LIST_U]), bol(nl), lob(nb);
+    VFMM_CUDA(cudaMemcpy(ptr.data(), T.lptr[VFMM_LIST_U], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(idx.data(), T.lidx[VFMM_LIST_U], idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(cfg.data(), T.lcfg[VFMM_LIST_U], cfg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(bol.data(), T.box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(lob.data(), T.leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
     std::vector<int32_t> tgt(nl);
     std::vector<std::vector<std::pair<int32_t, int32_t>>> items(nl);
     std::vector<std::pair<uint64_t, uint64_t>> key(nl);
@@ -524,22 +544,54 @@ int build_mixed_plan(DeviceTree* T) {
         }
         key[t] = {sig, (uint64_t)t};
     }
-    const int R = 3 * T->k * T->k;
-    VFMM_CHECK(build_split_plan(tgt, items, key, kNearCfg, (R + kTileN - 1) / kTileN, &T->plan_near));
-    return build_far_plans(T);
+    const int rows = 3 * T.k * T.k;
+    VFMM_CHECK(build_split_plan(tgt, items, key, kNearCfg, (rows + kTileN - 1) / kTileN, R, &PS->near));
+    return build_far_plans(T, R, PS);
 }
 
-int near_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, const MixedWork& w, cudaStream_t st) {
+int build_mixed_plan(DeviceTree* T) {
+    VFMM_CHECK(build_far_slots(T));
+    T->plans_r = new std::map<int, PlanSet*>();
+    T->plans_mu = new std::mutex();
+    return build_plans(*T, 1, &T->plans);
+}
+
+int plans_for(const DeviceTree& T, int R, const PlanSet** out) {
+    if (R == 1) {
+        *out = &T.plans;
+        return VFMM_OK;
+    }
+    if (!T.plans_mu || !T.plans_r) return fail(VFMM_ERR_INTERNAL, "tree has no plan cache");
+    std::lock_guard<std::mutex> lock(*T.plans_mu);
+    auto it = T.plans_r->find(R);
+    if (it != T.plans_r->end()) {
+        *out = it->second;
+        return VFMM_OK;
+    }
+    PlanSet* ps = new PlanSet();
+    int rc = build_plans(T, R, ps);
+    if (rc != VFMM_OK) {
+        free_plan_set(ps);
+        delete ps;
+        return rc;
+    }
+    (*T.plans_r)[R] = ps;
+    *out = ps;
+    return VFMM_OK;
+}
+
+int near_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, const MixedWork& w,
+               cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    const int kk = o.k * o.k;
-    VFMM_CUDA(cudaMemsetAsync(w.fmax, 0, sizeof(unsigned long long), st));
+    const int kk = o.k * o.k, R = PS.R;
+    VFMM_CUDA(cudaMemsetAsync(w.fmax, 0, (size_t)R * sizeof(unsigned long long), st));
     const int64_t n = (int64_t)T.n_leaves * kk;
-    fmax_abs_kernel<<<std::min<int64_t>(1024, (n + 255) / 256), 256, 0, st>>>(f, n, w.fmax);
-    const int64_t ns = (int64_t)T.n_leaves * mo->Kp;
-    f_slice_kernel<<<(unsigned)std::min<int64_t>(65535, (ns + 255) / 256), 256, 0, st>>>(f, T.n_leaves, kk, mo->Kp,
+    fmax_abs_kernel<<<dim3((unsigned)std::min<int64_t>(1024, (n + 255) / 256), R), 256, 0, st>>>(f, n, w.fmax);
+    const int64_t ns = (int64_t)T.n_leaves * R * mo->Kp;
+    f_slice_kernel<<<(unsigned)std::min<int64_t>(65535, (ns + 255) / 256), 256, 0, st>>>(f, T.n_leaves, kk, mo->Kp, R,
                                                                                          w.fmax, w.Ef, (bf16*)w.fsl);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(T.plan_near, w.fsl, mo->tsl, mo->Kp, mo->Rp, w.out, w.err, w.part, T.n_leaves, st);
+    return split_gemm(PS.near, w.fsl, mo->tsl, mo->Kp, mo->Rp, w.out, w.err, w.part, (size_t)T.n_leaves * R, st);
 }
 
 }  // namespace vfmm

@@ -47,6 +47,14 @@ __device__ __forceinline__ void slice_fixed(double v, int E, __nv_bfloat16* out,
     }
 }
 
+// Binary exponent e with |m| < 2^e (frexp convention), from the bits; 0 for m = 0.
+__device__ __forceinline__ int exp_bound(double m) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+    if ((bits << 1) == 0) return 0;
+    const int ev = (int)((bits >> 52) & 0x7FF);
+    return (ev ? ev : 1) - 1022;
+}
+
 struct MixedOps {
     int N = kTileN; // table rows per tile
     int Rp = 0;     // 3k^2 rounded up to N
@@ -72,12 +80,13 @@ struct MixedOps {
 struct MixedWork {
     void* fsl = nullptr;                  // bf16 [n_leaves][kSlices][Kp]
     float2* out = nullptr;                // [n_leaves][Rp] (hi, lo), scaled by 2^-(E_f + E_r)
-    unsigned long long* fmax = nullptr;   // max |f| (bits)
-    int* Ef = nullptr;                    // exponent of f
+    unsigned long long* fmax = nullptr;   // [R] max |f| per right-hand side (bits)
+    int* Ef = nullptr;                    // [R] exponent of f per right-hand side
     int* err = nullptr;                   // non-zero after a bounded wait expired
     // far field
     float2* s2m_out = nullptr;            // [n_leaves][Rx]
-    int* glev = nullptr;                  // [depth + 1] G(l): |coefficient k| 2^floor(k/4) < 2^G(l) on level l
+    int* bexp = nullptr;                  // [n_boxes * R] exponent bound of each virtual box's multipole
+    int* glev = nullptr;                  // [(depth + 1) * R] G(l, r): |coefficient k| 2^floor(k/4) < 2^G
     void* msl = nullptr;                  // bf16 [n_boxes][kSlices][Kx]
     float2* m2l_out = nullptr;            // [n_boxes][Rx]
     double* m2l_c0 = nullptr;             // [n_boxes] Re local coefficient 0 from the V and X lists
@@ -90,22 +99,26 @@ struct MixedWork {
 
 int build_split_plan(const std::vector<int32_t>& tgt_id,
                      const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
-                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, SplitPlan* P);
+                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
+                     SplitPlan* P);
 int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int Rp, float2* out, int* err,
                float2* part, size_t n_out_rows, cudaStream_t st);
-size_t split_part_elems(const DeviceTree& T, const vfmm_ops& o);
+size_t split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o);
 int build_mixed_plan(DeviceTree* T);
-int build_far_plans(DeviceTree* T);
-int near_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, const MixedWork& w, cudaStream_t st);
+int build_far_slots(DeviceTree* T);
+int build_far_plans(const DeviceTree& T, int R, PlanSet* PS);
+int near_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, const MixedWork& w,
+               cudaStream_t st);
 int far_prepare(vfmm_ops* o, cudaStream_t st);
 void far_free(MixedOps* mo);
-size_t far_workspace_doubles(const DeviceTree& T, const vfmm_ops& o);
-// Stages of the split-precision far field (see mixed_far.cu).
-int s2m_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, double* Mexp, const MixedWork& w,
+// Stages of the split-precision far field (see mixed_far.cu). Multipoles and locals are stored per
+// virtual box (box * R + r); f is [R][n_leaves][k^2].
+int s2m_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* Mexp,
+              const MixedWork& w, cudaStream_t st);
+int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* Mexp, const MixedWork& w,
               cudaStream_t st);
-int m2l_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const MixedWork& w, cudaStream_t st);
-int s2l_mixed(const DeviceTree& T, const vfmm_ops& o, const MixedWork& w, cudaStream_t st);
-int far_leaf_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const double* Lexp,
+int s2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st);
+int far_leaf_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* Mexp, const double* Lexp,
                    const MixedWork& w, cudaStream_t st);
 
 }  // namespace vfmm

@@ -180,20 +180,33 @@ void far_free(MixedOps* mo) {
 }
 
 // ---------------------------------------------------------------- schedules
-int build_far_plans(DeviceTree* T) {
+// Rows of the leaf far-field operand: per leaf, slot 0 = its own local (L2T), slot 1 + j = its
+// j-th W entry; far_slot[leaf] = first slot (right-hand side r of slot s is row s * R + r).
+int build_far_slots(DeviceTree* T) {
     const int nb = T->n_boxes, nl = T->n_leaves;
-    std::vector<int32_t> bol(nl), lob(nb), lev(nb);
+    std::vector<int32_t> bol(nl), ptr(nb + 1), slot(nl + 1, 0);
     VFMM_CUDA(cudaMemcpy(bol.data(), T->box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(lob.data(), T->leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(lev.data(), T->level, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(ptr.data(), T->lptr[VFMM_LIST_W], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int t = 0; t < nl; ++t) slot[t + 1] = slot[t] + 1 + (ptr[bol[t] + 1] - ptr[bol[t]]);
+    T->n_far_slots = slot[nl];
+    VFMM_CUDA(cudaMalloc(&T->far_slot, (nl + 1) * sizeof(int32_t)));
+    VFMM_CUDA(cudaMemcpy(T->far_slot, slot.data(), (nl + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return VFMM_OK;
+}
+
+int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
+    const int nb = T.n_boxes, nl = T.n_leaves;
+    std::vector<int32_t> bol(nl), lob(nb);
+    VFMM_CUDA(cudaMemcpy(bol.data(), T.box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(lob.data(), T.leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
     auto fetch = [&](int q, std::vector<int32_t>& ptr, std::vector<int32_t>& idx, std::vector<int32_t>& cfg) -> int {
         ptr.resize(nb + 1);
-        idx.resize(T->llen[q]);
-        cfg.resize(T->llen[q]);
-        VFMM_CUDA(cudaMemcpy(ptr.data(), T->lptr[q], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        if (T->llen[q]) {
-            VFMM_CUDA(cudaMemcpy(idx.data(), T->lidx[q], idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-            VFMM_CUDA(cudaMemcpy(cfg.data(), T->lcfg[q], cfg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        idx.resize(T.llen[q]);
+        cfg.resize(T.llen[q]);
+        VFMM_CUDA(cudaMemcpy(ptr.data(), T.lptr[q], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (T.llen[q]) {
+            VFMM_CUDA(cudaMemcpy(idx.data(), T.lidx[q], idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            VFMM_CUDA(cudaMemcpy(cfg.data(), T.lcfg[q], cfg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
         }
         return VFMM_OK;
     };
@@ -207,7 +220,7 @@ int build_far_plans(DeviceTree* T) {
             items[t].push_back({0, t});
             key[t] = {0, (uint64_t)t};
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, &T->plan_s2m));
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, R, &PS->s2m));
     }
     // M2L: boxes with a V list, tables = the 40 offsets, A row = source box
     {
@@ -227,7 +240,7 @@ int build_far_plans(DeviceTree* T) {
             }
             key.push_back({sig, (uint64_t)b});
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, kVCfg, 1, &T->plan_m2l));
+        VFMM_CHECK(build_split_plan(tgt, items, key, kVCfg, 1, R, &PS->m2l));
     }
     // S2L: boxes with an X list, tables 20 configurations, A row = source leaf
     {
@@ -247,7 +260,7 @@ int build_far_plans(DeviceTree* T) {
             }
             key.push_back({sig, (uint64_t)b});
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, kFarCfg, 1, &T->plan_s2l));
+        VFMM_CHECK(build_split_plan(tgt, items, key, kFarCfg, 1, R, &PS->s2l));
     }
     // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
     {
@@ -256,10 +269,7 @@ int build_far_plans(DeviceTree* T) {
         std::vector<int32_t> tgt(nl), slot(nl + 1, 0);
         std::vector<std::vector<std::pair<int32_t, int32_t>>> items(nl);
         std::vector<std::pair<uint64_t, uint64_t>> key(nl);
-        for (int t = 0; t < nl; ++t) {
-            int b = bol[t];
-            slot[t + 1] = slot[t] + 1 + (ptr[b + 1] - ptr[b]);
-        }
+        for (int t = 0; t < nl; ++t) slot[t + 1] = slot[t] + 1 + (ptr[bol[t] + 1] - ptr[bol[t]]);
         for (int t = 0; t < nl; ++t) {
             int b = bol[t];
             tgt[t] = t;
@@ -271,130 +281,154 @@ int build_far_plans(DeviceTree* T) {
             }
             key[t] = {sig, (uint64_t)t};
         }
-        const int R = 3 * T->k * T->k;
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1 + kFarCfg, (R + kTileN - 1) / kTileN, &T->plan_far));
-        T->n_far_slots = slot[nl];
-        VFMM_CUDA(cudaMalloc(&T->far_slot, (nl + 1) * sizeof(int32_t)));
-        VFMM_CUDA(cudaMemcpy(T->far_slot, slot.data(), (nl + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+        const int rows = 3 * T.k * T.k;
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1 + kFarCfg, (rows + kTileN - 1) / kTileN, R, &PS->far));
     }
     return VFMM_OK;
 }
 
-// Largest partial-sum buffer any split contraction of this tree needs (float2 elements).
-size_t split_part_elems(const DeviceTree& T, const vfmm_ops& o) {
+// Largest partial-sum buffer any split contraction of this plan set needs (float2 elements).
+size_t split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    size_t a = T.plan_near.split > 1 ? (size_t)T.plan_near.split * T.n_leaves * mo->Rp : 0;
-    size_t b = T.plan_m2l.split > 1 ? (size_t)T.plan_m2l.split * T.n_boxes * mo->Rx : 0;
-    size_t c = T.plan_far.split > 1 ? (size_t)T.plan_far.split * T.n_leaves * mo->Rp : 0;
-    size_t d = T.plan_s2l.split > 1 ? (size_t)T.plan_s2l.split * T.n_boxes * mo->Rx : 0;
+    const size_t R = (size_t)PS.R;
+    size_t a = PS.near.split > 1 ? (size_t)PS.near.split * T.n_leaves * R * mo->Rp : 0;
+    size_t b = PS.m2l.split > 1 ? (size_t)PS.m2l.split * T.n_boxes * R * mo->Rx : 0;
+    size_t c = PS.far.split > 1 ? (size_t)PS.far.split * T.n_leaves * R * mo->Rp : 0;
+    size_t d = PS.s2l.split > 1 ? (size_t)PS.s2l.split * T.n_boxes * R * mo->Rx : 0;
     return std::max(std::max(a, d), std::max(b, c));
 }
 
 // ---------------------------------------------------------------- S2M
-__global__ void s2m_finish_kernel(int nleaf, int kk, int p, int Rx, const int32_t* __restrict__ box_of_leaf,
+// One CTA per virtual leaf (leaf, r): coefficient 0 (the mass) in FP64, the rest from the split
+// contraction scaled back by 2^(E_f[r] + E_row).
+__global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const int32_t* __restrict__ box_of_leaf,
                                   const int32_t* __restrict__ level, double width, const double* __restrict__ f,
                                   const double* __restrict__ s2m, const float2* __restrict__ out,
                                   const int* __restrict__ E, const int* __restrict__ Ef, double* __restrict__ Mexp) {
-    const int leaf = blockIdx.x;
+    const int vl = blockIdx.x;
+    const int leaf = vl / R, r = vl - leaf * R;
     const int b = box_of_leaf[leaf];
     const double h = ldexp(width, -level[b]);
     const int P2 = 2 * (p + 1);
-    double* M = Mexp + (size_t)b * P2;
+    double* M = Mexp + ((size_t)b * R + r) * P2;
+    const double* fl = f + ((size_t)r * nleaf + leaf) * kk;
     if (threadIdx.x < 32) {
         double m = 0.0;
-        for (int s = threadIdx.x; s < kk; s += 32) m += s2m[s] * f[(size_t)leaf * kk + s];
+        for (int s = threadIdx.x; s < kk; s += 32) m += s2m[s] * fl[s];
         for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
         if (threadIdx.x == 0) {
             M[0] = h * h * m;
             M[1] = 0.0;
         }
     }
-    const int ef = *Ef;
-    for (int r = threadIdx.x; r < 2 * p; r += blockDim.x) {
-        float2 v = out[(size_t)leaf * Rx + r];
-        M[2 + r] = h * h * ldexp((double)v.x + (double)v.y, ef + E[r]);
+    const int ef = Ef[r];
+    for (int q = threadIdx.x; q < 2 * p; q += blockDim.x) {
+        float2 v = out[(size_t)vl * Rx + q];
+        M[2 + q] = h * h * ldexp((double)v.x + (double)v.y, ef + E[q]);
     }
 }
 
-int s2m_mixed(const DeviceTree& T, const vfmm_ops& o, const double* f, double* Mexp, const MixedWork& w,
-              cudaStream_t st) {
+int s2m_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* Mexp,
+              const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    VFMM_CHECK(split_gemm(T.plan_s2m, w.fsl, mo->s2m_sl, mo->Kp, mo->Rx, w.s2m_out, w.err, nullptr, 0, st));
-    s2m_finish_kernel<<<T.n_leaves, 128, 0, st>>>(T.n_leaves, o.k * o.k, o.p, mo->Rx, T.box_of_leaf, T.level, T.width,
-                                                  f, o.s2m, w.s2m_out, mo->s2m_E, w.Ef, Mexp);
+    VFMM_CHECK(split_gemm(PS.s2m, w.fsl, mo->s2m_sl, mo->Kp, mo->Rx, w.s2m_out, w.err, nullptr, 0, st));
+    s2m_finish_kernel<<<T.n_leaves * PS.R, 128, 0, st>>>(T.n_leaves, PS.R, o.k * o.k, o.p, mo->Rx, T.box_of_leaf,
+                                                         T.level, T.width, f, o.s2m, w.s2m_out, mo->s2m_E, w.Ef,
+                                                         Mexp);
     VFMM_CUDA(cudaGetLastError());
     return VFMM_OK;
 }
 
 // ---------------------------------------------------------------- M2L
-// G(l) = max over the level's boxes and coefficients k of the binary exponent of |a_k| 2^floor(k/4)
-// (frexp convention, from the bits: integer work only), so that |a_k| 2^floor(k/4) < 2^G(l).
-constexpr int kLevelChunk = 64;  // boxes per CTA
-__global__ void level_exp_kernel(const int32_t* __restrict__ level, int begin, int end, int P2,
-                                 const double* __restrict__ Mexp, int* __restrict__ G) {
-    __shared__ int sG[32];
-    if (threadIdx.x < 32) sG[threadIdx.x] = INT_MIN;
-    __syncthreads();
-    const int b0 = begin + blockIdx.x * kLevelChunk, b1 = min(end, b0 + kLevelChunk);
-    for (int q = threadIdx.x; q < (b1 - b0) * P2; q += blockDim.x) {
-        const int b = b0 + q / P2, k = q % P2;
-        const unsigned long long bits = (unsigned long long)__double_as_longlong(Mexp[(size_t)b * P2 + k]);
+// bexp[vb] = max over coefficients k of the binary exponent of |a_k| 2^floor(k/4) (frexp
+// convention, from the bits: integer work only); INT_MIN when the multipole is zero. A warp per
+// virtual box.
+__global__ void box_exp_kernel(int64_t vb0, int64_t vb1, int P2, const double* __restrict__ Mexp,
+                               int* __restrict__ bexp) {
+    const int64_t vb = vb0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (vb >= vb1) return;
+    int e = INT_MIN;
+    for (int k = lane; k < P2; k += 32) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(Mexp[(size_t)vb * P2 + k]);
         if ((bits << 1) == 0) continue;  // +-0
-        int ev = (int)((bits >> 52) & 0x7FF);
-        if (ev == 0) ev = 1;
-        atomicMax(&sG[level[b] & 31], ev - 1022 + (k >> 2));
+        const int ev = (int)((bits >> 52) & 0x7FF);
+        e = max(e, (ev ? ev : 1) - 1022 + (k >> 2));
     }
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0) bexp[vb] = e;
+}
+
+// G[l * R + r] = max of bexp over the boxes of level l for right-hand side r (grid: levels x R).
+__global__ void level_exp_kernel(const int32_t* __restrict__ level_start, int lmin, int R,
+                                 const int* __restrict__ bexp, int* __restrict__ G) {
+    __shared__ int red[256];
+    const int l = lmin + blockIdx.x, r = blockIdx.y;
+    int e = INT_MIN;
+    for (int b = level_start[l] + threadIdx.x; b < level_start[l + 1]; b += blockDim.x)
+        e = max(e, bexp[(size_t)b * R + r]);
+    red[threadIdx.x] = e;
     __syncthreads();
-    if (threadIdx.x < 32 && sG[threadIdx.x] != INT_MIN) atomicMax(&G[threadIdx.x], sG[threadIdx.x]);
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    // a level whose multipoles are all zero: any scale works (every operand is 0)
+    if (threadIdx.x == 0) G[(size_t)l * R + r] = red[0] == INT_MIN ? 0 : red[0];
 }
 
-__global__ void multipole_slice_kernel(const int32_t* __restrict__ level, int begin, int end, int P2, int Kx,
-                                       const double* __restrict__ Mexp, const int* __restrict__ G,
+__global__ void multipole_slice_kernel(const int32_t* __restrict__ level, int64_t vb0, int64_t vb1, int R, int P2,
+                                       int Kx, const double* __restrict__ Mexp, const int* __restrict__ G,
                                        bf16* __restrict__ msl) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t total = (int64_t)(end - begin) * Kx;
-    if (q >= total) return;
-    int b = begin + (int)(q / Kx), k = (int)(q % Kx);
-    const double a = k < P2 ? Mexp[(size_t)b * P2 + k] : 0.0;
-    slice_fixed(a, G[level[b]] - (k >> 2), msl + slice_at(b, Kx, k), kKBlock);
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (vb1 - vb0) * Kx) return;
+    const int64_t vb = vb0 + q / Kx;
+    const int k = (int)(q % Kx);
+    const int64_t b = vb / R;
+    const int r = (int)(vb - b * R);
+    const double a = k < P2 ? Mexp[(size_t)vb * P2 + k] : 0.0;
+    slice_fixed(a, G[(size_t)level[b] * R + r] - (k >> 2), msl + slice_at(vb, Kx, k), kKBlock);
 }
 
-int m2l_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const MixedWork& w, cudaStream_t st) {
+int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* Mexp, const MixedWork& w,
+              cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    if (T.depth < 2 || T.plan_m2l.n_groups == 0) return VFMM_OK;
-    const int P2 = 2 * (o.p + 1);
-    const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
-    // 0x80 bytes: a very negative start value (levels whose multipoles are all zero keep it)
-    VFMM_CUDA(cudaMemsetAsync(w.glev, 0x80, (size_t)(T.depth + 1) * sizeof(int), st));
-    level_exp_kernel<<<(end - begin + kLevelChunk - 1) / kLevelChunk, 256, 0, st>>>(T.level, begin, end, P2, Mexp,
-                                                                                  w.glev);
-    int64_t n2 = (int64_t)(end - begin) * mo->Kx;
-    multipole_slice_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(T.level, begin, end, P2, mo->Kx, Mexp,
+    if (T.depth < 2 || PS.m2l.n_groups == 0) return VFMM_OK;
+    const int P2 = 2 * (o.p + 1), R = PS.R;
+    const int64_t vb0 = (int64_t)T.level_start[2] * R, vb1 = (int64_t)T.level_start[T.depth + 1] * R;
+    box_exp_kernel<<<(unsigned)((vb1 - vb0 + 7) / 8), 256, 0, st>>>(vb0, vb1, P2, Mexp, w.bexp);
+    level_exp_kernel<<<dim3(T.depth - 1, R), 256, 0, st>>>(T.level_start_dev, 2, R, w.bexp, w.glev);
+    const int64_t n2 = (vb1 - vb0) * mo->Kx;
+    multipole_slice_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(T.level, vb0, vb1, R, P2, mo->Kx, Mexp,
                                                                           w.glev, (bf16*)w.msl);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(T.plan_m2l, w.msl, mo->m2l_sl, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, T.n_boxes, st);
+    return split_gemm(PS.m2l, w.msl, mo->m2l_sl, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, (size_t)T.n_boxes * R,
+                      st);
 }
 
 // ---------------------------------------------------------------- S2L
-int s2l_mixed(const DeviceTree& T, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
+int s2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    return split_gemm(T.plan_s2l, w.fsl, mo->s2l_sl, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part, T.n_boxes, st);
+    return split_gemm(PS.s2l, w.fsl, mo->s2l_sl, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part, (size_t)T.n_boxes * PS.R,
+                      st);
 }
 
 // ---------------------------------------------------------------- leaf far field
-// One CTA per leaf: operand rows (own local without coefficient 0, W multipoles) scaled by 2^-E_t.
-__global__ void far_operand_kernel(int nleaf, int P2, int Kx, const int32_t* __restrict__ box_of_leaf,
+// One CTA per virtual leaf (leaf, r): operand rows (own local without coefficient 0, W multipoles)
+// scaled by 2^-E_t, E_t the exponent of the largest of them.
+__global__ void far_operand_kernel(int nleaf, int R, int P2, int Kx, const int32_t* __restrict__ box_of_leaf,
                                    const int32_t* __restrict__ far_slot, const int32_t* __restrict__ wptr,
                                    const int32_t* __restrict__ widx, const double* __restrict__ Mexp,
                                    const double* __restrict__ Lexp, int* __restrict__ Et, bf16* __restrict__ aprep) {
     __shared__ double red[128];
-    const int leaf = blockIdx.x;
+    const int vl = blockIdx.x;
+    const int leaf = vl / R, r = vl - leaf * R;
     const int b = box_of_leaf[leaf];
     const int s0 = far_slot[leaf], ns = far_slot[leaf + 1] - s0;
     auto value = [&](int j, int k) -> double {
         if (k >= P2) return 0.0;
-        if (j == 0) return k >= 2 ? Lexp[(size_t)b * P2 + k] : 0.0;
-        return Mexp[(size_t)widx[wptr[b] + j - 1] * P2 + k];
+        if (j == 0) return k >= 2 ? Lexp[((size_t)b * R + r) * P2 + k] : 0.0;
+        return Mexp[((size_t)widx[wptr[b] + j - 1] * R + r) * P2 + k];
     };
     double m = 0.0;
     for (int q = threadIdx.x; q < ns * P2; q += blockDim.x) m = fmax(m, fabs(value(q / P2, q % P2)));
@@ -404,37 +438,41 @@ __global__ void far_operand_kernel(int nleaf, int P2, int Kx, const int32_t* __r
         if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
         __syncthreads();
     }
-    const int e = exp_of(red[0]);
-    if (threadIdx.x == 0) Et[leaf] = e;
+    const int e = exp_bound(red[0]);
+    if (threadIdx.x == 0) Et[vl] = e;
     for (int q = threadIdx.x; q < ns * Kx; q += blockDim.x) {
         int j = q / Kx, k = q % Kx;
-        slice_fixed(value(j, k), e, aprep + slice_at(s0 + j, Kx, k), kKBlock);
+        slice_fixed(value(j, k), e, aprep + slice_at((size_t)(s0 + j) * R + r, Kx, k), kKBlock);
     }
 }
 
-int far_leaf_mixed(const DeviceTree& T, const vfmm_ops& o, const double* Mexp, const double* Lexp,
+int far_leaf_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* Mexp, const double* Lexp,
                    const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    far_operand_kernel<<<T.n_leaves, 128, 0, st>>>(T.n_leaves, 2 * (o.p + 1), mo->Kx, T.box_of_leaf, T.far_slot,
-                                                   T.lptr[VFMM_LIST_W], T.lidx[VFMM_LIST_W], Mexp, Lexp, w.Et,
-                                                   (bf16*)w.aprep);
+    far_operand_kernel<<<T.n_leaves * PS.R, 128, 0, st>>>(T.n_leaves, PS.R, 2 * (o.p + 1), mo->Kx, T.box_of_leaf,
+                                                          T.far_slot, T.lptr[VFMM_LIST_W], T.lidx[VFMM_LIST_W], Mexp,
+                                                          Lexp, w.Et, (bf16*)w.aprep);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(T.plan_far, w.aprep, mo->far_sl, mo->Kx, mo->Rp, w.far_out, w.err, w.part, T.n_leaves, st);
+    return split_gemm(PS.far, w.aprep, mo->far_sl, mo->Kx, mo->Rp, w.far_out, w.err, w.part,
+                      (size_t)T.n_leaves * PS.R, st);
 }
 
 }  // namespace vfmm
 
 using namespace vfmm;
 
-extern "C" int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, double* out) {
+extern "C" int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs, double* out) {
     if (!tree || !ops || !out) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    if (nrhs < 1) return fail(VFMM_ERR_INVALID_ARG, "nrhs must be >= 1");
     const DeviceTree& T = tree->t;
     for (int i = 0; i < VFMM_N_WORK; ++i) out[i] = 0.0;
     const double kk = (double)ops->k * ops->k;
-    out[5] = 2.0 * 3.0 * kk * kk * (double)T.llen[VFMM_LIST_U];
+    out[5] = 2.0 * 3.0 * kk * kk * (double)T.llen[VFMM_LIST_U] * nrhs;
     out[6] = (double)T.llen[VFMM_LIST_U];
     const MixedOps* mo = (const MixedOps*)ops->mixed;
     if (ops->precision != VFMM_MIXED || !mo) return VFMM_OK;
+    const PlanSet* PS = nullptr;
+    VFMM_CHECK(plans_for(T, nrhs, &PS));
     int np = 0;
     for (int i = 1; i <= kSlices; ++i)
         for (int j = 1; i + j <= kSlices + 1; ++j) ++np;
@@ -442,10 +480,10 @@ extern "C" int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, doubl
     auto tc = [&](const SplitPlan& P, int Kp, int Rp) {
         return 2.0 * (double)P.entries * (Rp / kTileN) * (double)Kp * np * kTileM * kTileN;
     };
-    out[0] = tc(T.plan_near, mo->Kp, mo->Rp);
-    out[1] = tc(T.plan_m2l, mo->Kx, mo->Rx);
-    out[2] = tc(T.plan_far, mo->Kx, mo->Rp);
-    out[3] = tc(T.plan_s2l, mo->Kp, mo->Rx);
-    out[4] = tc(T.plan_s2m, mo->Kp, mo->Rx);
+    out[0] = tc(PS->near, mo->Kp, mo->Rp);
+    out[1] = tc(PS->m2l, mo->Kx, mo->Rx);
+    out[2] = tc(PS->far, mo->Kx, mo->Rp);
+    out[3] = tc(PS->s2l, mo->Kp, mo->Rx);
+    out[4] = tc(PS->s2m, mo->Kp, mo->Rx);
     return VFMM_OK;
 }

@@ -729,11 +729,15 @@ void free_tree(DeviceTree* t) {
     void* ps[] = {t->key,         t->level,       t->ix,       t->iy,           t->parent,     t->child0,
                   t->leaf_of_box, t->box_of_leaf, t->level_start_dev, t->u_by_cfg, t->u_tgt, t->near_tiles,
                   t->far_slot,    t->nonleaf};
-    free_split_plan(&t->plan_near);
-    free_split_plan(&t->plan_s2m);
-    free_split_plan(&t->plan_m2l);
-    free_split_plan(&t->plan_far);
-    free_split_plan(&t->plan_s2l);
+    free_plan_set(&t->plans);
+    if (t->plans_r) {
+        for (auto& kv : *t->plans_r) {
+            free_plan_set(kv.second);
+            delete kv.second;
+        }
+        delete t->plans_r;
+    }
+    delete t->plans_mu;
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int q = 0; q < 4; ++q) {

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -164,6 +166,17 @@ struct SplitPlan {
     int32_t split = 1;       // CTAs per group (each takes a share of the group's tables)
 };
 
+// The split contractions of the mixed form with R right-hand sides folded into the rows: the
+// virtual row of box or leaf x for right-hand side r is x * R + r (R consecutive rows per box).
+struct PlanSet {
+    int R = 1;
+    SplitPlan near;  // U list: targets leaves, tables 33 configurations, A rows leaves
+    SplitPlan s2m;   // targets leaves, one table, A rows leaves
+    SplitPlan m2l;   // V list: targets boxes, tables the 40 offsets, A rows boxes
+    SplitPlan far;   // L2T + W list: targets leaves, tables 0 (L2T) and 1 + W configuration, A rows far slots
+    SplitPlan s2l;   // X list: targets boxes, tables 20 configurations, A rows leaves
+};
+
 struct DeviceTree {
     // box table, canonical order
     int32_t n_boxes = 0, n_leaves = 0, depth = 0, k = 0;
@@ -191,12 +204,11 @@ struct DeviceTree {
     // GEMM tile schedule for the near field: per tile (cfg, first column)
     int32_t* near_tiles = nullptr;
     int32_t n_near_tiles = 0;
-    // split-precision schedules (VFMM_MIXED)
-    SplitPlan plan_near;  // U list: targets leaves, tables 33 configurations, A rows leaves
-    SplitPlan plan_s2m;   // targets leaves, one table, A rows leaves
-    SplitPlan plan_m2l;   // V list: targets boxes, tables level * 40 + offset, A rows boxes
-    SplitPlan plan_far;   // L2T + W list: targets leaves, tables 0 (L2T) and 1 + W configuration
-    SplitPlan plan_s2l;   // X list: targets boxes, tables 20 configurations, A rows leaves
+    // split-precision schedules (VFMM_MIXED): one right-hand side built with the tree, others on
+    // first use (plans_for), guarded by plans_mu
+    PlanSet plans;
+    std::map<int, PlanSet*>* plans_r = nullptr;
+    std::mutex* plans_mu = nullptr;
     int32_t* nonleaf = nullptr;           // non-leaf boxes in canonical order (grouped by level)
     std::vector<int32_t> nonleaf_start;   // host, depth + 2: first entry of each level
     int32_t* far_slot = nullptr;  // [n_leaves + 1] first A row of each leaf in the far operand
@@ -205,6 +217,9 @@ struct DeviceTree {
 
 void free_tree(DeviceTree* t);
 void free_split_plan(SplitPlan* p);
+void free_plan_set(PlanSet* ps);
+// Plans for R folded right-hand sides (R = 1: the tree's own set); builds and caches on first use.
+int plans_for(const DeviceTree& T, int R, const PlanSet** out);
 int build_near_tiles(DeviceTree* t);
 
 }  // namespace vfmm

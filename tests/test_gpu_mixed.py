@@ -79,3 +79,61 @@ def test_graph_replay_equals_direct_call(precision):
         stream.synchronize()
         for q in range(3):
             assert torch.equal(out[q], ref[q])
+
+
+def _stack_sources(gt, sources):
+    return torch.stack([v.source_sample(gt, s) for s in sources]).contiguous()
+
+
+def test_folded_rhs_shared_tree(oracle_ops):
+    """64 right-hand sides on the uniform depth-3, k = 8 tree (the shared-tree batch): the mixed form
+    folds them into one solve; every right-hand side against the FP64 form (all targets) and four of
+    them against the oracle."""
+    srcs = W.shared_tree_rhs(64)
+    gt = v.tree_build_uniform(0.0, 0.0, 1.0, 8, 3)
+    ot = T.build_uniform(0.0, 0.0, 1.0, 8, 3)
+    f = _stack_sources(gt, srcs)
+    ops64 = v.ops_create(8, 20, v.FP64)
+    opsmx = v.ops_create(8, 20, v.MIXED)
+    u64 = [x.cpu().numpy() for x in v.volume_potential(gt, ops64, f)]
+    umx = [x.cpu().numpy() for x in v.volume_potential(gt, opsmx, f)]
+    for r in range(len(srcs)):
+        for q in range(3):
+            assert rel(umx[q][r], u64[q][r]) < TOL, (r, q)
+    L = T.build_lists(ot)
+    for r in (0, 17, 40, 63):
+        ref = fmm.solve(ot, L, oracle_ops(8, 20), ot.sample(srcs[r]))
+        for q in range(3):
+            assert rel(umx[q][r].reshape(ref[q].shape), ref[q]) < TOL, (r, q)
+
+
+def test_folded_rhs_adaptive_tree_and_graph():
+    """Three right-hand sides on a deep adaptive k = 16 tree: folded mixed solve against the FP64
+    form, a zero right-hand side stays exactly zero, and graph replay equals the direct call."""
+    from paper_1610_00823_gb300.api import SolveGraph
+    src = W.narrow_gaussians(8, n=2, sigma=0.01, spread=0.4)
+    gt = v.tree_build(0.0, 0.0, 1.0, 16, src, 1e-10, 9)
+    f1 = v.source_sample(gt, src)
+    f2 = v.source_sample(gt, W.narrow_gaussians(9, n=3, sigma=0.03, spread=0.3))
+    f = torch.stack([f1, 1e-6 * f2, torch.zeros_like(f1)]).contiguous()
+    ops64 = v.ops_create(16, 40, v.FP64)
+    opsmx = v.ops_create(16, 40, v.MIXED)
+    u64 = v.volume_potential(gt, ops64, f)
+    umx = v.volume_potential(gt, opsmx, f)
+    for r in range(2):
+        for q in range(3):
+            assert rel(umx[q][r].cpu().numpy(), u64[q][r].cpu().numpy()) < TOL, (r, q)
+    for q in range(3):
+        assert torch.count_nonzero(umx[q][2]).item() == 0
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    out = tuple(torch.full_like(f, float("nan")) for _ in range(3))
+    ws = workspace(gt, opsmx, 3)
+    g = SolveGraph(gt, opsmx, f, out, ws, stream)
+    for q in range(3):
+        out[q].fill_(float("nan"))
+    torch.cuda.synchronize()
+    g.launch(stream)
+    stream.synchronize()
+    for q in range(3):
+        assert torch.equal(out[q], umx[q])
