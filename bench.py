@@ -22,6 +22,7 @@ for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import argparse  # noqa: E402
+import dataclasses  # noqa: E402
 import json  # noqa: E402
 import math  # noqa: E402
 import statistics  # noqa: E402
@@ -48,6 +49,9 @@ def workload(name):
         return W.uniform_gauss3()
     if name == "kinked":
         return W.kinked()
+    if name == "shared_rhs64":  # 64 right-hand sides sharing the uniform depth-3, k = 8 tree
+        base = W.uniform_gauss3()
+        return dataclasses.replace(base, name="shared_tree_rhs64_" + base.name, sources=W.shared_tree_rhs(64))
     if name.startswith("uniform_d") and "_k" in name:  # uniform_d<depth>_k<k>: 3 Gaussians, p = 2.5 k
         d, k = name[len("uniform_d"):].split("_k")
         return W.uniform_gauss3(depth=int(d), k=int(k), p=int(2.5 * int(k)))
@@ -250,9 +254,13 @@ def main():
     ops = v.ops_create(wl.k, wl.p, prec)
     torch.cuda.synchronize()
     t_ops = time.perf_counter() - t0
-    f = v.source_sample(tree, src)
+    nrhs = len(wl.sources)
+    if nrhs == 1:
+        f = v.source_sample(tree, src)
+    else:  # right-hand sides sharing the tree: [nrhs][n_leaves * k^2], one call solves them all
+        f = torch.stack([v.source_sample(tree, s) for s in wl.sources]).contiguous()
     kk = wl.k * wl.k
-    n_targets = tree.n_leaves * kk
+    n_targets = tree.n_leaves * kk * nrhs
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -260,7 +268,7 @@ def main():
     def time_form(ops_, steps, clk=None):
         """Warm-up, then `steps` timed solves (CUDA-graph replays unless --no-graph), L2 flushed between."""
         out_ = tuple(torch.empty_like(f) for _ in range(3))
-        ws_ = workspace(tree, ops_, 1)
+        ws_ = workspace(tree, ops_, nrhs)
         # the solve is captured once into a CUDA graph; every timed step replays it
         graph_ = SolveGraph(tree, ops_, f, out_, ws_, stream) if not args.no_graph else None
 
@@ -316,7 +324,7 @@ def main():
     # end to end through the host entry point (pinned buffers, copies inside the timed region)
     f_host = f.cpu().pin_memory()
     outs_host = tuple(torch.empty_like(f_host).pin_memory() for _ in range(3))
-    ws_io = workspace(tree, ops, 1, with_io=True)
+    ws_io = workspace(tree, ops, nrhs, with_io=True)
     for _ in range(2):
         v.volume_potential_host(tree, ops, f_host, out_host=outs_host, ws=ws_io, stream=stream)
     e2e_ms = []
@@ -331,7 +339,7 @@ def main():
 
     peaks, peak_kind = measured_peaks()
     if args.precision == "fp64":
-        flops = 2.0 * 3 * kk * kk * tree.list_len[0]  # near-field table applies, one launch
+        flops = 2.0 * 3 * kk * kk * tree.list_len[0] * nrhs  # near-field table applies per step
         achieved = flops / (stage_ms["near"] / 1e3) / 1e12
         peak = peaks["bf16_tflops"] * FP64_OVER_BF16
         roof = {"kernel": "near_gemm_kernel", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -339,7 +347,7 @@ def main():
                 "peak_source": "%s bf16 x nominal FP64/BF16 ratio (1.25/2250)" % peak_kind,
                 "flops_per_launch": flops, "ms_per_launch": stage_ms["near"]}
     else:
-        work = solve_work(tree, ops)
+        work = solve_work(tree, ops, nrhs)
         tc = work["near_tc_flops"]
         achieved = tc / (stage_ms["near"] / 1e3) / 1e12
         peak = peaks["bf16_tflops"]
@@ -373,9 +381,10 @@ def main():
     cpu = None
     errs = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        got = {args.precision: [o.cpu().numpy() for o in out]}
+        n1 = tree.n_leaves * kk  # the oracle checks the first right-hand side
+        got = {args.precision: [o.reshape(-1)[:n1].cpu().numpy() for o in out]}
         if out64 is not None:
-            got["fp64"] = [o.cpu().numpy() for o in out64]
+            got["fp64"] = [o.reshape(-1)[:n1].cpu().numpy() for o in out64]
         cpu, errs = cpu_baseline(wl, got)
 
     if rank == 0:
@@ -385,7 +394,8 @@ def main():
                 "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x8+f64",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "precision": args.precision, "n_leaves": tree.n_leaves,
-                           "n_boxes": tree.n_boxes, "depth": tree.depth, "n_targets": n_targets, "k": wl.k,
+                           "n_boxes": tree.n_boxes, "depth": tree.depth, "n_targets": n_targets, "nrhs": nrhs,
+                           "k": wl.k,
                            "p": wl.p, "tol": wl.tol, "u_list_len": tree.list_len[0],
                            "l2": "flushed between timed steps (256 MB write outside the events)",
                            "parallelism": "replicas" if world > 1 else "single GPU",

@@ -209,6 +209,49 @@ int vfmm_graph_create(const vfmm_tree* tree, const vfmm_ops* ops, const double* 
 int vfmm_graph_launch(const vfmm_graph* graph, void* stream);
 int vfmm_graph_destroy(vfmm_graph* graph);
 
+/* ---------------------------------------------------------------- batches of problems
+ * Many independent solves in one stream-ordered call (no counterpart in the paper, which
+ * solves one problem at a time). Each item is exactly one vfmm_volume_potential call:
+ * its own tree, operator set (shared between items is fine: read-only), nrhs, device
+ * buffers f/u/u_x/u_y laid out as for vfmm_volume_potential, and its own workspace (sized
+ * by vfmm_workspace_size; two items never share a workspace, since they may run at the
+ * same time). Buffers stay owned by the caller.
+ *
+ * A batch handle owns `n_streams` side streams (1..VFMM_BATCH_MAX_STREAMS) and events. A
+ * call forks the active side streams from `stream`, deals the items to them by estimated
+ * work (longest first, to the least loaded stream), and joins them back into `stream`, so
+ * the batch is ordered like one kernel on `stream` and independent items overlap on the
+ * GPU. One handle serves one host thread at a time. Errors: INVALID_ARG (null handle,
+ * item without tree or ops), and every error of vfmm_volume_potential (the first one
+ * stops the launches; streams are still joined). */
+#define VFMM_BATCH_MAX_STREAMS 64
+typedef struct vfmm_batch vfmm_batch;
+typedef struct {
+    const vfmm_tree* tree;
+    const vfmm_ops* ops;
+    int32_t nrhs;
+    const double* f;  /* device, [nrhs][n_leaves][k*k] */
+    double* u;        /* device, same layout */
+    double* ux;
+    double* uy;
+    void* workspace;  /* device, >= vfmm_workspace_size(tree, ops, nrhs, 0) bytes */
+    size_t workspace_bytes;
+} vfmm_batch_item;
+int vfmm_batch_create(int32_t n_streams, vfmm_batch** out);
+int vfmm_batch_destroy(vfmm_batch* batch);
+int vfmm_batch_potential(vfmm_batch* batch, int32_t n, const vfmm_batch_item* items, void* stream);
+/* The whole batch captured as one CUDA graph (replayed with vfmm_graph_launch, freed with
+ * vfmm_graph_destroy); runs the batch once before capturing and synchronises `stream`,
+ * which must not be the default stream. Item buffers must outlive the graph. */
+int vfmm_batch_graph_create(vfmm_batch* batch, int32_t n, const vfmm_batch_item* items, void* stream,
+                            vfmm_graph** out);
+/* Schedule autotuner: captures the batch with 1, 2, 4, ... (up to n_streams) side streams,
+ * times three graph replays of each with CUDA events on `stream`, keeps the fastest count
+ * as the handle's active one and returns it with its mean time in milliseconds. */
+int vfmm_batch_tune(vfmm_batch* batch, int32_t n, const vfmm_batch_item* items, void* stream,
+                    int32_t* best_streams, float* best_ms);
+int vfmm_batch_streams(const vfmm_batch* batch, int32_t* active);
+
 /* Work accounting for roofline reports, for a call with nrhs right-hand sides: out[VFMM_N_WORK] =
  * [0] BF16 tensor-core FLOPs the near-field contraction issues per call (VFMM_MIXED: every
  *     slice product of every tile, zero-padded rows included; 0 for VFMM_FP64),

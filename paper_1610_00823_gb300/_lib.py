@@ -27,6 +27,12 @@ class TreeInfo(ctypes.Structure):
                 ("min_margin", ctypes.c_double)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("tree", ctypes.c_void_p), ("ops", ctypes.c_void_p), ("nrhs", ctypes.c_int32),
+                ("f", ctypes.c_void_p), ("u", ctypes.c_void_p), ("ux", ctypes.c_void_p), ("uy", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
 EXPORTS = {
     "vfmm_tree_build": [ctypes.POINTER(TreeParams), ctypes.POINTER(Source), ctypes.c_void_p,
                         ctypes.POINTER(ctypes.c_void_p)],
@@ -62,6 +68,14 @@ EXPORTS = {
                           ctypes.POINTER(ctypes.c_void_p)],
     "vfmm_graph_launch": [ctypes.c_void_p, ctypes.c_void_p],
     "vfmm_graph_destroy": [ctypes.c_void_p],
+    "vfmm_batch_create": [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
+    "vfmm_batch_destroy": [ctypes.c_void_p],
+    "vfmm_batch_potential": [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(BatchItem), ctypes.c_void_p],
+    "vfmm_batch_graph_create": [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(BatchItem), ctypes.c_void_p,
+                                ctypes.POINTER(ctypes.c_void_p)],
+    "vfmm_batch_tune": [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(BatchItem), ctypes.c_void_p,
+                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)],
+    "vfmm_batch_streams": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)],
     "vfmm_strerror": [ctypes.c_int],
     "vfmm_last_error_detail": [],
 }

@@ -260,3 +260,79 @@ class SolveGraph:
             except Exception:
                 pass
             self._h = None
+
+
+class Batch:
+    """Many independent solves per call (vfmm_batch_*): items are (tree, ops, f, out, ws) tuples with
+    f and out[q] cuda float64 tensors laid out as for volume_potential and ws from workspace()."""
+
+    def __init__(self, n_streams: int = 16):
+        self._h = ctypes.c_void_p()
+        call("vfmm_batch_create", int(n_streams), ctypes.byref(self._h))
+
+    @staticmethod
+    def _items(items):
+        arr = (_lib.BatchItem * len(items))()
+        for i, (tree, ops, f, out, ws) in enumerate(items):
+            n = tree.n_leaves * tree.k * tree.k
+            if f.numel() % n or any(o.numel() != f.numel() for o in out):
+                raise ValueError("item %d: f/out sizes do not match the tree" % i)
+            arr[i] = _lib.BatchItem(tree.handle.value if hasattr(tree.handle, "value") else tree.handle,
+                                    ops.handle.value if hasattr(ops.handle, "value") else ops.handle,
+                                    f.numel() // n, f.data_ptr(), out[0].data_ptr(), out[1].data_ptr(),
+                                    out[2].data_ptr(), ws.data_ptr(), ws.numel())
+        return arr
+
+    def potential(self, items, stream=None):
+        arr = self._items(items)
+        call("vfmm_batch_potential", self._h, len(items), arr, _stream(stream))
+
+    def graph(self, items, stream):
+        """The whole batch captured as one CUDA graph (a Graph; keeps the items alive)."""
+        arr = self._items(items)
+        h = ctypes.c_void_p()
+        call("vfmm_batch_graph_create", self._h, len(items), arr, _stream(stream), ctypes.byref(h))
+        return Graph(h, keep=(self, items))
+
+    def tune(self, items, stream):
+        """Picks the number of side streams by timing graph replays; returns (streams, ms)."""
+        arr = self._items(items)
+        s = ctypes.c_int32()
+        ms = ctypes.c_float()
+        call("vfmm_batch_tune", self._h, len(items), arr, _stream(stream), ctypes.byref(s), ctypes.byref(ms))
+        return int(s.value), float(ms.value)
+
+    @property
+    def streams(self) -> int:
+        s = ctypes.c_int32()
+        call("vfmm_batch_streams", self._h, ctypes.byref(s))
+        return int(s.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                _lib.load().vfmm_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+class Graph:
+    """An instantiated CUDA graph returned by the library (replay with launch)."""
+
+    def __init__(self, handle, keep=None):
+        self._h = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        call("vfmm_graph_launch", self._h, _stream(stream))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                _lib.load().vfmm_graph_destroy(h)
+            except Exception:
+                pass
+            self._h = None

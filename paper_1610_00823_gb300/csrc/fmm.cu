@@ -913,11 +913,6 @@ extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_
     return rc;
 }
 
-struct vfmm_graph {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
-
 extern "C" int vfmm_graph_create(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
                                  double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
                                  size_t workspace_bytes, void* stream, vfmm_graph** out) {

@@ -227,3 +227,9 @@ int build_near_tiles(DeviceTree* t);
 struct vfmm_tree {
     vfmm::DeviceTree t;
 };
+
+// A captured, instantiated CUDA graph (one solve, or one batch of solves).
+struct vfmm_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};

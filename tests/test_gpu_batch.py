@@ -1,0 +1,74 @@
+"""Batch driver (many independent problems per call, one CUDA graph): every member's result
+equals its own single call bit for bit (same kernels, same inputs, only the stream differs),
+for both forms, mixed k, and a member with several right-hand sides."""
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1610_00823_gb300 as v  # noqa: E402
+from paper_1610_00823_gb300.api import Batch, workspace  # noqa: E402
+
+
+def _members(precision):
+    mem = W.batch_members(10)
+    ops = {k: v.ops_create(k, 20 if k == 8 else 40, precision) for k in (8, 16)}
+    items, refs = [], []
+    for i, m in enumerate(mem):
+        k = m["k"]
+        tol = (1e-6, 1e-9, 1e-12)[i % 3]
+        tree = v.tree_build(0.0, 0.0, 1.0, k, m["source"], tol, 16)
+        f = v.source_sample(tree, m["source"])
+        if i == 3:  # two right-hand sides on one member
+            f = torch.stack([f, 0.5 * f * f]).contiguous()
+        ref = v.volume_potential(tree, ops[k], f)
+        out = tuple(torch.full_like(f, float("nan")) for _ in range(3))
+        items.append((tree, ops[k], f, out, workspace(tree, ops[k], f.numel() // (tree.n_leaves * k * k))))
+        refs.append(ref)
+    return items, refs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_graph_equals_single_calls(precision):
+    items, refs = _members(v.MIXED if precision == "mixed" else v.FP64)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    b = Batch(8)
+    b.potential(items, stream)
+    stream.synchronize()
+    for (tree, ops, f, out, ws), ref in zip(items, refs):
+        for q in range(3):
+            assert torch.equal(out[q], ref[q])
+    g = b.graph(items, stream)
+    for _ in range(2):
+        for it in items:
+            for o in it[3]:
+                o.fill_(float("nan"))
+        torch.cuda.synchronize()
+        g.launch(stream)
+        stream.synchronize()
+        for (tree, ops, f, out, ws), ref in zip(items, refs):
+            for q in range(3):
+                assert torch.equal(out[q], ref[q])
+
+
+def test_batch_tune_picks_a_stream_count():
+    items, refs = _members(v.MIXED)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    b = Batch(8)
+    s, ms = b.tune(items, stream)
+    assert s in (1, 2, 4, 8) and ms > 0.0 and b.streams == s
+    for it in items:
+        for o in it[3]:
+            o.fill_(float("nan"))
+    b.potential(items, stream)
+    stream.synchronize()
+    for (tree, ops, f, out, ws), ref in zip(items, refs):
+        for q in range(3):
+            assert torch.equal(out[q], ref[q])
