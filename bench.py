@@ -200,6 +200,194 @@ def cpu_baseline(wl, gpu_u, budget_s=15.0):
                       % (len(leaves), ot.n_leaves, len(leaves) * kk, dt, setup_s)}, errs
 
 
+# ----------------------------------------------------------------------------- batched problems
+def batch_workloads(n):
+    """Member i of the uneven batch: 3 Gaussians, leaf target N_i, k_i (workloads.batch_members),
+    tree by the greedy leaf-count rule on the unit box, max depth 16."""
+    out = []
+    for m in W.batch_members(n):
+        wl = W.Workload("batch_member_k%d_n%d" % (m["k"], m["n_leaves_target"]), 0.0, 0.0, 1.0, m["k"], m["p"],
+                        0.0, 16, 0, -1, [m["source"]])
+        out.append((wl, m["n_leaves_target"]))
+    return out
+
+
+def run_batch(args):
+    """Config 'batchN': N independent uneven problems in one CUDA graph (mixed form), the same batch in
+    the FP64 form beside it. The reference arm times the oracle on the smallest members."""
+    n_members = int(args.workload[len("batch"):] or 256)
+    members = batch_workloads(n_members)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    name = "batch%d_uneven_gauss3" % n_members
+    if args.impl == "reference":
+        if rank == 0:
+            from oracle import fmm, tables
+            from oracle import tree as T
+            wl, n_t = min(members, key=lambda x: x[1])
+            src = wl.sources[0]
+            ot = T.build_greedy(0.0, 0.0, 1.0, wl.k, src, n_t, 16)
+            L, ops, F = T.build_lists(ot), tables.Ops(wl.k, wl.p), ot.sample(src)
+            times = []
+            for i in range(args.warmup + args.steps):
+                t0 = time.perf_counter()
+                fmm.solve(ot, L, ops, F)
+                if i >= args.warmup:
+                    times.append(time.perf_counter() - t0)
+            ms = 1e3 * statistics.mean(times)
+            value = ot.n_leaves * wl.k * wl.k / (ms / 1e3)
+            sample = "the smallest member (%d leaves, k = %d) solved whole per step" % (ot.n_leaves, wl.k)
+            print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                              "data": "synthetic", "config": {"workload": name, "parallelism": "replicas"},
+                              "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                               "sample": sample},
+                              "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                      "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1610_00823_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_1610_00823_gb300 import build as b
+        b.build()
+    import paper_1610_00823_gb300 as v
+    from paper_1610_00823_gb300.api import Batch, solve_work, volume_potential_profiled, workspace
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    trees, fs = [], []
+    for wl, n_t in members:
+        tree = v.tree_build_leaves(0.0, 0.0, 1.0, wl.k, wl.sources[0], n_t, 16)
+        trees.append(tree)
+        fs.append(v.source_sample(tree, wl.sources[0]))
+    torch.cuda.synchronize()
+    t_tree = time.perf_counter() - t0
+    n_targets = sum(f.numel() for f in fs)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make_items(precision):
+        ops = {k: v.ops_create(k, 20 if k == 8 else 40, precision) for k in sorted({wl.k for wl, _ in members})}
+        items = []
+        for (wl, _), tree, f in zip(members, trees, fs):
+            out = tuple(torch.empty_like(f) for _ in range(3))
+            items.append((tree, ops[wl.k], f, out, workspace(tree, ops[wl.k], 1)))
+        return ops, items
+
+    def time_graph(items, steps, clk=None, streams=None):
+        b = Batch(16)
+        if streams is None:
+            tuned = b.tune(items, stream)  # schedule autotuner: side-stream count by timed graph replays
+        else:
+            b = Batch(streams)
+            tuned = (streams, None)
+        g = b.graph(items, stream)
+        for _ in range(args.warmup):
+            g.launch(stream)
+        torch.cuda.synchronize()
+        times = []
+        if clk is not None:
+            clk.start()
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.launch(stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        if clk is not None:
+            clk.stop()
+        return statistics.mean(times), tuned, b, g
+
+    t0 = time.perf_counter()
+    ops_mx, items_mx = make_items(v.MIXED)
+    torch.cuda.synchronize()
+    t_ops = time.perf_counter() - t0
+    clk = ClockSampler(local)
+    ms, tuned, b, g = time_graph(items_mx, args.steps, clk)
+    value = n_targets / (ms / 1e3)
+    # near-field roofline: executed tensor flops over every member's near stage (profiled solves)
+    tc, near_ms, launches = 0.0, 0.0, 0
+    for tree, ops, f, out, ws in items_mx:
+        stages, nl = volume_potential_profiled(tree, ops, f, out, ws, stream=stream)
+        tc += solve_work(tree, ops)["near_tc_flops"]
+        near_ms += stages["near"]
+        launches += nl
+    peaks, peak_kind = measured_peaks()
+    achieved = tc / (near_ms / 1e3) / 1e12
+    roof = {"kernel": "split_gemm_kernel (near field, split-BF16 tcgen05), summed over members",
+            "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / peaks["bf16_tflops"], "traffic": None, "peak_source": "%s bf16 burst" % peak_kind,
+            "flops_per_launch": tc / n_members, "ms_per_launch": near_ms / n_members,
+            "note": "members profiled one at a time, outside the batch graph"}
+    # end to end: pinned host f in, u/u_x/u_y out, the batch graph between (copies on the same stream)
+    hosts = [(f.cpu().pin_memory(), tuple(torch.empty(f.shape, dtype=f.dtype).pin_memory() for _ in range(3)))
+             for f in fs]
+    e2e = []
+    for _ in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (fh, _), (tree, ops, f, out, ws) in zip(hosts, items_mx):
+            f.copy_(fh, non_blocking=True)
+        g.launch(stream)
+        for (_, oh), (tree, ops, f, out, ws) in zip(hosts, items_mx):
+            for q in range(3):
+                oh[q].copy_(out[q], non_blocking=True)
+        stream.synchronize()
+        e2e.append(1e3 * (time.perf_counter() - t0))
+    res_mx = [tuple(o.clone() for o in it[3]) for it in items_mx]
+    del g, b
+    fp64 = None
+    if not args.no_fp64_compare:
+        ops64, items64 = make_items(v.FP64)
+        ms64, tuned64, b64, g64 = time_graph(items64, 3, streams=tuned[0])
+        err = [0.0, 0.0, 0.0]
+        for rm, it in zip(res_mx, items64):
+            for q in range(3):
+                d = torch.max(torch.abs(rm[q] - it[3][q])).item() / max(torch.max(torch.abs(it[3][q])).item(), 1e-300)
+                err[q] = max(err[q], d)
+        fp64 = {"value": n_targets / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "streams": tuned64[0],
+                "mixed_over_fp64_speedup": ms64 / ms, "max_member_rel_diff_mixed_vs_fp64": err}
+        del g64, b64, items64
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import fmm, tables
+        from oracle import tree as T
+        i_small = min(range(n_members), key=lambda i: members[i][1])
+        wl, n_t = members[i_small]
+        ot = T.build_greedy(0.0, 0.0, 1.0, wl.k, wl.sources[0], n_t, 16)
+        L, ops_o, F = T.build_lists(ot), tables.Ops(wl.k, wl.p), ot.sample(wl.sources[0])
+        t0 = time.perf_counter()
+        ref = fmm.solve(ot, L, ops_o, F)
+        dt = time.perf_counter() - t0
+        got = [res_mx[i_small][q].cpu().numpy().reshape(ref[q].shape) for q in range(3)]
+        cpu = {"value": ot.n_leaves * wl.k * wl.k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "member %d (%d leaves, k = %d) solved whole, %.1f s" % (i_small, ot.n_leaves, wl.k, dt),
+               "rel_err_member_vs_oracle": [float(np.max(np.abs(got[q] - ref[q])) / np.max(np.abs(ref[q])))
+                                            for q in range(3)]}
+    if rank == 0:
+        n_leaves = sum(t.n_leaves for t in trees)
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x8+f64", "data": "synthetic",
+            "config": {"workload": name, "members": n_members, "n_leaves": n_leaves, "n_targets": n_targets,
+                       "k_mix": {str(k): sum(1 for wl, _ in members if wl.k == k) for k in (8, 16)},
+                       "leaf_targets": [min(n for _, n in members), max(n for _, n in members)],
+                       "streams": tuned[0], "tune_ms": tuned[1], "launch": "one CUDA graph (all members)",
+                       "l2": "flushed between timed steps (256 MB write outside the events)",
+                       "parallelism": "single GPU", "tree_build_s": t_tree, "ops_create_s": t_ops},
+            "roofline": roof, "cpu_baseline": cpu, "fp64_form": fp64,
+            "e2e": {"value": n_targets / (statistics.mean(e2e) / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": n_targets * 8, "d2h_bytes_per_step": 3 * n_targets * 8,
+                    "ms_per_step": statistics.mean(e2e)},
+            "gpu_launches": launches, "clocks": clk.summary()}), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -216,6 +404,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.workload.startswith("batch"):
+        return run_batch(args)
     wl = workload(args.workload)
 
     rank = int(os.environ.get("RANK", "0"))

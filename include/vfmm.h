@@ -107,6 +107,20 @@ typedef struct {
  * OOM, CUDA. */
 int vfmm_tree_build(const vfmm_tree_params* prm, const vfmm_source* src, void* stream, vfmm_tree** out);
 
+/* Tree with a leaf-count target (for batches of uneven problems; the paper refines to a
+ * tolerance only): starting from the root, the leaf of highest priority is split, one at a
+ * time, until the tree has >= n_leaves leaves or no leaf below prm->max_depth is left; then
+ * the same level restriction, numbering and lists as vfmm_tree_build. Priority of a leaf =
+ * the binary exponent e of its tail (the same trailing-coefficient test quantity, tail in
+ * [2^(e-1), 2^e)), raised to at least e_F - 30 where F = max |f| as for vfmm_tree_build
+ * (tails near rounding level all tie); ties go to the coarser leaf, then the smaller Morton
+ * key. The queue is kept on the host; tails are computed on the device in batches.
+ * tree_info.min_margin = smallest relative distance of a deciding tail to a power of two.
+ * prm->tol and prm->min_depth are ignored. Synchronises `stream`.
+ * Errors: INVALID_ARG (bad k, max_depth, width, n_leaves outside [1, 2^26], source), OOM, CUDA. */
+int vfmm_tree_build_leaves(const vfmm_tree_params* prm, const vfmm_source* src, int64_t n_leaves, void* stream,
+                           vfmm_tree** out);
+
 /* Uniform tree of the given depth (prm->tol and depths ignored). Synchronises. */
 int vfmm_tree_build_uniform(const vfmm_tree_params* prm, int32_t depth, void* stream, vfmm_tree** out);
 

@@ -240,6 +240,62 @@ def build_adaptive(cx, cy, width, k, src, tol, max_depth, min_depth=0, return_in
     return tree
 
 
+def build_greedy(cx, cy, width, k, src, n_leaves, max_depth=16, return_info=False):
+    """Leaf-count target for batches of uneven problems (the paper refines to a tolerance only).
+
+    One split at a time: the leaf of highest priority is split until the tree has at least
+    n_leaves leaves or no leaf below max_depth remains; then balance() as for the tolerance
+    rule. Priority = binary exponent e of the leaf's tail (the tolerance rule's quantity, with
+    tail in [2^(e-1), 2^e)), raised to at least e_F - 30 (F = f_scale = m 2^e_F, m in [0.5, 1)),
+    so that tails near rounding level all tie; ties: coarser level first, then smaller Morton key.
+    info["min_margin"]: smallest relative distance of a deciding tail to a power of two.
+    """
+    import heapq
+    import math
+    C = cheb.values_to_coeffs_matrix(k)
+    F = f_scale(cx, cy, width, k, src, max_depth)
+    e_floor = (math.frexp(F)[1] if F > 0 else 0) - 30
+    margin = [float("inf")]
+
+    def tails(boxes):
+        arr = np.array(boxes, dtype=np.int64)
+        X, Y = node_coords(cx, cy, width, k, arr[:, 0], arr[:, 1], arr[:, 2])
+        return cheb.tail(srcmod.evaluate_source(src, X, Y).reshape(-1, k, k), k, C)
+
+    def priority(t):
+        e = e_floor
+        if t > 0:
+            e = math.frexp(t)[1]
+            if e >= e_floor:
+                lo, hi = math.ldexp(1.0, e - 1), math.ldexp(1.0, e)
+                margin[0] = min(margin[0], t / lo - 1.0, 1.0 - t / hi)
+        return max(e, e_floor)
+
+    def entry(box, t):
+        l, a, b = box
+        return (-priority(float(t)), l, int(morton(np.array([a]), np.array([b]))[0]), box)
+
+    root = (0, 0, 0)
+    heap = [entry(root, tails([root])[0])] if max_depth > 0 else []
+    boxes = {root}
+    n = 1
+    while n < n_leaves and heap:
+        _, l, _, box = heapq.heappop(heap)
+        kids = _children([box])
+        tk = tails(kids)
+        boxes.update(kids)
+        n += 3
+        for kid, t in zip(kids, tk):
+            e = entry(kid, t)  # every child's tail decides a priority (also at max_depth)
+            if l + 1 < max_depth:
+                heapq.heappush(heap, e)
+    refined = set(boxes)
+    tree = Tree(cx, cy, width, k, balance(refined))
+    if return_info:
+        return tree, {"F": F, "min_margin": margin[0], "refined": refined}
+    return tree
+
+
 # ----------------------------------------------------------------------------- lists
 
 NEAR_PATTERN = sorted([(sx * a, sy * b) for (a, b) in ((3, 1), (1, 3), (3, 3))

@@ -36,6 +36,8 @@ class BatchItem(ctypes.Structure):
 EXPORTS = {
     "vfmm_tree_build": [ctypes.POINTER(TreeParams), ctypes.POINTER(Source), ctypes.c_void_p,
                         ctypes.POINTER(ctypes.c_void_p)],
+    "vfmm_tree_build_leaves": [ctypes.POINTER(TreeParams), ctypes.POINTER(Source), ctypes.c_int64, ctypes.c_void_p,
+                               ctypes.POINTER(ctypes.c_void_p)],
     "vfmm_tree_build_uniform": [ctypes.POINTER(TreeParams), ctypes.c_int32, ctypes.c_void_p,
                                 ctypes.POINTER(ctypes.c_void_p)],
     "vfmm_tree_info": [ctypes.c_void_p, ctypes.POINTER(TreeInfo)],

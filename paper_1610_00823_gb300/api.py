@@ -91,6 +91,16 @@ def tree_build(cx, cy, width, k, source, tol, max_depth, min_depth=0, stream=Non
     return Tree(h, k)
 
 
+def tree_build_leaves(cx, cy, width, k, source, n_leaves, max_depth=16, stream=None) -> Tree:
+    """Greedy refinement to at least n_leaves leaves (then balanced); see vfmm_tree_build_leaves."""
+    prm = _lib.TreeParams(cx, cy, width, k, max_depth, 0, 0.0)
+    s, keep = _source(source)
+    h = ctypes.c_void_p()
+    call("vfmm_tree_build_leaves", ctypes.byref(prm), ctypes.byref(s), int(n_leaves), _stream(stream), ctypes.byref(h))
+    del keep
+    return Tree(h, k)
+
+
 def tree_build_uniform(cx, cy, width, k, depth, stream=None) -> Tree:
     prm = _lib.TreeParams(cx, cy, width, k, depth, depth, 0.0)
     h = ctypes.c_void_p()

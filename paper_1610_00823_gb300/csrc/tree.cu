@@ -16,8 +16,12 @@
 //   5. U/V/W/X lists: one thread per box, neighbour lookups by binary search in the
 //      Morton-sorted key array of a level, a count pass and a fill pass.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
+#include <set>
+#include <tuple>
+#include <unordered_map>
 
 #include "mixed.cuh"
 #include "source.cuh"
@@ -170,20 +174,17 @@ __global__ void fscale_kernel(NodeGeom g, SourceDev src, int level, double* fmax
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(fmax_out, m);
 }
 
-// One CTA per candidate box, blockDim = k*k rounded up to a multiple of 32.
-// C[m*k + i] = (2 - delta_m0)/k T_m(t_i).
-__global__ void refine_kernel(NodeGeom g, SourceDev src, int level, const uint32_t* __restrict__ keys, int n,
-                              const double* __restrict__ C, double thresh, int32_t* __restrict__ flags,
-                              double* __restrict__ min_margin) {
-    __shared__ double V[16 * 16];
-    __shared__ double Tm[16 * 16];
-    __shared__ double red[8];
-    const int b = blockIdx.x;
+// Largest trailing Chebyshev coefficient (last two rows and columns) of the k x k interpolant of
+// f on the box (level, key): values -> coefficients as c = C V C^T with
+// C[m*k + i] = (2 - delta_m0)/k T_m(t_i). Called by a whole CTA (blockDim = k*k rounded up to
+// a multiple of 32); the result is valid in thread 0. V and Tm hold k*k doubles, red 8.
+__device__ double box_tail(const NodeGeom& g, const SourceDev& src, int level, uint32_t key,
+                           const double* __restrict__ C, double* V, double* Tm, double* red) {
     const int k = g.k;
     const int t = threadIdx.x;
     const bool active = t < k * k;
     int ix, iy;
-    morton_decode(keys[b], &ix, &iy);
+    morton_decode(key, &ix, &iy);
     const double h = ldexp(g.width, -level);
     const int i = t % k, j = t / k;
     if (active)
@@ -207,12 +208,37 @@ __global__ void refine_kernel(NodeGeom g, SourceDev src, int level, const uint32
     const int nw = blockDim.x / 32;
     if ((t & 31) == 0) red[t >> 5] = tail;
     __syncthreads();
-    if (t == 0 && b < n) {
-        double mx = 0.0;
+    double mx = 0.0;
+    if (t == 0)
         for (int w = 0; w < nw; ++w) mx = fmax(mx, red[w]);
+    return mx;
+}
+
+// One CTA per candidate box of one level: split flag = tail > thresh.
+__global__ void refine_kernel(NodeGeom g, SourceDev src, int level, const uint32_t* __restrict__ keys, int n,
+                              const double* __restrict__ C, double thresh, int32_t* __restrict__ flags,
+                              double* __restrict__ min_margin) {
+    __shared__ double V[16 * 16];
+    __shared__ double Tm[16 * 16];
+    __shared__ double red[8];
+    const int b = blockIdx.x;
+    const double mx = box_tail(g, src, level, keys[b], C, V, Tm, red);
+    if (threadIdx.x == 0 && b < n) {
         flags[b] = mx > thresh ? 1 : 0;
         if (thresh > 0.0) atomic_min_nonneg(min_margin, fabs(mx / thresh - 1.0));
     }
+}
+
+// One CTA per box of a list with per-box levels: tails[b] = box_tail.
+__global__ void tail_kernel(NodeGeom g, SourceDev src, const int32_t* __restrict__ lev,
+                            const uint32_t* __restrict__ keys, int n, const double* __restrict__ C,
+                            double* __restrict__ tails) {
+    __shared__ double V[16 * 16];
+    __shared__ double Tm[16 * 16];
+    __shared__ double red[8];
+    const int b = blockIdx.x;
+    const double mx = box_tail(g, src, lev[b], keys[b], C, V, Tm, red);
+    if (threadIdx.x == 0 && b < n) tails[b] = mx;
 }
 
 __global__ void fill_kernel(int32_t* a, int64_t n, int32_t v) {
@@ -571,9 +597,102 @@ static int compute_lists(DeviceTree* T, cudaStream_t st) {
     return build_near_tiles(T);
 }
 
-// Builds the tree. src == nullptr means a uniform tree of depth `uniform_depth`.
-static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_depth, cudaStream_t st,
-                 DeviceTree* T) {
+// Greedy refinement to a leaf count (no counterpart in the paper, which refines to a
+// tolerance): starting from the root, the leaf of highest priority is split, one at a time,
+// until there are at least n_target leaves (before balancing) or no leaf above max_depth is
+// left. Priority = the binary exponent e of the leaf's tail (tail in [2^(e-1), 2^e)), raised to
+// at least e_F - 30 (F = 2^e_F m, m in [0.5, 1)) so that tails near rounding level all tie; ties
+// go to the coarser leaf, then the smaller Morton key. The host keeps the priority queue and
+// asks the device for the tails of the children of the leaves most likely to be split next,
+// in batches, so the order of splits is exactly the one-at-a-time order.
+// lv[l] = sorted keys of every box of level l; *min_margin = smallest relative distance of a
+// tail that decided a priority to the nearest power of two.
+static int greedy_refine(const BuildCtx& B, const SourceDev& src, int max_depth, int64_t n_target, double F,
+                         std::vector<std::vector<uint32_t>>& lv, double* min_margin) {
+    typedef std::tuple<int, int, uint32_t> Item;  // (-priority, level, key): std::set begins with the next split
+    int eF = 0;
+    if (F > 0.0) std::frexp(F, &eF);
+    const int e_floor = eF - 30;
+    auto priority = [&](double t, double* margin) {
+        int e = e_floor;
+        if (t > 0.0) {
+            std::frexp(t, &e);
+            if (e >= e_floor) {
+                const double lo = std::ldexp(1.0, e - 1), hi = std::ldexp(1.0, e);
+                *margin = std::min(*margin, std::min(t / lo - 1.0, 1.0 - t / hi));
+            }
+        }
+        return std::max(e, e_floor);
+    };
+    auto id = [](int level, uint32_t key) { return ((uint64_t)level << 32) | key; };
+    std::unordered_map<uint64_t, std::array<double, 4>> kid_tails;
+    const int threads = ((B.g.k * B.g.k + 31) / 32) * 32;
+    auto compute = [&](const std::vector<int32_t>& lev, const std::vector<uint32_t>& key, std::vector<double>& out) {
+        const int n = (int)key.size();
+        DBuf<int32_t> dl;
+        DBuf<uint32_t> dk;
+        DBuf<double> dt;
+        VFMM_CHECK(dl.alloc(n));
+        VFMM_CHECK(dk.alloc(n));
+        VFMM_CHECK(dt.alloc(n));
+        VFMM_CUDA(cudaMemcpyAsync(dl.p, lev.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, B.st));
+        VFMM_CUDA(cudaMemcpyAsync(dk.p, key.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, B.st));
+        tail_kernel<<<(unsigned)n, threads, 0, B.st>>>(B.g, src, dl.p, dk.p, n, B.C.p, dt.p);
+        VFMM_CUDA(cudaGetLastError());
+        out.resize(n);
+        VFMM_CUDA(cudaMemcpyAsync(out.data(), dt.p, n * sizeof(double), cudaMemcpyDeviceToHost, B.st));
+        VFMM_CUDA(cudaStreamSynchronize(B.st));
+        return VFMM_OK;
+    };
+    lv.assign(1, std::vector<uint32_t>{0u});
+    std::vector<double> tails;
+    VFMM_CHECK(compute({0}, {0u}, tails));
+    std::set<Item> frontier;
+    if (max_depth > 0) frontier.insert(Item(-priority(tails[0], min_margin), 0, 0u));
+    int64_t n_leaves = 1;
+    while (n_leaves < n_target && !frontier.empty()) {
+        const Item top = *frontier.begin();
+        if (!kid_tails.count(id(std::get<1>(top), std::get<2>(top)))) {
+            // children of the next leaves in queue order whose children are not known yet
+            const int64_t want = std::max<int64_t>(64, (n_target - n_leaves + 2) / 3);
+            std::vector<int32_t> lev;
+            std::vector<uint32_t> key;
+            std::vector<uint64_t> parents;
+            for (auto it = frontier.begin(); it != frontier.end() && (int64_t)parents.size() < want; ++it) {
+                const int l = std::get<1>(*it);
+                const uint32_t kp = std::get<2>(*it);
+                if (kid_tails.count(id(l, kp))) continue;
+                parents.push_back(id(l, kp));
+                for (uint32_t c = 0; c < 4; ++c) {
+                    lev.push_back(l + 1);
+                    key.push_back((kp << 2) | c);
+                }
+            }
+            VFMM_CHECK(compute(lev, key, tails));
+            for (size_t q = 0; q < parents.size(); ++q)
+                kid_tails[parents[q]] = {tails[4 * q], tails[4 * q + 1], tails[4 * q + 2], tails[4 * q + 3]};
+        }
+        frontier.erase(frontier.begin());
+        const int l = std::get<1>(top);
+        const uint32_t kp = std::get<2>(top);
+        const std::array<double, 4> kt = kid_tails[id(l, kp)];
+        if ((int)lv.size() < l + 2) lv.emplace_back();
+        for (uint32_t c = 0; c < 4; ++c) {
+            const uint32_t kc = (kp << 2) | c;
+            lv[l + 1].push_back(kc);
+            const int pr = priority(kt[c], min_margin);
+            if (l + 1 < max_depth) frontier.insert(Item(-pr, l + 1, kc));
+        }
+        n_leaves += 3;
+    }
+    for (auto& v : lv) std::sort(v.begin(), v.end());
+    return VFMM_OK;
+}
+
+// Builds the tree. src == nullptr means a uniform tree of depth `uniform_depth`; leaf_target > 0
+// selects the greedy leaf-count refinement instead of the tolerance test.
+static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_depth, int64_t leaf_target,
+                 cudaStream_t st, DeviceTree* T) {
     const int k = prm->k;
     BuildCtx B;
     B.st = st;
@@ -604,37 +723,50 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
 
     std::vector<DBuf<uint32_t>> keys(max_depth + 1);
     std::vector<int64_t> cnt(max_depth + 1, 0);
-    VFMM_CHECK(keys[0].alloc(1));
-    uint32_t zero = 0;
-    VFMM_CUDA(cudaMemcpyAsync(keys[0].p, &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    cnt[0] = 1;
     int depth = 0;
-    for (int l = 0; l < max_depth; ++l) {
-        const int64_t n = cnt[l];
-        DBuf<int32_t> flags, offs;
-        VFMM_CHECK(flags.alloc(n));
-        VFMM_CHECK(offs.alloc(n));
-        if (l < min_depth) {
-            fill_kernel<<<nblk(n), 256, 0, st>>>(flags.p, n, 1);
-        } else {
-            refine_kernel<<<(unsigned)n, ((k * k + 31) / 32) * 32, 0, st>>>(B.g, *src, l, keys[l].p, (int)n, B.C.p, thresh, flags.p,
-                                                         scal.p + 1);
+    if (leaf_target > 0) {
+        std::vector<std::vector<uint32_t>> lv;
+        double mm = INFINITY;
+        VFMM_CHECK(greedy_refine(B, *src, max_depth, leaf_target, T->f_scale, lv, &mm));
+        depth = (int)lv.size() - 1;
+        for (int l = 0; l <= depth; ++l) {
+            cnt[l] = (int64_t)lv[l].size();
+            VFMM_CHECK(keys[l].alloc(cnt[l]));
+            VFMM_CUDA(cudaMemcpy(keys[l].p, lv[l].data(), cnt[l] * sizeof(uint32_t), cudaMemcpyHostToDevice));
         }
-        VFMM_CUDA(cudaGetLastError());
-        int64_t m = 0;
-        VFMM_CHECK(exclusive_scan(flags.p, offs.p, n, &m, st));
-        if (m == 0) break;
-        VFMM_CHECK(keys[l + 1].alloc(4 * m));
-        emit_children_kernel<<<nblk(n), 256, 0, st>>>(keys[l].p, flags.p, offs.p, (int)n, keys[l + 1].p);
-        VFMM_CUDA(cudaGetLastError());
-        cnt[l + 1] = 4 * m;
-        depth = l + 1;
-    }
-    if (!uniform) {
-        double mm = 0;
-        VFMM_CUDA(cudaMemcpyAsync(&mm, scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
-        VFMM_CUDA(cudaStreamSynchronize(st));
         T->min_margin = mm;
+    } else {
+        VFMM_CHECK(keys[0].alloc(1));
+        uint32_t zero = 0;
+        VFMM_CUDA(cudaMemcpyAsync(keys[0].p, &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        cnt[0] = 1;
+        for (int l = 0; l < max_depth; ++l) {
+            const int64_t n = cnt[l];
+            DBuf<int32_t> flags, offs;
+            VFMM_CHECK(flags.alloc(n));
+            VFMM_CHECK(offs.alloc(n));
+            if (l < min_depth) {
+                fill_kernel<<<nblk(n), 256, 0, st>>>(flags.p, n, 1);
+            } else {
+                refine_kernel<<<(unsigned)n, ((k * k + 31) / 32) * 32, 0, st>>>(B.g, *src, l, keys[l].p, (int)n, B.C.p, thresh, flags.p,
+                                                             scal.p + 1);
+            }
+            VFMM_CUDA(cudaGetLastError());
+            int64_t m = 0;
+            VFMM_CHECK(exclusive_scan(flags.p, offs.p, n, &m, st));
+            if (m == 0) break;
+            VFMM_CHECK(keys[l + 1].alloc(4 * m));
+            emit_children_kernel<<<nblk(n), 256, 0, st>>>(keys[l].p, flags.p, offs.p, (int)n, keys[l + 1].p);
+            VFMM_CUDA(cudaGetLastError());
+            cnt[l + 1] = 4 * m;
+            depth = l + 1;
+        }
+        if (!uniform) {
+            double mm = 0;
+            VFMM_CUDA(cudaMemcpyAsync(&mm, scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+            VFMM_CUDA(cudaStreamSynchronize(st));
+            T->min_margin = mm;
+        }
     }
 
     // level restriction, finest level first
@@ -827,7 +959,29 @@ extern "C" int vfmm_tree_build(const vfmm_tree_params* prm, const vfmm_source* s
     SourceDev sd;
     VFMM_CHECK(make_source(src, pbuf, &sd, st));
     vfmm_tree* t = new vfmm_tree();
-    int r = build(prm, &sd, 0, st, &t->t);
+    int r = build(prm, &sd, 0, 0, st, &t->t);
+    if (r != VFMM_OK) {
+        free_tree(&t->t);
+        delete t;
+        return r;
+    }
+    *out = t;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_build_leaves(const vfmm_tree_params* prm, const vfmm_source* src, int64_t n_leaves,
+                                      void* stream, vfmm_tree** out) {
+    if (!out) return fail(VFMM_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    VFMM_CHECK(check_params(prm));
+    if (prm->max_depth < 0 || prm->max_depth > kMaxDepth) return fail(VFMM_ERR_INVALID_ARG, "need 0 <= max_depth <= 16");
+    if (n_leaves < 1 || n_leaves > (1ll << 26)) return fail(VFMM_ERR_INVALID_ARG, "n_leaves must be in [1, 2^26]");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBuf<double> pbuf;
+    SourceDev sd;
+    VFMM_CHECK(make_source(src, pbuf, &sd, st));
+    vfmm_tree* t = new vfmm_tree();
+    int r = build(prm, &sd, 0, n_leaves, st, &t->t);
     if (r != VFMM_OK) {
         free_tree(&t->t);
         delete t;
@@ -843,7 +997,7 @@ extern "C" int vfmm_tree_build_uniform(const vfmm_tree_params* prm, int32_t dept
     VFMM_CHECK(check_params(prm));
     if (depth < 0 || depth > 10) return fail(VFMM_ERR_INVALID_ARG, "uniform depth must be in [0, 10]");
     vfmm_tree* t = new vfmm_tree();
-    int r = build(prm, nullptr, depth, (cudaStream_t)stream, &t->t);
+    int r = build(prm, nullptr, depth, 0, (cudaStream_t)stream, &t->t);
     if (r != VFMM_OK) {
         free_tree(&t->t);
         delete t;

@@ -78,6 +78,18 @@ def test_adaptive_tree_bit_exact(name, mk, k, tol, depth):
     assert abs(gt.f_scale - info["F"]) <= 1e-15 * info["F"]
 
 
+@pytest.mark.parametrize("member", [0, 1, 3, 4])
+def test_leaf_count_tree_bit_exact(member):
+    """Greedy leaf-count trees of batch members (targets capped at 3000 to keep the oracle fast)."""
+    m = W.batch_members(member + 1)[member]
+    n = min(m["n_leaves_target"], 3000)
+    gt = v.tree_build_leaves(0.0, 0.0, 1.0, m["k"], m["source"], n, 16)
+    ot, info = T.build_greedy(0.0, 0.0, 1.0, m["k"], m["source"], n, 16, return_info=True)
+    assert info["min_margin"] > 1e-6 and gt.min_margin > 1e-6  # no priority sits at a rounding tie
+    same_tree(gt, ot)
+    assert abs(gt.min_margin - info["min_margin"]) <= 1e-6
+
+
 def test_leaf_nodes_and_sampling():
     src = W.narrow_gaussians(5, n=3, sigma=0.04)
     gt = v.tree_build(0.0, 0.0, 1.0, 8, src, 1e-6, 7)

@@ -118,3 +118,46 @@ def test_kinked_source_zero_set_is_the_curve():
     assert np.max(np.abs(phi)) < 1e-14
     assert np.all(source.kinked_phi(prm, 0.5 * r * np.cos(th), 0.5 * r * np.sin(th)) > 0)
     assert np.all(source.kinked_phi(prm, 1.1 * r * np.cos(th), 1.1 * r * np.sin(th)) < 0)
+
+
+# ----------------------------------------------------------------------------- leaf-count target
+def _refined_leaves(refined):
+    """Leaves of a refinement given as a set of boxes (before balancing)."""
+    return [b for b in refined if (b[0] + 1, 2 * b[1], 2 * b[2]) not in refined]
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_greedy_constant_source_is_uniform(depth):
+    """f = 1 has zero tails everywhere: every priority ties, so coarser-first order builds
+    exactly the uniform tree when the target is 4^depth."""
+    src = W.constant_source(1.0)
+    ot = T.build_greedy(0.0, 0.0, 1.0, 8, src, 4 ** depth, 16)
+    ref = T.build_uniform(0.0, 0.0, 1.0, 8, depth)
+    assert ot.n_leaves == 4 ** depth
+    assert sorted(zip(ot.level, ot.ix, ot.iy)) == sorted(zip(ref.level, ref.ix, ref.iy))
+
+
+def test_greedy_counts_prefix_and_focus():
+    """One split adds 3 leaves, so the refinement stops at the first count >= target; the split
+    sequence is a prefix of the one for a larger target; a narrow Gaussian draws the deepest
+    leaves to its centre; the result is level-restricted."""
+    src = W.gauss_source([[0.31, -0.27]], 0.01, [1.0])
+    prev = None
+    for n in (10, 40, 100, 250):
+        ot, info = T.build_greedy(0.0, 0.0, 1.0, 8, src, n, 16, return_info=True)
+        leaves = _refined_leaves(info["refined"])
+        assert n <= len(leaves) < n + 3 and (len(leaves) - 1) % 3 == 0
+        if prev is not None:
+            assert prev <= info["refined"]
+        prev = info["refined"]
+        assert T.is_balanced(ot)
+    deepest = max(leaves, key=lambda b: b[0])
+    h = 2.0 ** -deepest[0]
+    cx, cy = -0.5 + (deepest[1] + 0.5) * h, -0.5 + (deepest[2] + 0.5) * h
+    assert abs(cx - 0.31) <= 1.5 * h and abs(cy + 0.27) <= 1.5 * h
+
+
+def test_greedy_max_depth_stops_refinement():
+    src = W.gauss_source([[0.0, 0.0]], 0.001, [1.0])
+    ot = T.build_greedy(0.0, 0.0, 1.0, 8, src, 10 ** 6, 2)
+    assert ot.depth == 2 and ot.n_leaves == 16
