@@ -29,6 +29,8 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "mixed.cuh"
@@ -119,8 +121,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 struct SplitArgs {
-    const bf16* asl;      // A rows: row r, slice i at asl + (r * kSlices + i) * Kp
-    const bf16* bsl;      // tables: [n_tables][Rp][kSlices][Kp]
+    const bf16* asl;      // A rows [rows][Kp / 32][kSlices][32]; the tables come through the tensor map
     const int32_t* gptr;  // [n_groups + 1] into gcfg
     const int32_t* gcfg;  // table of each (group, table) entry
     const int32_t* gsrc;  // [entries][128] A row or -1
@@ -129,6 +130,7 @@ struct SplitArgs {
     int* err;
     int Kp, Rp, nchunks;
     int split;            // CTAs sharing one group's tables (split-K over tables)
+    int drain_every;      // configurations accumulated in TMEM between two drains (exactness bound)
     size_t part_stride;   // n_out_rows * Rp
 };
 
@@ -162,7 +164,7 @@ __device__ __forceinline__ void issue_unit(uint32_t tmem, uint64_t ad0, uint64_t
 // Warps 0..7: epilogue (lane quadrant w % 4, column half w / 4); warps 8..10: producers;
 // warp 11: TMEM allocation and the MMA issuer (lane 0). Twelve warps keep three warps per SM
 // sub-partition, which leaves each thread up to 168 registers.
-__global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ unsigned char dsm[];
     __shared__ __align__(8) uint64_t bars[2 * kStages + 2];
     __shared__ uint32_t tmem_holder;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
     const uint32_t acc_empty = tc::smem_u32(&bars[2 * kStages + 1]);
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
-            tc::mbar_init(full0 + 8 * s, kProducerThreads);
+            tc::mbar_init(full0 + 8 * s, kProducerThreads + 1);  // cp.async producers + the TMA issuer
             tc::mbar_init(empty0 + 8 * s, 1);
         }
         tc::mbar_init(acc_full, 1);
@@ -211,9 +213,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
     const int r0 = rc * N;
 
     if (warp >= kEpilogueWarps && warp < kMmaWarp) {
-        // ------------------------------------------------ producers: gather slices with cp.async
+        // ------------------------------------------------ producers: table tile by TMA (one thread),
+        // gathered source rows by cp.async (all producer threads)
         const int ptid = tid - kEpilogueThreads;
-        bool alive = true;
+        if (ptid == 0) tc::tma_prefetch_desc(&tmB);
         for (int u = 0; u < U; ++u) {
             const int s = u & 1;
             if (u >= 2 && !tc::mbar_wait(empty0 + 8 * s, ((u >> 1) - 1) & 1, &abort_flag)) p_abort = 1;
@@ -223,7 +226,6 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
             if (p_abort) {
                 abort_flag = 1;
                 atomicExch(a.err, 1);
-                alive = false;
                 break;
             }
             const int ci = cbeg + u / nkb, kb = u % nkb;
@@ -234,6 +236,12 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
                 named_bar_sync(1, kProducerThreads);
             }
             const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
+            if (ptid == 0) {
+                // 8 boxes of 80 table rows x 64 bytes (one per slice), SW64-swizzled by the TMA unit
+                tc::mbar_arrive_expect_tx(full0 + 8 * s, kSlices * B_SLICE);
+                for (int sl_i = 0; sl_i < kSlices; ++sl_i)
+                    tc::tma_load_3d(sB + sl_i * B_SLICE, &tmB, 0, kb * kSlices + sl_i, cfg * a.Rp + r0, full0 + 8 * s);
+            }
             // a warp instruction covers 8 rows x 64 bytes of one slice: 512 contiguous bytes of shared
             // memory (no bank conflicts) from eight 64-byte pieces of global memory
             const int lrow = (ptid & 31) >> 2, ch = ptid & 3, pw = ptid >> 5;
@@ -245,31 +253,19 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
                 const uint32_t dst = sA + sl_i * A_SLICE + m * 64 + ((ch ^ ((m >> 1) & 3)) << 4);
                 tc::cp_async16(dst, gp, src < 0 ? 0u : 16u);
             }
-            const bf16* bbase = a.bsl + ((size_t)cfg * a.Rp + r0) * nkb * kSlices * kKBlock;
-#pragma unroll 4
-            for (int q = pw; q < kSlices * (N / 8); q += kProducerThreads / 32) {
-                const int sl_i = q / (N / 8), n = (q % (N / 8)) * 8 + lrow;
-                const bf16* gp = bbase + (((size_t)n * nkb + kb) * kSlices + sl_i) * kKBlock + ch * 8;
-                const uint32_t dst = sB + sl_i * B_SLICE + n * 64 + ((ch ^ ((n >> 1) & 3)) << 4);
-                tc::cp_async16(dst, gp, 16u);
-            }
-            tc::cp_async_commit();
-            if (u >= 1) {
-                tc::cp_async_wait<1>();
-                tc::fence_proxy_async();
-                tc::mbar_arrive(full0 + 8 * ((u - 1) & 1));
-            }
+            // the stage's full barrier gets this thread's arrival when its copies have landed
+            tc::cp_async_mbar_arrive(full0 + 8 * s);
         }
-        tc::cp_async_wait<0>();
-        tc::fence_proxy_async();
-        if (alive && U >= 1) tc::mbar_arrive(full0 + 8 * ((U - 1) & 1));
-    } else if (warp == kMmaWarp) {
+        tc::cp_async_wait_all();
+        } else if (warp == kMmaWarp) {
         // ------------------------------------------------ MMA issuer: one configuration at a time
         if (lane == 0) {
             const uint64_t adesc_base = tc::smem_desc(sbase, 16, 512, tc::kLayoutSwizzle64B);
             bool alive = true;
+            const int G = a.drain_every;
             for (int c = 0; c < ncfg && alive; ++c) {
-                if (c >= 1 && !tc::mbar_wait(acc_empty, (c - 1) & 1, &abort_flag)) {
+                // a drain group = G consecutive configurations summed in the same accumulators
+                if (c >= G && c % G == 0 && !tc::mbar_wait(acc_empty, (c / G - 1) & 1, &abort_flag)) {
                     abort_flag = 1;
                     atomicExch(a.err, 4);
                     break;
@@ -284,15 +280,18 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
                         break;
                     }
                     tc::tc_fence_after();
+                    // the gathered rows were written by cp.async (generic proxy): make them visible to
+                    // the tensor core's reads (async proxy) before the MMAs
+                    tc::fence_proxy_async();
                     // descriptors differ only in the 14-bit start-address field (address >> 4), so
                     // offsets within the stage are added to a base descriptor
                     const uint64_t ad0 = adesc_base + ((s * STAGE) >> 4);
                     const uint64_t bd0 = adesc_base + ((s * STAGE + kSlices * A_SLICE) >> 4);
-                    if (kb == 0) issue_unit<true>(tmem, ad0, bd0);
+                    if (kb == 0 && c % G == 0) issue_unit<true>(tmem, ad0, bd0);
                     else issue_unit<false>(tmem, ad0, bd0);
                     tc::umma_commit(empty0 + 8 * s);
                 }
-                if (alive) tc::umma_commit(acc_full);
+                if (alive && (c % G == G - 1 || c == ncfg - 1)) tc::umma_commit(acc_full);
             }
         }
         __syncwarp();
@@ -304,8 +303,9 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
 #pragma unroll
         for (int j = 0; j < HALF; ++j) hi[j] = lo[j] = 0.0f;
         bool ok = true;
-        for (int c = 0; c < ncfg; ++c) {
-            ok = ok && tc::mbar_wait(acc_full, c & 1, &abort_flag);
+        const int ngroups = (ncfg + a.drain_every - 1) / a.drain_every;
+        for (int grp = 0; grp < ngroups; ++grp) {
+            ok = ok && tc::mbar_wait(acc_full, grp & 1, &abort_flag);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) atomicExch(a.err, 3);
@@ -313,20 +313,23 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
                 break;
             }
             tc::tc_fence_after();
-#pragma unroll 1
-            for (int acc = 0; acc < kNumAcc; ++acc) {
+            // per 8-column chunk: the 6 accumulators loaded together, one wait, then summed in
+            // accumulator order into the double-FP32 (hi, lo) pairs
 #pragma unroll
-                for (int ch = 0; ch < HALF / 8; ++ch) {
-                    float v[8];
-                    tc::tmem_ld8(lane_base + acc * N + ch * 8, v);
+            for (int ch = 0; ch < HALF / 8; ++ch) {
+                uint32_t r[kNumAcc][8];
+#pragma unroll
+                for (int acc = 0; acc < kNumAcc; ++acc) tc::tmem_ld8_nowait(lane_base + acc * N + ch * 8, r[acc]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int acc = 0; acc < kNumAcc; ++acc)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         float s2, e2;
-                        two_sum(hi[ch * 8 + j], v[j], s2, e2);
+                        two_sum(hi[ch * 8 + j], __uint_as_float(r[acc][j]), s2, e2);
                         hi[ch * 8 + j] = s2;
                         lo[ch * 8 + j] = __fadd_rn(lo[ch * 8 + j], e2);
                     }
-                }
             }
             tc::tc_fence_before();
             tc::mbar_arrive(acc_empty);
@@ -357,6 +360,38 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a) {
 }
 
 // ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int make_table_map(const void* base, int64_t rows, int Kp, CUtensorMap* out) {
+    static EncodeTiledFn encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = (EncodeTiledFn)fn;
+    });
+    if (!encode) return fail(VFMM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    if (Kp % kKBlock || rows < 1 || rows > (int64_t)INT32_MAX || ((uintptr_t)base & 15))
+        return fail(VFMM_ERR_INTERNAL, "table shape not suitable for a tensor map");
+    // [rows][Kp / 32 K blocks][8 slices][32 values]: dim 0 = 32 values (64 bytes, one swizzle row),
+    // dim 1 = (K block, slice) segments, dim 2 = rows
+    const cuuint64_t nseg = (cuuint64_t)(Kp / kKBlock) * kSlices;
+    const cuuint64_t dims[3] = {(cuuint64_t)kKBlock, nseg, (cuuint64_t)rows};
+    const cuuint64_t strides[2] = {(cuuint64_t)kKBlock * 2, nseg * kKBlock * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kKBlock, 1, (cuuint32_t)kTileN};
+    const cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(VFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return VFMM_OK;
+}
+
 int mixed_prepare(vfmm_ops* o, cudaStream_t st) {
     if (o->k * o->k * 3 > 4096) return fail(VFMM_ERR_INVALID_ARG, "mixed precision supports k <= 16");
     MixedOps* mo = new MixedOps();
@@ -373,6 +408,7 @@ int mixed_prepare(vfmm_ops* o, cudaStream_t st) {
     table_slice_kernel<<<dim3(mo->Rp, kNearCfg), 128, 0, st>>>(o->near, R, kk, mo->Rp, mo->Kp, mo->Er, (bf16*)mo->tsl);
     VFMM_CUDA(cudaGetLastError());
     VFMM_CUDA(cudaStreamSynchronize(st));
+    VFMM_CHECK(make_table_map(mo->tsl, (int64_t)kNearCfg * mo->Rp, mo->Kp, &mo->tm_near));
     return far_prepare(o, st);
 }
 
@@ -487,7 +523,7 @@ __global__ void split_reduce_kernel(const float2* __restrict__ part, size_t stri
     out[o] = make_float2(h, __fsub_rn(lo, __fsub_rn(h, hi)));
 }
 
-int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int Rp, float2* out, int* err,
+int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
                float2* part, size_t n_out_rows, cudaStream_t st) {
     if (P.n_groups == 0) return VFMM_OK;
     if (Kp % kKBlock || Rp % kTileN) return fail(VFMM_ERR_INTERNAL, "split GEMM shape not tiled");
@@ -498,7 +534,6 @@ int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int
     }
     SplitArgs a;
     a.asl = (const bf16*)asl;
-    a.bsl = (const bf16*)bsl;
     a.gptr = P.ptr;
     a.gcfg = P.cfg;
     a.gsrc = P.src;
@@ -507,10 +542,13 @@ int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int
     a.Kp = Kp;
     a.Rp = Rp;
     a.nchunks = Rp / kTileN;
+    // A diagonal gets at most 5 slice products per K value (i + j = d <= 6), each below 63^2, so the
+    // FP32 accumulators stay exact while 5 * 3969 * Kp * configurations < 2^24.
+    a.drain_every = std::max(1, (int)((1 << 24) / (5ll * 3969 * Kp)));
     a.split = part ? P.split : 1;
     a.part_stride = n_out_rows * (size_t)Rp;
     a.out = a.split > 1 ? part : out;
-    split_gemm_kernel<<<(unsigned)P.n_groups * a.split * a.nchunks, kThreads, smem_bytes(), st>>>(a);
+    split_gemm_kernel<<<(unsigned)P.n_groups * a.split * a.nchunks, kThreads, smem_bytes(), st>>>(a, bmap);
     VFMM_CUDA(cudaGetLastError());
     if (a.split > 1) {
         const int64_t n = (int64_t)P.n_groups * kTileM * Rp;
@@ -591,7 +629,7 @@ int near_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const 
     f_slice_kernel<<<(unsigned)std::min<int64_t>(65535, (ns + 255) / 256), 256, 0, st>>>(f, T.n_leaves, kk, mo->Kp, R,
                                                                                          w.fmax, w.Ef, (bf16*)w.fsl);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(PS.near, w.fsl, mo->tsl, mo->Kp, mo->Rp, w.out, w.err, w.part, (size_t)T.n_leaves * R, st);
+    return split_gemm(PS.near, w.fsl, mo->tm_near, mo->Kp, mo->Rp, w.out, w.err, w.part, (size_t)T.n_leaves * R, st);
 }
 
 }  // namespace vfmm

@@ -1,6 +1,7 @@
 // Split-BF16 near field: constants and device buffers.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoder is fetched through the runtime's driver entry point)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -61,6 +62,8 @@ struct MixedOps {
     int Kp = 0;     // k^2 rounded up to kKBlock
     void* tsl = nullptr;  // bf16 [33][Rp][kSlices][Kp]
     int* Er = nullptr;    // [Rp] row exponents
+    // TMA descriptors of the sliced tables (box = 80 rows x 64 bytes of one slice and K block)
+    CUtensorMap tm_near, tm_s2m, tm_m2l, tm_far, tm_s2l;
     // far field: expansion coefficients as reals (Re, Im of 0..p), Kx = 2(p+1) padded
     int Kx = 0;           // 2(p+1) rounded up to kKBlock
     int Rx = 0;           // 2p rounded up to kTileN (rows of S2M and M2L without coefficient 0)
@@ -101,7 +104,9 @@ int build_split_plan(const std::vector<int32_t>& tgt_id,
                      const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                      const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
                      SplitPlan* P);
-int split_gemm(const SplitPlan& P, const void* asl, const void* bsl, int Kp, int Rp, float2* out, int* err,
+// Tensor map of a sliced table [rows][Kp / 32][kSlices][32] BF16 for the table operand of split_gemm.
+int make_table_map(const void* base, int64_t rows, int Kp, CUtensorMap* out);
+int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
                float2* part, size_t n_out_rows, cudaStream_t st);
 size_t split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o);
 int build_mixed_plan(DeviceTree* T);

@@ -98,6 +98,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
     std::vector<double> S((size_t)2 * p * kk);
     std::copy(s2m.begin() + 2 * kk, s2m.end(), S.begin());
     VFMM_CHECK(slice_table(S, 1, 2 * p, kk, mo->Rx, mo->Kp, &mo->s2m_sl, &mo->s2m_E, st));
+    VFMM_CHECK(make_table_map(mo->s2m_sl, mo->Rx, mo->Kp, &mo->tm_s2m));
     // M2L as real matrices: rows 2..2p+1, columns 0..2p+1
     std::vector<double> mt((size_t)kVCfg * P * P * 2);
     VFMM_CUDA(cudaMemcpy(mt.data(), o->m2l_t, mt.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -117,6 +118,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
     for (size_t r = 0; r < (size_t)kVCfg * mo->Rx; ++r)
         for (int q = 0; q < mo->Kx; ++q) MR[r * mo->Kx + q] = std::ldexp(MR[r * mo->Kx + q], -(q >> 2));
     VFMM_CHECK(slice_table(MR, kVCfg, mo->Rx, mo->Kx, mo->Rx, mo->Kx, &mo->m2l_sl, &mo->m2l_E, st));
+    VFMM_CHECK(make_table_map(mo->m2l_sl, (int64_t)kVCfg * mo->Rx, mo->Kx, &mo->tm_m2l));
     // leaf tables: 0 = L2T without coefficient 0, 1 + c = M2T of W configuration c
     std::vector<double> l2t((size_t)R * 2 * P), xh(k);
     VFMM_CUDA(cudaMemcpy(l2t.data(), o->l2t, l2t.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -155,6 +157,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
         }
     }
     VFMM_CHECK(slice_table(F, 1 + kFarCfg, R, KX, mo->Rp, mo->Kx, &mo->far_sl, &mo->far_E, st));
+    VFMM_CHECK(make_table_map(mo->far_sl, (int64_t)(1 + kFarCfg) * mo->Rp, mo->Kx, &mo->tm_far));
     // S2L: rows 2..2p+1 (Re, Im of coefficients 1..p) over the k*k source values; row 0 kept in FP64
     std::vector<double> st_((size_t)kFarCfg * kk * P * 2);
     VFMM_CUDA(cudaMemcpy(st_.data(), o->s2l_t, st_.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -168,6 +171,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
             }
         }
     VFMM_CHECK(slice_table(XL, kFarCfg, 2 * p, kk, mo->Rx, mo->Kp, &mo->s2l_sl, &mo->s2l_E, st));
+    VFMM_CHECK(make_table_map(mo->s2l_sl, (int64_t)kFarCfg * mo->Rx, mo->Kp, &mo->tm_s2l));
     VFMM_CUDA(cudaMalloc(&mo->s2l_r0, X0.size() * sizeof(double)));
     VFMM_CUDA(cudaMemcpy(mo->s2l_r0, X0.data(), X0.size() * sizeof(double), cudaMemcpyHostToDevice));
     return VFMM_OK;
@@ -331,7 +335,7 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
 int s2m_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* Mexp,
               const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    VFMM_CHECK(split_gemm(PS.s2m, w.fsl, mo->s2m_sl, mo->Kp, mo->Rx, w.s2m_out, w.err, nullptr, 0, st));
+    VFMM_CHECK(split_gemm(PS.s2m, w.fsl, mo->tm_s2m, mo->Kp, mo->Rx, w.s2m_out, w.err, nullptr, 0, st));
     s2m_finish_kernel<<<T.n_leaves * PS.R, 128, 0, st>>>(T.n_leaves, PS.R, o.k * o.k, o.p, mo->Rx, T.box_of_leaf,
                                                          T.level, T.width, f, o.s2m, w.s2m_out, mo->s2m_E, w.Ef,
                                                          Mexp);
@@ -402,14 +406,14 @@ int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const d
     multipole_slice_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(T.level, vb0, vb1, R, P2, mo->Kx, Mexp,
                                                                           w.glev, (bf16*)w.msl);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(PS.m2l, w.msl, mo->m2l_sl, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, (size_t)T.n_boxes * R,
+    return split_gemm(PS.m2l, w.msl, mo->tm_m2l, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, (size_t)T.n_boxes * R,
                       st);
 }
 
 // ---------------------------------------------------------------- S2L
 int s2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    return split_gemm(PS.s2l, w.fsl, mo->s2l_sl, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part, (size_t)T.n_boxes * PS.R,
+    return split_gemm(PS.s2l, w.fsl, mo->tm_s2l, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part, (size_t)T.n_boxes * PS.R,
                       st);
 }
 
@@ -453,7 +457,7 @@ int far_leaf_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, co
                                                           T.far_slot, T.lptr[VFMM_LIST_W], T.lidx[VFMM_LIST_W], Mexp,
                                                           Lexp, w.Et, (bf16*)w.aprep);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(PS.far, w.aprep, mo->far_sl, mo->Kx, mo->Rp, w.far_out, w.err, w.part,
+    return split_gemm(PS.far, w.aprep, mo->tm_far, mo->Kx, mo->Rp, w.far_out, w.err, w.part,
                       (size_t)T.n_leaves * PS.R, st);
 }
 
