@@ -19,6 +19,7 @@
 
 #include "mixed.cuh"
 #include "ops.cuh"
+#include "tc_ptx.cuh"
 #include "vfmm_internal.cuh"
 
 namespace vfmm {
@@ -31,42 +32,54 @@ __device__ __forceinline__ double pow2(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// Re of local coefficient 0 from the V and X lists of each virtual box (box, r), one warp per
-// virtual box: sum over V of Re(row 0 of M2L_c . a_c) + a_0(c) log h, and over X of
-// (2h)^2 Re(S2L row 0) . f_c + a_0(c) log h. FP64; the other coefficients come from the
-// split-precision M2L and S2L.
-__global__ void m2l_c0_kernel(int begin, int end, int R, int P, double width, const int32_t* __restrict__ level,
-                              const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
-                              const int32_t* __restrict__ vcfg, const double* __restrict__ m2l_t,
-                              const double* __restrict__ Mexp, double* __restrict__ c0,
-                              const int32_t* __restrict__ xptr, const int32_t* __restrict__ xidx,
-                              const int32_t* __restrict__ xcfg, const int32_t* __restrict__ leaf_of_box,
-                              const double* __restrict__ s2l_r0, const double* __restrict__ f, int nleaf, int kk) {
-    const int64_t vw = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+// Re of local coefficient 0 from the V and X lists of each virtual box (box, r): sum over V of
+// Re(row 0 of M2L_c . a_c) + a_0(c) log h, and over X of (2h)^2 Re(S2L row 0) . f_c + a_0(c) log h.
+// FP64; the other coefficients come from the split-precision M2L and S2L. Persistent CTAs hold the
+// row-0 tables in shared memory; one warp per virtual box, one lane per V entry.
+__global__ void __launch_bounds__(256) m2l_c0_kernel(int begin, int end, int R, int P, double width,
+                                                     const int32_t* __restrict__ level,
+                                                     const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
+                                                     const int32_t* __restrict__ vcfg, const double2* __restrict__ m2l_r0,
+                                                     const double* __restrict__ Mexp, double* __restrict__ c0,
+                                                     const int32_t* __restrict__ xptr, const int32_t* __restrict__ xidx,
+                                                     const int32_t* __restrict__ xcfg,
+                                                     const int32_t* __restrict__ leaf_of_box,
+                                                     const double* __restrict__ s2l_r0, const double* __restrict__ f,
+                                                     int nleaf, int kk) {
+    extern __shared__ __align__(16) unsigned char c0_raw[];
+    double2* sM = reinterpret_cast<double2*>(c0_raw);           // [40][P]
+    double* sX = reinterpret_cast<double*>(sM + kVCfg * P);      // [20][kk]
+    for (int q = threadIdx.x; q < kVCfg * P; q += blockDim.x) sM[q] = m2l_r0[q];
+    for (int q = threadIdx.x; q < kFarCfg * kk; q += blockDim.x) sX[q] = s2l_r0[q];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    if (vw >= (int64_t)(end - begin) * R) return;
-    const int b = begin + (int)(vw / R), r = (int)(vw % R);
-    const double logh = log(ldexp(width, -level[b]));
-    double acc = 0.0;
-    for (int e = vptr[b] + lane; e < vptr[b + 1]; e += 32) {
-        const double* a = Mexp + ((size_t)vidx[e] * R + r) * 2 * P;
-        const double* M = m2l_t + (size_t)vcfg[e] * P * P * 2;
-        double re = a[0] * logh;
-        for (int n = 0; n < P; ++n) re += M[(size_t)n * P * 2] * a[2 * n] - M[(size_t)n * P * 2 + 1] * a[2 * n + 1];
-        acc += re;
+    const int64_t total = (int64_t)(end - begin) * R;
+    for (int64_t vw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; vw < total;
+         vw += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int b = begin + (int)(vw / R), r = (int)(vw % R);
+        const double h = ldexp(width, -level[b]);
+        const double logh = log(h);
+        double acc = 0.0;
+        for (int e = vptr[b] + lane; e < vptr[b + 1]; e += 32) {
+            const double* a = Mexp + ((size_t)vidx[e] * R + r) * 2 * P;
+            const double2* M = sM + vcfg[e] * P;
+            double re = a[0] * logh;
+#pragma unroll 8
+            for (int n = 0; n < P; ++n) re += M[n].x * a[2 * n] - M[n].y * a[2 * n + 1];
+            acc += re;
+        }
+        // X list: (2h)^2 [Re(S2L row 0) . f_c + log(h) W . f_c], with W . f_c = a_0(c) / (2h)^2
+        for (int e = xptr[b]; e < xptr[b + 1]; ++e) {
+            const double* fc = f + ((size_t)r * nleaf + leaf_of_box[xidx[e]]) * kk;
+            const double* r0 = sX + xcfg[e] * kk;
+            double part = 0.0;
+            for (int s = lane; s < kk; s += 32) part += r0[s] * fc[s];
+            acc += 4.0 * h * h * part;
+            if (lane == 0) acc += logh * Mexp[((size_t)xidx[e] * R + r) * 2 * P];
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) c0[(size_t)b * R + r] = acc;
     }
-    // X list: (2h)^2 [Re(S2L row 0) . f_c + log(h) W . f_c], with W . f_c = a_0(c) / (2h)^2
-    const double h = ldexp(width, -level[b]);
-    for (int e = xptr[b]; e < xptr[b + 1]; ++e) {
-        const double* fc = f + ((size_t)r * nleaf + leaf_of_box[xidx[e]]) * kk;
-        const double* r0 = s2l_r0 + (size_t)xcfg[e] * kk;
-        double part = 0.0;
-        for (int s = lane; s < kk; s += 32) part += r0[s] * fc[s];
-        acc += 4.0 * h * h * part;
-        if (lane == 0) acc += logh * Mexp[((size_t)xidx[e] * R + r) * 2 * P];
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) c0[(size_t)b * R + r] = acc;
 }
 
 // ---------------------------------------------------------------- FP64 gather GEMM tile
@@ -263,10 +276,112 @@ __global__ void __launch_bounds__(128) translate_kernel(int mode, const int32_t*
     }
 }
 
+// Same translations with the 4 position tables held in shared memory (one bulk copy per CTA),
+// persistent CTAs looping over the virtual boxes of the level: the table is read from L2 once
+// per CTA instead of once per multiply-add. Used when 4 P^2 complex values fit (P <= 58).
+constexpr int kTranslateThreads = 128;
+__global__ void __launch_bounds__(kTranslateThreads) translate_smem_kernel(int mode, const int32_t* __restrict__ boxes,
+                                                                           int nbox, int R,
+                                                                           const int32_t* __restrict__ child0, int P,
+                                                                           const double2* __restrict__ tab,
+                                                                           double2* __restrict__ ex, int* err) {
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int no_abort;
+    double2* sT = reinterpret_cast<double2*>(sm_raw);  // [4][P][P]
+    double2* s_in = sT + 4 * P * P;                    // [4P]
+    double2* s_out = s_in + 4 * P;                     // [4P]
+    const uint32_t bar_a = tc::smem_u32(&bar);
+    const uint32_t bytes = (uint32_t)(4 * P * P) * sizeof(double2);
+    if (threadIdx.x == 0) {
+        no_abort = 0;
+        tc::mbar_init(bar_a, 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::mbar_arrive_expect_tx(bar_a, bytes);
+        constexpr uint32_t kChunk = 32768;
+        for (uint32_t off = 0; off < bytes; off += kChunk)
+            tc::bulk_copy_g2s(tc::smem_u32(sm_raw) + off, reinterpret_cast<const char*>(tab) + off,
+                              min(kChunk, bytes - off), bar_a);
+    }
+    const bool landed = tc::mbar_wait(bar_a, 0, &no_abort);
+    if (!__syncthreads_and(landed)) {  // one decision for the whole CTA
+        if (threadIdx.x == 0 && err) atomicExch(err, 5);
+        return;  // the copy itself completes on its own
+    }
+    const int npair = (P + 1) / 2;
+    for (int item = blockIdx.x; item < nbox * R; item += gridDim.x) {
+        const int bi = item / R, r = item - bi * R;  // virtual box (box, right-hand side)
+        const int b = boxes[bi], c0 = child0[b];
+        if (mode == 0) {
+            for (int q = threadIdx.x; q < 4 * P; q += blockDim.x)
+                s_in[q] = ex[((size_t)(c0 + q / P) * R + r) * P + q % P];
+        } else {
+            for (int q = threadIdx.x; q < P; q += blockDim.x) s_in[q] = ex[((size_t)b * R + r) * P + q];
+        }
+        __syncthreads();
+        for (int task = threadIdx.x; task < 4 * npair; task += blockDim.x) {
+            const int pos = task / npair, j = task - pos * npair;
+            const double2* M = sT + pos * P * P;
+            const double2* x = mode == 0 ? s_in + pos * P : s_in;
+            for (int half = 0; half < 2; ++half) {
+                const int o = half == 0 ? j : P - 1 - j;
+                if (half == 1 && o == j) break;
+                const int n0 = mode == 0 ? 0 : o, n1 = mode == 0 ? o : P - 1;
+                double re = 0.0, im = 0.0;
+                for (int n = n0; n <= n1; ++n) {
+                    const double2 m = M[n * P + o], v = x[n];
+                    re = fma(m.x, v.x, fma(-m.y, v.y, re));
+                    im = fma(m.x, v.y, fma(m.y, v.x, im));
+                }
+                s_out[pos * P + o] = make_double2(re, im);
+            }
+        }
+        __syncthreads();
+        if (mode == 0) {
+            for (int o = threadIdx.x; o < P; o += blockDim.x) {
+                const double2 a0 = s_out[o], a1 = s_out[P + o], a2 = s_out[2 * P + o], a3 = s_out[3 * P + o];
+                ex[((size_t)b * R + r) * P + o] =
+                    make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+            }
+        } else {
+            for (int q = threadIdx.x; q < 4 * P; q += blockDim.x)
+                ex[((size_t)(c0 + q / P) * R + r) * P + q % P] = s_out[q];
+        }
+        __syncthreads();
+    }
+}
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
 static void launch_translate(int mode, const DeviceTree& T, int level, int R, int P, const double* tab, double* ex,
-                             cudaStream_t st) {
+                             int* err, cudaStream_t st) {
     const int nbox = T.nonleaf_start[level + 1] - T.nonleaf_start[level];
     if (nbox <= 0) return;
+    const size_t smem = (size_t)(4 * P * P + 8 * P) * sizeof(double2);
+    // small levels: the table is fetched once per CTA; large levels (at least ~8 boxes per SM): one CTA
+    // per box keeps many warps per SM feeding the FP64 pipes, the table staying in L1/L2
+    if (smem <= 113 * 1024 && (long long)nbox * R <= 8ll * sm_count()) {  // two CTAs per SM
+        static thread_local int attr_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (attr_dev != dev) {
+            cudaFuncSetAttribute(translate_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+            attr_dev = dev;
+        }
+        const int grid = std::min<long long>((long long)nbox * R, 2ll * sm_count());
+        translate_smem_kernel<<<grid, kTranslateThreads, smem, st>>>(
+            mode, T.nonleaf + T.nonleaf_start[level], nbox, R, T.child0, P, reinterpret_cast<const double2*>(tab),
+            reinterpret_cast<double2*>(ex), err);
+        return;
+    }
     const int threads = std::min(128, ((4 * ((P + 1) / 2) + 31) / 32) * 32);
     translate_kernel<<<(unsigned)nbox * R, threads, (size_t)8 * P * sizeof(double2), st>>>(
         mode, T.nonleaf + T.nonleaf_start[level], nbox, R, T.child0, P, reinterpret_cast<const double2*>(tab),
@@ -375,10 +490,96 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
     }
 }
 
+// Mixed form: the downward pass reduces to a per-coefficient combine (M2L, S2L and the FP64
+// coefficient 0 are already computed): one thread per (virtual box, coefficient), level by level.
+__global__ void down_mixed_kernel(DownArgs d) {
+    const int P = d.P, R = d.R;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)(d.end - d.begin) * R * P) return;
+    const size_t vb = (size_t)d.begin * R + (size_t)(q / P);
+    const int t = (int)(q % P);
+    const int b = (int)(vb / R), r = (int)(vb % R);
+    const double h = ldexp(d.width, -d.level);
+    double re = 0.0, im = 0.0;
+    if (d.level >= 3) {  // L2L from the parent, written by the translation kernel just before
+        re = d.Lexp[vb * 2 * P + 2 * t];
+        im = d.Lexp[vb * 2 * P + 2 * t + 1];
+    }
+    const bool has_v = d.vptr[b + 1] > d.vptr[b], has_x = d.xptr[b + 1] > d.xptr[b];
+    if (has_x && t >= 1) {
+        const float2 vr = d.s2l_out[vb * d.Rx + 2 * (t - 1)];
+        const float2 vi = d.s2l_out[vb * d.Rx + 2 * (t - 1) + 1];
+        const double sc = 4.0 * h * h * pow2(d.Ef[r]);
+        re += sc * ((double)vr.x + (double)vr.y) * pow2(d.s2l_E[2 * (t - 1)]);
+        im += sc * ((double)vi.x + (double)vi.y) * pow2(d.s2l_E[2 * (t - 1) + 1]);
+    }
+    if (has_v || has_x) {
+        if (t == 0) {
+            re += d.m2l_c0[vb];
+        } else if (has_v) {
+            const float2 vr = d.m2l_out[vb * d.Rx + 2 * (t - 1)];
+            const float2 vi = d.m2l_out[vb * d.Rx + 2 * (t - 1) + 1];
+            const int g = d.m2l_G[(size_t)d.level * R + r];
+            re += ((double)vr.x + (double)vr.y) * pow2(g + d.m2l_E[2 * (t - 1)]);
+            im += ((double)vi.x + (double)vi.y) * pow2(g + d.m2l_E[2 * (t - 1) + 1]);
+        }
+    }
+    d.Lexp[vb * 2 * P + 2 * t] = re;
+    d.Lexp[vb * 2 * P + 2 * t + 1] = im;
+}
+
+// Mixed form, per virtual leaf (leaf, r): the FP64 scalar part of u at every node of the leaf,
+// -(1/2pi) [log(h) sum_U a_0 + Re b_0 + sum_W a_0 (log h_w)], h_w = h / 2.
+__global__ void leaf_scalar_kernel(int nleaf, int R, int P, double width, const int32_t* __restrict__ box_of_leaf,
+                                   const int32_t* __restrict__ level, const int32_t* __restrict__ uptr,
+                                   const int32_t* __restrict__ uidx, const int32_t* __restrict__ wptr,
+                                   const int32_t* __restrict__ widx, const double* __restrict__ Mexp,
+                                   const double* __restrict__ Lexp, double* __restrict__ scal) {
+    const int64_t vl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vl >= (int64_t)nleaf * R) return;
+    const int leaf = (int)(vl / R), r = (int)(vl % R);
+    const int b = box_of_leaf[leaf];
+    const double logh = log(ldexp(width, -level[b]));
+    double m = 0.0, w0 = 0.0;
+    for (int e = uptr[b]; e < uptr[b + 1]; ++e) m += Mexp[((size_t)uidx[e] * R + r) * 2 * P];
+    for (int e = wptr[b]; e < wptr[b + 1]; ++e) w0 += Mexp[((size_t)widx[e] * R + r) * 2 * P];
+    scal[vl] = -kInv2Pi * logh * m - kInv2Pi * (Lexp[((size_t)b * R + r) * 2 * P] + w0 * (logh - 0.6931471805599453));
+}
+
+// Mixed form, one thread per (virtual leaf, node): u, u_x, u_y = near + far + scalar, the split
+// contraction outputs (hi, lo) scaled back by their power-of-two exponents.
+__global__ void leaf_mixed_kernel(int nleaf, int R, int kk, int Rp, double width, double inv_width,
+                                  const int32_t* __restrict__ box_of_leaf, const int32_t* __restrict__ level,
+                                  const float2* __restrict__ nearmix, const int* __restrict__ Er,
+                                  const int* __restrict__ Ef, const float2* __restrict__ farmix,
+                                  const int* __restrict__ farE, const int* __restrict__ Et,
+                                  const double* __restrict__ scal, double* __restrict__ u, double* __restrict__ ux,
+                                  double* __restrict__ uy) {
+    const int64_t total = (int64_t)nleaf * R * kk;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t vl = q / kk;
+        const int t = (int)(q % kk);
+        const int leaf = (int)(vl / R), r = (int)(vl % R);
+        const int lv = level[box_of_leaf[leaf]];
+        const double h = width * pow2(-lv), ih = inv_width * pow2(lv);
+        const float2* nm = nearmix + (size_t)vl * Rp;
+        const float2* fm = farmix + (size_t)vl * Rp;
+        const int ef = Ef[r], et = Et[vl];
+        const float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
+        const float2 w0 = fm[t], w1 = fm[kk + t], w2 = fm[2 * kk + t];
+        const size_t o = ((size_t)r * nleaf + leaf) * kk + t;
+        u[o] = h * h * ((double)v0.x + (double)v0.y) * pow2(ef + Er[t]) + scal[vl] +
+               ((double)w0.x + (double)w0.y) * pow2(et + farE[t]);
+        ux[o] = h * ((double)v1.x + (double)v1.y) * pow2(ef + Er[kk + t]) +
+                ih * ((double)w1.x + (double)w1.y) * pow2(et + farE[kk + t]);
+        uy[o] = h * ((double)v2.x + (double)v2.y) * pow2(ef + Er[2 * kk + t]) +
+                ih * ((double)w2.x + (double)w2.y) * pow2(et + farE[2 * kk + t]);
+    }
+}
+
 // ---------------------------------------------------------------- leaf pass (one CTA per leaf)
 struct LeafArgs {
     int nleaf, kk, k, P;
-    int R;  // right-hand sides folded into the leaf rows (mixed form; 1 in the FP64 form)
     double width;
     const int32_t* box_of_leaf;
     const int32_t* level;
@@ -388,75 +589,30 @@ struct LeafArgs {
     const double* slab;
     const double* far;
     const double* Mexp;
-    // split-precision near field (null in the FP64 form): (hi, lo) per row, scaled by 2^-(E_f + E_r)
-    const float2* nearmix;
-    const int* Er;
-    const int* Ef;
-    int Rp;
-    // split-precision leaf far field (null in the FP64 form): (hi, lo) scaled by 2^-(E_t + E_r)
-    const float2* farmix;
-    const int* farE;
-    const int* Et;
-    const double* Lexp;
     double* u;
     double* ux;
     double* uy;
 };
 
+// FP64 form: one CTA per leaf sums the near-field slab rows, the log(h) term, the far values
+// and the W-list multipoles (direct series) at its nodes.
 __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
     __shared__ double sa[2 * 64];
-    const int vl = blockIdx.x, R = a.R;
-    const int leaf = vl / R, r = vl - leaf * R;
+    const int leaf = blockIdx.x;
     const int t = threadIdx.x;
     const int kk = a.kk, P = a.P;
     const bool act = t < kk;
     const int b = a.box_of_leaf[leaf];
     const double h = ldexp(a.width, -a.level[b]);
     double u = 0.0, gx = 0.0, gy = 0.0, mass = 0.0;
-    if (a.nearmix) {
-        __shared__ double sc[2];
-        if (t < 32) {
-            // per-leaf scalars: U-list mass (log(h) term), local coefficient 0, W-list a_0 log(h_w)
-            double m = 0.0, w0 = 0.0;
-            for (int e = a.uptr[b] + t; e < a.uptr[b + 1]; e += 32) m += a.Mexp[((size_t)a.uidx[e] * R + r) * 2 * P];
-            for (int e = a.wptr[b] + t; e < a.wptr[b + 1]; e += 32) w0 += a.Mexp[((size_t)a.widx[e] * R + r) * 2 * P];
-            for (int o = 16; o > 0; o >>= 1) {
-                m += __shfl_xor_sync(0xffffffffu, m, o);
-                w0 += __shfl_xor_sync(0xffffffffu, w0, o);
-            }
-            if (t == 0) {
-                const double logh = log(h);
-                sc[0] = -kInv2Pi * logh * m;
-                sc[1] = -kInv2Pi * (a.Lexp[((size_t)b * R + r) * 2 * P] + w0 * (logh - 0.6931471805599453));
-            }
-        }
-        __syncthreads();
+    for (int e = a.uptr[b]; e < a.uptr[b + 1]; ++e) {
         if (act) {
-            const float2* nm = a.nearmix + (size_t)vl * a.Rp;
-            const float2* fm = a.farmix + (size_t)vl * a.Rp;
-            const int ef = a.Ef[r], et = a.Et[vl];
-            const double hh = h * h, ih = 1.0 / h;
-            float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
-            float2 w0 = fm[t], w1 = fm[kk + t], w2 = fm[2 * kk + t];
-            const size_t o = ((size_t)r * a.nleaf + leaf) * kk + t;
-            a.u[o] = hh * ((double)v0.x + (double)v0.y) * pow2(ef + a.Er[t]) + sc[0] + sc[1] +
-                     ((double)w0.x + (double)w0.y) * pow2(et + a.farE[t]);
-            a.ux[o] = h * ((double)v1.x + (double)v1.y) * pow2(ef + a.Er[kk + t]) +
-                      ih * ((double)w1.x + (double)w1.y) * pow2(et + a.farE[kk + t]);
-            a.uy[o] = h * ((double)v2.x + (double)v2.y) * pow2(ef + a.Er[2 * kk + t]) +
-                      ih * ((double)w2.x + (double)w2.y) * pow2(et + a.farE[2 * kk + t]);
+            const double* s = a.slab + (size_t)e * 3 * kk;
+            u += s[t];
+            gx += s[kk + t];
+            gy += s[2 * kk + t];
         }
-        return;
-    } else {
-        for (int e = a.uptr[b]; e < a.uptr[b + 1]; ++e) {
-            if (act) {
-                const double* s = a.slab + (size_t)e * 3 * kk;
-                u += s[t];
-                gx += s[kk + t];
-                gy += s[2 * kk + t];
-            }
-            mass += a.Mexp[(size_t)a.uidx[e] * 2 * P];
-        }
+        mass += a.Mexp[(size_t)a.uidx[e] * 2 * P];
     }
     u = h * h * u - kInv2Pi * log(h) * mass;
     gx *= h;
@@ -581,6 +737,8 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
         if (w) w->mix.Et = (int*)p;
         take(&p, nl * mo->Rp);
         if (w) w->mix.far_out = (float2*)p;
+        take(&p, nl);
+        if (w) w->mix.scal = p;
         const size_t np = split_part_elems(T, *PS, o);
         take(&p, std::max<size_t>(np, 1));
         if (w) w->mix.part = np ? (float2*)p : nullptr;
@@ -690,7 +848,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
     mark(se, ST_M2M, false, st);
     for (int l = T.depth - 1; l >= 2; --l) {
         if (T.nonleaf_start[l + 1] > T.nonleaf_start[l]) ++launches;
-        launch_translate(0, T, l, R, P, o.m2m_t, w.Mexp, st);
+        launch_translate(0, T, l, R, P, o.m2m_t, w.Mexp, w.mix.err, st);
     }
     mark(se, ST_M2M, true, st);
     // downward pass
@@ -700,10 +858,19 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         if (PS.m2l.n_groups > 0) launches += 4 + (PS.m2l.split > 1);
         const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
         const int64_t warps = (int64_t)(end - begin) * R;
-        m2l_c0_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(
+        const size_t c0_smem = (size_t)kVCfg * P * sizeof(double2) + (size_t)kFarCfg * kk * sizeof(double);
+        static thread_local int c0_attr_dev = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (c0_attr_dev != dev) {
+            cudaFuncSetAttribute(m2l_c0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+            c0_attr_dev = dev;
+        }
+        const unsigned c0_grid = (unsigned)std::min<int64_t>((warps + 7) / 8, 2ll * sm_count());
+        m2l_c0_kernel<<<c0_grid, 256, c0_smem, st>>>(
             begin, end, R, P, T.width, T.level, T.lptr[VFMM_LIST_V], T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V],
-            o.m2l_t, w.Mexp, w.mix.m2l_c0, T.lptr[VFMM_LIST_X], T.lidx[VFMM_LIST_X], T.lcfg[VFMM_LIST_X],
-            T.leaf_of_box, mo->s2l_r0, f, nleaf, kk);
+            reinterpret_cast<const double2*>(mo->m2l_r0), w.Mexp, w.mix.m2l_c0, T.lptr[VFMM_LIST_X],
+            T.lidx[VFMM_LIST_X], T.lcfg[VFMM_LIST_X], T.leaf_of_box, mo->s2l_r0, f, nleaf, kk);
         VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, st));
         launches += 1 + (PS.s2l.n_groups > 0) + (PS.s2l.n_groups > 0 && PS.s2l.split > 1);
     }
@@ -714,11 +881,16 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         if (n <= 0) continue;
         if (l >= 3) {
             // L2L for every box of level l (children of the non-leaf boxes of level l - 1)
-            launch_translate(1, T, l - 1, R, P, o.l2l_t, w.Lexp, st);
+            launch_translate(1, T, l - 1, R, P, o.l2l_t, w.Lexp, w.mix.err, st);
             ++launches;
         }
         ++launches;
-        down_kernel<<<(unsigned)n * R, 64, 0, st>>>(d);
+        if (mixed) {
+            const int64_t nt = (int64_t)n * R * P;
+            down_mixed_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(d);
+        } else {
+            down_kernel<<<(unsigned)n * R, 64, 0, st>>>(d);
+        }
     }
     if (T.depth < 2) VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.n_boxes * R * P2 * sizeof(double), st));
     else VFMM_CUDA(cudaMemsetAsync(w.Lexp, 0, (size_t)T.level_start[2] * R * P2 * sizeof(double), st));
@@ -747,7 +919,6 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
     mark(se, ST_LEAF, false, st);
     LeafArgs a;
     a.nleaf = nleaf;
-    a.R = R;
     a.kk = kk;
     a.k = o.k;
     a.P = P;
@@ -763,28 +934,24 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
     a.slab = w.slab;
     a.far = w.far;
     a.Mexp = w.Mexp;
-    a.nearmix = nullptr;
-    a.Er = nullptr;
-    a.Ef = nullptr;
-    a.Rp = 0;
-    a.farmix = nullptr;
-    a.farE = nullptr;
-    a.Et = nullptr;
-    a.Lexp = w.Lexp;
-    if (mixed) {
-        a.nearmix = w.mix.out;
-        a.Er = mo->Er;
-        a.Ef = w.mix.Ef;
-        a.Rp = mo->Rp;
-        a.farmix = w.mix.far_out;
-        a.farE = mo->far_E;
-        a.Et = w.mix.Et;
-    }
     a.u = u;
     a.ux = ux;
     a.uy = uy;
-    leaf_kernel<<<(unsigned)nleaf * R, ((kk + 31) / 32) * 32, 0, st>>>(a);
-    ++launches;
+    if (mixed) {
+        const int64_t nv = (int64_t)nleaf * R;
+        leaf_scalar_kernel<<<(unsigned)((nv + 127) / 128), 128, 0, st>>>(
+            nleaf, R, P, T.width, T.box_of_leaf, T.level, T.lptr[VFMM_LIST_U], T.lidx[VFMM_LIST_U],
+            T.lptr[VFMM_LIST_W], T.lidx[VFMM_LIST_W], w.Mexp, w.Lexp, w.mix.scal);
+        const int64_t ne = nv * kk;
+        const unsigned grid = (unsigned)std::min<int64_t>((ne + 255) / 256, 64ll * sm_count());
+        leaf_mixed_kernel<<<grid, 256, 0, st>>>(nleaf, R, kk, mo->Rp, T.width, 1.0 / T.width, T.box_of_leaf, T.level,
+                                                w.mix.out, mo->Er, w.mix.Ef, w.mix.far_out, mo->far_E, w.mix.Et,
+                                                w.mix.scal, u, ux, uy);
+        launches += 2;
+    } else {
+        leaf_kernel<<<(unsigned)nleaf, ((kk + 31) / 32) * 32, 0, st>>>(a);
+        ++launches;
+    }
     mark(se, ST_LEAF, true, st);
     VFMM_CUDA(cudaGetLastError());
     if (se) se->launches += launches;

@@ -78,6 +78,7 @@ struct MixedOps {
     void* s2l_sl = nullptr;   // bf16 [20][Rx][kSlices][Kp]: S2L rows of coefficients 1..p
     int* s2l_E = nullptr;     // [Rx]
     double* s2l_r0 = nullptr; // [20][kk] FP64: Re of S2L row 0
+    double* m2l_r0 = nullptr; // [40][p+1] complex FP64: M2L row 0 (output coefficient 0) per offset
 };
 
 struct MixedWork {
@@ -97,6 +98,7 @@ struct MixedWork {
     void* aprep = nullptr;                // bf16 [n_far_slots][kSlices][Kx]
     int* Et = nullptr;                    // [n_leaves]
     float2* far_out = nullptr;            // [n_leaves][Rp]
+    double* scal = nullptr;               // [n_leaves * R] FP64 scalar part of u per virtual leaf
     float2* part = nullptr;               // partial sums of split contractions (largest plan)
 };
 

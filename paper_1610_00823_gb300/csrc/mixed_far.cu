@@ -118,6 +118,17 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
     for (size_t r = 0; r < (size_t)kVCfg * mo->Rx; ++r)
         for (int q = 0; q < mo->Kx; ++q) MR[r * mo->Kx + q] = std::ldexp(MR[r * mo->Kx + q], -(q >> 2));
     VFMM_CHECK(slice_table(MR, kVCfg, mo->Rx, mo->Kx, mo->Rx, mo->Kx, &mo->m2l_sl, &mo->m2l_E, st));
+    {
+        // output coefficient 0 stays FP64: its row of every M2L matrix, [offset][n] complex
+        std::vector<double> r0((size_t)kVCfg * P * 2);
+        for (int c = 0; c < kVCfg; ++c)
+            for (int n = 0; n <= p; ++n) {
+                r0[((size_t)c * P + n) * 2] = mt[(((size_t)c * P + n) * P + 0) * 2];
+                r0[((size_t)c * P + n) * 2 + 1] = mt[(((size_t)c * P + n) * P + 0) * 2 + 1];
+            }
+        VFMM_CUDA(cudaMalloc(&mo->m2l_r0, r0.size() * sizeof(double)));
+        VFMM_CUDA(cudaMemcpy(mo->m2l_r0, r0.data(), r0.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
     VFMM_CHECK(make_table_map(mo->m2l_sl, (int64_t)kVCfg * mo->Rx, mo->Kx, &mo->tm_m2l));
     // leaf tables: 0 = L2T without coefficient 0, 1 + c = M2T of W configuration c
     std::vector<double> l2t((size_t)R * 2 * P), xh(k);
@@ -178,7 +189,8 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
 }
 
 void far_free(MixedOps* mo) {
-    void* ps[] = {mo->s2m_sl, mo->s2m_E, mo->m2l_sl, mo->m2l_E, mo->far_sl, mo->far_E, mo->s2l_sl, mo->s2l_E, mo->s2l_r0};
+    void* ps[] = {mo->s2m_sl, mo->s2m_E, mo->m2l_sl, mo->m2l_E, mo->far_sl, mo->far_E,
+                  mo->s2l_sl, mo->s2l_E, mo->s2l_r0, mo->m2l_r0};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
