@@ -254,7 +254,7 @@ def run_batch(args):
         from paper_1610_00823_gb300 import build as b
         b.build()
     import paper_1610_00823_gb300 as v
-    from paper_1610_00823_gb300.api import Batch, solve_work, volume_potential_profiled, workspace
+    from paper_1610_00823_gb300.api import Batch, solve_work, tune, volume_potential_profiled, workspace
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
@@ -273,7 +273,10 @@ def run_batch(args):
         items = []
         for (wl, _), tree, f in zip(members, trees, fs):
             out = tuple(torch.empty_like(f) for _ in range(3))
-            items.append((tree, ops[wl.k], f, out, workspace(tree, ops[wl.k], 1)))
+            ws = workspace(tree, ops[wl.k], 1)
+            if precision == v.MIXED and not args.no_tune:
+                tune(tree, ops[wl.k], f, out, ws, stream)  # split-K autotuner, per member
+            items.append((tree, ops[wl.k], f, out, ws))
         return ops, items
 
     def time_graph(items, steps, clk=None, streams=None):
@@ -401,6 +404,7 @@ def main():
                     help="with --precision mixed, skip timing the plain FP64 form on the same tree")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of CUDA-graph replays")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default split-K factors (no autotuner run)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -429,7 +433,7 @@ def main():
         from paper_1610_00823_gb300 import build as b
         b.build()
     import paper_1610_00823_gb300 as v
-    from paper_1610_00823_gb300.api import SolveGraph, solve_work, volume_potential_profiled, workspace
+    from paper_1610_00823_gb300.api import SolveGraph, solve_work, tune, volume_potential_profiled, workspace
 
     src = wl.sources[0]
     t0 = time.perf_counter()
@@ -455,10 +459,13 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
 
+    tuned_ = [None]
+
     def time_form(ops_, steps, clk=None):
         """Warm-up, then `steps` timed solves (CUDA-graph replays unless --no-graph), L2 flushed between."""
         out_ = tuple(torch.empty_like(f) for _ in range(3))
         ws_ = workspace(tree, ops_, nrhs)
+        tuned_[0] = tune(tree, ops_, f, out_, ws_, stream) if not args.no_tune else None  # split-K autotuner
         # the solve is captured once into a CUDA graph; every timed step replays it
         graph_ = SolveGraph(tree, ops_, f, out_, ws_, stream) if not args.no_graph else None
 
@@ -496,6 +503,7 @@ def main():
 
     clk = ClockSampler(local)
     step_ms, out, ws, graph = time_form(ops, args.steps, clk)
+    split_k = tuned_[0]
     # stage times (CUDA events between stages on the same stream) from separate profiled solves
     stage_acc, launches, n_prof = {}, 0, 3
     for _ in range(n_prof):
@@ -590,6 +598,7 @@ def main():
                            "l2": "flushed between timed steps (256 MB write outside the events)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "launch": "CUDA graph replay" if graph is not None else "direct calls",
+                           "split_k": split_k,
                            "tree_build_s": t_tree, "ops_create_s": t_ops},
                 "stage_ms": stage_ms,
                 "roofline": roof,

@@ -266,6 +266,18 @@ int vfmm_batch_tune(vfmm_batch* batch, int32_t n, const vfmm_batch_item* items, 
                     int32_t* best_streams, float* best_ms);
 int vfmm_batch_streams(const vfmm_batch* batch, int32_t* active);
 
+/* Schedule autotuner (no counterpart in the paper): for the VFMM_MIXED form, times each small
+ * split contraction of this tree and nrhs (near field, M2L, S2L, leaf far field: those with fewer
+ * CTAs than two per SM) with split-K factors 1, 2, 4, 8 on the caller's data, keeps the fastest
+ * in the tree's schedule (used by every later call with this nrhs) and returns them in
+ * splits[4] (near, M2L, S2L, far; may be NULL). Runs two ordinary solves around the timing, so
+ * u, u_x, u_y hold the solution afterwards; synchronises `stream`. Must not overlap other calls
+ * on the same tree; graphs captured earlier keep the schedule they captured. No-op (splits = 1)
+ * for VFMM_FP64. Errors as vfmm_volume_potential. */
+int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs, double* u_dev,
+              double* ux_dev, double* uy_dev, void* workspace_dev, size_t workspace_bytes, void* stream,
+              int32_t* splits);
+
 /* Work accounting for roofline reports, for a call with nrhs right-hand sides: out[VFMM_N_WORK] =
  * [0] BF16 tensor-core FLOPs the near-field contraction issues per call (VFMM_MIXED: every
  *     slice product of every tile, zero-padded rows included; 0 for VFMM_FP64),

@@ -236,6 +236,16 @@ def volume_potential_noalloc(tree: Tree, ops: Ops, f, out=None, stream=None):
     return out
 
 
+def tune(tree: Tree, ops: Ops, f, out, ws, stream=None):
+    """Split-K autotuner (vfmm_tune): returns the chosen factors {near, m2l, s2l, far}; out holds the solution."""
+    n = tree.n_leaves * tree.k * tree.k
+    splits = np.zeros(4, dtype=np.int32)
+    call("vfmm_tune", tree.handle, ops.handle, ctypes.c_void_p(f.data_ptr()), f.numel() // n,
+         ctypes.c_void_p(out[0].data_ptr()), ctypes.c_void_p(out[1].data_ptr()), ctypes.c_void_p(out[2].data_ptr()),
+         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream), splits.ctypes.data_as(c_int32_p))
+    return dict(zip(("near", "m2l", "s2l", "far"), splits.tolist()))
+
+
 WORK = ("near_tc_flops", "m2l_tc_flops", "far_tc_flops", "s2l_tc_flops", "s2m_tc_flops", "near_fp64eq_flops",
         "u_entries", "reserved")
 

@@ -490,21 +490,13 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
     }
 }
 
-// Mixed form: the downward pass reduces to a per-coefficient combine (M2L, S2L and the FP64
-// coefficient 0 are already computed): one thread per (virtual box, coefficient), level by level.
-__global__ void down_mixed_kernel(DownArgs d) {
-    const int P = d.P, R = d.R;
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)(d.end - d.begin) * R * P) return;
-    const size_t vb = (size_t)d.begin * R + (size_t)(q / P);
-    const int t = (int)(q % P);
-    const int b = (int)(vb / R), r = (int)(vb % R);
-    const double h = ldexp(d.width, -d.level);
-    double re = 0.0, im = 0.0;
-    if (d.level >= 3) {  // L2L from the parent, written by the translation kernel just before
-        re = d.Lexp[vb * 2 * P + 2 * t];
-        im = d.Lexp[vb * 2 * P + 2 * t + 1];
-    }
+// Mixed form: coefficient t of the local expansion of virtual box (b, r) at `level` = the L2L
+// value (re, im) plus the split-precision M2L and S2L outputs scaled back by their exponents and
+// the FP64 coefficient 0 (V and X rows 0 with the log(h) terms).
+__device__ __forceinline__ double2 combine_local(const DownArgs& d, int level, int b, int r, int t, double re,
+                                                 double im) {
+    const size_t vb = (size_t)b * d.R + r;
+    const double h = ldexp(d.width, -level);
     const bool has_v = d.vptr[b + 1] > d.vptr[b], has_x = d.xptr[b + 1] > d.xptr[b];
     if (has_x && t >= 1) {
         const float2 vr = d.s2l_out[vb * d.Rx + 2 * (t - 1)];
@@ -519,13 +511,204 @@ __global__ void down_mixed_kernel(DownArgs d) {
         } else if (has_v) {
             const float2 vr = d.m2l_out[vb * d.Rx + 2 * (t - 1)];
             const float2 vi = d.m2l_out[vb * d.Rx + 2 * (t - 1) + 1];
-            const int g = d.m2l_G[(size_t)d.level * R + r];
+            const int g = d.m2l_G[(size_t)level * d.R + r];
             re += ((double)vr.x + (double)vr.y) * pow2(g + d.m2l_E[2 * (t - 1)]);
             im += ((double)vi.x + (double)vi.y) * pow2(g + d.m2l_E[2 * (t - 1) + 1]);
         }
     }
-    d.Lexp[vb * 2 * P + 2 * t] = re;
-    d.Lexp[vb * 2 * P + 2 * t + 1] = im;
+    return make_double2(re, im);
+}
+
+// Mixed form, one level: one thread per (virtual box, coefficient).
+__global__ void down_mixed_kernel(DownArgs d) {
+    const int P = d.P, R = d.R;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)(d.end - d.begin) * R * P) return;
+    const size_t vb = (size_t)d.begin * R + (size_t)(q / P);
+    const int t = (int)(q % P);
+    const int b = (int)(vb / R), r = (int)(vb % R);
+    double re = 0.0, im = 0.0;
+    if (d.level >= 3) {  // L2L from the parent, written by the translation kernel just before
+        re = d.Lexp[vb * 2 * P + 2 * t];
+        im = d.Lexp[vb * 2 * P + 2 * t + 1];
+    }
+    const double2 v = combine_local(d, d.level, b, r, t, re, im);
+    d.Lexp[vb * 2 * P + 2 * t] = v.x;
+    d.Lexp[vb * 2 * P + 2 * t + 1] = v.y;
+}
+
+// ---------------------------------------------------------------- persistent tree passes
+// One cooperative launch walks all levels: CTAs take groups of 128 threads per virtual box, the
+// 4 position tables sit in shared memory for the whole pass, and a bounded grid barrier separates
+// the levels. Data written by other CTAs in an earlier level are read through L2 (ld.global.cg).
+constexpr int kPassGroups = 4;                  // 128-thread groups per CTA
+constexpr int kPassThreads = 128 * kPassGroups;
+
+// Grid barrier: every CTA adds one to *count and waits (bounded) for `target`.
+__device__ bool grid_sync(unsigned int* count, unsigned int target, int* err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        int good = 1;
+        for (long long it = 0;; ++it) {
+            if (*(volatile unsigned int*)count >= target) break;
+            if (it > (1ll << 24)) {
+                good = 0;
+                if (err) atomicExch(err, 6);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ void group_sync(int group) {
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + group) : "memory");
+}
+
+// Loads the 4 position tables into shared memory (bulk copy); one decision for the whole CTA.
+__device__ bool load_tables(double2* sT, const double2* tab, int P, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int no_abort;
+    const uint32_t bar_a = tc::smem_u32(&bar);
+    const uint32_t bytes = (uint32_t)(4 * P * P) * sizeof(double2);
+    if (threadIdx.x == 0) {
+        no_abort = 0;
+        tc::mbar_init(bar_a, 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::mbar_arrive_expect_tx(bar_a, bytes);
+        constexpr uint32_t kChunk = 32768;
+        for (uint32_t off = 0; off < bytes; off += kChunk)
+            tc::bulk_copy_g2s(tc::smem_u32(sT) + off, reinterpret_cast<const char*>(tab) + off,
+                              min(kChunk, bytes - off), bar_a);
+    }
+    const bool landed = tc::mbar_wait(bar_a, 0, &no_abort);
+    if (!__syncthreads_and(landed)) {
+        if (threadIdx.x == 0 && err) atomicExch(err, 5);
+        return false;
+    }
+    return true;
+}
+
+// Triangular translation of one virtual box by one 128-thread group (see translate_kernel):
+// mode 0 = M2M (in: 4 child multipoles), 1 = L2L (in: parent local); s_out[pos][o] results.
+__device__ __forceinline__ void translate_group(int mode, const double2* sT, const double2* s_in, double2* s_out,
+                                                int P, int gt) {
+    const int npair = (P + 1) / 2;
+    for (int task = gt; task < 4 * npair; task += 128) {
+        const int pos = task / npair, j = task - pos * npair;
+        const double2* M = sT + pos * P * P;
+        const double2* x = mode == 0 ? s_in + pos * P : s_in;
+        for (int half = 0; half < 2; ++half) {
+            const int o = half == 0 ? j : P - 1 - j;
+            if (half == 1 && o == j) break;
+            const int n0 = mode == 0 ? 0 : o, n1 = mode == 0 ? o : P - 1;
+            double re = 0.0, im = 0.0;
+            for (int n = n0; n <= n1; ++n) {
+                const double2 m = M[n * P + o], v = x[n];
+                re = fma(m.x, v.x, fma(-m.y, v.y, re));
+                im = fma(m.x, v.y, fma(m.y, v.x, im));
+            }
+            s_out[pos * P + o] = make_double2(re, im);
+        }
+    }
+}
+
+struct PassArgs {
+    int depth, R, P;
+    const int32_t* nonleaf;
+    const int32_t* nonleaf_start;  // device, depth + 2
+    const int32_t* level_start;    // device, depth + 2
+    const int32_t* child0;
+    const double2* tab;
+    double2* ex;           // Mexp (upward) or Lexp (downward), [n_boxes * R][P] complex
+    unsigned int* count;   // grid-barrier counter, zero at launch
+    int* err;
+};
+
+// All M2M levels, finest parents first.
+__global__ void __launch_bounds__(kPassThreads, 1) upward_pass_kernel(PassArgs a) {
+    extern __shared__ __align__(128) unsigned char pass_raw[];
+    const int P = a.P, R = a.R;
+    double2* sT = reinterpret_cast<double2*>(pass_raw);
+    const int group = threadIdx.x >> 7, gt = threadIdx.x & 127;
+    double2* s_in = sT + 4 * P * P + group * 8 * P;
+    double2* s_out = s_in + 4 * P;
+    if (!load_tables(sT, a.tab, P, a.err)) return;
+    unsigned int target = 0;
+    for (int l = a.depth - 1; l >= 2; --l) {
+        const int nb0 = a.nonleaf_start[l], nbox = a.nonleaf_start[l + 1] - nb0;
+        for (int item = group * gridDim.x + blockIdx.x; item < nbox * R; item += gridDim.x * kPassGroups) {
+            const int bi = item / R, r = item - bi * R;
+            const int b = a.nonleaf[nb0 + bi], c0 = a.child0[b];
+            for (int q = gt; q < 4 * P; q += 128) s_in[q] = __ldcg(&a.ex[((size_t)(c0 + q / P) * R + r) * P + q % P]);
+            group_sync(group);
+            translate_group(0, sT, s_in, s_out, P, gt);
+            group_sync(group);
+            for (int o = gt; o < P; o += 128) {
+                const double2 a0 = s_out[o], a1 = s_out[P + o], a2 = s_out[2 * P + o], a3 = s_out[3 * P + o];
+                a.ex[((size_t)b * R + r) * P + o] =
+                    make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+            }
+            group_sync(group);
+        }
+        target += gridDim.x;
+        if (!grid_sync(a.count, target, a.err)) return;
+    }
+}
+
+// Mixed form, all downward levels: level 2 boxes combine their M2L/S2L terms; below, each
+// non-leaf parent's local is shifted to its 4 children (L2L) and each child's terms are added.
+__global__ void __launch_bounds__(kPassThreads, 1) downward_pass_kernel(PassArgs a, DownArgs d) {
+    extern __shared__ __align__(128) unsigned char pass_raw[];
+    const int P = a.P, R = a.R;
+    double2* sT = reinterpret_cast<double2*>(pass_raw);
+    const int group = threadIdx.x >> 7, gt = threadIdx.x & 127;
+    double2* s_in = sT + 4 * P * P + group * 8 * P;
+    double2* s_out = s_in + 4 * P;
+    if (!load_tables(sT, a.tab, P, a.err)) return;
+    // level 2: no parent term
+    {
+        const int b0 = a.level_start[2], n2 = a.level_start[3] - b0;
+        const int64_t total = (int64_t)n2 * R * P;
+        for (int64_t q = (int64_t)blockIdx.x * kPassThreads + threadIdx.x; q < total;
+             q += (int64_t)gridDim.x * kPassThreads) {
+            const int t = (int)(q % P);
+            const int64_t vb = (int64_t)b0 * R + q / P;
+            const int b = (int)(vb / R), r = (int)(vb % R);
+            const double2 v = combine_local(d, 2, b, r, t, 0.0, 0.0);
+            a.ex[(size_t)vb * P + t] = v;
+        }
+    }
+    unsigned int target = gridDim.x;
+    if (!grid_sync(a.count, target, a.err)) return;
+    for (int l = 3; l <= a.depth; ++l) {
+        const int nb0 = a.nonleaf_start[l - 1], nbox = a.nonleaf_start[l] - nb0;
+        for (int item = group * gridDim.x + blockIdx.x; item < nbox * R; item += gridDim.x * kPassGroups) {
+            const int bi = item / R, r = item - bi * R;
+            const int b = a.nonleaf[nb0 + bi], c0 = a.child0[b];
+            for (int q = gt; q < P; q += 128) s_in[q] = __ldcg(&a.ex[((size_t)b * R + r) * P + q]);
+            group_sync(group);
+            translate_group(1, sT, s_in, s_out, P, gt);
+            group_sync(group);
+            for (int q = gt; q < 4 * P; q += 128) {
+                const int c = c0 + q / P, t = q % P;
+                a.ex[((size_t)c * R + r) * P + t] = combine_local(d, l, c, r, t, s_out[q].x, s_out[q].y);
+            }
+            group_sync(group);
+        }
+        target += gridDim.x;
+        if (!grid_sync(a.count, target, a.err)) return;
+    }
 }
 
 // Mixed form, per virtual leaf (leaf, r): the FP64 scalar part of u at every node of the leaf,
@@ -671,6 +854,7 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
 // ---------------------------------------------------------------- host side
 struct Workspace {
     const PlanSet* ps;  // split-contraction plans for the folded right-hand sides (mixed form)
+    unsigned int* gbar; // [2] grid-barrier counters of the persistent tree passes
     double* Mexp;
     double* Lexp;
     double* slab;
@@ -697,6 +881,11 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
     const size_t R = mixed ? (size_t)nrhs : 1;
     take(w ? &w->Mexp : &dummy, (size_t)T.n_boxes * R * P2);
     take(w ? &w->Lexp : &dummy, (size_t)T.n_boxes * R * P2);
+    {
+        double* g = nullptr;
+        take(&g, 1);
+        if (w) w->gbar = reinterpret_cast<unsigned int*>(g);
+    }
     take(w ? &w->slab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
     take(w ? &w->far : &dummy, mixed ? 1 : (size_t)T.n_leaves * 3 * kk);
     if (mixed) {
@@ -815,6 +1004,46 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     d.Rx = mo ? mo->Rx : 0;
 }
 
+// Persistent passes (one cooperative launch for all levels) when every level is small enough that
+// per-level launches would mostly wait on launch latency; larger levels keep one launch per level.
+static bool use_passes(const DeviceTree& T, int R, int P) {
+    const size_t smem = (size_t)(4 * P * P + kPassGroups * 8 * P) * sizeof(double2);
+    if (smem > 200 * 1024 || T.depth < 3) return false;
+    int widest = 0;
+    for (int l = 1; l <= T.depth; ++l) widest = std::max(widest, T.nonleaf_start[l + 1] - T.nonleaf_start[l]);
+    return (long long)widest * R <= 16ll * sm_count();
+}
+
+template <typename... Args>
+static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, cudaStream_t st, Args... args) {
+    const size_t smem = (size_t)(4 * P * P + kPassGroups * 8 * P) * sizeof(double2);
+    static thread_local int attr_dev[2] = {-1, -1};
+    const int slot = (void*)kernel == (void*)upward_pass_kernel ? 0 : 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev[slot] != dev) {
+        VFMM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_dev[slot] = dev;
+    }
+    int per_sm = 0;
+    VFMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPassThreads, smem));
+    if (per_sm < 1) return fail(VFMM_ERR_INTERNAL, "tree pass kernel does not fit on an SM");
+    // items go to group 0 of every CTA first, so one CTA per item up to one CTA per SM
+    const int grid = std::max(1, std::min(per_sm * sm_count(), widest_items));
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kPassThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    VFMM_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
+    return VFMM_OK;
+}
+
 // One solve of R right-hand sides (f: [R][n_leaves][k^2]). The mixed form folds them into the
 // rows of every contraction (PS holds plans for R); the FP64 form takes R = 1.
 static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* u,
@@ -846,9 +1075,30 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
     mark(se, ST_S2M, true, st);
     // M2M, finest parents first (levels >= 2 are the ones the lists read)
     mark(se, ST_M2M, false, st);
-    for (int l = T.depth - 1; l >= 2; --l) {
-        if (T.nonleaf_start[l + 1] > T.nonleaf_start[l]) ++launches;
-        launch_translate(0, T, l, R, P, o.m2m_t, w.Mexp, w.mix.err, st);
+    const bool passes = use_passes(T, R, P);
+    int widest = 0;
+    for (int l = 1; l <= T.depth; ++l) widest = std::max(widest, T.nonleaf_start[l + 1] - T.nonleaf_start[l]);
+    if (passes) {
+        VFMM_CUDA(cudaMemsetAsync(w.gbar, 0, 2 * sizeof(unsigned int), st));
+        PassArgs pa;
+        pa.depth = T.depth;
+        pa.R = R;
+        pa.P = P;
+        pa.nonleaf = T.nonleaf;
+        pa.nonleaf_start = T.nonleaf_start_dev;
+        pa.level_start = T.level_start_dev;
+        pa.child0 = T.child0;
+        pa.tab = reinterpret_cast<const double2*>(o.m2m_t);
+        pa.ex = reinterpret_cast<double2*>(w.Mexp);
+        pa.count = w.gbar;
+        pa.err = w.mix.err;
+        VFMM_CHECK(launch_pass(upward_pass_kernel, R, P, widest * R, st, pa));
+        ++launches;
+    } else {
+        for (int l = T.depth - 1; l >= 2; --l) {
+            if (T.nonleaf_start[l + 1] > T.nonleaf_start[l]) ++launches;
+            launch_translate(0, T, l, R, P, o.m2m_t, w.Mexp, w.mix.err, st);
+        }
     }
     mark(se, ST_M2M, true, st);
     // downward pass
@@ -874,7 +1124,25 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, st));
         launches += 1 + (PS.s2l.n_groups > 0) + (PS.s2l.n_groups > 0 && PS.s2l.split > 1);
     }
-    for (int l = 2; l <= T.depth; ++l) {
+    if (mixed && passes) {
+        DownArgs d;
+        fill_down_args(d, T, o, f, w, 2, R);
+        PassArgs pa;
+        pa.depth = T.depth;
+        pa.R = R;
+        pa.P = P;
+        pa.nonleaf = T.nonleaf;
+        pa.nonleaf_start = T.nonleaf_start_dev;
+        pa.level_start = T.level_start_dev;
+        pa.child0 = T.child0;
+        pa.tab = reinterpret_cast<const double2*>(o.l2l_t);
+        pa.ex = reinterpret_cast<double2*>(w.Lexp);
+        pa.count = w.gbar + 1;
+        pa.err = w.mix.err;
+        VFMM_CHECK(launch_pass(downward_pass_kernel, R, P, std::max(widest * R, 16 * R), st, pa, d));
+        ++launches;
+    }
+    for (int l = 2; l <= T.depth && !(mixed && passes); ++l) {
         DownArgs d;
         fill_down_args(d, T, o, f, w, l, R);
         int n = d.end - d.begin;
@@ -1126,4 +1394,78 @@ extern "C" int vfmm_graph_destroy(vfmm_graph* g) {
     if (g->graph) cudaGraphDestroy(g->graph);
     delete g;
     return VFMM_OK;
+}
+
+// ---------------------------------------------------------------- schedule autotuner
+extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs, double* u_dev,
+                         double* ux_dev, double* uy_dev, void* workspace_dev, size_t workspace_bytes, void* stream,
+                         int32_t* splits) {
+    VFMM_CHECK(check_solve_args(tree, ops, nrhs));
+    if (!f_dev || !u_dev || !ux_dev || !uy_dev || !workspace_dev) return fail(VFMM_ERR_INVALID_ARG, "null buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace w;
+    size_t need = 0;
+    VFMM_CHECK(layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev, &need));
+    if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small");
+    if (splits)
+        for (int i = 0; i < 4; ++i) splits[i] = 1;
+    if (ops->precision != VFMM_MIXED) return VFMM_OK;
+    const DeviceTree& T = tree->t;
+    const MixedOps* mo = (const MixedOps*)ops->mixed;
+    // one solve leaves every contraction's operands in the workspace
+    VFMM_CHECK(reset_status(w, st));
+    VFMM_CHECK(solve_all(T, *ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, w, st));
+    VFMM_CUDA(cudaStreamSynchronize(st));
+    PlanSet* PS = const_cast<PlanSet*>(w.ps);
+    const size_t R = (size_t)PS->R;
+    struct Job {
+        SplitPlan* P;
+        const void* a;
+        const CUtensorMap* map;
+        int Kp, Rp;
+        float2* out;
+        size_t rows;
+    } jobs[4] = {{&PS->near, w.mix.fsl, &mo->tm_near, mo->Kp, mo->Rp, w.mix.out, T.n_leaves * R},
+                 {&PS->m2l, w.mix.msl, &mo->tm_m2l, mo->Kx, mo->Rx, w.mix.m2l_out, T.n_boxes * R},
+                 {&PS->s2l, w.mix.fsl, &mo->tm_s2l, mo->Kp, mo->Rx, w.mix.s2l_out, T.n_boxes * R},
+                 {&PS->far, w.mix.aprep, &mo->tm_far, mo->Kx, mo->Rp, w.mix.far_out, T.n_leaves * R}};
+    cudaEvent_t e0, e1;
+    VFMM_CUDA(cudaEventCreate(&e0));
+    VFMM_CUDA(cudaEventCreate(&e1));
+    int rc = VFMM_OK;
+    for (int j = 0; j < 4 && rc == VFMM_OK; ++j) {
+        Job& jb = jobs[j];
+        if (!jb.P->may_split || jb.P->n_groups == 0) continue;
+        const double avg_cfg = (double)jb.P->entries / jb.P->n_groups;
+        int best = jb.P->split;
+        float best_ms = -1.0f;
+        for (int sp = 1; sp <= kMaxSplit && sp <= std::max(1.0, avg_cfg) && rc == VFMM_OK; sp *= 2) {
+            jb.P->split = sp;
+            float total = 0.0f;
+            for (int rep = 0; rep < 4 && rc == VFMM_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                rc = split_gemm(*jb.P, jb.a, *jb.map, jb.Kp, jb.Rp, jb.out, w.mix.err, w.mix.part, jb.rows, st);
+                cudaEventRecord(e1, st);
+                if (rc != VFMM_OK) break;
+                cudaError_t e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) rc = cuda_fail(e, "timing a split contraction");
+                if (rep > 0) total += ms;  // the first run warms up
+            }
+            if (rc == VFMM_OK && (best_ms < 0.0f || total < best_ms)) {
+                best_ms = total;
+                best = sp;
+            }
+        }
+        jb.P->split = best;
+        if (splits) splits[j] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    VFMM_CHECK(rc);
+    // leave the outputs of an ordinary solve with the chosen schedule
+    VFMM_CHECK(solve_all(T, *ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, w, st));
+    VFMM_CUDA(cudaStreamSynchronize(st));
+    return read_status(w);
 }

@@ -468,9 +468,23 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t ctas = (int64_t)std::max(ng, 1) * n_chunks;
-        const int64_t avg_cfg = ng ? (P->entries + ng - 1) / ng : 1;
+        const double avg_cfg = ng ? (double)P->entries / ng : 1.0;
+        // split-K over tables only for small contractions (fewer than two CTAs per SM): default = the
+        // split minimising (CTAs / SMs, at least 1) x (tables per CTA + about one table of fixed cost);
+        // vfmm_tune replaces it by timing
         int split = 1;
-        while (ctas * split < 2 * sms && avg_cfg / (split * 2) >= 2) split *= 2;
+        P->may_split = ctas < 2 * sms;
+        if (ctas < 2 * sms) {
+            double best = 1e300;
+            for (int sp = 1; sp <= kMaxSplit && sp <= std::max(1.0, avg_cfg); sp *= 2) {
+                const double waves = std::max(1.0, (double)(ctas * sp) / sms);
+                const double est = waves * (avg_cfg / sp + 1.0);
+                if (est < best - 1e-9) {
+                    best = est;
+                    split = sp;
+                }
+            }
+        }
         P->split = split;
     }
     auto up = [](int32_t** dst, const std::vector<int32_t>& v) -> int {

@@ -26,6 +26,7 @@ constexpr int kEpilogueThreads = 32 * kEpilogueWarps;
 constexpr int kProducerThreads = 96;
 constexpr int kMmaWarp = kEpilogueWarps + kProducerThreads / 32;  // 11
 constexpr int kThreads = 32 * (kMmaWarp + 1);                     // 384: 3 warps per SM sub-partition
+constexpr int kMaxSplit = 8;  // largest split-K factor (partial sums held for small contractions only)
 static_assert(kNumAcc * kTileN <= kTmemCols, "TMEM budget");
 
 // Splits v / 2^E (|v| < 2^E) into kSlices signed base-64 digits, out[(i - 1) * stride] =

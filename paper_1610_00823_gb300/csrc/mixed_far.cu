@@ -303,14 +303,20 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
     return VFMM_OK;
 }
 
-// Largest partial-sum buffer any split contraction of this plan set needs (float2 elements).
+// Largest partial-sum buffer any split contraction of this plan set may need (float2 elements):
+// room for kMaxSplit partial sets wherever a contraction may split (so that vfmm_tune can pick any
+// factor without a new workspace), the current factor elsewhere.
 size_t split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     const size_t R = (size_t)PS.R;
-    size_t a = PS.near.split > 1 ? (size_t)PS.near.split * T.n_leaves * R * mo->Rp : 0;
-    size_t b = PS.m2l.split > 1 ? (size_t)PS.m2l.split * T.n_boxes * R * mo->Rx : 0;
-    size_t c = PS.far.split > 1 ? (size_t)PS.far.split * T.n_leaves * R * mo->Rp : 0;
-    size_t d = PS.s2l.split > 1 ? (size_t)PS.s2l.split * T.n_boxes * R * mo->Rx : 0;
+    auto need = [](const SplitPlan& P, size_t rows, int Rp) -> size_t {
+        const int f = P.may_split ? kMaxSplit : P.split;
+        return f > 1 ? (size_t)f * rows * Rp : 0;
+    };
+    size_t a = need(PS.near, T.n_leaves * R, mo->Rp);
+    size_t b = need(PS.m2l, T.n_boxes * R, mo->Rx);
+    size_t c = need(PS.far, T.n_leaves * R, mo->Rp);
+    size_t d = need(PS.s2l, T.n_boxes * R, mo->Rx);
     return std::max(std::max(a, d), std::max(b, c));
 }
 

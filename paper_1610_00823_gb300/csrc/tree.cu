@@ -852,6 +852,9 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
         VFMM_CUDA(cudaMalloc(&T->nonleaf, std::max<size_t>(1, nl.size()) * sizeof(int32_t)));
         if (!nl.empty())
             VFMM_CUDA(cudaMemcpy(T->nonleaf, nl.data(), nl.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        VFMM_CUDA(cudaMalloc(&T->nonleaf_start_dev, (depth + 2) * sizeof(int32_t)));
+        VFMM_CUDA(cudaMemcpy(T->nonleaf_start_dev, T->nonleaf_start.data(), (depth + 2) * sizeof(int32_t),
+                             cudaMemcpyHostToDevice));
     }
     VFMM_CHECK(build_mixed_plan(T));
     return VFMM_OK;
@@ -860,7 +863,7 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
 void free_tree(DeviceTree* t) {
     void* ps[] = {t->key,         t->level,       t->ix,       t->iy,           t->parent,     t->child0,
                   t->leaf_of_box, t->box_of_leaf, t->level_start_dev, t->u_by_cfg, t->u_tgt, t->near_tiles,
-                  t->far_slot,    t->nonleaf};
+                  t->far_slot,    t->nonleaf,     t->nonleaf_start_dev};
     free_plan_set(&t->plans);
     if (t->plans_r) {
         for (auto& kv : *t->plans_r) {

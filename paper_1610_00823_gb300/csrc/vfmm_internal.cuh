@@ -164,6 +164,7 @@ struct SplitPlan {
     int32_t* cfg = nullptr;  // [entries] table index
     int32_t* src = nullptr;  // [entries][128] A row or -1
     int32_t split = 1;       // CTAs per group (each takes a share of the group's tables)
+    bool may_split = false;  // small contraction (fewer CTAs than two per SM): split-K allowed
 };
 
 // The split contractions of the mixed form with R right-hand sides folded into the rows: the
@@ -211,6 +212,7 @@ struct DeviceTree {
     std::mutex* plans_mu = nullptr;
     int32_t* nonleaf = nullptr;           // non-leaf boxes in canonical order (grouped by level)
     std::vector<int32_t> nonleaf_start;   // host, depth + 2: first entry of each level
+    int32_t* nonleaf_start_dev = nullptr; // device copy
     int32_t* far_slot = nullptr;  // [n_leaves + 1] first A row of each leaf in the far operand
     int64_t n_far_slots = 0;
 };

@@ -137,3 +137,24 @@ def test_folded_rhs_adaptive_tree_and_graph():
     stream.synchronize()
     for q in range(3):
         assert torch.equal(out[q], umx[q])
+
+
+def test_autotuned_schedule_keeps_results():
+    """vfmm_tune picks split-K factors by timing; the solution it leaves and later solves with the
+    tuned schedule stay within the bar of the FP64 form."""
+    from paper_1610_00823_gb300.api import tune
+    src = W.narrow_gaussians(8, n=2, sigma=0.01, spread=0.4)
+    gt = v.tree_build(0.0, 0.0, 1.0, 16, src, 1e-10, 9)
+    f = v.source_sample(gt, src)
+    u64 = v.volume_potential(gt, v.ops_create(16, 40, v.FP64), f)
+    ops = v.ops_create(16, 40, v.MIXED)
+    out = tuple(torch.empty_like(f) for _ in range(3))
+    ws = workspace(gt, ops, 1)
+    stream = torch.cuda.Stream()
+    splits = tune(gt, ops, f, out, ws, stream)
+    assert set(splits) == {"near", "m2l", "s2l", "far"} and all(s in (1, 2, 4, 8) for s in splits.values())
+    again = v.volume_potential(gt, ops, f, ws=ws, stream=stream)
+    stream.synchronize()
+    for q in range(3):
+        assert rel(out[q].cpu().numpy(), u64[q].cpu().numpy()) < TOL
+        assert rel(again[q].cpu().numpy(), u64[q].cpu().numpy()) < TOL
