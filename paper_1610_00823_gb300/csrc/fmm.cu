@@ -27,15 +27,12 @@ namespace vfmm {
 constexpr double kInv2Pi = 0.15915494309189533577;
 
 // 2^e as a double, built from its exponent bits (exact, no libm call).
-__device__ __forceinline__ double pow2(int e) {
-    e = max(-1022, min(1023, e));
-    return __longlong_as_double((long long)(e + 1023) << 52);
-}
 
 // Re of local coefficient 0 from the V and X lists of each virtual box (box, r): sum over V of
 // Re(row 0 of M2L_c . a_c) + a_0(c) log h, and over X of (2h)^2 Re(S2L row 0) . f_c + a_0(c) log h.
 // FP64; the other coefficients come from the split-precision M2L and S2L. Persistent CTAs hold the
-// row-0 tables in shared memory; one warp per virtual box, one lane per V entry.
+// row-0 tables in shared memory; one warp per virtual box, lanes over the coefficients of each
+// source multipole (coalesced), four V entries in flight.
 __global__ void __launch_bounds__(256) m2l_c0_kernel(int begin, int end, int R, int P, double width,
                                                      const int32_t* __restrict__ level,
                                                      const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
@@ -59,14 +56,31 @@ __global__ void __launch_bounds__(256) m2l_c0_kernel(int begin, int end, int R, 
         const int b = begin + (int)(vw / R), r = (int)(vw % R);
         const double h = ldexp(width, -level[b]);
         const double logh = log(h);
+        // V list: the warp walks the entries; lane n takes coefficients n, n + 32 of the source
+        // multipole (coalesced), partial sums stay per lane until one final reduction
         double acc = 0.0;
-        for (int e = vptr[b] + lane; e < vptr[b + 1]; e += 32) {
-            const double* a = Mexp + ((size_t)vidx[e] * R + r) * 2 * P;
-            const double2* M = sM + vcfg[e] * P;
-            double re = a[0] * logh;
-#pragma unroll 8
-            for (int n = 0; n < P; ++n) re += M[n].x * a[2 * n] - M[n].y * a[2 * n + 1];
-            acc += re;
+        const int e_end = vptr[b + 1];
+        for (int e0 = vptr[b]; e0 < e_end; e0 += 4) {
+            // four entries at a time, every load issued before the arithmetic
+            double2 x[4][2];
+            int cf[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool live = e0 + j < e_end;
+                const double2* a =
+                    reinterpret_cast<const double2*>(Mexp + ((size_t)vidx[live ? e0 + j : e0] * R + r) * 2 * P);
+                cf[j] = live ? vcfg[e0 + j] : -1;
+                x[j][0] = live && lane < P ? a[lane] : make_double2(0.0, 0.0);
+                x[j][1] = live && lane + 32 < P ? a[lane + 32] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (cf[j] < 0) continue;
+                const double2* M = sM + cf[j] * P;
+                if (lane < P) acc += M[lane].x * x[j][0].x - M[lane].y * x[j][0].y;
+                if (lane + 32 < P) acc += M[lane + 32].x * x[j][1].x - M[lane + 32].y * x[j][1].y;
+                if (lane == 0) acc += x[j][0].x * logh;
+            }
         }
         // X list: (2h)^2 [Re(S2L row 0) . f_c + log(h) W . f_c], with W . f_c = a_0(c) / (2h)^2
         for (int e = xptr[b]; e < xptr[b + 1]; ++e) {
@@ -738,25 +752,25 @@ __global__ void leaf_mixed_kernel(int nleaf, int R, int kk, int Rp, double width
                                   const int* __restrict__ farE, const int* __restrict__ Et,
                                   const double* __restrict__ scal, double* __restrict__ u, double* __restrict__ ux,
                                   double* __restrict__ uy) {
+    const double w2h = width * width;
     const int64_t total = (int64_t)nleaf * R * kk;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t vl = q / kk;
         const int t = (int)(q % kk);
         const int leaf = (int)(vl / R), r = (int)(vl % R);
         const int lv = level[box_of_leaf[leaf]];
-        const double h = width * pow2(-lv), ih = inv_width * pow2(lv);
         const float2* nm = nearmix + (size_t)vl * Rp;
         const float2* fm = farmix + (size_t)vl * Rp;
-        const int ef = Ef[r], et = Et[vl];
+        const int ef = Ef[r] - lv, et = Et[vl] + lv;  // h = width 2^-lv: scales are exact powers of two
         const float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
         const float2 w0 = fm[t], w1 = fm[kk + t], w2 = fm[2 * kk + t];
         const size_t o = ((size_t)r * nleaf + leaf) * kk + t;
-        u[o] = h * h * ((double)v0.x + (double)v0.y) * pow2(ef + Er[t]) + scal[vl] +
-               ((double)w0.x + (double)w0.y) * pow2(et + farE[t]);
-        ux[o] = h * ((double)v1.x + (double)v1.y) * pow2(ef + Er[kk + t]) +
-                ih * ((double)w1.x + (double)w1.y) * pow2(et + farE[kk + t]);
-        uy[o] = h * ((double)v2.x + (double)v2.y) * pow2(ef + Er[2 * kk + t]) +
-                ih * ((double)w2.x + (double)w2.y) * pow2(et + farE[2 * kk + t]);
+        u[o] = w2h * ((double)v0.x + (double)v0.y) * pow2(ef - lv + Er[t]) + scal[vl] +
+               ((double)w0.x + (double)w0.y) * pow2(et - lv + farE[t]);
+        ux[o] = width * ((double)v1.x + (double)v1.y) * pow2(ef + Er[kk + t]) +
+                inv_width * ((double)w1.x + (double)w1.y) * pow2(et + farE[kk + t]);
+        uy[o] = width * ((double)v2.x + (double)v2.y) * pow2(ef + Er[2 * kk + t]) +
+                inv_width * ((double)w2.x + (double)w2.y) * pow2(et + farE[2 * kk + t]);
     }
 }
 
@@ -1116,7 +1130,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
             cudaFuncSetAttribute(m2l_c0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
             c0_attr_dev = dev;
         }
-        const unsigned c0_grid = (unsigned)std::min<int64_t>((warps + 7) / 8, 2ll * sm_count());
+        const unsigned c0_grid = (unsigned)std::min<int64_t>((warps + 7) / 8, 3ll * sm_count());
         m2l_c0_kernel<<<c0_grid, 256, c0_smem, st>>>(
             begin, end, R, P, T.width, T.level, T.lptr[VFMM_LIST_V], T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V],
             reinterpret_cast<const double2*>(mo->m2l_r0), w.Mexp, w.mix.m2l_c0, T.lptr[VFMM_LIST_X],

@@ -49,6 +49,12 @@ __device__ __forceinline__ void slice_fixed(double v, int E, __nv_bfloat16* out,
     }
 }
 
+// 2^e as a double built from its exponent bits (e clamped to the normal range).
+__device__ __forceinline__ double pow2(int e) {
+    e = max(-1022, min(1023, e));
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
 // Binary exponent e with |m| < 2^e (frexp convention), from the bits; 0 for m = 0.
 __device__ __forceinline__ int exp_bound(double m) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(m);

@@ -344,9 +344,10 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
         }
     }
     const int ef = Ef[r];
+    const double hh = h * h;
     for (int q = threadIdx.x; q < 2 * p; q += blockDim.x) {
         float2 v = out[(size_t)vl * Rx + q];
-        M[2 + q] = h * h * ldexp((double)v.x + (double)v.y, ef + E[q]);
+        M[2 + q] = hh * (((double)v.x + (double)v.y) * pow2(ef + E[q]));
     }
 }
 
