@@ -198,8 +198,10 @@ int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const
  * cudaMalloc is available to this library). It runs vfmm_volume_potential with its
  * workspace in a fixed 32 MiB static device array that every GPU loading the library
  * holds until the process exits, and never calls cudaMalloc or cudaFree.
- *  - Size limit: trees whose vfmm_workspace_size (with_io = 0) exceeds 32 MiB are
- *    rejected with VFMM_ERR_WORKSPACE (roughly a few hundred leaves at k = 8).
+ *  - Size limit: trees whose vfmm_workspace_size (nrhs = 1, with_io = 0) exceeds 32 MiB
+ *    are rejected with VFMM_ERR_WORKSPACE (roughly a few hundred leaves at k = 8).
+ *  - Right-hand sides are solved one after another in the same scratch (the mixed form
+ *    does not fold them here, since that would build new schedules in device memory).
  *  - Set-up: the first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call before
  *    any stream capture.

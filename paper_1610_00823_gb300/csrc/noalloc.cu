@@ -50,8 +50,13 @@ extern "C" int vfmm_volume_potential_noalloc(const vfmm_tree* tree, const vfmm_o
                                              int32_t nrhs, double* u_dev, double* ux_dev, double* uy_dev,
                                              void* stream) {
     if (!tree || !ops) return fail(VFMM_ERR_INVALID_ARG, "null tree or ops");
+    if (nrhs < 1) return fail(VFMM_ERR_INVALID_ARG, "nrhs must be >= 1");
+    if (!f_dev || !u_dev || !ux_dev || !uy_dev) return fail(VFMM_ERR_INVALID_ARG, "null buffer");
+    // One right-hand side per solve: the schedules for a single right-hand side are built with the
+    // tree, whereas folding several into one solve (the mixed form's usual path) would build new
+    // schedules in device memory on first use.
     size_t need = 0;
-    VFMM_CHECK(vfmm_workspace_size(tree, ops, nrhs, 0, &need));
+    VFMM_CHECK(vfmm_workspace_size(tree, ops, 1, 0, &need));
     if (need > kStaticScratchBytes)
         return fail(VFMM_ERR_WORKSPACE, "tree needs " + std::to_string(need) +
                                             " bytes of scratch; the static scratch holds " +
@@ -60,7 +65,10 @@ extern "C" int vfmm_volume_potential_noalloc(const vfmm_tree* tree, const vfmm_o
     VFMM_CHECK(scratch_address(&scratch));
     // Nothing in the scratch has to start at zero: the solve writes every
     // expansion, partial product and far value before reading it, and clears the
-    // local expansions of levels 0 and 1 itself on every call.
-    return vfmm_volume_potential(tree, ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, scratch, kStaticScratchBytes,
-                                 stream);
+    // local expansions of levels 0 and 1 (and its barrier counters) itself on every call.
+    const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
+    for (int r = 0; r < nrhs; ++r)
+        VFMM_CHECK(vfmm_volume_potential(tree, ops, f_dev + r * n, 1, u_dev + r * n, ux_dev + r * n, uy_dev + r * n,
+                                         scratch, kStaticScratchBytes, stream));
+    return VFMM_OK;
 }

@@ -22,6 +22,7 @@ import paper_1610_00823_gb300 as v  # noqa: E402
 from paper_1610_00823_gb300 import _lib  # noqa: E402
 
 TOL = 1e-12  # the tolerance of the FP64 parity tests
+TOL_MIXED = 1e-10  # the tolerance of the split-BF16 (mixed) tests
 
 
 def _noalloc(tree, ops, f, out):
@@ -57,6 +58,27 @@ def test_noalloc_matches_workspace_solve_twice(case):
         for q in range(3):
             assert torch.isfinite(out[q]).all()
             assert _rel(out[q], want[q]) < TOL
+
+
+def test_noalloc_mixed_form_two_right_hand_sides_twice():
+    """Mixed form, two right-hand sides per call on a tree never solved with two: the allocation-free
+    entry point solves them one at a time with the schedules built with the tree."""
+    src = W.narrow_gaussians(5, n=3, sigma=0.04)
+    tree = v.tree_build(0.0, 0.0, 1.0, 8, src, 1e-6, 7)
+    ops = v.ops_create(8, 20, v.MIXED)
+    f1 = v.source_sample(tree, src)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    f2 = torch.randn(f1.numel(), generator=g, dtype=torch.float64).cuda()
+    f = torch.stack([f1, f2]).contiguous()
+    want = [v.volume_potential(tree, ops, x) for x in (f1, f2)]
+    for _ in range(2):  # two calls in a row
+        out = tuple(torch.full_like(f, float("nan")) for _ in range(3))
+        assert _noalloc(tree, ops, f, out) == 0
+        torch.cuda.synchronize()
+        for r in range(2):
+            for q in range(3):
+                assert torch.isfinite(out[q][r]).all()
+                assert _rel(out[q][r], want[r][q]) < TOL_MIXED
 
 
 def test_noalloc_rejects_trees_beyond_the_static_scratch():
