@@ -237,6 +237,31 @@ __global__ void __launch_bounds__(256) l2t_gemm_kernel(const double* __restrict_
     gemm_tile_fp64(L2T, 3 * kk, P2, blockIdx.x * GBM, ncols, cp);
 }
 
+// Outputs j and P-1-j of one position of a triangular translation (mode 0, M2M: output o takes
+// inputs n <= o; mode 1, L2L: n >= o), n ascending for each, fused into one loop of P + 1 steps so
+// that every thread of a warp runs the same number of steps. M: [n][o] complex, x: inputs.
+__device__ __forceinline__ void translate_pair(int mode, const double2* __restrict__ M, const double2* x, int P, int j,
+                                               double2* out) {
+    const int oa = j, ob = P - 1 - j;
+    const int la = mode == 0 ? oa + 1 : P - oa;
+    const int lb = ob != oa ? (mode == 0 ? ob + 1 : P - ob) : 0;
+    const int na = mode == 0 ? 0 : oa, nb = mode == 0 ? 0 : ob;
+    double re = 0.0, im = 0.0;
+    for (int i = 0; i < la + lb; ++i) {
+        if (i == la) {
+            out[oa] = make_double2(re, im);
+            re = im = 0.0;
+        }
+        const bool first = i < la;
+        const int o = first ? oa : ob;
+        const int n = first ? na + i : nb + (i - la);
+        const double2 m = M[(size_t)n * P + o], v = x[n];
+        re = fma(m.x, v.x, fma(-m.y, v.y, re));
+        im = fma(m.x, v.y, fma(m.y, v.x, im));
+    }
+    out[lb ? ob : oa] = make_double2(re, im);
+}
+
 // ---------------------------------------------------------------- M2M and L2L (one CTA per non-leaf box)
 // The translations are triangular: M2M output l of the parent takes child coefficients n <= l,
 // L2L output m of a child takes parent coefficients l >= m. A thread owns one child position and
@@ -265,18 +290,7 @@ __global__ void __launch_bounds__(128) translate_kernel(int mode, const int32_t*
         const int pos = task / npair, j = task - pos * npair;
         const double2* M = tab + (size_t)pos * P * P;
         const double2* x = mode == 0 ? s_in + pos * P : s_in;
-        for (int half = 0; half < 2; ++half) {
-            const int o = half == 0 ? j : P - 1 - j;
-            if (half == 1 && o == j) break;
-            const int n0 = mode == 0 ? 0 : o, n1 = mode == 0 ? o : P - 1;
-            double re = 0.0, im = 0.0;
-            for (int n = n0; n <= n1; ++n) {
-                const double2 m = M[(size_t)n * P + o], v = x[n];
-                re = fma(m.x, v.x, fma(-m.y, v.y, re));
-                im = fma(m.x, v.y, fma(m.y, v.x, im));
-            }
-            s_out[pos * P + o] = make_double2(re, im);
-        }
+        translate_pair(mode, M, x, P, j, s_out + pos * P);
     }
     __syncthreads();
     if (mode == 0) {
@@ -340,18 +354,7 @@ __global__ void __launch_bounds__(kTranslateThreads) translate_smem_kernel(int m
             const int pos = task / npair, j = task - pos * npair;
             const double2* M = sT + pos * P * P;
             const double2* x = mode == 0 ? s_in + pos * P : s_in;
-            for (int half = 0; half < 2; ++half) {
-                const int o = half == 0 ? j : P - 1 - j;
-                if (half == 1 && o == j) break;
-                const int n0 = mode == 0 ? 0 : o, n1 = mode == 0 ? o : P - 1;
-                double re = 0.0, im = 0.0;
-                for (int n = n0; n <= n1; ++n) {
-                    const double2 m = M[n * P + o], v = x[n];
-                    re = fma(m.x, v.x, fma(-m.y, v.y, re));
-                    im = fma(m.x, v.y, fma(m.y, v.x, im));
-                }
-                s_out[pos * P + o] = make_double2(re, im);
-            }
+            translate_pair(mode, M, x, P, j, s_out + pos * P);
         }
         __syncthreads();
         if (mode == 0) {
@@ -622,18 +625,7 @@ __device__ __forceinline__ void translate_group(int mode, const double2* sT, con
         const int pos = task / npair, j = task - pos * npair;
         const double2* M = sT + pos * P * P;
         const double2* x = mode == 0 ? s_in + pos * P : s_in;
-        for (int half = 0; half < 2; ++half) {
-            const int o = half == 0 ? j : P - 1 - j;
-            if (half == 1 && o == j) break;
-            const int n0 = mode == 0 ? 0 : o, n1 = mode == 0 ? o : P - 1;
-            double re = 0.0, im = 0.0;
-            for (int n = n0; n <= n1; ++n) {
-                const double2 m = M[n * P + o], v = x[n];
-                re = fma(m.x, v.x, fma(-m.y, v.y, re));
-                im = fma(m.x, v.y, fma(m.y, v.x, im));
-            }
-            s_out[pos * P + o] = make_double2(re, im);
-        }
+        translate_pair(mode, M, x, P, j, s_out + pos * P);
     }
 }
 
@@ -743,8 +735,8 @@ __global__ void leaf_scalar_kernel(int nleaf, int R, int P, double width, const 
     scal[vl] = -kInv2Pi * logh * m - kInv2Pi * (Lexp[((size_t)b * R + r) * 2 * P] + w0 * (logh - 0.6931471805599453));
 }
 
-// Mixed form, one thread per (virtual leaf, node): u, u_x, u_y = near + far + scalar, the split
-// contraction outputs (hi, lo) scaled back by their power-of-two exponents.
+// Mixed form, one CTA per virtual leaf (leaf, r), one thread per node: u, u_x, u_y = near + far +
+// scalar, the split contraction outputs (hi, lo) scaled back by their power-of-two exponents.
 __global__ void leaf_mixed_kernel(int nleaf, int R, int kk, int Rp, double width, double inv_width,
                                   const int32_t* __restrict__ box_of_leaf, const int32_t* __restrict__ level,
                                   const float2* __restrict__ nearmix, const int* __restrict__ Er,
@@ -752,26 +744,24 @@ __global__ void leaf_mixed_kernel(int nleaf, int R, int kk, int Rp, double width
                                   const int* __restrict__ farE, const int* __restrict__ Et,
                                   const double* __restrict__ scal, double* __restrict__ u, double* __restrict__ ux,
                                   double* __restrict__ uy) {
+    const unsigned vl = blockIdx.x;
+    const int t = threadIdx.x;
+    if (t >= kk) return;
+    const unsigned leaf = vl / (unsigned)R, r = vl - leaf * (unsigned)R;
     const double w2h = width * width;
-    const int64_t total = (int64_t)nleaf * R * kk;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t vl = q / kk;
-        const int t = (int)(q % kk);
-        const int leaf = (int)(vl / R), r = (int)(vl % R);
-        const int lv = level[box_of_leaf[leaf]];
-        const float2* nm = nearmix + (size_t)vl * Rp;
-        const float2* fm = farmix + (size_t)vl * Rp;
-        const int ef = Ef[r] - lv, et = Et[vl] + lv;  // h = width 2^-lv: scales are exact powers of two
-        const float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
-        const float2 w0 = fm[t], w1 = fm[kk + t], w2 = fm[2 * kk + t];
-        const size_t o = ((size_t)r * nleaf + leaf) * kk + t;
-        u[o] = w2h * ((double)v0.x + (double)v0.y) * pow2(ef - lv + Er[t]) + scal[vl] +
-               ((double)w0.x + (double)w0.y) * pow2(et - lv + farE[t]);
-        ux[o] = width * ((double)v1.x + (double)v1.y) * pow2(ef + Er[kk + t]) +
-                inv_width * ((double)w1.x + (double)w1.y) * pow2(et + farE[kk + t]);
-        uy[o] = width * ((double)v2.x + (double)v2.y) * pow2(ef + Er[2 * kk + t]) +
-                inv_width * ((double)w2.x + (double)w2.y) * pow2(et + farE[2 * kk + t]);
-    }
+    const int lv = level[box_of_leaf[leaf]];
+    const float2* nm = nearmix + (size_t)vl * Rp;
+    const float2* fm = farmix + (size_t)vl * Rp;
+    const int ef = Ef[r] - lv, et = Et[vl] + lv;  // h = width 2^-lv: scales are exact powers of two
+    const float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
+    const float2 w0 = fm[t], w1 = fm[kk + t], w2 = fm[2 * kk + t];
+    const size_t o = ((size_t)r * nleaf + leaf) * kk + t;
+    u[o] = w2h * ((double)v0.x + (double)v0.y) * pow2(ef - lv + Er[t]) + scal[vl] +
+           ((double)w0.x + (double)w0.y) * pow2(et - lv + farE[t]);
+    ux[o] = width * ((double)v1.x + (double)v1.y) * pow2(ef + Er[kk + t]) +
+            inv_width * ((double)w1.x + (double)w1.y) * pow2(et + farE[kk + t]);
+    uy[o] = width * ((double)v2.x + (double)v2.y) * pow2(ef + Er[2 * kk + t]) +
+            inv_width * ((double)w2.x + (double)w2.y) * pow2(et + farE[2 * kk + t]);
 }
 
 // ---------------------------------------------------------------- leaf pass (one CTA per leaf)
@@ -1224,9 +1214,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         leaf_scalar_kernel<<<(unsigned)((nv + 127) / 128), 128, 0, st>>>(
             nleaf, R, P, T.width, T.box_of_leaf, T.level, T.lptr[VFMM_LIST_U], T.lidx[VFMM_LIST_U],
             T.lptr[VFMM_LIST_W], T.lidx[VFMM_LIST_W], w.Mexp, w.Lexp, w.mix.scal);
-        const int64_t ne = nv * kk;
-        const unsigned grid = (unsigned)std::min<int64_t>((ne + 255) / 256, 64ll * sm_count());
-        leaf_mixed_kernel<<<grid, 256, 0, st>>>(nleaf, R, kk, mo->Rp, T.width, 1.0 / T.width, T.box_of_leaf, T.level,
+        leaf_mixed_kernel<<<(unsigned)nv, ((kk + 31) / 32) * 32, 0, st>>>(nleaf, R, kk, mo->Rp, T.width, 1.0 / T.width, T.box_of_leaf, T.level,
                                                 w.mix.out, mo->Er, w.mix.Ef, w.mix.far_out, mo->far_E, w.mix.Et,
                                                 w.mix.scal, u, ux, uy);
         launches += 2;
