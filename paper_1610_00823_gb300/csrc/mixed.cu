@@ -129,6 +129,7 @@ struct SplitArgs {
     int Kp, Rp, nchunks;
     int split;            // CTAs sharing one group's tables (split-K over tables)
     int drain_every;      // configurations accumulated in TMEM between two drains (exactness bound)
+    int transposed;       // table rows on the M side (see near_transposed)
     size_t part_stride;   // n_out_rows * Rp
 };
 
@@ -175,6 +176,8 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
     constexpr uint32_t STAGE = kSlices * (A_SLICE + B_SLICE);
     constexpr int HALF = N / 2;  // columns per epilogue warp
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool tr = a.transposed != 0;     // table rows on M (TMA into the A region), targets on N
+    const int G = tr ? kTileN : kTileM;    // gathered rows (targets) per group
     const int q = blockIdx.x / a.nchunks, rc = blockIdx.x % a.nchunks;
     const int g = q / a.split, sp = q % a.split;
     const uint32_t base = tc::smem_u32(dsm);
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
     const int ncfg = cend - cbeg;
     const int nkb = a.Kp / kKBlock;
     const int U = ncfg * nkb;
-    const int r0 = rc * N;
+    const int r0 = rc * (tr ? kTileM : N);  // first table row of this CTA's tile
 
     if (warp >= kEpilogueWarps && warp < kMmaWarp) {
         // ------------------------------------------------ producers: table tile by TMA (one thread),
@@ -230,25 +233,28 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
             const int cfg = a.gcfg[ci];
             if (kb == 0) {
                 // gather rows of this table for the 128 targets, once per table
-                for (int m = ptid; m < kTileM; m += kProducerThreads) s_src[m] = a.gsrc[(size_t)ci * kTileM + m];
+                for (int m = ptid; m < G; m += kProducerThreads) s_src[m] = a.gsrc[(size_t)ci * G + m];
                 named_bar_sync(1, kProducerThreads);
             }
             const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
+            // table tile by TMA into the region of its side, gathered rows into the other
+            const uint32_t sT = tr ? sA : sB, sG = tr ? sB : sA;
+            const uint32_t T_SLICE = tr ? A_SLICE : B_SLICE, G_SLICE = tr ? B_SLICE : A_SLICE;
             if (ptid == 0) {
-                // 8 boxes of 80 table rows x 64 bytes (one per slice), SW64-swizzled by the TMA unit
-                tc::mbar_arrive_expect_tx(full0 + 8 * s, kSlices * B_SLICE);
+                // 8 boxes of (128 or 80) table rows x 64 bytes (one per slice), SW64-swizzled by TMA
+                tc::mbar_arrive_expect_tx(full0 + 8 * s, kSlices * T_SLICE);
                 for (int sl_i = 0; sl_i < kSlices; ++sl_i)
-                    tc::tma_load_3d(sB + sl_i * B_SLICE, &tmB, 0, kb * kSlices + sl_i, cfg * a.Rp + r0, full0 + 8 * s);
+                    tc::tma_load_3d(sT + sl_i * T_SLICE, &tmB, 0, kb * kSlices + sl_i, cfg * a.Rp + r0, full0 + 8 * s);
             }
             // a warp instruction covers 8 rows x 64 bytes of one slice: 512 contiguous bytes of shared
             // memory (no bank conflicts) from eight 64-byte pieces of global memory
             const int lrow = (ptid & 31) >> 2, ch = ptid & 3, pw = ptid >> 5;
 #pragma unroll 4
-            for (int q = pw; q < kSlices * (kTileM / 8); q += kProducerThreads / 32) {
-                const int sl_i = q / (kTileM / 8), m = (q % (kTileM / 8)) * 8 + lrow;
+            for (int q = pw; q < kSlices * (G / 8); q += kProducerThreads / 32) {
+                const int sl_i = q / (G / 8), m = (q % (G / 8)) * 8 + lrow;
                 const int src = s_src[m];
                 const bf16* gp = a.asl + (((size_t)(src < 0 ? 0 : src) * nkb + kb) * kSlices + sl_i) * kKBlock + ch * 8;
-                const uint32_t dst = sA + sl_i * A_SLICE + m * 64 + ((ch ^ ((m >> 1) & 3)) << 4);
+                const uint32_t dst = sG + sl_i * G_SLICE + m * 64 + ((ch ^ ((m >> 1) & 3)) << 4);
                 tc::cp_async16(dst, gp, src < 0 ? 0u : 16u);
             }
             // the stage's full barrier gets this thread's arrival when its copies have landed
@@ -333,18 +339,32 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
             tc::mbar_arrive(acc_empty);
         }
         if (ok) {
-            const int m = quad * 32 + lane;
-            const int tgt = a.gtgt[(size_t)g * kTileM + m];
-            if (tgt >= 0) {
-                float2* outp = a.split > 1 ? a.out + (size_t)sp * a.part_stride : a.out;
-                float4* o = reinterpret_cast<float4*>(outp + (size_t)tgt * a.Rp + r0 + half * HALF);
+            float2* outp = a.split > 1 ? a.out + (size_t)sp * a.part_stride : a.out;
+            const int m = quad * 32 + lane;  // TMEM lane
+            if (tr) {
+                // lane = table row r0 + m, columns = targets half * HALF + j of the group
+                const int row = r0 + m;
 #pragma unroll
-                for (int j = 0; j < HALF / 2; ++j) {
-                    float h0 = __fadd_rn(hi[2 * j], lo[2 * j]);
-                    float l0 = __fsub_rn(lo[2 * j], __fsub_rn(h0, hi[2 * j]));
-                    float h1 = __fadd_rn(hi[2 * j + 1], lo[2 * j + 1]);
-                    float l1 = __fsub_rn(lo[2 * j + 1], __fsub_rn(h1, hi[2 * j + 1]));
-                    o[j] = make_float4(h0, l0, h1, l1);
+                for (int j = 0; j < HALF; ++j) {
+                    const int tgt = a.gtgt[(size_t)g * G + half * HALF + j];
+                    if (tgt < 0) continue;
+                    const float h = __fadd_rn(hi[j], lo[j]);
+                    const float l = __fsub_rn(lo[j], __fsub_rn(h, hi[j]));
+                    outp[(size_t)tgt * a.Rp + row] = make_float2(h, l);
+                }
+            } else {
+                // lane = target m of the group, columns = table rows r0 + half * HALF + j
+                const int tgt = a.gtgt[(size_t)g * G + m];
+                if (tgt >= 0) {
+                    float4* o = reinterpret_cast<float4*>(outp + (size_t)tgt * a.Rp + r0 + half * HALF);
+#pragma unroll
+                    for (int j = 0; j < HALF / 2; ++j) {
+                        float h0 = __fadd_rn(hi[2 * j], lo[2 * j]);
+                        float l0 = __fsub_rn(lo[2 * j], __fsub_rn(h0, hi[2 * j]));
+                        float h1 = __fadd_rn(hi[2 * j + 1], lo[2 * j + 1]);
+                        float l1 = __fsub_rn(lo[2 * j + 1], __fsub_rn(h1, hi[2 * j + 1]));
+                        o[j] = make_float4(h0, l0, h1, l1);
+                    }
                 }
             }
         }
@@ -362,7 +382,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int make_table_map(const void* base, int64_t rows, int Kp, CUtensorMap* out) {
+int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtensorMap* out) {
     static EncodeTiledFn encode = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -374,14 +394,15 @@ int make_table_map(const void* base, int64_t rows, int Kp, CUtensorMap* out) {
             encode = (EncodeTiledFn)fn;
     });
     if (!encode) return fail(VFMM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-    if (Kp % kKBlock || rows < 1 || rows > (int64_t)INT32_MAX || ((uintptr_t)base & 15))
+    if (Kp % kKBlock || rows < box_rows || rows > (int64_t)INT32_MAX || ((uintptr_t)base & 15) || box_rows < 1 ||
+        box_rows > 256)
         return fail(VFMM_ERR_INTERNAL, "table shape not suitable for a tensor map");
     // [rows][Kp / 32 K blocks][8 slices][32 values]: dim 0 = 32 values (64 bytes, one swizzle row),
     // dim 1 = (K block, slice) segments, dim 2 = rows
     const cuuint64_t nseg = (cuuint64_t)(Kp / kKBlock) * kSlices;
     const cuuint64_t dims[3] = {(cuuint64_t)kKBlock, nseg, (cuuint64_t)rows};
     const cuuint64_t strides[2] = {(cuuint64_t)kKBlock * 2, nseg * kKBlock * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)kKBlock, 1, (cuuint32_t)kTileN};
+    const cuuint32_t box[3] = {(cuuint32_t)kKBlock, 1, (cuuint32_t)box_rows};
     const cuuint32_t es[3] = {1, 1, 1};
     CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -397,7 +418,8 @@ int mixed_prepare(vfmm_ops* o, cudaStream_t st) {
     const int kk = o->k * o->k;
     const int R = 3 * kk;
     mo->N = kTileN;
-    mo->Rp = (R + mo->N - 1) / mo->N * mo->N;
+    const int tile_rows = table_rows_per_tile(near_transposed(o->k));
+    mo->Rp = (R + tile_rows - 1) / tile_rows * tile_rows;
     mo->Kp = (kk + kKBlock - 1) / kKBlock * kKBlock;
     VFMM_CUDA(cudaMalloc(&mo->Er, mo->Rp * sizeof(int)));
     VFMM_CUDA(cudaMemsetAsync(mo->Er, 0, mo->Rp * sizeof(int), st));
@@ -406,7 +428,7 @@ int mixed_prepare(vfmm_ops* o, cudaStream_t st) {
     table_slice_kernel<<<dim3(mo->Rp, kNearCfg), 128, 0, st>>>(o->near, R, kk, mo->Rp, mo->Kp, mo->Er, (bf16*)mo->tsl);
     VFMM_CUDA(cudaGetLastError());
     VFMM_CUDA(cudaStreamSynchronize(st));
-    VFMM_CHECK(make_table_map(mo->tsl, (int64_t)kNearCfg * mo->Rp, mo->Kp, &mo->tm_near));
+    VFMM_CHECK(make_table_map(mo->tsl, (int64_t)kNearCfg * mo->Rp, mo->Kp, tile_rows, &mo->tm_near));
     return far_prepare(o, st);
 }
 
@@ -424,7 +446,8 @@ void mixed_free(vfmm_ops* o) {
 // of each target (-1 when the target has no entry for that table).
 int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                      const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                     SplitPlan* P) {
+                     bool transposed, SplitPlan* P) {
+    const int G = transposed ? kTileN : kTileM;  // targets per group
     // Targets sorted by key; target t stands for the R consecutive virtual targets t * R + r, whose
     // A rows are src * R + r: the right-hand sides of one target share its set of tables.
     const int nt0 = (int)tgt_id.size();
@@ -433,34 +456,36 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key[x] < key[y]; });
     const int64_t nt = (int64_t)nt0 * R;
     if (nt > (int64_t)INT32_MAX / 2) return fail(VFMM_ERR_INVALID_ARG, "too many rows for one split contraction");
-    const int ng = (int)((nt + kTileM - 1) / kTileM);
-    std::vector<int32_t> gtgt((size_t)std::max(ng, 1) * kTileM, -1), gptr(ng + 1, 0), gcfg, gsrc;
+    const int ng = (int)((nt + G - 1) / G);
+    std::vector<int32_t> gtgt((size_t)std::max(ng, 1) * G, -1), gptr(ng + 1, 0), gcfg, gsrc;
     std::vector<int32_t> slot(n_tables, -1);
     std::vector<char> present(n_tables, 0);
     for (int g = 0; g < ng; ++g) {
         std::fill(present.begin(), present.end(), 0);
-        const int m_end = (int)std::min<int64_t>(kTileM, nt - (int64_t)g * kTileM);
+        const int m_end = (int)std::min<int64_t>(G, nt - (int64_t)g * G);
         for (int m = 0; m < m_end; ++m) {
-            const int64_t v = (int64_t)g * kTileM + m;
+            const int64_t v = (int64_t)g * G + m;
             const int t = order[v / R], r = (int)(v % R);
-            gtgt[(size_t)g * kTileM + m] = tgt_id[t] * R + r;
+            gtgt[(size_t)g * G + m] = tgt_id[t] * R + r;
             for (auto& it : items[t]) present[it.first] = 1;
         }
         for (int c = 0; c < n_tables; ++c) {
             if (!present[c]) continue;
             slot[c] = (int32_t)gcfg.size();
             gcfg.push_back(c);
-            gsrc.resize(gsrc.size() + kTileM, -1);
+            gsrc.resize(gsrc.size() + G, -1);
         }
         for (int m = 0; m < m_end; ++m) {
-            const int64_t v = (int64_t)g * kTileM + m;
+            const int64_t v = (int64_t)g * G + m;
             const int t = order[v / R], r = (int)(v % R);
-            for (auto& it : items[t]) gsrc[(size_t)slot[it.first] * kTileM + m] = it.second * R + r;
+            for (auto& it : items[t]) gsrc[(size_t)slot[it.first] * G + m] = it.second * R + r;
         }
         gptr[g + 1] = (int32_t)gcfg.size();
     }
     P->n_groups = ng;
     P->entries = (int64_t)gcfg.size();
+    P->transposed = transposed;
+    P->group = G;
     {
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
@@ -538,7 +563,8 @@ __global__ void split_reduce_kernel(const float2* __restrict__ part, size_t stri
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
                float2* part, size_t n_out_rows, cudaStream_t st) {
     if (P.n_groups == 0) return VFMM_OK;
-    if (Kp % kKBlock || Rp % kTileN) return fail(VFMM_ERR_INTERNAL, "split GEMM shape not tiled");
+    const int tile_rows = table_rows_per_tile(P.transposed);
+    if (Kp % kKBlock || Rp % tile_rows) return fail(VFMM_ERR_INTERNAL, "split GEMM shape not tiled");
     static bool attr = false;
     if (!attr) {
         VFMM_CUDA(cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
@@ -553,7 +579,8 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
     a.err = err;
     a.Kp = Kp;
     a.Rp = Rp;
-    a.nchunks = Rp / kTileN;
+    a.nchunks = Rp / tile_rows;
+    a.transposed = P.transposed ? 1 : 0;
     // A diagonal gets at most 5 slice products per K value (i + j = d <= 6), each below 63^2, so the
     // exact FP32 accumulators stay exact while 5 * 3969 * Kp * configurations < 2^24. The shared
     // accumulator of diagonals 7..9 truncates as it grows, so a drain group also holds at most 512
@@ -565,9 +592,9 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
     split_gemm_kernel<<<(unsigned)P.n_groups * a.split * a.nchunks, kThreads, smem_bytes(), st>>>(a, bmap);
     VFMM_CUDA(cudaGetLastError());
     if (a.split > 1) {
-        const int64_t n = (int64_t)P.n_groups * kTileM * Rp;
+        const int64_t n = (int64_t)P.n_groups * P.group * Rp;
         split_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, a.part_stride, a.split, P.tgt,
-                                                                          P.n_groups * kTileM, Rp, out);
+                                                                          P.n_groups * P.group, Rp, out);
         VFMM_CUDA(cudaGetLastError());
     }
     return VFMM_OK;
@@ -597,7 +624,9 @@ static int build_plans(const DeviceTree& T, int R, PlanSet* PS) {
         key[t] = {sig, (uint64_t)t};
     }
     const int rows = 3 * T.k * T.k;
-    VFMM_CHECK(build_split_plan(tgt, items, key, kNearCfg, (rows + kTileN - 1) / kTileN, R, &PS->near));
+    const bool tr = near_transposed(T.k);
+    const int tile_rows = table_rows_per_tile(tr);
+    VFMM_CHECK(build_split_plan(tgt, items, key, kNearCfg, (rows + tile_rows - 1) / tile_rows, R, tr, &PS->near));
     return build_far_plans(T, R, PS);
 }
 

@@ -29,6 +29,13 @@ constexpr int kThreads = 32 * (kMmaWarp + 1);                     // 384: 3 warp
 constexpr int kMaxSplit = 8;  // largest split-K factor (partial sums held for small contractions only)
 static_assert(kNumAcc * kTileN <= kTmemCols, "TMEM budget");
 
+// Orientation of the near-field and leaf far-field contractions: with 3k^2 a multiple of 128
+// (k = 16) the table rows are the M side (128 per tile, TMA) and the targets the N side (80 per
+// group, gathered), which gathers 40 % fewer bytes; otherwise targets are the M side (128 per group)
+// and table rows the N side (80 per tile). M2L, S2L and S2M (2p rows) always use the latter.
+__host__ __device__ constexpr bool near_transposed(int k) { return (3 * k * k) % kTileM == 0; }
+__host__ __device__ constexpr int table_rows_per_tile(bool transposed) { return transposed ? kTileM : kTileN; }
+
 // Splits v / 2^E (|v| < 2^E) into kSlices signed base-64 digits, out[(i - 1) * stride] =
 // sign(v) d_i 2^(-6 i), d_i = floor(|v| 2^(6 i - E)) mod 64: the digits that repeated
 // t <- 64 t, d <- trunc(t), t <- t - d give in exact arithmetic, taken here from the bits of v
@@ -112,9 +119,10 @@ struct MixedWork {
 int build_split_plan(const std::vector<int32_t>& tgt_id,
                      const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                      const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                     SplitPlan* P);
-// Tensor map of a sliced table [rows][Kp / 32][kSlices][32] BF16 for the table operand of split_gemm.
-int make_table_map(const void* base, int64_t rows, int Kp, CUtensorMap* out);
+                     bool transposed, SplitPlan* P);
+// Tensor map of a sliced table [rows][Kp / 32][kSlices][32] BF16 for the table operand of split_gemm
+// (box = box_rows rows x 64 bytes of one slice and K block).
+int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtensorMap* out);
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
                float2* part, size_t n_out_rows, cudaStream_t st);
 size_t split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o);

@@ -98,7 +98,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
     std::vector<double> S((size_t)2 * p * kk);
     std::copy(s2m.begin() + 2 * kk, s2m.end(), S.begin());
     VFMM_CHECK(slice_table(S, 1, 2 * p, kk, mo->Rx, mo->Kp, &mo->s2m_sl, &mo->s2m_E, st));
-    VFMM_CHECK(make_table_map(mo->s2m_sl, mo->Rx, mo->Kp, &mo->tm_s2m));
+    VFMM_CHECK(make_table_map(mo->s2m_sl, mo->Rx, mo->Kp, kTileN, &mo->tm_s2m));
     // M2L as real matrices: rows 2..2p+1, columns 0..2p+1
     std::vector<double> mt((size_t)kVCfg * P * P * 2);
     VFMM_CUDA(cudaMemcpy(mt.data(), o->m2l_t, mt.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -129,7 +129,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
         VFMM_CUDA(cudaMalloc(&mo->m2l_r0, r0.size() * sizeof(double)));
         VFMM_CUDA(cudaMemcpy(mo->m2l_r0, r0.data(), r0.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
-    VFMM_CHECK(make_table_map(mo->m2l_sl, (int64_t)kVCfg * mo->Rx, mo->Kx, &mo->tm_m2l));
+    VFMM_CHECK(make_table_map(mo->m2l_sl, (int64_t)kVCfg * mo->Rx, mo->Kx, kTileN, &mo->tm_m2l));
     // leaf tables: 0 = L2T without coefficient 0, 1 + c = M2T of W configuration c
     std::vector<double> l2t((size_t)R * 2 * P), xh(k);
     VFMM_CUDA(cudaMemcpy(l2t.data(), o->l2t, l2t.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -168,7 +168,8 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
         }
     }
     VFMM_CHECK(slice_table(F, 1 + kFarCfg, R, KX, mo->Rp, mo->Kx, &mo->far_sl, &mo->far_E, st));
-    VFMM_CHECK(make_table_map(mo->far_sl, (int64_t)(1 + kFarCfg) * mo->Rp, mo->Kx, &mo->tm_far));
+    VFMM_CHECK(make_table_map(mo->far_sl, (int64_t)(1 + kFarCfg) * mo->Rp, mo->Kx,
+                              table_rows_per_tile(near_transposed(o->k)), &mo->tm_far));
     // S2L: rows 2..2p+1 (Re, Im of coefficients 1..p) over the k*k source values; row 0 kept in FP64
     std::vector<double> st_((size_t)kFarCfg * kk * P * 2);
     VFMM_CUDA(cudaMemcpy(st_.data(), o->s2l_t, st_.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -182,7 +183,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
             }
         }
     VFMM_CHECK(slice_table(XL, kFarCfg, 2 * p, kk, mo->Rx, mo->Kp, &mo->s2l_sl, &mo->s2l_E, st));
-    VFMM_CHECK(make_table_map(mo->s2l_sl, (int64_t)kFarCfg * mo->Rx, mo->Kp, &mo->tm_s2l));
+    VFMM_CHECK(make_table_map(mo->s2l_sl, (int64_t)kFarCfg * mo->Rx, mo->Kp, kTileN, &mo->tm_s2l));
     VFMM_CUDA(cudaMalloc(&mo->s2l_r0, X0.size() * sizeof(double)));
     VFMM_CUDA(cudaMemcpy(mo->s2l_r0, X0.data(), X0.size() * sizeof(double), cudaMemcpyHostToDevice));
     return VFMM_OK;
@@ -236,7 +237,7 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             items[t].push_back({0, t});
             key[t] = {0, (uint64_t)t};
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, R, &PS->s2m));
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, R, false, &PS->s2m));
     }
     // M2L: boxes with a V list, tables = the 40 offsets, A row = source box
     {
@@ -256,7 +257,7 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             }
             key.push_back({sig, (uint64_t)b});
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, kVCfg, 1, R, &PS->m2l));
+        VFMM_CHECK(build_split_plan(tgt, items, key, kVCfg, 1, R, false, &PS->m2l));
     }
     // S2L: boxes with an X list, tables 20 configurations, A row = source leaf
     {
@@ -276,7 +277,7 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             }
             key.push_back({sig, (uint64_t)b});
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, kFarCfg, 1, R, &PS->s2l));
+        VFMM_CHECK(build_split_plan(tgt, items, key, kFarCfg, 1, R, false, &PS->s2l));
     }
     // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
     {
@@ -298,7 +299,9 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             key[t] = {sig, (uint64_t)t};
         }
         const int rows = 3 * T.k * T.k;
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1 + kFarCfg, (rows + kTileN - 1) / kTileN, R, &PS->far));
+        const bool tr = near_transposed(T.k);
+        const int tile_rows = table_rows_per_tile(tr);
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1 + kFarCfg, (rows + tile_rows - 1) / tile_rows, R, tr, &PS->far));
     }
     return VFMM_OK;
 }
@@ -499,9 +502,9 @@ extern "C" int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32
     int np = 0;
     for (int i = 1; i <= kSlices; ++i)
         for (int j = 1; i + j <= kSlices + 1; ++j) ++np;
-    // per table of a tile and per K value: np products of 128 x kTileN MACs
+    // per table of a tile and per K value: np products of 128 x 80 MACs
     auto tc = [&](const SplitPlan& P, int Kp, int Rp) {
-        return 2.0 * (double)P.entries * (Rp / kTileN) * (double)Kp * np * kTileM * kTileN;
+        return 2.0 * (double)P.entries * (Rp / table_rows_per_tile(P.transposed)) * (double)Kp * np * kTileM * kTileN;
     };
     out[0] = tc(PS->near, mo->Kp, mo->Rp);
     out[1] = tc(PS->m2l, mo->Kx, mo->Rx);

@@ -159,12 +159,14 @@ __host__ __device__ inline void near_config_geometry(int cfg, double* rho, doubl
 struct SplitPlan {
     int32_t n_groups = 0;
     int64_t entries = 0;
-    int32_t* tgt = nullptr;  // [n_groups][128] output row or -1
+    int32_t* tgt = nullptr;  // [n_groups][group] output row or -1
     int32_t* ptr = nullptr;  // [n_groups + 1]
     int32_t* cfg = nullptr;  // [entries] table index
-    int32_t* src = nullptr;  // [entries][128] A row or -1
+    int32_t* src = nullptr;  // [entries][group] gathered operand row or -1
     int32_t split = 1;       // CTAs per group (each takes a share of the group's tables)
     bool may_split = false;  // small contraction (fewer CTAs than two per SM): split-K allowed
+    bool transposed = false; // table rows on the M side (128 per tile), targets on the N side
+    int32_t group = 128;     // targets per group: 128, or 80 when transposed
 };
 
 // The split contractions of the mixed form with R right-hand sides folded into the rows: the
