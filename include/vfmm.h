@@ -292,9 +292,11 @@ int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs, do
 /* Stage timers (tracing): the same solve as vfmm_volume_potential with CUDA events
  * recorded on `stream` between its stages; synchronises `stream` and returns the
  * elapsed milliseconds of each stage summed over the right-hand sides
- * (stage_ms[VFMM_N_STAGES]: S2M, M2M, DOWN (M2L + S2L + L2L), NEAR, L2T, LEAF)
- * and the number of kernels the solve launched (*launches). */
-#define VFMM_N_STAGES 6
+ * (stage_ms[VFMM_N_STAGES]: S2M, M2M, DOWN (M2L + S2L + L2L), NEAR, L2T, LEAF, then for
+ * VFMM_MIXED the split tensor-core contractions alone (each with its partial-sum reduction):
+ * NEAR_TC, S2M_TC, M2L_TC, S2L_TC, FAR_TC; these five are 0 for VFMM_FP64) and the number of
+ * kernels the solve launched (*launches). */
+#define VFMM_N_STAGES 11
 int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
                                    double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
                                    size_t workspace_bytes, void* stream, float* stage_ms, int32_t* launches);

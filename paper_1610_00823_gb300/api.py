@@ -200,7 +200,7 @@ def volume_potential_host(tree: Tree, ops: Ops, f_host, out_host=None, ws=None, 
     return out_host
 
 
-STAGES = ("s2m", "m2m", "down", "near", "l2t", "leaf")
+STAGES = ("s2m", "m2m", "down", "near", "l2t", "leaf", "near_tc", "s2m_tc", "m2l_tc", "s2l_tc", "far_tc")
 
 
 def volume_potential_profiled(tree: Tree, ops: Ops, f, out, ws, stream=None):

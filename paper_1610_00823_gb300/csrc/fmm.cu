@@ -31,8 +31,8 @@ constexpr double kInv2Pi = 0.15915494309189533577;
 // Re of local coefficient 0 from the V and X lists of each virtual box (box, r): sum over V of
 // Re(row 0 of M2L_c . a_c) + a_0(c) log h, and over X of (2h)^2 Re(S2L row 0) . f_c + a_0(c) log h.
 // FP64; the other coefficients come from the split-precision M2L and S2L. Persistent CTAs hold the
-// row-0 tables in shared memory; one warp per virtual box, lanes over the coefficients of each
-// source multipole (coalesced), four V entries in flight.
+// row-0 tables in shared memory; one warp per virtual box, the (entry, coefficient) pairs of eight
+// V entries at a time spread over the lanes.
 __global__ void __launch_bounds__(256) m2l_c0_kernel(int begin, int end, int R, int P, double width,
                                                      const int32_t* __restrict__ level,
                                                      const int32_t* __restrict__ vptr, const int32_t* __restrict__ vidx,
@@ -60,26 +60,27 @@ __global__ void __launch_bounds__(256) m2l_c0_kernel(int begin, int end, int R, 
         // multipole (coalesced), partial sums stay per lane until one final reduction
         double acc = 0.0;
         const int e_end = vptr[b + 1];
-        for (int e0 = vptr[b]; e0 < e_end; e0 += 4) {
-            // four entries at a time, every load issued before the arithmetic
-            double2 x[4][2];
-            int cf[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const bool live = e0 + j < e_end;
-                const double2* a =
-                    reinterpret_cast<const double2*>(Mexp + ((size_t)vidx[live ? e0 + j : e0] * R + r) * 2 * P);
-                cf[j] = live ? vcfg[e0 + j] : -1;
-                x[j][0] = live && lane < P ? a[lane] : make_double2(0.0, 0.0);
-                x[j][1] = live && lane + 32 < P ? a[lane + 32] : make_double2(0.0, 0.0);
+        // V list in batches of 8 entries: the batch's (entry, coefficient) pairs spread over the lanes,
+        // so all 32 lanes work whatever p is (coalesced within an entry's multipole)
+        for (int e0 = vptr[b]; e0 < e_end; e0 += 8) {
+            const int nb = min(8, e_end - e0);
+            int j = 0, n = lane;
+            while (n >= P) {
+                n -= P;
+                ++j;
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (cf[j] < 0) continue;
-                const double2* M = sM + cf[j] * P;
-                if (lane < P) acc += M[lane].x * x[j][0].x - M[lane].y * x[j][0].y;
-                if (lane + 32 < P) acc += M[lane + 32].x * x[j][1].x - M[lane + 32].y * x[j][1].y;
-                if (lane == 0) acc += x[j][0].x * logh;
+#pragma unroll 4
+            for (int item = lane; item < nb * P; item += 32) {
+                const int e = e0 + j;
+                const double2 x = reinterpret_cast<const double2*>(Mexp + ((size_t)vidx[e] * R + r) * 2 * P)[n];
+                const double2 m = sM[vcfg[e] * P + n];
+                acc += m.x * x.x - m.y * x.y;
+                if (n == 0) acc += x.x * logh;
+                n += 32;
+                while (n >= P) {
+                    n -= P;
+                    ++j;
+                }
             }
         }
         // X list: (2h)^2 [Re(S2L row 0) . f_c + log(h) W . f_c], with W . f_c = a_0(c) / (2h)^2
@@ -965,7 +966,7 @@ struct StageEvents {
     int launches = 0;
 };
 
-enum { ST_S2M = 0, ST_M2M = 1, ST_DOWN = 2, ST_NEAR = 3, ST_L2T = 4, ST_LEAF = 5 };
+enum { ST_S2M = 0, ST_M2M = 1, ST_DOWN = 2, ST_NEAR = 3, ST_L2T = 4, ST_LEAF = 5, ST_CONTRACTIONS = 6 };
 
 static inline void mark(StageEvents* se, int stage, bool stop, cudaStream_t st) {
     if (se) cudaEventRecord(se->ev[2 * stage + (stop ? 1 : 0)], st);
@@ -1325,6 +1326,11 @@ extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_
     StageEvents se;
     for (int i = 0; i < 2 * VFMM_N_STAGES; ++i) VFMM_CUDA(cudaEventCreate(&se.ev[i]));
     for (int i = 0; i < VFMM_N_STAGES; ++i) stage_ms[i] = 0.0f;
+    if (ops->precision == VFMM_MIXED) {
+        // contraction timers: recorded once here so that a contraction the tree lacks reads 0
+        w.mix.cev = se.ev + 2 * ST_CONTRACTIONS;
+        for (int i = 2 * ST_CONTRACTIONS; i < 2 * VFMM_N_STAGES; ++i) VFMM_CUDA(cudaEventRecord(se.ev[i], st));
+    }
     const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
     const bool folded = ops->precision == VFMM_MIXED;
     int rc = VFMM_OK;
@@ -1338,7 +1344,8 @@ extern "C" int vfmm_volume_potential_profiled(const vfmm_tree* tree, const vfmm_
             rc = cuda_fail(e, "cudaEventSynchronize");
             break;
         }
-        for (int i = 0; i < VFMM_N_STAGES; ++i) {
+        const int n_timed = ops->precision == VFMM_MIXED ? VFMM_N_STAGES : ST_CONTRACTIONS;
+        for (int i = 0; i < n_timed; ++i) {
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, se.ev[2 * i], se.ev[2 * i + 1]);
             stage_ms[i] += ms;

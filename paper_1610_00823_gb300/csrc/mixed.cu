@@ -561,8 +561,12 @@ __global__ void split_reduce_kernel(const float2* __restrict__ part, size_t stri
 }
 
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
-               float2* part, size_t n_out_rows, cudaStream_t st) {
-    if (P.n_groups == 0) return VFMM_OK;
+               float2* part, size_t n_out_rows, cudaStream_t st, cudaEvent_t* ev) {
+    if (ev) VFMM_CUDA(cudaEventRecord(ev[0], st));
+    if (P.n_groups == 0) {
+        if (ev) VFMM_CUDA(cudaEventRecord(ev[1], st));
+        return VFMM_OK;
+    }
     const int tile_rows = table_rows_per_tile(P.transposed);
     if (Kp % kKBlock || Rp % tile_rows) return fail(VFMM_ERR_INTERNAL, "split GEMM shape not tiled");
     static bool attr = false;
@@ -597,6 +601,7 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
                                                                           P.n_groups * P.group, Rp, out);
         VFMM_CUDA(cudaGetLastError());
     }
+    if (ev) VFMM_CUDA(cudaEventRecord(ev[1], st));
     return VFMM_OK;
 }
 
@@ -671,7 +676,8 @@ int near_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const 
     f_slice_kernel<<<(unsigned)((int64_t)T.n_leaves * R), mo->Kp, 0, st>>>(f, T.n_leaves, kk, mo->Kp, R, w.fmax, w.Ef,
                                                                            (bf16*)w.fsl);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(PS.near, w.fsl, mo->tm_near, mo->Kp, mo->Rp, w.out, w.err, w.part, (size_t)T.n_leaves * R, st);
+    return split_gemm(PS.near, w.fsl, mo->tm_near, mo->Kp, mo->Rp, w.out, w.err, w.part, (size_t)T.n_leaves * R, st,
+                      w.cev ? w.cev + 0 : nullptr);
 }
 
 }  // namespace vfmm

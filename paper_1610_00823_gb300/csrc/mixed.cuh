@@ -114,6 +114,7 @@ struct MixedWork {
     float2* far_out = nullptr;            // [n_leaves][Rp]
     double* scal = nullptr;               // [n_leaves * R] FP64 scalar part of u per virtual leaf
     float2* part = nullptr;               // partial sums of split contractions (largest plan)
+    cudaEvent_t* cev = nullptr;           // optional (start, stop) pairs: near, S2M, M2L, S2L, far
 };
 
 int build_split_plan(const std::vector<int32_t>& tgt_id,
@@ -123,8 +124,9 @@ int build_split_plan(const std::vector<int32_t>& tgt_id,
 // Tensor map of a sliced table [rows][Kp / 32][kSlices][32] BF16 for the table operand of split_gemm
 // (box = box_rows rows x 64 bytes of one slice and K block).
 int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtensorMap* out);
+// ev (optional): a (start, stop) event pair recorded around the contraction and its reduction.
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
-               float2* part, size_t n_out_rows, cudaStream_t st);
+               float2* part, size_t n_out_rows, cudaStream_t st, cudaEvent_t* ev = nullptr);
 size_t split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o);
 int build_mixed_plan(DeviceTree* T);
 int build_far_slots(DeviceTree* T);

@@ -357,7 +357,8 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
 int s2m_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* Mexp,
               const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    VFMM_CHECK(split_gemm(PS.s2m, w.fsl, mo->tm_s2m, mo->Kp, mo->Rx, w.s2m_out, w.err, nullptr, 0, st));
+    VFMM_CHECK(split_gemm(PS.s2m, w.fsl, mo->tm_s2m, mo->Kp, mo->Rx, w.s2m_out, w.err, nullptr, 0, st,
+                          w.cev ? w.cev + 2 : nullptr));
     s2m_finish_kernel<<<T.n_leaves * PS.R, 128, 0, st>>>(T.n_leaves, PS.R, o.k * o.k, o.p, mo->Rx, T.box_of_leaf,
                                                          T.level, T.width, f, o.s2m, w.s2m_out, mo->s2m_E, w.Ef,
                                                          Mexp);
@@ -429,14 +430,14 @@ int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const d
                                                                           w.glev, (bf16*)w.msl);
     VFMM_CUDA(cudaGetLastError());
     return split_gemm(PS.m2l, w.msl, mo->tm_m2l, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, (size_t)T.n_boxes * R,
-                      st);
+                      st, w.cev ? w.cev + 4 : nullptr);
 }
 
 // ---------------------------------------------------------------- S2L
 int s2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     return split_gemm(PS.s2l, w.fsl, mo->tm_s2l, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part, (size_t)T.n_boxes * PS.R,
-                      st);
+                      st, w.cev ? w.cev + 6 : nullptr);
 }
 
 // ---------------------------------------------------------------- leaf far field
@@ -480,7 +481,7 @@ int far_leaf_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, co
                                                           Lexp, w.Et, (bf16*)w.aprep);
     VFMM_CUDA(cudaGetLastError());
     return split_gemm(PS.far, w.aprep, mo->tm_far, mo->Kx, mo->Rp, w.far_out, w.err, w.part,
-                      (size_t)T.n_leaves * PS.R, st);
+                      (size_t)T.n_leaves * PS.R, st, w.cev ? w.cev + 8 : nullptr);
 }
 
 }  // namespace vfmm
