@@ -270,7 +270,7 @@ int vfmm_batch_streams(const vfmm_batch* batch, int32_t* active);
 
 /* Schedule autotuner (no counterpart in the paper): for the VFMM_MIXED form, times each small
  * split contraction of this tree and nrhs (near field, M2L, S2L, leaf far field: those with fewer
- * CTAs than two per SM) with split-K factors 1, 2, 4, 8 on the caller's data, keeps the fastest
+ * CTAs than two per SM) with split-K factors 1, 2, 4, 8, 16 on the caller's data, keeps the fastest
  * in the tree's schedule (used by every later call with this nrhs) and returns them in
  * splits[4] (near, M2L, S2L, far; may be NULL). Runs two ordinary solves around the timing, so
  * u, u_x, u_y hold the solution afterwards; synchronises `stream`. Must not overlap other calls

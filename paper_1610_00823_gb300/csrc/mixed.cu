@@ -569,10 +569,12 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
     }
     const int tile_rows = table_rows_per_tile(P.transposed);
     if (Kp % kKBlock || Rp % tile_rows) return fail(VFMM_ERR_INTERNAL, "split GEMM shape not tiled");
-    static bool attr = false;
-    if (!attr) {
+    static thread_local int attr_dev = -1;  // the attribute is per device
+    int dev = 0;
+    VFMM_CUDA(cudaGetDevice(&dev));
+    if (attr_dev != dev) {
         VFMM_CUDA(cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
-        attr = true;
+        attr_dev = dev;
     }
     SplitArgs a;
     a.asl = (const bf16*)asl;

@@ -26,7 +26,7 @@ constexpr int kEpilogueThreads = 32 * kEpilogueWarps;
 constexpr int kProducerThreads = 96;
 constexpr int kMmaWarp = kEpilogueWarps + kProducerThreads / 32;  // 11
 constexpr int kThreads = 32 * (kMmaWarp + 1);                     // 384: 3 warps per SM sub-partition
-constexpr int kMaxSplit = 8;  // largest split-K factor (partial sums held for small contractions only)
+constexpr int kMaxSplit = 16;  // largest split-K factor (partial sums held for small contractions only)
 static_assert(kNumAcc * kTileN <= kTmemCols, "TMEM budget");
 
 // Orientation of the near-field and leaf far-field contractions: with 3k^2 a multiple of 128

@@ -152,7 +152,7 @@ def test_autotuned_schedule_keeps_results():
     ws = workspace(gt, ops, 1)
     stream = torch.cuda.Stream()
     splits = tune(gt, ops, f, out, ws, stream)
-    assert set(splits) == {"near", "m2l", "s2l", "far"} and all(s in (1, 2, 4, 8) for s in splits.values())
+    assert set(splits) == {"near", "m2l", "s2l", "far"} and all(s in (1, 2, 4, 8, 16) for s in splits.values())
     again = v.volume_potential(gt, ops, f, ws=ws, stream=stream)
     stream.synchronize()
     for q in range(3):
