@@ -254,7 +254,7 @@ def run_batch(args):
         from paper_1610_00823_gb300 import build as b
         b.build()
     import paper_1610_00823_gb300 as v
-    from paper_1610_00823_gb300.api import Batch, solve_work, tune, volume_potential_profiled, workspace
+    from paper_1610_00823_gb300.api import Batch, tune, volume_potential_profiled, workspace
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
@@ -317,12 +317,14 @@ def run_batch(args):
     tc, near_ms, launches = 0.0, 0.0, 0
     for tree, ops, f, out, ws in items_mx:
         stages, nl = volume_potential_profiled(tree, ops, f, out, ws, stream=stream)
-        tc += solve_work(tree, ops)["near_tc_flops"]
+        kk_m = tree.k * tree.k
+        tc += 36.0 * 2.0 * 3 * kk_m * kk_m * tree.list_len[0]  # algorithmic slice-product flops
         near_ms += stages.get("near_tc") or stages["near"]
         launches += nl
     peaks, peak_kind = measured_peaks()
     achieved = tc / (near_ms / 1e3) / 1e12
     roof = {"kernel": "split_gemm_kernel (near field, split-BF16 tcgen05), summed over members",
+            "flops": "algorithmic: 36 slice products x 2 x 3k^2 x k^2 per U-list entry",
             "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
             "frac": achieved / peaks["bf16_tflops"], "traffic": None, "peak_source": "%s bf16 burst" % peak_kind,
             "flops_per_launch": tc / n_members, "ms_per_launch": near_ms / n_members,
@@ -434,6 +436,7 @@ def main():
         b.build()
     import paper_1610_00823_gb300 as v
     from paper_1610_00823_gb300.api import SolveGraph, solve_work, tune, volume_potential_profiled, workspace
+    from paper_1610_00823_gb300.replicas import barrier, max_over_ranks, whole_job_rate
 
     src = wl.sources[0]
     t0 = time.perf_counter()
@@ -478,8 +481,7 @@ def main():
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
+        barrier(dist)
         torch.cuda.synchronize()
         times = []
         if clk is not None:
@@ -496,8 +498,7 @@ def main():
         torch.cuda.synchronize()
         if clk is not None:
             clk.stop()
-        if dist is not None:
-            dist.barrier()
+        barrier(dist)
         torch.cuda.synchronize()
         return times, out_, ws_, graph_
 
@@ -511,12 +512,8 @@ def main():
         stages, launches = volume_potential_profiled(tree, ops, f, out, ws, stream=stream)
         for kname, val in stages.items():
             stage_acc[kname] = stage_acc.get(kname, 0.0) + val
-    ms = statistics.mean(step_ms)
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * n_targets / (ms / 1e3)
+    ms = max_over_ranks(statistics.mean(step_ms), dist)
+    value = whole_job_rate(n_targets, ms, world)
     stage_ms = {kname: val / n_prof for kname, val in stage_acc.items()}
 
     # end to end through the host entry point (pinned buffers, copies inside the timed region)
@@ -532,7 +529,7 @@ def main():
         t0 = time.perf_counter()
         v.volume_potential_host(tree, ops, f_host, out_host=outs_host, ws=ws_io, stream=stream)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = world * n_targets / (statistics.mean(e2e_ms) / 1e3)
+    e2e_value = whole_job_rate(n_targets, max_over_ranks(statistics.mean(e2e_ms), dist), world)
     del ws_io
 
     peaks, peak_kind = measured_peaks()
@@ -547,22 +544,33 @@ def main():
     else:
         work = solve_work(tree, ops, nrhs)
         peak = peaks["bf16_tflops"]
-        # every split tensor-core contraction: executed BF16 flops (all 36 slice products, padded
-        # tiles included) over its own CUDA-event time (the kernel and its split-K reduction)
+        # algorithmic work of each split contraction: the 36 BF16 slice products of every real
+        # multiply-add the method needs (list entries x rows x K, no zero rows, no padding); the
+        # kernels also execute zero rows of targets lacking a table in their group and padded tiles
+        # ("executed")
+        P2 = 2 * (wl.p + 1)
+        n_u, n_v, n_w, n_x = tree.list_len
+        alg_fp64eq = {"near": 2.0 * 3 * kk * kk * n_u, "s2m": 2.0 * 2 * wl.p * kk * tree.n_leaves,
+                      "m2l": 2.0 * 2 * wl.p * P2 * n_v, "s2l": 2.0 * 2 * wl.p * kk * n_x,
+                      "far": 2.0 * 3 * kk * (P2 - 2) * tree.n_leaves + 2.0 * 3 * kk * P2 * n_w}
         contractions = {}
         for name in ("near", "s2m", "m2l", "s2l", "far"):
             ms_c = stage_ms.get(name + "_tc", 0.0)
-            fl = work[name + "_tc_flops"]
-            if ms_c > 0 and fl > 0:
-                contractions[name] = {"tflop_executed": fl / 1e12, "ms": ms_c,
-                                      "tflops": fl / (ms_c / 1e3) / 1e12,
-                                      "frac_of_bf16_peak": fl / (ms_c / 1e3) / 1e12 / peak}
-        tc = work["near_tc_flops"]
+            ex = work[name + "_tc_flops"]
+            alg = 36.0 * alg_fp64eq[name] * nrhs
+            if ms_c > 0 and ex > 0:
+                contractions[name] = {"tflop_algorithmic": alg / 1e12, "tflop_executed": ex / 1e12, "ms": ms_c,
+                                      "tflops": alg / (ms_c / 1e3) / 1e12,
+                                      "frac_of_bf16_peak": alg / (ms_c / 1e3) / 1e12 / peak,
+                                      "executed_tflops": ex / (ms_c / 1e3) / 1e12, "useful_fraction": alg / ex}
+        alg_near = 36.0 * alg_fp64eq["near"] * nrhs
         near_ms = stage_ms.get("near_tc") or stage_ms["near"]
-        achieved = tc / (near_ms / 1e3) / 1e12
+        achieved = alg_near / (near_ms / 1e3) / 1e12
         roof = {"kernel": "split_gemm_kernel (near field, split-BF16 tcgen05)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "%s bf16 burst" % peak_kind, "flops_per_launch": tc, "ms_per_launch": near_ms,
+                "peak_source": "%s bf16 burst" % peak_kind, "flops_per_launch": alg_near, "ms_per_launch": near_ms,
+                "flops": "algorithmic: 36 slice products x 2 x 3k^2 x k^2 per U-list entry",
+                "executed_tflops": work["near_tc_flops"] / (near_ms / 1e3) / 1e12,
                 "fp64_equivalent_tflops": work["near_fp64eq_flops"] / (near_ms / 1e3) / 1e12,
                 "contractions": contractions}
 
@@ -574,14 +582,10 @@ def main():
         torch.cuda.synchronize()
         t_ops64 = time.perf_counter() - t0
         ms64_list, out64, ws64, _g64 = time_form(ops64, max(3, min(args.steps, 10)))
-        ms64 = statistics.mean(ms64_list)
-        if dist is not None:
-            tt = torch.tensor([ms64], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms64 = float(tt.item())
+        ms64 = max_over_ranks(statistics.mean(ms64_list), dist)
         d = [torch.max(torch.abs(out[q] - out64[q])).item() / torch.max(torch.abs(out64[q])).item()
              for q in range(3)]
-        fp64_form = {"value": world * n_targets / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+        fp64_form = {"value": whole_job_rate(n_targets, ms64, world), "unit": UNIT, "ms_per_step": ms64,
                      "steps": len(ms64_list), "ops_create_s": t_ops64,
                      "mixed_over_fp64_speedup": ms64 / ms, "rel_diff_mixed_vs_fp64_all_targets": d}
         del ws64, _g64
