@@ -447,7 +447,7 @@ __global__ void far_operand_kernel(int nleaf, int R, int P2, int Kx, const int32
                                    const int32_t* __restrict__ far_slot, const int32_t* __restrict__ wptr,
                                    const int32_t* __restrict__ widx, const double* __restrict__ Mexp,
                                    const double* __restrict__ Lexp, int* __restrict__ Et, bf16* __restrict__ aprep) {
-    __shared__ double red[128];
+    __shared__ int red[4];
     const int vl = blockIdx.x;
     const int leaf = vl / R, r = vl - leaf * R;
     const int b = box_of_leaf[leaf];
@@ -457,15 +457,18 @@ __global__ void far_operand_kernel(int nleaf, int R, int P2, int Kx, const int32
         if (j == 0) return k >= 2 ? Lexp[((size_t)b * R + r) * P2 + k] : 0.0;
         return Mexp[((size_t)widx[wptr[b] + j - 1] * R + r) * P2 + k];
     };
-    double m = 0.0;
-    for (int q = threadIdx.x; q < ns * P2; q += blockDim.x) m = fmax(m, fabs(value(q / P2, q % P2)));
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
+    // E_t = exponent bound of the largest value, as the largest exponent bound (integer work)
+    int em = INT_MIN;
+    for (int q = threadIdx.x; q < ns * P2; q += blockDim.x) {
+        const double v = value(q / P2, q % P2);
+        if (v != 0.0) em = max(em, exp_bound(v));
     }
-    const int e = exp_bound(red[0]);
+    for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = em;
+    __syncthreads();
+    int e = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) e = max(e, red[w]);
+    if (e == INT_MIN) e = 0;  // all zero
     if (threadIdx.x == 0) Et[vl] = e;
     for (int q = threadIdx.x; q < ns * Kx; q += blockDim.x) {
         int j = q / Kx, k = q % Kx;
