@@ -738,31 +738,44 @@ __global__ void leaf_scalar_kernel(int nleaf, int R, int P, double width, const 
 
 // Mixed form, one CTA per virtual leaf (leaf, r), one thread per node: u, u_x, u_y = near + far +
 // scalar, the split contraction outputs (hi, lo) scaled back by their power-of-two exponents.
-__global__ void leaf_mixed_kernel(int nleaf, int R, int kk, int Rp, double width, double inv_width,
+__global__ void leaf_mixed_kernel(int nleaf, int R, int kk, int Rp, int lw, double wm,
                                   const int32_t* __restrict__ box_of_leaf, const int32_t* __restrict__ level,
                                   const float2* __restrict__ nearmix, const int* __restrict__ Er,
                                   const int* __restrict__ Ef, const float2* __restrict__ farmix,
                                   const int* __restrict__ farE, const int* __restrict__ Et,
                                   const double* __restrict__ scal, double* __restrict__ u, double* __restrict__ ux,
                                   double* __restrict__ uy) {
+    // width = wm 2^lw with wm in [1, 2): h = wm 2^(lw - lv), so every power-of-two scale is folded
+    // into the exponents (f2d_scaled), times wm^(2, 1, -1) when wm is not one
     const unsigned vl = blockIdx.x;
     const int t = threadIdx.x;
     if (t >= kk) return;
     const unsigned leaf = vl / (unsigned)R, r = vl - leaf * (unsigned)R;
-    const double w2h = width * width;
     const int lv = level[box_of_leaf[leaf]];
     const float2* nm = nearmix + (size_t)vl * Rp;
     const float2* fm = farmix + (size_t)vl * Rp;
-    const int ef = Ef[r] - lv, et = Et[vl] + lv;  // h = width 2^-lv: scales are exact powers of two
+    const int en = Ef[r] + lw - lv, ef = Et[vl] + lv - lw;  // near scale h 2^E_f, far scale 2^E_t / h
     const float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
     const float2 w0 = fm[t], w1 = fm[kk + t], w2 = fm[2 * kk + t];
+    const int e0 = en + lw - lv + Er[t], e1 = en + Er[kk + t], e2 = en + Er[2 * kk + t];
+    double n0 = f2d_scaled(v0.x, e0) + f2d_scaled(v0.y, e0);  // h^2 x near u
+    double n1 = f2d_scaled(v1.x, e1) + f2d_scaled(v1.y, e1);  // h x near u_x
+    double n2 = f2d_scaled(v2.x, e2) + f2d_scaled(v2.y, e2);
+    const int g0 = Et[vl] + farE[t], g1 = ef + farE[kk + t], g2 = ef + farE[2 * kk + t];
+    const double f0 = f2d_scaled(w0.x, g0) + f2d_scaled(w0.y, g0);
+    double f1 = f2d_scaled(w1.x, g1) + f2d_scaled(w1.y, g1);  // far u_x / h
+    double f2 = f2d_scaled(w2.x, g2) + f2d_scaled(w2.y, g2);
+    if (wm != 1.0) {
+        n0 *= wm * wm;
+        n1 *= wm;
+        n2 *= wm;
+        f1 /= wm;
+        f2 /= wm;
+    }
     const size_t o = ((size_t)r * nleaf + leaf) * kk + t;
-    u[o] = w2h * ((double)v0.x + (double)v0.y) * pow2(ef - lv + Er[t]) + scal[vl] +
-           ((double)w0.x + (double)w0.y) * pow2(et - lv + farE[t]);
-    ux[o] = width * ((double)v1.x + (double)v1.y) * pow2(ef + Er[kk + t]) +
-            inv_width * ((double)w1.x + (double)w1.y) * pow2(et + farE[kk + t]);
-    uy[o] = width * ((double)v2.x + (double)v2.y) * pow2(ef + Er[2 * kk + t]) +
-            inv_width * ((double)w2.x + (double)w2.y) * pow2(et + farE[2 * kk + t]);
+    u[o] = n0 + scal[vl] + f0;
+    ux[o] = n1 + f1;
+    uy[o] = n2 + f2;
 }
 
 // ---------------------------------------------------------------- leaf pass (one CTA per leaf)
@@ -1215,9 +1228,12 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         leaf_scalar_kernel<<<(unsigned)((nv + 127) / 128), 128, 0, st>>>(
             nleaf, R, P, T.width, T.box_of_leaf, T.level, T.lptr[VFMM_LIST_U], T.lidx[VFMM_LIST_U],
             T.lptr[VFMM_LIST_W], T.lidx[VFMM_LIST_W], w.Mexp, w.Lexp, w.mix.scal);
-        leaf_mixed_kernel<<<(unsigned)nv, ((kk + 31) / 32) * 32, 0, st>>>(nleaf, R, kk, mo->Rp, T.width, 1.0 / T.width, T.box_of_leaf, T.level,
-                                                w.mix.out, mo->Er, w.mix.Ef, w.mix.far_out, mo->far_E, w.mix.Et,
-                                                w.mix.scal, u, ux, uy);
+        int lw = 0;
+        const double wm = 2.0 * std::frexp(T.width, &lw);  // width = wm 2^lw, wm in [1, 2)
+        lw -= 1;
+        leaf_mixed_kernel<<<(unsigned)nv, ((kk + 31) / 32) * 32, 0, st>>>(
+            nleaf, R, kk, mo->Rp, lw, wm, T.box_of_leaf, T.level, w.mix.out, mo->Er, w.mix.Ef, w.mix.far_out,
+            mo->far_E, w.mix.Et, w.mix.scal, u, ux, uy);
         launches += 2;
     } else {
         leaf_kernel<<<(unsigned)nleaf, ((kk + 31) / 32) * 32, 0, st>>>(a);

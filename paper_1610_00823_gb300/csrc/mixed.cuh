@@ -62,6 +62,20 @@ __device__ __forceinline__ double pow2(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
+// (double)x * 2^e for a float x from the bits, with integer operations only (the FP64 units are
+// the scarce ones): sign and mantissa move over, the exponent is rebiased and shifted by e. A zero
+// or subnormal x gives (signed) zero: the (hi, lo) outputs of the split contractions are
+// normalised, so a part below 2^-126 is far below the rounding of the sum it belongs to. The
+// result must lie in the normal double range.
+__device__ __forceinline__ double f2d_scaled(float x, int e) {
+    const unsigned int u = __float_as_uint(x);
+    const int ex = (int)((u >> 23) & 0xFF);
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long mag = ((unsigned long long)(ex - 127 + 1023 + e) << 52) |
+                                   ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)(sign | (ex == 0 ? 0ull : mag)));
+}
+
 // Binary exponent e with |m| < 2^e (frexp convention), from the bits; 0 for m = 0.
 __device__ __forceinline__ int exp_bound(double m) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
