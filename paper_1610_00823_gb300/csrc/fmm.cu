@@ -428,6 +428,8 @@ struct DownArgs {
     const int* m2l_E;   // [Rx] row exponents of the M2L tables
     const int* m2l_G;   // [depth + 1] level exponents of the multipole operand
     const double* m2l_c0;  // Re of local coefficient 0 from the V and X lists, with the log(h) terms
+    int lw;                 // root width = wm 2^lw, wm in [1, 2)
+    double wm;
     const float2* s2l_out; // split-precision S2L rows 2..2p+1, scaled by 2^-(E_f + E_r)
     const int* s2l_E;
     const int* Ef;
@@ -513,15 +515,23 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
 // the FP64 coefficient 0 (V and X rows 0 with the log(h) terms).
 __device__ __forceinline__ double2 combine_local(const DownArgs& d, int level, int b, int r, int t, double re,
                                                  double im) {
+    // (hi, lo) outputs to FP64 with their power-of-two scales folded into the exponent bits; the
+    // S2L factor (2h)^2 = wm^2 2^(2 + 2 (lw - level)) for a root width wm 2^lw
     const size_t vb = (size_t)b * d.R + r;
-    const double h = ldexp(d.width, -level);
     const bool has_v = d.vptr[b + 1] > d.vptr[b], has_x = d.xptr[b + 1] > d.xptr[b];
     if (has_x && t >= 1) {
         const float2 vr = d.s2l_out[vb * d.Rx + 2 * (t - 1)];
         const float2 vi = d.s2l_out[vb * d.Rx + 2 * (t - 1) + 1];
-        const double sc = 4.0 * h * h * pow2(d.Ef[r]);
-        re += sc * ((double)vr.x + (double)vr.y) * pow2(d.s2l_E[2 * (t - 1)]);
-        im += sc * ((double)vi.x + (double)vi.y) * pow2(d.s2l_E[2 * (t - 1) + 1]);
+        const int e = d.Ef[r] + 2 + 2 * (d.lw - level);
+        const int er = e + d.s2l_E[2 * (t - 1)], ei = e + d.s2l_E[2 * (t - 1) + 1];
+        double sr = f2d_scaled(vr.x, er) + f2d_scaled(vr.y, er);
+        double si = f2d_scaled(vi.x, ei) + f2d_scaled(vi.y, ei);
+        if (d.wm != 1.0) {
+            sr *= d.wm * d.wm;
+            si *= d.wm * d.wm;
+        }
+        re += sr;
+        im += si;
     }
     if (has_v || has_x) {
         if (t == 0) {
@@ -530,8 +540,9 @@ __device__ __forceinline__ double2 combine_local(const DownArgs& d, int level, i
             const float2 vr = d.m2l_out[vb * d.Rx + 2 * (t - 1)];
             const float2 vi = d.m2l_out[vb * d.Rx + 2 * (t - 1) + 1];
             const int g = d.m2l_G[(size_t)level * d.R + r];
-            re += ((double)vr.x + (double)vr.y) * pow2(g + d.m2l_E[2 * (t - 1)]);
-            im += ((double)vi.x + (double)vi.y) * pow2(g + d.m2l_E[2 * (t - 1) + 1]);
+            const int er = g + d.m2l_E[2 * (t - 1)], ei = g + d.m2l_E[2 * (t - 1) + 1];
+            re += f2d_scaled(vr.x, er) + f2d_scaled(vr.y, er);
+            im += f2d_scaled(vi.x, ei) + f2d_scaled(vi.y, ei);
         }
     }
     return make_double2(re, im);
@@ -990,6 +1001,8 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     const MixedOps* mo = (const MixedOps*)o.mixed;
     d.R = R;
     d.nleaf = T.n_leaves;
+    d.wm = 2.0 * std::frexp(T.width, &d.lw);
+    d.lw -= 1;
     d.begin = T.level_start[l];
     d.end = T.level_start[l + 1];
     d.P = o.p + 1;

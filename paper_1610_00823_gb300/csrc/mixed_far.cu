@@ -346,11 +346,14 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
             M[1] = 0.0;
         }
     }
-    const int ef = Ef[r];
-    const double hh = h * h;
+    // h^2 = wm^2 2^(2 (lw - level)): the power of two goes into the exponent bits
+    int lw = 0;
+    const double wm = 2.0 * frexp(width, &lw);
+    const int ef = Ef[r] + 2 * (lw - 1 - level[b]);
     for (int q = threadIdx.x; q < 2 * p; q += blockDim.x) {
-        float2 v = out[(size_t)vl * Rx + q];
-        M[2 + q] = hh * (((double)v.x + (double)v.y) * pow2(ef + E[q]));
+        const float2 v = out[(size_t)vl * Rx + q];
+        const double m = f2d_scaled(v.x, ef + E[q]) + f2d_scaled(v.y, ef + E[q]);
+        M[2 + q] = wm == 1.0 ? m : wm * wm * m;
     }
 }
 
