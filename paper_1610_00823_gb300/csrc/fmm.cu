@@ -75,7 +75,6 @@ __global__ void __launch_bounds__(256) m2l_c0_kernel(int begin, int end, int R, 
                 const double2 x = reinterpret_cast<const double2*>(Mexp + ((size_t)vidx[e] * R + r) * 2 * P)[n];
                 const double2 m = sM[vcfg[e] * P + n];
                 acc += m.x * x.x - m.y * x.y;
-                if (n == 0) acc += x.x * logh;
                 n += 32;
                 while (n >= P) {
                     n -= P;
@@ -83,6 +82,10 @@ __global__ void __launch_bounds__(256) m2l_c0_kernel(int begin, int end, int R, 
                 }
             }
         }
+        // log(h) a_0(c) of every V entry: one lane per entry
+        double a0 = 0.0;
+        for (int e = vptr[b] + lane; e < e_end; e += 32) a0 += Mexp[((size_t)vidx[e] * R + r) * 2 * P];
+        acc += a0 * logh;
         // X list: (2h)^2 [Re(S2L row 0) . f_c + log(h) W . f_c], with W . f_c = a_0(c) / (2h)^2
         for (int e = xptr[b]; e < xptr[b + 1]; ++e) {
             const double* fc = f + ((size_t)r * nleaf + leaf_of_box[xidx[e]]) * kk;

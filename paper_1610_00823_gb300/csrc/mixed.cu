@@ -91,19 +91,26 @@ __global__ void fmax_abs_kernel(const double* __restrict__ f, int64_t n, unsigne
     if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(m));
 }
 
-// fsl[leaf * R + r][i][k] from f_r[leaf][k] / 2^E_f[r]; also stores E_f[r]. One CTA per row
-// (virtual leaf), one thread per k.
+// fsl[leaf * R + r][i][k] from f_r[leaf][k] / 2^E_f[r]; also stores E_f[r]. One thread per 8
+// consecutive values of a row (one 16-byte store per slice).
 __global__ void f_slice_kernel(const double* __restrict__ f, int nleaf, int kk, int Kp, int R,
                                const unsigned long long* __restrict__ fmax_bits, int* __restrict__ Ef,
                                bf16* __restrict__ fsl) {
-    const unsigned row = blockIdx.x;
-    const int k = threadIdx.x;
-    if (k >= Kp) return;
+    const unsigned cpr = (unsigned)Kp / 8;  // chunks per row
+    const unsigned g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (unsigned)nleaf * (unsigned)R * cpr) return;
+    const unsigned row = g / cpr, c = g - row * cpr;
     const unsigned leaf = row / (unsigned)R, r = row - leaf * (unsigned)R;
     const int e = exp_bound(__longlong_as_double((long long)fmax_bits[r]));
-    const double v = k < kk ? f[((size_t)r * nleaf + leaf) * kk + k] : 0.0;
-    slice_fixed(v, e, fsl + slice_off(row, Kp, k), kKBlock);
-    if (leaf == 0 && k == 0) Ef[r] = e;
+    const double* fr = f + ((size_t)r * nleaf + leaf) * kk;
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int k = 8 * (int)c + j;
+        v[j] = k < kk ? fr[k] : 0.0;
+    }
+    slice8_fixed(v, e, fsl + slice_off(row, Kp, 8 * (int)c), kKBlock);
+    if (leaf == 0 && c == 0) Ef[r] = e;
 }
 
 // ---------------------------------------------------------------- the tcgen05 kernel
@@ -675,8 +682,9 @@ int near_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const 
     VFMM_CUDA(cudaMemsetAsync(w.fmax, 0, (size_t)R * sizeof(unsigned long long), st));
     const int64_t n = (int64_t)T.n_leaves * kk;
     fmax_abs_kernel<<<dim3((unsigned)std::min<int64_t>(1024, (n + 255) / 256), R), 256, 0, st>>>(f, n, w.fmax);
-    f_slice_kernel<<<(unsigned)((int64_t)T.n_leaves * R), mo->Kp, 0, st>>>(f, T.n_leaves, kk, mo->Kp, R, w.fmax, w.Ef,
-                                                                           (bf16*)w.fsl);
+    const int64_t nchunk = (int64_t)T.n_leaves * R * (mo->Kp / 8);
+    f_slice_kernel<<<(unsigned)((nchunk + 255) / 256), 256, 0, st>>>(f, T.n_leaves, kk, mo->Kp, R, w.fmax, w.Ef,
+                                                                     (bf16*)w.fsl);
     VFMM_CUDA(cudaGetLastError());
     return split_gemm(PS.near, w.fsl, mo->tm_near, mo->Kp, mo->Rp, w.out, w.err, w.part, (size_t)T.n_leaves * R, st,
                       w.cev ? w.cev + 0 : nullptr);

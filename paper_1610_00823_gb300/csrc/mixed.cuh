@@ -84,6 +84,16 @@ __device__ __forceinline__ int exp_bound(double m) {
     return (ev ? ev : 1) - 1022;
 }
 
+// slice_fixed of 8 consecutive values (one exponent bound E) with each slice's 8 BF16 written
+// by one 16-byte store: out + i * stride for slice i (16-byte aligned).
+__device__ __forceinline__ void slice8_fixed(const double* v, int E, __nv_bfloat16* out, int stride) {
+    __align__(16) __nv_bfloat16 tmp[kSlices][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) slice_fixed(v[j], E, &tmp[0][j], 8);
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i) *reinterpret_cast<uint4*>(out + (size_t)i * stride) = *reinterpret_cast<uint4*>(tmp[i]);
+}
+
 struct MixedOps {
     int N = kTileN; // table rows per tile
     int Rp = 0;     // 3k^2 rounded up to N

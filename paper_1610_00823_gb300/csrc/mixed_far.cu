@@ -407,17 +407,32 @@ __global__ void level_exp_kernel(const int32_t* __restrict__ level_start, int lm
     if (threadIdx.x == 0) G[(size_t)l * R + r] = red[0] == INT_MIN ? 0 : red[0];
 }
 
+// One thread per 8 consecutive coefficients of a virtual box (one 16-byte store per slice).
 __global__ void multipole_slice_kernel(const int32_t* __restrict__ level, int64_t vb0, int64_t vb1, int R, int P2,
                                        int Kx, const double* __restrict__ Mexp, const int* __restrict__ G,
                                        bf16* __restrict__ msl) {
+    const int cpr = Kx / 8;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (vb1 - vb0) * Kx) return;
-    const int64_t vb = vb0 + q / Kx;
-    const int k = (int)(q % Kx);
+    if (q >= (vb1 - vb0) * cpr) return;
+    const int64_t vb = vb0 + q / cpr;
+    const int c = (int)(q % cpr);
     const int64_t b = vb / R;
     const int r = (int)(vb - b * R);
-    const double a = k < P2 ? Mexp[(size_t)vb * P2 + k] : 0.0;
-    slice_fixed(a, G[(size_t)level[b] * R + r] - (k >> 2), msl + slice_at(vb, Kx, k), kKBlock);
+    // coefficient k is scaled by 2^(floor(k/4) - G): within a chunk of 8, k/4 takes two values
+    const int g = G[(size_t)level[b] * R + r];
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int k = 8 * c + j;
+        v[j] = k < P2 ? Mexp[(size_t)vb * P2 + k] : 0.0;
+    }
+    __align__(16) bf16 tmp[kSlices][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) slice_fixed(v[j], g - ((8 * c + j) >> 2), &tmp[0][j], 8);
+    bf16* out = msl + slice_at(vb, Kx, 8 * c);
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i)
+        *reinterpret_cast<uint4*>(out + (size_t)i * kKBlock) = *reinterpret_cast<uint4*>(tmp[i]);
 }
 
 int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* Mexp, const MixedWork& w,
@@ -428,7 +443,7 @@ int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const d
     const int64_t vb0 = (int64_t)T.level_start[2] * R, vb1 = (int64_t)T.level_start[T.depth + 1] * R;
     box_exp_kernel<<<(unsigned)((vb1 - vb0 + 7) / 8), 256, 0, st>>>(vb0, vb1, P2, Mexp, w.bexp);
     level_exp_kernel<<<dim3(T.depth - 1, R), 256, 0, st>>>(T.level_start_dev, 2, R, w.bexp, w.glev);
-    const int64_t n2 = (vb1 - vb0) * mo->Kx;
+    const int64_t n2 = (vb1 - vb0) * (mo->Kx / 8);
     multipole_slice_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(T.level, vb0, vb1, R, P2, mo->Kx, Mexp,
                                                                           w.glev, (bf16*)w.msl);
     VFMM_CUDA(cudaGetLastError());
