@@ -268,6 +268,15 @@ int vfmm_batch_tune(vfmm_batch* batch, int32_t n, const vfmm_batch_item* items, 
                     int32_t* best_streams, float* best_ms);
 int vfmm_batch_streams(const vfmm_batch* batch, int32_t* active);
 
+/* Failure-path self-test (no counterpart in the paper). Every wait inside the tensor-core kernels
+ * is bounded; when one runs out the kernel records an error word and returns, and the call
+ * reports VFMM_ERR_TIMEOUT instead of hanging. This call exercises that path without any fault:
+ * a one-warp kernel waits, through the same bounded wait, on an mbarrier that nothing arrives on,
+ * gives up after `polls` polls (1..2^20) and records the word, which is read back as a solve does.
+ * Returns VFMM_ERR_TIMEOUT (the expected outcome; the context stays usable), INVALID_ARG for a
+ * bad `polls`, INTERNAL if the wait completed, CUDA on a CUDA error. Synchronises `stream`. */
+int vfmm_selftest_wait_timeout(int64_t polls, void* stream);
+
 /* Schedule autotuner (no counterpart in the paper): for the VFMM_MIXED form, times each small
  * split contraction of this tree and nrhs (near field, M2L, S2L, leaf far field: those with fewer
  * CTAs than two per SM) with split-K factors 1, 2, 4, 8, 16 on the caller's data, keeps the fastest

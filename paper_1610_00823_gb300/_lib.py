@@ -65,6 +65,7 @@ EXPORTS = {
     "vfmm_volume_potential_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vfmm_solve_work": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, c_double_p],
+    "vfmm_selftest_wait_timeout": [ctypes.c_int64, ctypes.c_void_p],
     "vfmm_tune": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, c_int32_p],
     "vfmm_graph_create": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,

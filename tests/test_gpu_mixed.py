@@ -158,3 +158,25 @@ def test_autotuned_schedule_keeps_results():
     for q in range(3):
         assert rel(out[q].cpu().numpy(), u64[q].cpu().numpy()) < TOL
         assert rel(again[q].cpu().numpy(), u64[q].cpu().numpy()) < TOL
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """The failure path of the tensor-core kernels: a bounded wait that runs out (an mbarrier that
+    nothing arrives on) is reported as VFMM_ERR_TIMEOUT, and the GPU context stays usable."""
+    import ctypes
+    import time
+    from paper_1610_00823_gb300 import _lib
+    lib = _lib.load()
+    t0 = time.time()
+    rc = lib.vfmm_selftest_wait_timeout(ctypes.c_int64(4096), ctypes.c_void_p(0))
+    assert rc == -5  # VFMM_ERR_TIMEOUT
+    assert b"bounded wait ran out" in lib.vfmm_last_error_detail()
+    assert time.time() - t0 < 60.0
+    # a solve afterwards still works and still matches the FP64 form
+    src = W.narrow_gaussians(5, n=3, sigma=0.04)
+    gt = v.tree_build(0.0, 0.0, 1.0, 8, src, 1e-6, 7)
+    f = v.source_sample(gt, src)
+    ref = v.volume_potential(gt, v.ops_create(8, 20, v.FP64), f)
+    got = v.volume_potential(gt, v.ops_create(8, 20, v.MIXED), f)
+    for q in range(3):
+        assert rel(got[q].cpu().numpy(), ref[q].cpu().numpy()) < TOL
