@@ -166,14 +166,15 @@ __device__ inline void gemm_tile_fp64(const double* __restrict__ A, int M, int K
     }
 }
 
-// Near field: one tile = (configuration, range of its U entries); blockIdx.x = row tile.
+// Near field: one tile = (configuration, range of its U entries). Every gather GEMM here takes
+// its column tile from blockIdx.x (no 65,535 limit) and its row tile from blockIdx.y.
 __global__ void __launch_bounds__(256) near_gemm_kernel(const int4* __restrict__ tiles, const double* __restrict__ T,
                                                         int kk, const int32_t* __restrict__ u_by_cfg,
                                                         const int32_t* __restrict__ lidxU,
                                                         const int32_t* __restrict__ leaf_of_box,
                                                         const double* __restrict__ f, double* __restrict__ slab) {
     __shared__ ColPtrs cp;
-    const int4 tl = tiles[blockIdx.y];  // cfg, begin, end
+    const int4 tl = tiles[blockIdx.x];  // cfg, begin, end
     const int ncols = min(GBN, tl.z - tl.y);
     if (threadIdx.x < GBN) {
         int j = threadIdx.x;
@@ -188,7 +189,61 @@ __global__ void __launch_bounds__(256) near_gemm_kernel(const int4* __restrict__
         cp.scale[j] = 1.0;
     }
     __syncthreads();
-    gemm_tile_fp64(T + (size_t)tl.x * 3 * kk * kk, 3 * kk, kk, blockIdx.x * GBM, ncols, cp);
+    gemm_tile_fp64(T + (size_t)tl.x * 3 * kk * kk, 3 * kk, kk, blockIdx.y * GBM, ncols, cp);
+}
+
+// FP64 M2L over the V list: one tile = (offset, run of its V entries in offset order); column j =
+// entry e, slab row e = M2L_real[offset] . multipole of the entry's source box (all 2(p+1) rows).
+__global__ void __launch_bounds__(256) v_gemm_kernel(const int4* __restrict__ tiles, const double* __restrict__ A,
+                                                     int P2, const int32_t* __restrict__ by_cfg,
+                                                     const int32_t* __restrict__ lidxV, const double* __restrict__ Mexp,
+                                                     double* __restrict__ vslab) {
+    __shared__ ColPtrs cp;
+    const int4 tl = tiles[blockIdx.x];  // offset, begin, end
+    const int ncols = min(GBN, tl.z - tl.y);
+    if (threadIdx.x < GBN) {
+        const int j = threadIdx.x;
+        if (j < ncols) {
+            const int e = by_cfg[tl.y + j];
+            cp.b[j] = Mexp + (size_t)lidxV[e] * P2;
+            cp.c[j] = vslab + (size_t)e * P2;
+        } else {
+            cp.b[j] = nullptr;
+            cp.c[j] = nullptr;
+        }
+        cp.scale[j] = 1.0;
+    }
+    __syncthreads();
+    gemm_tile_fp64(A + (size_t)tl.x * P2 * P2, P2, P2, blockIdx.y * GBM, ncols, cp);
+}
+
+// FP64 S2L over the X list: column j = entry e (target box b, source leaf c), slab row e =
+// (2 h_b)^2 S2L_real[configuration] . f_c.
+__global__ void __launch_bounds__(256) x_gemm_kernel(const int4* __restrict__ tiles, const double* __restrict__ A,
+                                                     int P2, int kk, const int32_t* __restrict__ by_cfg,
+                                                     const int32_t* __restrict__ lidxX, const int32_t* __restrict__ x_tgt,
+                                                     const int32_t* __restrict__ level, double width,
+                                                     const int32_t* __restrict__ leaf_of_box,
+                                                     const double* __restrict__ f, double* __restrict__ xslab) {
+    __shared__ ColPtrs cp;
+    const int4 tl = tiles[blockIdx.x];
+    const int ncols = min(GBN, tl.z - tl.y);
+    if (threadIdx.x < GBN) {
+        const int j = threadIdx.x;
+        if (j < ncols) {
+            const int e = by_cfg[tl.y + j];
+            const double h = ldexp(width, -level[x_tgt[e]]);
+            cp.b[j] = f + (size_t)leaf_of_box[lidxX[e]] * kk;
+            cp.c[j] = xslab + (size_t)e * P2;
+            cp.scale[j] = 4.0 * h * h;
+        } else {
+            cp.b[j] = nullptr;
+            cp.c[j] = nullptr;
+            cp.scale[j] = 0.0;
+        }
+    }
+    __syncthreads();
+    gemm_tile_fp64(A + (size_t)tl.x * P2 * kk, P2, kk, blockIdx.y * GBM, ncols, cp);
 }
 
 // S2M: columns are leaves; output row = multipole of the leaf's box, scaled by h^2.
@@ -197,7 +252,7 @@ __global__ void __launch_bounds__(256) s2m_gemm_kernel(const double* __restrict_
                                                        const int32_t* __restrict__ level, double width,
                                                        const double* __restrict__ f, double* __restrict__ Mexp) {
     __shared__ ColPtrs cp;
-    const int col0 = blockIdx.y * GBN;
+    const int col0 = blockIdx.x * GBN;
     const int ncols = min(GBN, nleaf - col0);
     if (threadIdx.x < GBN) {
         int j = threadIdx.x;
@@ -215,7 +270,7 @@ __global__ void __launch_bounds__(256) s2m_gemm_kernel(const double* __restrict_
         }
     }
     __syncthreads();
-    gemm_tile_fp64(S2M, P2, kk, blockIdx.x * GBM, ncols, cp);
+    gemm_tile_fp64(S2M, P2, kk, blockIdx.y * GBM, ncols, cp);
 }
 
 // L2T: columns are leaves; input = local expansion of the leaf's box.
@@ -223,7 +278,7 @@ __global__ void __launch_bounds__(256) l2t_gemm_kernel(const double* __restrict_
                                                        const int32_t* __restrict__ box_of_leaf,
                                                        const double* __restrict__ Lexp, double* __restrict__ far) {
     __shared__ ColPtrs cp;
-    const int col0 = blockIdx.y * GBN;
+    const int col0 = blockIdx.x * GBN;
     const int ncols = min(GBN, nleaf - col0);
     if (threadIdx.x < GBN) {
         int j = threadIdx.x;
@@ -238,7 +293,7 @@ __global__ void __launch_bounds__(256) l2t_gemm_kernel(const double* __restrict_
         cp.scale[j] = 1.0;
     }
     __syncthreads();
-    gemm_tile_fp64(L2T, 3 * kk, P2, blockIdx.x * GBM, ncols, cp);
+    gemm_tile_fp64(L2T, 3 * kk, P2, blockIdx.y * GBM, ncols, cp);
 }
 
 // Outputs j and P-1-j of one position of a triangular translation (mode 0, M2M: output o takes
@@ -431,6 +486,8 @@ struct DownArgs {
     const int* m2l_E;   // [Rx] row exponents of the M2L tables
     const int* m2l_G;   // [depth + 1] level exponents of the multipole operand
     const double* m2l_c0;  // Re of local coefficient 0 from the V and X lists, with the log(h) terms
+    const double* vslab;   // FP64 form: [n_V][2(p+1)] M2L of every V entry
+    const double* xslab;   // FP64 form: [n_X][2(p+1)] S2L of every X entry
     int lw;                 // root width = wm 2^lw, wm in [1, 2)
     double wm;
     const float2* s2l_out; // split-precision S2L rows 2..2p+1, scaled by 2^-(E_f + E_r)
@@ -440,7 +497,6 @@ struct DownArgs {
 };
 
 __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
-    __shared__ double src[2 * 256];
     const int R = d.R;
     const int b = d.begin + blockIdx.x / R, r = blockIdx.x % R;
     if (b >= d.end) return;
@@ -454,40 +510,19 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
         re = d.Lexp[vb * 2 * P + 2 * t];
         im = d.Lexp[vb * 2 * P + 2 * t + 1];
     }
-    for (int e = d.m2l_out ? d.vptr[b + 1] : d.vptr[b]; e < d.vptr[b + 1]; ++e) {
-        const int c = d.vidx[e];
-        for (int q = t; q < 2 * P; q += blockDim.x) src[q] = d.Mexp[((size_t)c * R + r) * 2 * P + q];
-        __syncthreads();
-        const double* M = d.m2l_t + (size_t)d.vcfg[e] * P * P * 2;
-        if (t < P) {
-            for (int n = 0; n < P; ++n) {
-                double mr = M[((size_t)n * P + t) * 2], mi = M[((size_t)n * P + t) * 2 + 1];
-                double xr = src[2 * n], xi = src[2 * n + 1];
-                re = fma(mr, xr, fma(-mi, xi, re));
-                im = fma(mr, xi, fma(mi, xr, im));
-            }
-            if (t == 0) re += src[0] * logh;
+    if (!d.m2l_out && t < P) {
+        // FP64 form: M2L and S2L rows from the per-entry slabs of the V and X GEMMs, in list order,
+        // with the log(h) a_0 terms of the scaling
+        for (int e = d.vptr[b]; e < d.vptr[b + 1]; ++e) {
+            re += d.vslab[(size_t)e * 2 * P + 2 * t];
+            im += d.vslab[(size_t)e * 2 * P + 2 * t + 1];
+            if (t == 0) re += d.Mexp[((size_t)d.vidx[e] * R + r) * 2 * P] * logh;
         }
-        __syncthreads();
-    }
-    for (int e = d.m2l_out ? d.xptr[b + 1] : d.xptr[b]; e < d.xptr[b + 1]; ++e) {
-        const int c = d.xidx[e];
-        const double* fc = d.f + ((size_t)r * d.nleaf + d.leaf_of_box[c]) * d.kk;
-        for (int q = t; q < d.kk; q += blockDim.x) src[q] = fc[q];
-        __syncthreads();
-        const double* X = d.s2l_t + (size_t)d.xcfg[e] * d.kk * P * 2;
-        if (t < P) {
-            double sr = 0.0, si = 0.0;
-            for (int s = 0; s < d.kk; ++s) {
-                sr = fma(X[((size_t)s * P + t) * 2], src[s], sr);
-                si = fma(X[((size_t)s * P + t) * 2 + 1], src[s], si);
-            }
-            const double hc2 = 4.0 * h * h;
-            re += hc2 * sr;
-            im += hc2 * si;
-            if (t == 0) re += logh * d.Mexp[((size_t)c * R + r) * 2 * P];
+        for (int e = d.xptr[b]; e < d.xptr[b + 1]; ++e) {
+            re += d.xslab[(size_t)e * 2 * P + 2 * t];
+            im += d.xslab[(size_t)e * 2 * P + 2 * t + 1];
+            if (t == 0) re += logh * d.Mexp[((size_t)d.xidx[e] * R + r) * 2 * P];
         }
-        __syncthreads();
     }
     if (d.m2l_out && t >= 1 && t < P && d.xptr[b + 1] > d.xptr[b]) {
         const float2 vr = d.s2l_out[vb * d.Rx + 2 * (t - 1)];
@@ -885,6 +920,8 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
 
 // ---------------------------------------------------------------- host side
 struct Workspace {
+    double* vslab;      // FP64 form: per V entry M2L rows
+    double* xslab;      // FP64 form: per X entry S2L rows
     const PlanSet* ps;  // split-contraction plans for the folded right-hand sides (mixed form)
     unsigned int* gbar; // [2] grid-barrier counters of the persistent tree passes
     double* Mexp;
@@ -920,6 +957,8 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
     }
     take(w ? &w->slab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
     take(w ? &w->far : &dummy, mixed ? 1 : (size_t)T.n_leaves * 3 * kk);
+    take(w ? &w->vslab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_V] * P2);
+    take(w ? &w->xslab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_X] * P2);
     if (mixed) {
         const MixedOps* mo = (const MixedOps*)o.mixed;
         const PlanSet* PS = nullptr;
@@ -974,7 +1013,43 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
     return VFMM_OK;
 }
 
+// V or X list grouped by configuration (host counting sort of the entries) and cut into GEMM
+// tiles of at most GBN entries of one configuration.
+static int build_list_groups(DeviceTree* T, int q, int ncfg, int32_t** by_cfg, int32_t** tiles_out, int32_t* n_tiles,
+                             int32_t** tgt_out) {
+    const int64_t n = T->llen[q];
+    std::vector<int32_t> cfg(n), ptr(T->n_boxes + 1);
+    if (n) VFMM_CUDA(cudaMemcpy(cfg.data(), T->lcfg[q], n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(ptr.data(), T->lptr[q], (T->n_boxes + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> start(ncfg + 1, 0);
+    for (int64_t e = 0; e < n; ++e) ++start[cfg[e] + 1];
+    for (int c = 0; c < ncfg; ++c) start[c + 1] += start[c];
+    std::vector<int32_t> order(std::max<int64_t>(n, 1));
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t e = 0; e < n; ++e) order[fill[cfg[e]]++] = (int32_t)e;
+    std::vector<int4> tiles;
+    for (int c = 0; c < ncfg; ++c)
+        for (int64_t b = start[c]; b < start[c + 1]; b += GBN)
+            tiles.push_back(make_int4(c, (int)b, (int)std::min<int64_t>(b + GBN, start[c + 1]), 0));
+    *n_tiles = (int32_t)tiles.size();
+    VFMM_CUDA(cudaMalloc(by_cfg, order.size() * sizeof(int32_t)));
+    VFMM_CUDA(cudaMemcpy(*by_cfg, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    VFMM_CUDA(cudaMalloc(tiles_out, std::max<size_t>(1, tiles.size()) * sizeof(int4)));
+    if (!tiles.empty())
+        VFMM_CUDA(cudaMemcpy(*tiles_out, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (tgt_out) {
+        std::vector<int32_t> tgt(std::max<int64_t>(n, 1), 0);
+        for (int b = 0; b < T->n_boxes; ++b)
+            for (int e = ptr[b]; e < ptr[b + 1]; ++e) tgt[e] = b;
+        VFMM_CUDA(cudaMalloc(tgt_out, tgt.size() * sizeof(int32_t)));
+        VFMM_CUDA(cudaMemcpy(*tgt_out, tgt.data(), tgt.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    return VFMM_OK;
+}
+
 int build_near_tiles(DeviceTree* T) {
+    VFMM_CHECK(build_list_groups(T, VFMM_LIST_V, kVCfg, &T->v_by_cfg, &T->v_tiles, &T->n_v_tiles, nullptr));
+    VFMM_CHECK(build_list_groups(T, VFMM_LIST_X, kFarCfg, &T->x_by_cfg, &T->x_tiles, &T->n_x_tiles, &T->x_tgt));
     std::vector<int4> tiles;
     for (int c = 0; c < kNearCfg; ++c)
         for (int64_t b = T->u_cfg_start[c]; b < T->u_cfg_start[c + 1]; b += GBN)
@@ -1028,6 +1103,8 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     d.Mexp = w.Mexp;
     d.f = f;
     d.Lexp = w.Lexp;
+    d.vslab = w.vslab;
+    d.xslab = w.xslab;
     d.m2l_out = mo ? w.mix.m2l_out : nullptr;
     d.m2l_E = mo ? mo->m2l_E : nullptr;
     d.m2l_G = mo ? w.mix.glev : nullptr;
@@ -1103,7 +1180,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         launches += 1 + (PS.s2m.n_groups > 0);
     } else {
         ++launches;
-        dim3 g((P2 + GBM - 1) / GBM, (nleaf + GBN - 1) / GBN);
+        dim3 g((nleaf + GBN - 1) / GBN, (P2 + GBM - 1) / GBM);
         s2m_gemm_kernel<<<g, 256, 0, st>>>(o.s2m, P2, kk, nleaf, T.box_of_leaf, T.level, T.width, f, w.Mexp);
     }
     mark(se, ST_S2M, true, st);
@@ -1158,6 +1235,23 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, st));
         launches += 1 + (PS.s2l.n_groups > 0) + (PS.s2l.n_groups > 0 && PS.s2l.split > 1);
     }
+    if (!mixed) {
+        // FP64 form: every M2L (V list) and S2L (X list) product as gather GEMMs grouped by
+        // configuration, one slab row per list entry; the per-level kernels below sum them
+        if (T.n_v_tiles > 0) {
+            ++launches;
+            dim3 g(T.n_v_tiles, (P2 + GBM - 1) / GBM);
+            v_gemm_kernel<<<g, 256, 0, st>>>((const int4*)T.v_tiles, o.m2l_real, P2, T.v_by_cfg,
+                                             T.lidx[VFMM_LIST_V], w.Mexp, w.vslab);
+        }
+        if (T.n_x_tiles > 0) {
+            ++launches;
+            dim3 g(T.n_x_tiles, (P2 + GBM - 1) / GBM);
+            x_gemm_kernel<<<g, 256, 0, st>>>((const int4*)T.x_tiles, o.s2l_real, P2, kk, T.x_by_cfg,
+                                             T.lidx[VFMM_LIST_X], T.x_tgt, T.level, T.width, T.leaf_of_box, f,
+                                             w.xslab);
+        }
+    }
     if (mixed && passes) {
         DownArgs d;
         fill_down_args(d, T, o, f, w, 2, R);
@@ -1201,7 +1295,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         mark(se, ST_NEAR, false, st);
         if (T.n_near_tiles > 0) {
             ++launches;
-            dim3 g((3 * kk + GBM - 1) / GBM, T.n_near_tiles);
+            dim3 g(T.n_near_tiles, (3 * kk + GBM - 1) / GBM);
             near_gemm_kernel<<<g, 256, 0, st>>>((const int4*)T.near_tiles, o.near, kk, T.u_by_cfg,
                                                 T.lidx[VFMM_LIST_U], T.leaf_of_box, f, w.slab);
         }
@@ -1214,7 +1308,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         launches += 1 + (PS.far.n_groups > 0) + (PS.far.n_groups > 0 && PS.far.split > 1);
     } else {
         ++launches;
-        dim3 g((3 * kk + GBM - 1) / GBM, (nleaf + GBN - 1) / GBN);
+        dim3 g((nleaf + GBN - 1) / GBN, (3 * kk + GBM - 1) / GBM);
         l2t_gemm_kernel<<<g, 256, 0, st>>>(o.l2t, P2, kk, nleaf, T.box_of_leaf, w.Lexp, w.far);
     }
     mark(se, ST_L2T, true, st);

@@ -16,6 +16,9 @@ struct vfmm_ops {
     double* l2l_t = nullptr;  // [4][in][out] complex
     double* m2l_t = nullptr;  // [40][in][out] complex
     double* l2t = nullptr;    // [3kk][2(p+1)] real
+    // real forms for the FP64 form's gather GEMMs: rows 2l (Re), 2l + 1 (Im) of output coefficient l
+    double* m2l_real = nullptr;  // [40][2(p+1)][2(p+1)]: columns 2n, 2n + 1 of input coefficient n
+    double* s2l_real = nullptr;  // [20][2(p+1)][kk]
     // split-precision near-field operands (VFMM_MIXED)
     void* mixed = nullptr;
 };

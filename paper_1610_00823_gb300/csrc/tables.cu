@@ -390,6 +390,32 @@ static int create(int k, int p, int precision, cudaStream_t st, vfmm_ops* o) {
     VFMM_CHECK(dalloc_copy(&o->l2l_t, l2l_t, st));
     VFMM_CHECK(dalloc_copy(&o->m2l_t, m2l_t, st));
     VFMM_CHECK(dalloc_copy(&o->l2t, l2t, st));
+    if (precision == VFMM_FP64) {
+        // real M2L and S2L matrices: complex c_l = sum M[n][l] x_n -> rows (Re c_l, Im c_l)
+        const size_t P2 = 2 * (size_t)P;
+        std::vector<double> mr((size_t)kVCfg * P2 * P2), sr((size_t)kFarCfg * P2 * kk), st_((size_t)kFarCfg * kk * P * 2);
+        for (int c = 0; c < kVCfg; ++c)
+            for (int n = 0; n < P; ++n)
+                for (int l = 0; l < P; ++l) {
+                    const double re = m2l_t[(((size_t)c * P + n) * P + l) * 2],
+                                 im = m2l_t[(((size_t)c * P + n) * P + l) * 2 + 1];
+                    double* A = mr.data() + (size_t)c * P2 * P2;
+                    A[(2 * l) * P2 + 2 * n] = re;
+                    A[(2 * l) * P2 + 2 * n + 1] = -im;
+                    A[(2 * l + 1) * P2 + 2 * n] = im;
+                    A[(2 * l + 1) * P2 + 2 * n + 1] = re;
+                }
+        VFMM_CUDA(cudaMemcpyAsync(st_.data(), o->s2l_t, st_.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        VFMM_CUDA(cudaStreamSynchronize(st));
+        for (int c = 0; c < kFarCfg; ++c)
+            for (int s = 0; s < kk; ++s)
+                for (int l = 0; l < P; ++l) {
+                    sr[((size_t)c * P2 + 2 * l) * kk + s] = st_[(((size_t)c * kk + s) * P + l) * 2];
+                    sr[((size_t)c * P2 + 2 * l + 1) * kk + s] = st_[(((size_t)c * kk + s) * P + l) * 2 + 1];
+                }
+        VFMM_CHECK(dalloc_copy(&o->m2l_real, mr, st));
+        VFMM_CHECK(dalloc_copy(&o->s2l_real, sr, st));
+    }
     VFMM_CUDA(cudaStreamSynchronize(st));
     cudaFree(d_bw);
     cudaFree(d_gx);
@@ -402,7 +428,7 @@ static int create(int k, int p, int precision, cudaStream_t st, vfmm_ops* o) {
 }
 
 void free_ops(vfmm_ops* o) {
-    double* ps[] = {o->xhat, o->near, o->s2m, o->s2l_t, o->m2m_t, o->l2l_t, o->m2l_t, o->l2t};
+    double* ps[] = {o->xhat, o->near, o->s2m, o->s2l_t, o->m2m_t, o->l2l_t, o->m2l_t, o->l2t, o->m2l_real, o->s2l_real};
     for (double* p : ps)
         if (p) cudaFree(p);
     mixed_free(o);

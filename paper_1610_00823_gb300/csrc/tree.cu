@@ -863,7 +863,8 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
 void free_tree(DeviceTree* t) {
     void* ps[] = {t->key,         t->level,       t->ix,       t->iy,           t->parent,     t->child0,
                   t->leaf_of_box, t->box_of_leaf, t->level_start_dev, t->u_by_cfg, t->u_tgt, t->near_tiles,
-                  t->far_slot,    t->nonleaf,     t->nonleaf_start_dev};
+                  t->far_slot,    t->nonleaf,     t->nonleaf_start_dev, t->v_by_cfg, t->v_tiles,
+                  t->x_by_cfg,    t->x_tiles,     t->x_tgt};
     free_plan_set(&t->plans);
     if (t->plans_r) {
         for (auto& kv : *t->plans_r) {

@@ -207,6 +207,15 @@ struct DeviceTree {
     // GEMM tile schedule for the near field: per tile (cfg, first column)
     int32_t* near_tiles = nullptr;
     int32_t n_near_tiles = 0;
+    // V and X entries grouped by configuration, with GEMM tiles (configuration, first, end) over
+    // the grouped order and each entry's target box (FP64 form's M2L and S2L)
+    int32_t* v_by_cfg = nullptr;
+    int32_t* v_tiles = nullptr;
+    int32_t n_v_tiles = 0;
+    int32_t* x_by_cfg = nullptr;
+    int32_t* x_tiles = nullptr;
+    int32_t* x_tgt = nullptr;
+    int32_t n_x_tiles = 0;
     // split-precision schedules (VFMM_MIXED): one right-hand side built with the tree, others on
     // first use (plans_for), guarded by plans_mu
     PlanSet plans;
