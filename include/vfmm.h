@@ -177,8 +177,12 @@ int vfmm_workspace_size(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs
  * nodes). VFMM_FP64 solves the right-hand sides one after another; VFMM_MIXED folds them
  * into one solve whose tensor-core contractions carry nrhs rows per leaf or box (no
  * counterpart in the paper, which solves one right-hand side at a time).
- * Everything runs on `stream`, with no host synchronisation and no allocation (the first
+ * Everything is ordered on `stream`, with no host synchronisation and no allocation (the first
  * VFMM_MIXED call for a new nrhs builds its schedules on the host, see vfmm_workspace_size).
+ * VFMM_MIXED forks its near-field and S2L contractions onto a second stream that the library
+ * keeps per host thread and device (created by the thread's first call made outside stream
+ * capture), and joins it back into `stream` by events before the call returns its last launch;
+ * under stream capture the fork becomes parallel branches of the graph.
  * Errors: INVALID_ARG (k or p of ops differ from the tree's k, nrhs < 1), WORKSPACE
  * (workspace_bytes below vfmm_workspace_size), CUDA. */
 int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
@@ -201,7 +205,8 @@ int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const
  *  - Size limit: trees whose vfmm_workspace_size (nrhs = 1, with_io = 0) exceeds 32 MiB
  *    are rejected with VFMM_ERR_WORKSPACE (roughly a few hundred leaves at k = 8).
  *  - Right-hand sides are solved one after another in the same scratch (the mixed form
- *    does not fold them here, since that would build new schedules in device memory).
+ *    does not fold them here, since that would build new schedules in device memory),
+ *    every launch on `stream` (no second stream is created).
  *  - Set-up: the first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call before
  *    any stream capture.

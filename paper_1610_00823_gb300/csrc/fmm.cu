@@ -920,6 +920,7 @@ __global__ void __launch_bounds__(256) leaf_kernel(LeafArgs a) {
 
 // ---------------------------------------------------------------- host side
 struct Workspace {
+    bool fork = false;  // mixed form: run the near field and S2L on the thread's second stream
     double* vslab;      // FP64 form: per V entry M2L rows
     double* xslab;      // FP64 form: per X entry S2L rows
     const PlanSet* ps;  // split-contraction plans for the folded right-hand sides (mixed form)
@@ -999,9 +1000,12 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
         if (w) w->mix.far_out = (float2*)p;
         take(&p, nl);
         if (w) w->mix.scal = p;
-        const size_t np = split_part_elems(T, *PS, o);
+        size_t np = 0, nps = 0;
+        split_part_elems(T, *PS, o, &np, &nps);
         take(&p, std::max<size_t>(np, 1));
         if (w) w->mix.part = np ? (float2*)p : nullptr;
+        take(&p, std::max<size_t>(nps, 1));
+        if (w) w->mix.part_side = nps ? (float2*)p : nullptr;
     } else if (w) {
         w->mix = MixedWork();
         w->ps = &T.plans;
@@ -1155,6 +1159,39 @@ static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, 
     return VFMM_OK;
 }
 
+// Second stream of the calling host thread on the current device, with its fork and join events:
+// a split-precision solve runs its near-field and S2L contractions there, beside S2M, M2M and M2L.
+// Created by the first call outside stream capture (a call under capture before that runs on one
+// stream) and kept for the life of the process. One per thread, so that the event sequence of a
+// solve cannot interleave with another thread's.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // f sliced; S2L done; near field done
+};
+
+static SideStream* side_stream(cudaStream_t st) {
+    constexpr int kMaxDevices = 16;
+    thread_local SideStream slots[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    SideStream& ss = slots[dev];
+    if (ss.s) return &ss;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    SideStream n;
+    bool ok = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; i < 3 && ok; ++i) ok = cudaEventCreateWithFlags(&n.ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (cudaEvent_t e : n.ev)
+            if (e) cudaEventDestroy(e);
+        if (n.s) cudaStreamDestroy(n.s);
+        cudaGetLastError();
+        return nullptr;
+    }
+    ss = n;
+    return &ss;
+}
+
 // One solve of R right-hand sides (f: [R][n_leaves][k^2]). The mixed form folds them into the
 // rows of every contraction (PS holds plans for R); the FP64 form takes R = 1.
 static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* u,
@@ -1166,11 +1203,29 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
     if (!mixed && R != 1) return fail(VFMM_ERR_INTERNAL, "the FP64 form solves one right-hand side at a time");
     const MixedOps* mo = (const MixedOps*)o.mixed;
     int launches = 0;
+    // Mixed form with a second stream: once f is sliced, S2L and then the near field run there
+    // while this stream takes S2M, M2M, M2L and coefficient 0; it waits for S2L before the
+    // downward combine and for the near field before the leaf kernels. Timed calls keep one stream.
+    SideStream* side = (mixed && w.fork && !se && !w.mix.cev) ? side_stream(st) : nullptr;
     if (mixed) {
-        // near field first: its f slices also feed S2M
+        // near field first: its f slices also feed S2M and S2L
         mark(se, ST_NEAR, false, st);
-        VFMM_CHECK(near_mixed(T, PS, o, f, w.mix, st));
-        launches += 3 + (PS.near.split > 1 && PS.near.n_groups > 0);
+        VFMM_CHECK(near_slices(T, PS, o, f, w.mix, st));
+        launches += 2;
+        if (side) {
+            VFMM_CUDA(cudaEventRecord(side->ev[0], st));
+            VFMM_CUDA(cudaStreamWaitEvent(side->s, side->ev[0], 0));
+            if (T.depth >= 2) {
+                VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, side->s));
+                launches += (PS.s2l.n_groups > 0) + (PS.s2l.n_groups > 0 && PS.s2l.split > 1);
+            }
+            VFMM_CUDA(cudaEventRecord(side->ev[1], side->s));
+            VFMM_CHECK(near_contract(T, PS, o, w.mix, side->s));
+            VFMM_CUDA(cudaEventRecord(side->ev[2], side->s));
+        } else {
+            VFMM_CHECK(near_contract(T, PS, o, w.mix, st));
+        }
+        launches += 1 + (PS.near.split > 1 && PS.near.n_groups > 0);
         mark(se, ST_NEAR, true, st);
     }
     // S2M
@@ -1232,9 +1287,13 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
             begin, end, R, P, T.width, T.level, T.lptr[VFMM_LIST_V], T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V],
             reinterpret_cast<const double2*>(mo->m2l_r0), w.Mexp, w.mix.m2l_c0, T.lptr[VFMM_LIST_X],
             T.lidx[VFMM_LIST_X], T.lcfg[VFMM_LIST_X], T.leaf_of_box, mo->s2l_r0, f, nleaf, kk);
-        VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, st));
-        launches += 1 + (PS.s2l.n_groups > 0) + (PS.s2l.n_groups > 0 && PS.s2l.split > 1);
+        ++launches;
+        if (!side) {
+            VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, st));
+            launches += (PS.s2l.n_groups > 0) + (PS.s2l.n_groups > 0 && PS.s2l.split > 1);
+        }
     }
+    if (side) VFMM_CUDA(cudaStreamWaitEvent(st, side->ev[1], 0));
     if (!mixed) {
         // FP64 form: every M2L (V list) and S2L (X list) product as gather GEMMs grouped by
         // configuration, one slab row per list entry; the per-level kernels below sum them
@@ -1312,6 +1371,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         l2t_gemm_kernel<<<g, 256, 0, st>>>(o.l2t, P2, kk, nleaf, T.box_of_leaf, w.Lexp, w.far);
     }
     mark(se, ST_L2T, true, st);
+    if (side) VFMM_CUDA(cudaStreamWaitEvent(st, side->ev[2], 0));
     mark(se, ST_LEAF, false, st);
     LeafArgs a;
     a.nleaf = nleaf;
@@ -1398,17 +1458,25 @@ static int read_status(const Workspace& w) {
     return VFMM_OK;
 }
 
-extern "C" int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
-                                     double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
-                                     size_t workspace_bytes, void* stream) {
+int vfmm::volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
+                           double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev, size_t workspace_bytes,
+                           cudaStream_t st, bool fork) {
     VFMM_CHECK(check_solve_args(tree, ops, nrhs));
     if (!f_dev || !u_dev || !ux_dev || !uy_dev || !workspace_dev) return fail(VFMM_ERR_INVALID_ARG, "null buffer");
     Workspace w;
     size_t need = 0;
     VFMM_CHECK(layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev, &need));
     if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small");
-    VFMM_CHECK(reset_status(w, (cudaStream_t)stream));
-    return solve_all(tree->t, *ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, w, (cudaStream_t)stream);
+    w.fork = fork;
+    VFMM_CHECK(reset_status(w, st));
+    return solve_all(tree->t, *ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, w, st);
+}
+
+extern "C" int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
+                                     double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
+                                     size_t workspace_bytes, void* stream) {
+    return volume_potential(tree, ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, workspace_dev, workspace_bytes,
+                            (cudaStream_t)stream, true);
 }
 
 extern "C" int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_host,
@@ -1420,6 +1488,7 @@ extern "C" int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops*
     size_t need = 0;
     VFMM_CHECK(layout(tree->t, *ops, nrhs, true, &w, (char*)workspace_dev, &need));
     if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small (with_io = 1 required)");
+    w.fork = true;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k * nrhs;
     double* f = w.io;
@@ -1579,7 +1648,8 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
             float total = 0.0f;
             for (int rep = 0; rep < 4 && rc == VFMM_OK; ++rep) {
                 cudaEventRecord(e0, st);
-                rc = split_gemm(*jb.P, jb.a, *jb.map, jb.Kp, jb.Rp, jb.out, w.mix.err, w.mix.part, jb.rows, st);
+                rc = split_gemm(*jb.P, jb.a, *jb.map, jb.Kp, jb.Rp, jb.out, w.mix.err,
+                                (j == 0 || j == 2) ? w.mix.part_side : w.mix.part, jb.rows, st);
                 cudaEventRecord(e1, st);
                 if (rc != VFMM_OK) break;
                 cudaError_t e = cudaEventSynchronize(e1);

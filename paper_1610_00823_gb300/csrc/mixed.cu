@@ -675,8 +675,8 @@ int plans_for(const DeviceTree& T, int R, const PlanSet** out) {
     return VFMM_OK;
 }
 
-int near_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, const MixedWork& w,
-               cudaStream_t st) {
+int near_slices(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, const MixedWork& w,
+                cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     const int kk = o.k * o.k, R = PS.R;
     VFMM_CUDA(cudaMemsetAsync(w.fmax, 0, (size_t)R * sizeof(unsigned long long), st));
@@ -686,8 +686,13 @@ int near_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const 
     f_slice_kernel<<<(unsigned)((nchunk + 255) / 256), 256, 0, st>>>(f, T.n_leaves, kk, mo->Kp, R, w.fmax, w.Ef,
                                                                      (bf16*)w.fsl);
     VFMM_CUDA(cudaGetLastError());
-    return split_gemm(PS.near, w.fsl, mo->tm_near, mo->Kp, mo->Rp, w.out, w.err, w.part, (size_t)T.n_leaves * R, st,
-                      w.cev ? w.cev + 0 : nullptr);
+    return VFMM_OK;
+}
+
+int near_contract(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
+    const MixedOps* mo = (const MixedOps*)o.mixed;
+    return split_gemm(PS.near, w.fsl, mo->tm_near, mo->Kp, mo->Rp, w.out, w.err, w.part_side,
+                      (size_t)T.n_leaves * PS.R, st, w.cev ? w.cev + 0 : nullptr);
 }
 
 }  // namespace vfmm

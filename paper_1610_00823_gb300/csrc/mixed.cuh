@@ -137,7 +137,8 @@ struct MixedWork {
     int* Et = nullptr;                    // [n_leaves]
     float2* far_out = nullptr;            // [n_leaves][Rp]
     double* scal = nullptr;               // [n_leaves * R] FP64 scalar part of u per virtual leaf
-    float2* part = nullptr;               // partial sums of split contractions (largest plan)
+    float2* part = nullptr;               // partial sums of the split M2L and leaf far-field contractions
+    float2* part_side = nullptr;          // partial sums of the split near-field and S2L contractions
     cudaEvent_t* cev = nullptr;           // optional (start, stop) pairs: near, S2M, M2L, S2L, far
 };
 
@@ -151,12 +152,18 @@ int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtenso
 // ev (optional): a (start, stop) event pair recorded around the contraction and its reduction.
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
                float2* part, size_t n_out_rows, cudaStream_t st, cudaEvent_t* ev = nullptr);
-size_t split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o);
+// Partial-sum elements (float2) for the M2L and leaf far-field contractions (*main_elems) and for
+// the near-field and S2L contractions (*side_elems), which may run at the same time.
+void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t* main_elems,
+                      size_t* side_elems);
 int build_mixed_plan(DeviceTree* T);
 int build_far_slots(DeviceTree* T);
 int build_far_plans(const DeviceTree& T, int R, PlanSet* PS);
-int near_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, const MixedWork& w,
-               cudaStream_t st);
+// Near field in two parts: max |f| and the f slices (also the operand of S2M and S2L), then the
+// split contraction.
+int near_slices(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, const MixedWork& w,
+                cudaStream_t st);
+int near_contract(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st);
 int far_prepare(vfmm_ops* o, cudaStream_t st);
 void far_free(MixedOps* mo);
 // Stages of the split-precision far field (see mixed_far.cu). Multipoles and locals are stored per

@@ -306,10 +306,12 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
     return VFMM_OK;
 }
 
-// Largest partial-sum buffer any split contraction of this plan set may need (float2 elements):
-// room for kMaxSplit partial sets wherever a contraction may split (so that vfmm_tune can pick any
-// factor without a new workspace), the current factor elsewhere.
-size_t split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o) {
+// Partial-sum buffers of the split contractions (float2 elements): room for kMaxSplit partial sets
+// wherever a contraction may split (so that vfmm_tune can pick any factor without a new
+// workspace), the current factor elsewhere. The near field and S2L (one buffer) may run beside
+// M2L and the leaf far field (the other).
+void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t* main_elems,
+                      size_t* side_elems) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     const size_t R = (size_t)PS.R;
     auto need = [](const SplitPlan& P, size_t rows, int Rp) -> size_t {
@@ -320,7 +322,8 @@ size_t split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& 
     size_t b = need(PS.m2l, T.n_boxes * R, mo->Rx);
     size_t c = need(PS.far, T.n_leaves * R, mo->Rp);
     size_t d = need(PS.s2l, T.n_boxes * R, mo->Rx);
-    return std::max(std::max(a, d), std::max(b, c));
+    *side_elems = std::max(a, d);
+    *main_elems = std::max(b, c);
 }
 
 // ---------------------------------------------------------------- S2M
@@ -454,8 +457,8 @@ int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const d
 // ---------------------------------------------------------------- S2L
 int s2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    return split_gemm(PS.s2l, w.fsl, mo->tm_s2l, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part, (size_t)T.n_boxes * PS.R,
-                      st, w.cev ? w.cev + 6 : nullptr);
+    return split_gemm(PS.s2l, w.fsl, mo->tm_s2l, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part_side,
+                      (size_t)T.n_boxes * PS.R, st, w.cev ? w.cev + 6 : nullptr);
 }
 
 // ---------------------------------------------------------------- leaf far field

@@ -63,12 +63,13 @@ extern "C" int vfmm_volume_potential_noalloc(const vfmm_tree* tree, const vfmm_o
                                             std::to_string(kStaticScratchBytes) + " bytes");
     void* scratch = nullptr;
     VFMM_CHECK(scratch_address(&scratch));
-    // Nothing in the scratch has to start at zero: the solve writes every
+    // Everything runs on `stream` alone (no second stream is created). Nothing in the scratch has
+    // to start at zero: the solve writes every
     // expansion, partial product and far value before reading it, and clears the
     // local expansions of levels 0 and 1 (and its barrier counters) itself on every call.
     const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
     for (int r = 0; r < nrhs; ++r)
-        VFMM_CHECK(vfmm_volume_potential(tree, ops, f_dev + r * n, 1, u_dev + r * n, ux_dev + r * n, uy_dev + r * n,
-                                         scratch, kStaticScratchBytes, stream));
+        VFMM_CHECK(volume_potential(tree, ops, f_dev + r * n, 1, u_dev + r * n, ux_dev + r * n, uy_dev + r * n,
+                                    scratch, kStaticScratchBytes, (cudaStream_t)stream, false));
     return VFMM_OK;
 }

@@ -234,6 +234,10 @@ void free_plan_set(PlanSet* ps);
 // Plans for R folded right-hand sides (R = 1: the tree's own set); builds and caches on first use.
 int plans_for(const DeviceTree& T, int R, const PlanSet** out);
 int build_near_tiles(DeviceTree* t);
+// vfmm_volume_potential with a flag: fork = false keeps every launch on `st` (no second stream).
+int volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs, double* u_dev,
+                     double* ux_dev, double* uy_dev, void* workspace_dev, size_t workspace_bytes, cudaStream_t st,
+                     bool fork);
 
 }  // namespace vfmm
 
