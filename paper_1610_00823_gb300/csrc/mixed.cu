@@ -503,8 +503,8 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
         // split minimising (CTAs / SMs, at least 1) x (tables per CTA + about one table of fixed cost);
         // vfmm_tune replaces it by timing
         int split = 1;
-        P->may_split = ctas < 2 * sms;
-        if (ctas < 2 * sms) {
+        P->may_split = ctas < 2 * sms && avg_cfg >= 2.0;
+        if (P->may_split) {
             double best = 1e300;
             for (int sp = 1; sp <= kMaxSplit && sp <= std::max(1.0, avg_cfg); sp *= 2) {
                 const double waves = std::max(1.0, (double)(ctas * sp) / sms);
@@ -529,8 +529,61 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
     return VFMM_OK;
 }
 
+int build_contraction_plan(const std::vector<int32_t>& tgt_id,
+                           const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
+                           const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
+                           bool transposed, double slab_overhead, size_t slab_row_bytes, SplitPlan* P) {
+    constexpr size_t kMaxSlabBytes = size_t(256) << 20;
+    VFMM_CHECK(build_split_plan(tgt_id, items, key, n_tables, n_chunks, R, transposed, P));
+    const int nt = (int)tgt_id.size();
+    const int64_t G = P->group;
+    std::vector<int64_t> per_table(n_tables, 0);
+    int64_t n_entries = 0;
+    for (int t = 0; t < nt; ++t)
+        for (auto& it : items[t]) {
+            ++per_table[it.first];
+            ++n_entries;
+        }
+    int64_t entry_cols = 0;
+    for (int c = 0; c < n_tables; ++c) entry_cols += (per_table[c] * R + G - 1) / G * G;
+    const double grouped_cols = (double)P->entries * G;
+    const size_t slab_bytes = (size_t)n_entries * R * slab_row_bytes;
+    if (n_entries == 0 || slab_bytes > kMaxSlabBytes || (double)n_entries * R > (double)INT32_MAX / 2 ||
+        (double)entry_cols * (1.0 + slab_overhead) >= 0.85 * grouped_cols)
+        return VFMM_OK;
+    // entry q of target t: a target of its own with the one item, keyed by (table, q)
+    std::vector<int32_t> e_tgt(n_entries), seg(nt + 1, 0), seg_out(nt);
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> e_items(n_entries);
+    std::vector<std::pair<uint64_t, uint64_t>> e_key(n_entries);
+    int64_t q = 0;
+    for (int t = 0; t < nt; ++t) {
+        seg[t] = (int32_t)q;
+        seg_out[t] = tgt_id[t];
+        for (auto& it : items[t]) {
+            e_tgt[q] = (int32_t)q;
+            e_items[q].push_back(it);
+            e_key[q] = {(uint64_t)it.first, (uint64_t)q};
+            ++q;
+        }
+    }
+    seg[nt] = (int32_t)q;
+    free_split_plan(P);
+    VFMM_CHECK(build_split_plan(e_tgt, e_items, e_key, n_tables, n_chunks, R, transposed, P));
+    P->entry = true;
+    P->may_split = false;
+    P->split = 1;
+    P->R = R;
+    P->n_seg = nt;
+    P->slab_rows = n_entries * R;
+    VFMM_CUDA(cudaMalloc(&P->seg, seg.size() * sizeof(int32_t)));
+    VFMM_CUDA(cudaMemcpy(P->seg, seg.data(), seg.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    VFMM_CUDA(cudaMalloc(&P->seg_out, std::max<size_t>(1, seg_out.size()) * sizeof(int32_t)));
+    if (nt) VFMM_CUDA(cudaMemcpy(P->seg_out, seg_out.data(), seg_out.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return VFMM_OK;
+}
+
 void free_split_plan(SplitPlan* P) {
-    int32_t* ps[] = {P->tgt, P->ptr, P->cfg, P->src};
+    int32_t* ps[] = {P->tgt, P->ptr, P->cfg, P->src, P->seg, P->seg_out};
     for (int32_t* p : ps)
         if (p) cudaFree(p);
     *P = SplitPlan();
@@ -546,6 +599,35 @@ void free_plan_set(PlanSet* ps) {
 
 static size_t smem_bytes() { return (size_t)kStages * kSlices * (kTileM * 64 + kTileN * 64) + 1024; }
 
+// (hi, lo) += v in double-float with exact two-sums; df_final renormalises.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float2 v) {
+    float s1, e1, s2, e2;
+    two_sum(hi, v.x, s1, e1);
+    two_sum(s1, v.y, s2, e2);
+    hi = s2;
+    lo = __fadd_rn(lo, __fadd_rn(e1, e2));
+}
+
+__device__ __forceinline__ float2 df_final(float hi, float lo) {
+    const float h = __fadd_rn(hi, lo);
+    return make_float2(h, __fsub_rn(lo, __fsub_rn(h, hi)));
+}
+
+// Entry-major contraction: output row of target t (right-hand side r) = sum of the slab rows of
+// its entries, in entry order (double-float); one thread per (target, r, row).
+__global__ void segment_reduce_kernel(const float2* __restrict__ slab, const int32_t* __restrict__ seg,
+                                      const int32_t* __restrict__ seg_out, int n_seg, int R, int Rp,
+                                      float2* __restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n_seg * R * Rp) return;
+    const int row = (int)(q % Rp);
+    const int64_t vt = q / Rp;
+    const int t = (int)(vt / R), r = (int)(vt % R);
+    float hi = 0.0f, lo = 0.0f;
+    for (int e = seg[t]; e < seg[t + 1]; ++e) df_add(hi, lo, slab[((size_t)e * R + r) * Rp + row]);
+    out[((size_t)seg_out[t] * R + r) * Rp + row] = df_final(hi, lo);
+}
+
 // out[row][r] = sum over the partial sums (double-float, exact two-sums).
 __global__ void split_reduce_kernel(const float2* __restrict__ part, size_t stride, int split, const int32_t* __restrict__ tgt,
                                     int n_tgt, int Rp, float2* __restrict__ out) {
@@ -555,16 +637,8 @@ __global__ void split_reduce_kernel(const float2* __restrict__ part, size_t stri
     if (t < 0) return;
     const size_t o = (size_t)t * Rp + q % Rp;
     float hi = 0.0f, lo = 0.0f;
-    for (int s = 0; s < split; ++s) {
-        float2 v = part[(size_t)s * stride + o];
-        float s1, e1, s2, e2;
-        two_sum(hi, v.x, s1, e1);
-        two_sum(s1, v.y, s2, e2);
-        hi = s2;
-        lo = __fadd_rn(lo, __fadd_rn(e1, e2));
-    }
-    float h = __fadd_rn(hi, lo);
-    out[o] = make_float2(h, __fsub_rn(lo, __fsub_rn(h, hi)));
+    for (int s = 0; s < split; ++s) df_add(hi, lo, part[(size_t)s * stride + o]);
+    out[o] = df_final(hi, lo);
 }
 
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
@@ -599,6 +673,22 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
     // accumulator of diagonals 7..9 truncates as it grows, so a drain group also holds at most 512
     // K values (measured: 2.6e-11 -> 1.5e-11 for the gradient on the 20-Gaussian tree, < 1 % time).
     a.drain_every = std::max(1, std::min((int)((1 << 24) / (5ll * 3969 * Kp)), 512 / Kp));
+    if (P.entry) {
+        // one slab row per entry in the partial-sum buffer, then the per-target sums
+        if (!part) return fail(VFMM_ERR_INTERNAL, "entry-major contraction without a slab buffer");
+        a.split = 1;
+        a.part_stride = 0;
+        a.out = part;
+        split_gemm_kernel<<<(unsigned)P.n_groups * a.nchunks, kThreads, smem_bytes(), st>>>(a, bmap);
+        VFMM_CUDA(cudaGetLastError());
+        const int64_t n = (int64_t)P.n_seg * P.R * Rp;
+        if (n > 0)
+            segment_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, P.seg, P.seg_out, P.n_seg, P.R,
+                                                                                Rp, out);
+        VFMM_CUDA(cudaGetLastError());
+        if (ev) VFMM_CUDA(cudaEventRecord(ev[1], st));
+        return VFMM_OK;
+    }
     a.split = part ? P.split : 1;
     a.part_stride = n_out_rows * (size_t)Rp;
     a.out = a.split > 1 ? part : out;
@@ -640,7 +730,9 @@ static int build_plans(const DeviceTree& T, int R, PlanSet* PS) {
     const int rows = 3 * T.k * T.k;
     const bool tr = near_transposed(T.k);
     const int tile_rows = table_rows_per_tile(tr);
-    VFMM_CHECK(build_split_plan(tgt, items, key, kNearCfg, (rows + tile_rows - 1) / tile_rows, R, tr, &PS->near));
+    const int Kp = (T.k * T.k + kKBlock - 1) / kKBlock * kKBlock;
+    VFMM_CHECK(build_contraction_plan(tgt, items, key, kNearCfg, (rows + tile_rows - 1) / tile_rows, R, tr,
+                                      48.0 / Kp, (size_t)rows * sizeof(float2), &PS->near));
     return build_far_plans(T, R, PS);
 }
 

@@ -146,6 +146,14 @@ int build_split_plan(const std::vector<int32_t>& tgt_id,
                      const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                      const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
                      bool transposed, SplitPlan* P);
+// build_split_plan, or its entry-major form when that executes enough fewer columns: chosen when
+// (entry-major columns) x (1 + slab_overhead) < 0.85 x (grouped columns, padding included) and the
+// slab (entries x R x slab_row_bytes) stays within 256 MB. slab_overhead = the slab's write and read
+// time per column relative to its tensor time.
+int build_contraction_plan(const std::vector<int32_t>& tgt_id,
+                           const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
+                           const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
+                           bool transposed, double slab_overhead, size_t slab_row_bytes, SplitPlan* P);
 // Tensor map of a sliced table [rows][Kp / 32][kSlices][32] BF16 for the table operand of split_gemm
 // (box = box_rows rows x 64 bytes of one slice and K block).
 int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtensorMap* out);

@@ -257,7 +257,8 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             }
             key.push_back({sig, (uint64_t)b});
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, kVCfg, 1, R, false, &PS->m2l));
+        // slab costs relative to the tensor work per column: K = 2(p+1) padded (about 96), rows <= 128
+        VFMM_CHECK(build_contraction_plan(tgt, items, key, kVCfg, 1, R, false, 0.5, 128 * sizeof(float2), &PS->m2l));
     }
     // S2L: boxes with an X list, tables 20 configurations, A row = source leaf
     {
@@ -277,7 +278,9 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             }
             key.push_back({sig, (uint64_t)b});
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, kFarCfg, 1, R, false, &PS->s2l));
+        const int Kp = (T.k * T.k + kKBlock - 1) / kKBlock * kKBlock;
+        VFMM_CHECK(
+            build_contraction_plan(tgt, items, key, kFarCfg, 1, R, false, 48.0 / Kp, 128 * sizeof(float2), &PS->s2l));
     }
     // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
     {
@@ -301,20 +304,22 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
         const int rows = 3 * T.k * T.k;
         const bool tr = near_transposed(T.k);
         const int tile_rows = table_rows_per_tile(tr);
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1 + kFarCfg, (rows + tile_rows - 1) / tile_rows, R, tr, &PS->far));
+        VFMM_CHECK(build_contraction_plan(tgt, items, key, 1 + kFarCfg, (rows + tile_rows - 1) / tile_rows, R, tr,
+                                          0.5, (size_t)rows * sizeof(float2), &PS->far));
     }
     return VFMM_OK;
 }
 
 // Partial-sum buffers of the split contractions (float2 elements): room for kMaxSplit partial sets
 // wherever a contraction may split (so that vfmm_tune can pick any factor without a new
-// workspace), the current factor elsewhere. The near field and S2L (one buffer) may run beside
-// M2L and the leaf far field (the other).
+// workspace), the current factor elsewhere, and the slab of an entry-major contraction. The near
+// field and S2L (one buffer) may run beside M2L and the leaf far field (the other).
 void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t* main_elems,
                       size_t* side_elems) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     const size_t R = (size_t)PS.R;
     auto need = [](const SplitPlan& P, size_t rows, int Rp) -> size_t {
+        if (P.entry) return (size_t)P.slab_rows * Rp;  // one slab row per entry
         const int f = P.may_split ? kMaxSplit : P.split;
         return f > 1 ? (size_t)f * rows * Rp : 0;
     };

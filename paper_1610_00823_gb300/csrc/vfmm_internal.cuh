@@ -167,6 +167,15 @@ struct SplitPlan {
     bool may_split = false;  // small contraction (fewer CTAs than two per SM): split-K allowed
     bool transposed = false; // table rows on the M side (128 per tile), targets on the N side
     int32_t group = 128;     // targets per group: 128, or 80 when transposed
+    // Entry-major form: every (target, table) entry is a column of its own, grouped by table, so
+    // no column is empty; the contraction writes one slab row per entry (in the partial-sum
+    // buffer) and a segmented reduction sums each target's entries into its output row.
+    bool entry = false;
+    int32_t R = 1;             // folded right-hand sides (slab row of entry q: q * R + r)
+    int32_t n_seg = 0;         // targets
+    int64_t slab_rows = 0;     // entries * R
+    int32_t* seg = nullptr;    // [n_seg + 1] first entry of each target
+    int32_t* seg_out = nullptr;  // [n_seg] output row (before the R fold) of each target
 };
 
 // The split contractions of the mixed form with R right-hand sides folded into the rows: the
