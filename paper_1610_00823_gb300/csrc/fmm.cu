@@ -1000,12 +1000,14 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
         if (w) w->mix.far_out = (float2*)p;
         take(&p, nl);
         if (w) w->mix.scal = p;
-        size_t np = 0, nps = 0;
-        split_part_elems(T, *PS, o, &np, &nps);
-        take(&p, std::max<size_t>(np, 1));
-        if (w) w->mix.part = np ? (float2*)p : nullptr;
-        take(&p, std::max<size_t>(nps, 1));
-        if (w) w->mix.part_side = nps ? (float2*)p : nullptr;
+        size_t np[3] = {0, 0, 0};
+        split_part_elems(T, *PS, o, np);
+        float2** bufs[3] = {w ? &w->mix.part : nullptr, w ? &w->mix.part_side : nullptr,
+                            w ? &w->mix.part_s2l : nullptr};
+        for (int i = 0; i < 3; ++i) {
+            take(&p, std::max<size_t>(np[i], 1));  // one float2 per double
+            if (w) *bufs[i] = np[i] ? (float2*)p : nullptr;
+        }
     } else if (w) {
         w->mix = MixedWork();
         w->ps = &T.plans;
@@ -1160,7 +1162,7 @@ static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, 
 }
 
 // Second stream of the calling host thread on the current device, with its fork and join events:
-// a split-precision solve runs its near-field and S2L contractions there, beside S2M, M2M and M2L.
+// a split-precision solve runs its S2L and near-field contractions there, beside S2M, M2M and M2L.
 // Created by the first call outside stream capture (a call under capture before that runs on one
 // stream) and kept for the life of the process. One per thread, so that the event sequence of a
 // solve cannot interleave with another thread's.
@@ -1192,6 +1194,11 @@ static SideStream* side_stream(cudaStream_t st) {
     return &ss;
 }
 
+// Kernels one split contraction launches: the contraction, and its split-K or segmented reduction.
+static int gemm_launches(const SplitPlan& P) {
+    return P.n_groups > 0 ? 1 + ((P.split > 1 || P.entry) ? 1 : 0) : 0;
+}
+
 // One solve of R right-hand sides (f: [R][n_leaves][k^2]). The mixed form folds them into the
 // rows of every contraction (PS holds plans for R); the FP64 form takes R = 1.
 static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* u,
@@ -1217,7 +1224,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
             VFMM_CUDA(cudaStreamWaitEvent(side->s, side->ev[0], 0));
             if (T.depth >= 2) {
                 VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, side->s));
-                launches += (PS.s2l.n_groups > 0) + (PS.s2l.n_groups > 0 && PS.s2l.split > 1);
+                launches += gemm_launches(PS.s2l);
             }
             VFMM_CUDA(cudaEventRecord(side->ev[1], side->s));
             VFMM_CHECK(near_contract(T, PS, o, w.mix, side->s));
@@ -1225,14 +1232,14 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         } else {
             VFMM_CHECK(near_contract(T, PS, o, w.mix, st));
         }
-        launches += 1 + (PS.near.split > 1 && PS.near.n_groups > 0);
+        launches += gemm_launches(PS.near);
         mark(se, ST_NEAR, true, st);
     }
     // S2M
     mark(se, ST_S2M, false, st);
     if (mixed) {
         VFMM_CHECK(s2m_mixed(T, PS, o, f, w.Mexp, w.mix, st));
-        launches += 1 + (PS.s2m.n_groups > 0);
+        launches += 1 + gemm_launches(PS.s2m);
     } else {
         ++launches;
         dim3 g((nleaf + GBN - 1) / GBN, (P2 + GBM - 1) / GBM);
@@ -1271,7 +1278,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
     mark(se, ST_DOWN, false, st);
     if (mixed && T.depth >= 2) {
         VFMM_CHECK(m2l_mixed(T, PS, o, w.Mexp, w.mix, st));
-        if (PS.m2l.n_groups > 0) launches += 4 + (PS.m2l.split > 1);
+        if (PS.m2l.n_groups > 0) launches += 3 + gemm_launches(PS.m2l);
         const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
         const int64_t warps = (int64_t)(end - begin) * R;
         const size_t c0_smem = (size_t)kVCfg * P * sizeof(double2) + (size_t)kFarCfg * kk * sizeof(double);
@@ -1290,7 +1297,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
         ++launches;
         if (!side) {
             VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, st));
-            launches += (PS.s2l.n_groups > 0) + (PS.s2l.n_groups > 0 && PS.s2l.split > 1);
+            launches += gemm_launches(PS.s2l);
         }
     }
     if (side) VFMM_CUDA(cudaStreamWaitEvent(st, side->ev[1], 0));
@@ -1364,7 +1371,7 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
     mark(se, ST_L2T, false, st);
     if (mixed) {
         VFMM_CHECK(far_leaf_mixed(T, PS, o, w.Mexp, w.Lexp, w.mix, st));
-        launches += 1 + (PS.far.n_groups > 0) + (PS.far.n_groups > 0 && PS.far.split > 1);
+        launches += 1 + gemm_launches(PS.far);
     } else {
         ++launches;
         dim3 g((nleaf + GBN - 1) / GBN, (3 * kk + GBM - 1) / GBM);
@@ -1640,16 +1647,16 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
     for (int j = 0; j < 4 && rc == VFMM_OK; ++j) {
         Job& jb = jobs[j];
         if (!jb.P->may_split || jb.P->n_groups == 0) continue;
-        const double avg_cfg = (double)jb.P->entries / jb.P->n_groups;
+        const double avg_units = (double)jb.P->entries * (jb.Kp / kKBlock) / jb.P->n_groups;
         int best = jb.P->split;
         float best_ms = -1.0f;
-        for (int sp = 1; sp <= kMaxSplit && sp <= std::max(1.0, avg_cfg) && rc == VFMM_OK; sp *= 2) {
+        for (int sp = 1; sp <= kMaxSplit && sp <= std::max(1.0, avg_units) && rc == VFMM_OK; sp *= 2) {
             jb.P->split = sp;
             float total = 0.0f;
             for (int rep = 0; rep < 4 && rc == VFMM_OK; ++rep) {
                 cudaEventRecord(e0, st);
                 rc = split_gemm(*jb.P, jb.a, *jb.map, jb.Kp, jb.Rp, jb.out, w.mix.err,
-                                (j == 0 || j == 2) ? w.mix.part_side : w.mix.part, jb.rows, st);
+                                j == 0 ? w.mix.part_side : j == 2 ? w.mix.part_s2l : w.mix.part, jb.rows, st);
                 cudaEventRecord(e1, st);
                 if (rc != VFMM_OK) break;
                 cudaError_t e = cudaEventSynchronize(e1);

@@ -212,12 +212,14 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = tmem_holder;
+    // units = (table, K block) pairs of the group in table order; CTA sp of the split takes a
+    // contiguous share, which may begin or end inside a table (split-K over tables and K blocks)
     const int gbeg = a.gptr[g], gcnt = a.gptr[g + 1] - gbeg;
-    const int cbeg = gbeg + (int)(((long long)gcnt * sp) / a.split);
-    const int cend = gbeg + (int)(((long long)gcnt * (sp + 1)) / a.split);
-    const int ncfg = cend - cbeg;
     const int nkb = a.Kp / kKBlock;
-    const int U = ncfg * nkb;
+    const long long Ug = (long long)gcnt * nkb;
+    const int ubeg = (int)((Ug * sp) / a.split);
+    const int U = (int)((Ug * (sp + 1)) / a.split) - ubeg;
+    const int DU = a.drain_every * nkb;  // units summed in TMEM between two drains
     const int r0 = rc * (tr ? kTileM : N);  // first table row of this CTA's tile
 
     if (warp >= kEpilogueWarps && warp < kMmaWarp) {
@@ -236,9 +238,9 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
                 atomicExch(a.err, 1);
                 break;
             }
-            const int ci = cbeg + u / nkb, kb = u % nkb;
+            const int ci = gbeg + (ubeg + u) / nkb, kb = (ubeg + u) % nkb;
             const int cfg = a.gcfg[ci];
-            if (kb == 0) {
+            if (kb == 0 || u == 0) {
                 // gather rows of this table for the 128 targets, once per table
                 for (int m = ptid; m < G; m += kProducerThreads) s_src[m] = a.gsrc[(size_t)ci * G + m];
                 named_bar_sync(1, kProducerThreads);
@@ -269,40 +271,34 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
         }
         tc::cp_async_wait_all();
         } else if (warp == kMmaWarp) {
-        // ------------------------------------------------ MMA issuer: one configuration at a time
+        // ------------------------------------------------ MMA issuer: one unit at a time
         if (lane == 0) {
             const uint64_t adesc_base = tc::smem_desc(sbase, 16, 512, tc::kLayoutSwizzle64B);
-            bool alive = true;
-            const int G = a.drain_every;
-            for (int c = 0; c < ncfg && alive; ++c) {
-                // a drain group = G consecutive configurations summed in the same accumulators
-                if (c >= G && c % G == 0 && !tc::mbar_wait(acc_empty, (c / G - 1) & 1, &abort_flag)) {
+            for (int u = 0; u < U; ++u) {
+                // a drain group = DU consecutive units summed in the same accumulators
+                if (u >= DU && u % DU == 0 && !tc::mbar_wait(acc_empty, (u / DU - 1) & 1, &abort_flag)) {
                     abort_flag = 1;
                     atomicExch(a.err, 4);
                     break;
                 }
-                tc::tc_fence_after();
-                for (int kb = 0; kb < nkb; ++kb) {
-                    const int u = c * nkb + kb, s = u & 1;
-                    if (!tc::mbar_wait(full0 + 8 * s, (u >> 1) & 1, &abort_flag)) {
-                        abort_flag = 1;
-                        atomicExch(a.err, 2);
-                        alive = false;
-                        break;
-                    }
-                    tc::tc_fence_after();
-                    // the gathered rows were written by cp.async (generic proxy): make them visible to
-                    // the tensor core's reads (async proxy) before the MMAs
-                    tc::fence_proxy_async();
-                    // descriptors differ only in the 14-bit start-address field (address >> 4), so
-                    // offsets within the stage are added to a base descriptor
-                    const uint64_t ad0 = adesc_base + ((s * STAGE) >> 4);
-                    const uint64_t bd0 = adesc_base + ((s * STAGE + kSlices * A_SLICE) >> 4);
-                    if (kb == 0 && c % G == 0) issue_unit<true>(tmem, ad0, bd0);
-                    else issue_unit<false>(tmem, ad0, bd0);
-                    tc::umma_commit(empty0 + 8 * s);
+                const int s = u & 1;
+                if (!tc::mbar_wait(full0 + 8 * s, (u >> 1) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    atomicExch(a.err, 2);
+                    break;
                 }
-                if (alive && (c % G == G - 1 || c == ncfg - 1)) tc::umma_commit(acc_full);
+                tc::tc_fence_after();
+                // the gathered rows were written by cp.async (generic proxy): make them visible to
+                // the tensor core's reads (async proxy) before the MMAs
+                tc::fence_proxy_async();
+                // descriptors differ only in the 14-bit start-address field (address >> 4), so
+                // offsets within the stage are added to a base descriptor
+                const uint64_t ad0 = adesc_base + ((s * STAGE) >> 4);
+                const uint64_t bd0 = adesc_base + ((s * STAGE + kSlices * A_SLICE) >> 4);
+                if (u % DU == 0) issue_unit<true>(tmem, ad0, bd0);
+                else issue_unit<false>(tmem, ad0, bd0);
+                tc::umma_commit(empty0 + 8 * s);
+                if (u % DU == DU - 1 || u == U - 1) tc::umma_commit(acc_full);
             }
         }
         __syncwarp();
@@ -314,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
 #pragma unroll
         for (int j = 0; j < HALF; ++j) hi[j] = lo[j] = 0.0f;
         bool ok = true;
-        const int ngroups = (ncfg + a.drain_every - 1) / a.drain_every;
+        const int ngroups = (U + DU - 1) / DU;
         for (int grp = 0; grp < ngroups; ++grp) {
             ok = ok && tc::mbar_wait(acc_full, grp & 1, &abort_flag);
             ok = __all_sync(0xffffffffu, ok);
@@ -453,7 +449,7 @@ void mixed_free(vfmm_ops* o) {
 // of each target (-1 when the target has no entry for that table).
 int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                      const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                     bool transposed, SplitPlan* P) {
+                     bool transposed, int nkb, SplitPlan* P) {
     const int G = transposed ? kTileN : kTileM;  // targets per group
     // Targets sorted by key; target t stands for the R consecutive virtual targets t * R + r, whose
     // A rows are src * R + r: the right-hand sides of one target share its set of tables.
@@ -498,17 +494,18 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t ctas = (int64_t)std::max(ng, 1) * n_chunks;
-        const double avg_cfg = ng ? (double)P->entries / ng : 1.0;
-        // split-K over tables only for small contractions (fewer than two CTAs per SM): default = the
-        // split minimising (CTAs / SMs, at least 1) x (tables per CTA + about one table of fixed cost);
-        // vfmm_tune replaces it by timing
+        // units of work per group: (table, K block) pairs
+        const double avg_units = ng ? (double)P->entries * nkb / ng : 1.0;
+        // split-K over the units only for small contractions (fewer than two CTAs per SM): default =
+        // the split minimising (CTAs / SMs, at least 1) x (units per CTA + about one table of fixed
+        // cost); vfmm_tune replaces it by timing
         int split = 1;
-        P->may_split = ctas < 2 * sms && avg_cfg >= 2.0;
+        P->may_split = ctas < 2 * sms && avg_units >= 2.0;
         if (P->may_split) {
             double best = 1e300;
-            for (int sp = 1; sp <= kMaxSplit && sp <= std::max(1.0, avg_cfg); sp *= 2) {
+            for (int sp = 1; sp <= kMaxSplit && sp <= std::max(1.0, avg_units); sp *= 2) {
                 const double waves = std::max(1.0, (double)(ctas * sp) / sms);
-                const double est = waves * (avg_cfg / sp + 1.0);
+                const double est = waves * (avg_units / sp + nkb);
                 if (est < best - 1e-9) {
                     best = est;
                     split = sp;
@@ -532,9 +529,9 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
 int build_contraction_plan(const std::vector<int32_t>& tgt_id,
                            const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                            const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                           bool transposed, double slab_overhead, size_t slab_row_bytes, SplitPlan* P) {
+                           bool transposed, int nkb, double slab_overhead, size_t slab_row_bytes, SplitPlan* P) {
     constexpr size_t kMaxSlabBytes = size_t(256) << 20;
-    VFMM_CHECK(build_split_plan(tgt_id, items, key, n_tables, n_chunks, R, transposed, P));
+    VFMM_CHECK(build_split_plan(tgt_id, items, key, n_tables, n_chunks, R, transposed, nkb, P));
     const int nt = (int)tgt_id.size();
     const int64_t G = P->group;
     std::vector<int64_t> per_table(n_tables, 0);
@@ -568,8 +565,8 @@ int build_contraction_plan(const std::vector<int32_t>& tgt_id,
     }
     seg[nt] = (int32_t)q;
     free_split_plan(P);
-    VFMM_CHECK(build_split_plan(e_tgt, e_items, e_key, n_tables, n_chunks, R, transposed, P));
-    P->entry = true;
+    VFMM_CHECK(build_split_plan(e_tgt, e_items, e_key, n_tables, n_chunks, R, transposed, nkb, P));
+    P->entry = true;  // the slab occupies the partial-sum buffer: no split-K
     P->may_split = false;
     P->split = 1;
     P->R = R;
@@ -732,7 +729,7 @@ static int build_plans(const DeviceTree& T, int R, PlanSet* PS) {
     const int tile_rows = table_rows_per_tile(tr);
     const int Kp = (T.k * T.k + kKBlock - 1) / kKBlock * kKBlock;
     VFMM_CHECK(build_contraction_plan(tgt, items, key, kNearCfg, (rows + tile_rows - 1) / tile_rows, R, tr,
-                                      48.0 / Kp, (size_t)rows * sizeof(float2), &PS->near));
+                                      Kp / kKBlock, 48.0 / Kp, (size_t)rows * sizeof(float2), &PS->near));
     return build_far_plans(T, R, PS);
 }
 

@@ -137,15 +137,16 @@ struct MixedWork {
     int* Et = nullptr;                    // [n_leaves]
     float2* far_out = nullptr;            // [n_leaves][Rp]
     double* scal = nullptr;               // [n_leaves * R] FP64 scalar part of u per virtual leaf
-    float2* part = nullptr;               // partial sums of the split M2L and leaf far-field contractions
-    float2* part_side = nullptr;          // partial sums of the split near-field and S2L contractions
+    float2* part = nullptr;               // partial sums or slab of S2M, M2L and the leaf far field
+    float2* part_side = nullptr;          // partial sums or slab of the near field
+    float2* part_s2l = nullptr;           // partial sums or slab of S2L
     cudaEvent_t* cev = nullptr;           // optional (start, stop) pairs: near, S2M, M2L, S2L, far
 };
 
 int build_split_plan(const std::vector<int32_t>& tgt_id,
                      const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                      const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                     bool transposed, SplitPlan* P);
+                     bool transposed, int nkb, SplitPlan* P);
 // build_split_plan, or its entry-major form when that executes enough fewer columns: chosen when
 // (entry-major columns) x (1 + slab_overhead) < 0.85 x (grouped columns, padding included) and the
 // slab (entries x R x slab_row_bytes) stays within 256 MB. slab_overhead = the slab's write and read
@@ -153,17 +154,16 @@ int build_split_plan(const std::vector<int32_t>& tgt_id,
 int build_contraction_plan(const std::vector<int32_t>& tgt_id,
                            const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                            const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                           bool transposed, double slab_overhead, size_t slab_row_bytes, SplitPlan* P);
+                           bool transposed, int nkb, double slab_overhead, size_t slab_row_bytes, SplitPlan* P);
 // Tensor map of a sliced table [rows][Kp / 32][kSlices][32] BF16 for the table operand of split_gemm
 // (box = box_rows rows x 64 bytes of one slice and K block).
 int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtensorMap* out);
 // ev (optional): a (start, stop) event pair recorded around the contraction and its reduction.
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
                float2* part, size_t n_out_rows, cudaStream_t st, cudaEvent_t* ev = nullptr);
-// Partial-sum elements (float2) for the M2L and leaf far-field contractions (*main_elems) and for
-// the near-field and S2L contractions (*side_elems), which may run at the same time.
-void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t* main_elems,
-                      size_t* side_elems);
+// Partial-sum elements (float2) of the three buffers whose contractions may run at the same time:
+// [0] S2M, M2L and the leaf far field (one after another), [1] the near field, [2] S2L.
+void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t elems[3]);
 int build_mixed_plan(DeviceTree* T);
 int build_far_slots(DeviceTree* T);
 int build_far_plans(const DeviceTree& T, int R, PlanSet* PS);

@@ -213,6 +213,10 @@ int build_far_slots(DeviceTree* T) {
 
 int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
     const int nb = T.n_boxes, nl = T.n_leaves;
+    // K blocks per table: k^2 for S2M and S2L; 2(p+1) for M2L and the leaf far field, where p is not
+    // known to the tree (3 blocks = p up to 47; only the default split-K choice depends on it)
+    const int Kp = (T.k * T.k + kKBlock - 1) / kKBlock * kKBlock;
+    constexpr int kFarKb = 3;
     std::vector<int32_t> bol(nl), lob(nb);
     VFMM_CUDA(cudaMemcpy(bol.data(), T.box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
     VFMM_CUDA(cudaMemcpy(lob.data(), T.leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -237,7 +241,7 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             items[t].push_back({0, t});
             key[t] = {0, (uint64_t)t};
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, R, false, &PS->s2m));
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, R, false, Kp / kKBlock, &PS->s2m));
     }
     // M2L: boxes with a V list, tables = the 40 offsets, A row = source box
     {
@@ -258,7 +262,8 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             key.push_back({sig, (uint64_t)b});
         }
         // slab costs relative to the tensor work per column: K = 2(p+1) padded (about 96), rows <= 128
-        VFMM_CHECK(build_contraction_plan(tgt, items, key, kVCfg, 1, R, false, 0.5, 128 * sizeof(float2), &PS->m2l));
+        VFMM_CHECK(build_contraction_plan(tgt, items, key, kVCfg, 1, R, false, kFarKb, 0.5, 128 * sizeof(float2),
+                                          &PS->m2l));
     }
     // S2L: boxes with an X list, tables 20 configurations, A row = source leaf
     {
@@ -278,9 +283,8 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             }
             key.push_back({sig, (uint64_t)b});
         }
-        const int Kp = (T.k * T.k + kKBlock - 1) / kKBlock * kKBlock;
-        VFMM_CHECK(
-            build_contraction_plan(tgt, items, key, kFarCfg, 1, R, false, 48.0 / Kp, 128 * sizeof(float2), &PS->s2l));
+        VFMM_CHECK(build_contraction_plan(tgt, items, key, kFarCfg, 1, R, false, Kp / kKBlock, 48.0 / Kp,
+                                          128 * sizeof(float2), &PS->s2l));
     }
     // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
     {
@@ -305,7 +309,7 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
         const bool tr = near_transposed(T.k);
         const int tile_rows = table_rows_per_tile(tr);
         VFMM_CHECK(build_contraction_plan(tgt, items, key, 1 + kFarCfg, (rows + tile_rows - 1) / tile_rows, R, tr,
-                                          0.5, (size_t)rows * sizeof(float2), &PS->far));
+                                          kFarKb, 0.5, (size_t)rows * sizeof(float2), &PS->far));
     }
     return VFMM_OK;
 }
@@ -313,9 +317,8 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
 // Partial-sum buffers of the split contractions (float2 elements): room for kMaxSplit partial sets
 // wherever a contraction may split (so that vfmm_tune can pick any factor without a new
 // workspace), the current factor elsewhere, and the slab of an entry-major contraction. The near
-// field and S2L (one buffer) may run beside M2L and the leaf far field (the other).
-void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t* main_elems,
-                      size_t* side_elems) {
+// field and S2L each have their own, since they may run beside each other and beside the rest.
+void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t elems[3]) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     const size_t R = (size_t)PS.R;
     auto need = [](const SplitPlan& P, size_t rows, int Rp) -> size_t {
@@ -327,8 +330,10 @@ void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o,
     size_t b = need(PS.m2l, T.n_boxes * R, mo->Rx);
     size_t c = need(PS.far, T.n_leaves * R, mo->Rp);
     size_t d = need(PS.s2l, T.n_boxes * R, mo->Rx);
-    *side_elems = std::max(a, d);
-    *main_elems = std::max(b, c);
+    size_t e = need(PS.s2m, T.n_leaves * R, mo->Rx);
+    elems[0] = std::max(std::max(b, c), e);
+    elems[1] = a;
+    elems[2] = d;
 }
 
 // ---------------------------------------------------------------- S2M
@@ -368,8 +373,8 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
 int s2m_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* Mexp,
               const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    VFMM_CHECK(split_gemm(PS.s2m, w.fsl, mo->tm_s2m, mo->Kp, mo->Rx, w.s2m_out, w.err, nullptr, 0, st,
-                          w.cev ? w.cev + 2 : nullptr));
+    VFMM_CHECK(split_gemm(PS.s2m, w.fsl, mo->tm_s2m, mo->Kp, mo->Rx, w.s2m_out, w.err, w.part,
+                          (size_t)T.n_leaves * PS.R, st, w.cev ? w.cev + 2 : nullptr));
     s2m_finish_kernel<<<T.n_leaves * PS.R, 128, 0, st>>>(T.n_leaves, PS.R, o.k * o.k, o.p, mo->Rx, T.box_of_leaf,
                                                          T.level, T.width, f, o.s2m, w.s2m_out, mo->s2m_E, w.Ef,
                                                          Mexp);
@@ -462,7 +467,7 @@ int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const d
 // ---------------------------------------------------------------- S2L
 int s2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
-    return split_gemm(PS.s2l, w.fsl, mo->tm_s2l, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part_side,
+    return split_gemm(PS.s2l, w.fsl, mo->tm_s2l, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part_s2l,
                       (size_t)T.n_boxes * PS.R, st, w.cev ? w.cev + 6 : nullptr);
 }
 
