@@ -554,6 +554,7 @@ def main():
                       "m2l": 2.0 * 2 * wl.p * P2 * n_v, "s2l": 2.0 * 2 * wl.p * kk * n_x,
                       "far": 2.0 * 3 * kk * (P2 - 2) * tree.n_leaves + 2.0 * 3 * kk * P2 * n_w}
         contractions = {}
+        ENTRY_BIT = {"near": 1, "m2l": 2, "far": 4, "s2l": 8}  # vfmm_solve_work out[7]
         for name in ("near", "s2m", "m2l", "s2l", "far"):
             ms_c = stage_ms.get(name + "_tc", 0.0)
             ex = work[name + "_tc_flops"]
@@ -562,7 +563,9 @@ def main():
                 contractions[name] = {"tflop_algorithmic": alg / 1e12, "tflop_executed": ex / 1e12, "ms": ms_c,
                                       "tflops": alg / (ms_c / 1e3) / 1e12,
                                       "frac_of_bf16_peak": alg / (ms_c / 1e3) / 1e12 / peak,
-                                      "executed_tflops": ex / (ms_c / 1e3) / 1e12, "useful_fraction": alg / ex}
+                                      "executed_tflops": ex / (ms_c / 1e3) / 1e12, "useful_fraction": alg / ex,
+                                      "form": "entry-major" if int(work["entry_major_mask"]) & ENTRY_BIT.get(name, 0)
+                                      else "grouped"}
         alg_near = 36.0 * alg_fp64eq["near"] * nrhs
         near_ms = stage_ms.get("near_tc") or stage_ms["near"]
         achieved = alg_near / (near_ms / 1e3) / 1e12

@@ -284,9 +284,11 @@ int vfmm_selftest_wait_timeout(int64_t polls, void* stream);
 
 /* Schedule autotuner (no counterpart in the paper): for the VFMM_MIXED form, times each small
  * split contraction of this tree and nrhs (near field, M2L, S2L, leaf far field: those with fewer
- * CTAs than two per SM) with split-K factors 1, 2, 4, 8, 16 on the caller's data, keeps the fastest
- * in the tree's schedule (used by every later call with this nrhs) and returns them in
- * splits[4] (near, M2L, S2L, far; may be NULL). Runs two ordinary solves around the timing, so
+ * CTAs than two per SM) with split-K factors 1, 2, 4, 8, 16 on the caller's data, and where the
+ * schedule holds both forms of a contraction (targets grouped, or one column per list entry with
+ * a per-target sum) times both; keeps the fastest in the tree's schedule (used by every later
+ * call with this nrhs) and returns the split-K factors in splits[4] (near, M2L, S2L, far; may be
+ * NULL; 1 for the entry-major form, see vfmm_solve_work out[7]). Runs two ordinary solves around the timing, so
  * u, u_x, u_y hold the solution afterwards; synchronises `stream`. Must not overlap other calls
  * on the same tree; graphs captured earlier keep the schedule they captured. No-op (splits = 1)
  * for VFMM_FP64. Errors as vfmm_volume_potential. */
@@ -299,7 +301,9 @@ int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, i
  *     slice product of every tile, zero-padded rows included; 0 for VFMM_FP64),
  * [1] the same for M2L, [2] for the leaf far field (L2T + M2T), [3] for S2L, [4] for S2M,
  * [5] FP64-equivalent FLOPs of the near field, 2 * 3k^2 * k^2 per U-list entry and right-hand side,
- * [6] number of U-list entries, [7] reserved (0). Host-only; no device work. */
+ * [6] number of U-list entries, [7] which contractions run in the entry-major form (one column
+ *     per list entry, summed per target afterwards): bit 0 near field, 1 M2L, 2 leaf far field,
+ *     3 S2L. Host-only; no device work. */
 #define VFMM_N_WORK 8
 int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs, double* out);
 

@@ -247,7 +247,7 @@ def tune(tree: Tree, ops: Ops, f, out, ws, stream=None):
 
 
 WORK = ("near_tc_flops", "m2l_tc_flops", "far_tc_flops", "s2l_tc_flops", "s2m_tc_flops", "near_fp64eq_flops",
-        "u_entries", "reserved")
+        "u_entries", "entry_major_mask")
 
 
 def solve_work(tree: Tree, ops: Ops, nrhs: int = 1):

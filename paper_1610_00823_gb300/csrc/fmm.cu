@@ -1167,8 +1167,9 @@ static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, 
 // stream) and kept for the life of the process. One per thread, so that the event sequence of a
 // solve cannot interleave with another thread's.
 struct SideStream {
-    cudaStream_t s = nullptr;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // f sliced; S2L done; near field done
+    cudaStream_t s = nullptr;   // S2L and the near field, lowest priority
+    cudaStream_t hp = nullptr;  // everything else, highest priority: first to get SMs that free up
+    cudaEvent_t ev[5] = {};     // f sliced; S2L done; near field done; solve start; solve end
 };
 
 static SideStream* side_stream(cudaStream_t st) {
@@ -1181,12 +1182,16 @@ static SideStream* side_stream(cudaStream_t st) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
     SideStream n;
-    bool ok = cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking) == cudaSuccess;
-    for (int i = 0; i < 3 && ok; ++i) ok = cudaEventCreateWithFlags(&n.ev[i], cudaEventDisableTiming) == cudaSuccess;
+    int least = 0, greatest = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&n.s, cudaStreamNonBlocking, least) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&n.hp, cudaStreamNonBlocking, greatest) == cudaSuccess;
+    for (int i = 0; i < 5 && ok; ++i) ok = cudaEventCreateWithFlags(&n.ev[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         for (cudaEvent_t e : n.ev)
             if (e) cudaEventDestroy(e);
         if (n.s) cudaStreamDestroy(n.s);
+        if (n.hp) cudaStreamDestroy(n.hp);
         cudaGetLastError();
         return nullptr;
     }
@@ -1201,8 +1206,29 @@ static int gemm_launches(const SplitPlan& P) {
 
 // One solve of R right-hand sides (f: [R][n_leaves][k^2]). The mixed form folds them into the
 // rows of every contraction (PS holds plans for R); the FP64 form takes R = 1.
+static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* u,
+                       double* ux, double* uy, const Workspace& w, cudaStream_t st, StageEvents* se,
+                       SideStream* side);
+
 static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* u,
                      double* ux, double* uy, const Workspace& w, cudaStream_t st, StageEvents* se = nullptr) {
+    // Mixed form with side streams: once f is sliced, S2L and then the near field run on a
+    // low-priority stream while a high-priority stream takes every other step; the latter waits
+    // for S2L before the downward combine and for the near field before the leaf kernels, and the
+    // caller's stream waits for it at the end. Timed calls keep to the caller's stream.
+    SideStream* side = (o.precision == VFMM_MIXED && w.fork && !se && !w.mix.cev) ? side_stream(st) : nullptr;
+    if (!side) return solve_steps(T, PS, o, f, u, ux, uy, w, st, se, nullptr);
+    VFMM_CUDA(cudaEventRecord(side->ev[3], st));
+    VFMM_CUDA(cudaStreamWaitEvent(side->hp, side->ev[3], 0));
+    VFMM_CHECK(solve_steps(T, PS, o, f, u, ux, uy, w, side->hp, se, side));
+    VFMM_CUDA(cudaEventRecord(side->ev[4], side->hp));
+    VFMM_CUDA(cudaStreamWaitEvent(st, side->ev[4], 0));
+    return VFMM_OK;
+}
+
+static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* u,
+                       double* ux, double* uy, const Workspace& w, cudaStream_t st, StageEvents* se,
+                       SideStream* side) {
     const int P = o.p + 1, P2 = 2 * P, kk = o.k * o.k;
     const int nleaf = T.n_leaves;
     const bool mixed = o.precision == VFMM_MIXED;
@@ -1210,10 +1236,6 @@ static int solve_one(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, 
     if (!mixed && R != 1) return fail(VFMM_ERR_INTERNAL, "the FP64 form solves one right-hand side at a time");
     const MixedOps* mo = (const MixedOps*)o.mixed;
     int launches = 0;
-    // Mixed form with a second stream: once f is sliced, S2L and then the near field run there
-    // while this stream takes S2M, M2M, M2L and coefficient 0; it waits for S2L before the
-    // downward combine and for the near field before the leaf kernels. Timed calls keep one stream.
-    SideStream* side = (mixed && w.fork && !se && !w.mix.cev) ? side_stream(st) : nullptr;
     if (mixed) {
         // near field first: its f slices also feed S2M and S2L
         mark(se, ST_NEAR, false, st);
@@ -1583,7 +1605,8 @@ extern "C" int vfmm_graph_create(const vfmm_tree* tree, const vfmm_ops* ops, con
         delete g;
         return rc != VFMM_OK ? rc : cuda_fail(e, "cudaStreamEndCapture");
     }
-    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    // kernels keep the priority of the stream they were captured on
+    e = cudaGraphInstantiate(&g->exec, g->graph, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g->graph);
         delete g;
@@ -1644,19 +1667,20 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
     VFMM_CUDA(cudaEventCreate(&e0));
     VFMM_CUDA(cudaEventCreate(&e1));
     int rc = VFMM_OK;
-    for (int j = 0; j < 4 && rc == VFMM_OK; ++j) {
-        Job& jb = jobs[j];
-        if (!jb.P->may_split || jb.P->n_groups == 0) continue;
-        const double avg_units = (double)jb.P->entries * (jb.Kp / kKBlock) / jb.P->n_groups;
-        int best = jb.P->split;
-        float best_ms = -1.0f;
-        for (int sp = 1; sp <= kMaxSplit && sp <= std::max(1.0, avg_units) && rc == VFMM_OK; sp *= 2) {
-            jb.P->split = sp;
+    // fastest split-K factor of one form of a contraction (its current factor when it cannot split)
+    auto time_form = [&](const Job& jb, SplitPlan* P, float2* part, int* best_sp, float* best_ms) {
+        const double avg_units = (double)P->entries * (jb.Kp / kKBlock) / std::max(1, P->n_groups);
+        const int max_sp = P->may_split ? kMaxSplit : 1;
+        const int keep = P->split;
+        *best_sp = keep;
+        *best_ms = -1.0f;
+        for (int sp = P->may_split ? 1 : keep; sp <= std::max(max_sp, keep) && rc == VFMM_OK; sp *= 2) {
+            if (P->may_split && sp > std::max(1.0, avg_units)) break;
+            P->split = sp;
             float total = 0.0f;
             for (int rep = 0; rep < 4 && rc == VFMM_OK; ++rep) {
                 cudaEventRecord(e0, st);
-                rc = split_gemm(*jb.P, jb.a, *jb.map, jb.Kp, jb.Rp, jb.out, w.mix.err,
-                                j == 0 ? w.mix.part_side : j == 2 ? w.mix.part_s2l : w.mix.part, jb.rows, st);
+                rc = split_gemm(*P, jb.a, *jb.map, jb.Kp, jb.Rp, jb.out, w.mix.err, part, jb.rows, st);
                 cudaEventRecord(e1, st);
                 if (rc != VFMM_OK) break;
                 cudaError_t e = cudaEventSynchronize(e1);
@@ -1665,13 +1689,34 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
                 if (e != cudaSuccess) rc = cuda_fail(e, "timing a split contraction");
                 if (rep > 0) total += ms;  // the first run warms up
             }
-            if (rc == VFMM_OK && (best_ms < 0.0f || total < best_ms)) {
-                best_ms = total;
-                best = sp;
+            if (rc == VFMM_OK && (*best_ms < 0.0f || total < *best_ms)) {
+                *best_ms = total;
+                *best_sp = sp;
+            }
+            if (!P->may_split) break;
+        }
+        P->split = *best_sp;
+    };
+    for (int j = 0; j < 4 && rc == VFMM_OK; ++j) {
+        Job& jb = jobs[j];
+        if (jb.P->n_groups == 0 || (!jb.P->may_split && !jb.P->alt)) continue;
+        float2* part = j == 0 ? w.mix.part_side : j == 2 ? w.mix.part_s2l : w.mix.part;
+        int sp = 1;
+        float ms = -1.0f;
+        time_form(jb, jb.P, part, &sp, &ms);
+        if (rc == VFMM_OK && jb.P->alt && jb.P->alt->n_groups > 0) {
+            // the other form (grouped or entry-major): kept if faster
+            int sp_alt = 1;
+            float ms_alt = -1.0f;
+            time_form(jb, jb.P->alt, part, &sp_alt, &ms_alt);
+            if (rc == VFMM_OK && ms_alt >= 0.0f && ms_alt < ms) {
+                SplitPlan* alt = jb.P->alt;
+                jb.P->alt = nullptr;
+                std::swap(*jb.P, *alt);
+                jb.P->alt = alt;
             }
         }
-        jb.P->split = best;
-        if (splits) splits[j] = best;
+        if (splits) splits[j] = jb.P->split;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -545,9 +545,10 @@ int build_contraction_plan(const std::vector<int32_t>& tgt_id,
     for (int c = 0; c < n_tables; ++c) entry_cols += (per_table[c] * R + G - 1) / G * G;
     const double grouped_cols = (double)P->entries * G;
     const size_t slab_bytes = (size_t)n_entries * R * slab_row_bytes;
-    if (n_entries == 0 || slab_bytes > kMaxSlabBytes || (double)n_entries * R > (double)INT32_MAX / 2 ||
-        (double)entry_cols * (1.0 + slab_overhead) >= 0.85 * grouped_cols)
+    if (n_entries == 0 || slab_bytes > kMaxSlabBytes || (double)n_entries * R > (double)INT32_MAX / 2)
         return VFMM_OK;
+    const bool prefer_entry = (double)entry_cols * (1.0 + slab_overhead) < 0.85 * grouped_cols;
+    if (!prefer_entry && !P->may_split) return VFMM_OK;  // large grouped contraction: no alternative
     // entry q of target t: a target of its own with the one item, keyed by (table, q)
     std::vector<int32_t> e_tgt(n_entries), seg(nt + 1, 0), seg_out(nt);
     std::vector<std::vector<std::pair<int32_t, int32_t>>> e_items(n_entries);
@@ -564,22 +565,46 @@ int build_contraction_plan(const std::vector<int32_t>& tgt_id,
         }
     }
     seg[nt] = (int32_t)q;
-    free_split_plan(P);
-    VFMM_CHECK(build_split_plan(e_tgt, e_items, e_key, n_tables, n_chunks, R, transposed, nkb, P));
-    P->entry = true;  // the slab occupies the partial-sum buffer: no split-K
-    P->may_split = false;
-    P->split = 1;
-    P->R = R;
-    P->n_seg = nt;
-    P->slab_rows = n_entries * R;
-    VFMM_CUDA(cudaMalloc(&P->seg, seg.size() * sizeof(int32_t)));
-    VFMM_CUDA(cudaMemcpy(P->seg, seg.data(), seg.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    VFMM_CUDA(cudaMalloc(&P->seg_out, std::max<size_t>(1, seg_out.size()) * sizeof(int32_t)));
-    if (nt) VFMM_CUDA(cudaMemcpy(P->seg_out, seg_out.data(), seg_out.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    SplitPlan* E = new SplitPlan();
+    int rc = build_split_plan(e_tgt, e_items, e_key, n_tables, n_chunks, R, transposed, nkb, E);
+    if (rc == VFMM_OK) {
+        E->entry = true;  // the slab occupies the partial-sum buffer: no split-K
+        E->may_split = false;
+        E->split = 1;
+        E->R = R;
+        E->n_seg = nt;
+        E->slab_rows = n_entries * R;
+        cudaError_t e = cudaMalloc(&E->seg, seg.size() * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMemcpy(E->seg, seg.data(), seg.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&E->seg_out, std::max<size_t>(1, seg_out.size()) * sizeof(int32_t));
+        if (e == cudaSuccess && nt)
+            e = cudaMemcpy(E->seg_out, seg_out.data(), seg_out.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_fail(e, "entry-major plan");
+    }
+    if (rc != VFMM_OK) {
+        free_split_plan(E);
+        delete E;
+        return rc;
+    }
+    if (prefer_entry) {
+        // the entry-major form runs; the grouped one stays as the alternative
+        SplitPlan* Gp = new SplitPlan(*P);
+        *P = *E;
+        *E = SplitPlan();
+        delete E;
+        P->alt = Gp;
+    } else {
+        P->alt = E;
+    }
     return VFMM_OK;
 }
 
 void free_split_plan(SplitPlan* P) {
+    if (P->alt) {
+        free_split_plan(P->alt);
+        delete P->alt;
+        P->alt = nullptr;
+    }
     int32_t* ps[] = {P->tgt, P->ptr, P->cfg, P->src, P->seg, P->seg_out};
     for (int32_t* p : ps)
         if (p) cudaFree(p);

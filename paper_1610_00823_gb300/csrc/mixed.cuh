@@ -150,7 +150,8 @@ int build_split_plan(const std::vector<int32_t>& tgt_id,
 // build_split_plan, or its entry-major form when that executes enough fewer columns: chosen when
 // (entry-major columns) x (1 + slab_overhead) < 0.85 x (grouped columns, padding included) and the
 // slab (entries x R x slab_row_bytes) stays within 256 MB. slab_overhead = the slab's write and read
-// time per column relative to its tensor time.
+// time per column relative to its tensor time. A small contraction (fewer CTAs than two per SM)
+// whose slab fits keeps the form not chosen in P->alt.
 int build_contraction_plan(const std::vector<int32_t>& tgt_id,
                            const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                            const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,

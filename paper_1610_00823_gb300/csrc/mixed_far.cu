@@ -321,10 +321,14 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
 void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t elems[3]) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     const size_t R = (size_t)PS.R;
-    auto need = [](const SplitPlan& P, size_t rows, int Rp) -> size_t {
+    auto need1 = [](const SplitPlan& P, size_t rows, int Rp) -> size_t {
         if (P.entry) return (size_t)P.slab_rows * Rp;  // one slab row per entry
         const int f = P.may_split ? kMaxSplit : P.split;
         return f > 1 ? (size_t)f * rows * Rp : 0;
+    };
+    // room for the alternative form too, so that vfmm_tune can switch without a new workspace
+    auto need = [&](const SplitPlan& P, size_t rows, int Rp) -> size_t {
+        return std::max(need1(P, rows, Rp), P.alt ? need1(*P.alt, rows, Rp) : size_t(0));
     };
     size_t a = need(PS.near, T.n_leaves * R, mo->Rp);
     size_t b = need(PS.m2l, T.n_boxes * R, mo->Rx);
@@ -546,5 +550,6 @@ extern "C" int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32
     out[2] = tc(PS->far, mo->Kx, mo->Rp);
     out[3] = tc(PS->s2l, mo->Kp, mo->Rx);
     out[4] = tc(PS->s2m, mo->Kp, mo->Rx);
+    out[7] = (PS->near.entry ? 1 : 0) + (PS->m2l.entry ? 2 : 0) + (PS->far.entry ? 4 : 0) + (PS->s2l.entry ? 8 : 0);
     return VFMM_OK;
 }

@@ -176,6 +176,8 @@ struct SplitPlan {
     int64_t slab_rows = 0;     // entries * R
     int32_t* seg = nullptr;    // [n_seg + 1] first entry of each target
     int32_t* seg_out = nullptr;  // [n_seg] output row (before the R fold) of each target
+    // the other form of a small contraction (grouped or entry-major), for vfmm_tune to time
+    SplitPlan* alt = nullptr;
 };
 
 // The split contractions of the mixed form with R right-hand sides folded into the rows: the
