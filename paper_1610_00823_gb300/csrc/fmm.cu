@@ -1167,9 +1167,11 @@ static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, 
 // stream) and kept for the life of the process. One per thread, so that the event sequence of a
 // solve cannot interleave with another thread's.
 struct SideStream {
-    cudaStream_t s = nullptr;   // S2L and the near field, lowest priority
-    cudaStream_t hp = nullptr;  // everything else, highest priority: first to get SMs that free up
-    cudaEvent_t ev[5] = {};     // f sliced; S2L done; near field done; solve start; solve end
+    cudaStream_t s = nullptr;    // S2L and the near field, lowest priority
+    cudaStream_t hp = nullptr;   // everything else, highest priority: first to get SMs that free up
+    cudaStream_t aux = nullptr;  // coefficient 0 beside M2L, highest priority
+    // f sliced; S2L done; near field done; solve start; solve end; M2M done; coefficient 0 done
+    cudaEvent_t ev[7] = {};
 };
 
 static SideStream* side_stream(cudaStream_t st) {
@@ -1186,12 +1188,14 @@ static SideStream* side_stream(cudaStream_t st) {
     bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
     ok = ok && cudaStreamCreateWithPriority(&n.s, cudaStreamNonBlocking, least) == cudaSuccess;
     ok = ok && cudaStreamCreateWithPriority(&n.hp, cudaStreamNonBlocking, greatest) == cudaSuccess;
-    for (int i = 0; i < 5 && ok; ++i) ok = cudaEventCreateWithFlags(&n.ev[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&n.aux, cudaStreamNonBlocking, greatest) == cudaSuccess;
+    for (int i = 0; i < 7 && ok; ++i) ok = cudaEventCreateWithFlags(&n.ev[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         for (cudaEvent_t e : n.ev)
             if (e) cudaEventDestroy(e);
         if (n.s) cudaStreamDestroy(n.s);
         if (n.hp) cudaStreamDestroy(n.hp);
+        if (n.aux) cudaStreamDestroy(n.aux);
         cudaGetLastError();
         return nullptr;
     }
@@ -1299,6 +1303,13 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
     // downward pass
     mark(se, ST_DOWN, false, st);
     if (mixed && T.depth >= 2) {
+        // coefficient 0 (FP64) needs only the multipoles: beside M2L when forked
+        cudaStream_t c0s = st;
+        if (side) {
+            VFMM_CUDA(cudaEventRecord(side->ev[5], st));
+            VFMM_CUDA(cudaStreamWaitEvent(side->aux, side->ev[5], 0));
+            c0s = side->aux;
+        }
         VFMM_CHECK(m2l_mixed(T, PS, o, w.Mexp, w.mix, st));
         if (PS.m2l.n_groups > 0) launches += 3 + gemm_launches(PS.m2l);
         const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
@@ -1312,11 +1323,15 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
             c0_attr_dev = dev;
         }
         const unsigned c0_grid = (unsigned)std::min<int64_t>((warps + 7) / 8, 3ll * sm_count());
-        m2l_c0_kernel<<<c0_grid, 256, c0_smem, st>>>(
+        m2l_c0_kernel<<<c0_grid, 256, c0_smem, c0s>>>(
             begin, end, R, P, T.width, T.level, T.lptr[VFMM_LIST_V], T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V],
             reinterpret_cast<const double2*>(mo->m2l_r0), w.Mexp, w.mix.m2l_c0, T.lptr[VFMM_LIST_X],
             T.lidx[VFMM_LIST_X], T.lcfg[VFMM_LIST_X], T.leaf_of_box, mo->s2l_r0, f, nleaf, kk);
         ++launches;
+        if (side) {
+            VFMM_CUDA(cudaEventRecord(side->ev[6], side->aux));
+            VFMM_CUDA(cudaStreamWaitEvent(st, side->ev[6], 0));
+        }
         if (!side) {
             VFMM_CHECK(s2l_mixed(T, PS, o, w.mix, st));
             launches += gemm_launches(PS.s2l);
@@ -1400,7 +1415,6 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         l2t_gemm_kernel<<<g, 256, 0, st>>>(o.l2t, P2, kk, nleaf, T.box_of_leaf, w.Lexp, w.far);
     }
     mark(se, ST_L2T, true, st);
-    if (side) VFMM_CUDA(cudaStreamWaitEvent(st, side->ev[2], 0));
     mark(se, ST_LEAF, false, st);
     LeafArgs a;
     a.nleaf = nleaf;
@@ -1430,6 +1444,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         int lw = 0;
         const double wm = 2.0 * std::frexp(T.width, &lw);  // width = wm 2^lw, wm in [1, 2)
         lw -= 1;
+        if (side) VFMM_CUDA(cudaStreamWaitEvent(st, side->ev[2], 0));  // the near-field output
         leaf_mixed_kernel<<<(unsigned)nv, ((kk + 31) / 32) * 32, 0, st>>>(
             nleaf, R, kk, mo->Rp, lw, wm, T.box_of_leaf, T.level, w.mix.out, mo->Er, w.mix.Ef, w.mix.far_out,
             mo->far_E, w.mix.Et, w.mix.scal, u, ux, uy);
