@@ -179,10 +179,11 @@ int vfmm_workspace_size(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs
  * counterpart in the paper, which solves one right-hand side at a time).
  * Everything is ordered on `stream`, with no host synchronisation and no allocation (the first
  * VFMM_MIXED call for a new nrhs builds its schedules on the host, see vfmm_workspace_size).
- * VFMM_MIXED forks its near-field and S2L contractions onto a second stream that the library
- * keeps per host thread and device (created by the thread's first call made outside stream
- * capture), and joins it back into `stream` by events before the call returns its last launch;
- * under stream capture the fork becomes parallel branches of the graph.
+ * VFMM_MIXED forks its work onto internal streams that the library keeps per host thread and
+ * device (created by the thread's first call made outside stream capture): S2L and the near field
+ * on a lowest-priority stream, the rest of the solve on a highest-priority one (coefficient 0 on
+ * a third), all joined back into `stream` by events before the call returns; under stream
+ * capture the fork becomes parallel branches of the graph (kernel nodes keep their priorities).
  * Errors: INVALID_ARG (k or p of ops differ from the tree's k, nrhs < 1), WORKSPACE
  * (workspace_bytes below vfmm_workspace_size), CUDA. */
 int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
@@ -242,7 +243,7 @@ int vfmm_graph_destroy(vfmm_graph* graph);
  * call forks the active side streams from `stream`, deals the items to them by estimated
  * work (longest first, to the least loaded stream), and joins them back into `stream`, so
  * the batch is ordered like one kernel on `stream` and independent items overlap on the
- * GPU. One handle serves one host thread at a time. Errors: INVALID_ARG (null handle,
+ * GPU. Each item runs on its side stream alone (no further fork inside an item). One handle serves one host thread at a time. Errors: INVALID_ARG (null handle,
  * item without tree or ops), and every error of vfmm_volume_potential (the first one
  * stops the launches; streams are still joined). */
 #define VFMM_BATCH_MAX_STREAMS 64

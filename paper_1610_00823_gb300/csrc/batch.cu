@@ -67,8 +67,9 @@ int run_batch(vfmm_batch* b, int n, const vfmm_batch_item* items, int S, cudaStr
     int rc = VFMM_OK;
     for (int i : order) {
         const vfmm_batch_item& it = items[i];
-        rc = vfmm_volume_potential(it.tree, it.ops, it.f, it.nrhs, it.u, it.ux, it.uy, it.workspace,
-                                   it.workspace_bytes, b->side[assignment[i]]);
+        // each item on its own side stream only: the batch's streams already run items side by side
+        rc = volume_potential(it.tree, it.ops, it.f, it.nrhs, it.u, it.ux, it.uy, it.workspace, it.workspace_bytes,
+                              b->side[assignment[i]], false);
         if (rc != VFMM_OK) break;
     }
     // join every side stream even after an error, so that a capture in progress stays well formed
