@@ -569,8 +569,13 @@ def main():
         alg_near = 36.0 * alg_fp64eq["near"] * nrhs
         near_ms = stage_ms.get("near_tc") or stage_ms["near"]
         achieved = alg_near / (near_ms / 1e3) / 1e12
+        # DRAM bytes read + written by this launch in one ncu capture (--set full) of this command with
+        # --no-tune, on this workload with the near field in the entry-major form; null elsewhere
+        traffic = None
+        if wl.name == "adaptive_gauss20_k16_p40" and nrhs == 1 and int(work["entry_major_mask"]) & 1:
+            traffic = 110657792 + 48339712
         roof = {"kernel": "split_gemm_kernel (near field, split-BF16 tcgen05)", "bound": "tensor",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "%s bf16 burst" % peak_kind, "flops_per_launch": alg_near, "ms_per_launch": near_ms,
                 "flops": "algorithmic: 36 slice products x 2 x 3k^2 x k^2 per U-list entry",
                 "executed_tflops": work["near_tc_flops"] / (near_ms / 1e3) / 1e12,
