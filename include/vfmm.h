@@ -124,6 +124,33 @@ int vfmm_tree_build_leaves(const vfmm_tree_params* prm, const vfmm_source* src, 
 /* Uniform tree of the given depth (prm->tol and depths ignored). Synchronises. */
 int vfmm_tree_build_uniform(const vfmm_tree_params* prm, int32_t depth, void* stream, vfmm_tree** out);
 
+/* Adaptive build for an f the caller evaluates (Section 3.1 refinement; the method asks the
+ * user for nothing about f but a way to evaluate it, Section 7): a pull protocol over an
+ * opaque builder.
+ *   vfmm_tree_begin            starts a build with vfmm_tree_build's parameters, on `stream`;
+ *   vfmm_tree_pending          number of nodes where f is wanted next (0: refinement complete);
+ *   vfmm_tree_pending_nodes    writes those nodes' x and y to caller-owned device buffers of
+ *                              that length (enqueued on the builder's stream);
+ *   vfmm_tree_submit           takes f at those nodes (device, same order; read on the builder's
+ *                              stream, which the call synchronises before returning);
+ *   vfmm_tree_finish           after pending reached 0: the level restriction, numbering and
+ *                              lists, as vfmm_tree_build; returns the tree (once per builder);
+ *   vfmm_tree_builder_destroy  frees the builder (the tree stays valid).
+ * Rounds: first the k*k nodes of every box of the uniform level min(5, max_depth) (their max |f|
+ * is the F of the tail test), then, per level from min_depth on, the k*k nodes of every candidate
+ * box (box-major, node j*k + i with x varying fastest, as leaf nodes). Levels below min_depth
+ * split without f. With f equal to a built-in source at the same nodes the tree equals
+ * vfmm_tree_build's. Errors: INVALID_ARG (parameters as vfmm_tree_build, null pointers, nodes
+ * or f requested when none are pending, finish before refinement completes or twice), OOM,
+ * CUDA. */
+typedef struct vfmm_tree_builder vfmm_tree_builder;
+int vfmm_tree_begin(const vfmm_tree_params* prm, void* stream, vfmm_tree_builder** out);
+int vfmm_tree_pending(const vfmm_tree_builder* b, int64_t* n_nodes);
+int vfmm_tree_pending_nodes(const vfmm_tree_builder* b, double* x_dev, double* y_dev);
+int vfmm_tree_submit(vfmm_tree_builder* b, const double* f_dev);
+int vfmm_tree_finish(vfmm_tree_builder* b, vfmm_tree** out);
+int vfmm_tree_builder_destroy(vfmm_tree_builder* b);
+
 int vfmm_tree_info(const vfmm_tree* tree, vfmm_tree_info_t* info);
 
 /* Host copies of the box table: level, ix, iy, each [n_boxes] int32. Synchronous. */

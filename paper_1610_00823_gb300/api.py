@@ -101,6 +101,34 @@ def tree_build_leaves(cx, cy, width, k, source, n_leaves, max_depth=16, stream=N
     return Tree(h, k)
 
 
+def tree_build_pull(cx, cy, width, k, f, tol, max_depth, min_depth=0, stream=None) -> Tree:
+    """Adaptive tree for a caller-evaluated f (vfmm_tree_begin ... vfmm_tree_finish). f(x, y) takes
+    cuda float64 tensors of node coordinates and returns f at them (same length); it is called once
+    for the f-scale grid and once per tested level, on the current stream."""
+    prm = _lib.TreeParams(cx, cy, width, k, max_depth, min_depth, tol)
+    st = _stream(stream)
+    b = ctypes.c_void_p()
+    call("vfmm_tree_begin", ctypes.byref(prm), st, ctypes.byref(b))
+    try:
+        while True:
+            n = ctypes.c_int64()
+            call("vfmm_tree_pending", b, ctypes.byref(n))
+            if n.value == 0:
+                break
+            x = torch.empty(n.value, dtype=torch.float64, device="cuda")
+            y = torch.empty_like(x)
+            call("vfmm_tree_pending_nodes", b, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()))
+            fv = torch.as_tensor(f(x, y), dtype=torch.float64, device="cuda").reshape(-1).contiguous()
+            if fv.numel() != n.value:
+                raise ValueError("f returned %d values for %d nodes" % (fv.numel(), n.value))
+            call("vfmm_tree_submit", b, ctypes.c_void_p(fv.data_ptr()))
+        h = ctypes.c_void_p()
+        call("vfmm_tree_finish", b, ctypes.byref(h))
+    finally:
+        _lib.load().vfmm_tree_builder_destroy(b)
+    return Tree(h, k)
+
+
 def tree_build_uniform(cx, cy, width, k, depth, stream=None) -> Tree:
     prm = _lib.TreeParams(cx, cy, width, k, depth, depth, 0.0)
     h = ctypes.c_void_p()

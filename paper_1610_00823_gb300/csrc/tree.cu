@@ -179,7 +179,8 @@ __global__ void fscale_kernel(NodeGeom g, SourceDev src, int level, double* fmax
 // C[m*k + i] = (2 - delta_m0)/k T_m(t_i). Called by a whole CTA (blockDim = k*k rounded up to
 // a multiple of 32); the result is valid in thread 0. V and Tm hold k*k doubles, red 8.
 __device__ double box_tail(const NodeGeom& g, const SourceDev& src, int level, uint32_t key,
-                           const double* __restrict__ C, double* V, double* Tm, double* red) {
+                           const double* __restrict__ C, double* V, double* Tm, double* red,
+                           const double* __restrict__ fv = nullptr) {
     const int k = g.k;
     const int t = threadIdx.x;
     const bool active = t < k * k;
@@ -187,8 +188,10 @@ __device__ double box_tail(const NodeGeom& g, const SourceDev& src, int level, u
     morton_decode(key, &ix, &iy);
     const double h = ldexp(g.width, -level);
     const int i = t % k, j = t / k;
+    // f at the box's nodes: the caller's values (pull protocol) or the built-in source
     if (active)
-        V[j * k + i] = source_eval(src, node_coord(g.lox, ix, g.xhat[i], h), node_coord(g.loy, iy, g.xhat[j], h));
+        V[j * k + i] = fv ? fv[t]
+                          : source_eval(src, node_coord(g.lox, ix, g.xhat[i], h), node_coord(g.loy, iy, g.xhat[j], h));
     __syncthreads();
     // Tm[m][i] = sum_q C[m][q] V[q][i], thread (m = j, i)
     if (active) {
@@ -214,15 +217,16 @@ __device__ double box_tail(const NodeGeom& g, const SourceDev& src, int level, u
     return mx;
 }
 
-// One CTA per candidate box of one level: split flag = tail > thresh.
+// One CTA per candidate box of one level: split flag = tail > thresh. fv (optional): the caller's
+// f values, k^2 per candidate box in candidate order.
 __global__ void refine_kernel(NodeGeom g, SourceDev src, int level, const uint32_t* __restrict__ keys, int n,
                               const double* __restrict__ C, double thresh, int32_t* __restrict__ flags,
-                              double* __restrict__ min_margin) {
+                              double* __restrict__ min_margin, const double* __restrict__ fv = nullptr) {
     __shared__ double V[16 * 16];
     __shared__ double Tm[16 * 16];
     __shared__ double red[8];
     const int b = blockIdx.x;
-    const double mx = box_tail(g, src, level, keys[b], C, V, Tm, red);
+    const double mx = box_tail(g, src, level, keys[b], C, V, Tm, red, fv ? fv + (size_t)b * g.k * g.k : nullptr);
     if (threadIdx.x == 0 && b < n) {
         flags[b] = mx > thresh ? 1 : 0;
         if (thresh > 0.0) atomic_min_nonneg(min_margin, fabs(mx / thresh - 1.0));
@@ -689,6 +693,9 @@ static int greedy_refine(const BuildCtx& B, const SourceDev& src, int max_depth,
     return VFMM_OK;
 }
 
+static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt, int depth, cudaStream_t st,
+                    DeviceTree* T);
+
 // Builds the tree. src == nullptr means a uniform tree of depth `uniform_depth`; leaf_target > 0
 // selects the greedy leaf-count refinement instead of the tolerance test.
 static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_depth, int64_t leaf_target,
@@ -769,6 +776,13 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
         }
     }
 
+    return finalize(keys, cnt, depth, st, T);
+}
+
+// Balance (2:1, finest level first), canonical numbering, lists and schedules of a refined tree
+// given its boxes per level (T's root geometry, k, f scale and margin already set).
+static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt, int depth, cudaStream_t st,
+                    DeviceTree* T) {
     // level restriction, finest level first
     for (int l = depth; l >= 2; --l) {
         const int m = l - 2;
@@ -947,9 +961,212 @@ static int leaf_nodes_impl(const DeviceTree* T, const vfmm_source* s, double* o0
     return VFMM_OK;
 }
 
+// ---------------------------------------------------------------- caller-evaluated f (pull protocol)
+// Nodes where the caller evaluates f: box b of `level` (Morton key keys[b], or the full grid
+// b = iy 2^level + ix when keys is null), node t = j k + i, the same coordinates the built-in
+// sources are evaluated at.
+__global__ void pending_nodes_kernel(NodeGeom g, int level, const uint32_t* __restrict__ keys, int64_t nbox,
+                                     double* __restrict__ x, double* __restrict__ y) {
+    const int kk = g.k * g.k;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nbox * kk) return;
+    const int64_t b = q / kk;
+    const int t = (int)(q - b * kk);
+    int ix, iy;
+    if (keys) {
+        morton_decode(keys[b], &ix, &iy);
+    } else {
+        const int side = 1 << level;
+        ix = (int)(b % side);
+        iy = (int)(b / side);
+    }
+    const double h = ldexp(g.width, -level);
+    x[q] = node_coord(g.lox, ix, g.xhat[t % g.k], h);
+    y[q] = node_coord(g.loy, iy, g.xhat[t / g.k], h);
+}
+
+// F = max |f| over the caller's values on the f-scale grid.
+__global__ void fmax_values_kernel(const double* __restrict__ f, int64_t n, double* __restrict__ out) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(f[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+}  // namespace vfmm
+
+// Refinement state of a tree whose f the caller evaluates (same test, order and balance as
+// vfmm_tree_build).
+struct vfmm_tree_builder {
+    vfmm_tree_params prm{};
+    cudaStream_t st = nullptr;
+    vfmm::BuildCtx B;
+    int phase = 0;  // 0: f wanted on the f-scale grid; 1: on the candidates of `level`; 2: refined; 3: finished
+    int level = 0, m0 = 0, depth = 0;
+    double F = 0.0, thresh = 0.0;
+    std::vector<vfmm::DBuf<uint32_t>> keys;
+    std::vector<int64_t> cnt;
+    vfmm::DBuf<double> scal;  // [0] F, [1] smallest |tail / threshold - 1|
+};
+
+namespace vfmm {
+
+// Splits the candidates of the builder's current level: every box (fv null) or those whose tail
+// on the caller's values fv exceeds the threshold; phase 2 when none splits.
+static int builder_split(vfmm_tree_builder* b, const double* fv) {
+    const int l = b->level, k = b->prm.k;
+    const int64_t n = b->cnt[l];
+    cudaStream_t st = b->st;
+    DBuf<int32_t> flags, offs;
+    VFMM_CHECK(flags.alloc(n));
+    VFMM_CHECK(offs.alloc(n));
+    if (!fv)
+        fill_kernel<<<nblk(n), 256, 0, st>>>(flags.p, n, 1);
+    else
+        refine_kernel<<<(unsigned)n, ((k * k + 31) / 32) * 32, 0, st>>>(b->B.g, SourceDev(), l, b->keys[l].p, (int)n,
+                                                                         b->B.C.p, b->thresh, flags.p, b->scal.p + 1,
+                                                                         fv);
+    VFMM_CUDA(cudaGetLastError());
+    int64_t m = 0;
+    VFMM_CHECK(exclusive_scan(flags.p, offs.p, n, &m, st));
+    if (m == 0) {
+        b->phase = 2;
+        return VFMM_OK;
+    }
+    VFMM_CHECK(b->keys[l + 1].alloc(4 * m));
+    emit_children_kernel<<<nblk(n), 256, 0, st>>>(b->keys[l].p, flags.p, offs.p, (int)n, b->keys[l + 1].p);
+    VFMM_CUDA(cudaGetLastError());
+    b->cnt[l + 1] = 4 * m;
+    b->depth = l + 1;
+    b->level = l + 1;
+    return VFMM_OK;
+}
+
+// Levels below min_depth split without a test; then either the candidates of the current level
+// want f (phase 1) or the refinement is over (phase 2: max_depth reached).
+static int builder_advance(vfmm_tree_builder* b) {
+    while (b->phase != 2 && b->level < b->prm.max_depth && b->level < b->prm.min_depth)
+        VFMM_CHECK(builder_split(b, nullptr));
+    if (b->phase != 2) b->phase = b->level < b->prm.max_depth ? 1 : 2;
+    return VFMM_OK;
+}
+
+static int64_t builder_pending(const vfmm_tree_builder* b) {
+    const int64_t kk = (int64_t)b->prm.k * b->prm.k;
+    if (b->phase == 0) return (1ll << (2 * b->m0)) * kk;
+    if (b->phase == 1) return b->cnt[b->level] * kk;
+    return 0;
+}
+
 }  // namespace vfmm
 
 using namespace vfmm;
+
+extern "C" int vfmm_tree_begin(const vfmm_tree_params* prm, void* stream, vfmm_tree_builder** out) {
+    if (!out) return fail(VFMM_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    VFMM_CHECK(check_params(prm));
+    if (prm->max_depth < 0 || prm->max_depth > kMaxDepth || prm->min_depth < 0 || prm->min_depth > prm->max_depth)
+        return fail(VFMM_ERR_INVALID_ARG, "need 0 <= min_depth <= max_depth <= 16");
+    if (!(prm->tol >= 0.0)) return fail(VFMM_ERR_INVALID_ARG, "tol must be >= 0");
+    vfmm_tree_builder* b = new vfmm_tree_builder();
+    b->prm = *prm;
+    b->st = (cudaStream_t)stream;
+    b->B.st = b->st;
+    b->m0 = std::min(5, prm->max_depth);
+    b->keys.resize(prm->max_depth + 1);
+    b->cnt.assign(prm->max_depth + 1, 0);
+    int rc = upload_node_tables(prm->k, b->B);
+    b->B.g = NodeGeom{prm->cx - prm->width / 2.0, prm->cy - prm->width / 2.0, prm->width, prm->k, b->B.xhat.p};
+    if (rc == VFMM_OK) rc = b->keys[0].alloc(1);
+    if (rc == VFMM_OK) rc = b->scal.alloc(2);
+    if (rc == VFMM_OK) {
+        const uint32_t zero = 0;
+        const double init[2] = {0.0, INFINITY};
+        cudaError_t e = cudaMemcpyAsync(b->keys[0].p, &zero, sizeof(zero), cudaMemcpyHostToDevice, b->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->scal.p, init, sizeof(init), cudaMemcpyHostToDevice, b->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "tree begin");
+    }
+    if (rc != VFMM_OK) {
+        delete b;
+        return rc;
+    }
+    b->cnt[0] = 1;
+    *out = b;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_pending(const vfmm_tree_builder* b, int64_t* n_nodes) {
+    if (!b || !n_nodes) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    *n_nodes = builder_pending(b);
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_pending_nodes(const vfmm_tree_builder* b, double* x_dev, double* y_dev) {
+    if (!b || !x_dev || !y_dev) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    const int64_t n = builder_pending(b);
+    if (n == 0) return fail(VFMM_ERR_INVALID_ARG, "no nodes pending");
+    const int64_t nbox = n / ((int64_t)b->prm.k * b->prm.k);
+    if (b->phase == 0)
+        pending_nodes_kernel<<<nblk(n), 256, 0, b->st>>>(b->B.g, b->m0, nullptr, nbox, x_dev, y_dev);
+    else
+        pending_nodes_kernel<<<nblk(n), 256, 0, b->st>>>(b->B.g, b->level, b->keys[b->level].p, nbox, x_dev, y_dev);
+    VFMM_CUDA(cudaGetLastError());
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_submit(vfmm_tree_builder* b, const double* f_dev) {
+    if (!b || !f_dev) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    if (b->phase >= 2) return fail(VFMM_ERR_INVALID_ARG, "refinement is complete: no f wanted");
+    if (b->phase == 0) {
+        const int64_t n = builder_pending(b);
+        fmax_values_kernel<<<(unsigned)std::min<int64_t>(1024, nblk(n)), 256, 0, b->st>>>(f_dev, n, b->scal.p);
+        VFMM_CUDA(cudaGetLastError());
+        VFMM_CUDA(cudaMemcpyAsync(&b->F, b->scal.p, sizeof(double), cudaMemcpyDeviceToHost, b->st));
+        VFMM_CUDA(cudaStreamSynchronize(b->st));
+        b->thresh = b->prm.tol * b->F;
+        b->phase = 1;
+        return builder_advance(b);
+    }
+    VFMM_CHECK(builder_split(b, f_dev));
+    VFMM_CHECK(builder_advance(b));
+    VFMM_CUDA(cudaStreamSynchronize(b->st));  // f_dev may be reused or freed once this returns
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_finish(vfmm_tree_builder* b, vfmm_tree** out) {
+    if (!b || !out) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (b->phase != 2) return fail(VFMM_ERR_INVALID_ARG, b->phase == 3 ? "tree already finished" : "f still pending");
+    vfmm_tree* t = new vfmm_tree();
+    DeviceTree* T = &t->t;
+    T->k = b->prm.k;
+    T->cx = b->prm.cx;
+    T->cy = b->prm.cy;
+    T->width = b->prm.width;
+    T->f_scale = b->F;
+    double mm = INFINITY;
+    cudaError_t e = cudaMemcpyAsync(&mm, b->scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    int rc = e == cudaSuccess ? VFMM_OK : cuda_fail(e, "tree finish");
+    T->min_margin = mm;
+    if (rc == VFMM_OK) rc = finalize(b->keys, b->cnt, b->depth, b->st, T);
+    b->phase = 3;
+    if (rc != VFMM_OK) {
+        free_tree(T);
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_builder_destroy(vfmm_tree_builder* b) {
+    delete b;
+    return VFMM_OK;
+}
 
 extern "C" int vfmm_tree_build(const vfmm_tree_params* prm, const vfmm_source* src, void* stream, vfmm_tree** out) {
     if (!out) return fail(VFMM_ERR_INVALID_ARG, "null out");
