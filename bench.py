@@ -169,7 +169,7 @@ def run_reference(args, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "n_leaves": ot.n_leaves, "n_targets": ot.n_leaves * kk, "k": wl.k,
-                       "p": wl.p, "parallelism": "replicas"},
+                       "p": wl.p, "parallelism": "replicas" if args.gpus > 1 else "single GPU"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -241,7 +241,8 @@ def run_batch(args):
             print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                              "data": "synthetic", "config": {"workload": name, "parallelism": "replicas"},
+                              "data": "synthetic",
+                              "config": {"workload": name, "parallelism": "replicas" if world > 1 else "single GPU"},
                               "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                                                "sample": sample},
                               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
