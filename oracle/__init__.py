@@ -19,6 +19,7 @@ Modules:
   tables  - unit-scale operators: near tables, S2M, S2L, M2T, L2T, M2M, M2L, L2L
   fmm     - the FMM passes (Section 3.1) producing u, u_x, u_y at leaf nodes
   brute   - direct quadrature of V[f~] without FMM or tables, for small trees
+  interp  - the leaf interpolant v~ of computed values at arbitrary points (Section 3.1)
 
 Parity status: every function is pinned by tests/test_oracle_*.py except where
 its docstring says "parity unpinned".
