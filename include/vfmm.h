@@ -224,6 +224,22 @@ int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const
                                double* u_host, double* ux_host, double* uy_host, void* workspace_dev,
                                size_t workspace_bytes, void* stream);
 
+/* v~: values at arbitrary points (Section 3.1: away from the collocation nodes the paper takes
+ * the polynomial that interpolates the computed values on the leaf holding the point; Section
+ * 3.3 on its error). For each point (x_dev[i], y_dev[i]) and each of the n_fields fields
+ * (1..8; fields_dev and out_dev are host arrays of n_fields device pointers), out_dev[q][i] =
+ * the tensor Lagrange interpolant on the leaf's k x k nodes of fields_dev[q] ([n_leaves][k*k],
+ * the layout of f and u, e.g. u, u_x, u_y of one right-hand side) at the point.
+ * The leaf of a point comes from its integer coordinates at the finest level,
+ * floor(2^depth (x - lo) / width) (clamped to 2^depth - 1 on the root's upper edges), so a
+ * point on an edge shared by two leaves belongs to the one above or to its right; leaf_dev
+ * (optional, [n_points] int32) receives its canonical leaf index. Points outside the closed
+ * root box or with a NaN coordinate get NaN and leaf -1. Stream-ordered, no allocation.
+ * Errors: INVALID_ARG (null tree or pointers, n_fields outside [1, 8], n_points < 0), CUDA. */
+int vfmm_leaf_interpolate(const vfmm_tree* tree, int32_t n_fields, const double* const* fields_dev,
+                          int64_t n_points, const double* x_dev, const double* y_dev, double* const* out_dev,
+                          int32_t* leaf_dev, void* stream);
+
 /* Allocation-free solve. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory, such as hosts whose device memory is
  * owned entirely by their own pool allocator (so neither a workspace buffer nor a

@@ -46,6 +46,9 @@ EXPORTS = {
     "vfmm_tree_submit": [ctypes.c_void_p, ctypes.c_void_p],
     "vfmm_tree_finish": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
     "vfmm_tree_builder_destroy": [ctypes.c_void_p],
+    "vfmm_leaf_interpolate": [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                              ctypes.c_void_p],
     "vfmm_tree_info": [ctypes.c_void_p, ctypes.POINTER(TreeInfo)],
     "vfmm_tree_export_boxes": [ctypes.c_void_p, c_int32_p, c_int32_p, c_int32_p],
     "vfmm_tree_export_list": [ctypes.c_void_p, ctypes.c_int32, c_int32_p, c_int32_p, c_int32_p],

@@ -129,6 +129,26 @@ def tree_build_pull(cx, cy, width, k, f, tol, max_depth, min_depth=0, stream=Non
     return Tree(h, k)
 
 
+def leaf_interpolate(tree: Tree, fields, x, y, with_leaf=False, stream=None):
+    """v~ (vfmm_leaf_interpolate): each field (cuda float64, n_leaves*k*k values, e.g. u, u_x, u_y)
+    interpolated on its leaf at the points (x, y: cuda float64, same length). Returns the list of
+    value tensors, and the int32 leaf index per point when with_leaf."""
+    fields = [f.contiguous() for f in fields]
+    n_f = len(fields)
+    n = tree.n_leaves * tree.k * tree.k
+    if not 1 <= n_f <= 8 or any(f.dtype != torch.float64 or not f.is_cuda or f.numel() != n for f in fields):
+        raise ValueError("fields: 1..8 cuda float64 tensors of n_leaves*k*k values")
+    x = x.contiguous()
+    y = y.contiguous()
+    out = [torch.empty_like(x) for _ in range(n_f)]
+    leaf = torch.empty(x.numel(), dtype=torch.int32, device="cuda") if with_leaf else None
+    fp = (ctypes.c_void_p * n_f)(*[f.data_ptr() for f in fields])
+    op = (ctypes.c_void_p * n_f)(*[o.data_ptr() for o in out])
+    call("vfmm_leaf_interpolate", tree.handle, n_f, fp, x.numel(), ctypes.c_void_p(x.data_ptr()),
+         ctypes.c_void_p(y.data_ptr()), op, ctypes.c_void_p(leaf.data_ptr() if with_leaf else None), _stream(stream))
+    return (out, leaf) if with_leaf else out
+
+
 def tree_build_uniform(cx, cy, width, k, depth, stream=None) -> Tree:
     prm = _lib.TreeParams(cx, cy, width, k, depth, depth, 0.0)
     h = ctypes.c_void_p()
