@@ -534,6 +534,36 @@ def main():
     del ws_io
 
     peaks, peak_kind = measured_peaks()
+    offnode = None
+    if nrhs == 1:
+        # v~ (vfmm_leaf_interpolate): the solve's u, u_x, u_y at 2^22 seeded uniform random points of
+        # the root box; L2 flushed between the timed calls
+        gen = torch.Generator(device="cuda").manual_seed(20161003)
+        n_pts = 1 << 22
+        px = (wl.cx - wl.width / 2) + wl.width * torch.rand(n_pts, dtype=torch.float64, device="cuda", generator=gen)
+        py = (wl.cy - wl.width / 2) + wl.width * torch.rand(n_pts, dtype=torch.float64, device="cuda", generator=gen)
+        fields = [o.reshape(-1) for o in out]
+        for _ in range(2):
+            v.leaf_interpolate(tree, fields, px, py, stream=stream)
+        its = []
+        for _ in range(5):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            v.leaf_interpolate(tree, fields, px, py, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            its.append(e0.elapsed_time(e1))
+        ims = statistics.mean(its)
+        iflops = n_pts * 3 * 2.0 * kk  # the tensor contraction r_j = sum_i l_i V_ji, sum_j l_j r_j per field
+        ipeak = peaks["bf16_tflops"] * FP64_OVER_BF16
+        iach = iflops / (ims / 1e3) / 1e12
+        offnode = {"kernel": "leaf_interp_kernel", "points": n_pts, "fields": 3, "ms": ims,
+                   "pts_per_s": n_pts / (ims / 1e3), "sample": "uniform random in the root box, seed 20161003",
+                   "roofline": {"bound": "fp64", "achieved": iach, "peak": ipeak, "unit": "TFLOP/s",
+                                "frac": iach / ipeak, "flops": "3 fields x 2 k^2 per point",
+                                "peak_source": "%s bf16 x nominal FP64/BF16 ratio (1.25/2250)" % peak_kind}}
     if args.precision == "fp64":
         flops = 2.0 * 3 * kk * kk * tree.list_len[0] * nrhs  # near-field table applies per step
         achieved = flops / (stage_ms["near"] / 1e3) / 1e12
@@ -631,6 +661,7 @@ def main():
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_targets * 8,
                         "d2h_bytes_per_step": 3 * n_targets * 8, "ms_per_step": statistics.mean(e2e_ms)},
                 "gpu_launches": launches,
+                "offnode": offnode,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist is not None:
