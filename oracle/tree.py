@@ -12,6 +12,13 @@ Readings of the paper taken here:
   its interpolant (last two rows and columns) exceeds tol * F, with F = max |f|
   over the nodes of the uniform tree of level min(5, max_depth). Boxes above
   min_depth are always split.
+* The a-priori alternatives of Section 6.1 ("A note on adaptivity"): the same
+  comparison with the interpolation error e (max |f - p| on the nodes of the four
+  children, the "finer grid"), unweighted, times the relative area (h/W)^2, or times
+  the area for boxes that meet the boundary and the relative side length h/W
+  elsewhere. Readings: the weights are relative to the root width W so that tol
+  stays dimensionless; a box meets the boundary when the kinked source's level set
+  takes both signs on those nodes (the paper's boundary is where f_e is only C^0).
 * Canonical order: boxes sorted by (level, Morton key); the Morton key puts
   bit b of ix at bit 2b and bit b of iy at bit 2b + 1. Lists are sorted by box
   index.
@@ -208,8 +215,74 @@ def f_scale(cx, cy, width, k, src, max_depth) -> float:
     return float(np.max(np.abs(srcmod.evaluate_source(src, X, Y))))
 
 
-def build_adaptive(cx, cy, width, k, src, tol, max_depth, min_depth=0, return_info=False):
-    """Level-by-level refinement followed by balancing (Section 3.1)."""
+RULES = ("tail", "interp", "interp_area", "interp_mixed")
+
+
+def child_grid(cx, cy, width, k, level, ix, iy):
+    """The 2k x 2k grid of the nodes of the four children of each box: X, Y [n, 2k, 2k] indexed
+    [J, I], child column I // k and node I % k (rows likewise), i.e. the nodes of box
+    (level + 1, 2 ix + I // k, 2 iy + J // k)."""
+    level = np.asarray(level, dtype=np.int64).reshape(-1)
+    ix = np.asarray(ix, dtype=np.int64).reshape(-1)
+    iy = np.asarray(iy, dtype=np.int64).reshape(-1)
+    n = level.shape[0]
+    X = np.empty((n, 2 * k, 2 * k))
+    Y = np.empty((n, 2 * k, 2 * k))
+    for d in range(2):
+        for c in range(2):
+            Xc, Yc = node_coords(cx, cy, width, k, level + 1, 2 * ix + c, 2 * iy + d)
+            X[:, d * k:(d + 1) * k, c * k:(c + 1) * k] = Xc.reshape(n, k, k)
+            Y[:, d * k:(d + 1) * k, c * k:(c + 1) * k] = Yc.reshape(n, k, k)
+    return X, Y
+
+
+def interp_error(cx, cy, width, k, src, level, ix, iy):
+    """The paper's a-priori test quantity (Section 6.1): the error of the box's interpolant of f,
+    found by comparing f with it on a finer grid, here the nodes of the box's four children:
+    e = max |f - p| over that grid, p interpolating f at the box's own k x k nodes (Lagrange
+    basis of cheb.lagrange at the child nodes' positions in the box's unit coordinates).
+    Also whether the box meets the boundary: for the kinked source, the level set phi (whose
+    zero set is the curve where f is only continuous) takes both signs on the box's own and
+    children's nodes; other sources have no boundary. Returns (e [n], meets_boundary [n])."""
+    X, Y = node_coords(cx, cy, width, k, level, ix, iy)
+    V = srcmod.evaluate_source(src, X, Y).reshape(-1, k, k)
+    Xc, Yc = child_grid(cx, cy, width, k, level, ix, iy)
+    Fc = srcmod.evaluate_source(src, Xc, Yc)
+    u = np.concatenate([-0.25 + cheb.nodes(k) / 2.0, 0.25 + cheb.nodes(k) / 2.0])
+    L = cheb.lagrange(k, u)  # [2k, k]
+    P = np.einsum("Jj,nji,Ii->nJI", L, V, L)
+    e = np.max(np.abs(Fc - P).reshape(V.shape[0], -1), axis=1)
+    meets = np.zeros(V.shape[0], dtype=bool)
+    if getattr(src, "kind", None) == srcmod.SRC_KINKED:
+        ph = np.concatenate([srcmod.kinked_phi(np.asarray(src.params), X, Y).reshape(V.shape[0], -1),
+                             srcmod.kinked_phi(np.asarray(src.params), Xc, Yc).reshape(V.shape[0], -1)], axis=1)
+        meets = np.any(ph > 0.0, axis=1) & np.any(ph <= 0.0, axis=1)
+    return e, meets
+
+
+def rule_indicator(rule, cx, cy, width, k, src, level, ix, iy, C=None):
+    """Quantity compared with tol * F for each box (split when larger), per refinement rule:
+    "tail" the trailing Chebyshev coefficients (Section 3.1 reading), "interp" the interpolation
+    error e, "interp_area" e (h / W)^2, "interp_mixed" e (h / W)^2 for boxes that meet the boundary
+    and e (h / W) elsewhere (Section 6.1, the weightings by area and by side length)."""
+    level = np.asarray(level, dtype=np.int64).reshape(-1)
+    if rule == "tail":
+        X, Y = node_coords(cx, cy, width, k, level, ix, iy)
+        V = srcmod.evaluate_source(src, X, Y).reshape(-1, k, k)
+        return cheb.tail(V, k, C)
+    if rule not in RULES:
+        raise ValueError("unknown refinement rule %r" % rule)
+    e, meets = interp_error(cx, cy, width, k, src, level, ix, iy)
+    side = np.ldexp(1.0, -level)
+    if rule == "interp":
+        return e
+    if rule == "interp_area":
+        return e * side * side
+    return np.where(meets, e * side * side, e * side)
+
+
+def build_adaptive(cx, cy, width, k, src, tol, max_depth, min_depth=0, return_info=False, rule="tail"):
+    """Level-by-level refinement followed by balancing (Section 3.1); rule as rule_indicator."""
     C = cheb.values_to_coeffs_matrix(k)
     F = f_scale(cx, cy, width, k, src, max_depth)
     thresh = tol * F
@@ -223,9 +296,7 @@ def build_adaptive(cx, cy, width, k, src, tol, max_depth, min_depth=0, return_in
         if l < min_depth:
             split = np.ones(len(cur), dtype=bool)
         else:
-            X, Y = node_coords(cx, cy, width, k, arr[:, 0], arr[:, 1], arr[:, 2])
-            V = srcmod.evaluate_source(src, X, Y).reshape(-1, k, k)
-            tl = cheb.tail(V, k, C)
+            tl = rule_indicator(rule, cx, cy, width, k, src, arr[:, 0], arr[:, 1], arr[:, 2], C)
             split = tl > thresh
             if thresh > 0:
                 margins.append(np.abs(tl / thresh - 1.0))

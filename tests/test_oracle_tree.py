@@ -161,3 +161,66 @@ def test_greedy_max_depth_stops_refinement():
     src = W.gauss_source([[0.0, 0.0]], 0.001, [1.0])
     ot = T.build_greedy(0.0, 0.0, 1.0, 8, src, 10 ** 6, 2)
     assert ot.depth == 2 and ot.n_leaves == 16
+
+
+# ----------------------------------------------------------------------------- Section 6.1 rules
+class _Fn:
+    """A source for the oracle's builders defined by a plain function (kind is not a built-in)."""
+    kind = "fn"
+
+    def __init__(self, fn):
+        self.fn = fn
+
+
+def _with_fn(monkeypatch, fn):
+    from oracle import source as srcmod
+    orig = srcmod.evaluate_source
+    monkeypatch.setattr(srcmod, "evaluate_source",
+                        lambda s, x, y: s.fn(np.asarray(x), np.asarray(y)) if isinstance(s, _Fn) else orig(s, x, y))
+    return _Fn(fn)
+
+
+@pytest.mark.parametrize("rule", ["interp", "interp_area", "interp_mixed"])
+def test_interp_rules_do_not_refine_polynomials(monkeypatch, rule):
+    k = 8
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((k, k)) / 10.0
+    src = _with_fn(monkeypatch, lambda x, y: np.polynomial.polynomial.polyval2d(y, x, a))
+    t = T.build_adaptive(0.0, 0.0, 1.0, k, src, 1e-10, 6, 2, rule=rule)
+    assert t.n_leaves == 16 and t.depth == 2
+
+
+def test_interp_error_of_chebyshev_polynomial_at_its_roots(monkeypatch):
+    # p interpolates T_k at the k roots of T_k, so p = 0 and e = max |T_k| on the children's nodes
+    from oracle import cheb
+    for k in (4, 8, 16):
+        src = _with_fn(monkeypatch, lambda x, y, k=k: np.cos(k * np.arccos(np.clip(2.0 * x, -1.0, 1.0))))
+        e, meets = T.interp_error(0.0, 0.0, 1.0, k, src, [0], [0], [0])
+        u = np.concatenate([-0.25 + cheb.nodes(k) / 2.0, 0.25 + cheb.nodes(k) / 2.0])
+        exact = np.max(np.abs(np.cos(k * np.arccos(2.0 * u))))
+        assert abs(e[0] - exact) < 1e-13 and not meets[0]
+
+
+def test_rule_weights_area_and_side_length(monkeypatch):
+    src = _with_fn(monkeypatch, lambda x, y: np.exp(3.0 * x) * np.sin(5.0 * y))
+    lev, ix, iy = [2, 2], [1, 3], [0, 2]
+    e = T.rule_indicator("interp", 0.0, 0.0, 1.0, 8, src, lev, ix, iy)
+    assert np.all(e > 0)
+    assert np.allclose(T.rule_indicator("interp_area", 0.0, 0.0, 1.0, 8, src, lev, ix, iy), e / 16.0, rtol=0, atol=0)
+    assert np.allclose(T.rule_indicator("interp_mixed", 0.0, 0.0, 1.0, 8, src, lev, ix, iy), e / 4.0, rtol=0, atol=0)
+
+
+def test_boundary_boxes_of_the_kinked_source():
+    wl = W.kinked()
+    src = wl.sources[0]
+    a, c = np.asarray(src.params)[0:7], np.asarray(src.params)[7:14]
+    r0 = 0.6 + np.sum(a * np.cos(c))  # the curve crosses the positive x axis at r0
+    lev = 6
+    h = 2.0 / (1 << lev)
+    on = (int((r0 + 1.0) // h), int(1.0 // h))  # the box holding (r0, 0) (lower left of the axis)
+    inside = (int((0.3 + 1.0) // h), int((0.1 + 1.0) // h))
+    outside = (int((0.95 + 1.0) // h), int((0.1 + 1.0) // h))
+    ixs = [on[0], inside[0], outside[0]]
+    iys = [on[1], inside[1], outside[1]]
+    _, meets = T.interp_error(0.0, 0.0, 2.0, wl.k, src, [lev] * 3, ixs, iys)
+    assert meets.tolist() == [True, False, False]
