@@ -107,6 +107,23 @@ typedef struct {
  * OOM, CUDA. */
 int vfmm_tree_build(const vfmm_tree_params* prm, const vfmm_source* src, void* stream, vfmm_tree** out);
 
+/* Refinement rules of vfmm_tree_build_rule. */
+#define VFMM_REFINE_TAIL 0          /* trailing Chebyshev coefficients (vfmm_tree_build) */
+#define VFMM_REFINE_INTERP 1        /* interpolation error */
+#define VFMM_REFINE_INTERP_AREA 2   /* interpolation error x (h / width)^2 */
+#define VFMM_REFINE_INTERP_MIXED 3  /* x (h / width)^2 on boxes meeting the boundary, x h / width elsewhere */
+
+/* vfmm_tree_build with the a-priori rules of Section 6.1 ("A note on adaptivity") as the split
+ * test: the interpolation error e = max |f - p| over the nodes of the box's four children, p the
+ * interpolant of f on the box's own nodes, compared with tol * F unweighted (INTERP), times the
+ * relative area (INTERP_AREA), or times the relative area where the box meets the source's
+ * boundary and the relative side length elsewhere (INTERP_MIXED). Boundary: the curve where the
+ * kinked source is only continuous (its level set takes both signs on those nodes); other
+ * sources have none. F, depths, balance, numbering and lists as vfmm_tree_build; TAIL is
+ * vfmm_tree_build itself. Errors as vfmm_tree_build, and INVALID_ARG for an unknown rule. */
+int vfmm_tree_build_rule(const vfmm_tree_params* prm, const vfmm_source* src, int32_t rule, void* stream,
+                         vfmm_tree** out);
+
 /* Tree with a leaf-count target (for batches of uneven problems; the paper refines to a
  * tolerance only): starting from the root, the leaf of highest priority is split, one at a
  * time, until the tree has >= n_leaves leaves or no leaf below prm->max_depth is left; then

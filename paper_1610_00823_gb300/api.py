@@ -82,11 +82,19 @@ class Tree:
         return x, y
 
 
-def tree_build(cx, cy, width, k, source, tol, max_depth, min_depth=0, stream=None) -> Tree:
+REFINE_RULES = {"tail": 0, "interp": 1, "interp_area": 2, "interp_mixed": 3}
+
+
+def tree_build(cx, cy, width, k, source, tol, max_depth, min_depth=0, stream=None, rule="tail") -> Tree:
+    """Adaptive tree; rule: "tail" (vfmm_tree_build) or a Section 6.1 rule of vfmm_tree_build_rule."""
     prm = _lib.TreeParams(cx, cy, width, k, max_depth, min_depth, tol)
     s, keep = _source(source)
     h = ctypes.c_void_p()
-    call("vfmm_tree_build", ctypes.byref(prm), ctypes.byref(s), _stream(stream), ctypes.byref(h))
+    if rule == "tail":
+        call("vfmm_tree_build", ctypes.byref(prm), ctypes.byref(s), _stream(stream), ctypes.byref(h))
+    else:
+        call("vfmm_tree_build_rule", ctypes.byref(prm), ctypes.byref(s), REFINE_RULES[rule], _stream(stream),
+             ctypes.byref(h))
     del keep
     return Tree(h, k)
 

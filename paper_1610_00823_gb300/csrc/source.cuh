@@ -49,4 +49,19 @@ __device__ inline double source_eval(const SourceDev& s, double x, double y) {
     return g * (phi > 0.0 ? phi : 0.0) + h;
 }
 
+// Level set of the kinked source, phi = r_chi^2 - |x|^2 (its zero set is the curve where f is only
+// continuous); the same arithmetic as in source_eval. Other sources: 1 (no boundary).
+__device__ inline double source_phi(const SourceDev& s, double x, double y) {
+    if (s.kind != VFMM_SRC_KINKED) return 1.0;
+    const double* a = s.params;
+    const double* c = s.params + 7;
+    double rho = hypot(x, y);
+    double th = atan2(y, x);
+    double sum = 0.0;
+    for (int i = 0; i < 7; ++i) sum += a[i] * cos((i + 2) * th + c[i]);
+    double chi = smooth_step_eval((rho - 0.1) / 0.2);
+    double r = 0.6 + chi * sum;
+    return r * r - rho * rho;
+}
+
 }  // namespace vfmm

@@ -233,6 +233,81 @@ __global__ void refine_kernel(NodeGeom g, SourceDev src, int level, const uint32
     }
 }
 
+// The a-priori rules of Section 6.1: one CTA (4k^2 threads) per candidate box. e = max |f - p| over
+// the nodes of the box's four children, p the interpolant of f on the box's own nodes
+// (L: [2k][k] Lagrange basis of the own nodes at the children's node positions); weighted by 1
+// (rule 1), (h/W)^2 (rule 2), or (h/W)^2 where the source's boundary level set takes both signs on
+// those nodes and h/W elsewhere (rule 3); split flag = weighted e > thresh.
+__global__ void __launch_bounds__(1024) interp_rule_kernel(NodeGeom g, SourceDev src, int level,
+                                                           const uint32_t* __restrict__ keys, int n,
+                                                           const double* __restrict__ L, int rule, double thresh,
+                                                           int32_t* __restrict__ flags,
+                                                           double* __restrict__ min_margin) {
+    __shared__ double V[16 * 16];
+    __shared__ double R[16 * 32];
+    __shared__ double Ls[32 * 16];
+    __shared__ double red[32];
+    __shared__ int pos, nonpos;
+    const int k = g.k, K2 = 2 * k, t = threadIdx.x;
+    const int b = blockIdx.x;
+    int ix, iy;
+    morton_decode(keys[b], &ix, &iy);
+    const double h = ldexp(g.width, -level), hc = ldexp(g.width, -(level + 1));
+    if (t == 0) {
+        pos = 0;
+        nonpos = 0;
+    }
+    bool p_pos = false, p_non = false;
+    if (t < k * k) {
+        const double x = node_coord(g.lox, ix, g.xhat[t % k], h), y = node_coord(g.loy, iy, g.xhat[t / k], h);
+        V[t] = source_eval(src, x, y);
+        const double ph = source_phi(src, x, y);
+        p_pos = ph > 0.0;
+        p_non = !(ph > 0.0);
+    }
+    if (t < K2 * k) Ls[t] = L[t];
+    double fc = 0.0;
+    const bool active = t < K2 * K2;
+    const int J = t / K2, I = t % K2;
+    if (active) {
+        const int c = I / k, i = I % k, d = J / k, j = J % k;
+        const double x = node_coord(g.lox, 2 * ix + c, g.xhat[i], hc), y = node_coord(g.loy, 2 * iy + d, g.xhat[j], hc);
+        fc = source_eval(src, x, y);
+        const double ph = source_phi(src, x, y);
+        p_pos = p_pos || ph > 0.0;
+        p_non = p_non || !(ph > 0.0);
+    }
+    __syncthreads();
+    if (p_pos) pos = 1;
+    if (p_non) nonpos = 1;
+    if (t < k * K2) {  // R[j][I] = sum_i V[j][i] L[I][i]
+        const int j = t / K2, Ii = t % K2;
+        double acc = 0.0;
+        for (int i = 0; i < k; ++i) acc += V[j * k + i] * Ls[Ii * k + i];
+        R[t] = acc;
+    }
+    __syncthreads();
+    double e = 0.0;
+    if (active) {
+        double p = 0.0;
+        for (int j = 0; j < k; ++j) p += Ls[J * k + j] * R[j * K2 + I];
+        e = fabs(fc - p);
+    }
+    for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((t & 31) == 0) red[t >> 5] = e;
+    __syncthreads();
+    if (t == 0 && b < n) {
+        double mx = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+        const double side = ldexp(1.0, -level);
+        double ind = mx;
+        if (rule == 2 || (rule == 3 && pos && nonpos)) ind = mx * side * side;
+        else if (rule == 3) ind = mx * side;
+        flags[b] = ind > thresh ? 1 : 0;
+        if (thresh > 0.0) atomic_min_nonneg(min_margin, fabs(ind / thresh - 1.0));
+    }
+}
+
 // One CTA per box of a list with per-box levels: tails[b] = box_tail.
 __global__ void tail_kernel(NodeGeom g, SourceDev src, const int32_t* __restrict__ lev,
                             const uint32_t* __restrict__ keys, int n, const double* __restrict__ C,
@@ -521,6 +596,7 @@ struct BuildCtx {
     NodeGeom g;
     DBuf<double> xhat;
     DBuf<double> C;
+    DBuf<double> L;  // [2k][k] Lagrange basis of a box's nodes at its children's nodes (Section 6.1 rules)
 };
 
 static int upload_node_tables(int k, BuildCtx& B) {
@@ -537,6 +613,29 @@ static int upload_node_tables(int k, BuildCtx& B) {
     VFMM_CHECK(B.C.alloc(k * k));
     VFMM_CUDA(cudaMemcpyAsync(B.xhat.p, xh.data(), k * sizeof(double), cudaMemcpyHostToDevice, B.st));
     VFMM_CUDA(cudaMemcpyAsync(B.C.p, C.data(), k * k * sizeof(double), cudaMemcpyHostToDevice, B.st));
+    return VFMM_OK;
+}
+
+// L[I][i] = l_i(u_I): the Lagrange basis of the k nodes x_i on [-1/2, 1/2] at the positions
+// u_I = -1/4 + x_I / 2 (I < k) and 1/4 + x_{I-k} / 2 of the children's nodes, product formula.
+static int upload_child_basis(int k, BuildCtx& B) {
+    std::vector<double> x(k), L(2 * k * k);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < k; ++i) x[i] = -std::cos(pi * (2.0 * i + 1.0) / (2.0 * k)) / 2.0;
+    for (int I = 0; I < 2 * k; ++I) {
+        const double u = (I < k ? -0.25 : 0.25) + x[I % k] / 2.0;
+        for (int i = 0; i < k; ++i) {
+            double num = 1.0, den = 1.0;
+            for (int m = 0; m < k; ++m)
+                if (m != i) {
+                    num *= u - x[m];
+                    den *= x[i] - x[m];
+                }
+            L[I * k + i] = num / den;
+        }
+    }
+    VFMM_CHECK(B.L.alloc(2 * k * k));
+    VFMM_CUDA(cudaMemcpyAsync(B.L.p, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, B.st));
     return VFMM_OK;
 }
 
@@ -699,7 +798,7 @@ static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt
 // Builds the tree. src == nullptr means a uniform tree of depth `uniform_depth`; leaf_target > 0
 // selects the greedy leaf-count refinement instead of the tolerance test.
 static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_depth, int64_t leaf_target,
-                 cudaStream_t st, DeviceTree* T) {
+                 cudaStream_t st, DeviceTree* T, int rule = VFMM_REFINE_TAIL) {
     const int k = prm->k;
     BuildCtx B;
     B.st = st;
@@ -754,9 +853,13 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
             VFMM_CHECK(offs.alloc(n));
             if (l < min_depth) {
                 fill_kernel<<<nblk(n), 256, 0, st>>>(flags.p, n, 1);
-            } else {
+            } else if (rule == VFMM_REFINE_TAIL) {
                 refine_kernel<<<(unsigned)n, ((k * k + 31) / 32) * 32, 0, st>>>(B.g, *src, l, keys[l].p, (int)n, B.C.p, thresh, flags.p,
                                                              scal.p + 1);
+            } else {
+                if (!B.L.p) VFMM_CHECK(upload_child_basis(k, B));
+                interp_rule_kernel<<<(unsigned)n, ((4 * k * k + 31) / 32) * 32, 0, st>>>(
+                    B.g, *src, l, keys[l].p, (int)n, B.L.p, rule, thresh, flags.p, scal.p + 1);
             }
             VFMM_CUDA(cudaGetLastError());
             int64_t m = 0;
@@ -1165,6 +1268,30 @@ extern "C" int vfmm_tree_finish(vfmm_tree_builder* b, vfmm_tree** out) {
 
 extern "C" int vfmm_tree_builder_destroy(vfmm_tree_builder* b) {
     delete b;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_build_rule(const vfmm_tree_params* prm, const vfmm_source* src, int32_t rule, void* stream,
+                                    vfmm_tree** out) {
+    if (!out) return fail(VFMM_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    if (rule < VFMM_REFINE_TAIL || rule > VFMM_REFINE_INTERP_MIXED) return fail(VFMM_ERR_INVALID_ARG, "unknown rule");
+    VFMM_CHECK(check_params(prm));
+    if (prm->max_depth < 0 || prm->max_depth > kMaxDepth || prm->min_depth < 0 || prm->min_depth > prm->max_depth)
+        return fail(VFMM_ERR_INVALID_ARG, "need 0 <= min_depth <= max_depth <= 16");
+    if (!(prm->tol >= 0.0)) return fail(VFMM_ERR_INVALID_ARG, "tol must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    DBuf<double> pbuf;
+    SourceDev sd;
+    VFMM_CHECK(make_source(src, pbuf, &sd, st));
+    vfmm_tree* t = new vfmm_tree();
+    int r = build(prm, &sd, 0, 0, st, &t->t, rule);
+    if (r != VFMM_OK) {
+        free_tree(&t->t);
+        delete t;
+        return r;
+    }
+    *out = t;
     return VFMM_OK;
 }
 
