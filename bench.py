@@ -408,6 +408,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of CUDA-graph replays")
     ap.add_argument("--no-tune", action="store_true", help="keep the default split-K factors (no autotuner run)")
+    ap.add_argument("--refine", default="tail", choices=["tail", "interp", "interp_area", "interp_mixed"],
+                    help="refinement rule of the adaptive tree (Section 6.1 alternatives to the tail test)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -444,7 +446,7 @@ def main():
     if wl.uniform_depth >= 0:
         tree = v.tree_build_uniform(wl.cx, wl.cy, wl.width, wl.k, wl.uniform_depth)
     else:
-        tree = v.tree_build(wl.cx, wl.cy, wl.width, wl.k, src, wl.tol, wl.max_depth, wl.min_depth)
+        tree = v.tree_build(wl.cx, wl.cy, wl.width, wl.k, src, wl.tol, wl.max_depth, wl.min_depth, rule=args.refine)
     torch.cuda.synchronize()
     t_tree = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -603,7 +605,8 @@ def main():
         # DRAM bytes read + written by this launch in one ncu capture (--set full) of this command with
         # --no-tune, on this workload with the near field in the entry-major form; null elsewhere
         traffic = None
-        if wl.name == "adaptive_gauss20_k16_p40" and nrhs == 1 and int(work["entry_major_mask"]) & 1:
+        if (wl.name == "adaptive_gauss20_k16_p40" and args.refine == "tail" and nrhs == 1
+                and int(work["entry_major_mask"]) & 1):
             traffic = 110657792 + 48339712
         roof = {"kernel": "split_gemm_kernel (near field, split-BF16 tcgen05)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
@@ -652,7 +655,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "launch": "CUDA graph replay" if graph is not None else "direct calls",
                            "split_k": split_k,
-                           "tree_build_s": t_tree, "ops_create_s": t_ops},
+                           "refine": args.refine, "tree_build_s": t_tree, "ops_create_s": t_ops},
                 "stage_ms": stage_ms,
                 "roofline": roof,
                 "cpu_baseline": cpu,
