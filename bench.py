@@ -122,14 +122,14 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_setup(wl):
+def oracle_setup(wl, rule="tail"):
     from oracle import tables
     from oracle import tree as T
     src = wl.sources[0]
     if wl.uniform_depth >= 0:
         ot = T.build_uniform(wl.cx, wl.cy, wl.width, wl.k, wl.uniform_depth)
     else:
-        ot = T.build_adaptive(wl.cx, wl.cy, wl.width, wl.k, src, wl.tol, wl.max_depth, wl.min_depth)
+        ot = T.build_adaptive(wl.cx, wl.cy, wl.width, wl.k, src, wl.tol, wl.max_depth, wl.min_depth, rule=rule)
     return ot, T.build_lists(ot), tables.Ops(wl.k, wl.p), ot.sample(src)
 
 
@@ -152,7 +152,7 @@ def pick_sample(ot, L, ops, F, budget_s, rng):
 
 
 def run_reference(args, wl):
-    ot, L, ops, F = oracle_setup(wl)
+    ot, L, ops, F = oracle_setup(wl, args.refine)
     rng = np.random.default_rng(7)
     leaves = pick_sample(ot, L, ops, F, budget_s=max(2.0, 120.0 / max(1, args.steps + args.warmup)), rng=rng)
     kk = wl.k * wl.k
@@ -169,17 +169,18 @@ def run_reference(args, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "n_leaves": ot.n_leaves, "n_targets": ot.n_leaves * kk, "k": wl.k,
-                       "p": wl.p, "parallelism": "replicas" if args.gpus > 1 else "single GPU"},
+                       "p": wl.p, "parallelism": "replicas" if args.gpus > 1 else "single GPU",
+                       "refine": args.refine},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(wl, gpu_u, budget_s=15.0):
+def cpu_baseline(wl, gpu_u, budget_s=15.0, rule="tail"):
     """Oracle on a bounded sample of the same workload; also the sampled error of each GPU result
     (gpu_u: {form: (u, u_x, u_y)})."""
     t0 = time.perf_counter()
-    ot, L, ops, F = oracle_setup(wl)
+    ot, L, ops, F = oracle_setup(wl, rule)
     setup_s = time.perf_counter() - t0
     rng = np.random.default_rng(11)
     leaves = pick_sample(ot, L, ops, F, budget_s, rng)
@@ -639,7 +640,7 @@ def main():
         got = {args.precision: [o.reshape(-1)[:n1].cpu().numpy() for o in out]}
         if out64 is not None:
             got["fp64"] = [o.reshape(-1)[:n1].cpu().numpy() for o in out64]
-        cpu, errs = cpu_baseline(wl, got)
+        cpu, errs = cpu_baseline(wl, got, rule=args.refine)
 
     if rank == 0:
         clocks = clk.summary()
