@@ -5,9 +5,10 @@
 // One thread per point: the leaf is found by descending from the root with the point's integer
 // coordinates at the finest level, floor(2^D (x - lo) / W) clamped to 2^D - 1 (a point on an edge
 // shared by two leaves belongs to the one above or to the right), then every field is evaluated
-// by the barycentric form of the tensor Lagrange interpolant on the leaf's first-kind Chebyshev
-// nodes: r_j = sum_i l_i(x^) V[j][i], value = sum_j l_j(y^) r_j, with
-// l_i(t) = (w_i / (t - t_i)) / sum_m (w_m / (t - t_m)) and l_i = delta at a node.
+// by the tensor Lagrange interpolant on the leaf's first-kind Chebyshev nodes:
+// r_j = sum_i l_i(x^) V[j][i], value = sum_j l_j(y^) r_j, with the product form
+// l_i(t) = prod_{m<i} (t - t_m) prod_{m>i} (t - t_m) w_i, w_i = 1 / prod_{m != i} (t_i - t_m),
+// from prefix and suffix products (no division; exact 0 and 1 at the nodes).
 #include <cmath>
 
 #include "vfmm_internal.cuh"
@@ -22,30 +23,26 @@ struct InterpArgs {
     int nf, k, depth;
     double lox, loy, width;
     double t[16];  // nodes on [-1, 1], ascending
-    double w[16];  // barycentric weights 1 / prod_{m != i} (t_i - t_m)
+    double w[16];  // 1 / prod_{m != i} (t_i - t_m)
 };
 
-// Barycentric basis at t (k <= 16): l[i], exact delta when t is a node. K > 0: k = K, unrolled.
+// Lagrange basis at t (k <= 16), product form: l[i] = (prefix product before i) (suffix product
+// after i) w_i. K > 0: k = K, unrolled.
 template <int K>
-__device__ inline void bary_basis(const InterpArgs& a, double t, double* l) {
+__device__ inline void lagrange_basis(const InterpArgs& a, double t, double* l) {
     const int k = K > 0 ? K : a.k;
-    int hit = -1;
-    double s = 0.0;
+    double pre = 1.0;
 #pragma unroll
     for (int i = 0; i < k; ++i) {
-        const double d = t - a.t[i];
-        if (d == 0.0) hit = i;
-        l[i] = a.w[i] / d;
-        s += l[i];
+        l[i] = pre;
+        pre *= t - a.t[i];
     }
-    if (hit >= 0) {
+    double suf = 1.0;
 #pragma unroll
-        for (int i = 0; i < k; ++i) l[i] = i == hit ? 1.0 : 0.0;
-        return;
+    for (int i = k - 1; i >= 0; --i) {
+        l[i] *= suf * a.w[i];
+        suf *= t - a.t[i];
     }
-    const double inv = 1.0 / s;
-#pragma unroll
-    for (int i = 0; i < k; ++i) l[i] *= inv;
 }
 
 template <int K>
@@ -79,18 +76,32 @@ __global__ void __launch_bounds__(128) leaf_interp_kernel(InterpArgs a, const in
     const double h = ldexp(a.width, -level[b]);
     const double cxb = a.lox + ((double)ix[b] + 0.5) * h, cyb = a.loy + ((double)iy[b] + 0.5) * h;
     double lx[16], ly[16];
-    bary_basis<K>(a, (px - cxb) * (2.0 / h), lx);
-    bary_basis<K>(a, (py - cyb) * (2.0 / h), ly);
+    lagrange_basis<K>(a, (px - cxb) * (2.0 / h), lx);
+    lagrange_basis<K>(a, (py - cyb) * (2.0 / h), ly);
     const int k = K > 0 ? K : a.k, kk = k * k;
     for (int q = 0; q < a.nf; ++q) {
         const double* V = a.f[q] + (size_t)leaf * kk;
         double acc = 0.0;
+        if (K > 0) {
+            // even k: rows of 16-byte pairs (a leaf's k*k doubles start on a 16-byte boundary)
+            const double2* V2 = reinterpret_cast<const double2*>(V);
 #pragma unroll
-        for (int j = 0; j < k; ++j) {
-            double r = 0.0;
+            for (int j = 0; j < k; ++j) {
+                double r = 0.0;
 #pragma unroll
-            for (int i = 0; i < k; ++i) r = fma(lx[i], __ldg(V + j * k + i), r);
-            acc = fma(ly[j], r, acc);
+                for (int i = 0; i < k; i += 2) {
+                    const double2 v = __ldg(V2 + (j * k + i) / 2);
+                    r = fma(lx[i], v.x, r);
+                    r = fma(lx[i + 1], v.y, r);
+                }
+                acc = fma(ly[j], r, acc);
+            }
+        } else {
+            for (int j = 0; j < k; ++j) {
+                double r = 0.0;
+                for (int i = 0; i < k; ++i) r = fma(lx[i], __ldg(V + j * k + i), r);
+                acc = fma(ly[j], r, acc);
+            }
         }
         a.o[q][p] = acc;
     }
