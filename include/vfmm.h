@@ -97,6 +97,9 @@ typedef struct {
     int64_t list_len[4]; /* entries in the U, V, W, X lists */
     double f_scale;      /* F of the refinement test (0 for uniform trees) */
     double min_margin;   /* min over refinement decisions of |tail / (tol F) - 1| */
+    int64_t n_depth_capped; /* leaves at max_depth whose split test still fails (informational:
+                               the tree is complete but that refinement stopped at the depth cap;
+                               0 for uniform trees, -1 where not tested: leaf-count and pull builds) */
 } vfmm_tree_info_t;
 
 /* Adaptive build (Section 3.1): level-by-level refinement of the root box by the

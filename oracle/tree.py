@@ -302,12 +302,17 @@ def build_adaptive(cx, cy, width, k, src, tol, max_depth, min_depth=0, return_in
                 margins.append(np.abs(tl / thresh - 1.0))
         cur = _children([cur[i] for i in np.nonzero(split)[0]])
         boxes += cur
+    # leaves the depth cap stopped: boxes created at level max_depth that the test would still split
+    n_capped = 0
+    if cur and (max_depth == 0 or cur[0][0] == max_depth):
+        arr = np.array(cur, dtype=np.int64)
+        n_capped = int(np.sum(rule_indicator(rule, cx, cy, width, k, src, arr[:, 0], arr[:, 1], arr[:, 2], C) > thresh))
     refined = set(boxes)
     boxes = balance(refined)
     tree = Tree(cx, cy, width, k, boxes)
     if return_info:
         mm = float(np.min(np.concatenate(margins))) if margins else float("inf")
-        return tree, {"F": F, "min_margin": mm, "refined": refined}
+        return tree, {"F": F, "min_margin": mm, "refined": refined, "n_capped": n_capped}
     return tree
 
 

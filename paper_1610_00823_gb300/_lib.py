@@ -24,7 +24,7 @@ class Source(ctypes.Structure):
 class TreeInfo(ctypes.Structure):
     _fields_ = [("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("depth", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("list_len", ctypes.c_int64 * 4), ("f_scale", ctypes.c_double),
-                ("min_margin", ctypes.c_double)]
+                ("min_margin", ctypes.c_double), ("n_depth_capped", ctypes.c_int64)]
 
 
 class BatchItem(ctypes.Structure):

@@ -43,6 +43,7 @@ class Tree:
         self.list_len = [int(v) for v in info.list_len]
         self.f_scale = float(info.f_scale)
         self.min_margin = float(info.min_margin)
+        self.n_depth_capped = int(info.n_depth_capped)
 
     @property
     def handle(self):

@@ -813,9 +813,9 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
     T->cy = prm->cy;
     T->width = prm->width;
 
-    DBuf<double> scal;  // [0] = F, [1] = min margin
-    VFMM_CHECK(scal.alloc(2));
-    double init[2] = {0.0, INFINITY};
+    DBuf<double> scal;  // [0] = F, [1] = min margin, [2] = margin sink of the depth-cap test
+    VFMM_CHECK(scal.alloc(3));
+    double init[3] = {0.0, INFINITY, INFINITY};
     VFMM_CUDA(cudaMemcpyAsync(scal.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
     double thresh = 0.0;
     if (!uniform) {
@@ -841,6 +841,7 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
             VFMM_CUDA(cudaMemcpy(keys[l].p, lv[l].data(), cnt[l] * sizeof(uint32_t), cudaMemcpyHostToDevice));
         }
         T->min_margin = mm;
+        T->n_capped = -1;  // refined to a leaf count, not to the test
     } else {
         VFMM_CHECK(keys[0].alloc(1));
         uint32_t zero = 0;
@@ -876,6 +877,24 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
             VFMM_CUDA(cudaMemcpyAsync(&mm, scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
             VFMM_CUDA(cudaStreamSynchronize(st));
             T->min_margin = mm;
+            // leaves the depth cap stopped: the split test on the boxes of level max_depth
+            const int64_t nc = cnt[max_depth];
+            T->n_capped = 0;
+            if (nc > 0) {
+                DBuf<int32_t> cf, co;
+                VFMM_CHECK(cf.alloc(nc));
+                VFMM_CHECK(co.alloc(nc));
+                if (rule == VFMM_REFINE_TAIL) {
+                    refine_kernel<<<(unsigned)nc, ((k * k + 31) / 32) * 32, 0, st>>>(
+                        B.g, *src, max_depth, keys[max_depth].p, (int)nc, B.C.p, thresh, cf.p, scal.p + 2);
+                } else {
+                    if (!B.L.p) VFMM_CHECK(upload_child_basis(k, B));
+                    interp_rule_kernel<<<(unsigned)nc, ((4 * k * k + 31) / 32) * 32, 0, st>>>(
+                        B.g, *src, max_depth, keys[max_depth].p, (int)nc, B.L.p, rule, thresh, cf.p, scal.p + 2);
+                }
+                VFMM_CUDA(cudaGetLastError());
+                VFMM_CHECK(exclusive_scan(cf.p, co.p, nc, &T->n_capped, st));
+            }
         }
     }
 
@@ -1250,6 +1269,7 @@ extern "C" int vfmm_tree_finish(vfmm_tree_builder* b, vfmm_tree** out) {
     T->cy = b->prm.cy;
     T->width = b->prm.width;
     T->f_scale = b->F;
+    T->n_capped = -1;  // the last level's boxes were not offered for a test
     double mm = INFINITY;
     cudaError_t e = cudaMemcpyAsync(&mm, b->scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
@@ -1365,6 +1385,7 @@ extern "C" int vfmm_tree_info(const vfmm_tree* tree, vfmm_tree_info_t* info) {
     for (int q = 0; q < 4; ++q) info->list_len[q] = T.llen[q];
     info->f_scale = T.f_scale;
     info->min_margin = T.min_margin;
+    info->n_depth_capped = T.n_capped;
     return VFMM_OK;
 }
 

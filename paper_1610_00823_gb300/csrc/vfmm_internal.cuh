@@ -196,6 +196,7 @@ struct DeviceTree {
     int32_t n_boxes = 0, n_leaves = 0, depth = 0, k = 0;
     double cx = 0, cy = 0, width = 0;
     double f_scale = 0, min_margin = 0;
+    int64_t n_capped = 0;  // leaves at max_depth still failing the split test (-1: not tested)
     std::vector<int32_t> level_start;  // host copy, depth + 2 entries
     uint32_t* key = nullptr;           // Morton key per box
     int32_t* level = nullptr;

@@ -66,3 +66,23 @@ def test_tail_rule_is_tree_build_and_unknown_rule_is_rejected():
     h2 = ctypes.c_void_p()
     assert lib.vfmm_tree_build_rule(ctypes.byref(prm), ctypes.byref(s), 4, stream, ctypes.byref(h2)) == -1
     del keep
+
+
+@pytest.mark.parametrize("case,rule,depth", [("gauss", "tail", 4), ("kinked", "tail", 4), ("gauss", "interp", 3),
+                                             ("kinked", "interp_mixed", 2), ("gauss", "tail", 7)])
+def test_depth_capped_leaves_match_oracle(case, rule, depth):
+    mk, k, tol, _, width = CASES[case]
+    src = mk()
+    gt = v.tree_build(0.0, 0.0, width, k, src, tol, depth, rule=rule)
+    ot, info = T.build_adaptive(0.0, 0.0, width, k, src, tol, depth, return_info=True, rule=rule)
+    same_tree(gt, ot)
+    assert gt.n_depth_capped == info["n_capped"]
+    if depth < 7:
+        assert gt.n_depth_capped > 0
+
+
+def test_depth_capped_conventions():
+    assert v.tree_build_uniform(0.0, 0.0, 1.0, 8, 3).n_depth_capped == 0
+    src = W.narrow_gaussians(5, n=3, sigma=0.04)
+    assert v.tree_build_leaves(0.0, 0.0, 1.0, 8, src, 50).n_depth_capped == -1
+    assert v.tree_build_pull(0.0, 0.0, 1.0, 8, lambda x, y: x * y, 1e-6, 2).n_depth_capped == -1

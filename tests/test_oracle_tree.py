@@ -224,3 +224,14 @@ def test_boundary_boxes_of_the_kinked_source():
     iys = [on[1], inside[1], outside[1]]
     _, meets = T.interp_error(0.0, 0.0, 2.0, wl.k, src, [lev] * 3, ixs, iys)
     assert meets.tolist() == [True, False, False]
+
+
+@pytest.mark.parametrize("rule", ["tail", "interp"])
+def test_depth_cap_count_with_zero_tolerance(rule):
+    # tol = 0: every box with a nonzero test quantity splits, so the tree is uniform to max_depth and
+    # every leaf there is capped
+    src = W.narrow_gaussians(5, n=3, sigma=0.04)
+    t, info = T.build_adaptive(0.0, 0.0, 1.0, 8, src, 0.0, 3, return_info=True, rule=rule)
+    assert t.n_leaves == 64 and info["n_capped"] == 64
+    t, info = T.build_adaptive(0.0, 0.0, 1.0, 8, src, 1e-6, 7, return_info=True, rule=rule)
+    assert t.depth < 7 and info["n_capped"] == 0
