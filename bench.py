@@ -185,6 +185,11 @@ def cpu_baseline(wl, gpu_u, budget_s=15.0, rule="tail"):
     rng = np.random.default_rng(11)
     leaves = pick_sample(ot, L, ops, F, budget_s, rng)
     dt, ref = oracle_sample_step(ot, L, ops, F, leaves)
+    # when the sample is the whole workload and quick, repeat it up to about 10 s and take the mean
+    runs = [dt]
+    while sum(runs) < min(10.0, budget_s) and len(runs) < 20:
+        runs.append(oracle_sample_step(ot, L, ops, F, leaves)[0])
+    dt = statistics.mean(runs)
     kk = wl.k * wl.k
     errs = None
     if gpu_u:
@@ -197,8 +202,9 @@ def cpu_baseline(wl, gpu_u, budget_s=15.0, rule="tail"):
                 got = res[q].reshape(ot.n_leaves, kk)[leaves]
                 errs[form][nm] = float(np.max(np.abs(got - ref[q])) / np.max(np.abs(ref[q])))
     return {"value": len(leaves) * kk / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d of %d leaves (%d targets), full upward pass included, %.1f s; oracle setup %.1f s untimed"
-                      % (len(leaves), ot.n_leaves, len(leaves) * kk, dt, setup_s)}, errs
+            "sample": "%d of %d leaves (%d targets), full upward pass included, %.1f s per run, mean of %d runs; "
+                      "oracle setup %.1f s untimed" % (len(leaves), ot.n_leaves, len(leaves) * kk, dt, len(runs),
+                                                         setup_s)}, errs
 
 
 # ----------------------------------------------------------------------------- batched problems
