@@ -235,3 +235,23 @@ def test_depth_cap_count_with_zero_tolerance(rule):
     assert t.n_leaves == 64 and info["n_capped"] == 64
     t, info = T.build_adaptive(0.0, 0.0, 1.0, 8, src, 1e-6, 7, return_info=True, rule=rule)
     assert t.depth < 7 and info["n_capped"] == 0
+
+
+def test_interp_rules_against_closed_form_potential():
+    """Section 6.1: refining until the interpolation error is within tol gives an overall error
+    well below tol; weighting it by the box area gets close to tol. Checked on Gaussians well
+    inside the box (closed-form potential), k = 8, p = 20, tol = 1e-6."""
+    pytest.importorskip("scipy.special")
+    from oracle import fmm
+    from test_oracle_fmm import _gauss_closed_form
+    ops = tables.Ops(8, 20)
+    src = W.narrow_gaussians(31, n=3, sigma=0.03, spread=0.2)
+    errs = {}
+    for rule in ("interp", "interp_area"):
+        t = T.build_adaptive(0, 0, 1, 8, src, 1e-6, 12, rule=rule)
+        u = fmm.solve(t, T.build_lists(t), ops, t.sample(src))
+        X, Y = t.leaf_nodes()
+        ref = _gauss_closed_form(src.params, X, Y)
+        errs[rule] = float(np.max(np.abs(u[0] - ref[0])) / np.max(np.abs(ref[0])))
+    assert errs["interp"] < 1e-7
+    assert 1e-7 < errs["interp_area"] < 1e-5
