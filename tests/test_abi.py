@@ -38,3 +38,21 @@ def test_error_strings_need_no_gpu(lib):
     assert lib.vfmm_strerror(0) == b"ok"
     assert lib.vfmm_strerror(-6) == b"workspace too small"
     assert lib.vfmm_strerror(12345) == b"unknown error code"
+
+
+def _declared_arity():
+    """Parameter count of every declared function, from the header text."""
+    txt = open(HEADER).read()
+    out = {}
+    for m in re.finditer(r"^\s*(?:int|const char\*)\s+(vfmm_\w+)\s*\(([^;]*?)\)\s*;", txt, flags=re.M | re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    from paper_1610_00823_gb300 import _lib
+    arity = _declared_arity()
+    assert set(arity) == set(declared())
+    for name, n in arity.items():
+        assert len(_lib.EXPORTS[name]) == n, (name, len(_lib.EXPORTS[name]), n)
