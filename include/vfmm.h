@@ -96,7 +96,8 @@ typedef struct {
     int32_t depth, k;
     int64_t list_len[4]; /* entries in the U, V, W, X lists */
     double f_scale;      /* F of the refinement test (0 for uniform trees) */
-    double min_margin;   /* min over refinement decisions of |tail / (tol F) - 1| */
+    double min_margin;   /* min over refinement decisions of |q / (tol F) - 1|, q the split test's
+                            quantity (the tail, or a vfmm_tree_build_rule rule's weighted error) */
     int64_t n_depth_capped; /* leaves at max_depth whose split test still fails (informational:
                                the tree is complete but that refinement stopped at the depth cap;
                                0 for uniform trees, -1 where not tested: leaf-count and pull builds) */
