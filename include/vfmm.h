@@ -67,7 +67,10 @@ extern "C" {
 
 /* Arithmetic of the solve. */
 #define VFMM_FP64 0  /* every product and sum in FP64 */
-#define VFMM_MIXED 1 /* near-field table apply as split-BF16 tensor-core products, FP64 elsewhere */
+/* VFMM_MIXED: every dense contraction (near-field tables, S2M, M2L, S2L, L2T + M2T) as split-BF16
+ * tcgen05 products with FP32 accumulators; FP64 for the log(h) terms, coefficient 0 of every
+ * expansion, M2M, L2L and the final per-target sums. */
+#define VFMM_MIXED 1
 
 #define VFMM_LIST_U 0 /* leaves: the leaf itself and every adjacent leaf (near field) */
 #define VFMM_LIST_V 1 /* boxes: children of parent's colleagues not adjacent to the box (M2L) */
@@ -178,10 +181,17 @@ int vfmm_tree_info(const vfmm_tree* tree, vfmm_tree_info_t* info);
 int vfmm_tree_export_boxes(const vfmm_tree* tree, int32_t* level, int32_t* ix, int32_t* iy);
 
 /* Host copy of one list in CSR form: ptr [n_boxes + 1], idx [len], cfg [len] (box
- * indices ascending within a row). cfg: U -> near configuration 0..32, V -> offset
- * index 0..39, W and X -> pattern index 0..19 (conventions in the tables section
- * of the design notes: same-level (dy+1)*3+(dx+1); coarse/fine patterns sorted by
- * (y, x)). Any output pointer may be NULL. Synchronous. */
+ * indices ascending within a row). D = (centre of the entry - centre of the row's box)
+ * / h, h the width of the row's box. cfg:
+ *  U -> 0..8 for a leaf of the same level, (dy + 1) * 3 + (dx + 1) with (dx, dy) = D;
+ *       9..20 for a leaf one level coarser, 9 + the position of 2D and 21..32 for a
+ *       leaf one level finer, 21 + the position of 4D in the 12-entry pattern
+ *       {(+-3, +-1), (+-1, +-3), (+-3, +-3)} sorted by (y, x);
+ *  V -> the position of D in the 40 offsets of [-3, 3]^2 outside [-1, 1]^2, row-major
+ *       (dy outer, dx inner, ascending);
+ *  W -> the position of 4D, X -> the position of 2D, in the 20-entry pattern
+ *       {(+-5, +-1), (+-1, +-5), (+-5, +-3), (+-3, +-5), (+-5, +-5)} sorted by (y, x).
+ * Any output pointer may be NULL. Synchronous. */
 int vfmm_tree_export_list(const vfmm_tree* tree, int32_t which, int32_t* ptr, int32_t* idx, int32_t* cfg);
 
 /* Node coordinates of every leaf, x_dev and y_dev [n_leaves * k * k]. */
@@ -233,17 +243,31 @@ int vfmm_workspace_size(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs
  * a third), all joined back into `stream` by events before the call returns; under stream
  * capture the fork becomes parallel branches of the graph (kernel nodes keep their priorities).
  * Errors: INVALID_ARG (k or p of ops differ from the tree's k, nrhs < 1), WORKSPACE
- * (workspace_bytes below vfmm_workspace_size), CUDA. */
+ * (workspace_bytes below vfmm_workspace_size), CUDA. A bounded device wait that runs out
+ * (VFMM_ERR_TIMEOUT) happens after this call has returned: it is recorded in a status word at
+ * the start of the workspace, cleared by each call, which vfmm_workspace_status reads once
+ * `stream` has been synchronised. */
 int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
                           double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev,
                           size_t workspace_bytes, void* stream);
 
 /* Same, from host buffers: copies f to the device, solves, copies u, u_x, u_y back
  * and synchronises `stream`. Host buffers should be pinned for full copy speed.
- * The workspace must be sized with with_io = 1. */
+ * The workspace must be sized with with_io = 1. Synchronous, so a bounded wait that ran
+ * out is returned as VFMM_ERR_TIMEOUT by this call itself. */
 int vfmm_volume_potential_host(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_host, int32_t nrhs,
                                double* u_host, double* ux_host, double* uy_host, void* workspace_dev,
                                size_t workspace_bytes, void* stream);
+
+/* Status of the last solve that used this workspace (no counterpart in the paper). The
+ * asynchronous calls (vfmm_volume_potential, graph replays, batch items, the allocation-free
+ * entry point) cannot return a timeout themselves; every bounded device wait that runs out
+ * records where in the status word at the start of the workspace that the solve used. Call
+ * this after synchronising the solve's stream: it copies the word to the host (synchronous) and
+ * returns VFMM_OK, or VFMM_ERR_TIMEOUT with the site in vfmm_last_error_detail; the results of
+ * such a solve are incomplete. workspace_dev = NULL reads the word of the allocation-free entry
+ * point's static scratch on the current device. Errors: CUDA. */
+int vfmm_workspace_status(const void* workspace_dev);
 
 /* v~: values at arbitrary points (Section 3.1: away from the collocation nodes the paper takes
  * the polynomial that interpolates the computed values on the leaf holding the point; Section
@@ -278,6 +302,8 @@ int vfmm_leaf_interpolate(const vfmm_tree* tree, int32_t n_fields, const double*
  *  - Sharing: all calls on a device use the same array, which keeps the last call's
  *    contents; calls that overlap on the GPU (different streams, or concurrent host
  *    threads) race with each other and must be serialised by the caller.
+ *  - Status: each call clears the array's status word once and every right-hand side's
+ *    solve adds to it; vfmm_workspace_status(NULL) reads it after `stream` is synchronised.
  * Inputs and outputs are as for vfmm_volume_potential. */
 int vfmm_volume_potential_noalloc(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
                                   double* u_dev, double* ux_dev, double* uy_dev, void* stream);

@@ -257,6 +257,13 @@ def volume_potential_host(tree: Tree, ops: Ops, f_host, out_host=None, ws=None, 
     return out_host
 
 
+def workspace_status(ws=None):
+    """Status of the last solve that used workspace ws (vfmm_workspace_status): raises VfmmError
+    (VFMM_ERR_TIMEOUT) when a bounded device wait of that solve ran out. Call it after synchronising
+    the solve's stream. ws = None reads the allocation-free entry point's static scratch."""
+    call("vfmm_workspace_status", ctypes.c_void_p(ws.data_ptr() if ws is not None else None))
+
+
 STAGES = ("s2m", "m2m", "down", "near", "l2t", "leaf", "near_tc", "s2m_tc", "m2l_tc", "s2l_tc", "far_tc")
 
 

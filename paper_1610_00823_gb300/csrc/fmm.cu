@@ -363,6 +363,14 @@ __global__ void __launch_bounds__(128) translate_kernel(int mode, const int32_t*
     }
 }
 
+// After a CTA has given up waiting for a bulk copy into its shared memory, thread 0 waits once
+// more, with a longer bound, for the copy to land (the other threads may leave): the CTA's shared
+// memory stays allocated, and no copy is left writing into it, until the copy has completed or
+// this second wait also runs out.
+__device__ __forceinline__ void settle_bulk_copy(uint32_t bar_a, const volatile int* never) {
+    if (threadIdx.x == 0) tc::mbar_wait(bar_a, 0, never, 1ll << 27);
+}
+
 // Same translations with the 4 position tables held in shared memory (one bulk copy per CTA),
 // persistent CTAs looping over the virtual boxes of the level: the table is read from L2 once
 // per CTA instead of once per multiply-add. Used when 4 P^2 complex values fit (P <= 58).
@@ -396,7 +404,8 @@ __global__ void __launch_bounds__(kTranslateThreads) translate_smem_kernel(int m
     const bool landed = tc::mbar_wait(bar_a, 0, &no_abort);
     if (!__syncthreads_and(landed)) {  // one decision for the whole CTA
         if (threadIdx.x == 0 && err) atomicExch(err, 5);
-        return;  // the copy itself completes on its own
+        settle_bulk_copy(bar_a, &no_abort);
+        return;
     }
     const int npair = (P + 1) / 2;
     for (int item = blockIdx.x; item < nbox * R; item += gridDim.x) {
@@ -661,6 +670,7 @@ __device__ bool load_tables(double2* sT, const double2* tab, int P, int* err) {
     const bool landed = tc::mbar_wait(bar_a, 0, &no_abort);
     if (!__syncthreads_and(landed)) {
         if (threadIdx.x == 0 && err) atomicExch(err, 5);
+        settle_bulk_copy(bar_a, &no_abort);
         return false;
     }
     return true;
@@ -949,6 +959,14 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
     double* dummy;
     const bool mixed = o.precision == VFMM_MIXED;
     const size_t R = mixed ? (size_t)nrhs : 1;
+    // the status word comes first in both forms, so that it can be read back knowing only the
+    // workspace address (vfmm_workspace_status)
+    int* err = nullptr;
+    {
+        double* e = nullptr;
+        take(&e, 1);
+        err = reinterpret_cast<int*>(e);
+    }
     take(w ? &w->Mexp : &dummy, (size_t)T.n_boxes * R * P2);
     take(w ? &w->Lexp : &dummy, (size_t)T.n_boxes * R * P2);
     {
@@ -975,8 +993,6 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
         if (w) w->mix.fmax = (unsigned long long*)p;
         take(&p, (R + 1) / 2);
         if (w) w->mix.Ef = (int*)p;
-        take(&p, 1);
-        if (w) w->mix.err = (int*)p;
         const size_t nlev = (size_t)T.depth + 1;
         take(&p, nl * mo->Rx);
         if (w) w->mix.s2m_out = (float2*)p;
@@ -1012,6 +1028,7 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
         w->mix = MixedWork();
         w->ps = &T.plans;
     }
+    if (w) w->mix.err = err;
     if (io) take(w ? &w->io : &dummy, (size_t)4 * nrhs * T.n_leaves * kk);
     else if (w) w->io = nullptr;
     if (w) w->bytes = off;
@@ -1492,19 +1509,36 @@ static int reset_status(const Workspace& w, cudaStream_t st) {
     return VFMM_OK;
 }
 
-// After a synchronised solve: a bounded device wait that expired shows up here.
-static int read_status(const Workspace& w) {
-    if (!w.mix.err) return VFMM_OK;
+// What a non-zero status word means: where the first bounded device wait that ran out was.
+static const char* status_site(int code) {
+    switch (code) {
+        case 1: return "a tensor-core producer waiting for a free stage";
+        case 2: return "the tensor-core MMA issuer waiting for operands";
+        case 3: return "a tensor-core epilogue waiting for its accumulators";
+        case 4: return "the tensor-core MMA issuer waiting for drained accumulators";
+        case 5: return "a translation-table copy into shared memory";
+        case 6: return "a grid barrier of a persistent tree pass";
+        case 7: return "the failure-path self-test's wait on an mbarrier nothing arrives on (expected)";
+        default: return "an unknown site";
+    }
+}
+
+// Reads the status word at `word` (device) after the solve that wrote it has finished.
+int vfmm::read_status_word(const int* word) {
+    if (!word) return VFMM_OK;
     int h = 0;
-    VFMM_CUDA(cudaMemcpy(&h, w.mix.err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (h) return fail(VFMM_ERR_TIMEOUT, "a bounded wait in the tensor-core near field expired (code " +
-                                             std::to_string(h) + ")");
+    VFMM_CUDA(cudaMemcpy(&h, word, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return fail(VFMM_ERR_TIMEOUT, std::string("a bounded wait ran out: ") + status_site(h) +
+                                             " (code " + std::to_string(h) + ")");
     return VFMM_OK;
 }
 
+// After a synchronised solve: a bounded device wait that expired shows up here.
+static int read_status(const Workspace& w) { return read_status_word(w.mix.err); }
+
 int vfmm::volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,
                            double* u_dev, double* ux_dev, double* uy_dev, void* workspace_dev, size_t workspace_bytes,
-                           cudaStream_t st, bool fork) {
+                           cudaStream_t st, bool fork, bool reset) {
     VFMM_CHECK(check_solve_args(tree, ops, nrhs));
     if (!f_dev || !u_dev || !ux_dev || !uy_dev || !workspace_dev) return fail(VFMM_ERR_INVALID_ARG, "null buffer");
     Workspace w;
@@ -1512,8 +1546,18 @@ int vfmm::volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const dou
     VFMM_CHECK(layout(tree->t, *ops, nrhs, false, &w, (char*)workspace_dev, &need));
     if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace too small");
     w.fork = fork;
-    VFMM_CHECK(reset_status(w, st));
+    if (reset) VFMM_CHECK(reset_status(w, st));
     return solve_all(tree->t, *ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, w, st);
+}
+
+extern "C" int vfmm_workspace_status(const void* workspace_dev) {
+    if (!workspace_dev) {
+        // the allocation-free entry point's scratch on the current device
+        const int* word = nullptr;
+        VFMM_CHECK(noalloc_status_word(&word));
+        return read_status_word(word);
+    }
+    return read_status_word(static_cast<const int*>(workspace_dev));
 }
 
 extern "C" int vfmm_volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs,

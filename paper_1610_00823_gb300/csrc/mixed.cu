@@ -172,7 +172,7 @@ __device__ __forceinline__ void issue_unit(uint32_t tmem, uint64_t ad0, uint64_t
 // sub-partition, which leaves each thread up to 168 registers.
 __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ unsigned char dsm[];
-    __shared__ __align__(8) uint64_t bars[2 * kStages + 2];
+    __shared__ __align__(8) uint64_t bars[2 * kStages + 3];
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_flag;
     __shared__ int32_t s_src[kTileM];
@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
     const uint32_t empty0 = tc::smem_u32(&bars[kStages]);
     const uint32_t acc_full = tc::smem_u32(&bars[2 * kStages]);
     const uint32_t acc_empty = tc::smem_u32(&bars[2 * kStages + 1]);
+    const uint32_t mma_done = tc::smem_u32(&bars[2 * kStages + 2]);  // used only after an abort
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             tc::mbar_init(full0 + 8 * s, kProducerThreads + 1);  // cp.async producers + the TMA issuer
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
         }
         tc::mbar_init(acc_full, 1);
         tc::mbar_init(acc_empty, kEpilogueThreads);
+        tc::mbar_init(mma_done, 1);
         abort_flag = 0;
         p_abort = 0;
         tc::mbar_fence_init();
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
     const int U = (int)((Ug * (sp + 1)) / a.split) - ubeg;
     const int DU = a.drain_every * nkb;  // units summed in TMEM between two drains
     const int r0 = rc * (tr ? kTileM : N);  // first table row of this CTA's tile
+    int issued = 0;  // producers: units whose copies were started
 
     if (warp >= kEpilogueWarps && warp < kMmaWarp) {
         // ------------------------------------------------ producers: table tile by TMA (one thread),
@@ -268,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
             }
             // the stage's full barrier gets this thread's arrival when its copies have landed
             tc::cp_async_mbar_arrive(full0 + 8 * s);
+            issued = u + 1;
         }
         tc::cp_async_wait_all();
         } else if (warp == kMmaWarp) {
@@ -374,6 +378,22 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
     }
     tc::tc_fence_before();
     __syncthreads();
+    if (abort_flag) {
+        // after an abort (a bounded wait ran out somewhere): wait, with a longer bound, for the work
+        // still in flight, so that no copy writes this CTA's shared memory and no MMA its
+        // accumulators once they are released. Units may have been started that no MMA consumed
+        // (their table tiles come by TMA; the cp.async rows are complete after cp.async.wait_all),
+        // and MMAs issued before the abort may still run.
+        const volatile int never = 0;
+        if (tid == kEpilogueThreads)
+            for (int u = issued - 2; u < issued; ++u)
+                if (u >= 0) tc::mbar_wait(full0 + 8 * (u & 1), (u >> 1) & 1, &never, 1ll << 27);
+        if (warp == kMmaWarp && lane == 0) {
+            tc::umma_commit(mma_done);
+            tc::mbar_wait(mma_done, 0, &never, 1ll << 27);
+        }
+        __syncthreads();
+    }
     if (warp == kMmaWarp) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, kTmemCols);

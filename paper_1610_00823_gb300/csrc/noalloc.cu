@@ -42,6 +42,14 @@ static int scratch_address(void** out) {
     return VFMM_OK;
 }
 
+// The solve keeps its status word at the start of its workspace, here the start of the scratch.
+int noalloc_status_word(const int** word) {
+    void* scratch = nullptr;
+    VFMM_CHECK(scratch_address(&scratch));
+    *word = static_cast<const int*>(scratch);
+    return VFMM_OK;
+}
+
 }  // namespace vfmm
 
 using namespace vfmm;
@@ -64,12 +72,14 @@ extern "C" int vfmm_volume_potential_noalloc(const vfmm_tree* tree, const vfmm_o
     void* scratch = nullptr;
     VFMM_CHECK(scratch_address(&scratch));
     // Everything runs on `stream` alone (no second stream is created). Nothing in the scratch has
-    // to start at zero: the solve writes every
+    // to start at zero but the status word at its start, cleared here once for the whole call (a
+    // bounded wait that ran out for any right-hand side stays reported): the solve writes every
     // expansion, partial product and far value before reading it, and clears the
     // local expansions of levels 0 and 1 (and its barrier counters) itself on every call.
+    VFMM_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int), (cudaStream_t)stream));
     const size_t n = (size_t)tree->t.n_leaves * ops->k * ops->k;
     for (int r = 0; r < nrhs; ++r)
         VFMM_CHECK(volume_potential(tree, ops, f_dev + r * n, 1, u_dev + r * n, ux_dev + r * n, uy_dev + r * n,
-                                    scratch, kStaticScratchBytes, (cudaStream_t)stream, false));
+                                    scratch, kStaticScratchBytes, (cudaStream_t)stream, false, false));
     return VFMM_OK;
 }

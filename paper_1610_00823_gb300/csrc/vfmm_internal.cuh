@@ -246,10 +246,17 @@ void free_plan_set(PlanSet* ps);
 // Plans for R folded right-hand sides (R = 1: the tree's own set); builds and caches on first use.
 int plans_for(const DeviceTree& T, int R, const PlanSet** out);
 int build_near_tiles(DeviceTree* t);
-// vfmm_volume_potential with a flag: fork = false keeps every launch on `st` (no second stream).
+// vfmm_volume_potential with flags: fork = false keeps every launch on `st` (no second stream);
+// reset = false leaves the workspace's status word as it is (a caller solving several right-hand
+// sides one after another clears it once, so that a timeout in an early one is not lost).
 int volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, int32_t nrhs, double* u_dev,
                      double* ux_dev, double* uy_dev, void* workspace_dev, size_t workspace_bytes, cudaStream_t st,
-                     bool fork);
+                     bool fork, bool reset = true);
+// Reads a status word (device address) after the solve that wrote it has finished: VFMM_OK, or
+// VFMM_ERR_TIMEOUT naming the bounded wait that ran out.
+int read_status_word(const int* word);
+// Device address of the allocation-free scratch's status word on the current device.
+int noalloc_status_word(const int** word);
 
 }  // namespace vfmm
 

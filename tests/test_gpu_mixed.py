@@ -236,3 +236,28 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     got = v.volume_potential(gt, v.ops_create(8, 20, v.MIXED), f)
     for q in range(3):
         assert rel(got[q].cpu().numpy(), ref[q].cpu().numpy()) < TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_workspace_status_reports_a_recorded_timeout(precision):
+    """The asynchronous solve records a bounded wait that ran out in the status word at the start of
+    its workspace; vfmm_workspace_status reads it after synchronisation. No wait is made to run out
+    here: the word is written from the host side (as a kernel would), read back as TIMEOUT, and the
+    next solve clears it again."""
+    from paper_1610_00823_gb300._lib import VfmmError
+    src = W.narrow_gaussians(5, n=3, sigma=0.04)
+    gt = v.tree_build(0.0, 0.0, 1.0, 8, src, 1e-6, 7)
+    f = v.source_sample(gt, src)
+    ops = v.ops_create(8, 20, v.MIXED if precision == "mixed" else v.FP64)
+    ws = workspace(gt, ops, 1)
+    v.volume_potential(gt, ops, f, ws=ws)
+    torch.cuda.synchronize()
+    v.workspace_status(ws)  # a normal solve: no timeout recorded
+    ws[:4].view(torch.int32).fill_(6)  # what a grid barrier that ran out records
+    torch.cuda.synchronize()
+    with pytest.raises(VfmmError) as e:
+        v.workspace_status(ws)
+    assert e.value.code == -5 and "grid barrier" in str(e.value)
+    v.volume_potential(gt, ops, f, ws=ws)  # every call clears the word
+    torch.cuda.synchronize()
+    v.workspace_status(ws)
