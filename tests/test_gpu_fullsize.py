@@ -6,7 +6,7 @@
 * The mixed result against the FP64 result on every target.
 
 Bar: 1e-10 relative L-infinity (u, u_x, u_y), the method's accuracy target; FP64 is held to
-1e-12. Normalisation: the largest |value| of the oracle over the sampled leaves.
+1e-13. Normalisation: the largest |value| of the oracle over the sampled leaves.
 """
 import numpy as np
 import pytest
@@ -24,7 +24,7 @@ if not torch.cuda.is_available():
 import paper_1610_00823_gb300 as v  # noqa: E402
 from paper_1610_00823_gb300.api import SolveGraph, workspace  # noqa: E402
 
-TOL = {"fp64": 1e-12, "mixed": 1e-10}
+TOL = {"fp64": 1e-13, "mixed": 1e-10}
 WORKLOADS = {"adaptive_gauss20": W.adaptive_gauss20, "kinked": W.kinked}
 _cache = {}
 
