@@ -614,38 +614,39 @@ __global__ void down_mixed_kernel(DownArgs d) {
 }
 
 // ---------------------------------------------------------------- persistent tree passes
-// One cooperative launch walks all levels: CTAs take groups of 128 threads per virtual box, the
-// 4 position tables sit in shared memory for the whole pass, and a bounded grid barrier separates
-// the levels. Data written by other CTAs in an earlier level are read through L2 (ld.global.cg).
-constexpr int kPassGroups = 4;                  // 128-thread groups per CTA
-constexpr int kPassThreads = 128 * kPassGroups;
+// One cooperative launch walks all levels: the translations are cut into one-warp units (a row pair
+// of one virtual box) dealt over the warps of every CTA, and the 4 position tables sit in shared
+// memory for the whole pass. There is no barrier between levels: a unit waits (bounded) only for
+// the expansions it reads, through per-box readiness counters, so a box starts as soon as its
+// children (M2M) or its parent (L2L) are done. Every unit's inputs are produced by units that come
+// earlier in the global unit order, and each warp takes its units in that order, so the earliest
+// unfinished unit can always proceed (all CTAs are resident: cooperative launch). Data written by
+// other CTAs are read through L2 (ld.global.cg).
+constexpr int kPassThreads = 512;
 
-// Grid barrier: every CTA adds one to *count and waits (bounded) for `target`.
-__device__ bool grid_sync(unsigned int* count, unsigned int target, int* err) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(count, 1u);
-        int good = 1;
-        for (long long it = 0;; ++it) {
-            if (*(volatile unsigned int*)count >= target) break;
-            if (it > (1ll << 24)) {
-                good = 0;
-                if (err) atomicExch(err, 6);
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
+// Readiness counters of the dataflow tree passes: ready[vb] counts the units that have written
+// their part of virtual box vb's expansion (M2M: the box's own multipole; L2L: the box's local), and
+// npair = (P + 1) / 2 units complete it. A producer publishes with a release add after its writes,
+// a consumer polls with acquire loads before reading the expansion through L2.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void group_sync(int group) {
-    asm volatile("bar.sync %0, 128;" ::"r"(1 + group) : "memory");
+// Waits (bounded) until *flag >= need. Gives up, recording code 6 in the status word, when the
+// bound runs out; gives up at once when another wait already did (the status word is set).
+__device__ bool wait_ready(const unsigned* flag, unsigned need, int* err) {
+    for (long long it = 0; it < (1ll << 22); ++it) {
+        if (ld_acquire_u32(flag) >= need) return true;
+        if ((it & 63) == 63 && *(volatile int*)err) return false;
+        __nanosleep(32);
+    }
+    atomicExch(err, 6);
+    return false;
 }
 
 // Loads the 4 position tables into shared memory (bulk copy); one decision for the whole CTA.
@@ -676,17 +677,50 @@ __device__ bool load_tables(double2* sT, const double2* tab, int P, int* err) {
     return true;
 }
 
-// Triangular translation of one virtual box by one 128-thread group (see translate_kernel):
-// mode 0 = M2M (in: 4 child multipoles), 1 = L2L (in: parent local); s_out[pos][o] results.
-__device__ __forceinline__ void translate_group(int mode, const double2* sT, const double2* s_in, double2* s_out,
-                                                int P, int gt) {
-    const int npair = (P + 1) / 2;
-    for (int task = gt; task < 4 * npair; task += 128) {
-        const int pos = task / npair, j = task - pos * npair;
-        const double2* M = sT + pos * P * P;
-        const double2* x = mode == 0 ? s_in + pos * P : s_in;
-        translate_pair(mode, M, x, P, j, s_out + pos * P);
+// One output row pair (j, P-1-j) of one virtual box's four child-position translations, computed
+// by one warp: lane (pos, ks) = (lane / 8, lane % 8) takes position pos and the inputs
+// n = ks, ks + 8, ... of its triangular ranges (M2M row o takes n <= o, L2L row m takes n >= m), so
+// the 4 (P + 1) complex multiply-adds of a row pair spread over the 32 lanes. Shuffles then sum
+// the 8 input slices of each position, and for M2M (mode 0) the four positions as well, in a
+// fixed order (the results are deterministic). Tables [pos][in][out] complex in shared memory: the
+// 8 lanes of a quarter warp read rows n one apart (stride P complex = 4P banks), which never
+// share a bank. Inputs: mode 0, child pos at x + pos * xs; mode 1, the parent local at x.
+// Returns the row-a and row-b sums: mode 0 in every lane, summed over the positions; mode 1 in
+// every lane of position pos, for that position.
+__device__ __forceinline__ void translate_warp(int mode, const double2* __restrict__ sT, const double2* x,
+                                               size_t xs, int P, int j, int lane, double2& ra, double2& rb) {
+    const int pos = lane >> 3, ks = lane & 7;
+    const int oa = j, ob = P - 1 - j;  // oa <= ob
+    const double2* M = sT + (size_t)pos * P * P;
+    const double2* xp = mode == 0 ? x + pos * xs : x;
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int n = ks + 8 * i;
+        if (n >= P || (mode == 0 && n > ob)) break;
+        const double2 v = __ldcg(xp + n);
+        if (mode == 0 ? n <= oa : n >= oa) {
+            const double2 m = M[(size_t)n * P + oa];
+            ar = fma(m.x, v.x, fma(-m.y, v.y, ar));
+            ai = fma(m.x, v.y, fma(m.y, v.x, ai));
+        }
+        if (ob != oa && (mode == 0 || n >= ob)) {
+            const double2 m = M[(size_t)n * P + ob];
+            br = fma(m.x, v.x, fma(-m.y, v.y, br));
+            bi = fma(m.x, v.y, fma(m.y, v.x, bi));
+        }
     }
+    const int lim = mode == 0 ? 32 : 8;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        if (off >= lim) break;
+        ar += __shfl_xor_sync(0xffffffffu, ar, off);
+        ai += __shfl_xor_sync(0xffffffffu, ai, off);
+        br += __shfl_xor_sync(0xffffffffu, br, off);
+        bi += __shfl_xor_sync(0xffffffffu, bi, off);
+    }
+    ra = make_double2(ar, ai);
+    rb = make_double2(br, bi);
 }
 
 struct PassArgs {
@@ -697,83 +731,104 @@ struct PassArgs {
     const int32_t* child0;
     const double2* tab;
     double2* ex;           // Mexp (upward) or Lexp (downward), [n_boxes * R][P] complex
-    unsigned int* count;   // grid-barrier counter, zero at launch
+    const int32_t* parent;
+    unsigned int* ready;   // [n_boxes * R] readiness counters, zero at launch
     int* err;
 };
 
-// All M2M levels, finest parents first.
+// The work of one level is a list of (virtual box, row pair) units dealt to warps striped over the
+// CTAs (warp w of CTA c is slot w * gridDim.x + c), so that even a level of a few boxes spreads over
+// many SMs and all four sub-partitions of each: this part retires about 2 FP64 FMAs per clock per
+// SM, so a level takes the FP64 work of its busiest sub-partition.
+constexpr int kPassWarps = kPassThreads / 32;
+
+// All M2M levels, finest parents first (the global unit order).
 __global__ void __launch_bounds__(kPassThreads, 1) upward_pass_kernel(PassArgs a) {
     extern __shared__ __align__(128) unsigned char pass_raw[];
     const int P = a.P, R = a.R;
     double2* sT = reinterpret_cast<double2*>(pass_raw);
-    const int group = threadIdx.x >> 7, gt = threadIdx.x & 127;
-    double2* s_in = sT + 4 * P * P + group * 8 * P;
-    double2* s_out = s_in + 4 * P;
     if (!load_tables(sT, a.tab, P, a.err)) return;
-    unsigned int target = 0;
-    for (int l = a.depth - 1; l >= 2; --l) {
-        const int nb0 = a.nonleaf_start[l], nbox = a.nonleaf_start[l + 1] - nb0;
-        for (int item = group * gridDim.x + blockIdx.x; item < nbox * R; item += gridDim.x * kPassGroups) {
-            const int bi = item / R, r = item - bi * R;
-            const int b = a.nonleaf[nb0 + bi], c0 = a.child0[b];
-            for (int q = gt; q < 4 * P; q += 128) s_in[q] = __ldcg(&a.ex[((size_t)(c0 + q / P) * R + r) * P + q % P]);
-            group_sync(group);
-            translate_group(0, sT, s_in, s_out, P, gt);
-            group_sync(group);
-            for (int o = gt; o < P; o += 128) {
-                const double2 a0 = s_out[o], a1 = s_out[P + o], a2 = s_out[2 * P + o], a3 = s_out[3 * P + o];
-                a.ex[((size_t)b * R + r) * P + o] =
-                    make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
-            }
-            group_sync(group);
+    const int lane = threadIdx.x & 31;
+    const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassWarps;
+    const unsigned npair = (unsigned)(P + 1) / 2;
+    int l = a.depth - 1, lbase = 0;
+    int lunits = l >= 2 ? (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * (int)npair : 0;
+    for (int u = slot;; u += nslots) {
+        while (l >= 2 && u >= lbase + lunits) {
+            lbase += lunits;
+            if (--l >= 2) lunits = (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * (int)npair;
         }
-        target += gridDim.x;
-        if (!grid_sync(a.count, target, a.err)) return;
+        if (l < 2) break;
+        const int lu = u - lbase;
+        const int vi = lu / (int)npair, j = lu - vi * (int)npair;
+        const int bi = vi / R, r = vi - bi * R;
+        const int b = a.nonleaf[a.nonleaf_start[l] + bi], c0 = a.child0[b];
+        // the non-leaf children's multipoles must be complete (leaf multipoles come from S2M)
+        bool ok = true;
+        if (lane < 4 && a.child0[c0 + lane] >= 0)
+            ok = wait_ready(a.ready + (size_t)(c0 + lane) * R + r, npair, a.err);
+        if (!__all_sync(0xffffffffu, ok)) return;
+        __syncwarp();
+        double2 ra, rb;
+        // the four children are consecutive boxes: position pos is virtual box (c0 + pos) R + r
+        translate_warp(0, sT, a.ex + ((size_t)c0 * R + r) * P, (size_t)R * P, P, j, lane, ra, rb);
+        if (lane == 0) {
+            double2* out = a.ex + ((size_t)b * R + r) * P;
+            out[j] = ra;
+            if (j != P - 1 - j) out[P - 1 - j] = rb;
+            red_release_add_u32(a.ready + (size_t)b * R + r, 1u);
+        }
     }
 }
 
-// Mixed form, all downward levels: level 2 boxes combine their M2L/S2L terms; below, each
-// non-leaf parent's local is shifted to its 4 children (L2L) and each child's terms are added.
+// Mixed form, all downward levels: level 2 boxes combine their M2L/S2L terms (one warp unit per
+// virtual box); below, each non-leaf parent's local is shifted to its 4 children (L2L) and each
+// child's terms are added (row-pair units).
 __global__ void __launch_bounds__(kPassThreads, 1) downward_pass_kernel(PassArgs a, DownArgs d) {
     extern __shared__ __align__(128) unsigned char pass_raw[];
     const int P = a.P, R = a.R;
     double2* sT = reinterpret_cast<double2*>(pass_raw);
-    const int group = threadIdx.x >> 7, gt = threadIdx.x & 127;
-    double2* s_in = sT + 4 * P * P + group * 8 * P;
-    double2* s_out = s_in + 4 * P;
     if (!load_tables(sT, a.tab, P, a.err)) return;
-    // level 2: no parent term
-    {
-        const int b0 = a.level_start[2], n2 = a.level_start[3] - b0;
-        const int64_t total = (int64_t)n2 * R * P;
-        for (int64_t q = (int64_t)blockIdx.x * kPassThreads + threadIdx.x; q < total;
-             q += (int64_t)gridDim.x * kPassThreads) {
-            const int t = (int)(q % P);
-            const int64_t vb = (int64_t)b0 * R + q / P;
+    const int lane = threadIdx.x & 31, pos = lane >> 3;
+    const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassWarps;
+    const unsigned npair = (unsigned)(P + 1) / 2;
+    const int b2 = a.level_start[2], n2 = (a.level_start[3] - b2) * R;  // level-2 units
+    int l = 3, lbase = n2;
+    int lunits = l <= a.depth ? (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * (int)npair : 0;
+    for (int u = slot;; u += nslots) {
+        if (u < n2) {
+            // level 2: no parent term; the whole local at once, published as npair contributions
+            const int64_t vb = (int64_t)b2 * R + u;
             const int b = (int)(vb / R), r = (int)(vb % R);
-            const double2 v = combine_local(d, 2, b, r, t, 0.0, 0.0);
-            a.ex[(size_t)vb * P + t] = v;
+            for (int t = lane; t < P; t += 32) a.ex[(size_t)vb * P + t] = combine_local(d, 2, b, r, t, 0.0, 0.0);
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) red_release_add_u32(a.ready + vb, npair);
+            continue;
         }
-    }
-    unsigned int target = gridDim.x;
-    if (!grid_sync(a.count, target, a.err)) return;
-    for (int l = 3; l <= a.depth; ++l) {
-        const int nb0 = a.nonleaf_start[l - 1], nbox = a.nonleaf_start[l] - nb0;
-        for (int item = group * gridDim.x + blockIdx.x; item < nbox * R; item += gridDim.x * kPassGroups) {
-            const int bi = item / R, r = item - bi * R;
-            const int b = a.nonleaf[nb0 + bi], c0 = a.child0[b];
-            for (int q = gt; q < P; q += 128) s_in[q] = __ldcg(&a.ex[((size_t)b * R + r) * P + q]);
-            group_sync(group);
-            translate_group(1, sT, s_in, s_out, P, gt);
-            group_sync(group);
-            for (int q = gt; q < 4 * P; q += 128) {
-                const int c = c0 + q / P, t = q % P;
-                a.ex[((size_t)c * R + r) * P + t] = combine_local(d, l, c, r, t, s_out[q].x, s_out[q].y);
-            }
-            group_sync(group);
+        while (l <= a.depth && u >= lbase + lunits) {
+            lbase += lunits;
+            if (++l <= a.depth) lunits = (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * (int)npair;
         }
-        target += gridDim.x;
-        if (!grid_sync(a.count, target, a.err)) return;
+        if (l > a.depth) break;
+        const int lu = u - lbase;
+        const int vi = lu / (int)npair, j = lu - vi * (int)npair;
+        const int bi = vi / R, r = vi - bi * R;
+        const int b = a.nonleaf[a.nonleaf_start[l - 1] + bi], c0 = a.child0[b];
+        // the parent's local must be complete
+        bool ok = true;
+        if (lane == 0) ok = wait_ready(a.ready + (size_t)b * R + r, npair, a.err);
+        if (!__all_sync(0xffffffffu, ok)) return;
+        __syncwarp();
+        double2 ra, rb;
+        translate_warp(1, sT, a.ex + ((size_t)b * R + r) * P, 0, P, j, lane, ra, rb);
+        if ((lane & 7) == 0) {  // one lane per child position: add the child's own terms
+            const int c = c0 + pos, mb = P - 1 - j;
+            double2* out = a.ex + ((size_t)c * R + r) * P;
+            out[j] = combine_local(d, l, c, r, j, ra.x, ra.y);
+            if (j != mb) out[mb] = combine_local(d, l, c, r, mb, rb.x, rb.y);
+            red_release_add_u32(a.ready + (size_t)c * R + r, 1u);
+        }
     }
 }
 
@@ -934,7 +989,7 @@ struct Workspace {
     double* vslab;      // FP64 form: per V entry M2L rows
     double* xslab;      // FP64 form: per X entry S2L rows
     const PlanSet* ps;  // split-contraction plans for the folded right-hand sides (mixed form)
-    unsigned int* gbar; // [2] grid-barrier counters of the persistent tree passes
+    unsigned int* ready; // [2][n_boxes * R] readiness counters of the persistent tree passes
     double* Mexp;
     double* Lexp;
     double* slab;
@@ -971,8 +1026,8 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
     take(w ? &w->Lexp : &dummy, (size_t)T.n_boxes * R * P2);
     {
         double* g = nullptr;
-        take(&g, 1);
-        if (w) w->gbar = reinterpret_cast<unsigned int*>(g);
+        take(&g, (2 * (size_t)T.n_boxes * R + 1) / 2);
+        if (w) w->ready = reinterpret_cast<unsigned int*>(g);
     }
     take(w ? &w->slab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
     take(w ? &w->far : &dummy, mixed ? 1 : (size_t)T.n_leaves * 3 * kk);
@@ -1141,7 +1196,7 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
 // Persistent passes (one cooperative launch for all levels) when every level is small enough that
 // per-level launches would mostly wait on launch latency; larger levels keep one launch per level.
 static bool use_passes(const DeviceTree& T, int R, int P) {
-    const size_t smem = (size_t)(4 * P * P + kPassGroups * 8 * P) * sizeof(double2);
+    const size_t smem = (size_t)(4 * P * P) * sizeof(double2);
     if (smem > 200 * 1024 || T.depth < 3) return false;
     int widest = 0;
     for (int l = 1; l <= T.depth; ++l) widest = std::max(widest, T.nonleaf_start[l + 1] - T.nonleaf_start[l]);
@@ -1150,7 +1205,7 @@ static bool use_passes(const DeviceTree& T, int R, int P) {
 
 template <typename... Args>
 static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, cudaStream_t st, Args... args) {
-    const size_t smem = (size_t)(4 * P * P + kPassGroups * 8 * P) * sizeof(double2);
+    const size_t smem = (size_t)(4 * P * P) * sizeof(double2);
     static thread_local int attr_dev[2] = {-1, -1};
     const int slot = (void*)kernel == (void*)upward_pass_kernel ? 0 : 1;
     int dev = 0;
@@ -1162,8 +1217,10 @@ static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, 
     int per_sm = 0;
     VFMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPassThreads, smem));
     if (per_sm < 1) return fail(VFMM_ERR_INTERNAL, "tree pass kernel does not fit on an SM");
-    // items go to group 0 of every CTA first, so one CTA per item up to one CTA per SM
-    const int grid = std::max(1, std::min(per_sm * sm_count(), widest_items));
+    // units (virtual box, row pair) are striped over the CTAs: enough CTAs that the widest level
+    // has at most about four units per sub-partition, up to one CTA per SM
+    const int units = widest_items * ((P + 1) / 2);
+    const int grid = std::max(1, std::min(per_sm * sm_count(), (units + 15) / 16));
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeCooperative;
     attr.val.cooperative = 1;
@@ -1295,7 +1352,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
     int widest = 0;
     for (int l = 1; l <= T.depth; ++l) widest = std::max(widest, T.nonleaf_start[l + 1] - T.nonleaf_start[l]);
     if (passes) {
-        VFMM_CUDA(cudaMemsetAsync(w.gbar, 0, 2 * sizeof(unsigned int), st));
+        VFMM_CUDA(cudaMemsetAsync(w.ready, 0, 2 * (size_t)T.n_boxes * R * sizeof(unsigned int), st));
         PassArgs pa;
         pa.depth = T.depth;
         pa.R = R;
@@ -1306,7 +1363,8 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.child0 = T.child0;
         pa.tab = reinterpret_cast<const double2*>(o.m2m_t);
         pa.ex = reinterpret_cast<double2*>(w.Mexp);
-        pa.count = w.gbar;
+        pa.parent = T.parent;
+        pa.ready = w.ready;
         pa.err = w.mix.err;
         VFMM_CHECK(launch_pass(upward_pass_kernel, R, P, widest * R, st, pa));
         ++launches;
@@ -1385,7 +1443,8 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.child0 = T.child0;
         pa.tab = reinterpret_cast<const double2*>(o.l2l_t);
         pa.ex = reinterpret_cast<double2*>(w.Lexp);
-        pa.count = w.gbar + 1;
+        pa.parent = T.parent;
+        pa.ready = w.ready + (size_t)T.n_boxes * R;
         pa.err = w.mix.err;
         VFMM_CHECK(launch_pass(downward_pass_kernel, R, P, std::max(widest * R, 16 * R), st, pa, d));
         ++launches;
@@ -1517,7 +1576,7 @@ static const char* status_site(int code) {
         case 3: return "a tensor-core epilogue waiting for its accumulators";
         case 4: return "the tensor-core MMA issuer waiting for drained accumulators";
         case 5: return "a translation-table copy into shared memory";
-        case 6: return "a grid barrier of a persistent tree pass";
+        case 6: return "a persistent tree pass waiting for an expansion another unit writes";
         case 7: return "the failure-path self-test's wait on an mbarrier nothing arrives on (expected)";
         default: return "an unknown site";
     }

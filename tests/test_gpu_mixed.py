@@ -253,11 +253,11 @@ def test_workspace_status_reports_a_recorded_timeout(precision):
     v.volume_potential(gt, ops, f, ws=ws)
     torch.cuda.synchronize()
     v.workspace_status(ws)  # a normal solve: no timeout recorded
-    ws[:4].view(torch.int32).fill_(6)  # what a grid barrier that ran out records
+    ws[:4].view(torch.int32).fill_(6)  # what a persistent tree pass records when a wait runs out
     torch.cuda.synchronize()
     with pytest.raises(VfmmError) as e:
         v.workspace_status(ws)
-    assert e.value.code == -5 and "grid barrier" in str(e.value)
+    assert e.value.code == -5 and "persistent tree pass" in str(e.value)
     v.volume_potential(gt, ops, f, ws=ws)  # every call clears the word
     torch.cuda.synchronize()
     v.workspace_status(ws)
