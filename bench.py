@@ -151,27 +151,65 @@ def pick_sample(ot, L, ops, F, budget_s, rng):
     return np.sort(rng.choice(n_leaves, size=m, replace=False))
 
 
+# The oracle over all host cores: a pool of spawned worker processes (spawned, since the GPU may
+# already be in use by this process), each building the oracle's tree, lists and tables once; one
+# step hands every worker an equal share of the sampled leaves, and each worker runs the full upward
+# pass plus the leaf pass of its share (the oracle as it stands, one process per core).
+_POOL_ORACLE = None
+
+
+def _pool_init(wl, rule):
+    global _POOL_ORACLE
+    _POOL_ORACLE = oracle_setup(wl, rule)
+
+
+def _pool_step(leaves):
+    ot, L, ops, F = _POOL_ORACLE
+    return oracle_sample_step(ot, L, ops, F, leaves)[0]
+
+
+class OraclePool:
+    def __init__(self, wl, rule, cores=None):
+        import multiprocessing as mp
+        self.cores = int(cores or os.cpu_count() or 1)
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_pool_init, initargs=(wl, rule))
+
+    def step(self, leaves):
+        """Wall time of one pass over `leaves`, split evenly over the workers."""
+        chunks = [c for c in np.array_split(np.asarray(leaves), self.cores) if len(c)]
+        t0 = time.perf_counter()
+        self.pool.map(_pool_step, chunks, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def run_reference(args, wl):
     ot, L, ops, F = oracle_setup(wl, args.refine)
+    pool = OraclePool(wl, args.refine)
     rng = np.random.default_rng(7)
+    # a step of about 120 s / (steps + warmup) on one core, spread over all cores
     leaves = pick_sample(ot, L, ops, F, budget_s=max(2.0, 120.0 / max(1, args.steps + args.warmup)), rng=rng)
     kk = wl.k * wl.k
     times = []
     for i in range(args.warmup + args.steps):
-        dt, _ = oracle_sample_step(ot, L, ops, F, leaves)
+        dt = pool.step(leaves)
         if i >= args.warmup:
             times.append(dt)
+    pool.close()
     ms = 1e3 * statistics.mean(times)
     value = len(leaves) * kk / (ms / 1e3)
-    sample = "%d of %d leaves (%d targets) per step, full upward pass included" % (
-        len(leaves), ot.n_leaves, len(leaves) * kk)
+    sample = ("%d of %d leaves (%d targets) per step split over %d worker processes, each with the full "
+              "upward pass" % (len(leaves), ot.n_leaves, len(leaves) * kk, pool.cores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "n_leaves": ot.n_leaves, "n_targets": ot.n_leaves * kk, "k": wl.k,
                        "p": wl.p, "parallelism": "replicas" if args.gpus > 1 else "single GPU",
                        "refine": args.refine},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -191,6 +229,14 @@ def cpu_baseline(wl, gpu_u, budget_s=15.0, rule="tail"):
         runs.append(oracle_sample_step(ot, L, ops, F, leaves)[0])
     dt = statistics.mean(runs)
     kk = wl.k * wl.k
+    # the same sample over all host cores, repeated up to about 10 s
+    pool = OraclePool(wl, rule)
+    pool.step(leaves)  # warm-up: every worker has built its oracle
+    pruns = []
+    while sum(pruns) < 10.0 and len(pruns) < 20:
+        pruns.append(pool.step(leaves))
+    pool.close()
+    pdt = statistics.mean(pruns)
     errs = None
     if gpu_u:
         errs = {}
@@ -201,10 +247,14 @@ def cpu_baseline(wl, gpu_u, budget_s=15.0, rule="tail"):
             for q, nm in enumerate(("u", "u_x", "u_y")):
                 got = res[q].reshape(ot.n_leaves, kk)[leaves]
                 errs[form][nm] = float(np.max(np.abs(got - ref[q])) / np.max(np.abs(ref[q])))
-    return {"value": len(leaves) * kk / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d of %d leaves (%d targets), full upward pass included, %.1f s per run, mean of %d runs; "
-                      "oracle setup %.1f s untimed" % (len(leaves), ot.n_leaves, len(leaves) * kk, dt, len(runs),
-                                                         setup_s)}, errs
+    one = {"value": len(leaves) * kk / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d of %d leaves (%d targets), full upward pass included, %.1f s per run, mean of %d runs; "
+                     "oracle setup %.1f s untimed" % (len(leaves), ot.n_leaves, len(leaves) * kk, dt, len(runs),
+                                                        setup_s)}
+    allc = {"value": len(leaves) * kk / pdt, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": "the same %d leaves split over %d worker processes (one per host core), each with the full "
+                      "upward pass, %.2f s per run, mean of %d runs" % (len(leaves), pool.cores, pdt, len(pruns))}
+    return allc, one, errs
 
 
 # ----------------------------------------------------------------------------- batched problems
@@ -401,6 +451,59 @@ def run_batch(args):
             "gpu_launches": launches, "clocks": clk.summary()}), flush=True)
 
 
+# ----------------------------------------------------------------------------- other workloads
+def _sub_bench(argv, timeout_s):
+    """One bench.py run in a child process (same GPU); its JSON line, or the reason it has none."""
+    cmd = [sys.executable, os.path.abspath(__file__)] + argv
+    t0 = time.perf_counter()
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return None, "timed out after %d s" % timeout_s
+    wall = time.perf_counter() - t0
+    for ln in reversed(r.stdout.splitlines()):
+        if ln.startswith("{"):
+            d = json.loads(ln)
+            d["_wall_s"] = wall
+            return d, None
+    return None, "exit %d: %s" % (r.returncode, (r.stderr or "").strip().splitlines()[-1:] or "")
+
+
+def _pick(d, keys):
+    return {k: d.get(k) for k in keys if k in d}
+
+
+def run_extras(args):
+    """The other workloads of the metric, each run as its own bench.py process and reported beside
+    the headline: the kinked source (mixed and FP64 forms), 256 uneven problems in one CUDA graph
+    (mixed and FP64 batches), and 64 right-hand sides sharing one tree (folded mixed solve, FP64 loop)."""
+    common = ["--steps", "3", "--warmup", "3", "--no-cpu-baseline", "--no-extras"]
+    out = {}
+    jobs = [("kinked", ["--workload", "kinked"] + common, 900),
+            ("batch256", ["--workload", "batch256"] + common, 900),
+            ("shared_rhs64", ["--workload", "shared_rhs64"] + common, 600)]
+    for key, argv, tmo in jobs:
+        d, why = _sub_bench(argv, tmo)
+        if d is None:
+            out[key] = {"unavailable": why}
+            continue
+        rec = _pick(d, ("value", "unit", "ms_per_step", "dtype", "config", "fp64_form", "e2e", "clocks",
+                        "gpu_launches", "_wall_s"))
+        roof = d.get("roofline") or {}
+        rec["roofline"] = _pick(roof, ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic",
+                                       "peak_source"))
+        if "contractions" in roof:
+            rec["roofline"]["contractions"] = {n: _pick(c, ("frac_of_bf16_peak", "useful_fraction", "ms", "form"))
+                                               for n, c in roof["contractions"].items()}
+        if key == "kinked":
+            rec["oracle_check"] = ("the oracle's tree and lists for this workload take over a minute on the host, "
+                                   "so the sampled comparison with the oracle runs in the full-size GPU parity "
+                                   "test instead; rel. difference of the mixed form from the FP64 form on every "
+                                   "target is in fp64_form")
+        out[key] = rec
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -417,6 +520,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default split-K factors (no autotuner run)")
     ap.add_argument("--refine", default="tail", choices=["tail", "interp", "interp_area", "interp_mixed"],
                     help="refinement rule of the adaptive tree (Section 6.1 alternatives to the tail test)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="on the default workload, skip the kinked, batch256 and shared_rhs64 runs that are "
+                         "reported beside the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -639,14 +745,19 @@ def main():
                      "mixed_over_fp64_speedup": ms64 / ms, "rel_diff_mixed_vs_fp64_all_targets": d}
         del ws64, _g64
 
-    cpu = None
+    cpu, cpu1 = None, None
     errs = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n1 = tree.n_leaves * kk  # the oracle checks the first right-hand side
         got = {args.precision: [o.reshape(-1)[:n1].cpu().numpy() for o in out]}
         if out64 is not None:
             got["fp64"] = [o.reshape(-1)[:n1].cpu().numpy() for o in out64]
-        cpu, errs = cpu_baseline(wl, got, rule=args.refine)
+        cpu, cpu1, errs = cpu_baseline(wl, got, rule=args.refine)
+
+    extras = None
+    if (rank == 0 and world == 1 and args.workload == "adaptive_gauss20" and args.precision == "mixed"
+            and not args.no_extras):
+        extras = run_extras(args)
 
     if rank == 0:
         clocks = clk.summary()
@@ -666,6 +777,7 @@ def main():
                 "stage_ms": stage_ms,
                 "roofline": roof,
                 "cpu_baseline": cpu,
+                "cpu_baseline_1core": cpu1,
                 "sampled_rel_err_vs_oracle": errs,
                 "fp64_form": fp64_form,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_targets * 8,
@@ -673,6 +785,8 @@ def main():
                 "gpu_launches": launches,
                 "offnode": offnode,
                 "clocks": clocks}
+        if extras:
+            line.update(extras)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
