@@ -72,3 +72,42 @@ def test_batch_tune_picks_a_stream_count():
     for (tree, ops, f, out, ws), ref in zip(items, refs):
         for q in range(3):
             assert torch.equal(out[q], ref[q])
+
+
+def _rel(a, b):
+    import numpy as np
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 1e-10)])
+def test_leaf_count_members_in_a_batch_match_the_oracle(precision, tol, oracle_ops):
+    """Members of the uneven batch of leaf-count trees (member 224: k = 8, 103 leaves targeted;
+    member 44: k = 16, 103 leaves targeted), solved together in one batch graph, against the
+    oracle's solve on the oracle's own greedy tree, element by element."""
+    from oracle import fmm
+    from oracle import tree as T
+    mem = W.batch_members(256)
+    prec = v.MIXED if precision == "mixed" else v.FP64
+    items, oracle_cases = [], []
+    for i in (224, 44):
+        m = mem[i]
+        k, p, src = m["k"], m["p"], m["source"]
+        tree = v.tree_build_leaves(0.0, 0.0, 1.0, k, src, m["n_leaves_target"], 16)
+        ot = T.build_greedy(0.0, 0.0, 1.0, k, src, m["n_leaves_target"], 16)
+        assert tree.n_leaves == ot.n_leaves
+        F = ot.sample(src)
+        f = torch.from_numpy(F.reshape(-1)).cuda()
+        ops = v.ops_create(k, p, prec)
+        out = tuple(torch.full_like(f, float("nan")) for _ in range(3))
+        items.append((tree, ops, f, out, workspace(tree, ops, 1)))
+        oracle_cases.append((ot, oracle_ops(k, p), F))
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    g = Batch(4).graph(items, stream)
+    g.launch(stream)
+    stream.synchronize()
+    for (tree, ops, f, out, ws), (ot, oops, F) in zip(items, oracle_cases):
+        ref = fmm.solve(ot, T.build_lists(ot), oops, F)
+        for q in range(3):
+            got = out[q].cpu().numpy().reshape(ref[q].shape)
+            assert _rel(got, ref[q]) < tol, (precision, tree.k, q, _rel(got, ref[q]))
