@@ -220,6 +220,21 @@ int vfmm_ops_export(const vfmm_ops* ops, int32_t which, double* host, int64_t n_
 
 int vfmm_ops_destroy(vfmm_ops* ops);
 
+/* Slices of the split-BF16 contractions of a VFMM_MIXED operator set (no counterpart in the paper,
+ * which computes in double precision). Every operand of a contraction is stored as 8 base-64 digits
+ * (48 bits below its power-of-two scale); a contraction that takes S of them (6 <= S <= 8) issues
+ * the S (S + 1) / 2 slice products i + j <= S + 1 and truncates each operand and the dropped
+ * products at about 2^(-6 S) of its scale: fewer tensor-core products and fewer gathered bytes,
+ * less accuracy. slices[5] = near field, S2M, M2L, S2L, leaf far field (L2T + M2T); a new operator
+ * set takes {8, 7, 8, 7, 8}, the fewest that left the error against the FP64 form unchanged on the
+ * adaptive 20-Gaussian (k = 16, p = 40), kinked and uniform depth-7 (k = 16) workloads (taking 7
+ * for the near field raised it there to 2.4e-10). Host-only; applies to later calls and graph
+ * captures (a graph keeps the
+ * counts it captured); not while a solve with these operators is being launched. Errors:
+ * INVALID_ARG (null pointer, not VFMM_MIXED, a count outside [6, 8]). */
+int vfmm_ops_set_slices(vfmm_ops* ops, const int32_t* slices);
+int vfmm_ops_get_slices(const vfmm_ops* ops, int32_t* slices);
+
 /* Device workspace the solve needs for this tree, operator set and nrhs
  * (multipole and local expansions, near-field partial products). with_io != 0
  * adds room for the device copies vfmm_volume_potential_host stages through.
@@ -389,7 +404,8 @@ int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, i
 
 /* Work accounting for roofline reports, for a call with nrhs right-hand sides: out[VFMM_N_WORK] =
  * [0] BF16 tensor-core FLOPs the near-field contraction issues per call (VFMM_MIXED: every
- *     slice product of every tile, zero-padded rows included; 0 for VFMM_FP64),
+ *     slice product of every tile at the operator set's slice counts, zero-padded rows included;
+ *     0 for VFMM_FP64),
  * [1] the same for M2L, [2] for the leaf far field (L2T + M2T), [3] for S2L, [4] for S2M,
  * [5] FP64-equivalent FLOPs of the near field, 2 * 3k^2 * k^2 per U-list entry and right-hand side,
  * [6] number of U-list entries, [7] which contractions run in the entry-major form (one column

@@ -193,6 +193,25 @@ class Ops:
                 pass
             self._h = None
 
+    CONTRACTIONS = ("near", "s2m", "m2l", "s2l", "far")
+
+    @property
+    def slices(self):
+        """Slices per split-BF16 contraction (VFMM_MIXED), {near, s2m, m2l, s2l, far} -> 6..8."""
+        out = np.zeros(5, dtype=np.int32)
+        call("vfmm_ops_get_slices", self._h, out.ctypes.data_as(c_int32_p))
+        return dict(zip(self.CONTRACTIONS, out.tolist()))
+
+    def set_slices(self, **counts):
+        """vfmm_ops_set_slices: e.g. set_slices(near=7, m2l=6); unnamed contractions keep theirs."""
+        cur = self.slices
+        unknown = set(counts) - set(cur)
+        if unknown:
+            raise ValueError("unknown contractions %s" % sorted(unknown))
+        cur.update(counts)
+        arr = np.array([cur[c] for c in self.CONTRACTIONS], dtype=np.int32)
+        call("vfmm_ops_set_slices", self._h, arr.ctypes.data_as(c_int32_p))
+
     def export(self, name):
         k, p = self.k, self.p
         kk, P = k * k, p + 1

@@ -493,7 +493,7 @@ struct DownArgs {
     // split-precision M2L rows 2..2p+1 (null in the FP64 form): (hi, lo) scaled by 2^-E[level][r]
     const float2* m2l_out;
     const int* m2l_E;   // [Rx] row exponents of the M2L tables
-    const int* m2l_G;   // [depth + 1] level exponents of the multipole operand
+    const unsigned* m2l_G;  // [(depth + 1) R] biased level exponents of the multipole operand
     const double* m2l_c0;  // Re of local coefficient 0 from the V and X lists, with the log(h) terms
     const double* vslab;   // FP64 form: [n_V][2(p+1)] M2L of every V entry
     const double* xslab;   // FP64 form: [n_X][2(p+1)] S2L of every X entry
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
         } else if (d.vptr[b + 1] > d.vptr[b]) {
             const float2 vr = d.m2l_out[vb * d.Rx + 2 * (t - 1)];
             const float2 vi = d.m2l_out[vb * d.Rx + 2 * (t - 1) + 1];
-            const int g = d.m2l_G[(size_t)d.level * R + r];
+            const int g = level_exp_value(d.m2l_G[(size_t)d.level * R + r]);
             re += ((double)vr.x + (double)vr.y) * pow2(g + d.m2l_E[2 * (t - 1)]);
             im += ((double)vi.x + (double)vi.y) * pow2(g + d.m2l_E[2 * (t - 1) + 1]);
         }
@@ -586,7 +586,7 @@ __device__ __forceinline__ double2 combine_local(const DownArgs& d, int level, i
         } else if (has_v) {
             const float2 vr = d.m2l_out[vb * d.Rx + 2 * (t - 1)];
             const float2 vi = d.m2l_out[vb * d.Rx + 2 * (t - 1) + 1];
-            const int g = d.m2l_G[(size_t)level * d.R + r];
+            const int g = level_exp_value(d.m2l_G[(size_t)level * d.R + r]);
             const int er = g + d.m2l_E[2 * (t - 1)], ei = g + d.m2l_E[2 * (t - 1) + 1];
             re += f2d_scaled(vr.x, er) + f2d_scaled(vr.y, er);
             im += f2d_scaled(vi.x, ei) + f2d_scaled(vi.y, ei);
@@ -614,15 +614,20 @@ __global__ void down_mixed_kernel(DownArgs d) {
 }
 
 // ---------------------------------------------------------------- persistent tree passes
-// One cooperative launch walks all levels: the translations are cut into one-warp units (a row pair
-// of one virtual box) dealt over the warps of every CTA, and the 4 position tables sit in shared
-// memory for the whole pass. There is no barrier between levels: a unit waits (bounded) only for
-// the expansions it reads, through per-box readiness counters, so a box starts as soon as its
-// children (M2M) or its parent (L2L) are done. Every unit's inputs are produced by units that come
-// earlier in the global unit order, and each warp takes its units in that order, so the earliest
-// unfinished unit can always proceed (all CTAs are resident: cooperative launch). Data written by
-// other CTAs are read through L2 (ld.global.cg).
-constexpr int kPassThreads = 512;
+// One launch walks all levels: the translations are cut into one-warp units (a block of row pairs
+// of one virtual box), numbered level by level, and warps take the next unit number from an atomic
+// counter, so units spread over whatever SMs the kernel holds. There is no barrier between levels:
+// a unit waits (bounded) only for the expansions it reads, through per-box readiness counters, so a
+// box starts as soon as its children (M2M) or its parent (L2L) are done. Every unit's inputs come
+// from units with smaller numbers, and numbers are taken in increasing order, so the unfinished unit
+// with the smallest number is always held by a running warp (a warp holds at most its current unit
+// and the next one it took, which has a larger number) and can proceed: no CTA needs another to be
+// resident, and the kernel starts as soon as any SM is free. Data written by other CTAs are read
+// through L2 (ld.global.cg).
+// Four warps per CTA (one per SM sub-partition) and up to four CTAs per SM: the units a CTA takes
+// one after another land on different sub-partitions, and CTAs are spread over the SMs first.
+constexpr int kPassThreads = 128;
+constexpr int kPassCtasPerSm = 4;
 
 // Readiness counters of the dataflow tree passes: ready[vb] counts the units that have written
 // their part of virtual box vb's expansion (M2M: the box's own multipole; L2L: the box's local), and
@@ -637,6 +642,13 @@ __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Next unit of a pass for this warp: one atomic increment by lane 0, broadcast to the warp.
+__device__ __forceinline__ int next_unit(unsigned* counter, int lane) {
+    unsigned u = 0;
+    if (lane == 0) u = atomicAdd(counter, 1u);
+    return (int)__shfl_sync(0xffffffffu, u, 0);
+}
+
 // Waits (bounded) until *flag >= need. Gives up, recording code 6 in the status word, when the
 // bound runs out; gives up at once when another wait already did (the status word is set).
 __device__ bool wait_ready(const unsigned* flag, unsigned need, int* err) {
@@ -649,76 +661,77 @@ __device__ bool wait_ready(const unsigned* flag, unsigned need, int* err) {
     return false;
 }
 
-// Loads the 4 position tables into shared memory (bulk copy); one decision for the whole CTA.
-__device__ bool load_tables(double2* sT, const double2* tab, int P, int* err) {
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ volatile int no_abort;
-    const uint32_t bar_a = tc::smem_u32(&bar);
-    const uint32_t bytes = (uint32_t)(4 * P * P) * sizeof(double2);
-    if (threadIdx.x == 0) {
-        no_abort = 0;
-        tc::mbar_init(bar_a, 1);
-        tc::mbar_fence_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        tc::mbar_arrive_expect_tx(bar_a, bytes);
-        constexpr uint32_t kChunk = 32768;
-        for (uint32_t off = 0; off < bytes; off += kChunk)
-            tc::bulk_copy_g2s(tc::smem_u32(sT) + off, reinterpret_cast<const char*>(tab) + off,
-                              min(kChunk, bytes - off), bar_a);
-    }
-    const bool landed = tc::mbar_wait(bar_a, 0, &no_abort);
-    if (!__syncthreads_and(landed)) {
-        if (threadIdx.x == 0 && err) atomicExch(err, 5);
-        settle_bulk_copy(bar_a, &no_abort);
-        return false;
-    }
-    return true;
+
+// ---- rotated real translations (the factorisation is written out in tables.cu): for child
+// position pos (sx = +1 when pos & 1, sy = +1 when pos & 2, s = sx sy), M2M is
+// A_l = sigma_l sum_n Rm[n][l] (rho_n a_n) and L2L is c_m = rho_m sum_l Rl[l][m] (sigma_l b_l), with
+// the Gaussian integers sigma_l = (i s)^floor(l/2) (sx + i sy)^(l mod 2) and rho_n = conj(sigma_n).
+
+// x with its sign bit flipped when neg = 0x80000000 (integer work, no FP64 operation)
+__device__ __forceinline__ double flip_sign(double x, unsigned neg) {
+    return __hiloint2double(__double2hiint(x) ^ (int)neg, __double2loint(x));
 }
 
-// One output row pair (j, P-1-j) of one virtual box's four child-position translations, computed
-// by one warp: lane (pos, ks) = (lane / 8, lane % 8) takes position pos and the inputs
-// n = ks, ks + 8, ... of its triangular ranges (M2M row o takes n <= o, L2L row m takes n >= m), so
-// the 4 (P + 1) complex multiply-adds of a row pair spread over the 32 lanes. Shuffles then sum
-// the 8 input slices of each position, and for M2M (mode 0) the four positions as well, in a
-// fixed order (the results are deterministic). Tables [pos][in][out] complex in shared memory: the
-// 8 lanes of a quarter warp read rows n one apart (stride P complex = 4P banks), which never
-// share a bank. Inputs: mode 0, child pos at x + pos * xs; mode 1, the parent local at x.
-// Returns the row-a and row-b sums: mode 0 in every lane, summed over the positions; mode 1 in
-// every lane of position pos, for that position.
-__device__ __forceinline__ void translate_warp(int mode, const double2* __restrict__ sT, const double2* x,
-                                               size_t xs, int P, int j, int lane, double2& ra, double2& rb) {
-    const int pos = lane >> 3, ks = lane & 7;
-    const int oa = j, ob = P - 1 - j;  // oa <= ob
-    const double2* M = sT + (size_t)pos * P * P;
-    const double2* xp = mode == 0 ? x + pos * xs : x;
+// v sigma_n (sig) or v rho_n (!sig) for child position pos: sign changes and swaps, then one
+// addition per component, exact for even n (the added term is zero).
+__device__ __forceinline__ double2 rotate(double2 v, int pos, int n, bool sig) {
+    constexpr unsigned kNeg = 0x80000000u;
+    const unsigned nx = (pos & 1) ? 0u : kNeg, ny = (pos & 2) ? 0u : kNeg;
+    const unsigned nc = sig ? (nx ^ ny) : (nx ^ ny ^ kNeg);  // unit u = i c: c = s (sigma), -s (rho)
+    const unsigned ne = sig ? ny : (ny ^ kNeg);              // odd factor sx + i e: e = sy (sigma), -sy (rho)
+    double wx, wy;  // v u^floor(n/2)
+    switch ((n >> 1) & 3) {
+        case 0: wx = v.x; wy = v.y; break;
+        case 1: wx = flip_sign(v.y, nc ^ kNeg); wy = flip_sign(v.x, nc); break;
+        case 2: wx = flip_sign(v.x, kNeg); wy = flip_sign(v.y, kNeg); break;
+        default: wx = flip_sign(v.y, nc); wy = flip_sign(v.x, nc ^ kNeg); break;
+    }
+    // times (sx + i e) for odd n: (wx sx - wy e) + i (wy sx + wx e)
+    const bool odd = n & 1;
+    const double ax = odd ? flip_sign(wx, nx) : wx, bx = odd ? flip_sign(wy, ne ^ kNeg) : 0.0;
+    const double ay = odd ? flip_sign(wy, nx) : wy, by = odd ? flip_sign(wx, ne) : 0.0;
+    return make_double2(ax + bx, ay + by);
+}
+
+// Lane roles of a translation unit: position pos = lane / 8, row pair j = 4 jb + (lane / 2) % 4 of
+// the unit's block jb, input half ks = lane % 2 (inputs n = ks, ks + 2, ...).
+constexpr int kPairsPerUnit = 4;
+
+// One unit: row pairs 4 jb .. 4 jb + 3 (rows j and P-1-j) of the four child positions' rotated
+// real translations, xs = the four rotated input vectors [4][P] staged in shared memory, M the
+// real matrix [in][out]. mode 0 (M2M: row o takes inputs n <= o), 1 (L2L: row m takes n >= m).
+// Returns the two row sums (complex, still rotated) summed over the lane's input half and its
+// partner's, in both lanes of the pair.
+__device__ __forceinline__ void translate_rows(int mode, const double* __restrict__ M, const double2* xs, int P, int j,
+                                               int lane, double2& ra, double2& rb) {
+    const int pos = lane >> 3, ks = lane & 1;
+    const int oa = j, ob = P - 1 - j;  // oa <= ob when j < (P + 1) / 2
+    const bool valid = j < (P + 1) / 2;
+    const bool two = valid && oa != ob;
+    const double2* x = xs + pos * P;
     double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int n = ks + 8 * i;
-        if (n >= P || (mode == 0 && n > ob)) break;
-        const double2 v = __ldcg(xp + n);
-        if (mode == 0 ? n <= oa : n >= oa) {
-            const double2 m = M[(size_t)n * P + oa];
-            ar = fma(m.x, v.x, fma(-m.y, v.y, ar));
-            ai = fma(m.x, v.y, fma(m.y, v.x, ai));
-        }
-        if (ob != oa && (mode == 0 || n >= ob)) {
-            const double2 m = M[(size_t)n * P + ob];
-            br = fma(m.x, v.x, fma(-m.y, v.y, br));
-            bi = fma(m.x, v.y, fma(m.y, v.x, bi));
+    if (valid) {
+        // M2M: n = ks .. ob; L2L: n = oa .. P-1 (first n of the lane's parity)
+        const int n0 = mode == 0 ? ks : oa + ((ks - oa) & 1);
+        const int n1 = mode == 0 ? ob : P - 1;
+        for (int n = n0; n <= n1; n += 2) {
+            const double2 v = x[n];
+            if (mode == 0 ? n <= oa : true) {
+                const double m = M[(size_t)n * P + oa];
+                ar = fma(m, v.x, ar);
+                ai = fma(m, v.y, ai);
+            }
+            if (two && (mode == 0 || n >= ob)) {
+                const double m = M[(size_t)n * P + ob];
+                br = fma(m, v.x, br);
+                bi = fma(m, v.y, bi);
+            }
         }
     }
-    const int lim = mode == 0 ? 32 : 8;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        if (off >= lim) break;
-        ar += __shfl_xor_sync(0xffffffffu, ar, off);
-        ai += __shfl_xor_sync(0xffffffffu, ai, off);
-        br += __shfl_xor_sync(0xffffffffu, br, off);
-        bi += __shfl_xor_sync(0xffffffffu, bi, off);
-    }
+    ar += __shfl_xor_sync(0xffffffffu, ar, 1);
+    ai += __shfl_xor_sync(0xffffffffu, ai, 1);
+    br += __shfl_xor_sync(0xffffffffu, br, 1);
+    bi += __shfl_xor_sync(0xffffffffu, bi, 1);
     ra = make_double2(ar, ai);
     rb = make_double2(br, bi);
 }
@@ -729,143 +742,238 @@ struct PassArgs {
     const int32_t* nonleaf_start;  // device, depth + 2
     const int32_t* level_start;    // device, depth + 2
     const int32_t* child0;
-    const double2* tab;
+    const double* tab;     // real matrix of the rotated translation [in][out]
     double2* ex;           // Mexp (upward) or Lexp (downward), [n_boxes * R][P] complex
     const int32_t* parent;
     unsigned int* ready;   // [n_boxes * R] readiness counters, zero at launch
+    unsigned int* work;    // unit counter, zero at launch
+    unsigned* glev;        // upward pass, mixed form: biased level exponents of the M2L operand (or null)
+    const int32_t* level;
     int* err;
 };
 
-// The work of one level is a list of (virtual box, row pair) units dealt to warps striped over the
-// CTAs (warp w of CTA c is slot w * gridDim.x + c), so that even a level of a few boxes spreads over
-// many SMs and all four sub-partitions of each: this part retires about 2 FP64 FMAs per clock per
-// SM, so a level takes the FP64 work of its busiest sub-partition.
+// The work of a pass is a list of units (a block of kPairsPerUnit row pairs of one virtual box),
+// level by level; warps take them in order from the pass's counter, so the units of a level spread
+// over the SMs and sub-partitions the kernel holds (this part retires about 2 FP64 FMAs per clock
+// per SM, so a unit's FP64 work is best alone on its sub-partition).
 constexpr int kPassWarps = kPassThreads / 32;
 
+// Shared memory of a pass: the real matrix [P][P], then per warp the staged inputs [4][P] complex.
+__host__ __device__ inline size_t pass_smem_bytes(int P) {
+    return ((size_t)P * P * sizeof(double) + 15) / 16 * 16 + (size_t)kPassWarps * 4 * P * sizeof(double2);
+}
+
+// Copies the real matrix into shared memory (plain loads: 8 P^2 bytes).
+__device__ __forceinline__ void load_real_table(double* sM, const double* tab, int P) {
+    for (int q = threadIdx.x; q < P * P; q += blockDim.x) sM[q] = tab[q];
+    __syncthreads();
+}
+
 // All M2M levels, finest parents first (the global unit order).
-__global__ void __launch_bounds__(kPassThreads, 1) upward_pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(kPassThreads, kPassCtasPerSm) upward_pass_kernel(PassArgs a) {
     extern __shared__ __align__(128) unsigned char pass_raw[];
     const int P = a.P, R = a.R;
-    double2* sT = reinterpret_cast<double2*>(pass_raw);
-    if (!load_tables(sT, a.tab, P, a.err)) return;
-    const int lane = threadIdx.x & 31;
-    const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassWarps;
-    const unsigned npair = (unsigned)(P + 1) / 2;
+    double* sM = reinterpret_cast<double*>(pass_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pos = lane >> 3;
+    double2* xs = reinterpret_cast<double2*>(pass_raw + ((size_t)P * P * sizeof(double) + 15) / 16 * 16) +
+                  (size_t)warp * 4 * P;
+    load_real_table(sM, a.tab, P);
+    const int npair = (P + 1) / 2, nu = (npair + kPairsPerUnit - 1) / kPairsPerUnit;  // units per box
     int l = a.depth - 1, lbase = 0;
-    int lunits = l >= 2 ? (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * (int)npair : 0;
-    for (int u = slot;; u += nslots) {
+    int lunits = l >= 2 ? (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * nu : 0;
+    for (int u = next_unit(a.work, lane);;) {
         while (l >= 2 && u >= lbase + lunits) {
             lbase += lunits;
-            if (--l >= 2) lunits = (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * (int)npair;
+            if (--l >= 2) lunits = (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * nu;
         }
         if (l < 2) break;
+        const int next = next_unit(a.work, lane);  // taken now: its latency overlaps this unit
         const int lu = u - lbase;
-        const int vi = lu / (int)npair, j = lu - vi * (int)npair;
+        const int vi = lu / nu, jb = lu - vi * nu;
         const int bi = vi / R, r = vi - bi * R;
         const int b = a.nonleaf[a.nonleaf_start[l] + bi], c0 = a.child0[b];
         // the non-leaf children's multipoles must be complete (leaf multipoles come from S2M)
         bool ok = true;
         if (lane < 4 && a.child0[c0 + lane] >= 0)
-            ok = wait_ready(a.ready + (size_t)(c0 + lane) * R + r, npair, a.err);
+            ok = wait_ready(a.ready + (size_t)(c0 + lane) * R + r, (unsigned)nu, a.err);
         if (!__all_sync(0xffffffffu, ok)) return;
         __syncwarp();
+        // stage the four children's multipoles, rotated by rho (children are consecutive boxes); all
+        // loads are issued before the first is used (4P <= 256: at most 8 per lane)
+        {
+            double2 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int q = lane + 32 * i, p = q / P;
+                if (q < 4 * P) v[i] = __ldcg(a.ex + ((size_t)(c0 + p) * R + r) * P + (q - p * P));
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int q = lane + 32 * i, p = q / P;
+                if (q < 4 * P) xs[q] = rotate(v[i], p, q - p * P, false);
+            }
+        }
+        __syncwarp();
+        const int j = kPairsPerUnit * jb + ((lane >> 1) & 3);
         double2 ra, rb;
-        // the four children are consecutive boxes: position pos is virtual box (c0 + pos) R + r
-        translate_warp(0, sT, a.ex + ((size_t)c0 * R + r) * P, (size_t)R * P, P, j, lane, ra, rb);
-        if (lane == 0) {
+        translate_rows(0, sM, xs, P, j, lane, ra, rb);
+        // rotate the rows back (sigma) and sum the four positions
+        ra = rotate(ra, pos, j, true);
+        rb = rotate(rb, pos, P - 1 - j, true);
+#pragma unroll
+        for (int off = 8; off < 32; off <<= 1) {
+            ra.x += __shfl_xor_sync(0xffffffffu, ra.x, off);
+            ra.y += __shfl_xor_sync(0xffffffffu, ra.y, off);
+            rb.x += __shfl_xor_sync(0xffffffffu, rb.x, off);
+            rb.y += __shfl_xor_sync(0xffffffffu, rb.y, off);
+        }
+        int e = INT_MIN;
+        if (lane < 8 && (lane & 1) == 0 && j < npair) {
             double2* out = a.ex + ((size_t)b * R + r) * P;
             out[j] = ra;
-            if (j != P - 1 - j) out[P - 1 - j] = rb;
-            red_release_add_u32(a.ready + (size_t)b * R + r, 1u);
+            e = max(part_exp(ra.x, 2 * j), part_exp(ra.y, 2 * j + 1));
+            if (j != P - 1 - j) {
+                out[P - 1 - j] = rb;
+                e = max(e, max(part_exp(rb.x, 2 * (P - 1 - j)), part_exp(rb.y, 2 * (P - 1 - j) + 1)));
+            }
+            __threadfence();
         }
+        if (a.glev) level_exp_max(e, a.glev + (size_t)l * R + r);
+        __syncwarp();
+        if (lane == 0) red_release_add_u32(a.ready + (size_t)b * R + r, 1u);
+        __syncwarp();  // the staging area is rewritten by the next unit
+        u = next;
     }
 }
 
 // Mixed form, all downward levels: level 2 boxes combine their M2L/S2L terms (one warp unit per
 // virtual box); below, each non-leaf parent's local is shifted to its 4 children (L2L) and each
-// child's terms are added (row-pair units).
-__global__ void __launch_bounds__(kPassThreads, 1) downward_pass_kernel(PassArgs a, DownArgs d) {
+// child's terms are added.
+__global__ void __launch_bounds__(kPassThreads, kPassCtasPerSm) downward_pass_kernel(PassArgs a, DownArgs d) {
     extern __shared__ __align__(128) unsigned char pass_raw[];
     const int P = a.P, R = a.R;
-    double2* sT = reinterpret_cast<double2*>(pass_raw);
-    if (!load_tables(sT, a.tab, P, a.err)) return;
-    const int lane = threadIdx.x & 31, pos = lane >> 3;
-    const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassWarps;
-    const unsigned npair = (unsigned)(P + 1) / 2;
+    double* sM = reinterpret_cast<double*>(pass_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pos = lane >> 3;
+    double2* xs = reinterpret_cast<double2*>(pass_raw + ((size_t)P * P * sizeof(double) + 15) / 16 * 16) +
+                  (size_t)warp * 4 * P;
+    load_real_table(sM, a.tab, P);
+    const int npair = (P + 1) / 2, nu = (npair + kPairsPerUnit - 1) / kPairsPerUnit;
     const int b2 = a.level_start[2], n2 = (a.level_start[3] - b2) * R;  // level-2 units
     int l = 3, lbase = n2;
-    int lunits = l <= a.depth ? (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * (int)npair : 0;
-    for (int u = slot;; u += nslots) {
+    int lunits = l <= a.depth ? (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * nu : 0;
+    for (int u = next_unit(a.work, lane), next = 0;; u = next) {
+        next = next_unit(a.work, lane);  // taken now: its latency overlaps this unit
         if (u < n2) {
-            // level 2: no parent term; the whole local at once, published as npair contributions
+            // level 2: no parent term; the whole local at once, published as all nu units
             const int64_t vb = (int64_t)b2 * R + u;
             const int b = (int)(vb / R), r = (int)(vb % R);
             for (int t = lane; t < P; t += 32) a.ex[(size_t)vb * P + t] = combine_local(d, 2, b, r, t, 0.0, 0.0);
             __threadfence();
             __syncwarp();
-            if (lane == 0) red_release_add_u32(a.ready + vb, npair);
+            if (lane == 0) red_release_add_u32(a.ready + vb, (unsigned)nu);
             continue;
         }
         while (l <= a.depth && u >= lbase + lunits) {
             lbase += lunits;
-            if (++l <= a.depth) lunits = (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * (int)npair;
+            if (++l <= a.depth) lunits = (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * nu;
         }
         if (l > a.depth) break;
         const int lu = u - lbase;
-        const int vi = lu / (int)npair, j = lu - vi * (int)npair;
+        const int vi = lu / nu, jb = lu - vi * nu;
         const int bi = vi / R, r = vi - bi * R;
         const int b = a.nonleaf[a.nonleaf_start[l - 1] + bi], c0 = a.child0[b];
         // the parent's local must be complete
         bool ok = true;
-        if (lane == 0) ok = wait_ready(a.ready + (size_t)b * R + r, npair, a.err);
+        if (lane == 0) ok = wait_ready(a.ready + (size_t)b * R + r, (unsigned)nu, a.err);
         if (!__all_sync(0xffffffffu, ok)) return;
         __syncwarp();
+        // stage the parent's local rotated for each child position (sigma): P <= 64 values, at most
+        // two loads per lane, issued before use; each lane rotates its values for all four positions
+        {
+            const double2* x = a.ex + ((size_t)b * R + r) * P;
+            const double2 v0 = lane < P ? __ldcg(x + lane) : make_double2(0.0, 0.0);
+            const double2 v1 = lane + 32 < P ? __ldcg(x + lane + 32) : make_double2(0.0, 0.0);
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                if (lane < P) xs[p * P + lane] = rotate(v0, p, lane, true);
+                if (lane + 32 < P) xs[p * P + lane + 32] = rotate(v1, p, lane + 32, true);
+            }
+        }
+        __syncwarp();
+        const int j = kPairsPerUnit * jb + ((lane >> 1) & 3), mb = P - 1 - j;
         double2 ra, rb;
-        translate_warp(1, sT, a.ex + ((size_t)b * R + r) * P, 0, P, j, lane, ra, rb);
-        if ((lane & 7) == 0) {  // one lane per child position: add the child's own terms
-            const int c = c0 + pos, mb = P - 1 - j;
+        translate_rows(1, sM, xs, P, j, lane, ra, rb);
+        if ((lane & 1) == 0 && j < npair) {  // one lane per (child, row pair): rotate back, add the child's terms
+            const int c = c0 + pos;
+            ra = rotate(ra, pos, j, false);
             double2* out = a.ex + ((size_t)c * R + r) * P;
             out[j] = combine_local(d, l, c, r, j, ra.x, ra.y);
-            if (j != mb) out[mb] = combine_local(d, l, c, r, mb, rb.x, rb.y);
-            red_release_add_u32(a.ready + (size_t)c * R + r, 1u);
+            if (j != mb) {
+                rb = rotate(rb, pos, mb, false);
+                out[mb] = combine_local(d, l, c, r, mb, rb.x, rb.y);
+            }
+            __threadfence();
         }
+        __syncwarp();
+        if ((lane & 7) == 0) red_release_add_u32(a.ready + (size_t)(c0 + pos) * R + r, 1u);
+        __syncwarp();
     }
 }
 
-// Mixed form, per virtual leaf (leaf, r): the FP64 scalar part of u at every node of the leaf,
-// -(1/2pi) [log(h) sum_U a_0 + Re b_0 + sum_W a_0 (log h_w)], h_w = h / 2.
-__global__ void leaf_scalar_kernel(int nleaf, int R, int P, double width, const int32_t* __restrict__ box_of_leaf,
-                                   const int32_t* __restrict__ level, const int32_t* __restrict__ uptr,
-                                   const int32_t* __restrict__ uidx, const int32_t* __restrict__ wptr,
-                                   const int32_t* __restrict__ widx, const double* __restrict__ Mexp,
-                                   const double* __restrict__ Lexp, double* __restrict__ scal) {
-    const int64_t vl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (vl >= (int64_t)nleaf * R) return;
-    const int leaf = (int)(vl / R), r = (int)(vl % R);
-    const int b = box_of_leaf[leaf];
-    const double logh = log(ldexp(width, -level[b]));
-    double m = 0.0, w0 = 0.0;
-    for (int e = uptr[b]; e < uptr[b + 1]; ++e) m += Mexp[((size_t)uidx[e] * R + r) * 2 * P];
-    for (int e = wptr[b]; e < wptr[b + 1]; ++e) w0 += Mexp[((size_t)widx[e] * R + r) * 2 * P];
-    scal[vl] = -kInv2Pi * logh * m - kInv2Pi * (Lexp[((size_t)b * R + r) * 2 * P] + w0 * (logh - 0.6931471805599453));
-}
-
 // Mixed form, one CTA per virtual leaf (leaf, r), one thread per node: u, u_x, u_y = near + far +
-// scalar, the split contraction outputs (hi, lo) scaled back by their power-of-two exponents.
-__global__ void leaf_mixed_kernel(int nleaf, int R, int kk, int Rp, int lw, double wm,
-                                  const int32_t* __restrict__ box_of_leaf, const int32_t* __restrict__ level,
-                                  const float2* __restrict__ nearmix, const int* __restrict__ Er,
-                                  const int* __restrict__ Ef, const float2* __restrict__ farmix,
-                                  const int* __restrict__ farE, const int* __restrict__ Et,
-                                  const double* __restrict__ scal, double* __restrict__ u, double* __restrict__ ux,
-                                  double* __restrict__ uy) {
+// scalar, the split contraction outputs (hi, lo) scaled back by their power-of-two exponents. The
+// scalar part, the same at every node of the leaf, is FP64:
+// -(1/2pi) [log(h) sum_U a_0 + Re b_0 + sum_W a_0 (log h_w)], h_w = h / 2 (first warp, fixed-order sums).
+struct LeafMixedArgs {
+    int nleaf, R, kk, Rp, P, lw;
+    double wm, width;
+    const int32_t* box_of_leaf;
+    const int32_t* level;
+    const int32_t *uptr, *uidx, *wptr, *widx;
+    const double* Mexp;
+    const double* Lexp;
+    const float2* nearmix;
+    const int* Er;
+    const int* Ef;
+    const float2* farmix;
+    const int* farE;
+    const int* Et;
+    double *u, *ux, *uy;
+};
+
+__global__ void leaf_mixed_kernel(LeafMixedArgs a) {
     // width = wm 2^lw with wm in [1, 2): h = wm 2^(lw - lv), so every power-of-two scale is folded
     // into the exponents (f2d_scaled), times wm^(2, 1, -1) when wm is not one
+    __shared__ double s_scal;
+    const int nleaf = a.nleaf, R = a.R, kk = a.kk, Rp = a.Rp, lw = a.lw;
+    const double wm = a.wm;
     const unsigned vl = blockIdx.x;
     const int t = threadIdx.x;
-    if (t >= kk) return;
     const unsigned leaf = vl / (unsigned)R, r = vl - leaf * (unsigned)R;
-    const int lv = level[box_of_leaf[leaf]];
+    const int b = a.box_of_leaf[leaf];
+    const int lv = a.level[b];
+    if (t < 32) {
+        const size_t P2 = 2 * (size_t)a.P;
+        const double logh = log(ldexp(a.width, -lv));
+        double m = 0.0, w0 = 0.0;
+        for (int e = a.uptr[b] + t; e < a.uptr[b + 1]; e += 32) m += a.Mexp[((size_t)a.uidx[e] * R + r) * P2];
+        for (int e = a.wptr[b] + t; e < a.wptr[b + 1]; e += 32) w0 += a.Mexp[((size_t)a.widx[e] * R + r) * P2];
+        for (int o = 16; o > 0; o >>= 1) {
+            m += __shfl_xor_sync(0xffffffffu, m, o);
+            w0 += __shfl_xor_sync(0xffffffffu, w0, o);
+        }
+        if (t == 0)
+            s_scal = -kInv2Pi * logh * m -
+                     kInv2Pi * (a.Lexp[((size_t)b * R + r) * P2] + w0 * (logh - 0.6931471805599453));
+    }
+    __syncthreads();
+    if (t >= kk) return;
+    const float2* __restrict__ nearmix = a.nearmix;
+    const float2* __restrict__ farmix = a.farmix;
+    const int* __restrict__ Er = a.Er;
+    const int* __restrict__ farE = a.farE;
+    const int* __restrict__ Et = a.Et;
+    const int* __restrict__ Ef = a.Ef;
     const float2* nm = nearmix + (size_t)vl * Rp;
     const float2* fm = farmix + (size_t)vl * Rp;
     const int en = Ef[r] + lw - lv, ef = Et[vl] + lv - lw;  // near scale h 2^E_f, far scale 2^E_t / h
@@ -887,9 +995,9 @@ __global__ void leaf_mixed_kernel(int nleaf, int R, int kk, int Rp, int lw, doub
         f2 /= wm;
     }
     const size_t o = ((size_t)r * nleaf + leaf) * kk + t;
-    u[o] = n0 + scal[vl] + f0;
-    ux[o] = n1 + f1;
-    uy[o] = n2 + f2;
+    a.u[o] = n0 + s_scal + f0;
+    a.ux[o] = n1 + f1;
+    a.uy[o] = n2 + f2;
 }
 
 // ---------------------------------------------------------------- leaf pass (one CTA per leaf)
@@ -989,7 +1097,11 @@ struct Workspace {
     double* vslab;      // FP64 form: per V entry M2L rows
     double* xslab;      // FP64 form: per X entry S2L rows
     const PlanSet* ps;  // split-contraction plans for the folded right-hand sides (mixed form)
-    unsigned int* ready; // [2][n_boxes * R] readiness counters of the persistent tree passes
+    unsigned int* ready; // [2][n_boxes * R] readiness counters of the persistent tree passes, then
+                         // [(depth + 1) R] biased level exponents (mixed form), then the two passes'
+                         // unit counters (work)
+    unsigned int* work;
+    size_t ready_words;
     double* Mexp;
     double* Lexp;
     double* slab;
@@ -1025,9 +1137,16 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
     take(w ? &w->Mexp : &dummy, (size_t)T.n_boxes * R * P2);
     take(w ? &w->Lexp : &dummy, (size_t)T.n_boxes * R * P2);
     {
+        // readiness counters of the persistent passes, then the mixed form's biased level exponents:
+        // one zeroing at the start of a solve covers both
         double* g = nullptr;
-        take(&g, (2 * (size_t)T.n_boxes * R + 1) / 2);
-        if (w) w->ready = reinterpret_cast<unsigned int*>(g);
+        const size_t words = 2 * (size_t)T.n_boxes * R + (size_t)(T.depth + 1) * R + 2;
+        take(&g, (words + 1) / 2);
+        if (w) {
+            w->ready = reinterpret_cast<unsigned int*>(g);
+            w->ready_words = words;
+            w->work = w->ready + words - 2;
+        }
     }
     take(w ? &w->slab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
     take(w ? &w->far : &dummy, mixed ? 1 : (size_t)T.n_leaves * 3 * kk);
@@ -1048,13 +1167,9 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
         if (w) w->mix.fmax = (unsigned long long*)p;
         take(&p, (R + 1) / 2);
         if (w) w->mix.Ef = (int*)p;
-        const size_t nlev = (size_t)T.depth + 1;
         take(&p, nl * mo->Rx);
         if (w) w->mix.s2m_out = (float2*)p;
-        take(&p, (nb + 1) / 2);
-        if (w) w->mix.bexp = (int*)p;
-        take(&p, (nlev * R + 1) / 2);
-        if (w) w->mix.glev = (int*)p;
+        if (w) w->mix.glev = w->ready + 2 * (size_t)T.n_boxes * R;
         take(&p, (nb * kSlices * mo->Kx * 2 + 7) / 8);
         if (w) w->mix.msl = (void*)p;
         take(&p, nb * mo->Rx);
@@ -1069,8 +1184,6 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
         if (w) w->mix.Et = (int*)p;
         take(&p, nl * mo->Rp);
         if (w) w->mix.far_out = (float2*)p;
-        take(&p, nl);
-        if (w) w->mix.scal = p;
         size_t np[3] = {0, 0, 0};
         split_part_elems(T, *PS, o, np);
         float2** bufs[3] = {w ? &w->mix.part : nullptr, w ? &w->mix.part_side : nullptr,
@@ -1193,10 +1306,10 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     d.Rx = mo ? mo->Rx : 0;
 }
 
-// Persistent passes (one cooperative launch for all levels) when every level is small enough that
+// Persistent passes (one launch for all levels) when every level is small enough that
 // per-level launches would mostly wait on launch latency; larger levels keep one launch per level.
 static bool use_passes(const DeviceTree& T, int R, int P) {
-    const size_t smem = (size_t)(4 * P * P) * sizeof(double2);
+    const size_t smem = pass_smem_bytes(P);
     if (smem > 200 * 1024 || T.depth < 3) return false;
     int widest = 0;
     for (int l = 1; l <= T.depth; ++l) widest = std::max(widest, T.nonleaf_start[l + 1] - T.nonleaf_start[l]);
@@ -1205,7 +1318,7 @@ static bool use_passes(const DeviceTree& T, int R, int P) {
 
 template <typename... Args>
 static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, cudaStream_t st, Args... args) {
-    const size_t smem = (size_t)(4 * P * P) * sizeof(double2);
+    const size_t smem = pass_smem_bytes(P);
     static thread_local int attr_dev[2] = {-1, -1};
     const int slot = (void*)kernel == (void*)upward_pass_kernel ? 0 : 1;
     int dev = 0;
@@ -1217,21 +1330,13 @@ static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, 
     int per_sm = 0;
     VFMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPassThreads, smem));
     if (per_sm < 1) return fail(VFMM_ERR_INTERNAL, "tree pass kernel does not fit on an SM");
-    // units (virtual box, row pair) are striped over the CTAs: enough CTAs that the widest level
-    // has at most about four units per sub-partition, up to one CTA per SM
-    const int units = widest_items * ((P + 1) / 2);
-    const int grid = std::max(1, std::min(per_sm * sm_count(), (units + 15) / 16));
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeCooperative;
-    attr.val.cooperative = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kPassThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    VFMM_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
+    // up to kPassCtasPerSm CTAs per SM, fewer when the widest level has fewer units than warps; an
+    // ordinary launch: warps take units from a counter in order, so CTAs that start late (SMs still
+    // busy with another stream's kernels) only find fewer units left
+    const int units = widest_items * (((P + 1) / 2 + kPairsPerUnit - 1) / kPairsPerUnit);
+    const int grid = std::max(1, std::min(std::min(per_sm, kPassCtasPerSm) * sm_count(), (units + kPassWarps - 1) / kPassWarps));
+    kernel<<<grid, kPassThreads, smem, st>>>(args...);
+    VFMM_CUDA(cudaGetLastError());
     return VFMM_OK;
 }
 
@@ -1314,6 +1419,9 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
     if (!mixed && R != 1) return fail(VFMM_ERR_INTERNAL, "the FP64 form solves one right-hand side at a time");
     const MixedOps* mo = (const MixedOps*)o.mixed;
     int launches = 0;
+    const bool passes = use_passes(T, R, P);
+    // readiness counters (persistent passes) and level exponents (mixed form) start at zero
+    if (passes || mixed) VFMM_CUDA(cudaMemsetAsync(w.ready, 0, w.ready_words * sizeof(unsigned int), st));
     if (mixed) {
         // near field first: its f slices also feed S2M and S2L
         mark(se, ST_NEAR, false, st);
@@ -1348,11 +1456,9 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
     mark(se, ST_S2M, true, st);
     // M2M, finest parents first (levels >= 2 are the ones the lists read)
     mark(se, ST_M2M, false, st);
-    const bool passes = use_passes(T, R, P);
     int widest = 0;
     for (int l = 1; l <= T.depth; ++l) widest = std::max(widest, T.nonleaf_start[l + 1] - T.nonleaf_start[l]);
     if (passes) {
-        VFMM_CUDA(cudaMemsetAsync(w.ready, 0, 2 * (size_t)T.n_boxes * R * sizeof(unsigned int), st));
         PassArgs pa;
         pa.depth = T.depth;
         pa.R = R;
@@ -1361,10 +1467,13 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.nonleaf_start = T.nonleaf_start_dev;
         pa.level_start = T.level_start_dev;
         pa.child0 = T.child0;
-        pa.tab = reinterpret_cast<const double2*>(o.m2m_t);
+        pa.tab = o.m2m_r;
         pa.ex = reinterpret_cast<double2*>(w.Mexp);
         pa.parent = T.parent;
         pa.ready = w.ready;
+        pa.work = w.work;
+        pa.glev = mixed ? w.mix.glev : nullptr;
+        pa.level = T.level;
         pa.err = w.mix.err;
         VFMM_CHECK(launch_pass(upward_pass_kernel, R, P, widest * R, st, pa));
         ++launches;
@@ -1385,7 +1494,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
             VFMM_CUDA(cudaStreamWaitEvent(side->aux, side->ev[5], 0));
             c0s = side->aux;
         }
-        VFMM_CHECK(m2l_mixed(T, PS, o, w.Mexp, w.mix, st));
+        VFMM_CHECK(m2l_mixed(T, PS, o, w.Mexp, w.mix, passes, st));
         if (PS.m2l.n_groups > 0) launches += 3 + gemm_launches(PS.m2l);
         const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
         const int64_t warps = (int64_t)(end - begin) * R;
@@ -1441,10 +1550,13 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.nonleaf_start = T.nonleaf_start_dev;
         pa.level_start = T.level_start_dev;
         pa.child0 = T.child0;
-        pa.tab = reinterpret_cast<const double2*>(o.l2l_t);
+        pa.tab = o.l2l_r;
         pa.ex = reinterpret_cast<double2*>(w.Lexp);
         pa.parent = T.parent;
         pa.ready = w.ready + (size_t)T.n_boxes * R;
+        pa.work = w.work + 1;
+        pa.glev = nullptr;
+        pa.level = T.level;
         pa.err = w.mix.err;
         VFMM_CHECK(launch_pass(downward_pass_kernel, R, P, std::max(widest * R, 16 * R), st, pa, d));
         ++launches;
@@ -1514,17 +1626,38 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
     a.uy = uy;
     if (mixed) {
         const int64_t nv = (int64_t)nleaf * R;
-        leaf_scalar_kernel<<<(unsigned)((nv + 127) / 128), 128, 0, st>>>(
-            nleaf, R, P, T.width, T.box_of_leaf, T.level, T.lptr[VFMM_LIST_U], T.lidx[VFMM_LIST_U],
-            T.lptr[VFMM_LIST_W], T.lidx[VFMM_LIST_W], w.Mexp, w.Lexp, w.mix.scal);
         int lw = 0;
         const double wm = 2.0 * std::frexp(T.width, &lw);  // width = wm 2^lw, wm in [1, 2)
         lw -= 1;
         if (side) VFMM_CUDA(cudaStreamWaitEvent(st, side->ev[2], 0));  // the near-field output
-        leaf_mixed_kernel<<<(unsigned)nv, ((kk + 31) / 32) * 32, 0, st>>>(
-            nleaf, R, kk, mo->Rp, lw, wm, T.box_of_leaf, T.level, w.mix.out, mo->Er, w.mix.Ef, w.mix.far_out,
-            mo->far_E, w.mix.Et, w.mix.scal, u, ux, uy);
-        launches += 2;
+        LeafMixedArgs la;
+        la.nleaf = nleaf;
+        la.R = R;
+        la.kk = kk;
+        la.Rp = mo->Rp;
+        la.P = P;
+        la.lw = lw;
+        la.wm = wm;
+        la.width = T.width;
+        la.box_of_leaf = T.box_of_leaf;
+        la.level = T.level;
+        la.uptr = T.lptr[VFMM_LIST_U];
+        la.uidx = T.lidx[VFMM_LIST_U];
+        la.wptr = T.lptr[VFMM_LIST_W];
+        la.widx = T.lidx[VFMM_LIST_W];
+        la.Mexp = w.Mexp;
+        la.Lexp = w.Lexp;
+        la.nearmix = w.mix.out;
+        la.Er = mo->Er;
+        la.Ef = w.mix.Ef;
+        la.farmix = w.mix.far_out;
+        la.farE = mo->far_E;
+        la.Et = w.mix.Et;
+        la.u = u;
+        la.ux = ux;
+        la.uy = uy;
+        leaf_mixed_kernel<<<(unsigned)nv, std::max(32, ((kk + 31) / 32) * 32), 0, st>>>(la);
+        ++launches;
     } else {
         leaf_kernel<<<(unsigned)nleaf, ((kk + 31) / 32) * 32, 0, st>>>(a);
         ++launches;
@@ -1777,10 +1910,12 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
         int Kp, Rp;
         float2* out;
         size_t rows;
-    } jobs[4] = {{&PS->near, w.mix.fsl, &mo->tm_near, mo->Kp, mo->Rp, w.mix.out, T.n_leaves * R},
-                 {&PS->m2l, w.mix.msl, &mo->tm_m2l, mo->Kx, mo->Rx, w.mix.m2l_out, T.n_boxes * R},
-                 {&PS->s2l, w.mix.fsl, &mo->tm_s2l, mo->Kp, mo->Rx, w.mix.s2l_out, T.n_boxes * R},
-                 {&PS->far, w.mix.aprep, &mo->tm_far, mo->Kx, mo->Rp, w.mix.far_out, T.n_leaves * R}};
+        int slices;
+    } jobs[4] = {{&PS->near, w.mix.fsl, &mo->tm_near, mo->Kp, mo->Rp, w.mix.out, T.n_leaves * R, mo->slices[kCtrNear]},
+                 {&PS->m2l, w.mix.msl, &mo->tm_m2l, mo->Kx, mo->Rx, w.mix.m2l_out, T.n_boxes * R, mo->slices[kCtrM2L]},
+                 {&PS->s2l, w.mix.fsl, &mo->tm_s2l, mo->Kp, mo->Rx, w.mix.s2l_out, T.n_boxes * R, mo->slices[kCtrS2L]},
+                 {&PS->far, w.mix.aprep, &mo->tm_far, mo->Kx, mo->Rp, w.mix.far_out, T.n_leaves * R,
+                  mo->slices[kCtrFar]}};
     cudaEvent_t e0, e1;
     VFMM_CUDA(cudaEventCreate(&e0));
     VFMM_CUDA(cudaEventCreate(&e1));
@@ -1798,7 +1933,7 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
             float total = 0.0f;
             for (int rep = 0; rep < 4 && rc == VFMM_OK; ++rep) {
                 cudaEventRecord(e0, st);
-                rc = split_gemm(*P, jb.a, *jb.map, jb.Kp, jb.Rp, jb.out, w.mix.err, part, jb.rows, st);
+                rc = split_gemm(*P, jb.a, *jb.map, jb.Kp, jb.Rp, jb.out, w.mix.err, part, jb.rows, jb.slices, st);
                 cudaEventRecord(e1, st);
                 if (rc != VFMM_OK) break;
                 cudaError_t e = cudaEventSynchronize(e1);

@@ -137,23 +137,26 @@ struct SplitArgs {
     int split;            // CTAs sharing one group's tables (split-K over tables)
     int drain_every;      // configurations accumulated in TMEM between two drains (exactness bound)
     int transposed;       // table rows on the M side (see near_transposed)
+    int slices;           // slices of each operand taken, kMinSlices .. kSlices (products i + j <= slices + 1)
     size_t part_stride;   // n_out_rows * Rp
 };
 
 // Accumulator of slice product (i, j): its diagonal i + j - 2; diagonals >= kNumAcc - 1 share the last.
 __host__ __device__ constexpr int acc_of(int i, int j) { return (i + j - 2) < (kNumAcc - 1) ? (i + j - 2) : (kNumAcc - 1); }
 
-// All slice products of one K block: accumulator acc_of(i, j); on the first K block of a
-// configuration the first product into each accumulator overwrites it.
-template <bool kFirst>
+// All slice products (i, j), i + j <= S + 1, of one K block: accumulator acc_of(i, j); on the
+// first K block of a configuration the first product into each accumulator overwrites it (with
+// S >= kMinSlices every accumulator gets a product).
+template <bool kFirst, int S>
 __device__ __forceinline__ void issue_unit(uint32_t tmem, uint64_t ad0, uint64_t bd0) {
     constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, kTileN);
     constexpr uint32_t A_SLICE = kTileM * 64, B_SLICE = kTileN * 64;
+    static_assert(S >= kMinSlices && S <= kSlices, "slice count");
 #pragma unroll
-    for (int i = 1; i <= kSlices; ++i)
+    for (int i = 1; i <= S; ++i)
 #pragma unroll
-        for (int j = 1; j <= kSlices; ++j) {
-            if (i + j > kSlices + 1) continue;
+        for (int j = 1; j <= S; ++j) {
+            if (i + j > S + 1) continue;
             const int acc = acc_of(i, j);
             // first product of accumulator acc in (i, j) order: i == 1 for acc < kNumAcc - 1, else (1, kNumAcc)
             const bool first_of_acc = (acc < kNumAcc - 1) ? (i == 1) : (i == 1 && j == kNumAcc);
@@ -254,15 +257,15 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
             const uint32_t T_SLICE = tr ? A_SLICE : B_SLICE, G_SLICE = tr ? B_SLICE : A_SLICE;
             if (ptid == 0) {
                 // 8 boxes of (128 or 80) table rows x 64 bytes (one per slice), SW64-swizzled by TMA
-                tc::mbar_arrive_expect_tx(full0 + 8 * s, kSlices * T_SLICE);
-                for (int sl_i = 0; sl_i < kSlices; ++sl_i)
+                tc::mbar_arrive_expect_tx(full0 + 8 * s, a.slices * T_SLICE);
+                for (int sl_i = 0; sl_i < a.slices; ++sl_i)
                     tc::tma_load_3d(sT + sl_i * T_SLICE, &tmB, 0, kb * kSlices + sl_i, cfg * a.Rp + r0, full0 + 8 * s);
             }
             // a warp instruction covers 8 rows x 64 bytes of one slice: 512 contiguous bytes of shared
             // memory (no bank conflicts) from eight 64-byte pieces of global memory
             const int lrow = (ptid & 31) >> 2, ch = ptid & 3, pw = ptid >> 5;
 #pragma unroll 4
-            for (int q = pw; q < kSlices * (G / 8); q += kProducerThreads / 32) {
+            for (int q = pw; q < a.slices * (G / 8); q += kProducerThreads / 32) {
                 const int sl_i = q / (G / 8), m = (q % (G / 8)) * 8 + lrow;
                 const int src = s_src[m];
                 const bf16* gp = a.asl + (((size_t)(src < 0 ? 0 : src) * nkb + kb) * kSlices + sl_i) * kKBlock + ch * 8;
@@ -299,8 +302,12 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
                 // offsets within the stage are added to a base descriptor
                 const uint64_t ad0 = adesc_base + ((s * STAGE) >> 4);
                 const uint64_t bd0 = adesc_base + ((s * STAGE + kSlices * A_SLICE) >> 4);
-                if (u % DU == 0) issue_unit<true>(tmem, ad0, bd0);
-                else issue_unit<false>(tmem, ad0, bd0);
+                const bool first = u % DU == 0;
+                switch (a.slices) {
+                    case 6: first ? issue_unit<true, 6>(tmem, ad0, bd0) : issue_unit<false, 6>(tmem, ad0, bd0); break;
+                    case 7: first ? issue_unit<true, 7>(tmem, ad0, bd0) : issue_unit<false, 7>(tmem, ad0, bd0); break;
+                    default: first ? issue_unit<true, 8>(tmem, ad0, bd0) : issue_unit<false, 8>(tmem, ad0, bd0); break;
+                }
                 tc::umma_commit(empty0 + 8 * s);
                 if (u % DU == DU - 1 || u == U - 1) tc::umma_commit(acc_full);
             }
@@ -684,7 +691,8 @@ __global__ void split_reduce_kernel(const float2* __restrict__ part, size_t stri
 }
 
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
-               float2* part, size_t n_out_rows, cudaStream_t st, cudaEvent_t* ev) {
+               float2* part, size_t n_out_rows, int slices, cudaStream_t st, cudaEvent_t* ev) {
+    if (slices < kMinSlices || slices > kSlices) return fail(VFMM_ERR_INTERNAL, "slice count out of range");
     if (ev) VFMM_CUDA(cudaEventRecord(ev[0], st));
     if (P.n_groups == 0) {
         if (ev) VFMM_CUDA(cudaEventRecord(ev[1], st));
@@ -710,6 +718,7 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
     a.Rp = Rp;
     a.nchunks = Rp / tile_rows;
     a.transposed = P.transposed ? 1 : 0;
+    a.slices = slices;
     // A diagonal gets at most 5 slice products per K value (i + j = d <= 6), each below 63^2, so the
     // exact FP32 accumulators stay exact while 5 * 3969 * Kp * configurations < 2^24. The shared
     // accumulator of diagonals 7..9 truncates as it grows, so a drain group also holds at most 512
@@ -826,7 +835,7 @@ int near_slices(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const
 int near_contract(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     return split_gemm(PS.near, w.fsl, mo->tm_near, mo->Kp, mo->Rp, w.out, w.err, w.part_side,
-                      (size_t)T.n_leaves * PS.R, st, w.cev ? w.cev + 0 : nullptr);
+                      (size_t)T.n_leaves * PS.R, mo->slices[kCtrNear], st, w.cev ? w.cev + 0 : nullptr);
 }
 
 }  // namespace vfmm

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
 #include <utility>
 #include <vector>
 
@@ -14,7 +16,10 @@
 
 namespace vfmm {
 
-constexpr int kSlices = 8;   // BF16 slices per operand (6-bit magnitudes, 48 bits)
+constexpr int kSlices = 8;   // BF16 slice slots per operand (6-bit magnitudes, 48 bits)
+constexpr int kMinSlices = 6;  // fewest slices a contraction may take (every accumulator gets a product)
+// contractions of the mixed form, in the order of vfmm_ops_set_slices
+enum { kCtrNear = 0, kCtrS2M = 1, kCtrM2L = 2, kCtrS2L = 3, kCtrFar = 4, kNumCtr = 5 };
 constexpr int kTileM = 128;  // target leaves per tile (TMEM lanes)
 constexpr int kKBlock = 32;  // K values per pipeline stage (64-byte rows)
 constexpr int kStages = 2;   // shared-memory stages
@@ -84,6 +89,35 @@ __device__ __forceinline__ int exp_bound(double m) {
     return (ev ? ev : 1) - 1022;
 }
 
+// Offset of (row, slice 0, k) in a sliced operand [row][K block of 32][slice][32 values].
+__device__ __forceinline__ size_t slice_at(size_t row, int Kp, int k) {
+    return ((row * (Kp / kKBlock) + k / kKBlock) * kSlices) * kKBlock + (k % kKBlock);
+}
+
+// Level exponents of the M2L operand: G(l, r) = max over the boxes b of level l and the parts k
+// (Re, Im of coefficient k / 2) of multipole row b of part_exp(value, k), kept as G + kGexpBias in
+// an unsigned array that starts at zero, so that every producer of a multipole can take the maximum
+// with atomicMax as it writes (order-independent, hence deterministic).
+constexpr unsigned kGexpBias = 1u << 20;
+
+// frexp exponent of |v| (from the bits, integer work) plus floor(k / 4); INT_MIN for +-0.
+__device__ __forceinline__ int part_exp(double v, int k) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    if ((bits << 1) == 0) return INT_MIN;
+    const int ev = (int)((bits >> 52) & 0x7FF);
+    return (ev ? ev : 1) - 1022 + (k >> 2);
+}
+
+// Warp-wide maximum of e, then one atomicMax into the biased level exponent (lanes with INT_MIN
+// contribute nothing).
+__device__ __forceinline__ void level_exp_max(int e, unsigned* slot) {
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0 && e != INT_MIN) atomicMax(slot, (unsigned)(e + (int)kGexpBias));
+}
+
+// Level exponent from its biased form.
+__device__ __forceinline__ int level_exp_value(unsigned g) { return g ? (int)g - (int)kGexpBias : 0; }
+
 // slice_fixed of 8 consecutive values (one exponent bound E) with each slice's 8 BF16 written
 // by one 16-byte store: out + i * stride for slice i (16-byte aligned).
 __device__ __forceinline__ void slice8_fixed(const double* v, int E, __nv_bfloat16* out, int stride) {
@@ -117,6 +151,11 @@ struct MixedOps {
     int* s2l_E = nullptr;     // [Rx]
     double* s2l_r0 = nullptr; // [20][kk] FP64: Re of S2L row 0
     double* m2l_r0 = nullptr; // [40][p+1] complex FP64: M2L row 0 (output coefficient 0) per offset
+    // slices taken per contraction (kCtr*): the first S of the 8 stored slices of each operand and
+    // the S(S+1)/2 products i + j <= S + 1. Defaults: the fewest that leave the error against the
+    // FP64 form unchanged on the 20-Gaussian, kinked and uniform k = 16 workloads (S2M and S2L take
+    // 7; with 7 the near field, M2L or leaf far field raise it to 2.4e-10, 2.4e-11, 3.6e-11)
+    int slices[kNumCtr] = {kSlices, 7, kSlices, 7, kSlices};
 };
 
 struct MixedWork {
@@ -127,8 +166,8 @@ struct MixedWork {
     int* err = nullptr;                   // non-zero after a bounded wait expired
     // far field
     float2* s2m_out = nullptr;            // [n_leaves][Rx]
-    int* bexp = nullptr;                  // [n_boxes * R] exponent bound of each virtual box's multipole
-    int* glev = nullptr;                  // [(depth + 1) * R] G(l, r): |coefficient k| 2^floor(k/4) < 2^G
+    unsigned* glev = nullptr;             // [(depth + 1) * R] G(l, r) + kGexpBias (0: level all zero):
+                                          // |multipole part k| 2^floor(k/4) < 2^G for parts k = 0 .. 2p+1
     void* msl = nullptr;                  // bf16 [n_boxes][kSlices][Kx]
     float2* m2l_out = nullptr;            // [n_boxes][Rx]
     double* m2l_c0 = nullptr;             // [n_boxes] Re local coefficient 0 from the V and X lists
@@ -136,7 +175,6 @@ struct MixedWork {
     void* aprep = nullptr;                // bf16 [n_far_slots][kSlices][Kx]
     int* Et = nullptr;                    // [n_leaves]
     float2* far_out = nullptr;            // [n_leaves][Rp]
-    double* scal = nullptr;               // [n_leaves * R] FP64 scalar part of u per virtual leaf
     float2* part = nullptr;               // partial sums or slab of S2M, M2L and the leaf far field
     float2* part_side = nullptr;          // partial sums or slab of the near field
     float2* part_s2l = nullptr;           // partial sums or slab of S2L
@@ -161,7 +199,7 @@ int build_contraction_plan(const std::vector<int32_t>& tgt_id,
 int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtensorMap* out);
 // ev (optional): a (start, stop) event pair recorded around the contraction and its reduction.
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
-               float2* part, size_t n_out_rows, cudaStream_t st, cudaEvent_t* ev = nullptr);
+               float2* part, size_t n_out_rows, int slices, cudaStream_t st, cudaEvent_t* ev = nullptr);
 // Partial-sum elements (float2) of the three buffers whose contractions may run at the same time:
 // [0] S2M, M2L and the leaf far field (one after another), [1] the near field, [2] S2L.
 void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t elems[3]);
@@ -179,8 +217,10 @@ void far_free(MixedOps* mo);
 // virtual box (box * R + r); f is [R][n_leaves][k^2].
 int s2m_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* Mexp,
               const MixedWork& w, cudaStream_t st);
+// exps_done: the level exponents of the non-leaf multipoles were already taken (persistent upward
+// pass); leaf multipoles always take theirs in S2M.
 int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* Mexp, const MixedWork& w,
-              cudaStream_t st);
+              bool exps_done, cudaStream_t st);
 int s2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st);
 int far_leaf_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* Mexp, const double* Lexp,
                    const MixedWork& w, cudaStream_t st);

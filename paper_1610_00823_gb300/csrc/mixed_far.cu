@@ -23,6 +23,7 @@
 #include <climits>
 #include <cmath>
 #include <complex>
+#include <string>
 #include <vector>
 
 #include "mixed.cuh"
@@ -32,10 +33,6 @@
 namespace vfmm {
 
 using bf16 = __nv_bfloat16;
-
-__device__ __forceinline__ size_t slice_at(size_t row, int Kp, int k) {
-    return ((row * (Kp / kKBlock) + k / kKBlock) * kSlices) * kKBlock + (k % kKBlock);
-}
 
 __device__ inline int exp_of(double m) {
     int e = 0;
@@ -346,7 +343,8 @@ void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o,
 __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const int32_t* __restrict__ box_of_leaf,
                                   const int32_t* __restrict__ level, double width, const double* __restrict__ f,
                                   const double* __restrict__ s2m, const float2* __restrict__ out,
-                                  const int* __restrict__ E, const int* __restrict__ Ef, double* __restrict__ Mexp) {
+                                  const int* __restrict__ E, const int* __restrict__ Ef, double* __restrict__ Mexp,
+                                  unsigned* __restrict__ glev) {
     const int vl = blockIdx.x;
     const int leaf = vl / R, r = vl - leaf * R;
     const int b = box_of_leaf[leaf];
@@ -354,6 +352,7 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
     const int P2 = 2 * (p + 1);
     double* M = Mexp + ((size_t)b * R + r) * P2;
     const double* fl = f + ((size_t)r * nleaf + leaf) * kk;
+    int e = INT_MIN;  // exponent bound of this thread's parts (level exponents of the M2L operand)
     if (threadIdx.x < 32) {
         double m = 0.0;
         for (int s = threadIdx.x; s < kk; s += 32) m += s2m[s] * fl[s];
@@ -361,6 +360,7 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
         if (threadIdx.x == 0) {
             M[0] = h * h * m;
             M[1] = 0.0;
+            e = part_exp(M[0], 0);
         }
     }
     // h^2 = wm^2 2^(2 (lw - level)): the power of two goes into the exponent bits
@@ -371,62 +371,40 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
         const float2 v = out[(size_t)vl * Rx + q];
         const double m = f2d_scaled(v.x, ef + E[q]) + f2d_scaled(v.y, ef + E[q]);
         M[2 + q] = wm == 1.0 ? m : wm * wm * m;
+        e = max(e, part_exp(M[2 + q], 2 + q));
     }
+    if (level[b] >= 2) level_exp_max(e, glev + (size_t)level[b] * R + r);
 }
 
 int s2m_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* Mexp,
               const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     VFMM_CHECK(split_gemm(PS.s2m, w.fsl, mo->tm_s2m, mo->Kp, mo->Rx, w.s2m_out, w.err, w.part,
-                          (size_t)T.n_leaves * PS.R, st, w.cev ? w.cev + 2 : nullptr));
+                          (size_t)T.n_leaves * PS.R, mo->slices[kCtrS2M], st, w.cev ? w.cev + 2 : nullptr));
     s2m_finish_kernel<<<T.n_leaves * PS.R, 128, 0, st>>>(T.n_leaves, PS.R, o.k * o.k, o.p, mo->Rx, T.box_of_leaf,
                                                          T.level, T.width, f, o.s2m, w.s2m_out, mo->s2m_E, w.Ef,
-                                                         Mexp);
+                                                         Mexp, w.glev);
     VFMM_CUDA(cudaGetLastError());
     return VFMM_OK;
 }
 
 // ---------------------------------------------------------------- M2L
-// bexp[vb] = max over coefficients k of the binary exponent of |a_k| 2^floor(k/4) (frexp
-// convention, from the bits: integer work only); INT_MIN when the multipole is zero. A warp per
-// virtual box.
-__global__ void box_exp_kernel(int64_t vb0, int64_t vb1, int P2, const double* __restrict__ Mexp,
-                               int* __restrict__ bexp) {
-    const int64_t vb = vb0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+// Level exponents of the non-leaf multipoles of levels >= 2 when no persistent pass computed them as
+// it wrote them (per-level translation launches): a warp per virtual box.
+__global__ void box_exp_kernel(const int32_t* __restrict__ boxes, int nbox, int R, int P2, const int32_t* __restrict__ level,
+                               const double* __restrict__ Mexp, unsigned* __restrict__ glev) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (vb >= vb1) return;
+    if (w >= (int64_t)nbox * R) return;
+    const int b = boxes[w / R], r = (int)(w % R);
     int e = INT_MIN;
-    for (int k = lane; k < P2; k += 32) {
-        const unsigned long long bits = (unsigned long long)__double_as_longlong(Mexp[(size_t)vb * P2 + k]);
-        if ((bits << 1) == 0) continue;  // +-0
-        const int ev = (int)((bits >> 52) & 0x7FF);
-        e = max(e, (ev ? ev : 1) - 1022 + (k >> 2));
-    }
-    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if (lane == 0) bexp[vb] = e;
-}
-
-// G[l * R + r] = max of bexp over the boxes of level l for right-hand side r (grid: levels x R).
-__global__ void level_exp_kernel(const int32_t* __restrict__ level_start, int lmin, int R,
-                                 const int* __restrict__ bexp, int* __restrict__ G) {
-    __shared__ int red[256];
-    const int l = lmin + blockIdx.x, r = blockIdx.y;
-    int e = INT_MIN;
-    for (int b = level_start[l] + threadIdx.x; b < level_start[l + 1]; b += blockDim.x)
-        e = max(e, bexp[(size_t)b * R + r]);
-    red[threadIdx.x] = e;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-    // a level whose multipoles are all zero: any scale works (every operand is 0)
-    if (threadIdx.x == 0) G[(size_t)l * R + r] = red[0] == INT_MIN ? 0 : red[0];
+    for (int k = lane; k < P2; k += 32) e = max(e, part_exp(Mexp[((size_t)b * R + r) * P2 + k], k));
+    level_exp_max(e, glev + (size_t)level[b] * R + r);
 }
 
 // One thread per 8 consecutive coefficients of a virtual box (one 16-byte store per slice).
 __global__ void multipole_slice_kernel(const int32_t* __restrict__ level, int64_t vb0, int64_t vb1, int R, int P2,
-                                       int Kx, const double* __restrict__ Mexp, const int* __restrict__ G,
+                                       int Kx, const double* __restrict__ Mexp, const unsigned* __restrict__ G,
                                        bf16* __restrict__ msl) {
     const int cpr = Kx / 8;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -436,7 +414,7 @@ __global__ void multipole_slice_kernel(const int32_t* __restrict__ level, int64_
     const int64_t b = vb / R;
     const int r = (int)(vb - b * R);
     // coefficient k is scaled by 2^(floor(k/4) - G): within a chunk of 8, k/4 takes two values
-    const int g = G[(size_t)level[b] * R + r];
+    const int g = level_exp_value(G[(size_t)level[b] * R + r]);
     double v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -453,26 +431,30 @@ __global__ void multipole_slice_kernel(const int32_t* __restrict__ level, int64_
 }
 
 int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* Mexp, const MixedWork& w,
-              cudaStream_t st) {
+              bool exps_done, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     if (T.depth < 2 || PS.m2l.n_groups == 0) return VFMM_OK;
     const int P2 = 2 * (o.p + 1), R = PS.R;
     const int64_t vb0 = (int64_t)T.level_start[2] * R, vb1 = (int64_t)T.level_start[T.depth + 1] * R;
-    box_exp_kernel<<<(unsigned)((vb1 - vb0 + 7) / 8), 256, 0, st>>>(vb0, vb1, P2, Mexp, w.bexp);
-    level_exp_kernel<<<dim3(T.depth - 1, R), 256, 0, st>>>(T.level_start_dev, 2, R, w.bexp, w.glev);
+    // leaf multipoles took their level maxima in s2m_finish_kernel, non-leaf ones in the persistent
+    // upward pass (exps_done) or here
+    const int nb0 = T.nonleaf_start[2], nnl = T.nonleaf_start[T.depth + 1] - nb0;
+    if (!exps_done && nnl > 0)
+        box_exp_kernel<<<(unsigned)(((int64_t)nnl * R + 7) / 8), 256, 0, st>>>(T.nonleaf + nb0, nnl, R, P2, T.level,
+                                                                             Mexp, w.glev);
     const int64_t n2 = (vb1 - vb0) * (mo->Kx / 8);
     multipole_slice_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(T.level, vb0, vb1, R, P2, mo->Kx, Mexp,
                                                                           w.glev, (bf16*)w.msl);
     VFMM_CUDA(cudaGetLastError());
     return split_gemm(PS.m2l, w.msl, mo->tm_m2l, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, (size_t)T.n_boxes * R,
-                      st, w.cev ? w.cev + 4 : nullptr);
+                      mo->slices[kCtrM2L], st, w.cev ? w.cev + 4 : nullptr);
 }
 
 // ---------------------------------------------------------------- S2L
 int s2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     return split_gemm(PS.s2l, w.fsl, mo->tm_s2l, mo->Kp, mo->Rx, w.s2l_out, w.err, w.part_s2l,
-                      (size_t)T.n_boxes * PS.R, st, w.cev ? w.cev + 6 : nullptr);
+                      (size_t)T.n_boxes * PS.R, mo->slices[kCtrS2L], st, w.cev ? w.cev + 6 : nullptr);
 }
 
 // ---------------------------------------------------------------- leaf far field
@@ -519,7 +501,7 @@ int far_leaf_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, co
                                                           Lexp, w.Et, (bf16*)w.aprep);
     VFMM_CUDA(cudaGetLastError());
     return split_gemm(PS.far, w.aprep, mo->tm_far, mo->Kx, mo->Rp, w.far_out, w.err, w.part,
-                      (size_t)T.n_leaves * PS.R, st, w.cev ? w.cev + 8 : nullptr);
+                      (size_t)T.n_leaves * PS.R, mo->slices[kCtrFar], st, w.cev ? w.cev + 8 : nullptr);
 }
 
 }  // namespace vfmm
@@ -538,18 +520,37 @@ extern "C" int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32
     if (ops->precision != VFMM_MIXED || !mo) return VFMM_OK;
     const PlanSet* PS = nullptr;
     VFMM_CHECK(plans_for(T, nrhs, &PS));
-    int np = 0;
-    for (int i = 1; i <= kSlices; ++i)
-        for (int j = 1; i + j <= kSlices + 1; ++j) ++np;
-    // per table of a tile and per K value: np products of 128 x 80 MACs
-    auto tc = [&](const SplitPlan& P, int Kp, int Rp) {
-        return 2.0 * (double)P.entries * (Rp / table_rows_per_tile(P.transposed)) * (double)Kp * np * kTileM * kTileN;
+    // per table of a tile and per K value: S (S + 1) / 2 products of 128 x 80 MACs
+    auto tc = [&](const SplitPlan& P, int Kp, int Rp, int ctr) {
+        const int S = mo->slices[ctr];
+        return 2.0 * (double)P.entries * (Rp / table_rows_per_tile(P.transposed)) * (double)Kp * (S * (S + 1) / 2) *
+               kTileM * kTileN;
     };
-    out[0] = tc(PS->near, mo->Kp, mo->Rp);
-    out[1] = tc(PS->m2l, mo->Kx, mo->Rx);
-    out[2] = tc(PS->far, mo->Kx, mo->Rp);
-    out[3] = tc(PS->s2l, mo->Kp, mo->Rx);
-    out[4] = tc(PS->s2m, mo->Kp, mo->Rx);
+    out[0] = tc(PS->near, mo->Kp, mo->Rp, kCtrNear);
+    out[1] = tc(PS->m2l, mo->Kx, mo->Rx, kCtrM2L);
+    out[2] = tc(PS->far, mo->Kx, mo->Rp, kCtrFar);
+    out[3] = tc(PS->s2l, mo->Kp, mo->Rx, kCtrS2L);
+    out[4] = tc(PS->s2m, mo->Kp, mo->Rx, kCtrS2M);
     out[7] = (PS->near.entry ? 1 : 0) + (PS->m2l.entry ? 2 : 0) + (PS->far.entry ? 4 : 0) + (PS->s2l.entry ? 8 : 0);
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_ops_set_slices(vfmm_ops* ops, const int32_t* slices) {
+    if (!ops || !slices) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    if (ops->precision != VFMM_MIXED || !ops->mixed) return fail(VFMM_ERR_INVALID_ARG, "not a VFMM_MIXED operator set");
+    for (int c = 0; c < kNumCtr; ++c)
+        if (slices[c] < kMinSlices || slices[c] > kSlices)
+            return fail(VFMM_ERR_INVALID_ARG, "slice counts must lie in [" + std::to_string(kMinSlices) + ", " +
+                                                  std::to_string(kSlices) + "]");
+    MixedOps* mo = (MixedOps*)ops->mixed;
+    for (int c = 0; c < kNumCtr; ++c) mo->slices[c] = slices[c];
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_ops_get_slices(const vfmm_ops* ops, int32_t* slices) {
+    if (!ops || !slices) return fail(VFMM_ERR_INVALID_ARG, "null argument");
+    if (ops->precision != VFMM_MIXED || !ops->mixed) return fail(VFMM_ERR_INVALID_ARG, "not a VFMM_MIXED operator set");
+    const MixedOps* mo = (const MixedOps*)ops->mixed;
+    for (int c = 0; c < kNumCtr; ++c) slices[c] = mo->slices[c];
     return VFMM_OK;
 }

@@ -14,6 +14,10 @@ struct vfmm_ops {
     double* s2l_t = nullptr;  // [20][kk][p+1] complex
     double* m2m_t = nullptr;  // [4][in][out] complex
     double* l2l_t = nullptr;  // [4][in][out] complex
+    // the same translations in rotated form (one real [in][out] matrix for all four child
+    // positions; the rotations are applied by the kernels, see tables.cu)
+    double* m2m_r = nullptr;  // [in][out] real
+    double* l2l_r = nullptr;  // [in][out] real
     double* m2l_t = nullptr;  // [40][in][out] complex
     double* l2t = nullptr;    // [3kk][2(p+1)] real
     // real forms for the FP64 form's gather GEMMs: rows 2l (Re), 2l + 1 (Im) of output coefficient l

@@ -14,6 +14,19 @@
 //       b_0 = a_0 log|D| + sum_n a_n (-D)^-n,  b_l = -a_0/(l D^l) + D^-l sum_n a_n (-D)^-n C(n+l-1, l)
 //   L2L (parent -> child, sigma = (z_c - z_P)/h_P):
 //       c_m = 2^-m sum_{l>=m} b_l C(l, m) sigma^(l-m)
+//
+// Rotated real form of M2M and L2L. For child position pos the shift is tau = g / 4 with the
+// Gaussian integer g = sx + i sy (sx, sy = +-1, |g|^2 = 2), so tau^(l-n) = g^l g^-n / 4^(l-n)
+// factors into a rotation of the input, a real matrix and a rotation of the output. With
+//   g^l  = sigma_l 2^floor(l/2),  sigma_l = (i s)^floor(l/2) (sx + i sy)^(l mod 2),
+//   g^-n = rho_n 2^-ceil(n/2),    rho_n = conj(sigma_n),  s = sx sy,
+// M2M is A_l = sigma_l sum_n Rm[n][l] (rho_n a_n) and L2L is c_m = rho_m sum_l Rl[l][m] (sigma_l b_l):
+//   Rm[n][l] = 2^-n C(l-1, n-1) 4^(n-l) 2^(floor(l/2) - ceil(n/2))  (n >= 1),
+//   Rm[0][l] = -4^-l / l 2^floor(l/2) (l >= 1), Rm[0][0] = 1,
+//   Rl[l][m] = 2^-m C(l, m) 4^(m-l) 2^(floor(l/2) - ceil(m/2))  (l >= m).
+// The real matrix is the same for the four positions, and rho_n, sigma_l are Gaussian integers
+// whose products with an expansion coefficient take sign changes, swaps and at most one addition
+// per component: half the FP64 work of the complex form.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -273,6 +286,24 @@ static double binom(int n, int r) {
 
 typedef std::complex<double> cd;
 
+// The real matrices of the rotated M2M and L2L ([in][out]).
+static void rotated_ops(int p, std::vector<double>& m2m_r, std::vector<double>& l2l_r) {
+    const int P = p + 1;
+    m2m_r.assign((size_t)P * P, 0.0);
+    l2l_r.assign((size_t)P * P, 0.0);
+    // 2^(floor(a / 2) - ceil(b / 2)): a is the index rotated by sigma, b the one rotated by rho
+    auto scale = [](int a, int b) { return std::ldexp(1.0, a / 2 - (b + 1) / 2); };
+    m2m_r[0] = 1.0;
+    for (int l = 1; l <= p; ++l) {
+        m2m_r[l] = -std::ldexp(1.0, -2 * l) / (double)l * scale(l, 0);
+        for (int n = 1; n <= l; ++n)
+            m2m_r[(size_t)n * P + l] = std::ldexp(binom(l - 1, n - 1), -n + 2 * (n - l)) * scale(l, n);
+    }
+    for (int m = 0; m <= p; ++m)
+        for (int l = m; l <= p; ++l)
+            l2l_r[(size_t)l * P + m] = std::ldexp(binom(l, m), -m + 2 * (m - l)) * scale(l, m);
+}
+
 static void closed_form_ops(int p, std::vector<double>& m2m_t, std::vector<double>& l2l_t, std::vector<double>& m2l_t) {
     const int P = p + 1;
     m2m_t.assign((size_t)4 * P * P * 2, 0.0);
@@ -388,6 +419,12 @@ static int create(int k, int p, int precision, cudaStream_t st, vfmm_ops* o) {
     l2t_matrix(k, p, xh, l2t);
     VFMM_CHECK(dalloc_copy(&o->m2m_t, m2m_t, st));
     VFMM_CHECK(dalloc_copy(&o->l2l_t, l2l_t, st));
+    {
+        std::vector<double> m2m_r, l2l_r;
+        rotated_ops(p, m2m_r, l2l_r);
+        VFMM_CHECK(dalloc_copy(&o->m2m_r, m2m_r, st));
+        VFMM_CHECK(dalloc_copy(&o->l2l_r, l2l_r, st));
+    }
     VFMM_CHECK(dalloc_copy(&o->m2l_t, m2l_t, st));
     VFMM_CHECK(dalloc_copy(&o->l2t, l2t, st));
     if (precision == VFMM_FP64) {
@@ -428,7 +465,8 @@ static int create(int k, int p, int precision, cudaStream_t st, vfmm_ops* o) {
 }
 
 void free_ops(vfmm_ops* o) {
-    double* ps[] = {o->xhat, o->near, o->s2m, o->s2l_t, o->m2m_t, o->l2l_t, o->m2l_t, o->l2t, o->m2l_real, o->s2l_real};
+    double* ps[] = {o->xhat,  o->near,  o->s2m, o->s2l_t,    o->m2m_t,   o->l2l_t,
+                    o->m2m_r, o->l2l_r, o->m2l_t, o->l2t, o->m2l_real, o->s2l_real};
     for (double* p : ps)
         if (p) cudaFree(p);
     mixed_free(o);

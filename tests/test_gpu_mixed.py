@@ -261,3 +261,31 @@ def test_workspace_status_reports_a_recorded_timeout(precision):
     v.volume_potential(gt, ops, f, ws=ws)  # every call clears the word
     torch.cuda.synchronize()
     v.workspace_status(ws)
+
+
+def test_slice_counts_trade_accuracy_for_products():
+    """vfmm_ops_set_slices: defaults, validation, and the error bound of each setting on a small
+    adaptive k = 16 tree (fewer slices: the truncation at 2^-6S of each operand's scale)."""
+    from paper_1610_00823_gb300._lib import VfmmError
+    from paper_1610_00823_gb300.api import solve_work
+    src = W.narrow_gaussians(8, n=2, sigma=0.01, spread=0.4)
+    gt = v.tree_build(0.0, 0.0, 1.0, 16, src, 1e-10, 9)
+    f = v.source_sample(gt, src)
+    u64 = v.volume_potential(gt, v.ops_create(16, 40, v.FP64), f)
+    ops = v.ops_create(16, 40, v.MIXED)
+    assert ops.slices == {"near": 8, "s2m": 7, "m2l": 8, "s2l": 7, "far": 8}
+    for bad in (5, 9):
+        with pytest.raises(VfmmError):
+            ops.set_slices(near=bad)
+    assert ops.slices["near"] == 8
+    with pytest.raises(VfmmError):
+        v.ops_create(16, 40, v.FP64).set_slices(near=7)
+    base = solve_work(gt, ops)["near_tc_flops"]
+    errs = {}
+    for S in (8, 7, 6):
+        ops.set_slices(**{c: S for c in ops.CONTRACTIONS})
+        u = v.volume_potential(gt, ops, f)
+        errs[S] = max(rel(u[q].cpu().numpy(), u64[q].cpu().numpy()) for q in range(3))
+        assert solve_work(gt, ops)["near_tc_flops"] == base * (S * (S + 1) // 2) / 36
+    assert errs[8] < TOL and errs[7] < 10 * TOL and errs[6] < 1e3 * TOL
+    assert errs[6] > errs[8]
