@@ -20,6 +20,8 @@ Modules:
   fmm     - the FMM passes (Section 3.1) producing u, u_x, u_y at leaf nodes
   brute   - direct quadrature of V[f~] without FMM or tables, for small trees
   interp  - the leaf interpolant v~ of computed values at arbitrary points (Section 3.1)
+  offnode - V f~ at arbitrary points from the stored expansions plus per-point near-field
+            quadrature (Sections 3.1 and 5.3)
 
 Parity status: every function is pinned by tests/test_oracle_*.py except where
 its docstring says "parity unpinned".
