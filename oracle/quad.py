@@ -105,7 +105,10 @@ def _accumulate(Wq, l1, l2):
 
 
 def self_integrals(x, c, w, k):
-    """(G, G1, G2) for one target x strictly inside S (triangles with apex x)."""
+    """(G, G1, G2) for one target x in the closed box S (triangles with apex x). On the boundary
+    of S (a point of an edge shared with a neighbour leaf) the triangle over its own edge has no
+    area and is dropped: the potential and its gradient are continuous there and the other
+    triangles give their value at the point."""
     x = np.asarray(x, dtype=np.float64)
     c = np.asarray(c, dtype=np.float64)
     hw = w / 2.0
@@ -122,8 +125,10 @@ def self_integrals(x, c, w, k):
         E = P1 - P0
         L = math.hypot(E[0], E[1])
         D = (P0[0] - x[0]) * E[1] - (P0[1] - x[1]) * E[0]
-        if D <= 0.0:
-            raise ValueError("target not strictly inside the source box")
+        if D < 0.0:
+            raise ValueError("target outside the source box")
+        if D == 0.0:
+            continue  # x on this edge's line: a triangle of zero area
         d = D / L
         t0 = min(max(float(np.dot(x - P0, E)) / (L * L), 0.0), 1.0)
         t, wt = graded_rule(t0, d / L, nt)
@@ -198,10 +203,10 @@ def outside_integrals(X, c, w, k, cs=None, ws=None, ng=None):
 
 
 def box_integrals(X, c, w, k):
-    """(G, G1, G2) for any targets X [m, 2] not on the boundary of S: [3, m, k*k]."""
+    """(G, G1, G2) for any targets X [m, 2] (the closed box S included): [3, m, k*k]."""
     X = np.asarray(X, dtype=np.float64).reshape(-1, 2)
     c = np.asarray(c, dtype=np.float64)
-    inside = (np.abs(X[:, 0] - c[0]) < w / 2.0) & (np.abs(X[:, 1] - c[1]) < w / 2.0)
+    inside = (np.abs(X[:, 0] - c[0]) <= w / 2.0) & (np.abs(X[:, 1] - c[1]) <= w / 2.0)
     out = np.zeros((3, X.shape[0], k * k))
     if np.any(~inside):
         out[:, ~inside] = outside_integrals(X[~inside], c, w, k)

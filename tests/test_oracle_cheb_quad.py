@@ -137,3 +137,22 @@ def test_box_integrals_single_basis_vs_adaptive_quadpack():
                     v, _ = integrate.dblquad(f, a, b, cc, d, args=(q,), epsabs=1e-13, epsrel=1e-12)
                     ref += v
             assert abs(G[q] - ref) < 1e-10, (x, s, q, G[q], ref)
+
+
+def test_box_integrals_on_the_boundary_of_the_source_box():
+    """Targets on an edge or a corner of the source box (a point on an edge shared by two leaves):
+    the potential and its gradient are continuous there; f = 1 against the antiderivative (at the
+    corner, where the antiderivative's 0 log 0 terms need the limit, against a point 1e-12 inside)."""
+    k = 8
+    c = np.array([0.05, -0.02])
+    w = 1.3
+    hw = w / 2
+    for x in ([c[0] + hw, c[1] + 0.1], [c[0] - hw, c[1] - 0.4], [c[0] + 0.2, c[1] - hw], [c[0] - 0.3, c[1] + hw]):
+        x = np.array(x)
+        G = quad.box_integrals(x[None, :], c, w, k).sum(axis=2)[:, 0]
+        ref = uniform_density_closed_form(x, c, w)
+        assert np.max(np.abs(G - ref)) < 2e-15, (x, G, ref)
+    corner = c + np.array([hw, hw])
+    G = quad.box_integrals(corner[None, :], c, w, k).sum(axis=2)[:, 0]
+    ref = uniform_density_closed_form(corner - 1e-12, c, w)
+    assert np.max(np.abs(G - ref)) < 1e-10, (G, ref)
