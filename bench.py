@@ -376,13 +376,15 @@ def run_batch(args):
     for tree, ops, f, out, ws in items_mx:
         stages, nl = volume_potential_profiled(tree, ops, f, out, ws, stream=stream)
         kk_m = tree.k * tree.k
-        tc += 36.0 * 2.0 * 3 * kk_m * kk_m * tree.list_len[0]  # algorithmic slice-product flops
+        sn = ops.slices["near"]
+        tc += sn * (sn + 1) / 2 * 2.0 * 3 * kk_m * kk_m * tree.list_len[0]  # algorithmic slice-product flops
         near_ms += stages.get("near_tc") or stages["near"]
         launches += nl
     peaks, peak_kind = measured_peaks()
     achieved = tc / (near_ms / 1e3) / 1e12
     roof = {"kernel": "split_gemm_kernel (near field, split-BF16 tcgen05), summed over members",
-            "flops": "algorithmic: 36 slice products x 2 x 3k^2 x k^2 per U-list entry",
+            "flops": "algorithmic: S(S+1)/2 slice products (S = the near field's slices) x 2 x 3k^2 x k^2 "
+                     "per U-list entry",
             "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
             "frac": achieved / peaks["bf16_tflops"], "traffic": None, "peak_source": "%s bf16 burst" % peak_kind,
             "flops_per_launch": tc / n_members, "ms_per_launch": near_ms / n_members,
@@ -690,7 +692,7 @@ def main():
     else:
         work = solve_work(tree, ops, nrhs)
         peak = peaks["bf16_tflops"]
-        # algorithmic work of each split contraction: the 36 BF16 slice products of every real
+        # algorithmic work of each split contraction: the S(S+1)/2 BF16 slice products (S = its slices) of every real
         # multiply-add the method needs (list entries x rows x K, no zero rows, no padding); the
         # kernels also execute zero rows of targets lacking a table in their group and padded tiles
         # ("executed")
@@ -704,7 +706,8 @@ def main():
         for name in ("near", "s2m", "m2l", "s2l", "far"):
             ms_c = stage_ms.get(name + "_tc", 0.0)
             ex = work[name + "_tc_flops"]
-            alg = 36.0 * alg_fp64eq[name] * nrhs
+            S = ops.slices[name]
+            alg = S * (S + 1) / 2 * alg_fp64eq[name] * nrhs
             if ms_c > 0 and ex > 0:
                 contractions[name] = {"tflop_algorithmic": alg / 1e12, "tflop_executed": ex / 1e12, "ms": ms_c,
                                       "tflops": alg / (ms_c / 1e3) / 1e12,
@@ -712,7 +715,8 @@ def main():
                                       "executed_tflops": ex / (ms_c / 1e3) / 1e12, "useful_fraction": alg / ex,
                                       "form": "entry-major" if int(work["entry_major_mask"]) & ENTRY_BIT.get(name, 0)
                                       else "grouped"}
-        alg_near = 36.0 * alg_fp64eq["near"] * nrhs
+        sn = ops.slices["near"]
+        alg_near = sn * (sn + 1) / 2 * alg_fp64eq["near"] * nrhs
         near_ms = stage_ms.get("near_tc") or stage_ms["near"]
         achieved = alg_near / (near_ms / 1e3) / 1e12
         # DRAM bytes read + written by this launch in one ncu capture (--set full) of this command with
@@ -724,7 +728,8 @@ def main():
         roof = {"kernel": "split_gemm_kernel (near field, split-BF16 tcgen05)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "%s bf16 burst" % peak_kind, "flops_per_launch": alg_near, "ms_per_launch": near_ms,
-                "flops": "algorithmic: 36 slice products x 2 x 3k^2 x k^2 per U-list entry",
+                "flops": "algorithmic: S(S+1)/2 slice products (S = the near field's slices) x 2 x 3k^2 x k^2 "
+                         "per U-list entry", "slices": ops.slices,
                 "executed_tflops": work["near_tc_flops"] / (near_ms / 1e3) / 1e12,
                 "fp64_equivalent_tflops": work["near_fp64eq_flops"] / (near_ms / 1e3) / 1e12,
                 "contractions": contractions}

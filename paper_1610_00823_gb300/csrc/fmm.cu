@@ -328,28 +328,93 @@ __device__ __forceinline__ void translate_pair(int mode, const double2* __restri
 // entry is read. mode 0 (M2M): in = the 4 consecutive child multipoles, out = parent multipole.
 // mode 1 (L2L): in = parent local, out = the 4 child locals (written, later added to by the
 // downward pass). Tables [pos][in][out] complex.
+// ---- rotated real form of M2M and L2L (the factorisation is written out in tables.cu): for child
+// position pos (sx = +1 when pos & 1, sy = +1 when pos & 2, s = sx sy), M2M is
+// A_l = sigma_l sum_n Rm[n][l] (rho_n a_n) and L2L is c_m = rho_m sum_l Rl[l][m] (sigma_l b_l), with
+// the Gaussian integers sigma_l = (i s)^floor(l/2) (sx + i sy)^(l mod 2) and rho_n = conj(sigma_n):
+// one real triangular matrix for the four positions, 2 FP64 FMAs per entry instead of 4.
+
+// x with its sign bit flipped when neg = 0x80000000 (integer work, no FP64 operation)
+__device__ __forceinline__ double flip_sign(double x, unsigned neg) {
+    return __hiloint2double(__double2hiint(x) ^ (int)neg, __double2loint(x));
+}
+
+// v sigma_n (sig) or v rho_n (!sig) for child position pos: sign changes and swaps, then one
+// addition per component, exact for even n (the added term is zero).
+__device__ __forceinline__ double2 rotate(double2 v, int pos, int n, bool sig) {
+    constexpr unsigned kNeg = 0x80000000u;
+    const unsigned nx = (pos & 1) ? 0u : kNeg, ny = (pos & 2) ? 0u : kNeg;
+    const unsigned nc = sig ? (nx ^ ny) : (nx ^ ny ^ kNeg);  // unit u = i c: c = s (sigma), -s (rho)
+    const unsigned ne = sig ? ny : (ny ^ kNeg);              // odd factor sx + i e: e = sy (sigma), -sy (rho)
+    double wx, wy;  // v u^floor(n/2)
+    switch ((n >> 1) & 3) {
+        case 0: wx = v.x; wy = v.y; break;
+        case 1: wx = flip_sign(v.y, nc ^ kNeg); wy = flip_sign(v.x, nc); break;
+        case 2: wx = flip_sign(v.x, kNeg); wy = flip_sign(v.y, kNeg); break;
+        default: wx = flip_sign(v.y, nc); wy = flip_sign(v.x, nc ^ kNeg); break;
+    }
+    // times (sx + i e) for odd n: (wx sx - wy e) + i (wy sx + wx e)
+    const bool odd = n & 1;
+    const double ax = odd ? flip_sign(wx, nx) : wx, bx = odd ? flip_sign(wy, ne ^ kNeg) : 0.0;
+    const double ay = odd ? flip_sign(wy, nx) : wy, by = odd ? flip_sign(wx, ne) : 0.0;
+    return make_double2(ax + bx, ay + by);
+}
+
+// One CTA per virtual box of a level, in the rotated real form (for levels with many boxes, where
+// the FP64 pipes bound the translations): the four rotated input vectors are staged in shared
+// memory, each thread takes one child position and one output row pair (j, P-1-j) of the real
+// triangular matrix Mr [in][out] (P + 1 real-times-complex multiply-adds), rotates its two rows
+// back, and M2M sums the four positions. mode 0 (M2M): in = the 4 consecutive child multipoles,
+// out = parent multipole; mode 1 (L2L): in = parent local, out = the 4 child locals.
 __global__ void __launch_bounds__(128) translate_kernel(int mode, const int32_t* __restrict__ boxes, int nbox, int R,
                                                         const int32_t* __restrict__ child0, int P,
-                                                        const double2* __restrict__ tab, double2* __restrict__ ex) {
-    extern __shared__ double2 sx[];  // [4P] in, [4P] per-position results
+                                                        const double* __restrict__ Mr, double2* __restrict__ ex) {
+    extern __shared__ double2 sx[];  // [4P] rotated inputs, [4P] per-position results
     const int bi = blockIdx.x / R, r = blockIdx.x - bi * R;  // virtual box (box, right-hand side)
     if (bi >= nbox) return;
     const int b = boxes[bi], c0 = child0[b];
     double2* s_in = sx;
     double2* s_out = sx + 4 * P;
-    if (mode == 0) {
-        for (int q = threadIdx.x; q < 4 * P; q += blockDim.x)
-            s_in[q] = ex[((size_t)(c0 + q / P) * R + r) * P + q % P];
-    } else {
-        for (int q = threadIdx.x; q < P; q += blockDim.x) s_in[q] = ex[((size_t)b * R + r) * P + q];
+    for (int q = threadIdx.x; q < 4 * P; q += blockDim.x) {
+        const int pos = q / P, n = q - pos * P;
+        const double2 v = mode == 0 ? ex[((size_t)(c0 + pos) * R + r) * P + n] : ex[((size_t)b * R + r) * P + n];
+        s_in[q] = rotate(v, pos, n, mode == 1);  // rho for M2M inputs, sigma for L2L inputs
     }
     __syncthreads();
     const int npair = (P + 1) / 2;
     for (int task = threadIdx.x; task < 4 * npair; task += blockDim.x) {
         const int pos = task / npair, j = task - pos * npair;
-        const double2* M = tab + (size_t)pos * P * P;
-        const double2* x = mode == 0 ? s_in + pos * P : s_in;
-        translate_pair(mode, M, x, P, j, s_out + pos * P);
+        const int oa = j, ob = P - 1 - j;
+        const double2* x = s_in + pos * P;
+        double ar = 0.0, ai = 0.0, br = 0.0, bi2 = 0.0;
+        if (mode == 0) {
+            for (int n = 0; n <= ob; ++n) {  // row oa takes n <= oa, row ob n <= ob
+                const double2 v = x[n];
+                if (n <= oa) {
+                    const double m = __ldg(Mr + (size_t)n * P + oa);
+                    ar = fma(m, v.x, ar);
+                    ai = fma(m, v.y, ai);
+                }
+                const double m = __ldg(Mr + (size_t)n * P + ob);
+                br = fma(m, v.x, br);
+                bi2 = fma(m, v.y, bi2);
+            }
+        } else {
+            for (int n = oa; n < P; ++n) {  // row oa takes n >= oa, row ob n >= ob
+                const double2 v = x[n];
+                const double m = __ldg(Mr + (size_t)n * P + oa);
+                ar = fma(m, v.x, ar);
+                ai = fma(m, v.y, ai);
+                if (n >= ob) {
+                    const double mb = __ldg(Mr + (size_t)n * P + ob);
+                    br = fma(mb, v.x, br);
+                    bi2 = fma(mb, v.y, bi2);
+                }
+            }
+        }
+        // rotate back: sigma for M2M outputs, rho for L2L outputs
+        s_out[pos * P + oa] = rotate(make_double2(ar, ai), pos, oa, mode == 0);
+        if (ob != oa) s_out[pos * P + ob] = rotate(make_double2(br, bi2), pos, ob, mode == 0);
     }
     __syncthreads();
     if (mode == 0) {
@@ -446,8 +511,8 @@ static int sm_count() {
     return n > 0 ? n : 1;
 }
 
-static void launch_translate(int mode, const DeviceTree& T, int level, int R, int P, const double* tab, double* ex,
-                             int* err, cudaStream_t st) {
+static void launch_translate(int mode, const DeviceTree& T, int level, int R, int P, const double* tab,
+                             const double* tab_r, double* ex, int* err, cudaStream_t st) {
     const int nbox = T.nonleaf_start[level + 1] - T.nonleaf_start[level];
     if (nbox <= 0) return;
     const size_t smem = (size_t)(4 * P * P + 8 * P) * sizeof(double2);
@@ -469,8 +534,7 @@ static void launch_translate(int mode, const DeviceTree& T, int level, int R, in
     }
     const int threads = std::min(128, ((4 * ((P + 1) / 2) + 31) / 32) * 32);
     translate_kernel<<<(unsigned)nbox * R, threads, (size_t)8 * P * sizeof(double2), st>>>(
-        mode, T.nonleaf + T.nonleaf_start[level], nbox, R, T.child0, P, reinterpret_cast<const double2*>(tab),
-        reinterpret_cast<double2*>(ex));
+        mode, T.nonleaf + T.nonleaf_start[level], nbox, R, T.child0, P, tab_r, reinterpret_cast<double2*>(ex));
 }
 
 // ---------------------------------------------------------------- downward pass (one CTA per box)
@@ -614,20 +678,16 @@ __global__ void down_mixed_kernel(DownArgs d) {
 }
 
 // ---------------------------------------------------------------- persistent tree passes
-// One launch walks all levels: the translations are cut into one-warp units (a block of row pairs
-// of one virtual box), numbered level by level, and warps take the next unit number from an atomic
-// counter, so units spread over whatever SMs the kernel holds. There is no barrier between levels:
-// a unit waits (bounded) only for the expansions it reads, through per-box readiness counters, so a
-// box starts as soon as its children (M2M) or its parent (L2L) are done. Every unit's inputs come
-// from units with smaller numbers, and numbers are taken in increasing order, so the unfinished unit
-// with the smallest number is always held by a running warp (a warp holds at most its current unit
-// and the next one it took, which has a larger number) and can proceed: no CTA needs another to be
-// resident, and the kernel starts as soon as any SM is free. Data written by other CTAs are read
-// through L2 (ld.global.cg).
-// Four warps per CTA (one per SM sub-partition) and up to four CTAs per SM: the units a CTA takes
-// one after another land on different sub-partitions, and CTAs are spread over the SMs first.
-constexpr int kPassThreads = 128;
-constexpr int kPassCtasPerSm = 4;
+// One cooperative launch walks all levels: the translations are cut into one-warp units (a row pair
+// of one virtual box) dealt over the warps of every CTA, and the 4 position tables sit in shared
+// memory for the whole pass. There is no barrier between levels: a unit waits (bounded) only for
+// the expansions it reads, through per-box readiness counters, so a box starts as soon as its
+// children (M2M) or its parent (L2L) are done. Every unit's inputs are produced by units that come
+// earlier in the global unit order, and each warp takes its units in that order, so the earliest
+// unfinished unit can always proceed (all CTAs are resident: cooperative launch). Data written by
+// other CTAs are read through L2 (ld.global.cg).
+constexpr int kPassThreads = 512;
+constexpr int kPassMaxCtas = 152;  // largest pass grid (measured against smaller grids on the 20-Gaussian tree)
 
 // Readiness counters of the dataflow tree passes: ready[vb] counts the units that have written
 // their part of virtual box vb's expansion (M2M: the box's own multipole; L2L: the box's local), and
@@ -640,13 +700,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Next unit of a pass for this warp: one atomic increment by lane 0, broadcast to the warp.
-__device__ __forceinline__ int next_unit(unsigned* counter, int lane) {
-    unsigned u = 0;
-    if (lane == 0) u = atomicAdd(counter, 1u);
-    return (int)__shfl_sync(0xffffffffu, u, 0);
 }
 
 // Waits (bounded) until *flag >= need. Gives up, recording code 6 in the status word, when the
@@ -662,76 +715,81 @@ __device__ bool wait_ready(const unsigned* flag, unsigned need, int* err) {
 }
 
 
-// ---- rotated real translations (the factorisation is written out in tables.cu): for child
-// position pos (sx = +1 when pos & 1, sy = +1 when pos & 2, s = sx sy), M2M is
-// A_l = sigma_l sum_n Rm[n][l] (rho_n a_n) and L2L is c_m = rho_m sum_l Rl[l][m] (sigma_l b_l), with
-// the Gaussian integers sigma_l = (i s)^floor(l/2) (sx + i sy)^(l mod 2) and rho_n = conj(sigma_n).
-
-// x with its sign bit flipped when neg = 0x80000000 (integer work, no FP64 operation)
-__device__ __forceinline__ double flip_sign(double x, unsigned neg) {
-    return __hiloint2double(__double2hiint(x) ^ (int)neg, __double2loint(x));
-}
-
-// v sigma_n (sig) or v rho_n (!sig) for child position pos: sign changes and swaps, then one
-// addition per component, exact for even n (the added term is zero).
-__device__ __forceinline__ double2 rotate(double2 v, int pos, int n, bool sig) {
-    constexpr unsigned kNeg = 0x80000000u;
-    const unsigned nx = (pos & 1) ? 0u : kNeg, ny = (pos & 2) ? 0u : kNeg;
-    const unsigned nc = sig ? (nx ^ ny) : (nx ^ ny ^ kNeg);  // unit u = i c: c = s (sigma), -s (rho)
-    const unsigned ne = sig ? ny : (ny ^ kNeg);              // odd factor sx + i e: e = sy (sigma), -sy (rho)
-    double wx, wy;  // v u^floor(n/2)
-    switch ((n >> 1) & 3) {
-        case 0: wx = v.x; wy = v.y; break;
-        case 1: wx = flip_sign(v.y, nc ^ kNeg); wy = flip_sign(v.x, nc); break;
-        case 2: wx = flip_sign(v.x, kNeg); wy = flip_sign(v.y, kNeg); break;
-        default: wx = flip_sign(v.y, nc); wy = flip_sign(v.x, nc ^ kNeg); break;
+// Loads the 4 position tables into shared memory (bulk copy); one decision for the whole CTA.
+__device__ bool load_tables(double2* sT, const double2* tab, int P, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int no_abort;
+    const uint32_t bar_a = tc::smem_u32(&bar);
+    const uint32_t bytes = (uint32_t)(4 * P * P) * sizeof(double2);
+    if (threadIdx.x == 0) {
+        no_abort = 0;
+        tc::mbar_init(bar_a, 1);
+        tc::mbar_fence_init();
     }
-    // times (sx + i e) for odd n: (wx sx - wy e) + i (wy sx + wx e)
-    const bool odd = n & 1;
-    const double ax = odd ? flip_sign(wx, nx) : wx, bx = odd ? flip_sign(wy, ne ^ kNeg) : 0.0;
-    const double ay = odd ? flip_sign(wy, nx) : wy, by = odd ? flip_sign(wx, ne) : 0.0;
-    return make_double2(ax + bx, ay + by);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::mbar_arrive_expect_tx(bar_a, bytes);
+        constexpr uint32_t kChunk = 32768;
+        for (uint32_t off = 0; off < bytes; off += kChunk)
+            tc::bulk_copy_g2s(tc::smem_u32(sT) + off, reinterpret_cast<const char*>(tab) + off,
+                              min(kChunk, bytes - off), bar_a);
+    }
+    const bool landed = tc::mbar_wait(bar_a, 0, &no_abort);
+    if (!__syncthreads_and(landed)) {
+        if (threadIdx.x == 0 && err) atomicExch(err, 5);
+        settle_bulk_copy(bar_a, &no_abort);
+        return false;
+    }
+    return true;
 }
 
-// Lane roles of a translation unit: position pos = lane / 8, row pair j = 4 jb + (lane / 2) % 4 of
-// the unit's block jb, input half ks = lane % 2 (inputs n = ks, ks + 2, ...).
-constexpr int kPairsPerUnit = 4;
-
-// One unit: row pairs 4 jb .. 4 jb + 3 (rows j and P-1-j) of the four child positions' rotated
-// real translations, xs = the four rotated input vectors [4][P] staged in shared memory, M the
-// real matrix [in][out]. mode 0 (M2M: row o takes inputs n <= o), 1 (L2L: row m takes n >= m).
-// Returns the two row sums (complex, still rotated) summed over the lane's input half and its
-// partner's, in both lanes of the pair.
-__device__ __forceinline__ void translate_rows(int mode, const double* __restrict__ M, const double2* xs, int P, int j,
-                                               int lane, double2& ra, double2& rb) {
-    const int pos = lane >> 3, ks = lane & 1;
-    const int oa = j, ob = P - 1 - j;  // oa <= ob when j < (P + 1) / 2
-    const bool valid = j < (P + 1) / 2;
-    const bool two = valid && oa != ob;
-    const double2* x = xs + pos * P;
+// One output row pair (j, P-1-j) of one virtual box's four child-position translations, computed
+// by one warp: lane (pos, ks) = (lane / 8, lane % 8) takes position pos and the inputs
+// n = ks, ks + 8, ... of its triangular ranges (M2M row o takes n <= o, L2L row m takes n >= m), so
+// the 4 (P + 1) complex multiply-adds of a row pair spread over the 32 lanes. All of a lane's
+// inputs are loaded before its first multiply-add. Shuffles then sum the 8 input slices of each
+// position, and for M2M (mode 0) the four positions as well, in a fixed order (the results are
+// deterministic). Tables [pos][in][out] complex in shared memory: the 8 lanes of a quarter warp read
+// rows n one apart (stride P complex = 4P banks), which never share a bank. Inputs: mode 0, child
+// pos at x + pos * xs; mode 1, the parent local at x. Returns the row-a and row-b sums: mode 0 in
+// every lane, summed over the positions; mode 1 in every lane of position pos, for that position.
+__device__ __forceinline__ void translate_warp(int mode, const double2* __restrict__ sT, const double2* x,
+                                               size_t xs, int P, int j, int lane, double2& ra, double2& rb) {
+    const int pos = lane >> 3, ks = lane & 7;
+    const int oa = j, ob = P - 1 - j;  // oa <= ob
+    const double2* M = sT + (size_t)pos * P * P;
+    const double2* xp = mode == 0 ? x + pos * xs : x;
+    double2 v[8];  // P <= 64
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int n = ks + 8 * i;
+        v[i] = (n < P && (mode != 0 || n <= ob)) ? __ldcg(xp + n) : make_double2(0.0, 0.0);
+    }
     double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
-    if (valid) {
-        // M2M: n = ks .. ob; L2L: n = oa .. P-1 (first n of the lane's parity)
-        const int n0 = mode == 0 ? ks : oa + ((ks - oa) & 1);
-        const int n1 = mode == 0 ? ob : P - 1;
-        for (int n = n0; n <= n1; n += 2) {
-            const double2 v = x[n];
-            if (mode == 0 ? n <= oa : true) {
-                const double m = M[(size_t)n * P + oa];
-                ar = fma(m, v.x, ar);
-                ai = fma(m, v.y, ai);
-            }
-            if (two && (mode == 0 || n >= ob)) {
-                const double m = M[(size_t)n * P + ob];
-                br = fma(m, v.x, br);
-                bi = fma(m, v.y, bi);
-            }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int n = ks + 8 * i;
+        if (n >= P || (mode == 0 && n > ob)) break;
+        if (mode == 0 ? n <= oa : n >= oa) {
+            const double2 m = M[(size_t)n * P + oa];
+            ar = fma(m.x, v[i].x, fma(-m.y, v[i].y, ar));
+            ai = fma(m.x, v[i].y, fma(m.y, v[i].x, ai));
+        }
+        if (ob != oa && (mode == 0 || n >= ob)) {
+            const double2 m = M[(size_t)n * P + ob];
+            br = fma(m.x, v[i].x, fma(-m.y, v[i].y, br));
+            bi = fma(m.x, v[i].y, fma(m.y, v[i].x, bi));
         }
     }
-    ar += __shfl_xor_sync(0xffffffffu, ar, 1);
-    ai += __shfl_xor_sync(0xffffffffu, ai, 1);
-    br += __shfl_xor_sync(0xffffffffu, br, 1);
-    bi += __shfl_xor_sync(0xffffffffu, bi, 1);
+    const int lim = mode == 0 ? 32 : 8;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        if (off >= lim) break;
+        ar += __shfl_xor_sync(0xffffffffu, ar, off);
+        ai += __shfl_xor_sync(0xffffffffu, ai, off);
+        br += __shfl_xor_sync(0xffffffffu, br, off);
+        bi += __shfl_xor_sync(0xffffffffu, bi, off);
+    }
     ra = make_double2(ar, ai);
     rb = make_double2(br, bi);
 }
@@ -742,181 +800,116 @@ struct PassArgs {
     const int32_t* nonleaf_start;  // device, depth + 2
     const int32_t* level_start;    // device, depth + 2
     const int32_t* child0;
-    const double* tab;     // real matrix of the rotated translation [in][out]
+    const double2* tab;    // the 4 position tables [pos][in][out] complex
     double2* ex;           // Mexp (upward) or Lexp (downward), [n_boxes * R][P] complex
     const int32_t* parent;
     unsigned int* ready;   // [n_boxes * R] readiness counters, zero at launch
-    unsigned int* work;    // unit counter, zero at launch
     unsigned* glev;        // upward pass, mixed form: biased level exponents of the M2L operand (or null)
     const int32_t* level;
     int* err;
 };
 
-// The work of a pass is a list of units (a block of kPairsPerUnit row pairs of one virtual box),
-// level by level; warps take them in order from the pass's counter, so the units of a level spread
-// over the SMs and sub-partitions the kernel holds (this part retires about 2 FP64 FMAs per clock
-// per SM, so a unit's FP64 work is best alone on its sub-partition).
+// The work of a pass is a list of units (a row pair of one virtual box), level by level; warp w of
+// CTA c takes units slot, slot + nslots, ... with slot = w * gridDim.x + c, so that the units of a
+// level spread over the SMs first (this part retires about 2 FP64 FMAs per clock per SM).
 constexpr int kPassWarps = kPassThreads / 32;
 
-// Shared memory of a pass: the real matrix [P][P], then per warp the staged inputs [4][P] complex.
-__host__ __device__ inline size_t pass_smem_bytes(int P) {
-    return ((size_t)P * P * sizeof(double) + 15) / 16 * 16 + (size_t)kPassWarps * 4 * P * sizeof(double2);
-}
-
-// Copies the real matrix into shared memory (plain loads: 8 P^2 bytes).
-__device__ __forceinline__ void load_real_table(double* sM, const double* tab, int P) {
-    for (int q = threadIdx.x; q < P * P; q += blockDim.x) sM[q] = tab[q];
-    __syncthreads();
-}
+// Shared memory of a pass: the 4 position tables [4][P][P] complex.
+__host__ __device__ inline size_t pass_smem_bytes(int P) { return (size_t)4 * P * P * sizeof(double2); }
 
 // All M2M levels, finest parents first (the global unit order).
-__global__ void __launch_bounds__(kPassThreads, kPassCtasPerSm) upward_pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(kPassThreads, 1) upward_pass_kernel(PassArgs a) {
     extern __shared__ __align__(128) unsigned char pass_raw[];
     const int P = a.P, R = a.R;
-    double* sM = reinterpret_cast<double*>(pass_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pos = lane >> 3;
-    double2* xs = reinterpret_cast<double2*>(pass_raw + ((size_t)P * P * sizeof(double) + 15) / 16 * 16) +
-                  (size_t)warp * 4 * P;
-    load_real_table(sM, a.tab, P);
-    const int npair = (P + 1) / 2, nu = (npair + kPairsPerUnit - 1) / kPairsPerUnit;  // units per box
+    double2* sT = reinterpret_cast<double2*>(pass_raw);
+    if (!load_tables(sT, a.tab, P, a.err)) return;
+    const int lane = threadIdx.x & 31;
+    const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassWarps;
+    const unsigned npair = (unsigned)(P + 1) / 2;
     int l = a.depth - 1, lbase = 0;
-    int lunits = l >= 2 ? (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * nu : 0;
-    for (int u = next_unit(a.work, lane);;) {
+    int lunits = l >= 2 ? (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * (int)npair : 0;
+    for (int u = slot;; u += nslots) {
         while (l >= 2 && u >= lbase + lunits) {
             lbase += lunits;
-            if (--l >= 2) lunits = (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * nu;
+            if (--l >= 2) lunits = (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * (int)npair;
         }
         if (l < 2) break;
-        const int next = next_unit(a.work, lane);  // taken now: its latency overlaps this unit
         const int lu = u - lbase;
-        const int vi = lu / nu, jb = lu - vi * nu;
+        const int vi = lu / (int)npair, j = lu - vi * (int)npair;
         const int bi = vi / R, r = vi - bi * R;
         const int b = a.nonleaf[a.nonleaf_start[l] + bi], c0 = a.child0[b];
         // the non-leaf children's multipoles must be complete (leaf multipoles come from S2M)
         bool ok = true;
         if (lane < 4 && a.child0[c0 + lane] >= 0)
-            ok = wait_ready(a.ready + (size_t)(c0 + lane) * R + r, (unsigned)nu, a.err);
+            ok = wait_ready(a.ready + (size_t)(c0 + lane) * R + r, npair, a.err);
         if (!__all_sync(0xffffffffu, ok)) return;
         __syncwarp();
-        // stage the four children's multipoles, rotated by rho (children are consecutive boxes); all
-        // loads are issued before the first is used (4P <= 256: at most 8 per lane)
-        {
-            double2 v[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int q = lane + 32 * i, p = q / P;
-                if (q < 4 * P) v[i] = __ldcg(a.ex + ((size_t)(c0 + p) * R + r) * P + (q - p * P));
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int q = lane + 32 * i, p = q / P;
-                if (q < 4 * P) xs[q] = rotate(v[i], p, q - p * P, false);
-            }
-        }
-        __syncwarp();
-        const int j = kPairsPerUnit * jb + ((lane >> 1) & 3);
         double2 ra, rb;
-        translate_rows(0, sM, xs, P, j, lane, ra, rb);
-        // rotate the rows back (sigma) and sum the four positions
-        ra = rotate(ra, pos, j, true);
-        rb = rotate(rb, pos, P - 1 - j, true);
-#pragma unroll
-        for (int off = 8; off < 32; off <<= 1) {
-            ra.x += __shfl_xor_sync(0xffffffffu, ra.x, off);
-            ra.y += __shfl_xor_sync(0xffffffffu, ra.y, off);
-            rb.x += __shfl_xor_sync(0xffffffffu, rb.x, off);
-            rb.y += __shfl_xor_sync(0xffffffffu, rb.y, off);
-        }
-        int e = INT_MIN;
-        if (lane < 8 && (lane & 1) == 0 && j < npair) {
+        // the four children are consecutive boxes: position pos is virtual box (c0 + pos) R + r
+        translate_warp(0, sT, a.ex + ((size_t)c0 * R + r) * P, (size_t)R * P, P, j, lane, ra, rb);
+        if (lane == 0) {
             double2* out = a.ex + ((size_t)b * R + r) * P;
             out[j] = ra;
-            e = max(part_exp(ra.x, 2 * j), part_exp(ra.y, 2 * j + 1));
+            int e = max(part_exp(ra.x, 2 * j), part_exp(ra.y, 2 * j + 1));
             if (j != P - 1 - j) {
                 out[P - 1 - j] = rb;
                 e = max(e, max(part_exp(rb.x, 2 * (P - 1 - j)), part_exp(rb.y, 2 * (P - 1 - j) + 1)));
             }
-            __threadfence();
+            // the M2L operand's level exponent (mixed form), taken as the coefficients are written
+            if (a.glev && e != INT_MIN) atomicMax(a.glev + (size_t)l * R + r, (unsigned)(e + (int)kGexpBias));
+            red_release_add_u32(a.ready + (size_t)b * R + r, 1u);
         }
-        if (a.glev) level_exp_max(e, a.glev + (size_t)l * R + r);
-        __syncwarp();
-        if (lane == 0) red_release_add_u32(a.ready + (size_t)b * R + r, 1u);
-        __syncwarp();  // the staging area is rewritten by the next unit
-        u = next;
     }
 }
 
 // Mixed form, all downward levels: level 2 boxes combine their M2L/S2L terms (one warp unit per
 // virtual box); below, each non-leaf parent's local is shifted to its 4 children (L2L) and each
-// child's terms are added.
-__global__ void __launch_bounds__(kPassThreads, kPassCtasPerSm) downward_pass_kernel(PassArgs a, DownArgs d) {
+// child's terms are added (row-pair units).
+__global__ void __launch_bounds__(kPassThreads, 1) downward_pass_kernel(PassArgs a, DownArgs d) {
     extern __shared__ __align__(128) unsigned char pass_raw[];
     const int P = a.P, R = a.R;
-    double* sM = reinterpret_cast<double*>(pass_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pos = lane >> 3;
-    double2* xs = reinterpret_cast<double2*>(pass_raw + ((size_t)P * P * sizeof(double) + 15) / 16 * 16) +
-                  (size_t)warp * 4 * P;
-    load_real_table(sM, a.tab, P);
-    const int npair = (P + 1) / 2, nu = (npair + kPairsPerUnit - 1) / kPairsPerUnit;
+    double2* sT = reinterpret_cast<double2*>(pass_raw);
+    if (!load_tables(sT, a.tab, P, a.err)) return;
+    const int lane = threadIdx.x & 31, pos = lane >> 3;
+    const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassWarps;
+    const unsigned npair = (unsigned)(P + 1) / 2;
     const int b2 = a.level_start[2], n2 = (a.level_start[3] - b2) * R;  // level-2 units
     int l = 3, lbase = n2;
-    int lunits = l <= a.depth ? (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * nu : 0;
-    for (int u = next_unit(a.work, lane), next = 0;; u = next) {
-        next = next_unit(a.work, lane);  // taken now: its latency overlaps this unit
+    int lunits = l <= a.depth ? (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * (int)npair : 0;
+    for (int u = slot;; u += nslots) {
         if (u < n2) {
-            // level 2: no parent term; the whole local at once, published as all nu units
+            // level 2: no parent term; the whole local at once, published as npair contributions
             const int64_t vb = (int64_t)b2 * R + u;
             const int b = (int)(vb / R), r = (int)(vb % R);
             for (int t = lane; t < P; t += 32) a.ex[(size_t)vb * P + t] = combine_local(d, 2, b, r, t, 0.0, 0.0);
             __threadfence();
             __syncwarp();
-            if (lane == 0) red_release_add_u32(a.ready + vb, (unsigned)nu);
+            if (lane == 0) red_release_add_u32(a.ready + vb, npair);
             continue;
         }
         while (l <= a.depth && u >= lbase + lunits) {
             lbase += lunits;
-            if (++l <= a.depth) lunits = (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * nu;
+            if (++l <= a.depth) lunits = (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * (int)npair;
         }
         if (l > a.depth) break;
         const int lu = u - lbase;
-        const int vi = lu / nu, jb = lu - vi * nu;
+        const int vi = lu / (int)npair, j = lu - vi * (int)npair;
         const int bi = vi / R, r = vi - bi * R;
         const int b = a.nonleaf[a.nonleaf_start[l - 1] + bi], c0 = a.child0[b];
         // the parent's local must be complete
         bool ok = true;
-        if (lane == 0) ok = wait_ready(a.ready + (size_t)b * R + r, (unsigned)nu, a.err);
+        if (lane == 0) ok = wait_ready(a.ready + (size_t)b * R + r, npair, a.err);
         if (!__all_sync(0xffffffffu, ok)) return;
         __syncwarp();
-        // stage the parent's local rotated for each child position (sigma): P <= 64 values, at most
-        // two loads per lane, issued before use; each lane rotates its values for all four positions
-        {
-            const double2* x = a.ex + ((size_t)b * R + r) * P;
-            const double2 v0 = lane < P ? __ldcg(x + lane) : make_double2(0.0, 0.0);
-            const double2 v1 = lane + 32 < P ? __ldcg(x + lane + 32) : make_double2(0.0, 0.0);
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                if (lane < P) xs[p * P + lane] = rotate(v0, p, lane, true);
-                if (lane + 32 < P) xs[p * P + lane + 32] = rotate(v1, p, lane + 32, true);
-            }
-        }
-        __syncwarp();
-        const int j = kPairsPerUnit * jb + ((lane >> 1) & 3), mb = P - 1 - j;
         double2 ra, rb;
-        translate_rows(1, sM, xs, P, j, lane, ra, rb);
-        if ((lane & 1) == 0 && j < npair) {  // one lane per (child, row pair): rotate back, add the child's terms
-            const int c = c0 + pos;
-            ra = rotate(ra, pos, j, false);
+        translate_warp(1, sT, a.ex + ((size_t)b * R + r) * P, 0, P, j, lane, ra, rb);
+        if ((lane & 7) == 0) {  // one lane per child position: add the child's own terms
+            const int c = c0 + pos, mb = P - 1 - j;
             double2* out = a.ex + ((size_t)c * R + r) * P;
             out[j] = combine_local(d, l, c, r, j, ra.x, ra.y);
-            if (j != mb) {
-                rb = rotate(rb, pos, mb, false);
-                out[mb] = combine_local(d, l, c, r, mb, rb.x, rb.y);
-            }
-            __threadfence();
+            if (j != mb) out[mb] = combine_local(d, l, c, r, mb, rb.x, rb.y);
+            red_release_add_u32(a.ready + (size_t)c * R + r, 1u);
         }
-        __syncwarp();
-        if ((lane & 7) == 0) red_release_add_u32(a.ready + (size_t)(c0 + pos) * R + r, 1u);
-        __syncwarp();
     }
 }
 
@@ -1098,9 +1091,7 @@ struct Workspace {
     double* xslab;      // FP64 form: per X entry S2L rows
     const PlanSet* ps;  // split-contraction plans for the folded right-hand sides (mixed form)
     unsigned int* ready; // [2][n_boxes * R] readiness counters of the persistent tree passes, then
-                         // [(depth + 1) R] biased level exponents (mixed form), then the two passes'
-                         // unit counters (work)
-    unsigned int* work;
+                         // [(depth + 1) R] biased level exponents (mixed form)
     size_t ready_words;
     double* Mexp;
     double* Lexp;
@@ -1140,12 +1131,11 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
         // readiness counters of the persistent passes, then the mixed form's biased level exponents:
         // one zeroing at the start of a solve covers both
         double* g = nullptr;
-        const size_t words = 2 * (size_t)T.n_boxes * R + (size_t)(T.depth + 1) * R + 2;
+        const size_t words = 2 * (size_t)T.n_boxes * R + (size_t)(T.depth + 1) * R;
         take(&g, (words + 1) / 2);
         if (w) {
             w->ready = reinterpret_cast<unsigned int*>(g);
             w->ready_words = words;
-            w->work = w->ready + words - 2;
         }
     }
     take(w ? &w->slab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
@@ -1306,7 +1296,7 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     d.Rx = mo ? mo->Rx : 0;
 }
 
-// Persistent passes (one launch for all levels) when every level is small enough that
+// Persistent passes (one cooperative launch for all levels) when every level is small enough that
 // per-level launches would mostly wait on launch latency; larger levels keep one launch per level.
 static bool use_passes(const DeviceTree& T, int R, int P) {
     const size_t smem = pass_smem_bytes(P);
@@ -1330,13 +1320,23 @@ static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, 
     int per_sm = 0;
     VFMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPassThreads, smem));
     if (per_sm < 1) return fail(VFMM_ERR_INTERNAL, "tree pass kernel does not fit on an SM");
-    // up to kPassCtasPerSm CTAs per SM, fewer when the widest level has fewer units than warps; an
-    // ordinary launch: warps take units from a counter in order, so CTAs that start late (SMs still
-    // busy with another stream's kernels) only find fewer units left
-    const int units = widest_items * (((P + 1) / 2 + kPairsPerUnit - 1) / kPairsPerUnit);
-    const int grid = std::max(1, std::min(std::min(per_sm, kPassCtasPerSm) * sm_count(), (units + kPassWarps - 1) / kPassWarps));
-    kernel<<<grid, kPassThreads, smem, st>>>(args...);
-    VFMM_CUDA(cudaGetLastError());
+    // A cooperative launch: a unit may wait for units held by any other CTA, so all CTAs must be
+    // resident. Enough CTAs for one unit per warp at the widest level, at most one per SM and at
+    // most kPassMaxCtas: a smaller grid starts sooner when another stream's kernels still hold SMs
+    // (the launch waits until the whole grid fits).
+    const int units = widest_items * ((P + 1) / 2);
+    const int grid = std::max(1, std::min(std::min(per_sm * sm_count(), kPassMaxCtas), (units + kPassWarps - 1) / kPassWarps));
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kPassThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    VFMM_CUDA(cudaLaunchKernelEx(&cfg, kernel, args...));
     return VFMM_OK;
 }
 
@@ -1467,11 +1467,10 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.nonleaf_start = T.nonleaf_start_dev;
         pa.level_start = T.level_start_dev;
         pa.child0 = T.child0;
-        pa.tab = o.m2m_r;
+        pa.tab = reinterpret_cast<const double2*>(o.m2m_t);
         pa.ex = reinterpret_cast<double2*>(w.Mexp);
         pa.parent = T.parent;
         pa.ready = w.ready;
-        pa.work = w.work;
         pa.glev = mixed ? w.mix.glev : nullptr;
         pa.level = T.level;
         pa.err = w.mix.err;
@@ -1480,7 +1479,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
     } else {
         for (int l = T.depth - 1; l >= 2; --l) {
             if (T.nonleaf_start[l + 1] > T.nonleaf_start[l]) ++launches;
-            launch_translate(0, T, l, R, P, o.m2m_t, w.Mexp, w.mix.err, st);
+            launch_translate(0, T, l, R, P, o.m2m_t, o.m2m_r, w.Mexp, w.mix.err, st);
         }
     }
     mark(se, ST_M2M, true, st);
@@ -1550,11 +1549,10 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.nonleaf_start = T.nonleaf_start_dev;
         pa.level_start = T.level_start_dev;
         pa.child0 = T.child0;
-        pa.tab = o.l2l_r;
+        pa.tab = reinterpret_cast<const double2*>(o.l2l_t);
         pa.ex = reinterpret_cast<double2*>(w.Lexp);
         pa.parent = T.parent;
         pa.ready = w.ready + (size_t)T.n_boxes * R;
-        pa.work = w.work + 1;
         pa.glev = nullptr;
         pa.level = T.level;
         pa.err = w.mix.err;
@@ -1568,7 +1566,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         if (n <= 0) continue;
         if (l >= 3) {
             // L2L for every box of level l (children of the non-leaf boxes of level l - 1)
-            launch_translate(1, T, l - 1, R, P, o.l2l_t, w.Lexp, w.mix.err, st);
+            launch_translate(1, T, l - 1, R, P, o.l2l_t, o.l2l_r, w.Lexp, w.mix.err, st);
             ++launches;
         }
         ++launches;
@@ -1740,6 +1738,18 @@ int vfmm::volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const dou
     w.fork = fork;
     if (reset) VFMM_CHECK(reset_status(w, st));
     return solve_all(tree->t, *ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, w, st);
+}
+
+int vfmm::solve_expansions(const vfmm_tree* tree, const vfmm_ops* ops, const void* workspace_dev,
+                           size_t workspace_bytes, const double** Mexp, const double** Lexp, int* R) {
+    Workspace w;
+    size_t need = 0;
+    VFMM_CHECK(layout(tree->t, *ops, 1, false, &w, (char*)const_cast<void*>(workspace_dev), &need));
+    if (workspace_bytes < need) return fail(VFMM_ERR_WORKSPACE, "workspace smaller than a one-right-hand-side solve's");
+    *Mexp = w.Mexp;
+    *Lexp = w.Lexp;
+    *R = 1;
+    return VFMM_OK;
 }
 
 extern "C" int vfmm_workspace_status(const void* workspace_dev) {
@@ -1950,6 +1960,36 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
         }
         P->split = *best_sp;
     };
+    // persistent CTAs (one per SM, each walking several work items) against one CTA per item, for a
+    // contraction with more items than SMs; the faster is kept
+    auto time_ctas = [&](const Job& jb, SplitPlan* P, float2* part) {
+        const int nchunks = jb.Rp / table_rows_per_tile(P->transposed, jb.Rp);
+        const long long items = (long long)P->n_groups * (P->entry ? 1 : P->split) * nchunks;
+        const int sms = sm_count();
+        if (items <= sms) return;
+        float best = -1.0f;
+        int best_c = P->ctas;
+        for (int c : {0, sms}) {
+            P->ctas = c;
+            float total = 0.0f;
+            for (int rep = 0; rep < 4 && rc == VFMM_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                rc = split_gemm(*P, jb.a, *jb.map, jb.Kp, jb.Rp, jb.out, w.mix.err, part, jb.rows, jb.slices, st);
+                cudaEventRecord(e1, st);
+                if (rc != VFMM_OK) break;
+                cudaError_t e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) rc = cuda_fail(e, "timing a split contraction");
+                if (rep > 0) total += ms;
+            }
+            if (rc == VFMM_OK && (best < 0.0f || total < best)) {
+                best = total;
+                best_c = c;
+            }
+        }
+        P->ctas = best_c;
+    };
     for (int j = 0; j < 4 && rc == VFMM_OK; ++j) {
         Job& jb = jobs[j];
         if (jb.P->n_groups == 0 || (!jb.P->may_split && !jb.P->alt)) continue;
@@ -1969,6 +2009,7 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
                 jb.P->alt = alt;
             }
         }
+        if (rc == VFMM_OK) time_ctas(jb, jb.P, part);
         if (splits) splits[j] = jb.P->split;
     }
     cudaEventDestroy(e0);

@@ -138,6 +138,7 @@ struct SplitArgs {
     int drain_every;      // configurations accumulated in TMEM between two drains (exactness bound)
     int transposed;       // table rows on the M side (see near_transposed)
     int slices;           // slices of each operand taken, kMinSlices .. kSlices (products i + j <= slices + 1)
+    int n_items;          // work items (n_groups * split * nchunks); the grid may be smaller (persistent CTAs)
     size_t part_stride;   // n_out_rows * Rp
 };
 
@@ -147,10 +148,10 @@ __host__ __device__ constexpr int acc_of(int i, int j) { return (i + j - 2) < (k
 // All slice products (i, j), i + j <= S + 1, of one K block: accumulator acc_of(i, j); on the
 // first K block of a configuration the first product into each accumulator overwrites it (with
 // S >= kMinSlices every accumulator gets a product).
-template <bool kFirst, int S>
+template <bool kFirst, int S, int N>
 __device__ __forceinline__ void issue_unit(uint32_t tmem, uint64_t ad0, uint64_t bd0) {
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, kTileN);
-    constexpr uint32_t A_SLICE = kTileM * 64, B_SLICE = kTileN * 64;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTileM, N);
+    constexpr uint32_t A_SLICE = kTileM * 64, B_SLICE = N * 64;
     static_assert(S >= kMinSlices && S <= kSlices, "slice count");
 #pragma unroll
     for (int i = 1; i <= S; ++i)
@@ -165,7 +166,7 @@ __device__ __forceinline__ void issue_unit(uint32_t tmem, uint64_t ad0, uint64_t
                 const uint64_t ad = ad0 + (((i - 1) * A_SLICE + ks * 32) >> 4);
                 const uint64_t bd = bd0 + (((j - 1) * B_SLICE + ks * 32) >> 4);
                 const uint32_t accum = (kFirst && first_of_acc && ks == 0) ? 0u : 1u;
-                tc::umma_bf16(tmem + acc * kTileN, ad, bd, idesc, accum);
+                tc::umma_bf16(tmem + acc * N, ad, bd, idesc, accum);
             }
         }
 }
@@ -173,6 +174,9 @@ __device__ __forceinline__ void issue_unit(uint32_t tmem, uint64_t ad0, uint64_t
 // Warps 0..7: epilogue (lane quadrant w % 4, column half w / 4); warps 8..10: producers;
 // warp 11: TMEM allocation and the MMA issuer (lane 0). Twelve warps keep three warps per SM
 // sub-partition, which leaves each thread up to 168 registers.
+// N: the MMA's N (TMEM columns per accumulator): 80, or 48 for the 48-row tables of small
+// expansions (targets on M only).
+template <int N>
 __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ unsigned char dsm[];
     __shared__ __align__(8) uint64_t bars[2 * kStages + 3];
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
     __shared__ volatile int abort_flag;
     __shared__ int32_t s_src[kTileM];
     __shared__ volatile int p_abort;  // written by producers only, read after a producer barrier
-    constexpr int N = kTileN;
+    static_assert(N % 16 == 0 && (N / 2) % 8 == 0 && kNumAcc * N <= kTmemCols, "tile N");
     constexpr uint32_t A_SLICE = kTileM * 64;
     constexpr uint32_t B_SLICE = N * 64;
     constexpr uint32_t STAGE = kSlices * (A_SLICE + B_SLICE);
@@ -188,8 +192,6 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool tr = a.transposed != 0;     // table rows on M (TMA into the A region), targets on N
     const int G = tr ? kTileN : kTileM;    // gathered rows (targets) per group
-    const int q = blockIdx.x / a.nchunks, rc = blockIdx.x % a.nchunks;
-    const int g = q / a.split, sp = q % a.split;
     const uint32_t base = tc::smem_u32(dsm);
     const uint32_t sbase = (base + 1023u) & ~1023u;
     const uint32_t full0 = tc::smem_u32(&bars[0]);
@@ -217,150 +219,188 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = tmem_holder;
-    // units = (table, K block) pairs of the group in table order; CTA sp of the split takes a
-    // contiguous share, which may begin or end inside a table (split-K over tables and K blocks)
-    const int gbeg = a.gptr[g], gcnt = a.gptr[g + 1] - gbeg;
+    // Work items (group g, split share sp, row chunk rc), item = (g * split + sp) * nchunks + rc; this
+    // CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ... (one item per CTA unless the launch
+    // caps the grid). Within an item, units = (table, K block) pairs of the group in table order;
+    // share sp of the split takes a contiguous range of them, which may begin or end inside a table
+    // (split-K over tables and K blocks). The stage ring and the accumulator hand-offs run on
+    // CTA-wide counters (gu: units, dg: drain groups), so one item's loads start while the previous
+    // item's accumulators drain.
+    const int n_items = a.n_items;
     const int nkb = a.Kp / kKBlock;
-    const long long Ug = (long long)gcnt * nkb;
-    const int ubeg = (int)((Ug * sp) / a.split);
-    const int U = (int)((Ug * (sp + 1)) / a.split) - ubeg;
     const int DU = a.drain_every * nkb;  // units summed in TMEM between two drains
-    const int r0 = rc * (tr ? kTileM : N);  // first table row of this CTA's tile
-    int issued = 0;  // producers: units whose copies were started
+    struct Item {
+        int g, sp, rc, gbeg, ubeg, U;
+    };
+    auto item = [&](int it) {
+        Item x;
+        const int qq = it / a.nchunks;
+        x.rc = it - qq * a.nchunks;
+        x.g = qq / a.split;
+        x.sp = qq - x.g * a.split;
+        x.gbeg = a.gptr[x.g];
+        const long long Ug = (long long)(a.gptr[x.g + 1] - x.gbeg) * nkb;
+        x.ubeg = (int)((Ug * x.sp) / a.split);
+        x.U = (int)((Ug * (x.sp + 1)) / a.split) - x.ubeg;
+        return x;
+    };
+    int issued = 0;  // producers: units (CTA-wide count) whose copies were started
 
     if (warp >= kEpilogueWarps && warp < kMmaWarp) {
         // ------------------------------------------------ producers: table tile by TMA (one thread),
         // gathered source rows by cp.async (all producer threads)
         const int ptid = tid - kEpilogueThreads;
         if (ptid == 0) tc::tma_prefetch_desc(&tmB);
-        for (int u = 0; u < U; ++u) {
-            const int s = u & 1;
-            if (u >= 2 && !tc::mbar_wait(empty0 + 8 * s, ((u >> 1) - 1) & 1, &abort_flag)) p_abort = 1;
-            // every producer passes this barrier once per unit, so the exit decision below is uniform
-            // and nobody rewrites s_src while another producer still reads it
-            named_bar_sync(1, kProducerThreads);
-            if (p_abort) {
-                abort_flag = 1;
-                atomicExch(a.err, 1);
-                break;
-            }
-            const int ci = gbeg + (ubeg + u) / nkb, kb = (ubeg + u) % nkb;
-            const int cfg = a.gcfg[ci];
-            if (kb == 0 || u == 0) {
-                // gather rows of this table for the 128 targets, once per table
-                for (int m = ptid; m < G; m += kProducerThreads) s_src[m] = a.gsrc[(size_t)ci * G + m];
+        int gu = 0;
+        for (int it = blockIdx.x; it < n_items && !p_abort; it += gridDim.x) {
+            const Item x = item(it);
+            const int r0 = x.rc * (tr ? kTileM : N);  // first table row of this item's tile
+            for (int u = 0; u < x.U; ++u, ++gu) {
+                const int s = gu & 1;
+                if (gu >= 2 && !tc::mbar_wait(empty0 + 8 * s, ((gu >> 1) - 1) & 1, &abort_flag)) p_abort = 1;
+                // every producer passes this barrier once per unit, so the exit decision below is uniform
+                // and nobody rewrites s_src while another producer still reads it
                 named_bar_sync(1, kProducerThreads);
-            }
-            const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
-            // table tile by TMA into the region of its side, gathered rows into the other
-            const uint32_t sT = tr ? sA : sB, sG = tr ? sB : sA;
-            const uint32_t T_SLICE = tr ? A_SLICE : B_SLICE, G_SLICE = tr ? B_SLICE : A_SLICE;
-            if (ptid == 0) {
-                // 8 boxes of (128 or 80) table rows x 64 bytes (one per slice), SW64-swizzled by TMA
-                tc::mbar_arrive_expect_tx(full0 + 8 * s, a.slices * T_SLICE);
-                for (int sl_i = 0; sl_i < a.slices; ++sl_i)
-                    tc::tma_load_3d(sT + sl_i * T_SLICE, &tmB, 0, kb * kSlices + sl_i, cfg * a.Rp + r0, full0 + 8 * s);
-            }
-            // a warp instruction covers 8 rows x 64 bytes of one slice: 512 contiguous bytes of shared
-            // memory (no bank conflicts) from eight 64-byte pieces of global memory
-            const int lrow = (ptid & 31) >> 2, ch = ptid & 3, pw = ptid >> 5;
+                if (p_abort) {
+                    abort_flag = 1;
+                    atomicExch(a.err, 1);
+                    break;
+                }
+                const int ci = x.gbeg + (x.ubeg + u) / nkb, kb = (x.ubeg + u) % nkb;
+                const int cfg = a.gcfg[ci];
+                if (kb == 0 || u == 0) {
+                    // gather rows of this table for the group's targets, once per table
+                    for (int m = ptid; m < G; m += kProducerThreads) s_src[m] = a.gsrc[(size_t)ci * G + m];
+                    named_bar_sync(1, kProducerThreads);
+                }
+                const uint32_t sA = sbase + s * STAGE, sB = sA + kSlices * A_SLICE;
+                // table tile by TMA into the region of its side, gathered rows into the other
+                const uint32_t sT = tr ? sA : sB, sG = tr ? sB : sA;
+                const uint32_t T_SLICE = tr ? A_SLICE : B_SLICE, G_SLICE = tr ? B_SLICE : A_SLICE;
+                if (ptid == 0) {
+                    // boxes of (128 or 80) table rows x 64 bytes (one per slice), SW64-swizzled by TMA
+                    tc::mbar_arrive_expect_tx(full0 + 8 * s, a.slices * T_SLICE);
+                    for (int sl_i = 0; sl_i < a.slices; ++sl_i)
+                        tc::tma_load_3d(sT + sl_i * T_SLICE, &tmB, 0, kb * kSlices + sl_i, cfg * a.Rp + r0,
+                                        full0 + 8 * s);
+                }
+                // a warp instruction covers 8 rows x 64 bytes of one slice: 512 contiguous bytes of
+                // shared memory (no bank conflicts) from eight 64-byte pieces of global memory
+                const int lrow = (ptid & 31) >> 2, ch = ptid & 3, pw = ptid >> 5;
 #pragma unroll 4
-            for (int q = pw; q < a.slices * (G / 8); q += kProducerThreads / 32) {
-                const int sl_i = q / (G / 8), m = (q % (G / 8)) * 8 + lrow;
-                const int src = s_src[m];
-                const bf16* gp = a.asl + (((size_t)(src < 0 ? 0 : src) * nkb + kb) * kSlices + sl_i) * kKBlock + ch * 8;
-                const uint32_t dst = sG + sl_i * G_SLICE + m * 64 + ((ch ^ ((m >> 1) & 3)) << 4);
-                tc::cp_async16(dst, gp, src < 0 ? 0u : 16u);
+                for (int q = pw; q < a.slices * (G / 8); q += kProducerThreads / 32) {
+                    const int sl_i = q / (G / 8), m = (q % (G / 8)) * 8 + lrow;
+                    const int src = s_src[m];
+                    const bf16* gp =
+                        a.asl + (((size_t)(src < 0 ? 0 : src) * nkb + kb) * kSlices + sl_i) * kKBlock + ch * 8;
+                    const uint32_t dst = sG + sl_i * G_SLICE + m * 64 + ((ch ^ ((m >> 1) & 3)) << 4);
+                    tc::cp_async16(dst, gp, src < 0 ? 0u : 16u);
+                }
+                // the stage's full barrier gets this thread's arrival when its copies have landed
+                tc::cp_async_mbar_arrive(full0 + 8 * s);
+                issued = gu + 1;
             }
-            // the stage's full barrier gets this thread's arrival when its copies have landed
-            tc::cp_async_mbar_arrive(full0 + 8 * s);
-            issued = u + 1;
         }
         tc::cp_async_wait_all();
-        } else if (warp == kMmaWarp) {
+    } else if (warp == kMmaWarp) {
         // ------------------------------------------------ MMA issuer: one unit at a time
         if (lane == 0) {
             const uint64_t adesc_base = tc::smem_desc(sbase, 16, 512, tc::kLayoutSwizzle64B);
-            for (int u = 0; u < U; ++u) {
-                // a drain group = DU consecutive units summed in the same accumulators
-                if (u >= DU && u % DU == 0 && !tc::mbar_wait(acc_empty, (u / DU - 1) & 1, &abort_flag)) {
-                    abort_flag = 1;
-                    atomicExch(a.err, 4);
-                    break;
+            int gu = 0, dg = 0;  // units and drain groups of this CTA so far
+            bool stop = false;
+            for (int it = blockIdx.x; it < n_items && !stop; it += gridDim.x) {
+                const Item x = item(it);
+                for (int u = 0; u < x.U; ++u, ++gu) {
+                    // a drain group = DU consecutive units of an item summed in the same accumulators;
+                    // before one starts, the epilogue must have drained the previous one
+                    if (u % DU == 0 && dg > 0 && !tc::mbar_wait(acc_empty, (dg - 1) & 1, &abort_flag)) {
+                        abort_flag = 1;
+                        atomicExch(a.err, 4);
+                        stop = true;
+                        break;
+                    }
+                    const int s = gu & 1;
+                    if (!tc::mbar_wait(full0 + 8 * s, (gu >> 1) & 1, &abort_flag)) {
+                        abort_flag = 1;
+                        atomicExch(a.err, 2);
+                        stop = true;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    // the gathered rows were written by cp.async (generic proxy): make them visible to
+                    // the tensor core's reads (async proxy) before the MMAs
+                    tc::fence_proxy_async();
+                    // descriptors differ only in the 14-bit start-address field (address >> 4), so
+                    // offsets within the stage are added to a base descriptor
+                    const uint64_t ad0 = adesc_base + ((s * STAGE) >> 4);
+                    const uint64_t bd0 = adesc_base + ((s * STAGE + kSlices * A_SLICE) >> 4);
+                    const bool first = u % DU == 0;
+                    switch (a.slices) {
+                        case 6: first ? issue_unit<true, 6, N>(tmem, ad0, bd0) : issue_unit<false, 6, N>(tmem, ad0, bd0); break;
+                        case 7: first ? issue_unit<true, 7, N>(tmem, ad0, bd0) : issue_unit<false, 7, N>(tmem, ad0, bd0); break;
+                        default: first ? issue_unit<true, 8, N>(tmem, ad0, bd0) : issue_unit<false, 8, N>(tmem, ad0, bd0); break;
+                    }
+                    tc::umma_commit(empty0 + 8 * s);
+                    if (u % DU == DU - 1 || u == x.U - 1) {
+                        tc::umma_commit(acc_full);
+                        ++dg;
+                    }
                 }
-                const int s = u & 1;
-                if (!tc::mbar_wait(full0 + 8 * s, (u >> 1) & 1, &abort_flag)) {
-                    abort_flag = 1;
-                    atomicExch(a.err, 2);
-                    break;
-                }
-                tc::tc_fence_after();
-                // the gathered rows were written by cp.async (generic proxy): make them visible to
-                // the tensor core's reads (async proxy) before the MMAs
-                tc::fence_proxy_async();
-                // descriptors differ only in the 14-bit start-address field (address >> 4), so
-                // offsets within the stage are added to a base descriptor
-                const uint64_t ad0 = adesc_base + ((s * STAGE) >> 4);
-                const uint64_t bd0 = adesc_base + ((s * STAGE + kSlices * A_SLICE) >> 4);
-                const bool first = u % DU == 0;
-                switch (a.slices) {
-                    case 6: first ? issue_unit<true, 6>(tmem, ad0, bd0) : issue_unit<false, 6>(tmem, ad0, bd0); break;
-                    case 7: first ? issue_unit<true, 7>(tmem, ad0, bd0) : issue_unit<false, 7>(tmem, ad0, bd0); break;
-                    default: first ? issue_unit<true, 8>(tmem, ad0, bd0) : issue_unit<false, 8>(tmem, ad0, bd0); break;
-                }
-                tc::umma_commit(empty0 + 8 * s);
-                if (u % DU == DU - 1 || u == U - 1) tc::umma_commit(acc_full);
             }
         }
         __syncwarp();
     } else {
-        // ------------------------------------------------ epilogue: drain each configuration
+        // ------------------------------------------------ epilogue: drain each drain group, write each item
         const int quad = warp & 3, half = warp >> 2;
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + half * HALF;
-        float hi[HALF], lo[HALF];
-#pragma unroll
-        for (int j = 0; j < HALF; ++j) hi[j] = lo[j] = 0.0f;
         bool ok = true;
-        const int ngroups = (U + DU - 1) / DU;
-        for (int grp = 0; grp < ngroups; ++grp) {
-            ok = ok && tc::mbar_wait(acc_full, grp & 1, &abort_flag);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                if (lane == 0) atomicExch(a.err, 3);
-                abort_flag = 1;
-                break;
+        int dg = 0;
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            const Item x = item(it);
+            float hi[HALF], lo[HALF];
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) hi[j] = lo[j] = 0.0f;
+            const int ngroups = (x.U + DU - 1) / DU;
+            for (int grp = 0; grp < ngroups; ++grp, ++dg) {
+                ok = ok && tc::mbar_wait(acc_full, dg & 1, &abort_flag);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) {
+                    if (lane == 0) atomicExch(a.err, 3);
+                    abort_flag = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                // per 8-column chunk: the 6 accumulators loaded together, one wait, then summed in
+                // accumulator order into the double-FP32 (hi, lo) pairs
+#pragma unroll
+                for (int ch = 0; ch < HALF / 8; ++ch) {
+                    uint32_t r[kNumAcc][8];
+#pragma unroll
+                    for (int acc = 0; acc < kNumAcc; ++acc) tc::tmem_ld8_nowait(lane_base + acc * N + ch * 8, r[acc]);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int acc = 0; acc < kNumAcc; ++acc)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float s2, e2;
+                            two_sum(hi[ch * 8 + j], __uint_as_float(r[acc][j]), s2, e2);
+                            hi[ch * 8 + j] = s2;
+                            lo[ch * 8 + j] = __fadd_rn(lo[ch * 8 + j], e2);
+                        }
+                }
+                tc::tc_fence_before();
+                tc::mbar_arrive(acc_empty);
             }
-            tc::tc_fence_after();
-            // per 8-column chunk: the 6 accumulators loaded together, one wait, then summed in
-            // accumulator order into the double-FP32 (hi, lo) pairs
-#pragma unroll
-            for (int ch = 0; ch < HALF / 8; ++ch) {
-                uint32_t r[kNumAcc][8];
-#pragma unroll
-                for (int acc = 0; acc < kNumAcc; ++acc) tc::tmem_ld8_nowait(lane_base + acc * N + ch * 8, r[acc]);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int acc = 0; acc < kNumAcc; ++acc)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float s2, e2;
-                        two_sum(hi[ch * 8 + j], __uint_as_float(r[acc][j]), s2, e2);
-                        hi[ch * 8 + j] = s2;
-                        lo[ch * 8 + j] = __fadd_rn(lo[ch * 8 + j], e2);
-                    }
-            }
-            tc::tc_fence_before();
-            tc::mbar_arrive(acc_empty);
-        }
-        if (ok) {
-            float2* outp = a.split > 1 ? a.out + (size_t)sp * a.part_stride : a.out;
+            if (!ok) break;
+            float2* outp = a.split > 1 ? a.out + (size_t)x.sp * a.part_stride : a.out;
             const int m = quad * 32 + lane;  // TMEM lane
+            const int r0 = x.rc * (tr ? kTileM : N);
             if (tr) {
                 // lane = table row r0 + m, columns = targets half * HALF + j of the group
                 const int row = r0 + m;
 #pragma unroll
                 for (int j = 0; j < HALF; ++j) {
-                    const int tgt = a.gtgt[(size_t)g * G + half * HALF + j];
+                    const int tgt = a.gtgt[(size_t)x.g * G + half * HALF + j];
                     if (tgt < 0) continue;
                     const float h = __fadd_rn(hi[j], lo[j]);
                     const float l = __fsub_rn(lo[j], __fsub_rn(h, hi[j]));
@@ -368,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_gemm_kernel(SplitArgs a, co
                 }
             } else {
                 // lane = target m of the group, columns = table rows r0 + half * HALF + j
-                const int tgt = a.gtgt[(size_t)g * G + m];
+                const int tgt = a.gtgt[(size_t)x.g * G + m];
                 if (tgt >= 0) {
                     float4* o = reinterpret_cast<float4*>(outp + (size_t)tgt * a.Rp + r0 + half * HALF);
 #pragma unroll
@@ -646,7 +686,26 @@ void free_plan_set(PlanSet* ps) {
     free_split_plan(&ps->s2l);
 }
 
-static size_t smem_bytes() { return (size_t)kStages * kSlices * (kTileM * 64 + kTileN * 64) + 1024; }
+static size_t smem_bytes(int N) { return (size_t)kStages * kSlices * (kTileM * 64 + N * 64) + 1024; }
+
+template <int N>
+static int launch_split(const SplitArgs& a, const CUtensorMap& bmap, int grid, cudaStream_t st) {
+    static thread_local int attr_dev = -1;  // the attribute is per device
+    int dev = 0;
+    VFMM_CUDA(cudaGetDevice(&dev));
+    if (attr_dev != dev) {
+        VFMM_CUDA(cudaFuncSetAttribute(split_gemm_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes(N)));
+        attr_dev = dev;
+    }
+    split_gemm_kernel<N><<<(unsigned)grid, kThreads, smem_bytes(N), st>>>(a, bmap);
+    VFMM_CUDA(cudaGetLastError());
+    return VFMM_OK;
+}
+
+static int launch_split_n(int n, const SplitArgs& a, const CUtensorMap& bmap, int grid, cudaStream_t st) {
+    return n == kTileNSmall ? launch_split<kTileNSmall>(a, bmap, grid, st) : launch_split<kTileN>(a, bmap, grid, st);
+}
 
 // (hi, lo) += v in double-float with exact two-sums; df_final renormalises.
 __device__ __forceinline__ void df_add(float& hi, float& lo, float2 v) {
@@ -698,15 +757,9 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
         if (ev) VFMM_CUDA(cudaEventRecord(ev[1], st));
         return VFMM_OK;
     }
-    const int tile_rows = table_rows_per_tile(P.transposed);
+    const int tile_rows = table_rows_per_tile(P.transposed, Rp);
     if (Kp % kKBlock || Rp % tile_rows) return fail(VFMM_ERR_INTERNAL, "split GEMM shape not tiled");
-    static thread_local int attr_dev = -1;  // the attribute is per device
-    int dev = 0;
-    VFMM_CUDA(cudaGetDevice(&dev));
-    if (attr_dev != dev) {
-        VFMM_CUDA(cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
-        attr_dev = dev;
-    }
+    const int n_mma = mma_n(P.transposed, Rp);
     SplitArgs a;
     a.asl = (const bf16*)asl;
     a.gptr = P.ptr;
@@ -730,8 +783,8 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
         a.split = 1;
         a.part_stride = 0;
         a.out = part;
-        split_gemm_kernel<<<(unsigned)P.n_groups * a.nchunks, kThreads, smem_bytes(), st>>>(a, bmap);
-        VFMM_CUDA(cudaGetLastError());
+        a.n_items = P.n_groups * a.nchunks;
+        VFMM_CHECK(launch_split_n(n_mma, a, bmap, P.ctas > 0 ? std::min(P.ctas, a.n_items) : a.n_items, st));
         const int64_t n = (int64_t)P.n_seg * P.R * Rp;
         if (n > 0)
             segment_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, P.seg, P.seg_out, P.n_seg, P.R,
@@ -743,8 +796,8 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
     a.split = part ? P.split : 1;
     a.part_stride = n_out_rows * (size_t)Rp;
     a.out = a.split > 1 ? part : out;
-    split_gemm_kernel<<<(unsigned)P.n_groups * a.split * a.nchunks, kThreads, smem_bytes(), st>>>(a, bmap);
-    VFMM_CUDA(cudaGetLastError());
+    a.n_items = P.n_groups * a.split * a.nchunks;
+    VFMM_CHECK(launch_split_n(n_mma, a, bmap, P.ctas > 0 ? std::min(P.ctas, a.n_items) : a.n_items, st));
     if (a.split > 1) {
         const int64_t n = (int64_t)P.n_groups * P.group * Rp;
         split_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, a.part_stride, a.split, P.tgt,

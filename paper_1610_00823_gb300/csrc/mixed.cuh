@@ -24,6 +24,7 @@ constexpr int kTileM = 128;  // target leaves per tile (TMEM lanes)
 constexpr int kKBlock = 32;  // K values per pipeline stage (64-byte rows)
 constexpr int kStages = 2;   // shared-memory stages
 constexpr int kTileN = 80;   // table rows per tile
+constexpr int kTileNSmall = 48;  // table rows per tile when 2p <= 48 (S2M, M2L, S2L at p <= 24)
 constexpr int kNumAcc = 6;   // TMEM accumulators (diagonals 0..4 exact, 5+ shared)
 constexpr int kTmemCols = 512;                  // allocation (power of two >= kNumAcc * kTileN)
 constexpr int kEpilogueWarps = 8;
@@ -39,7 +40,16 @@ static_assert(kNumAcc * kTileN <= kTmemCols, "TMEM budget");
 // group, gathered), which gathers 40 % fewer bytes; otherwise targets are the M side (128 per group)
 // and table rows the N side (80 per tile). M2L, S2L and S2M (2p rows) always use the latter.
 __host__ __device__ constexpr bool near_transposed(int k) { return (3 * k * k) % kTileM == 0; }
-__host__ __device__ constexpr int table_rows_per_tile(bool transposed) { return transposed ? kTileM : kTileN; }
+// Table rows per tile of a contraction whose tables have Rp rows: 128 (transposed), else 80, or 48
+// for the 48-row tables of small expansions.
+__host__ __device__ constexpr int table_rows_per_tile(bool transposed, int Rp = kTileN) {
+    return transposed ? kTileM : (Rp % kTileN == 0 ? kTileN : kTileNSmall);
+}
+// N of the MMAs (TMEM columns per accumulator): the gathered targets (80) when transposed, else the
+// table rows per tile.
+__host__ __device__ constexpr int mma_n(bool transposed, int Rp) {
+    return transposed ? kTileN : table_rows_per_tile(false, Rp);
+}
 
 // Splits v / 2^E (|v| < 2^E) into kSlices signed base-64 digits, out[(i - 1) * stride] =
 // sign(v) d_i 2^(-6 i), d_i = floor(|v| 2^(6 i - E)) mod 64: the digits that repeated
@@ -138,7 +148,7 @@ struct MixedOps {
     CUtensorMap tm_near, tm_s2m, tm_m2l, tm_far, tm_s2l;
     // far field: expansion coefficients as reals (Re, Im of 0..p), Kx = 2(p+1) padded
     int Kx = 0;           // 2(p+1) rounded up to kKBlock
-    int Rx = 0;           // 2p rounded up to kTileN (rows of S2M and M2L without coefficient 0)
+    int Rx = 0;           // 2p rounded up to 48 (2p <= 48) or to kTileN (rows of S2M and M2L without coefficient 0)
     void* s2m_sl = nullptr;   // bf16 [1][Rx][kSlices][Kp]: S2M rows 2..2p+1
     int* s2m_E = nullptr;     // [Rx]
     // M2L rows 2..2p+1 over input columns 0..2p+1, column k scaled by 2^-floor(k/4) (the decay

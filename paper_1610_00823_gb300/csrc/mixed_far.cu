@@ -87,7 +87,8 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
     const int k = o->k, kk = k * k, p = o->p, P = p + 1;
     const int R = 3 * kk;
     mo->Kx = (2 * P + kKBlock - 1) / kKBlock * kKBlock;
-    mo->Rx = (2 * p + kTileN - 1) / kTileN * kTileN;
+    mo->Rx = 2 * p <= kTileNSmall ? kTileNSmall : (2 * p + kTileN - 1) / kTileN * kTileN;
+    const int rx_tile = table_rows_per_tile(false, mo->Rx);
     const double inv2pi = 1.0 / (2.0 * 3.14159265358979323846);
     // S2M rows 2..2p+1 (coefficients 1..p)
     std::vector<double> s2m((size_t)2 * P * kk);
@@ -95,7 +96,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
     std::vector<double> S((size_t)2 * p * kk);
     std::copy(s2m.begin() + 2 * kk, s2m.end(), S.begin());
     VFMM_CHECK(slice_table(S, 1, 2 * p, kk, mo->Rx, mo->Kp, &mo->s2m_sl, &mo->s2m_E, st));
-    VFMM_CHECK(make_table_map(mo->s2m_sl, mo->Rx, mo->Kp, kTileN, &mo->tm_s2m));
+    VFMM_CHECK(make_table_map(mo->s2m_sl, mo->Rx, mo->Kp, rx_tile, &mo->tm_s2m));
     // M2L as real matrices: rows 2..2p+1, columns 0..2p+1
     std::vector<double> mt((size_t)kVCfg * P * P * 2);
     VFMM_CUDA(cudaMemcpy(mt.data(), o->m2l_t, mt.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -126,7 +127,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
         VFMM_CUDA(cudaMalloc(&mo->m2l_r0, r0.size() * sizeof(double)));
         VFMM_CUDA(cudaMemcpy(mo->m2l_r0, r0.data(), r0.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
-    VFMM_CHECK(make_table_map(mo->m2l_sl, (int64_t)kVCfg * mo->Rx, mo->Kx, kTileN, &mo->tm_m2l));
+    VFMM_CHECK(make_table_map(mo->m2l_sl, (int64_t)kVCfg * mo->Rx, mo->Kx, rx_tile, &mo->tm_m2l));
     // leaf tables: 0 = L2T without coefficient 0, 1 + c = M2T of W configuration c
     std::vector<double> l2t((size_t)R * 2 * P), xh(k);
     VFMM_CUDA(cudaMemcpy(l2t.data(), o->l2t, l2t.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -180,7 +181,7 @@ int far_prepare(vfmm_ops* o, cudaStream_t st) {
             }
         }
     VFMM_CHECK(slice_table(XL, kFarCfg, 2 * p, kk, mo->Rx, mo->Kp, &mo->s2l_sl, &mo->s2l_E, st));
-    VFMM_CHECK(make_table_map(mo->s2l_sl, (int64_t)kFarCfg * mo->Rx, mo->Kp, kTileN, &mo->tm_s2l));
+    VFMM_CHECK(make_table_map(mo->s2l_sl, (int64_t)kFarCfg * mo->Rx, mo->Kp, rx_tile, &mo->tm_s2l));
     VFMM_CUDA(cudaMalloc(&mo->s2l_r0, X0.size() * sizeof(double)));
     VFMM_CUDA(cudaMemcpy(mo->s2l_r0, X0.data(), X0.size() * sizeof(double), cudaMemcpyHostToDevice));
     return VFMM_OK;
@@ -523,8 +524,8 @@ extern "C" int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32
     // per table of a tile and per K value: S (S + 1) / 2 products of 128 x 80 MACs
     auto tc = [&](const SplitPlan& P, int Kp, int Rp, int ctr) {
         const int S = mo->slices[ctr];
-        return 2.0 * (double)P.entries * (Rp / table_rows_per_tile(P.transposed)) * (double)Kp * (S * (S + 1) / 2) *
-               kTileM * kTileN;
+        return 2.0 * (double)P.entries * (Rp / table_rows_per_tile(P.transposed, Rp)) * (double)Kp * (S * (S + 1) / 2) *
+               kTileM * mma_n(P.transposed, Rp);
     };
     out[0] = tc(PS->near, mo->Kp, mo->Rp, kCtrNear);
     out[1] = tc(PS->m2l, mo->Kx, mo->Rx, kCtrM2L);

@@ -164,6 +164,7 @@ struct SplitPlan {
     int32_t* cfg = nullptr;  // [entries] table index
     int32_t* src = nullptr;  // [entries][group] gathered operand row or -1
     int32_t split = 1;       // CTAs per group (each takes a share of the group's tables)
+    int32_t ctas = 0;        // CTA cap of the launch (persistent CTAs walk several work items); 0: one CTA per item
     bool may_split = false;  // small contraction (fewer CTAs than two per SM): split-K allowed
     bool transposed = false; // table rows on the M side (128 per tile), targets on the N side
     int32_t group = 128;     // targets per group: 128, or 80 when transposed
@@ -257,6 +258,10 @@ int volume_potential(const vfmm_tree* tree, const vfmm_ops* ops, const double* f
 int read_status_word(const int* word);
 // Device address of the allocation-free scratch's status word on the current device.
 int noalloc_status_word(const int** word);
+// Multipole and local expansions ([n_boxes][2(p+1)] scaled, complex interleaved) that a
+// one-right-hand-side solve with this tree and ops left in its workspace.
+int solve_expansions(const vfmm_tree* tree, const vfmm_ops* ops, const void* workspace_dev, size_t workspace_bytes,
+                     const double** Mexp, const double** Lexp, int* R);
 
 }  // namespace vfmm
 
