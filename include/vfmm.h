@@ -300,6 +300,23 @@ int vfmm_leaf_interpolate(const vfmm_tree* tree, int32_t n_fields, const double*
                           int64_t n_points, const double* x_dev, const double* y_dev, double* const* out_dev,
                           int32_t* leaf_dev, void* stream);
 
+/* The computed potential at arbitrary points from the stored expansions (Section 5.3: the FMM's
+ * multipole and local expansions are kept after the call, so that a new target costs O(p) for its
+ * far field instead of a new FMM). For each point t (x_dev[i], y_dev[i]) of leaf b (located as
+ * vfmm_leaf_interpolate locates it): u, u_x, u_y = the far field of b's local expansion and of the
+ * multipoles of b's W list at t, plus the near field of every leaf of b's U list, integrated
+ * against f~ at t itself by on-the-fly quadrature (tanh-sinh rules on triangles with apex at the
+ * source box's point nearest to t). At a leaf node it gives the solve's value there; elsewhere it is
+ * V f~(t), not the interpolant v~. Reads the expansions a vfmm_volume_potential call with nrhs = 1
+ * and the same tree, ops and f_dev ([n_leaves][k*k]) left in workspace_dev (workspace_bytes as
+ * given to that call), so it must follow that call on the same stream and precede any other use of
+ * the workspace. Points outside the closed root box or with a NaN coordinate get NaN. FP64;
+ * stream-ordered, no allocation. Errors: INVALID_ARG (null pointers, n_points < 0 or > 2^31 - 1,
+ * k differs), WORKSPACE (smaller than a one-right-hand-side workspace), CUDA. */
+int vfmm_evaluate_points(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, const void* workspace_dev,
+                         size_t workspace_bytes, int64_t n_points, const double* x_dev, const double* y_dev,
+                         double* u_dev, double* ux_dev, double* uy_dev, void* stream);
+
 /* Allocation-free solve. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory, such as hosts whose device memory is
  * owned entirely by their own pool allocator (so neither a workspace buffer nor a

@@ -76,6 +76,9 @@ EXPORTS = {
                                        ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
                                        ctypes.POINTER(ctypes.c_int32)],
     "vfmm_workspace_status": [ctypes.c_void_p],
+    "vfmm_evaluate_points": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p],
     "vfmm_volume_potential_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "vfmm_solve_work": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, c_double_p],

@@ -276,6 +276,22 @@ def volume_potential_host(tree: Tree, ops: Ops, f_host, out_host=None, ws=None, 
     return out_host
 
 
+def evaluate_points(tree: Tree, ops: Ops, f, ws, x, y, stream=None):
+    """V f~ and its gradient at arbitrary points from the expansions a one-right-hand-side
+    volume_potential call with workspace ws and leaf values f left there (vfmm_evaluate_points).
+    x, y: cuda float64 tensors of the same length; returns (u, u_x, u_y)."""
+    x = x.contiguous()
+    y = y.contiguous()
+    if x.dtype != torch.float64 or y.dtype != torch.float64 or not x.is_cuda or x.numel() != y.numel():
+        raise ValueError("x, y: cuda float64 tensors of equal length")
+    out = tuple(torch.empty_like(x) for _ in range(3))
+    call("vfmm_evaluate_points", tree.handle, ops.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+         ws.numel(), x.numel(), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+         ctypes.c_void_p(out[0].data_ptr()), ctypes.c_void_p(out[1].data_ptr()), ctypes.c_void_p(out[2].data_ptr()),
+         _stream(stream))
+    return out
+
+
 def workspace_status(ws=None):
     """Status of the last solve that used workspace ws (vfmm_workspace_status): raises VfmmError
     (VFMM_ERR_TIMEOUT) when a bounded device wait of that solve ran out. Call it after synchronising
