@@ -221,17 +221,16 @@ int vfmm_ops_export(const vfmm_ops* ops, int32_t which, double* host, int64_t n_
 int vfmm_ops_destroy(vfmm_ops* ops);
 
 /* Slices of the split-BF16 contractions of a VFMM_MIXED operator set (no counterpart in the paper,
- * which computes in double precision). Every operand of a contraction is stored as 8 base-64 digits
- * (48 bits below its power-of-two scale); a contraction that takes S of them (6 <= S <= 8) issues
- * the S (S + 1) / 2 slice products i + j <= S + 1 and truncates each operand and the dropped
- * products at about 2^(-6 S) of its scale: fewer tensor-core products and fewer gathered bytes,
- * less accuracy. slices[5] = near field, S2M, M2L, S2L, leaf far field (L2T + M2T); a new operator
- * set takes {8, 7, 8, 7, 8}, the fewest that left the error against the FP64 form unchanged on the
- * adaptive 20-Gaussian (k = 16, p = 40), kinked and uniform depth-7 (k = 16) workloads (taking 7
- * for the near field raised it there to 2.4e-10). Host-only; applies to later calls and graph
- * captures (a graph keeps the
- * counts it captured); not while a solve with these operators is being launched. Errors:
- * INVALID_ARG (null pointer, not VFMM_MIXED, a count outside [6, 8]). */
+ * which computes in double precision). Every operand of a contraction is stored as 8 balanced
+ * base-128 digits (56 bits below its power-of-two scale); a contraction that takes S of them
+ * (6 <= S <= 8) issues the S (S + 1) / 2 slice products i + j <= S + 1 and rounds each operand at
+ * 2^(-7 S - 1) of its scale: fewer tensor-core products and fewer gathered bytes, less accuracy.
+ * slices[5] = near field, S2M, M2L, S2L, leaf far field (L2T + M2T); a new operator set takes
+ * {7, 6, 7, 6, 7}, the fewest that keep the error against the FP64 form at least 5x below 1e-10 on
+ * the adaptive 20-Gaussian (k = 16, p = 40), kinked and uniform depth-7 (k = 16) workloads.
+ * Host-only; applies to later calls and graph captures (a graph keeps the counts it captured); not
+ * while a solve with these operators is being launched. Errors: INVALID_ARG (null pointer, not
+ * VFMM_MIXED, a count outside [6, 8]). */
 int vfmm_ops_set_slices(vfmm_ops* ops, const int32_t* slices);
 int vfmm_ops_get_slices(const vfmm_ops* ops, int32_t* slices);
 

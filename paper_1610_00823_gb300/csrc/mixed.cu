@@ -4,26 +4,29 @@
 // is an exact-enough FP64 contraction computed from BF16 tensor-core products:
 //
 //  * f is normalised by a global power of two (|a| < 1) and each table row r by its own power
-//    of two shared by all 33 configurations; each normalised value is split into kSlices = 8
-//    slices a = sum_i m_i 2^(-6 i) with integers |m_i| <= 63 (exact in BF16), 48 bits in all.
-//  * Products (i, j) with i + j <= 9 are kept (dropped terms are below 2^-48). For one
-//    configuration, the products of one diagonal d = i + j - 2 sum at most (d + 1) * 256 * 63^2
-//    integers times 2^(-6(d+2)); for d <= 4 that is below 2^24 units, so the FP32 tensor-core
-//    accumulator holds it exactly. Diagonals 0..4 get one TMEM accumulator each; diagonals 5..7
-//    share a sixth, where the tensor core's truncating accumulation of terms much smaller than the
-//    running sum (measured: it does not round to nearest) costs about 2^-46 of the result.
-//  * After every configuration the epilogue warps drain the six accumulators into a running
-//    double-float sum (FP32 pairs, exact two-sums) in registers, so no accumulator ever sums more
-//    than one configuration; at the end they store (hi, lo). The leaf pass scales by
+//    of two shared by all 33 configurations; each normalised value is written as 8 balanced
+//    base-128 digits a = sum_i m_i 2^(-7 i) (integers |m_1| <= 128, |m_i| <= 64 for i >= 2, exact
+//    in BF16), of which a contraction takes the first S (S = 7: 49 bits).
+//  * Products (i, j) with i + j <= S + 1 are kept (the dropped terms are below 2^(-7 S - 7)). Per K
+//    value the products of one diagonal d = i + j - 2 sum to at most 2 * 128 * 64 + (d - 1) * 64^2
+//    integer units of 2^(-7(d+2)) (28672 for d = 4), so over a drain group of at most 512 K values
+//    diagonals 0..4 stay below 2^24 units and the FP32 tensor-core accumulator holds them exactly.
+//    Diagonals 0..4 get one TMEM accumulator each; diagonals 5 and up share a sixth, where the
+//    tensor core's truncating accumulation of terms much smaller than the running sum (it does not
+//    round to nearest) costs about 2^-51 of the result (2^-46 was measured with base-64 digits,
+//    whose diagonal 5 weighs 2^5 more).
+//  * After every drain group (one or more configurations, at most 512 K values) the epilogue warps
+//    drain the six accumulators into a running double-float sum (FP32 pairs, exact two-sums) in
+//    registers; at the end of an item they store (hi, lo). The leaf pass scales by
 //    2^(E_f + E_r) and by h^2 (potential) or h (gradient) in FP64.
 //
-// Tile: 128 target leaves (TMEM lanes, grouped by their configuration set) x 80 table rows.
-// For every configuration present in the group and every K block of 32 values, producer warps
-// gather the 8 slices of the 128 source rows and of the 80 table rows with cp.async into a
-// 64-byte-swizzled K-major layout (two stages); one thread issues the 36 x 2 UMMAs
-// (128 x 80 x 16) into the six TMEM accumulators; tcgen05.commit frees the stage and, after
-// the last K block of a configuration, hands the accumulators to the epilogue. Every mbarrier
-// wait is bounded and reports a timeout through an error word.
+// Tile: 128 rows on the M side (TMEM lanes) x 80 on the N side; which side holds the table rows
+// (by TMA) and which the gathered operand rows (by cp.async) depends on the contraction
+// (near_transposed). For every table of a group and every K block of 32 values the S slices of
+// both go into a 64-byte-swizzled K-major stage (two stages); one thread issues the
+// S(S+1)/2 x 2 UMMAs (128 x N x 16) into the six TMEM accumulators; tcgen05.commit frees the
+// stage and, after the last K block of a drain group, hands the accumulators to the epilogue.
+// Every mbarrier wait is bounded and reports a timeout through an error word.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -772,11 +775,11 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
     a.nchunks = Rp / tile_rows;
     a.transposed = P.transposed ? 1 : 0;
     a.slices = slices;
-    // A diagonal gets at most 5 slice products per K value (i + j = d <= 6), each below 63^2, so the
-    // exact FP32 accumulators stay exact while 5 * 3969 * Kp * configurations < 2^24. The shared
-    // accumulator of diagonals 7..9 truncates as it grows, so a drain group also holds at most 512
-    // K values (measured: 2.6e-11 -> 1.5e-11 for the gradient on the 20-Gaussian tree, < 1 % time).
-    a.drain_every = std::max(1, std::min((int)((1 << 24) / (5ll * 3969 * Kp)), 512 / Kp));
+    // Per K value the slice products of an exact diagonal (d <= 4) sum to at most
+    // 2 * 128 * 64 + 3 * 64^2 = 28672 units (balanced digits), so those accumulators stay exact while
+    // 28672 * Kp * configurations < 2^24. The shared accumulator of diagonals 5 and up truncates as
+    // it grows, so a drain group also holds at most 512 K values.
+    a.drain_every = std::max(1, std::min((int)((1 << 24) / (28672ll * Kp)), 512 / Kp));
     if (P.entry) {
         // one slab row per entry in the partial-sum buffer, then the per-target sums
         if (!part) return fail(VFMM_ERR_INTERNAL, "entry-major contraction without a slab buffer");

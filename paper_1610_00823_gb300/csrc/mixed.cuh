@@ -16,7 +16,7 @@
 
 namespace vfmm {
 
-constexpr int kSlices = 8;   // BF16 slice slots per operand (6-bit magnitudes, 48 bits)
+constexpr int kSlices = 8;   // BF16 slice slots per operand (balanced base-128 digits, 56 bits)
 constexpr int kMinSlices = 6;  // fewest slices a contraction may take (every accumulator gets a product)
 // contractions of the mixed form, in the order of vfmm_ops_set_slices
 enum { kCtrNear = 0, kCtrS2M = 1, kCtrM2L = 2, kCtrS2L = 3, kCtrFar = 4, kNumCtr = 5 };
@@ -51,23 +51,32 @@ __host__ __device__ constexpr int mma_n(bool transposed, int Rp) {
     return transposed ? kTileN : table_rows_per_tile(false, Rp);
 }
 
-// Splits v / 2^E (|v| < 2^E) into kSlices signed base-64 digits, out[(i - 1) * stride] =
-// sign(v) d_i 2^(-6 i), d_i = floor(|v| 2^(6 i - E)) mod 64: the digits that repeated
-// t <- 64 t, d <- trunc(t), t <- t - d give in exact arithmetic, taken here from the bits of v
-// with integer operations (v's significand shifted to 48 fractional bits).
+// Splits v / 2^E (|v| < 2^E) into kSlices balanced base-128 digits, out[(i - 1) * stride] =
+// d_i 2^(-7 i), with v / 2^E = sum_i d_i 2^(-7 i) + (|v| 2^(56 - E) - floor(|v| 2^(56 - E))) 2^-56:
+// q = floor(|v| 2^(56 - E)) is written in base 128 from its low end, a digit of 64 or more becoming
+// d - 128 with a carry into the next higher one, so d_2..d_8 lie in [-64, 63] and d_1 in [0, 128];
+// a negative v negates every digit. Each is an integer of at most 8 significant bits (exact in
+// BF16), the products of two are below 2^14, and the first S digits are v / 2^E rounded to the
+// nearest multiple of 2^(-7 S) (error at most 2^(-7 S - 1) of the scale 2^E). Integer work on the
+// bits of v (its significand shifted to 56 fractional bits).
 __device__ __forceinline__ void slice_fixed(double v, int E, __nv_bfloat16* out, int stride) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
     int ev = (int)((bits >> 52) & 0x7FF);
     unsigned long long mant = bits & ((1ull << 52) - 1);
     if (ev) mant |= 1ull << 52;
     else ev = 1;
-    const int shift = 1027 - ev + E;  // |v| 2^(48 - E) = mant 2^-(1027 - ev + E); > 0 when |v| < 2^E
-    const unsigned long long q = shift >= 64 ? 0ull : mant >> (shift < 0 ? 0 : shift);
+    // |v| 2^(56 - E) = mant 2^(ev - 1075 + 56 - E): a right shift by 1019 - ev + E (>= -3 when |v| < 2^E)
+    const int shift = 1019 - ev + E;
+    const unsigned long long q = shift >= 64 ? 0ull : (shift >= 0 ? mant >> shift : mant << (-shift));
     const bool neg = (bits >> 63) != 0;
+    int carry = 0;
 #pragma unroll
-    for (int i = 1; i <= kSlices; ++i) {
-        const float s = (float)((q >> (48 - 6 * i)) & 63ull) * __int_as_float((127 - 6 * i) << 23);
-        out[(i - 1) * stride] = __float2bfloat16_rn(neg ? -s : s);
+    for (int i = kSlices; i >= 1; --i) {
+        int d = (int)((q >> (7 * (kSlices - i))) & 127ull) + carry;
+        carry = (i > 1 && d >= 64) ? 1 : 0;
+        d -= carry << 7;
+        const float s = (float)(neg ? -d : d) * __int_as_float((127 - 7 * i) << 23);
+        out[(i - 1) * stride] = __float2bfloat16_rn(s);
     }
 }
 
@@ -162,10 +171,10 @@ struct MixedOps {
     double* s2l_r0 = nullptr; // [20][kk] FP64: Re of S2L row 0
     double* m2l_r0 = nullptr; // [40][p+1] complex FP64: M2L row 0 (output coefficient 0) per offset
     // slices taken per contraction (kCtr*): the first S of the 8 stored slices of each operand and
-    // the S(S+1)/2 products i + j <= S + 1. Defaults: the fewest that leave the error against the
-    // FP64 form unchanged on the 20-Gaussian, kinked and uniform k = 16 workloads (S2M and S2L take
-    // 7; with 7 the near field, M2L or leaf far field raise it to 2.4e-10, 2.4e-11, 3.6e-11)
-    int slices[kNumCtr] = {kSlices, 7, kSlices, 7, kSlices};
+    // the S(S+1)/2 products i + j <= S + 1. Defaults: 7 (49 bits) for the near field, M2L and the
+    // leaf far field, 6 (42 bits) for S2M and S2L, the fewest that keep the error against the FP64
+    // form at least 5x below 1e-10 on the 20-Gaussian, kinked and uniform k = 16 workloads
+    int slices[kNumCtr] = {7, 6, 7, 6, 7};
 };
 
 struct MixedWork {

@@ -265,7 +265,7 @@ def test_workspace_status_reports_a_recorded_timeout(precision):
 
 def test_slice_counts_trade_accuracy_for_products():
     """vfmm_ops_set_slices: defaults, validation, and the error bound of each setting on a small
-    adaptive k = 16 tree (fewer slices: the truncation at 2^-6S of each operand's scale)."""
+    adaptive k = 16 tree (fewer slices: the rounding at 2^(-7S - 1) of each operand's scale)."""
     from paper_1610_00823_gb300._lib import VfmmError
     from paper_1610_00823_gb300.api import solve_work
     src = W.narrow_gaussians(8, n=2, sigma=0.01, spread=0.4)
@@ -273,11 +273,11 @@ def test_slice_counts_trade_accuracy_for_products():
     f = v.source_sample(gt, src)
     u64 = v.volume_potential(gt, v.ops_create(16, 40, v.FP64), f)
     ops = v.ops_create(16, 40, v.MIXED)
-    assert ops.slices == {"near": 8, "s2m": 7, "m2l": 8, "s2l": 7, "far": 8}
+    assert ops.slices == {"near": 7, "s2m": 6, "m2l": 7, "s2l": 6, "far": 7}
     for bad in (5, 9):
         with pytest.raises(VfmmError):
             ops.set_slices(near=bad)
-    assert ops.slices["near"] == 8
+    assert ops.slices["near"] == 7
     with pytest.raises(VfmmError):
         v.ops_create(16, 40, v.FP64).set_slices(near=7)
     base = solve_work(gt, ops)["near_tc_flops"]
@@ -286,6 +286,6 @@ def test_slice_counts_trade_accuracy_for_products():
         ops.set_slices(**{c: S for c in ops.CONTRACTIONS})
         u = v.volume_potential(gt, ops, f)
         errs[S] = max(rel(u[q].cpu().numpy(), u64[q].cpu().numpy()) for q in range(3))
-        assert solve_work(gt, ops)["near_tc_flops"] == base * (S * (S + 1) // 2) / 36
+        assert solve_work(gt, ops)["near_tc_flops"] == base * (S * (S + 1) // 2) / 28
     assert errs[8] < TOL and errs[7] < 10 * TOL and errs[6] < 1e3 * TOL
     assert errs[6] > errs[8]
