@@ -439,7 +439,7 @@ def run_batch(args):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x7+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16x6+f64", "data": "synthetic",
             "config": {"workload": name, "members": n_members, "n_leaves": n_leaves, "n_targets": n_targets,
                        "k_mix": {str(k): sum(1 for wl, _ in members if wl.k == k) for k in (8, 16)},
                        "leaf_targets": [min(n for _, n in members), max(n for _, n in members)],
@@ -768,7 +768,7 @@ def main():
         clocks = clk.summary()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x7+f64",
+                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16x6+f64",
                 "data": "synthetic",
                 "config": {"workload": wl.name, "precision": args.precision, "n_leaves": tree.n_leaves,
                            "n_boxes": tree.n_boxes, "depth": tree.depth, "n_targets": n_targets, "nrhs": nrhs,

@@ -225,9 +225,9 @@ int vfmm_ops_destroy(vfmm_ops* ops);
  * base-128 digits (56 bits below its power-of-two scale); a contraction that takes S of them
  * (6 <= S <= 8) issues the S (S + 1) / 2 slice products i + j <= S + 1 and rounds each operand at
  * 2^(-7 S - 1) of its scale: fewer tensor-core products and fewer gathered bytes, less accuracy.
- * slices[5] = near field, S2M, M2L, S2L, leaf far field (L2T + M2T); a new operator set takes
- * {7, 6, 7, 6, 7}, the fewest that keep the error against the FP64 form at least 5x below 1e-10 on
- * the adaptive 20-Gaussian (k = 16, p = 40), kinked and uniform depth-7 (k = 16) workloads.
+ * slices[5] = near field, S2M, M2L, S2L, leaf far field (L2T + M2T); a new operator set takes 6
+ * for all, the fewest allowed: the error against the FP64 form stays at or below 6e-12 on the
+ * adaptive 20-Gaussian (k = 16, p = 40), kinked and uniform depth-7 (k = 16) workloads.
  * Host-only; applies to later calls and graph captures (a graph keeps the counts it captured); not
  * while a solve with these operators is being launched. Errors: INVALID_ARG (null pointer, not
  * VFMM_MIXED, a count outside [6, 8]). */

@@ -519,7 +519,7 @@ void mixed_free(vfmm_ops* o) {
 // of each target (-1 when the target has no entry for that table).
 int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                      const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                     bool transposed, int nkb, SplitPlan* P) {
+                     bool transposed, int nkb, PlanArena& A, SplitPlan* P) {
     const int G = transposed ? kTileN : kTileM;  // targets per group
     // Targets sorted by key; target t stands for the R consecutive virtual targets t * R + r, whose
     // A rows are src * R + r: the right-hand sides of one target share its set of tables.
@@ -584,24 +584,35 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
         }
         P->split = split;
     }
-    auto up = [](int32_t** dst, const std::vector<int32_t>& v) -> int {
-        VFMM_CUDA(cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(int32_t)));
-        if (!v.empty()) VFMM_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        return VFMM_OK;
-    };
-    VFMM_CHECK(up(&P->tgt, gtgt));
-    VFMM_CHECK(up(&P->ptr, gptr));
-    VFMM_CHECK(up(&P->cfg, gcfg));
-    VFMM_CHECK(up(&P->src, gsrc));
+    P->off[0] = A.put(gtgt);
+    P->off[1] = A.put(gptr);
+    P->off[2] = A.put(gcfg);
+    P->off[3] = A.put(gsrc);
+    return VFMM_OK;
+}
+
+int commit_plan_arena(PlanArena& A, PlanSet* PS) {
+    void* base = nullptr;
+    VFMM_CUDA(cudaMalloc(&base, std::max<size_t>(256, A.data.size() * sizeof(int32_t))));
+    PS->arena = base;
+    if (!A.data.empty())
+        VFMM_CUDA(cudaMemcpy(base, A.data.data(), A.data.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    int32_t* b = static_cast<int32_t*>(base);
+    for (SplitPlan* top : {&PS->near, &PS->s2m, &PS->m2l, &PS->far, &PS->s2l})
+        for (SplitPlan* P = top; P; P = P->alt) {
+            int32_t** field[6] = {&P->tgt, &P->ptr, &P->cfg, &P->src, &P->seg, &P->seg_out};
+            for (int i = 0; i < 6; ++i) *field[i] = P->off[i] >= 0 ? b + P->off[i] : nullptr;
+        }
     return VFMM_OK;
 }
 
 int build_contraction_plan(const std::vector<int32_t>& tgt_id,
                            const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                            const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                           bool transposed, int nkb, double slab_overhead, size_t slab_row_bytes, SplitPlan* P) {
+                           bool transposed, int nkb, double slab_overhead, size_t slab_row_bytes, PlanArena& A,
+                           SplitPlan* P) {
     constexpr size_t kMaxSlabBytes = size_t(256) << 20;
-    VFMM_CHECK(build_split_plan(tgt_id, items, key, n_tables, n_chunks, R, transposed, nkb, P));
+    VFMM_CHECK(build_split_plan(tgt_id, items, key, n_tables, n_chunks, R, transposed, nkb, A, P));
     const int nt = (int)tgt_id.size();
     const int64_t G = P->group;
     std::vector<int64_t> per_table(n_tables, 0);
@@ -636,7 +647,7 @@ int build_contraction_plan(const std::vector<int32_t>& tgt_id,
     }
     seg[nt] = (int32_t)q;
     SplitPlan* E = new SplitPlan();
-    int rc = build_split_plan(e_tgt, e_items, e_key, n_tables, n_chunks, R, transposed, nkb, E);
+    int rc = build_split_plan(e_tgt, e_items, e_key, n_tables, n_chunks, R, transposed, nkb, A, E);
     if (rc == VFMM_OK) {
         E->entry = true;  // the slab occupies the partial-sum buffer: no split-K
         E->may_split = false;
@@ -644,12 +655,8 @@ int build_contraction_plan(const std::vector<int32_t>& tgt_id,
         E->R = R;
         E->n_seg = nt;
         E->slab_rows = n_entries * R;
-        cudaError_t e = cudaMalloc(&E->seg, seg.size() * sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMemcpy(E->seg, seg.data(), seg.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&E->seg_out, std::max<size_t>(1, seg_out.size()) * sizeof(int32_t));
-        if (e == cudaSuccess && nt)
-            e = cudaMemcpy(E->seg_out, seg_out.data(), seg_out.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) rc = cuda_fail(e, "entry-major plan");
+        E->off[4] = A.put(seg);
+        E->off[5] = A.put(seg_out);
     }
     if (rc != VFMM_OK) {
         free_split_plan(E);
@@ -669,15 +676,13 @@ int build_contraction_plan(const std::vector<int32_t>& tgt_id,
     return VFMM_OK;
 }
 
+// The index arrays live in the plan set's arena: a plan owns only its alternative form.
 void free_split_plan(SplitPlan* P) {
     if (P->alt) {
         free_split_plan(P->alt);
         delete P->alt;
         P->alt = nullptr;
     }
-    int32_t* ps[] = {P->tgt, P->ptr, P->cfg, P->src, P->seg, P->seg_out};
-    for (int32_t* p : ps)
-        if (p) cudaFree(p);
     *P = SplitPlan();
 }
 
@@ -687,6 +692,8 @@ void free_plan_set(PlanSet* ps) {
     free_split_plan(&ps->m2l);
     free_split_plan(&ps->far);
     free_split_plan(&ps->s2l);
+    if (ps->arena) cudaFree(ps->arena);
+    ps->arena = nullptr;
 }
 
 static size_t smem_bytes(int N) { return (size_t)kStages * kSlices * (kTileM * 64 + N * 64) + 1024; }
@@ -812,15 +819,14 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
 }
 
 // Near field: targets are leaves; tables are the 33 configurations; A rows are leaves.
-static int build_plans(const DeviceTree& T, int R, PlanSet* PS) {
+static int build_plans(const DeviceTree& T, int R, const HostLists& H, PlanSet* PS) {
     PS->R = R;
-    const int nb = T.n_boxes, nl = T.n_leaves;
-    std::vector<int32_t> ptr(nb + 1), idx(T.llen[VFMM_LIST_U]), cfg(T.llen[VFMM_LIST_U]), bol(nl), lob(nb);
-    VFMM_CUDA(cudaMemcpy(ptr.data(), T.lptr[VFMM_LIST_U], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(idx.data(), T.lidx[VFMM_LIST_U], idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(cfg.data(), T.lcfg[VFMM_LIST_U], cfg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(bol.data(), T.box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(lob.data(), T.leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const int nl = T.n_leaves;
+    const std::vector<int32_t>& ptr = H.ptr[VFMM_LIST_U];
+    const std::vector<int32_t>& idx = H.idx[VFMM_LIST_U];
+    const std::vector<int32_t>& cfg = H.cfg[VFMM_LIST_U];
+    const std::vector<int32_t>& bol = H.bol;
+    const std::vector<int32_t>& lob = H.lob;
     std::vector<int32_t> tgt(nl);
     std::vector<std::vector<std::pair<int32_t, int32_t>>> items(nl);
     std::vector<std::pair<uint64_t, uint64_t>> key(nl);
@@ -838,16 +844,20 @@ static int build_plans(const DeviceTree& T, int R, PlanSet* PS) {
     const bool tr = near_transposed(T.k);
     const int tile_rows = table_rows_per_tile(tr);
     const int Kp = (T.k * T.k + kKBlock - 1) / kKBlock * kKBlock;
+    PlanArena A;
     VFMM_CHECK(build_contraction_plan(tgt, items, key, kNearCfg, (rows + tile_rows - 1) / tile_rows, R, tr,
-                                      Kp / kKBlock, 48.0 / Kp, (size_t)rows * sizeof(float2), &PS->near));
-    return build_far_plans(T, R, PS);
+                                      Kp / kKBlock, 48.0 / Kp, (size_t)rows * sizeof(float2), A, &PS->near));
+    VFMM_CHECK(build_far_plans(T, R, H, A, PS));
+    return commit_plan_arena(A, PS);
 }
 
 int build_mixed_plan(DeviceTree* T) {
-    VFMM_CHECK(build_far_slots(T));
+    HostLists H;
+    VFMM_CHECK(fetch_host_lists(*T, &H));
+    VFMM_CHECK(build_far_slots(T, H));
     T->plans_r = new std::map<int, PlanSet*>();
     T->plans_mu = new std::mutex();
-    return build_plans(*T, 1, &T->plans);
+    return build_plans(*T, 1, H, &T->plans);
 }
 
 int plans_for(const DeviceTree& T, int R, const PlanSet** out) {
@@ -863,7 +873,9 @@ int plans_for(const DeviceTree& T, int R, const PlanSet** out) {
         return VFMM_OK;
     }
     PlanSet* ps = new PlanSet();
-    int rc = build_plans(T, R, ps);
+    HostLists H;
+    int rc = fetch_host_lists(T, &H);
+    if (rc == VFMM_OK) rc = build_plans(T, R, H, ps);
     if (rc != VFMM_OK) {
         free_plan_set(ps);
         delete ps;

@@ -171,10 +171,10 @@ struct MixedOps {
     double* s2l_r0 = nullptr; // [20][kk] FP64: Re of S2L row 0
     double* m2l_r0 = nullptr; // [40][p+1] complex FP64: M2L row 0 (output coefficient 0) per offset
     // slices taken per contraction (kCtr*): the first S of the 8 stored slices of each operand and
-    // the S(S+1)/2 products i + j <= S + 1. Defaults: 7 (49 bits) for the near field, M2L and the
-    // leaf far field, 6 (42 bits) for S2M and S2L, the fewest that keep the error against the FP64
-    // form at least 5x below 1e-10 on the 20-Gaussian, kinked and uniform k = 16 workloads
-    int slices[kNumCtr] = {7, 6, 7, 6, 7};
+    // the S(S+1)/2 products i + j <= S + 1. Default 6 for all (42 bits, 21 products): the error
+    // against the FP64 form is then at most 6e-12 on the 20-Gaussian, kinked and uniform k = 16
+    // workloads, 17x below 1e-10 (7 for all: 6e-14)
+    int slices[kNumCtr] = {6, 6, 6, 6, 6};
 };
 
 struct MixedWork {
@@ -200,10 +200,26 @@ struct MixedWork {
     cudaEvent_t* cev = nullptr;           // optional (start, stop) pairs: near, S2M, M2L, S2L, far
 };
 
+// Host staging of the index arrays of one plan set: put() appends an array and returns its offset
+// (int32 elements; pieces start on 256-byte boundaries); commit_plan_arena() makes one device
+// allocation, copies everything once and points every plan of the set (and its alternative form)
+// into it.
+struct PlanArena {
+    std::vector<int32_t> data;
+    int64_t put(const std::vector<int32_t>& v) {
+        const int64_t off = (int64_t)data.size();
+        const size_t len = std::max<size_t>(64, (v.size() + 63) / 64 * 64);
+        data.resize(off + len, 0);
+        std::copy(v.begin(), v.end(), data.begin() + off);
+        return off;
+    }
+};
+int commit_plan_arena(PlanArena& A, PlanSet* PS);
+
 int build_split_plan(const std::vector<int32_t>& tgt_id,
                      const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                      const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                     bool transposed, int nkb, SplitPlan* P);
+                     bool transposed, int nkb, PlanArena& A, SplitPlan* P);
 // build_split_plan, or its entry-major form when that executes enough fewer columns: chosen when
 // (entry-major columns) x (1 + slab_overhead) < 0.85 x (grouped columns, padding included) and the
 // slab (entries x R x slab_row_bytes) stays within 256 MB. slab_overhead = the slab's write and read
@@ -212,7 +228,8 @@ int build_split_plan(const std::vector<int32_t>& tgt_id,
 int build_contraction_plan(const std::vector<int32_t>& tgt_id,
                            const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
                            const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                           bool transposed, int nkb, double slab_overhead, size_t slab_row_bytes, SplitPlan* P);
+                           bool transposed, int nkb, double slab_overhead, size_t slab_row_bytes, PlanArena& A,
+                           SplitPlan* P);
 // Tensor map of a sliced table [rows][Kp / 32][kSlices][32] BF16 for the table operand of split_gemm
 // (box = box_rows rows x 64 bytes of one slice and K block).
 int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtensorMap* out);
@@ -223,8 +240,13 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
 // [0] S2M, M2L and the leaf far field (one after another), [1] the near field, [2] S2L.
 void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t elems[3]);
 int build_mixed_plan(DeviceTree* T);
-int build_far_slots(DeviceTree* T);
-int build_far_plans(const DeviceTree& T, int R, PlanSet* PS);
+// Host copies of the tree arrays the plan builders read (fetched once per plan set).
+struct HostLists {
+    std::vector<int32_t> bol, lob, ptr[4], idx[4], cfg[4];
+};
+int fetch_host_lists(const DeviceTree& T, HostLists* H);
+int build_far_slots(DeviceTree* T, const HostLists& H);
+int build_far_plans(const DeviceTree& T, int R, const HostLists& H, PlanArena& A, PlanSet* PS);
 // Near field in two parts: max |f| and the f slices (also the operand of S2M and S2L), then the
 // split contraction.
 int near_slices(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, const MixedWork& w,

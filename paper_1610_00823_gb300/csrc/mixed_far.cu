@@ -197,11 +197,30 @@ void far_free(MixedOps* mo) {
 // ---------------------------------------------------------------- schedules
 // Rows of the leaf far-field operand: per leaf, slot 0 = its own local (L2T), slot 1 + j = its
 // j-th W entry; far_slot[leaf] = first slot (right-hand side r of slot s is row s * R + r).
-int build_far_slots(DeviceTree* T) {
-    const int nb = T->n_boxes, nl = T->n_leaves;
-    std::vector<int32_t> bol(nl), ptr(nb + 1), slot(nl + 1, 0);
-    VFMM_CUDA(cudaMemcpy(bol.data(), T->box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(ptr.data(), T->lptr[VFMM_LIST_W], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+int fetch_host_lists(const DeviceTree& T, HostLists* H) {
+    const int nb = T.n_boxes, nl = T.n_leaves;
+    H->bol.resize(nl);
+    H->lob.resize(nb);
+    VFMM_CUDA(cudaMemcpy(H->bol.data(), T.box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    VFMM_CUDA(cudaMemcpy(H->lob.data(), T.leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < 4; ++q) {
+        H->ptr[q].resize(nb + 1);
+        H->idx[q].resize(T.llen[q]);
+        H->cfg[q].resize(T.llen[q]);
+        VFMM_CUDA(cudaMemcpy(H->ptr[q].data(), T.lptr[q], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (T.llen[q]) {
+            VFMM_CUDA(cudaMemcpy(H->idx[q].data(), T.lidx[q], T.llen[q] * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            VFMM_CUDA(cudaMemcpy(H->cfg[q].data(), T.lcfg[q], T.llen[q] * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+    }
+    return VFMM_OK;
+}
+
+int build_far_slots(DeviceTree* T, const HostLists& H) {
+    const int nl = T->n_leaves;
+    const std::vector<int32_t>& bol = H.bol;
+    const std::vector<int32_t>& ptr = H.ptr[VFMM_LIST_W];
+    std::vector<int32_t> slot(nl + 1, 0);
     for (int t = 0; t < nl; ++t) slot[t + 1] = slot[t] + 1 + (ptr[bol[t] + 1] - ptr[bol[t]]);
     T->n_far_slots = slot[nl];
     VFMM_CUDA(cudaMalloc(&T->far_slot, (nl + 1) * sizeof(int32_t)));
@@ -209,24 +228,18 @@ int build_far_slots(DeviceTree* T) {
     return VFMM_OK;
 }
 
-int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
+int build_far_plans(const DeviceTree& T, int R, const HostLists& H, PlanArena& A, PlanSet* PS) {
     const int nb = T.n_boxes, nl = T.n_leaves;
     // K blocks per table: k^2 for S2M and S2L; 2(p+1) for M2L and the leaf far field, where p is not
     // known to the tree (3 blocks = p up to 47; only the default split-K choice depends on it)
     const int Kp = (T.k * T.k + kKBlock - 1) / kKBlock * kKBlock;
     constexpr int kFarKb = 3;
-    std::vector<int32_t> bol(nl), lob(nb);
-    VFMM_CUDA(cudaMemcpy(bol.data(), T.box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(lob.data(), T.leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const std::vector<int32_t>& bol = H.bol;
+    const std::vector<int32_t>& lob = H.lob;
     auto fetch = [&](int q, std::vector<int32_t>& ptr, std::vector<int32_t>& idx, std::vector<int32_t>& cfg) -> int {
-        ptr.resize(nb + 1);
-        idx.resize(T.llen[q]);
-        cfg.resize(T.llen[q]);
-        VFMM_CUDA(cudaMemcpy(ptr.data(), T.lptr[q], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        if (T.llen[q]) {
-            VFMM_CUDA(cudaMemcpy(idx.data(), T.lidx[q], idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-            VFMM_CUDA(cudaMemcpy(cfg.data(), T.lcfg[q], cfg.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        }
+        ptr = H.ptr[q];
+        idx = H.idx[q];
+        cfg = H.cfg[q];
         return VFMM_OK;
     };
     // S2M: every leaf, one table, A row = the leaf
@@ -239,7 +252,7 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             items[t].push_back({0, t});
             key[t] = {0, (uint64_t)t};
         }
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, R, false, Kp / kKBlock, &PS->s2m));
+        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, R, false, Kp / kKBlock, A, &PS->s2m));
     }
     // M2L: boxes with a V list, tables = the 40 offsets, A row = source box
     {
@@ -260,7 +273,7 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             key.push_back({sig, (uint64_t)b});
         }
         // slab costs relative to the tensor work per column: K = 2(p+1) padded (about 96), rows <= 128
-        VFMM_CHECK(build_contraction_plan(tgt, items, key, kVCfg, 1, R, false, kFarKb, 0.5, 128 * sizeof(float2),
+        VFMM_CHECK(build_contraction_plan(tgt, items, key, kVCfg, 1, R, false, kFarKb, 0.5, 128 * sizeof(float2), A,
                                           &PS->m2l));
     }
     // S2L: boxes with an X list, tables 20 configurations, A row = source leaf
@@ -282,7 +295,7 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
             key.push_back({sig, (uint64_t)b});
         }
         VFMM_CHECK(build_contraction_plan(tgt, items, key, kFarCfg, 1, R, false, Kp / kKBlock, 48.0 / Kp,
-                                          128 * sizeof(float2), &PS->s2l));
+                                          128 * sizeof(float2), A, &PS->s2l));
     }
     // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
     {
@@ -307,7 +320,7 @@ int build_far_plans(const DeviceTree& T, int R, PlanSet* PS) {
         const bool tr = near_transposed(T.k);
         const int tile_rows = table_rows_per_tile(tr);
         VFMM_CHECK(build_contraction_plan(tgt, items, key, 1 + kFarCfg, (rows + tile_rows - 1) / tile_rows, R, tr,
-                                          kFarKb, 0.5, (size_t)rows * sizeof(float2), &PS->far));
+                                          kFarKb, 0.5, (size_t)rows * sizeof(float2), A, &PS->far));
     }
     return VFMM_OK;
 }

@@ -19,6 +19,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <set>
 #include <tuple>
 #include <unordered_map>
@@ -29,19 +30,54 @@
 
 namespace vfmm {
 
+// Stream-ordered pool of the tree build's temporaries on the current device (created once, kept
+// for the life of the process; up to 256 MB of freed blocks stay reserved for the next build).
+static int build_pool(cudaMemPool_t* out) {
+    constexpr int kMaxDevices = 16;
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    int dev = 0;
+    VFMM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(VFMM_ERR_INTERNAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        VFMM_CUDA(cudaMemPoolCreate(&pools[dev], &props));
+        uint64_t keep = uint64_t(256) << 20;
+        VFMM_CUDA(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    *out = pools[dev];
+    return VFMM_OK;
+}
+
+// Device buffer of the tree build. alloc(count, st): a temporary from the build pool, allocated
+// and freed in the order of stream st (no free waits for the device; the stream must outlive the
+// buffer); alloc_keep(count): an array the tree or a builder keeps (cudaMalloc), which release()
+// hands over.
 template <class T>
 struct DBuf {
     T* p = nullptr;
     size_t n = 0;
+    cudaStream_t st = nullptr;
+    bool pooled = false;
     DBuf() = default;
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
-    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), st(o.st), pooled(o.pooled) {
+        o.p = nullptr;
+        o.n = 0;
+    }
     DBuf& operator=(DBuf&& o) noexcept {
         if (this != &o) {
             reset();
             p = o.p;
             n = o.n;
+            st = o.st;
+            pooled = o.pooled;
             o.p = nullptr;
             o.n = 0;
         }
@@ -49,11 +85,29 @@ struct DBuf {
     }
     ~DBuf() { reset(); }
     void reset() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (pooled) cudaFreeAsync(p, st);
+            else cudaFree(p);
+        }
         p = nullptr;
         n = 0;
     }
-    int alloc(size_t count) {
+    int alloc(size_t count, cudaStream_t s) {
+        reset();
+        n = count;
+        if (count == 0) return VFMM_OK;
+        cudaMemPool_t pool;
+        VFMM_CHECK(build_pool(&pool));
+        cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&p), count * sizeof(T), pool, s);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(VFMM_ERR_OOM, "stream-ordered allocation failed in tree build");
+        }
+        st = s;
+        pooled = true;
+        return VFMM_OK;
+    }
+    int alloc_keep(size_t count) {
         reset();
         n = count;
         if (count == 0) return VFMM_OK;
@@ -62,6 +116,7 @@ struct DBuf {
             p = nullptr;
             return fail(VFMM_ERR_OOM, "cudaMalloc failed in tree build");
         }
+        pooled = false;
         return VFMM_OK;
     }
     T* release() {
@@ -121,7 +176,7 @@ static int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* t
     }
     int64_t nb = (n + kScanItems - 1) / kScanItems;
     DBuf<int32_t> sums, sums_x;
-    VFMM_CHECK(sums.alloc(nb));
+    VFMM_CHECK(sums.alloc(nb, st));
     scan_blocks_kernel<<<(unsigned)nb, 256, 0, st>>>(in, out, sums.p, n);
     VFMM_CUDA(cudaGetLastError());
     if (nb == 1) {
@@ -131,7 +186,7 @@ static int exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int64_t* t
         *total = h;
         return VFMM_OK;
     }
-    VFMM_CHECK(sums_x.alloc(nb));
+    VFMM_CHECK(sums_x.alloc(nb, st));
     VFMM_CHECK(exclusive_scan(sums.p, sums_x.p, nb, total, st));
     scan_add_kernel<<<(unsigned)nb, 256, 0, st>>>(out, sums_x.p, n);
     VFMM_CUDA(cudaGetLastError());
@@ -609,8 +664,8 @@ static int upload_node_tables(int k, BuildCtx& B) {
             double v = std::cos(m * std::acos(std::min(1.0, std::max(-1.0, t))));
             C[m * k + i] = (m == 0 ? 1.0 : 2.0) / k * v;
         }
-    VFMM_CHECK(B.xhat.alloc(k));
-    VFMM_CHECK(B.C.alloc(k * k));
+    VFMM_CHECK(B.xhat.alloc_keep(k));
+    VFMM_CHECK(B.C.alloc_keep(k * k));
     VFMM_CUDA(cudaMemcpyAsync(B.xhat.p, xh.data(), k * sizeof(double), cudaMemcpyHostToDevice, B.st));
     VFMM_CUDA(cudaMemcpyAsync(B.C.p, C.data(), k * k * sizeof(double), cudaMemcpyHostToDevice, B.st));
     return VFMM_OK;
@@ -634,16 +689,21 @@ static int upload_child_basis(int k, BuildCtx& B) {
             L[I * k + i] = num / den;
         }
     }
-    VFMM_CHECK(B.L.alloc(2 * k * k));
+    VFMM_CHECK(B.L.alloc_keep(2 * k * k));
     VFMM_CUDA(cudaMemcpyAsync(B.L.p, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, B.st));
     return VFMM_OK;
+}
+
+// out[c] = in[c * stride], c < n.
+__global__ void strided_gather_kernel(const int32_t* __restrict__ in, int64_t stride, int n, int32_t* __restrict__ out) {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) out[c] = in[(int64_t)c * stride];
 }
 
 static int compute_lists(DeviceTree* T, cudaStream_t st) {
     const int n = T->n_boxes;
     TreeView V{T->key, T->level_start_dev, T->level, T->ix, T->iy, T->parent, T->child0, T->depth};
     DBuf<int32_t> cnt;
-    VFMM_CHECK(cnt.alloc((size_t)4 * n));
+    VFMM_CHECK(cnt.alloc((size_t)4 * n, st));
     list_count_kernel<<<nblk(n, 128), 128, 0, st>>>(V, n, cnt.p);
     VFMM_CUDA(cudaGetLastError());
     // one scan over the 4 concatenated count arrays; row q starts at total of rows < q
@@ -657,9 +717,9 @@ static int compute_lists(DeviceTree* T, cudaStream_t st) {
     DBuf<int32_t> idx[4], cfg[4], ptr[4];
     for (int q = 0; q < 4; ++q) {
         T->llen[q] = starts[q + 1] - starts[q];
-        VFMM_CHECK(idx[q].alloc(std::max<int64_t>(1, T->llen[q])));
-        VFMM_CHECK(cfg[q].alloc(std::max<int64_t>(1, T->llen[q])));
-        VFMM_CHECK(ptr[q].alloc(n + 1));
+        VFMM_CHECK(idx[q].alloc_keep(std::max<int64_t>(1, T->llen[q])));
+        VFMM_CHECK(cfg[q].alloc_keep(std::max<int64_t>(1, T->llen[q])));
+        VFMM_CHECK(ptr[q].alloc_keep(n + 1));
     }
     // offsets within each list: subtract the row start
     for (int q = 0; q < 4; ++q) {
@@ -677,9 +737,9 @@ static int compute_lists(DeviceTree* T, cudaStream_t st) {
     // U entries grouped by configuration, stable (flattened config-major scan)
     const int64_t nU = T->llen[VFMM_LIST_U];
     DBuf<int32_t> flags, byc, tgt;
-    VFMM_CHECK(flags.alloc((size_t)kNearCfg * nU));
-    VFMM_CHECK(byc.alloc(std::max<int64_t>(1, nU)));
-    VFMM_CHECK(tgt.alloc(std::max<int64_t>(1, nU)));
+    VFMM_CHECK(flags.alloc((size_t)kNearCfg * nU, st));
+    VFMM_CHECK(byc.alloc_keep(std::max<int64_t>(1, nU)));
+    VFMM_CHECK(tgt.alloc_keep(std::max<int64_t>(1, nU)));
     cfg_flags_kernel<<<nblk(nU), 256, 0, st>>>(T->lcfg[0], nU, kNearCfg, flags.p);
     VFMM_CUDA(cudaGetLastError());
     int64_t tot = 0;
@@ -687,12 +747,17 @@ static int compute_lists(DeviceTree* T, cudaStream_t st) {
     cfg_scatter_kernel<<<nblk(nU), 256, 0, st>>>(T->lcfg[0], flags.p, nU, byc.p);
     entry_target_kernel<<<nblk(n), 256, 0, st>>>(T->lptr[0], n, tgt.p);
     VFMM_CUDA(cudaGetLastError());
+    // first entry of each configuration: flags[c * nU], gathered and read back once
     T->u_cfg_start.assign(kNearCfg + 1, 0);
-    for (int c = 0; c < kNearCfg; ++c) {
-        int32_t v = 0;
-        VFMM_CUDA(cudaMemcpyAsync(&v, flags.p + (int64_t)c * nU, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (nU > 0) {
+        DBuf<int32_t> starts_dev;
+        VFMM_CHECK(starts_dev.alloc(kNearCfg, st));
+        strided_gather_kernel<<<1, 64, 0, st>>>(flags.p, nU, kNearCfg, starts_dev.p);
+        VFMM_CUDA(cudaGetLastError());
+        int32_t h[kNearCfg];
+        VFMM_CUDA(cudaMemcpyAsync(h, starts_dev.p, kNearCfg * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         VFMM_CUDA(cudaStreamSynchronize(st));
-        T->u_cfg_start[c] = v;
+        for (int c = 0; c < kNearCfg; ++c) T->u_cfg_start[c] = h[c];
     }
     T->u_cfg_start[kNearCfg] = nU;
     T->u_by_cfg = byc.release();
@@ -735,9 +800,9 @@ static int greedy_refine(const BuildCtx& B, const SourceDev& src, int max_depth,
         DBuf<int32_t> dl;
         DBuf<uint32_t> dk;
         DBuf<double> dt;
-        VFMM_CHECK(dl.alloc(n));
-        VFMM_CHECK(dk.alloc(n));
-        VFMM_CHECK(dt.alloc(n));
+        VFMM_CHECK(dl.alloc(n, B.st));
+        VFMM_CHECK(dk.alloc(n, B.st));
+        VFMM_CHECK(dt.alloc(n, B.st));
         VFMM_CUDA(cudaMemcpyAsync(dl.p, lev.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, B.st));
         VFMM_CUDA(cudaMemcpyAsync(dk.p, key.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, B.st));
         tail_kernel<<<(unsigned)n, threads, 0, B.st>>>(B.g, src, dl.p, dk.p, n, B.C.p, dt.p);
@@ -814,7 +879,7 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
     T->width = prm->width;
 
     DBuf<double> scal;  // [0] = F, [1] = min margin, [2] = margin sink of the depth-cap test
-    VFMM_CHECK(scal.alloc(3));
+    VFMM_CHECK(scal.alloc(3, st));
     double init[3] = {0.0, INFINITY, INFINITY};
     VFMM_CUDA(cudaMemcpyAsync(scal.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
     double thresh = 0.0;
@@ -837,21 +902,21 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
         depth = (int)lv.size() - 1;
         for (int l = 0; l <= depth; ++l) {
             cnt[l] = (int64_t)lv[l].size();
-            VFMM_CHECK(keys[l].alloc(cnt[l]));
+            VFMM_CHECK(keys[l].alloc(cnt[l], st));
             VFMM_CUDA(cudaMemcpy(keys[l].p, lv[l].data(), cnt[l] * sizeof(uint32_t), cudaMemcpyHostToDevice));
         }
         T->min_margin = mm;
         T->n_capped = -1;  // refined to a leaf count, not to the test
     } else {
-        VFMM_CHECK(keys[0].alloc(1));
+        VFMM_CHECK(keys[0].alloc(1, st));
         uint32_t zero = 0;
         VFMM_CUDA(cudaMemcpyAsync(keys[0].p, &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
         cnt[0] = 1;
         for (int l = 0; l < max_depth; ++l) {
             const int64_t n = cnt[l];
             DBuf<int32_t> flags, offs;
-            VFMM_CHECK(flags.alloc(n));
-            VFMM_CHECK(offs.alloc(n));
+            VFMM_CHECK(flags.alloc(n, st));
+            VFMM_CHECK(offs.alloc(n, st));
             if (l < min_depth) {
                 fill_kernel<<<nblk(n), 256, 0, st>>>(flags.p, n, 1);
             } else if (rule == VFMM_REFINE_TAIL) {
@@ -866,7 +931,7 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
             int64_t m = 0;
             VFMM_CHECK(exclusive_scan(flags.p, offs.p, n, &m, st));
             if (m == 0) break;
-            VFMM_CHECK(keys[l + 1].alloc(4 * m));
+            VFMM_CHECK(keys[l + 1].alloc(4 * m, st));
             emit_children_kernel<<<nblk(n), 256, 0, st>>>(keys[l].p, flags.p, offs.p, (int)n, keys[l + 1].p);
             VFMM_CUDA(cudaGetLastError());
             cnt[l + 1] = 4 * m;
@@ -882,8 +947,8 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
             T->n_capped = 0;
             if (nc > 0) {
                 DBuf<int32_t> cf, co;
-                VFMM_CHECK(cf.alloc(nc));
-                VFMM_CHECK(co.alloc(nc));
+                VFMM_CHECK(cf.alloc(nc, st));
+                VFMM_CHECK(co.alloc(nc, st));
                 if (rule == VFMM_REFINE_TAIL) {
                     refine_kernel<<<(unsigned)nc, ((k * k + 31) / 32) * 32, 0, st>>>(
                         B.g, *src, max_depth, keys[max_depth].p, (int)nc, B.C.p, thresh, cf.p, scal.p + 2);
@@ -912,8 +977,8 @@ static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt
         const int64_t nw = std::max<int64_t>(1, nbits / 32);
         DBuf<uint32_t> bm;
         DBuf<int32_t> wc;
-        VFMM_CHECK(bm.alloc(nw));
-        VFMM_CHECK(wc.alloc(nw));
+        VFMM_CHECK(bm.alloc(nw, st));
+        VFMM_CHECK(wc.alloc(nw, st));
         VFMM_CUDA(cudaMemsetAsync(bm.p, 0, nw * sizeof(uint32_t), st));
         int64_t nmax = std::max(cnt[l], cnt[l - 1]);
         balance_mark_kernel<<<nblk(nmax), 256, 0, st>>>(keys[l].p, (int)cnt[l], keys[l - 1].p, (int)cnt[l - 1], l,
@@ -923,9 +988,9 @@ static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt
         int64_t ns = 0;
         VFMM_CHECK(exclusive_scan(wc.p, wc.p, nw, &ns, st));
         DBuf<uint32_t> split;
-        VFMM_CHECK(split.alloc(ns));
+        VFMM_CHECK(split.alloc(ns, st));
         bitmap_emit_kernel<<<nblk(nw), 256, 0, st>>>(bm.p, nw, wc.p, split.p);
-        VFMM_CHECK(keys[l - 1].alloc(4 * ns));
+        VFMM_CHECK(keys[l - 1].alloc(4 * ns, st));
         children_of_kernel<<<nblk(ns), 256, 0, st>>>(split.p, (int)ns, keys[l - 1].p);
         VFMM_CUDA(cudaGetLastError());
         cnt[l - 1] = 4 * ns;
@@ -939,16 +1004,16 @@ static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt
     T->n_boxes = n;
     DBuf<uint32_t> key;
     DBuf<int32_t> level, ix, iy, parent, child0, isleaf, rank, lob, bol, lsd;
-    VFMM_CHECK(key.alloc(n));
-    VFMM_CHECK(level.alloc(n));
-    VFMM_CHECK(ix.alloc(n));
-    VFMM_CHECK(iy.alloc(n));
-    VFMM_CHECK(parent.alloc(n));
-    VFMM_CHECK(child0.alloc(n));
-    VFMM_CHECK(isleaf.alloc(n));
-    VFMM_CHECK(rank.alloc(n));
-    VFMM_CHECK(lob.alloc(n));
-    VFMM_CHECK(lsd.alloc(depth + 2));
+    VFMM_CHECK(key.alloc_keep(n));
+    VFMM_CHECK(level.alloc_keep(n));
+    VFMM_CHECK(ix.alloc_keep(n));
+    VFMM_CHECK(iy.alloc_keep(n));
+    VFMM_CHECK(parent.alloc_keep(n));
+    VFMM_CHECK(child0.alloc_keep(n));
+    VFMM_CHECK(isleaf.alloc(n, st));
+    VFMM_CHECK(rank.alloc(n, st));
+    VFMM_CHECK(lob.alloc_keep(n));
+    VFMM_CHECK(lsd.alloc_keep(depth + 2));
     for (int l = 0; l <= depth; ++l)
         VFMM_CUDA(cudaMemcpyAsync(key.p + T->level_start[l], keys[l].p, cnt[l] * sizeof(uint32_t),
                                   cudaMemcpyDeviceToDevice, st));
@@ -958,7 +1023,7 @@ static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt
     VFMM_CUDA(cudaGetLastError());
     int64_t nleaf = 0;
     VFMM_CHECK(exclusive_scan(isleaf.p, rank.p, n, &nleaf, st));
-    VFMM_CHECK(bol.alloc(nleaf));
+    VFMM_CHECK(bol.alloc_keep(nleaf));
     leaf_rank_kernel<<<nblk(n), 256, 0, st>>>(isleaf.p, rank.p, n, lob.p, bol.p);
     VFMM_CUDA(cudaGetLastError());
     T->n_leaves = (int32_t)nleaf;
@@ -1037,7 +1102,7 @@ int make_source(const vfmm_source* s, DBuf<double>& buf, SourceDev* out, cudaStr
         len = 4 * s->n;
     } else if (s->kind == VFMM_SRC_KINKED) len = 54;
     else return fail(VFMM_ERR_INVALID_ARG, "unknown source kind");
-    VFMM_CHECK(buf.alloc(len));
+    VFMM_CHECK(buf.alloc(len, st));
     VFMM_CUDA(cudaMemcpyAsync(buf.p, s->params, len * sizeof(double), cudaMemcpyHostToDevice, st));
     out->kind = s->kind;
     out->n = s->n;
@@ -1141,8 +1206,8 @@ static int builder_split(vfmm_tree_builder* b, const double* fv) {
     const int64_t n = b->cnt[l];
     cudaStream_t st = b->st;
     DBuf<int32_t> flags, offs;
-    VFMM_CHECK(flags.alloc(n));
-    VFMM_CHECK(offs.alloc(n));
+    VFMM_CHECK(flags.alloc(n, st));
+    VFMM_CHECK(offs.alloc(n, st));
     if (!fv)
         fill_kernel<<<nblk(n), 256, 0, st>>>(flags.p, n, 1);
     else
@@ -1156,7 +1221,7 @@ static int builder_split(vfmm_tree_builder* b, const double* fv) {
         b->phase = 2;
         return VFMM_OK;
     }
-    VFMM_CHECK(b->keys[l + 1].alloc(4 * m));
+    VFMM_CHECK(b->keys[l + 1].alloc_keep(4 * m));
     emit_children_kernel<<<nblk(n), 256, 0, st>>>(b->keys[l].p, flags.p, offs.p, (int)n, b->keys[l + 1].p);
     VFMM_CUDA(cudaGetLastError());
     b->cnt[l + 1] = 4 * m;
@@ -1201,8 +1266,8 @@ extern "C" int vfmm_tree_begin(const vfmm_tree_params* prm, void* stream, vfmm_t
     b->cnt.assign(prm->max_depth + 1, 0);
     int rc = upload_node_tables(prm->k, b->B);
     b->B.g = NodeGeom{prm->cx - prm->width / 2.0, prm->cy - prm->width / 2.0, prm->width, prm->k, b->B.xhat.p};
-    if (rc == VFMM_OK) rc = b->keys[0].alloc(1);
-    if (rc == VFMM_OK) rc = b->scal.alloc(2);
+    if (rc == VFMM_OK) rc = b->keys[0].alloc_keep(1);
+    if (rc == VFMM_OK) rc = b->scal.alloc_keep(2);
     if (rc == VFMM_OK) {
         const uint32_t zero = 0;
         const double init[2] = {0.0, INFINITY};
@@ -1277,6 +1342,9 @@ extern "C" int vfmm_tree_finish(vfmm_tree_builder* b, vfmm_tree** out) {
     T->min_margin = mm;
     if (rc == VFMM_OK) rc = finalize(b->keys, b->cnt, b->depth, b->st, T);
     b->phase = 3;
+    // balancing replaced keys by stream-ordered temporaries: release them on b->st while it is
+    // known to be valid (the builder may outlive the caller's stream)
+    for (auto& kb : b->keys) kb.reset();
     if (rc != VFMM_OK) {
         free_tree(T);
         delete t;

@@ -179,6 +179,9 @@ struct SplitPlan {
     int32_t* seg_out = nullptr;  // [n_seg] output row (before the R fold) of each target
     // the other form of a small contraction (grouped or entry-major), for vfmm_tune to time
     SplitPlan* alt = nullptr;
+    // offsets (int32 elements) of tgt, ptr, cfg, src, seg, seg_out in the plan set's arena while it
+    // is being built (-1: absent); the pointers above point into the arena once it is committed
+    int64_t off[6] = {-1, -1, -1, -1, -1, -1};
 };
 
 // The split contractions of the mixed form with R right-hand sides folded into the rows: the
@@ -190,6 +193,7 @@ struct PlanSet {
     SplitPlan m2l;   // V list: targets boxes, tables the 40 offsets, A rows boxes
     SplitPlan far;   // L2T + W list: targets leaves, tables 0 (L2T) and 1 + W configuration, A rows far slots
     SplitPlan s2l;   // X list: targets boxes, tables 20 configurations, A rows leaves
+    void* arena = nullptr;  // one device allocation holding every index array of the plans above
 };
 
 struct DeviceTree {

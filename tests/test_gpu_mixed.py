@@ -273,11 +273,11 @@ def test_slice_counts_trade_accuracy_for_products():
     f = v.source_sample(gt, src)
     u64 = v.volume_potential(gt, v.ops_create(16, 40, v.FP64), f)
     ops = v.ops_create(16, 40, v.MIXED)
-    assert ops.slices == {"near": 7, "s2m": 6, "m2l": 7, "s2l": 6, "far": 7}
+    assert ops.slices == {"near": 6, "s2m": 6, "m2l": 6, "s2l": 6, "far": 6}
     for bad in (5, 9):
         with pytest.raises(VfmmError):
             ops.set_slices(near=bad)
-    assert ops.slices["near"] == 7
+    assert ops.slices["near"] == 6
     with pytest.raises(VfmmError):
         v.ops_create(16, 40, v.FP64).set_slices(near=7)
     base = solve_work(gt, ops)["near_tc_flops"]
@@ -286,6 +286,6 @@ def test_slice_counts_trade_accuracy_for_products():
         ops.set_slices(**{c: S for c in ops.CONTRACTIONS})
         u = v.volume_potential(gt, ops, f)
         errs[S] = max(rel(u[q].cpu().numpy(), u64[q].cpu().numpy()) for q in range(3))
-        assert solve_work(gt, ops)["near_tc_flops"] == base * (S * (S + 1) // 2) / 28
-    assert errs[8] < TOL and errs[7] < 10 * TOL and errs[6] < 1e3 * TOL
-    assert errs[6] > errs[8]
+        assert solve_work(gt, ops)["near_tc_flops"] == base * (S * (S + 1) // 2) / 21
+    # balanced base-128 digits: 6 (the default) hold the bar with a 5x margin; more digits, less error
+    assert errs[6] < TOL / 5 and errs[7] < errs[6] and errs[8] < 1e-12, errs
