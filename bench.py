@@ -316,11 +316,10 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
-    trees, fs = [], []
-    for wl, n_t in members:
-        tree = v.tree_build_leaves(0.0, 0.0, 1.0, wl.k, wl.sources[0], n_t, 16)
-        trees.append(tree)
-        fs.append(v.source_sample(tree, wl.sources[0]))
+    # every member's tree in one native call (host threads, a stream each), then its f
+    trees = v.tree_build_many([dict(cx=0.0, cy=0.0, width=1.0, k=wl.k, source=wl.sources[0], n_leaves=n_t,
+                                    max_depth=16) for wl, n_t in members])
+    fs = [v.source_sample(tree, wl.sources[0]) for (wl, _), tree in zip(members, trees)]
     torch.cuda.synchronize()
     t_tree = time.perf_counter() - t0
     n_targets = sum(f.numel() for f in fs)

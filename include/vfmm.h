@@ -145,6 +145,17 @@ int vfmm_tree_build_rule(const vfmm_tree_params* prm, const vfmm_source* src, in
 int vfmm_tree_build_leaves(const vfmm_tree_params* prm, const vfmm_source* src, int64_t n_leaves, void* stream,
                            vfmm_tree** out);
 
+/* Builds n independent trees at once (a batch of uneven problems; no counterpart in the paper):
+ * tree i as vfmm_tree_build_leaves(&prm[i], &src[i], n_leaves[i], ...) when n_leaves[i] > 0, else as
+ * vfmm_tree_build(&prm[i], &src[i], ...). Up to n_threads host threads (<= 0: one per host core, at
+ * most 16) take trees in turn, each on a CUDA stream of its own on the current device, so that the
+ * host work (priority queues, lists, plans) and the device work of different trees overlap. The
+ * trees are the same as the single builds' (bit for bit). Returns when all are built; out[n] holds
+ * them. Errors: those of the single builds (the first failing tree's code; every tree built so far
+ * is then destroyed and out[] zeroed), INVALID_ARG (null pointers, n < 0). */
+int vfmm_tree_build_many(const vfmm_tree_params* prm, const vfmm_source* src, const int64_t* n_leaves, int32_t n,
+                         int32_t n_threads, vfmm_tree** out);
+
 /* Uniform tree of the given depth (prm->tol and depths ignored). Synchronises. */
 int vfmm_tree_build_uniform(const vfmm_tree_params* prm, int32_t depth, void* stream, vfmm_tree** out);
 

@@ -40,6 +40,8 @@ EXPORTS = {
                                ctypes.POINTER(ctypes.c_void_p)],
     "vfmm_tree_build_uniform": [ctypes.POINTER(TreeParams), ctypes.c_int32, ctypes.c_void_p,
                                 ctypes.POINTER(ctypes.c_void_p)],
+    "vfmm_tree_build_many": [ctypes.POINTER(TreeParams), ctypes.POINTER(Source), ctypes.POINTER(ctypes.c_int64),
+                             ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)],
     "vfmm_tree_build_rule": [ctypes.POINTER(TreeParams), ctypes.POINTER(Source), ctypes.c_int32, ctypes.c_void_p,
                              ctypes.POINTER(ctypes.c_void_p)],
     "vfmm_tree_begin": [ctypes.POINTER(TreeParams), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],

@@ -110,6 +110,29 @@ def tree_build_leaves(cx, cy, width, k, source, n_leaves, max_depth=16, stream=N
     return Tree(h, k)
 
 
+def tree_build_many(specs, n_threads=0) -> list:
+    """vfmm_tree_build_many. specs: dicts with cx, cy, width, k, source, max_depth and either
+    n_leaves (a leaf-count tree, as tree_build_leaves) or tol (and optionally min_depth; as
+    tree_build). The trees are built on up to n_threads host threads (0: one per core, at most 16)."""
+    n = len(specs)
+    prm = (_lib.TreeParams * max(1, n))()
+    src = (_lib.Source * max(1, n))()
+    nl = (ctypes.c_int64 * max(1, n))()
+    keep = []
+    for i, sp in enumerate(specs):
+        n_leaves = int(sp.get("n_leaves") or 0)
+        prm[i] = _lib.TreeParams(sp["cx"], sp["cy"], sp["width"], sp["k"], sp["max_depth"], sp.get("min_depth", 0),
+                                 0.0 if n_leaves > 0 else float(sp["tol"]))
+        s, arr = _source(sp["source"])
+        src[i] = s
+        keep.append(arr)
+        nl[i] = n_leaves
+    out = (ctypes.c_void_p * max(1, n))()
+    call("vfmm_tree_build_many", prm, src, nl, n, int(n_threads), out)
+    del keep
+    return [Tree(ctypes.c_void_p(out[i]), specs[i]["k"]) for i in range(n)]
+
+
 def tree_build_pull(cx, cy, width, k, f, tol, max_depth, min_depth=0, stream=None) -> Tree:
     """Adaptive tree for a caller-evaluated f (vfmm_tree_begin ... vfmm_tree_finish). f(x, y) takes
     cuda float64 tensors of node coordinates and returns f at them (same length); it is called once

@@ -34,6 +34,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mixed.cuh"
@@ -515,18 +516,12 @@ void mixed_free(vfmm_ops* o) {
     o->mixed = nullptr;
 }
 
-// Groups of 128 targets sorted by `key`; per group the tables present and, per table, the A row
-// of each target (-1 when the target has no entry for that table).
-int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
-                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
+int build_split_plan(const PlanItems& I, const std::vector<int32_t>& order, int n_tables, int n_chunks, int R,
                      bool transposed, int nkb, PlanArena& A, SplitPlan* P) {
     const int G = transposed ? kTileN : kTileM;  // targets per group
-    // Targets sorted by key; target t stands for the R consecutive virtual targets t * R + r, whose
-    // A rows are src * R + r: the right-hand sides of one target share its set of tables.
-    const int nt0 = (int)tgt_id.size();
-    std::vector<int32_t> order(nt0);
-    for (int t = 0; t < nt0; ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key[x] < key[y]; });
+    // target t stands for the R consecutive virtual targets t * R + r, whose gathered rows are
+    // src * R + r: the right-hand sides of one target share its set of tables
+    const int nt0 = (int)I.tgt.size();
     const int64_t nt = (int64_t)nt0 * R;
     if (nt > (int64_t)INT32_MAX / 2) return fail(VFMM_ERR_INVALID_ARG, "too many rows for one split contraction");
     const int ng = (int)((nt + G - 1) / G);
@@ -539,19 +534,19 @@ int build_split_plan(const std::vector<int32_t>& tgt_id, const std::vector<std::
         for (int m = 0; m < m_end; ++m) {
             const int64_t v = (int64_t)g * G + m;
             const int t = order[v / R], r = (int)(v % R);
-            gtgt[(size_t)g * G + m] = tgt_id[t] * R + r;
-            for (auto& it : items[t]) present[it.first] = 1;
+            gtgt[(size_t)g * G + m] = I.tgt[t] * R + r;
+            for (int e = I.ptr[t]; e < I.ptr[t + 1]; ++e) present[I.tab[e]] = 1;
         }
         for (int c = 0; c < n_tables; ++c) {
             if (!present[c]) continue;
             slot[c] = (int32_t)gcfg.size();
             gcfg.push_back(c);
-            gsrc.resize(gsrc.size() + G, -1);
         }
+        gsrc.resize(gcfg.size() * G, -1);
         for (int m = 0; m < m_end; ++m) {
             const int64_t v = (int64_t)g * G + m;
             const int t = order[v / R], r = (int)(v % R);
-            for (auto& it : items[t]) gsrc[(size_t)slot[it.first] * G + m] = it.second * R + r;
+            for (int e = I.ptr[t]; e < I.ptr[t + 1]; ++e) gsrc[(size_t)slot[I.tab[e]] * G + m] = I.src[e] * R + r;
         }
         gptr[g + 1] = (int32_t)gcfg.size();
     }
@@ -606,72 +601,78 @@ int commit_plan_arena(PlanArena& A, PlanSet* PS) {
     return VFMM_OK;
 }
 
-int build_contraction_plan(const std::vector<int32_t>& tgt_id,
-                           const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
-                           const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                           bool transposed, int nkb, double slab_overhead, size_t slab_row_bytes, PlanArena& A,
-                           SplitPlan* P) {
+// Targets in the order of their keys.
+static std::vector<int32_t> key_order(const PlanItems& I) {
+    std::vector<int32_t> order(I.tgt.size());
+    for (size_t t = 0; t < order.size(); ++t) order[t] = (int32_t)t;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return I.key[x] < I.key[y]; });
+    return order;
+}
+
+int build_contraction_plan(const PlanItems& I, int n_tables, int n_chunks, int R, bool transposed, int nkb,
+                           double slab_overhead, size_t slab_row_bytes, PlanArena& A, SplitPlan* P) {
     constexpr size_t kMaxSlabBytes = size_t(256) << 20;
-    VFMM_CHECK(build_split_plan(tgt_id, items, key, n_tables, n_chunks, R, transposed, nkb, A, P));
-    const int nt = (int)tgt_id.size();
+    VFMM_CHECK(build_split_plan(I, key_order(I), n_tables, n_chunks, R, transposed, nkb, A, P));
+    const int nt = (int)I.tgt.size();
     const int64_t G = P->group;
-    std::vector<int64_t> per_table(n_tables, 0);
-    int64_t n_entries = 0;
-    for (int t = 0; t < nt; ++t)
-        for (auto& it : items[t]) {
-            ++per_table[it.first];
-            ++n_entries;
-        }
+    const int64_t n_entries = (int64_t)I.tab.size();
+    std::vector<int64_t> per_table(n_tables + 1, 0);
+    for (int64_t e = 0; e < n_entries; ++e) ++per_table[I.tab[e] + 1];
     int64_t entry_cols = 0;
-    for (int c = 0; c < n_tables; ++c) entry_cols += (per_table[c] * R + G - 1) / G * G;
+    for (int c = 0; c < n_tables; ++c) entry_cols += (per_table[c + 1] * R + G - 1) / G * G;
     const double grouped_cols = (double)P->entries * G;
     const size_t slab_bytes = (size_t)n_entries * R * slab_row_bytes;
     if (n_entries == 0 || slab_bytes > kMaxSlabBytes || (double)n_entries * R > (double)INT32_MAX / 2)
         return VFMM_OK;
     const bool prefer_entry = (double)entry_cols * (1.0 + slab_overhead) < 0.85 * grouped_cols;
     if (!prefer_entry && !P->may_split) return VFMM_OK;  // large grouped contraction: no alternative
-    // entry q of target t: a target of its own with the one item, keyed by (table, q)
-    std::vector<int32_t> e_tgt(n_entries), seg(nt + 1, 0), seg_out(nt);
-    std::vector<std::vector<std::pair<int32_t, int32_t>>> e_items(n_entries);
-    std::vector<std::pair<uint64_t, uint64_t>> e_key(n_entries);
-    int64_t q = 0;
+    // entry q (targets in order, their items in order): a target of its own with the one item, in
+    // the order of (table, q) (a counting sort by table)
+    PlanItems E;
+    E.tgt.resize(n_entries);
+    E.ptr.resize(n_entries + 1);
+    E.tab = I.tab;
+    E.src = I.src;
+    for (int64_t q = 0; q <= n_entries; ++q) {
+        if (q < n_entries) E.tgt[q] = (int32_t)q;
+        E.ptr[q] = (int32_t)q;
+    }
+    for (int c = 0; c < n_tables; ++c) per_table[c + 1] += per_table[c];
+    std::vector<int32_t> e_order(n_entries);
+    for (int64_t q = 0; q < n_entries; ++q) e_order[per_table[I.tab[q]]++] = (int32_t)q;
+    std::vector<int32_t> seg(nt + 1), seg_out(nt);
     for (int t = 0; t < nt; ++t) {
-        seg[t] = (int32_t)q;
-        seg_out[t] = tgt_id[t];
-        for (auto& it : items[t]) {
-            e_tgt[q] = (int32_t)q;
-            e_items[q].push_back(it);
-            e_key[q] = {(uint64_t)it.first, (uint64_t)q};
-            ++q;
-        }
+        seg[t] = I.ptr[t];
+        seg_out[t] = I.tgt[t];
     }
-    seg[nt] = (int32_t)q;
-    SplitPlan* E = new SplitPlan();
-    int rc = build_split_plan(e_tgt, e_items, e_key, n_tables, n_chunks, R, transposed, nkb, A, E);
+    seg[nt] = (int32_t)n_entries;
+    SplitPlan* E_plan = new SplitPlan();
+    int rc = build_split_plan(E, e_order, n_tables, n_chunks, R, transposed, nkb, A, E_plan);
     if (rc == VFMM_OK) {
-        E->entry = true;  // the slab occupies the partial-sum buffer: no split-K
-        E->may_split = false;
-        E->split = 1;
-        E->R = R;
-        E->n_seg = nt;
-        E->slab_rows = n_entries * R;
-        E->off[4] = A.put(seg);
-        E->off[5] = A.put(seg_out);
+        E_plan->entry = true;  // the slab occupies the partial-sum buffer: no split-K
+        E_plan->may_split = false;
+        E_plan->split = 1;
+        E_plan->R = R;
+        E_plan->n_seg = nt;
+        E_plan->slab_rows = n_entries * R;
+        E_plan->off[4] = A.put(seg);
+        E_plan->off[5] = A.put(seg_out);
     }
+    SplitPlan* E_ = E_plan;
     if (rc != VFMM_OK) {
-        free_split_plan(E);
-        delete E;
+        free_split_plan(E_);
+        delete E_;
         return rc;
     }
     if (prefer_entry) {
         // the entry-major form runs; the grouped one stays as the alternative
         SplitPlan* Gp = new SplitPlan(*P);
-        *P = *E;
-        *E = SplitPlan();
-        delete E;
+        *P = *E_;
+        *E_ = SplitPlan();
+        delete E_;
         P->alt = Gp;
     } else {
-        P->alt = E;
+        P->alt = E_;
     }
     return VFMM_OK;
 }
@@ -819,36 +820,71 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
 }
 
 // Near field: targets are leaves; tables are the 33 configurations; A rows are leaves.
-static int build_plans(const DeviceTree& T, int R, const HostLists& H, PlanSet* PS) {
-    PS->R = R;
+// The near-field plan (U list: leaves as targets, 33 configurations, gathered row = source leaf).
+static int build_near_plan(const DeviceTree& T, int R, const HostLists& H, PlanArena& A, PlanSet* PS) {
     const int nl = T.n_leaves;
     const std::vector<int32_t>& ptr = H.ptr[VFMM_LIST_U];
     const std::vector<int32_t>& idx = H.idx[VFMM_LIST_U];
     const std::vector<int32_t>& cfg = H.cfg[VFMM_LIST_U];
     const std::vector<int32_t>& bol = H.bol;
     const std::vector<int32_t>& lob = H.lob;
-    std::vector<int32_t> tgt(nl);
-    std::vector<std::vector<std::pair<int32_t, int32_t>>> items(nl);
-    std::vector<std::pair<uint64_t, uint64_t>> key(nl);
+    PlanItems I;
+    I.tab.reserve(idx.size());
+    I.src.reserve(idx.size());
     for (int t = 0; t < nl; ++t) {
-        tgt[t] = t;
-        int b = bol[t];
+        const int b = bol[t];
         uint64_t sig = 0;
         for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
-            items[t].push_back({cfg[e], lob[idx[e]]});
+            I.add(cfg[e], lob[idx[e]]);
             sig |= 1ull << cfg[e];
         }
-        key[t] = {sig, (uint64_t)t};
+        I.close(t, sig, (uint64_t)t);
     }
     const int rows = 3 * T.k * T.k;
     const bool tr = near_transposed(T.k);
     const int tile_rows = table_rows_per_tile(tr);
     const int Kp = (T.k * T.k + kKBlock - 1) / kKBlock * kKBlock;
-    PlanArena A;
-    VFMM_CHECK(build_contraction_plan(tgt, items, key, kNearCfg, (rows + tile_rows - 1) / tile_rows, R, tr,
-                                      Kp / kKBlock, 48.0 / Kp, (size_t)rows * sizeof(float2), A, &PS->near));
-    VFMM_CHECK(build_far_plans(T, R, H, A, PS));
-    return commit_plan_arena(A, PS);
+    return build_contraction_plan(I, kNearCfg, (rows + tile_rows - 1) / tile_rows, R, tr, Kp / kKBlock, 48.0 / Kp,
+                                  (size_t)rows * sizeof(float2), A, &PS->near);
+}
+
+// All five plans of R folded right-hand sides. The contractions are independent: each is built on a
+// host thread of its own into its own arena; the arenas are then joined (offsets shifted) and
+// copied to the device at once.
+static int build_plans(const DeviceTree& T, int R, const HostLists& H, PlanSet* PS) {
+    PS->R = R;
+    int dev = 0;
+    VFMM_CUDA(cudaGetDevice(&dev));
+    PlanArena A[kNumCtr];
+    int rc[kNumCtr];
+    auto task = [&](int c) {
+        cudaSetDevice(dev);  // the split-K heuristic reads the device's SM count
+        rc[c] = c == kCtrNear ? build_near_plan(T, R, H, A[c], PS) : build_far_plan(c, T, R, H, A[c], PS);
+    };
+    std::vector<std::thread> workers;
+    for (int c = 1; c < kNumCtr; ++c) workers.emplace_back(task, c);
+    task(kCtrNear);
+    for (auto& w : workers) w.join();
+    for (int c = 0; c < kNumCtr; ++c)
+        if (rc[c] != VFMM_OK) return fail(rc[c], "split-contraction plan " + std::to_string(c) + " failed");
+    SplitPlan* top[kNumCtr];
+    top[kCtrNear] = &PS->near;
+    top[kCtrS2M] = &PS->s2m;
+    top[kCtrM2L] = &PS->m2l;
+    top[kCtrS2L] = &PS->s2l;
+    top[kCtrFar] = &PS->far;
+    PlanArena all;
+    size_t total = 0;
+    for (int c = 0; c < kNumCtr; ++c) total += A[c].data.size();
+    all.data.reserve(total);
+    for (int c = 0; c < kNumCtr; ++c) {
+        const int64_t base = (int64_t)all.data.size();
+        for (SplitPlan* P = top[c]; P; P = P->alt)
+            for (int i = 0; i < 6; ++i)
+                if (P->off[i] >= 0) P->off[i] += base;
+        all.data.insert(all.data.end(), A[c].data.begin(), A[c].data.end());
+    }
+    return commit_plan_arena(all, PS);
 }
 
 int build_mixed_plan(DeviceTree* T) {

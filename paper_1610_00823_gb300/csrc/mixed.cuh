@@ -216,20 +216,32 @@ struct PlanArena {
 };
 int commit_plan_arena(PlanArena& A, PlanSet* PS);
 
-int build_split_plan(const std::vector<int32_t>& tgt_id,
-                     const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
-                     const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
+// Targets of one split contraction in flat form: target t (output row tgt[t]) holds the items
+// (tab[e], src[e]) = (table, gathered operand row), e in [ptr[t], ptr[t + 1]), and sorts by key[t].
+struct PlanItems {
+    std::vector<int32_t> tgt, ptr{0}, tab, src;
+    std::vector<std::pair<uint64_t, uint64_t>> key;
+    void add(int32_t table, int32_t row) {
+        tab.push_back(table);
+        src.push_back(row);
+    }
+    void close(int32_t id, uint64_t k0, uint64_t k1) {  // ends the target whose items were just added
+        tgt.push_back(id);
+        ptr.push_back((int32_t)tab.size());
+        key.push_back({k0, k1});
+    }
+};
+// Groups of 128 (80 when transposed) targets taken in the given order; per group the tables present
+// and, per table, the gathered row of each target (-1 when the target has no entry for that table).
+int build_split_plan(const PlanItems& I, const std::vector<int32_t>& order, int n_tables, int n_chunks, int R,
                      bool transposed, int nkb, PlanArena& A, SplitPlan* P);
 // build_split_plan, or its entry-major form when that executes enough fewer columns: chosen when
 // (entry-major columns) x (1 + slab_overhead) < 0.85 x (grouped columns, padding included) and the
 // slab (entries x R x slab_row_bytes) stays within 256 MB. slab_overhead = the slab's write and read
 // time per column relative to its tensor time. A small contraction (fewer CTAs than two per SM)
 // whose slab fits keeps the form not chosen in P->alt.
-int build_contraction_plan(const std::vector<int32_t>& tgt_id,
-                           const std::vector<std::vector<std::pair<int32_t, int32_t>>>& items,
-                           const std::vector<std::pair<uint64_t, uint64_t>>& key, int n_tables, int n_chunks, int R,
-                           bool transposed, int nkb, double slab_overhead, size_t slab_row_bytes, PlanArena& A,
-                           SplitPlan* P);
+int build_contraction_plan(const PlanItems& I, int n_tables, int n_chunks, int R, bool transposed, int nkb,
+                           double slab_overhead, size_t slab_row_bytes, PlanArena& A, SplitPlan* P);
 // Tensor map of a sliced table [rows][Kp / 32][kSlices][32] BF16 for the table operand of split_gemm
 // (box = box_rows rows x 64 bytes of one slice and K block).
 int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtensorMap* out);
@@ -246,7 +258,8 @@ struct HostLists {
 };
 int fetch_host_lists(const DeviceTree& T, HostLists* H);
 int build_far_slots(DeviceTree* T, const HostLists& H);
-int build_far_plans(const DeviceTree& T, int R, const HostLists& H, PlanArena& A, PlanSet* PS);
+// Plan of one far-field contraction (kCtrS2M, kCtrM2L, kCtrS2L or kCtrFar) into PS.
+int build_far_plan(int which, const DeviceTree& T, int R, const HostLists& H, PlanArena& A, PlanSet* PS);
 // Near field in two parts: max |f| and the f slices (also the operand of S2M and S2L), then the
 // split contraction.
 int near_slices(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, const MixedWork& w,

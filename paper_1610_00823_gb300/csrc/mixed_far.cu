@@ -228,7 +228,7 @@ int build_far_slots(DeviceTree* T, const HostLists& H) {
     return VFMM_OK;
 }
 
-int build_far_plans(const DeviceTree& T, int R, const HostLists& H, PlanArena& A, PlanSet* PS) {
+int build_far_plan(int which, const DeviceTree& T, int R, const HostLists& H, PlanArena& A, PlanSet* PS) {
     const int nb = T.n_boxes, nl = T.n_leaves;
     // K blocks per table: k^2 for S2M and S2L; 2(p+1) for M2L and the leaf far field, where p is not
     // known to the tree (3 blocks = p up to 47; only the default split-K choice depends on it)
@@ -236,93 +236,66 @@ int build_far_plans(const DeviceTree& T, int R, const HostLists& H, PlanArena& A
     constexpr int kFarKb = 3;
     const std::vector<int32_t>& bol = H.bol;
     const std::vector<int32_t>& lob = H.lob;
-    auto fetch = [&](int q, std::vector<int32_t>& ptr, std::vector<int32_t>& idx, std::vector<int32_t>& cfg) -> int {
-        ptr = H.ptr[q];
-        idx = H.idx[q];
-        cfg = H.cfg[q];
-        return VFMM_OK;
+    // boxes with a non-empty list q as targets, one item per entry (table = its configuration)
+    auto list_items = [&](int q, bool src_leaf, PlanItems* I) {
+        const std::vector<int32_t>& ptr = H.ptr[q];
+        const std::vector<int32_t>& idx = H.idx[q];
+        const std::vector<int32_t>& cfg = H.cfg[q];
+        I->tab.reserve(idx.size());
+        I->src.reserve(idx.size());
+        for (int b = 0; b < nb; ++b) {
+            if (ptr[b + 1] == ptr[b]) continue;
+            uint64_t sig = 0;
+            for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
+                I->add(cfg[e], src_leaf ? lob[idx[e]] : idx[e]);
+                sig |= 1ull << cfg[e];
+            }
+            I->close(b, sig, (uint64_t)b);
+        }
     };
-    // S2M: every leaf, one table, A row = the leaf
-    {
-        std::vector<int32_t> tgt(nl);
-        std::vector<std::vector<std::pair<int32_t, int32_t>>> items(nl);
-        std::vector<std::pair<uint64_t, uint64_t>> key(nl);
-        for (int t = 0; t < nl; ++t) {
-            tgt[t] = t;
-            items[t].push_back({0, t});
-            key[t] = {0, (uint64_t)t};
-        }
-        VFMM_CHECK(build_split_plan(tgt, items, key, 1, 1, R, false, Kp / kKBlock, A, &PS->s2m));
-    }
-    // M2L: boxes with a V list, tables = the 40 offsets, A row = source box
-    {
-        std::vector<int32_t> ptr, idx, cfg;
-        VFMM_CHECK(fetch(VFMM_LIST_V, ptr, idx, cfg));
-        std::vector<int32_t> tgt;
-        std::vector<std::vector<std::pair<int32_t, int32_t>>> items;
-        std::vector<std::pair<uint64_t, uint64_t>> key;
-        for (int b = 0; b < nb; ++b) {
-            if (ptr[b + 1] == ptr[b]) continue;
-            tgt.push_back(b);
-            items.emplace_back();
-            uint64_t sig = 0;
-            for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
-                items.back().push_back({cfg[e], idx[e]});
-                sig |= 1ull << cfg[e];
+    PlanItems I;
+    switch (which) {
+        case kCtrS2M: {  // every leaf, one table, gathered row = the leaf
+            for (int t = 0; t < nl; ++t) {
+                I.add(0, t);
+                I.close(t, 0, (uint64_t)t);
             }
-            key.push_back({sig, (uint64_t)b});
+            std::vector<int32_t> order(nl);
+            for (int t = 0; t < nl; ++t) order[t] = t;
+            return build_split_plan(I, order, 1, 1, R, false, Kp / kKBlock, A, &PS->s2m);
         }
-        // slab costs relative to the tensor work per column: K = 2(p+1) padded (about 96), rows <= 128
-        VFMM_CHECK(build_contraction_plan(tgt, items, key, kVCfg, 1, R, false, kFarKb, 0.5, 128 * sizeof(float2), A,
-                                          &PS->m2l));
-    }
-    // S2L: boxes with an X list, tables 20 configurations, A row = source leaf
-    {
-        std::vector<int32_t> ptr, idx, cfg;
-        VFMM_CHECK(fetch(VFMM_LIST_X, ptr, idx, cfg));
-        std::vector<int32_t> tgt;
-        std::vector<std::vector<std::pair<int32_t, int32_t>>> items;
-        std::vector<std::pair<uint64_t, uint64_t>> key;
-        for (int b = 0; b < nb; ++b) {
-            if (ptr[b + 1] == ptr[b]) continue;
-            tgt.push_back(b);
-            items.emplace_back();
-            uint64_t sig = 0;
-            for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
-                items.back().push_back({cfg[e], lob[idx[e]]});
-                sig |= 1ull << cfg[e];
+        case kCtrM2L:  // boxes with a V list, tables = the 40 offsets, gathered row = source box
+            list_items(VFMM_LIST_V, false, &I);
+            // slab costs relative to the tensor work per column: K = 2(p+1) padded (about 96), rows <= 128
+            return build_contraction_plan(I, kVCfg, 1, R, false, kFarKb, 0.5, 128 * sizeof(float2), A, &PS->m2l);
+        case kCtrS2L:  // boxes with an X list, tables 20 configurations, gathered row = source leaf
+            list_items(VFMM_LIST_X, true, &I);
+            return build_contraction_plan(I, kFarCfg, 1, R, false, Kp / kKBlock, 48.0 / Kp, 128 * sizeof(float2), A,
+                                          &PS->s2l);
+        case kCtrFar: {  // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
+            const std::vector<int32_t>& ptr = H.ptr[VFMM_LIST_W];
+            const std::vector<int32_t>& cfg = H.cfg[VFMM_LIST_W];
+            int32_t slot = 0;
+            for (int t = 0; t < nl; ++t) {
+                const int b = bol[t];
+                I.add(0, slot);
+                uint64_t sig = 0;
+                for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
+                    I.add(1 + cfg[e], slot + 1 + (e - ptr[b]));
+                    sig |= 1ull << cfg[e];
+                }
+                slot += 1 + (ptr[b + 1] - ptr[b]);
+                I.close(t, sig, (uint64_t)t);
             }
-            key.push_back({sig, (uint64_t)b});
+            const int rows = 3 * T.k * T.k;
+            const bool tr = near_transposed(T.k);
+            const int tile_rows = table_rows_per_tile(tr);
+            return build_contraction_plan(I, 1 + kFarCfg, (rows + tile_rows - 1) / tile_rows, R, tr, kFarKb, 0.5,
+                                          (size_t)rows * sizeof(float2), A, &PS->far);
         }
-        VFMM_CHECK(build_contraction_plan(tgt, items, key, kFarCfg, 1, R, false, Kp / kKBlock, 48.0 / Kp,
-                                          128 * sizeof(float2), A, &PS->s2l));
+        default:
+            return fail(VFMM_ERR_INTERNAL, "unknown far-field contraction");
     }
-    // leaf far field: slot 0 = own local (L2T), slot 1 + j = j-th W entry (table 1 + its configuration)
-    {
-        std::vector<int32_t> ptr, idx, cfg;
-        VFMM_CHECK(fetch(VFMM_LIST_W, ptr, idx, cfg));
-        std::vector<int32_t> tgt(nl), slot(nl + 1, 0);
-        std::vector<std::vector<std::pair<int32_t, int32_t>>> items(nl);
-        std::vector<std::pair<uint64_t, uint64_t>> key(nl);
-        for (int t = 0; t < nl; ++t) slot[t + 1] = slot[t] + 1 + (ptr[bol[t] + 1] - ptr[bol[t]]);
-        for (int t = 0; t < nl; ++t) {
-            int b = bol[t];
-            tgt[t] = t;
-            items[t].push_back({0, slot[t]});
-            uint64_t sig = 0;
-            for (int e = ptr[b]; e < ptr[b + 1]; ++e) {
-                items[t].push_back({1 + cfg[e], slot[t] + 1 + (e - ptr[b])});
-                sig |= 1ull << cfg[e];
-            }
-            key[t] = {sig, (uint64_t)t};
-        }
-        const int rows = 3 * T.k * T.k;
-        const bool tr = near_transposed(T.k);
-        const int tile_rows = table_rows_per_tile(tr);
-        VFMM_CHECK(build_contraction_plan(tgt, items, key, 1 + kFarCfg, (rows + tile_rows - 1) / tile_rows, R, tr,
-                                          kFarKb, 0.5, (size_t)rows * sizeof(float2), A, &PS->far));
-    }
-    return VFMM_OK;
 }
 
 // Partial-sum buffers of the split contractions (float2 elements): room for kMaxSplit partial sets

@@ -20,6 +20,9 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <thread>
+#include <atomic>
 #include <set>
 #include <tuple>
 #include <unordered_map>
@@ -229,6 +232,24 @@ __global__ void fscale_kernel(NodeGeom g, SourceDev src, int level, double* fmax
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(fmax_out, m);
 }
 
+// f at the k^2 nodes of each of n boxes, one thread per node, out[b * k^2 + t] (node t = j k + i):
+// the source evaluations of a level spread over every SM (FP64 is the scarce unit, and one CTA per
+// box would leave most SMs idle on the coarse levels). lev: per-box levels, or null for `level`.
+__global__ void __launch_bounds__(64) node_values_kernel(NodeGeom g, SourceDev src, int level,
+                                                        const int32_t* __restrict__ lev,
+                                                        const uint32_t* __restrict__ keys, int n,
+                                                        double* __restrict__ out) {
+    const int kk = g.k * g.k;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * kk) return;
+    const int b = (int)(q / kk), t = (int)(q - (int64_t)b * kk);
+    const int l = lev ? lev[b] : level;
+    int ix, iy;
+    morton_decode(keys[b], &ix, &iy);
+    const double h = ldexp(g.width, -l);
+    out[q] = source_eval(src, node_coord(g.lox, ix, g.xhat[t % g.k], h), node_coord(g.loy, iy, g.xhat[t / g.k], h));
+}
+
 // Largest trailing Chebyshev coefficient (last two rows and columns) of the k x k interpolant of
 // f on the box (level, key): values -> coefficients as c = C V C^T with
 // C[m*k + i] = (2 - delta_m0)/k T_m(t_i). Called by a whole CTA (blockDim = k*k rounded up to
@@ -366,12 +387,12 @@ __global__ void __launch_bounds__(1024) interp_rule_kernel(NodeGeom g, SourceDev
 // One CTA per box of a list with per-box levels: tails[b] = box_tail.
 __global__ void tail_kernel(NodeGeom g, SourceDev src, const int32_t* __restrict__ lev,
                             const uint32_t* __restrict__ keys, int n, const double* __restrict__ C,
-                            double* __restrict__ tails) {
+                            double* __restrict__ tails, const double* __restrict__ fv) {
     __shared__ double V[16 * 16];
     __shared__ double Tm[16 * 16];
     __shared__ double red[8];
     const int b = blockIdx.x;
-    const double mx = box_tail(g, src, lev[b], keys[b], C, V, Tm, red);
+    const double mx = box_tail(g, src, lev[b], keys[b], C, V, Tm, red, fv + (size_t)b * g.k * g.k);
     if (threadIdx.x == 0 && b < n) tails[b] = mx;
 }
 
@@ -648,6 +669,7 @@ static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t -
 // ---------------------------------------------------------------- host orchestration
 struct BuildCtx {
     cudaStream_t st;
+    bool keep = false;  // tables outlive the call (a builder): cudaMalloc instead of the build pool
     NodeGeom g;
     DBuf<double> xhat;
     DBuf<double> C;
@@ -664,8 +686,8 @@ static int upload_node_tables(int k, BuildCtx& B) {
             double v = std::cos(m * std::acos(std::min(1.0, std::max(-1.0, t))));
             C[m * k + i] = (m == 0 ? 1.0 : 2.0) / k * v;
         }
-    VFMM_CHECK(B.xhat.alloc_keep(k));
-    VFMM_CHECK(B.C.alloc_keep(k * k));
+    VFMM_CHECK(B.keep ? B.xhat.alloc_keep(k) : B.xhat.alloc(k, B.st));
+    VFMM_CHECK(B.keep ? B.C.alloc_keep(k * k) : B.C.alloc(k * k, B.st));
     VFMM_CUDA(cudaMemcpyAsync(B.xhat.p, xh.data(), k * sizeof(double), cudaMemcpyHostToDevice, B.st));
     VFMM_CUDA(cudaMemcpyAsync(B.C.p, C.data(), k * k * sizeof(double), cudaMemcpyHostToDevice, B.st));
     return VFMM_OK;
@@ -689,7 +711,7 @@ static int upload_child_basis(int k, BuildCtx& B) {
             L[I * k + i] = num / den;
         }
     }
-    VFMM_CHECK(B.L.alloc_keep(2 * k * k));
+    VFMM_CHECK(B.keep ? B.L.alloc_keep(2 * k * k) : B.L.alloc(2 * k * k, B.st));
     VFMM_CUDA(cudaMemcpyAsync(B.L.p, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, B.st));
     return VFMM_OK;
 }
@@ -704,7 +726,9 @@ static int compute_lists(DeviceTree* T, cudaStream_t st) {
     TreeView V{T->key, T->level_start_dev, T->level, T->ix, T->iy, T->parent, T->child0, T->depth};
     DBuf<int32_t> cnt;
     VFMM_CHECK(cnt.alloc((size_t)4 * n, st));
-    list_count_kernel<<<nblk(n, 128), 128, 0, st>>>(V, n, cnt.p);
+    // 32 threads per CTA: each thread keeps its box's candidate entries (about 1 KB) in local memory,
+    // which then stays in L1, and the boxes spread over more SMs
+    list_count_kernel<<<nblk(n, 32), 32, 0, st>>>(V, n, cnt.p);
     VFMM_CUDA(cudaGetLastError());
     // one scan over the 4 concatenated count arrays; row q starts at total of rows < q
     int64_t total = 0;
@@ -726,7 +750,7 @@ static int compute_lists(DeviceTree* T, cudaStream_t st) {
         shift_kernel<<<nblk(n), 256, 0, st>>>(cnt.p + (int64_t)q * n, n, starts[q]);
         ptr_from_offsets_kernel<<<nblk(n + 1), 256, 0, st>>>(cnt.p + (int64_t)q * n, n, T->llen[q], ptr[q].p);
     }
-    list_fill_kernel<<<nblk(n, 128), 128, 0, st>>>(V, n, cnt.p, idx[0].p, cfg[0].p, idx[1].p, cfg[1].p, idx[2].p,
+    list_fill_kernel<<<nblk(n, 32), 32, 0, st>>>(V, n, cnt.p, idx[0].p, cfg[0].p, idx[1].p, cfg[1].p, idx[2].p,
                                                    cfg[2].p, idx[3].p, cfg[3].p);
     VFMM_CUDA(cudaGetLastError());
     for (int q = 0; q < 4; ++q) {
@@ -800,12 +824,16 @@ static int greedy_refine(const BuildCtx& B, const SourceDev& src, int max_depth,
         DBuf<int32_t> dl;
         DBuf<uint32_t> dk;
         DBuf<double> dt;
+        DBuf<double> fv;
+        const int64_t nv = (int64_t)n * B.g.k * B.g.k;
         VFMM_CHECK(dl.alloc(n, B.st));
         VFMM_CHECK(dk.alloc(n, B.st));
         VFMM_CHECK(dt.alloc(n, B.st));
+        VFMM_CHECK(fv.alloc(nv, B.st));
         VFMM_CUDA(cudaMemcpyAsync(dl.p, lev.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, B.st));
         VFMM_CUDA(cudaMemcpyAsync(dk.p, key.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, B.st));
-        tail_kernel<<<(unsigned)n, threads, 0, B.st>>>(B.g, src, dl.p, dk.p, n, B.C.p, dt.p);
+        node_values_kernel<<<(unsigned)((nv + 63) / 64), 64, 0, B.st>>>(B.g, src, 0, dl.p, dk.p, n, fv.p);
+        tail_kernel<<<(unsigned)n, threads, 0, B.st>>>(B.g, src, dl.p, dk.p, n, B.C.p, dt.p, fv.p);
         VFMM_CUDA(cudaGetLastError());
         out.resize(n);
         VFMM_CUDA(cudaMemcpyAsync(out.data(), dt.p, n * sizeof(double), cudaMemcpyDeviceToHost, B.st));
@@ -915,13 +943,17 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
         for (int l = 0; l < max_depth; ++l) {
             const int64_t n = cnt[l];
             DBuf<int32_t> flags, offs;
+            DBuf<double> vals;
             VFMM_CHECK(flags.alloc(n, st));
             VFMM_CHECK(offs.alloc(n, st));
             if (l < min_depth) {
                 fill_kernel<<<nblk(n), 256, 0, st>>>(flags.p, n, 1);
             } else if (rule == VFMM_REFINE_TAIL) {
-                refine_kernel<<<(unsigned)n, ((k * k + 31) / 32) * 32, 0, st>>>(B.g, *src, l, keys[l].p, (int)n, B.C.p, thresh, flags.p,
-                                                             scal.p + 1);
+                VFMM_CHECK(vals.alloc(n * k * k, st));
+                node_values_kernel<<<(unsigned)((n * k * k + 63) / 64), 64, 0, st>>>(B.g, *src, l, nullptr, keys[l].p,
+                                                                                    (int)n, vals.p);
+                refine_kernel<<<(unsigned)n, ((k * k + 31) / 32) * 32, 0, st>>>(B.g, *src, l, keys[l].p, (int)n, B.C.p,
+                                                                                 thresh, flags.p, scal.p + 1, vals.p);
             } else {
                 if (!B.L.p) VFMM_CHECK(upload_child_basis(k, B));
                 interp_rule_kernel<<<(unsigned)n, ((4 * k * k + 31) / 32) * 32, 0, st>>>(
@@ -950,8 +982,12 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
                 VFMM_CHECK(cf.alloc(nc, st));
                 VFMM_CHECK(co.alloc(nc, st));
                 if (rule == VFMM_REFINE_TAIL) {
+                    DBuf<double> vals;
+                    VFMM_CHECK(vals.alloc(nc * k * k, st));
+                    node_values_kernel<<<(unsigned)((nc * k * k + 63) / 64), 64, 0, st>>>(
+                        B.g, *src, max_depth, nullptr, keys[max_depth].p, (int)nc, vals.p);
                     refine_kernel<<<(unsigned)nc, ((k * k + 31) / 32) * 32, 0, st>>>(
-                        B.g, *src, max_depth, keys[max_depth].p, (int)nc, B.C.p, thresh, cf.p, scal.p + 2);
+                        B.g, *src, max_depth, keys[max_depth].p, (int)nc, B.C.p, thresh, cf.p, scal.p + 2, vals.p);
                 } else {
                     if (!B.L.p) VFMM_CHECK(upload_child_basis(k, B));
                     interp_rule_kernel<<<(unsigned)nc, ((4 * k * k + 31) / 32) * 32, 0, st>>>(
@@ -1264,6 +1300,7 @@ extern "C" int vfmm_tree_begin(const vfmm_tree_params* prm, void* stream, vfmm_t
     b->m0 = std::min(5, prm->max_depth);
     b->keys.resize(prm->max_depth + 1);
     b->cnt.assign(prm->max_depth + 1, 0);
+    b->B.keep = true;
     int rc = upload_node_tables(prm->k, b->B);
     b->B.g = NodeGeom{prm->cx - prm->width / 2.0, prm->cy - prm->width / 2.0, prm->width, prm->k, b->B.xhat.p};
     if (rc == VFMM_OK) rc = b->keys[0].alloc_keep(1);
@@ -1424,6 +1461,51 @@ extern "C" int vfmm_tree_build_leaves(const vfmm_tree_params* prm, const vfmm_so
         return r;
     }
     *out = t;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_tree_build_many(const vfmm_tree_params* prm, const vfmm_source* src, const int64_t* n_leaves,
+                                    int32_t n, int32_t n_threads, vfmm_tree** out) {
+    if (!prm || !src || !n_leaves || !out || n < 0) return fail(VFMM_ERR_INVALID_ARG, "null argument or n < 0");
+    for (int32_t i = 0; i < n; ++i) out[i] = nullptr;
+    if (n == 0) return VFMM_OK;
+    int dev = 0;
+    VFMM_CUDA(cudaGetDevice(&dev));
+    int nt = n_threads > 0 ? n_threads : (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+    nt = std::max(1, std::min(nt, (int)n));
+    std::atomic<int32_t> next(0);
+    std::atomic<int> first_err(VFMM_OK);
+    std::mutex msg_mu;
+    std::string msg;
+    auto worker = [&]() {
+        cudaStream_t st = nullptr;
+        int rc = VFMM_OK;
+        if (cudaSetDevice(dev) != cudaSuccess) rc = fail(VFMM_ERR_CUDA, "cudaSetDevice failed");
+        if (rc == VFMM_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            rc = fail(VFMM_ERR_CUDA, "cudaStreamCreateWithFlags failed");
+        for (int32_t i = next++; rc == VFMM_OK && i < n && first_err.load() == VFMM_OK; i = next++)
+            rc = n_leaves[i] > 0 ? vfmm_tree_build_leaves(&prm[i], &src[i], n_leaves[i], st, &out[i])
+                                 : vfmm_tree_build(&prm[i], &src[i], st, &out[i]);
+        if (rc != VFMM_OK) {
+            int expected = VFMM_OK;
+            if (first_err.compare_exchange_strong(expected, rc)) {
+                std::lock_guard<std::mutex> lock(msg_mu);
+                msg = vfmm_last_error_detail();
+            }
+        }
+        if (st) cudaStreamDestroy(st);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nt; ++w) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+    if (first_err.load() != VFMM_OK) {
+        for (int32_t i = 0; i < n; ++i) {
+            if (out[i]) vfmm_tree_destroy(out[i]);
+            out[i] = nullptr;
+        }
+        return fail(first_err.load(), "tree build of the batch failed: " + msg);
+    }
     return VFMM_OK;
 }
 

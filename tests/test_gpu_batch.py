@@ -111,3 +111,30 @@ def test_leaf_count_members_in_a_batch_match_the_oracle(precision, tol, oracle_o
         for q in range(3):
             got = out[q].cpu().numpy().reshape(ref[q].shape)
             assert _rel(got, ref[q]) < tol, (precision, tree.k, q, _rel(got, ref[q]))
+
+
+def test_tree_build_many_equals_single_builds():
+    """vfmm_tree_build_many on 4 host threads: every tree (leaf-count and tolerance trees, k = 8 and
+    16) has the boxes and the four lists of its own single build, entry for entry."""
+    mem = W.batch_members(12)
+    specs = []
+    for i, m in enumerate(mem):
+        sp = dict(cx=0.0, cy=0.0, width=1.0, k=m["k"], source=m["source"], max_depth=16)
+        if i % 2:
+            sp["n_leaves"] = 40 + 97 * i
+        else:
+            sp["tol"] = (1e-6, 1e-9, 1e-12)[i % 3]
+        specs.append(sp)
+    many = v.tree_build_many(specs, n_threads=4)
+    for sp, t in zip(specs, many):
+        if "n_leaves" in sp:
+            ref = v.tree_build_leaves(sp["cx"], sp["cy"], sp["width"], sp["k"], sp["source"], sp["n_leaves"], 16)
+        else:
+            ref = v.tree_build(sp["cx"], sp["cy"], sp["width"], sp["k"], sp["source"], sp["tol"], 16)
+        assert (t.n_boxes, t.n_leaves, t.depth, t.list_len) == (ref.n_boxes, ref.n_leaves, ref.depth, ref.list_len)
+        for a, b in zip(t.export_boxes(), ref.export_boxes()):
+            assert (a == b).all()
+        for name in ("U", "V", "W", "X"):
+            for a, b in zip(t.export_list(name), ref.export_list(name)):
+                assert (a == b).all()
+    assert v.tree_build_many([], n_threads=2) == []
