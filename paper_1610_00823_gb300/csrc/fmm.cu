@@ -15,6 +15,7 @@
 // [n_boxes][2(p+1)], near slabs [n_U][3kk], far values [n_leaves][3kk] (+ I/O copies).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 
 #include "mixed.cuh"
@@ -1195,13 +1196,10 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
 }
 
 // V or X list grouped by configuration (host counting sort of the entries) and cut into GEMM
-// tiles of at most GBN entries of one configuration.
-static int build_list_groups(DeviceTree* T, int q, int ncfg, int32_t** by_cfg, int32_t** tiles_out, int32_t* n_tiles,
-                             int32_t** tgt_out) {
-    const int64_t n = T->llen[q];
-    std::vector<int32_t> cfg(n), ptr(T->n_boxes + 1);
-    if (n) VFMM_CUDA(cudaMemcpy(cfg.data(), T->lcfg[q], n * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(ptr.data(), T->lptr[q], (T->n_boxes + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+// tiles of at most GBN entries of one configuration; all device arrays in one allocation.
+static int build_list_groups(DeviceTree* T, const std::vector<int32_t>& cfg, const std::vector<int32_t>& ptr, int ncfg,
+                             int32_t** by_cfg, int32_t** tiles_out, int32_t* n_tiles, int32_t** tgt_out) {
+    const int64_t n = (int64_t)cfg.size();
     std::vector<int64_t> start(ncfg + 1, 0);
     for (int64_t e = 0; e < n; ++e) ++start[cfg[e] + 1];
     for (int c = 0; c < ncfg; ++c) start[c + 1] += start[c];
@@ -1213,24 +1211,33 @@ static int build_list_groups(DeviceTree* T, int q, int ncfg, int32_t** by_cfg, i
         for (int64_t b = start[c]; b < start[c + 1]; b += GBN)
             tiles.push_back(make_int4(c, (int)b, (int)std::min<int64_t>(b + GBN, start[c + 1]), 0));
     *n_tiles = (int32_t)tiles.size();
-    VFMM_CUDA(cudaMalloc(by_cfg, order.size() * sizeof(int32_t)));
-    VFMM_CUDA(cudaMemcpy(*by_cfg, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    VFMM_CUDA(cudaMalloc(tiles_out, std::max<size_t>(1, tiles.size()) * sizeof(int4)));
-    if (!tiles.empty())
-        VFMM_CUDA(cudaMemcpy(*tiles_out, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    std::vector<int32_t> tgt;
     if (tgt_out) {
-        std::vector<int32_t> tgt(std::max<int64_t>(n, 1), 0);
+        tgt.assign(std::max<int64_t>(n, 1), 0);
         for (int b = 0; b < T->n_boxes; ++b)
             for (int e = ptr[b]; e < ptr[b + 1]; ++e) tgt[e] = b;
-        VFMM_CUDA(cudaMalloc(tgt_out, tgt.size() * sizeof(int32_t)));
-        VFMM_CUDA(cudaMemcpy(*tgt_out, tgt.data(), tgt.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
+    // [tiles (int4)][order][tgt], each piece 16-byte aligned
+    const size_t n_tile_ints = 4 * std::max<size_t>(1, tiles.size());
+    const size_t n_order = (order.size() + 3) / 4 * 4;
+    std::vector<int32_t> host(n_tile_ints + n_order + tgt.size(), 0);
+    if (!tiles.empty()) std::memcpy(host.data(), tiles.data(), tiles.size() * sizeof(int4));
+    std::copy(order.begin(), order.end(), host.begin() + n_tile_ints);
+    std::copy(tgt.begin(), tgt.end(), host.begin() + n_tile_ints + n_order);
+    int32_t* dev = nullptr;
+    VFMM_CUDA(cudaMalloc(&dev, host.size() * sizeof(int32_t)));
+    VFMM_CUDA(cudaMemcpy(dev, host.data(), host.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    *tiles_out = dev;  // owns the allocation
+    *by_cfg = dev + n_tile_ints;
+    if (tgt_out) *tgt_out = dev + n_tile_ints + n_order;
     return VFMM_OK;
 }
 
-int build_near_tiles(DeviceTree* T) {
-    VFMM_CHECK(build_list_groups(T, VFMM_LIST_V, kVCfg, &T->v_by_cfg, &T->v_tiles, &T->n_v_tiles, nullptr));
-    VFMM_CHECK(build_list_groups(T, VFMM_LIST_X, kFarCfg, &T->x_by_cfg, &T->x_tiles, &T->n_x_tiles, &T->x_tgt));
+int build_near_tiles(DeviceTree* T, const HostLists& H) {
+    VFMM_CHECK(build_list_groups(T, H.cfg[VFMM_LIST_V], H.ptr[VFMM_LIST_V], kVCfg, &T->v_by_cfg, &T->v_tiles,
+                                 &T->n_v_tiles, nullptr));
+    VFMM_CHECK(build_list_groups(T, H.cfg[VFMM_LIST_X], H.ptr[VFMM_LIST_X], kFarCfg, &T->x_by_cfg, &T->x_tiles,
+                                 &T->n_x_tiles, &T->x_tgt));
     std::vector<int4> tiles;
     for (int c = 0; c < kNearCfg; ++c)
         for (int64_t b = T->u_cfg_start[c]; b < T->u_cfg_start[c + 1]; b += GBN)
@@ -1239,7 +1246,8 @@ int build_near_tiles(DeviceTree* T) {
     if (T->near_tiles) cudaFree(T->near_tiles);
     T->near_tiles = nullptr;
     VFMM_CUDA(cudaMalloc(&T->near_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int4)));
-    VFMM_CUDA(cudaMemcpy(T->near_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!tiles.empty())
+        VFMM_CUDA(cudaMemcpy(T->near_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
     return VFMM_OK;
 }
 

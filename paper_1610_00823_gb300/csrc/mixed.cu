@@ -891,6 +891,7 @@ int build_mixed_plan(DeviceTree* T) {
     HostLists H;
     VFMM_CHECK(fetch_host_lists(*T, &H));
     VFMM_CHECK(build_far_slots(T, H));
+    VFMM_CHECK(build_near_tiles(T, H));  // the FP64 form's GEMM tiles
     T->plans_r = new std::map<int, PlanSet*>();
     T->plans_mu = new std::mutex();
     return build_plans(*T, 1, H, &T->plans);

@@ -197,21 +197,58 @@ void far_free(MixedOps* mo) {
 // ---------------------------------------------------------------- schedules
 // Rows of the leaf far-field operand: per leaf, slot 0 = its own local (L2T), slot 1 + j = its
 // j-th W entry; far_slot[leaf] = first slot (right-hand side r of slot s is row s * R + r).
+// Pinned staging for the plan builders' reads of device arrays: one buffer per host thread, grown on
+// demand, so that all reads go out as asynchronous copies followed by one synchronisation.
+static int pinned_stage(size_t bytes, void** out) {
+    struct Stage {
+        void* p = nullptr;
+        size_t n = 0;
+        ~Stage() {
+            if (p) cudaFreeHost(p);
+        }
+    };
+    thread_local Stage s;
+    if (s.n < bytes) {
+        if (s.p) cudaFreeHost(s.p);
+        s.p = nullptr;
+        s.n = 0;
+        VFMM_CUDA(cudaMallocHost(&s.p, bytes));
+        s.n = bytes;
+    }
+    *out = s.p;
+    return VFMM_OK;
+}
+
 int fetch_host_lists(const DeviceTree& T, HostLists* H) {
     const int nb = T.n_boxes, nl = T.n_leaves;
-    H->bol.resize(nl);
-    H->lob.resize(nb);
-    VFMM_CUDA(cudaMemcpy(H->bol.data(), T.box_of_leaf, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    VFMM_CUDA(cudaMemcpy(H->lob.data(), T.leaf_of_box, nb * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    struct Piece {
+        const int32_t* src;
+        std::vector<int32_t>* dst;
+        size_t n;
+    };
+    std::vector<Piece> pieces = {{T.box_of_leaf, &H->bol, (size_t)nl}, {T.leaf_of_box, &H->lob, (size_t)nb}};
     for (int q = 0; q < 4; ++q) {
-        H->ptr[q].resize(nb + 1);
-        H->idx[q].resize(T.llen[q]);
-        H->cfg[q].resize(T.llen[q]);
-        VFMM_CUDA(cudaMemcpy(H->ptr[q].data(), T.lptr[q], (nb + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        if (T.llen[q]) {
-            VFMM_CUDA(cudaMemcpy(H->idx[q].data(), T.lidx[q], T.llen[q] * sizeof(int32_t), cudaMemcpyDeviceToHost));
-            VFMM_CUDA(cudaMemcpy(H->cfg[q].data(), T.lcfg[q], T.llen[q] * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        }
+        pieces.push_back({T.lptr[q], &H->ptr[q], (size_t)nb + 1});
+        pieces.push_back({T.lidx[q], &H->idx[q], (size_t)T.llen[q]});
+        pieces.push_back({T.lcfg[q], &H->cfg[q], (size_t)T.llen[q]});
+    }
+    size_t total = 0;
+    for (const Piece& pc : pieces) total += pc.n;
+    void* stage = nullptr;
+    VFMM_CHECK(pinned_stage(std::max<size_t>(1, total) * sizeof(int32_t), &stage));
+    int32_t* h = static_cast<int32_t*>(stage);
+    size_t o = 0;
+    for (const Piece& pc : pieces) {
+        if (pc.n)
+            VFMM_CUDA(cudaMemcpyAsync(h + o, pc.src, pc.n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                      cudaStreamPerThread));
+        o += pc.n;
+    }
+    VFMM_CUDA(cudaStreamSynchronize(cudaStreamPerThread));
+    o = 0;
+    for (const Piece& pc : pieces) {
+        pc.dst->assign(h + o, h + o + pc.n);
+        o += pc.n;
     }
     return VFMM_OK;
 }

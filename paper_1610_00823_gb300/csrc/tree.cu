@@ -216,7 +216,7 @@ __device__ inline void atomic_min_nonneg(double* addr, double v) {
     atomicMin((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void fscale_kernel(NodeGeom g, SourceDev src, int level, double* fmax_out) {
+__global__ void fscale_kernel(NodeGeom g, SourceDev src, int level, double* fmax_out, double* vals) {
     const int side = 1 << level;
     const int b = blockIdx.x;
     const int ix = b % side, iy = b / side;
@@ -226,7 +226,9 @@ __global__ void fscale_kernel(NodeGeom g, SourceDev src, int level, double* fmax
         int i = t % g.k, j = t / g.k;
         double x = node_coord(g.lox, ix, g.xhat[i], h);
         double y = node_coord(g.loy, iy, g.xhat[j], h);
-        m = fmax(m, fabs(source_eval(src, x, y)));
+        const double f = source_eval(src, x, y);
+        if (vals) vals[(size_t)b * g.k * g.k + t] = f;  // kept for the refinement of this level
+        m = fmax(m, fabs(f));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(fmax_out, m);
@@ -248,6 +250,18 @@ __global__ void __launch_bounds__(64) node_values_kernel(NodeGeom g, SourceDev s
     morton_decode(keys[b], &ix, &iy);
     const double h = ldexp(g.width, -l);
     out[q] = source_eval(src, node_coord(g.lox, ix, g.xhat[t % g.k], h), node_coord(g.loy, iy, g.xhat[t / g.k], h));
+}
+
+// The values of n boxes of the f-scale level from that level's full grid of node values (box
+// (ix, iy) at row-major position iy 2^level + ix): the same evaluations, not repeated.
+__global__ void grid_values_kernel(const double* __restrict__ grid, int level, int kk, const uint32_t* __restrict__ keys,
+                                   int n, double* __restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * kk) return;
+    const int b = (int)(q / kk), t = (int)(q - (int64_t)b * kk);
+    int ix, iy;
+    morton_decode(keys[b], &ix, &iy);
+    out[q] = grid[((size_t)iy * (1u << level) + ix) * kk + t];
 }
 
 // Largest trailing Chebyshev coefficient (last two rows and columns) of the k x k interpolant of
@@ -786,7 +800,7 @@ static int compute_lists(DeviceTree* T, cudaStream_t st) {
     T->u_cfg_start[kNearCfg] = nU;
     T->u_by_cfg = byc.release();
     T->u_tgt = tgt.release();
-    return build_near_tiles(T);
+    return VFMM_OK;
 }
 
 // Greedy refinement to a leaf count (no counterpart in the paper, which refines to a
@@ -911,9 +925,12 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
     double init[3] = {0.0, INFINITY, INFINITY};
     VFMM_CUDA(cudaMemcpyAsync(scal.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
     double thresh = 0.0;
+    int m0 = -1;              // level of the f-scale grid
+    DBuf<double> grid_m0;     // f at every node of that level (tail refinement only)
     if (!uniform) {
-        int m0 = std::min(5, max_depth);
-        fscale_kernel<<<1u << (2 * m0), 128, 0, st>>>(B.g, *src, m0, scal.p);
+        m0 = std::min(5, max_depth);
+        if (rule == VFMM_REFINE_TAIL && leaf_target <= 0) VFMM_CHECK(grid_m0.alloc((size_t)k * k << (2 * m0), st));
+        fscale_kernel<<<1u << (2 * m0), 128, 0, st>>>(B.g, *src, m0, scal.p, grid_m0.p);
         VFMM_CUDA(cudaGetLastError());
         VFMM_CUDA(cudaMemcpyAsync(&T->f_scale, scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         VFMM_CUDA(cudaStreamSynchronize(st));
@@ -950,8 +967,12 @@ static int build(const vfmm_tree_params* prm, const SourceDev* src, int uniform_
                 fill_kernel<<<nblk(n), 256, 0, st>>>(flags.p, n, 1);
             } else if (rule == VFMM_REFINE_TAIL) {
                 VFMM_CHECK(vals.alloc(n * k * k, st));
-                node_values_kernel<<<(unsigned)((n * k * k + 63) / 64), 64, 0, st>>>(B.g, *src, l, nullptr, keys[l].p,
-                                                                                    (int)n, vals.p);
+                if (l == m0 && grid_m0.p)
+                    grid_values_kernel<<<(unsigned)((n * k * k + 255) / 256), 256, 0, st>>>(grid_m0.p, l, k * k,
+                                                                                           keys[l].p, (int)n, vals.p);
+                else
+                    node_values_kernel<<<(unsigned)((n * k * k + 63) / 64), 64, 0, st>>>(B.g, *src, l, nullptr,
+                                                                                        keys[l].p, (int)n, vals.p);
                 refine_kernel<<<(unsigned)n, ((k * k + 31) / 32) * 32, 0, st>>>(B.g, *src, l, keys[l].p, (int)n, B.C.p,
                                                                                  thresh, flags.p, scal.p + 1, vals.p);
             } else {
@@ -1098,10 +1119,10 @@ static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt
 }
 
 void free_tree(DeviceTree* t) {
+    // v_by_cfg, x_by_cfg and x_tgt point into the v_tiles and x_tiles allocations
     void* ps[] = {t->key,         t->level,       t->ix,       t->iy,           t->parent,     t->child0,
                   t->leaf_of_box, t->box_of_leaf, t->level_start_dev, t->u_by_cfg, t->u_tgt, t->near_tiles,
-                  t->far_slot,    t->nonleaf,     t->nonleaf_start_dev, t->v_by_cfg, t->v_tiles,
-                  t->x_by_cfg,    t->x_tiles,     t->x_tgt};
+                  t->far_slot,    t->nonleaf,     t->nonleaf_start_dev, t->v_tiles, t->x_tiles};
     free_plan_set(&t->plans);
     if (t->plans_r) {
         for (auto& kv : *t->plans_r) {

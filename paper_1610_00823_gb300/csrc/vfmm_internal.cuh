@@ -250,7 +250,8 @@ void free_split_plan(SplitPlan* p);
 void free_plan_set(PlanSet* ps);
 // Plans for R folded right-hand sides (R = 1: the tree's own set); builds and caches on first use.
 int plans_for(const DeviceTree& T, int R, const PlanSet** out);
-int build_near_tiles(DeviceTree* t);
+struct HostLists;
+int build_near_tiles(DeviceTree* t, const HostLists& h);
 // vfmm_volume_potential with flags: fork = false keeps every launch on `st` (no second stream);
 // reset = false leaves the workspace's status word as it is (a caller solving several right-hand
 // sides one after another clears it once, so that a timeout in an early one is not lost).
