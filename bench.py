@@ -697,6 +697,25 @@ def main():
                    "roofline": {"bound": "fp64", "achieved": iach, "peak": ipeak, "unit": "TFLOP/s",
                                 "frac": iach / ipeak, "flops": "3 fields x 2 k^2 per point",
                                 "peak_source": "%s bf16 x nominal FP64/BF16 ratio (1.25/2250)" % peak_kind}}
+        # V f~ itself at arbitrary points from the solve's stored expansions (vfmm_evaluate_points):
+        # the first 1024 of the same points; far part O(p), near part by on-the-fly quadrature (FP64)
+        n_ev = 1024
+        ex, ey = px[:n_ev].contiguous(), py[:n_ev].contiguous()
+        v.evaluate_points(tree, ops, f, ws, ex, ey, stream=stream)
+        ets = []
+        for _ in range(3):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            v.evaluate_points(tree, ops, f, ws, ex, ey, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ets.append(e0.elapsed_time(e1))
+        ems = statistics.mean(ets)
+        offnode["stored_expansions"] = {"kernel": "offnode_kernel", "points": n_ev, "ms": ems,
+                                        "pts_per_s": n_ev / (ems / 1e3),
+                                        "sample": "the first 1024 of the points above"}
     if args.precision == "fp64":
         flops = 2.0 * 3 * kk * kk * tree.list_len[0] * nrhs  # near-field table applies per step
         achieved = flops / (stage_ms["near"] / 1e3) / 1e12

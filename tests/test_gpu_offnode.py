@@ -3,7 +3,8 @@ the oracle's offnode.evaluate, element by element, through the C ABI.
 
 Cases: a uniform tree and adaptive trees with W and X lists (k = 8 and 16), seeded random points,
 points at leaf nodes (where it must give the solve's own values), points on shared leaf edges and
-corners (the leaf convention), and points outside the root (NaN). Bar: 1e-12 relative to the largest
+corners (the leaf convention), points 1e-3, 1e-6 and 1e-9 of a leaf width from a leaf edge (the
+kernel's finer quadrature rules) and points outside the root (NaN). Bar: 1e-12 relative to the largest
 |value| over the points (FP64 throughout; the near field by on-the-fly quadrature on both sides,
 with different rules: tanh-sinh on the GPU, Gauss-Legendre with log-product weights in the oracle).
 """
@@ -63,6 +64,15 @@ def test_evaluate_points_matches_oracle(name, k, p, mk, tol, depth, oracle_ops):
     pts.append(np.column_stack([X.reshape(-1)[node_sel], Y.reshape(-1)[node_sel]]))
     # on shared edges and a corner of the level-2 grid, and outside the root box
     pts.append(np.array([[0.0, 0.1], [0.25, -0.3], [0.25, 0.25], [-0.5, 0.5], [0.7, 0.0]]))
+    # 1e-3, 1e-6 and 1e-9 of a leaf width on either side of a leaf's right edge (the finer
+    # quadrature rules of the kernel)
+    for b in ot.leaves[len(ot.leaves) // 3:]:  # a leaf whose right edge is inside the root box
+        hb = float(ot.h(int(b)))
+        cx, cy = ot.centre(int(b))
+        if cx + hb < 0.5:
+            break
+    for d in (1e-3, 1e-6, 1e-9):
+        pts.append(np.array([[cx + hb / 2 - d * hb, cy + 0.1 * hb], [cx + hb / 2 + d * hb, cy - 0.2 * hb]]))
     pts = np.concatenate(pts)
     x = torch.from_numpy(pts[:, 0].copy()).cuda()
     y = torch.from_numpy(pts[:, 1].copy()).cuda()
@@ -70,6 +80,7 @@ def test_evaluate_points_matches_oracle(name, k, p, mk, tol, depth, oracle_ops):
     ref = offnode.evaluate(ot, L, oracle_ops(k, p), F, pts[:, 0], pts[:, 1])
     inside = ~np.isnan(ref[0])
     assert np.array_equal(np.isnan(got[0]), ~inside)
+    assert inside[-6:].all()
     for q in range(3):
         assert _rel(got[q][inside], ref[q][inside]) < TOL, (name, q, _rel(got[q][inside], ref[q][inside]))
     # at leaf nodes: the solve's own values
