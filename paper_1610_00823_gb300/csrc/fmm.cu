@@ -1198,7 +1198,8 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
 // V or X list grouped by configuration (host counting sort of the entries) and cut into GEMM
 // tiles of at most GBN entries of one configuration; all device arrays in one allocation.
 static int build_list_groups(DeviceTree* T, const std::vector<int32_t>& cfg, const std::vector<int32_t>& ptr, int ncfg,
-                             int32_t** by_cfg, int32_t** tiles_out, int32_t* n_tiles, int32_t** tgt_out) {
+                             int32_t** by_cfg, int32_t** tiles_out, int32_t* n_tiles, int32_t** tgt_out,
+                             cudaStream_t st) {
     const int64_t n = (int64_t)cfg.size();
     std::vector<int64_t> start(ncfg + 1, 0);
     for (int64_t e = 0; e < n; ++e) ++start[cfg[e] + 1];
@@ -1225,29 +1226,29 @@ static int build_list_groups(DeviceTree* T, const std::vector<int32_t>& cfg, con
     std::copy(order.begin(), order.end(), host.begin() + n_tile_ints);
     std::copy(tgt.begin(), tgt.end(), host.begin() + n_tile_ints + n_order);
     int32_t* dev = nullptr;
-    VFMM_CUDA(cudaMalloc(&dev, host.size() * sizeof(int32_t)));
-    VFMM_CUDA(cudaMemcpy(dev, host.data(), host.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    VFMM_CHECK(tree_malloc(reinterpret_cast<void**>(&dev), host.size() * sizeof(int32_t), st));
+    VFMM_CUDA(cudaMemcpyAsync(dev, host.data(), host.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     *tiles_out = dev;  // owns the allocation
     *by_cfg = dev + n_tile_ints;
     if (tgt_out) *tgt_out = dev + n_tile_ints + n_order;
     return VFMM_OK;
 }
 
-int build_near_tiles(DeviceTree* T, const HostLists& H) {
+int build_near_tiles(DeviceTree* T, const HostLists& H, cudaStream_t st) {
     VFMM_CHECK(build_list_groups(T, H.cfg[VFMM_LIST_V], H.ptr[VFMM_LIST_V], kVCfg, &T->v_by_cfg, &T->v_tiles,
-                                 &T->n_v_tiles, nullptr));
+                                 &T->n_v_tiles, nullptr, st));
     VFMM_CHECK(build_list_groups(T, H.cfg[VFMM_LIST_X], H.ptr[VFMM_LIST_X], kFarCfg, &T->x_by_cfg, &T->x_tiles,
-                                 &T->n_x_tiles, &T->x_tgt));
+                                 &T->n_x_tiles, &T->x_tgt, st));
     std::vector<int4> tiles;
     for (int c = 0; c < kNearCfg; ++c)
         for (int64_t b = T->u_cfg_start[c]; b < T->u_cfg_start[c + 1]; b += GBN)
             tiles.push_back(make_int4(c, (int)b, (int)std::min<int64_t>(b + GBN, T->u_cfg_start[c + 1]), 0));
     T->n_near_tiles = (int)tiles.size();
-    if (T->near_tiles) cudaFree(T->near_tiles);
+    tree_free(T->near_tiles);
     T->near_tiles = nullptr;
-    VFMM_CUDA(cudaMalloc(&T->near_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int4)));
+    VFMM_CHECK(tree_malloc(reinterpret_cast<void**>(&T->near_tiles), std::max<size_t>(1, tiles.size()) * sizeof(int4), st));
     if (!tiles.empty())
-        VFMM_CUDA(cudaMemcpy(T->near_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        VFMM_CUDA(cudaMemcpyAsync(T->near_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     return VFMM_OK;
 }
 

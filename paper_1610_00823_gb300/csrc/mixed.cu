@@ -586,12 +586,13 @@ int build_split_plan(const PlanItems& I, const std::vector<int32_t>& order, int 
     return VFMM_OK;
 }
 
-int commit_plan_arena(PlanArena& A, PlanSet* PS) {
+int commit_plan_arena(PlanArena& A, PlanSet* PS, cudaStream_t st) {
     void* base = nullptr;
-    VFMM_CUDA(cudaMalloc(&base, std::max<size_t>(256, A.data.size() * sizeof(int32_t))));
+    VFMM_CHECK(tree_malloc(&base, A.data.size() * sizeof(int32_t), st));
     PS->arena = base;
     if (!A.data.empty())
-        VFMM_CUDA(cudaMemcpy(base, A.data.data(), A.data.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        VFMM_CUDA(cudaMemcpyAsync(base, A.data.data(), A.data.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    VFMM_CUDA(cudaStreamSynchronize(st));
     int32_t* b = static_cast<int32_t*>(base);
     for (SplitPlan* top : {&PS->near, &PS->s2m, &PS->m2l, &PS->far, &PS->s2l})
         for (SplitPlan* P = top; P; P = P->alt) {
@@ -693,7 +694,7 @@ void free_plan_set(PlanSet* ps) {
     free_split_plan(&ps->m2l);
     free_split_plan(&ps->far);
     free_split_plan(&ps->s2l);
-    if (ps->arena) cudaFree(ps->arena);
+    tree_free(ps->arena);
     ps->arena = nullptr;
 }
 
@@ -851,7 +852,7 @@ static int build_near_plan(const DeviceTree& T, int R, const HostLists& H, PlanA
 // All five plans of R folded right-hand sides. The contractions are independent: each is built on a
 // host thread of its own into its own arena; the arenas are then joined (offsets shifted) and
 // copied to the device at once.
-static int build_plans(const DeviceTree& T, int R, const HostLists& H, PlanSet* PS) {
+static int build_plans(const DeviceTree& T, int R, const HostLists& H, PlanSet* PS, cudaStream_t st) {
     PS->R = R;
     int dev = 0;
     VFMM_CUDA(cudaGetDevice(&dev));
@@ -884,17 +885,17 @@ static int build_plans(const DeviceTree& T, int R, const HostLists& H, PlanSet* 
                 if (P->off[i] >= 0) P->off[i] += base;
         all.data.insert(all.data.end(), A[c].data.begin(), A[c].data.end());
     }
-    return commit_plan_arena(all, PS);
+    return commit_plan_arena(all, PS, st);
 }
 
-int build_mixed_plan(DeviceTree* T) {
+int build_mixed_plan(DeviceTree* T, cudaStream_t st) {
     HostLists H;
     VFMM_CHECK(fetch_host_lists(*T, &H));
-    VFMM_CHECK(build_far_slots(T, H));
-    VFMM_CHECK(build_near_tiles(T, H));  // the FP64 form's GEMM tiles
+    VFMM_CHECK(build_far_slots(T, H, st));
+    VFMM_CHECK(build_near_tiles(T, H, st));  // the FP64 form's GEMM tiles
     T->plans_r = new std::map<int, PlanSet*>();
     T->plans_mu = new std::mutex();
-    return build_plans(*T, 1, H, &T->plans);
+    return build_plans(*T, 1, H, &T->plans, st);
 }
 
 int plans_for(const DeviceTree& T, int R, const PlanSet** out) {
@@ -912,7 +913,7 @@ int plans_for(const DeviceTree& T, int R, const PlanSet** out) {
     PlanSet* ps = new PlanSet();
     HostLists H;
     int rc = fetch_host_lists(T, &H);
-    if (rc == VFMM_OK) rc = build_plans(T, R, H, ps);
+    if (rc == VFMM_OK) rc = build_plans(T, R, H, ps, cudaStreamPerThread);
     if (rc != VFMM_OK) {
         free_plan_set(ps);
         delete ps;

@@ -214,7 +214,7 @@ struct PlanArena {
         return off;
     }
 };
-int commit_plan_arena(PlanArena& A, PlanSet* PS);
+int commit_plan_arena(PlanArena& A, PlanSet* PS, cudaStream_t st);
 
 // Targets of one split contraction in flat form: target t (output row tgt[t]) holds the items
 // (tab[e], src[e]) = (table, gathered operand row), e in [ptr[t], ptr[t + 1]), and sorts by key[t].
@@ -251,13 +251,13 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
 // Partial-sum elements (float2) of the three buffers whose contractions may run at the same time:
 // [0] S2M, M2L and the leaf far field (one after another), [1] the near field, [2] S2L.
 void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t elems[3]);
-int build_mixed_plan(DeviceTree* T);
+int build_mixed_plan(DeviceTree* T, cudaStream_t st);
 // Host copies of the tree arrays the plan builders read (fetched once per plan set).
 struct HostLists {
     std::vector<int32_t> bol, lob, ptr[4], idx[4], cfg[4];
 };
 int fetch_host_lists(const DeviceTree& T, HostLists* H);
-int build_far_slots(DeviceTree* T, const HostLists& H);
+int build_far_slots(DeviceTree* T, const HostLists& H, cudaStream_t st);
 // Plan of one far-field contraction (kCtrS2M, kCtrM2L, kCtrS2L or kCtrFar) into PS.
 int build_far_plan(int which, const DeviceTree& T, int R, const HostLists& H, PlanArena& A, PlanSet* PS);
 // Near field in two parts: max |f| and the f slices (also the operand of S2M and S2L), then the

@@ -253,15 +253,15 @@ int fetch_host_lists(const DeviceTree& T, HostLists* H) {
     return VFMM_OK;
 }
 
-int build_far_slots(DeviceTree* T, const HostLists& H) {
+int build_far_slots(DeviceTree* T, const HostLists& H, cudaStream_t st) {
     const int nl = T->n_leaves;
     const std::vector<int32_t>& bol = H.bol;
     const std::vector<int32_t>& ptr = H.ptr[VFMM_LIST_W];
     std::vector<int32_t> slot(nl + 1, 0);
     for (int t = 0; t < nl; ++t) slot[t + 1] = slot[t] + 1 + (ptr[bol[t] + 1] - ptr[bol[t]]);
     T->n_far_slots = slot[nl];
-    VFMM_CUDA(cudaMalloc(&T->far_slot, (nl + 1) * sizeof(int32_t)));
-    VFMM_CUDA(cudaMemcpy(T->far_slot, slot.data(), (nl + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    VFMM_CHECK(tree_malloc(reinterpret_cast<void**>(&T->far_slot), (nl + 1) * sizeof(int32_t), st));
+    VFMM_CUDA(cudaMemcpyAsync(T->far_slot, slot.data(), (nl + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     return VFMM_OK;
 }
 

@@ -57,6 +57,21 @@ static int build_pool(cudaMemPool_t* out) {
     return VFMM_OK;
 }
 
+int tree_malloc(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool;
+    VFMM_CHECK(build_pool(&pool));
+    cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 256), pool, st);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(VFMM_ERR_OOM, "stream-ordered allocation failed for a tree array");
+    }
+    return VFMM_OK;
+}
+
+void tree_free(void* p) {
+    if (p) cudaFreeAsync(p, cudaStreamPerThread);
+}
+
 // Device buffer of the tree build. alloc(count, st): a temporary from the build pool, allocated
 // and freed in the order of stream st (no free waits for the device; the stream must outlive the
 // buffer); alloc_keep(count): an array the tree or a builder keeps (cudaMalloc), which release()
@@ -110,6 +125,9 @@ struct DBuf {
         pooled = true;
         return VFMM_OK;
     }
+    // an array the tree keeps, from the build pool in the order of stream s (release() hands it to
+    // the tree, whose free_tree returns it with tree_free)
+    int alloc_tree(size_t count, cudaStream_t s) { return alloc(count, s); }
     int alloc_keep(size_t count) {
         reset();
         n = count;
@@ -755,9 +773,9 @@ static int compute_lists(DeviceTree* T, cudaStream_t st) {
     DBuf<int32_t> idx[4], cfg[4], ptr[4];
     for (int q = 0; q < 4; ++q) {
         T->llen[q] = starts[q + 1] - starts[q];
-        VFMM_CHECK(idx[q].alloc_keep(std::max<int64_t>(1, T->llen[q])));
-        VFMM_CHECK(cfg[q].alloc_keep(std::max<int64_t>(1, T->llen[q])));
-        VFMM_CHECK(ptr[q].alloc_keep(n + 1));
+        VFMM_CHECK(idx[q].alloc_tree(std::max<int64_t>(1, T->llen[q]), st));
+        VFMM_CHECK(cfg[q].alloc_tree(std::max<int64_t>(1, T->llen[q]), st));
+        VFMM_CHECK(ptr[q].alloc_tree(n + 1, st));
     }
     // offsets within each list: subtract the row start
     for (int q = 0; q < 4; ++q) {
@@ -776,8 +794,8 @@ static int compute_lists(DeviceTree* T, cudaStream_t st) {
     const int64_t nU = T->llen[VFMM_LIST_U];
     DBuf<int32_t> flags, byc, tgt;
     VFMM_CHECK(flags.alloc((size_t)kNearCfg * nU, st));
-    VFMM_CHECK(byc.alloc_keep(std::max<int64_t>(1, nU)));
-    VFMM_CHECK(tgt.alloc_keep(std::max<int64_t>(1, nU)));
+    VFMM_CHECK(byc.alloc_tree(std::max<int64_t>(1, nU), st));
+    VFMM_CHECK(tgt.alloc_tree(std::max<int64_t>(1, nU), st));
     cfg_flags_kernel<<<nblk(nU), 256, 0, st>>>(T->lcfg[0], nU, kNearCfg, flags.p);
     VFMM_CUDA(cudaGetLastError());
     int64_t tot = 0;
@@ -1061,16 +1079,16 @@ static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt
     T->n_boxes = n;
     DBuf<uint32_t> key;
     DBuf<int32_t> level, ix, iy, parent, child0, isleaf, rank, lob, bol, lsd;
-    VFMM_CHECK(key.alloc_keep(n));
-    VFMM_CHECK(level.alloc_keep(n));
-    VFMM_CHECK(ix.alloc_keep(n));
-    VFMM_CHECK(iy.alloc_keep(n));
-    VFMM_CHECK(parent.alloc_keep(n));
-    VFMM_CHECK(child0.alloc_keep(n));
+    VFMM_CHECK(key.alloc_tree(n, st));
+    VFMM_CHECK(level.alloc_tree(n, st));
+    VFMM_CHECK(ix.alloc_tree(n, st));
+    VFMM_CHECK(iy.alloc_tree(n, st));
+    VFMM_CHECK(parent.alloc_tree(n, st));
+    VFMM_CHECK(child0.alloc_tree(n, st));
     VFMM_CHECK(isleaf.alloc(n, st));
     VFMM_CHECK(rank.alloc(n, st));
-    VFMM_CHECK(lob.alloc_keep(n));
-    VFMM_CHECK(lsd.alloc_keep(depth + 2));
+    VFMM_CHECK(lob.alloc_tree(n, st));
+    VFMM_CHECK(lsd.alloc_tree(depth + 2, st));
     for (int l = 0; l <= depth; ++l)
         VFMM_CUDA(cudaMemcpyAsync(key.p + T->level_start[l], keys[l].p, cnt[l] * sizeof(uint32_t),
                                   cudaMemcpyDeviceToDevice, st));
@@ -1080,7 +1098,7 @@ static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt
     VFMM_CUDA(cudaGetLastError());
     int64_t nleaf = 0;
     VFMM_CHECK(exclusive_scan(isleaf.p, rank.p, n, &nleaf, st));
-    VFMM_CHECK(bol.alloc_keep(nleaf));
+    VFMM_CHECK(bol.alloc_tree(nleaf, st));
     leaf_rank_kernel<<<nblk(n), 256, 0, st>>>(isleaf.p, rank.p, n, lob.p, bol.p);
     VFMM_CUDA(cudaGetLastError());
     T->n_leaves = (int32_t)nleaf;
@@ -1107,18 +1125,22 @@ static int finalize(std::vector<DBuf<uint32_t>>& keys, std::vector<int64_t>& cnt
                 if (c0[b] >= 0) nl.push_back(b);
         }
         T->nonleaf_start[depth + 1] = (int32_t)nl.size();
-        VFMM_CUDA(cudaMalloc(&T->nonleaf, std::max<size_t>(1, nl.size()) * sizeof(int32_t)));
+        VFMM_CHECK(tree_malloc(reinterpret_cast<void**>(&T->nonleaf), std::max<size_t>(1, nl.size()) * sizeof(int32_t),
+                               st));
         if (!nl.empty())
-            VFMM_CUDA(cudaMemcpy(T->nonleaf, nl.data(), nl.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        VFMM_CUDA(cudaMalloc(&T->nonleaf_start_dev, (depth + 2) * sizeof(int32_t)));
-        VFMM_CUDA(cudaMemcpy(T->nonleaf_start_dev, T->nonleaf_start.data(), (depth + 2) * sizeof(int32_t),
-                             cudaMemcpyHostToDevice));
+            VFMM_CUDA(cudaMemcpyAsync(T->nonleaf, nl.data(), nl.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        VFMM_CHECK(tree_malloc(reinterpret_cast<void**>(&T->nonleaf_start_dev), (depth + 2) * sizeof(int32_t), st));
+        VFMM_CUDA(cudaMemcpyAsync(T->nonleaf_start_dev, T->nonleaf_start.data(), (depth + 2) * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, st));
+        VFMM_CUDA(cudaStreamSynchronize(st));  // nl leaves scope; later readers use other streams
     }
-    VFMM_CHECK(build_mixed_plan(T));
+    VFMM_CHECK(build_mixed_plan(T, st));
     return VFMM_OK;
 }
 
 void free_tree(DeviceTree* t) {
+    // work queued on any stream may still read the tree
+    cudaDeviceSynchronize();
     // v_by_cfg, x_by_cfg and x_tgt point into the v_tiles and x_tiles allocations
     void* ps[] = {t->key,         t->level,       t->ix,       t->iy,           t->parent,     t->child0,
                   t->leaf_of_box, t->box_of_leaf, t->level_start_dev, t->u_by_cfg, t->u_tgt, t->near_tiles,
@@ -1132,12 +1154,11 @@ void free_tree(DeviceTree* t) {
         delete t->plans_r;
     }
     delete t->plans_mu;
-    for (void* p : ps)
-        if (p) cudaFree(p);
+    for (void* p : ps) tree_free(p);
     for (int q = 0; q < 4; ++q) {
-        if (t->lptr[q]) cudaFree(t->lptr[q]);
-        if (t->lidx[q]) cudaFree(t->lidx[q]);
-        if (t->lcfg[q]) cudaFree(t->lcfg[q]);
+        tree_free(t->lptr[q]);
+        tree_free(t->lidx[q]);
+        tree_free(t->lcfg[q]);
     }
     *t = DeviceTree();
 }

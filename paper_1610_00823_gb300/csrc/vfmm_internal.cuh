@@ -251,7 +251,13 @@ void free_plan_set(PlanSet* ps);
 // Plans for R folded right-hand sides (R = 1: the tree's own set); builds and caches on first use.
 int plans_for(const DeviceTree& T, int R, const PlanSet** out);
 struct HostLists;
-int build_near_tiles(DeviceTree* t, const HostLists& h);
+int build_near_tiles(DeviceTree* t, const HostLists& h, cudaStream_t st);
+// Device arrays a tree keeps (boxes, lists, schedules) come from a per-device stream-ordered pool:
+// tree_malloc allocates in the order of stream st (the tree build synchronises st before it
+// returns, after which the arrays are valid on every stream); tree_free returns one to the pool
+// and is called once the device has finished with it (free_tree synchronises the device first).
+int tree_malloc(void** p, size_t bytes, cudaStream_t st);
+void tree_free(void* p);
 // vfmm_volume_potential with flags: fork = false keeps every launch on `st` (no second stream);
 // reset = false leaves the workspace's status word as it is (a caller solving several right-hand
 // sides one after another clears it once, so that a timeout in an early one is not lost).
