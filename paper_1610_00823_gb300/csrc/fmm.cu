@@ -679,21 +679,35 @@ __global__ void down_mixed_kernel(DownArgs d) {
 }
 
 // ---------------------------------------------------------------- persistent tree passes
-// One cooperative launch walks all levels: the translations are cut into one-warp units (a row pair
-// of one virtual box) dealt over the warps of every CTA, and the 4 position tables sit in shared
-// memory for the whole pass. There is no barrier between levels: a unit waits (bounded) only for
-// the expansions it reads, through per-box readiness counters, so a box starts as soon as its
-// children (M2M) or its parent (L2L) are done. Every unit's inputs are produced by units that come
-// earlier in the global unit order, and each warp takes its units in that order, so the earliest
-// unfinished unit can always proceed (all CTAs are resident: cooperative launch). Data written by
-// other CTAs are read through L2 (ld.global.cg).
+// One cooperative launch walks all levels. A unit is one virtual box, taken by a group of
+// kGroupThreads threads (one warp on each of the SM's four schedulers, synchronised by a named
+// barrier), and the real triangular matrix of the translation sits in shared memory for the whole
+// pass. There is no barrier between levels: a unit waits (bounded) only for the expansions it reads,
+// through per-box readiness counters, so a box starts as soon as its children (M2M) or its parent
+// (L2L) are done. Every unit's inputs are produced by work that comes earlier in the global order,
+// and each group takes its units in that order, so the earliest unfinished unit can always proceed
+// (all CTAs are resident: cooperative launch). Data written by other CTAs are read through L2
+// (ld.global.cg).
+//
+// Position-DFT form of the translations (this part retires about 2 FP64 FMAs per clock per SM, so
+// the FP64 operation count per box sets the time of a level). With the rotated real form (tables.cu)
+// M2M is A_l = sum_pos sigma^pos_l sum_n Rm[n][l] rho^pos_n a^pos_n, and the four child shifts
+// are the Gaussian integers g_pos = i^e g_0, g_0 = 1 + i, with e = 0, 1, 2, 3 for the children
+// at (+,+), (-,+), (-,-), (+,-) (child slots 3, 2, 0, 1). Then sigma^pos_l = i^(e l) sigma0_l and
+// rho^pos_n = i^(-e n) rho0_n with sigma0_l = i^floor(l/2) (1 + i)^(l mod 2), rho0_n = conj(sigma0_n), so
+//   M2M:  A_l = sigma0_l sum_{n<=l} Rm[n][l] E^(l mod 4)_n,   E^(c)_n = rho0_n F^((c - n) mod 4)_n,
+//         F^(k)_n = sum_e i^(e k) a^(e)_n (a 4-point DFT over the children);
+//   L2L:  c^(e)_m = rho0_m sum_c i^(e c) S^(c)_m,   S^(c)_m = sum_{l>=m, l-m = c mod 4} Rl[l][m] sigma0_l b_l.
+// One real matrix-vector product per box instead of four complex ones: about P^2 FMAs plus 16 adds
+// per coefficient for the DFT, against 8 P^2 FMAs with the four complex position tables.
 constexpr int kPassThreads = 512;
-constexpr int kPassMaxCtas = 152;  // largest pass grid (measured against smaller grids on the 20-Gaussian tree)
+constexpr int kGroupThreads = 128;
+constexpr int kPassGroups = kPassThreads / kGroupThreads;
+constexpr int kPassWarps = kPassThreads / 32;
+constexpr int kPassMaxCtas = 152;  // largest pass grid
 
-// Readiness counters of the dataflow tree passes: ready[vb] counts the units that have written
-// their part of virtual box vb's expansion (M2M: the box's own multipole; L2L: the box's local), and
-// npair = (P + 1) / 2 units complete it. A producer publishes with a release add after its writes,
-// a consumer polls with acquire loads before reading the expansion through L2.
+// Readiness counters of the dataflow tree passes: a producer publishes with a release add after its
+// writes, a consumer polls with acquire loads before reading the expansion through L2.
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -715,85 +729,39 @@ __device__ bool wait_ready(const unsigned* flag, unsigned need, int* err) {
     return false;
 }
 
-
-// Loads the 4 position tables into shared memory (bulk copy); one decision for the whole CTA.
-__device__ bool load_tables(double2* sT, const double2* tab, int P, int* err) {
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ volatile int no_abort;
-    const uint32_t bar_a = tc::smem_u32(&bar);
-    const uint32_t bytes = (uint32_t)(4 * P * P) * sizeof(double2);
-    if (threadIdx.x == 0) {
-        no_abort = 0;
-        tc::mbar_init(bar_a, 1);
-        tc::mbar_fence_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        tc::mbar_arrive_expect_tx(bar_a, bytes);
-        constexpr uint32_t kChunk = 32768;
-        for (uint32_t off = 0; off < bytes; off += kChunk)
-            tc::bulk_copy_g2s(tc::smem_u32(sT) + off, reinterpret_cast<const char*>(tab) + off,
-                              min(kChunk, bytes - off), bar_a);
-    }
-    const bool landed = tc::mbar_wait(bar_a, 0, &no_abort);
-    if (!__syncthreads_and(landed)) {
-        if (threadIdx.x == 0 && err) atomicExch(err, 5);
-        settle_bulk_copy(bar_a, &no_abort);
-        return false;
-    }
-    return true;
+// Barrier of the kGroupThreads threads of group `grp` (named barrier 1 + grp; 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int grp) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "n"(kGroupThreads) : "memory");
 }
 
-// One output row pair (j, P-1-j) of one virtual box's four child-position translations, computed
-// by one warp: lane (pos, ks) = (lane / 8, lane % 8) takes position pos and the inputs
-// n = ks, ks + 8, ... of its triangular ranges (M2M row o takes n <= o, L2L row m takes n >= m), so
-// the 4 (P + 1) complex multiply-adds of a row pair spread over the 32 lanes. All of a lane's
-// inputs are loaded before its first multiply-add. Shuffles then sum the 8 input slices of each
-// position, and for M2M (mode 0) the four positions as well, in a fixed order (the results are
-// deterministic). Tables [pos][in][out] complex in shared memory: the 8 lanes of a quarter warp read
-// rows n one apart (stride P complex = 4P banks), which never share a bank. Inputs: mode 0, child
-// pos at x + pos * xs; mode 1, the parent local at x. Returns the row-a and row-b sums: mode 0 in
-// every lane, summed over the positions; mode 1 in every lane of position pos, for that position.
-__device__ __forceinline__ void translate_warp(int mode, const double2* __restrict__ sT, const double2* x,
-                                               size_t xs, int P, int j, int lane, double2& ra, double2& rb) {
-    const int pos = lane >> 3, ks = lane & 7;
-    const int oa = j, ob = P - 1 - j;  // oa <= ob
-    const double2* M = sT + (size_t)pos * P * P;
-    const double2* xp = mode == 0 ? x + pos * xs : x;
-    double2 v[8];  // P <= 64
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int n = ks + 8 * i;
-        v[i] = (n < P && (mode != 0 || n <= ob)) ? __ldcg(xp + n) : make_double2(0.0, 0.0);
+// v i^m (sign changes and swaps; exact).
+__device__ __forceinline__ double2 mul_ipow(double2 v, int m) {
+    switch (m & 3) {
+        case 0: return v;
+        case 1: return make_double2(-v.y, v.x);
+        case 2: return make_double2(-v.x, -v.y);
+        default: return make_double2(v.y, -v.x);
     }
-    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int n = ks + 8 * i;
-        if (n >= P || (mode == 0 && n > ob)) break;
-        if (mode == 0 ? n <= oa : n >= oa) {
-            const double2 m = M[(size_t)n * P + oa];
-            ar = fma(m.x, v[i].x, fma(-m.y, v[i].y, ar));
-            ai = fma(m.x, v[i].y, fma(m.y, v[i].x, ai));
-        }
-        if (ob != oa && (mode == 0 || n >= ob)) {
-            const double2 m = M[(size_t)n * P + ob];
-            br = fma(m.x, v[i].x, fma(-m.y, v[i].y, br));
-            bi = fma(m.x, v[i].y, fma(m.y, v[i].x, bi));
-        }
-    }
-    const int lim = mode == 0 ? 32 : 8;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        if (off >= lim) break;
-        ar += __shfl_xor_sync(0xffffffffu, ar, off);
-        ai += __shfl_xor_sync(0xffffffffu, ai, off);
-        br += __shfl_xor_sync(0xffffffffu, br, off);
-        bi += __shfl_xor_sync(0xffffffffu, bi, off);
-    }
-    ra = make_double2(ar, ai);
-    rb = make_double2(br, bi);
 }
+// v sigma0_l = v i^floor(l/2) (1 + i)^(l mod 2): one addition per component for odd l.
+__device__ __forceinline__ double2 mul_sigma0(double2 v, int l) {
+    if (l & 1) v = make_double2(v.x - v.y, v.x + v.y);
+    return mul_ipow(v, l >> 1);
+}
+// v rho0_n = v (-i)^floor(n/2) (1 - i)^(n mod 2).
+__device__ __forceinline__ double2 mul_rho0(double2 v, int n) {
+    if (n & 1) v = make_double2(v.x + v.y, v.y - v.x);
+    return mul_ipow(v, -(n >> 1));
+}
+// sum_e i^(e k) x_e (one output of a 4-point DFT): (x0 +- x2) + i^k (x1 +- x3).
+__device__ __forceinline__ double2 dft4(double2 x0, double2 x1, double2 x2, double2 x3, int k) {
+    const bool odd = k & 1;
+    const double2 u = odd ? make_double2(x0.x - x2.x, x0.y - x2.y) : make_double2(x0.x + x2.x, x0.y + x2.y);
+    const double2 w = mul_ipow(odd ? make_double2(x1.x - x3.x, x1.y - x3.y) : make_double2(x1.x + x3.x, x1.y + x3.y), k);
+    return make_double2(u.x + w.x, u.y + w.y);
+}
+// Child slot of DFT index e (g_pos = i^e (1 + i)).
+__device__ __forceinline__ int child_of_e(int e) { return (0x1023 >> (4 * e)) & 0xF; }
 
 struct PassArgs {
     int depth, R, P;
@@ -801,7 +769,7 @@ struct PassArgs {
     const int32_t* nonleaf_start;  // device, depth + 2
     const int32_t* level_start;    // device, depth + 2
     const int32_t* child0;
-    const double2* tab;    // the 4 position tables [pos][in][out] complex
+    const double* tab;     // the real triangular matrix of the rotated form, [in][out]
     double2* ex;           // Mexp (upward) or Lexp (downward), [n_boxes * R][P] complex
     const int32_t* parent;
     unsigned int* ready;   // [n_boxes * R] readiness counters, zero at launch
@@ -810,107 +778,186 @@ struct PassArgs {
     int* err;
 };
 
-// The work of a pass is a list of units (a row pair of one virtual box), level by level; warp w of
-// CTA c takes units slot, slot + nslots, ... with slot = w * gridDim.x + c, so that the units of a
-// level spread over the SMs first (this part retires about 2 FP64 FMAs per clock per SM).
-constexpr int kPassWarps = kPassThreads / 32;
+// Shared memory of a pass: the real matrix [P][P] (rounded up to 16 bytes), then per group the
+// scratch of one unit: M2M E [4][P] and the partial sums [kGroupThreads][2]; L2L sigma0 b [P] and
+// S [4][P] (complex).
+__host__ __device__ inline size_t pass_table_bytes(int P) { return ((size_t)P * P * sizeof(double) + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t pass_group_bytes(int P) { return (size_t)(4 * P + 2 * kGroupThreads) * sizeof(double2); }
+__host__ __device__ inline size_t pass_smem_bytes(int P) { return pass_table_bytes(P) + kPassGroups * pass_group_bytes(P); }
 
-// Shared memory of a pass: the 4 position tables [4][P][P] complex.
-__host__ __device__ inline size_t pass_smem_bytes(int P) { return (size_t)4 * P * P * sizeof(double2); }
+// The real matrix into shared memory (plain loads; P^2 doubles need not be a multiple of 16 bytes).
+__device__ __forceinline__ void load_real_table(double* sR, const double* tab, int P) {
+    for (int q = threadIdx.x; q < P * P; q += blockDim.x) sR[q] = __ldg(tab + q);
+    __syncthreads();
+}
 
-// All M2M levels, finest parents first (the global unit order).
+// All M2M levels, finest parents first (the global unit order): unit = one virtual parent box.
 __global__ void __launch_bounds__(kPassThreads, 1) upward_pass_kernel(PassArgs a) {
     extern __shared__ __align__(128) unsigned char pass_raw[];
+    __shared__ int abort_grp[kPassGroups];
     const int P = a.P, R = a.R;
-    double2* sT = reinterpret_cast<double2*>(pass_raw);
-    if (!load_tables(sT, a.tab, P, a.err)) return;
-    const int lane = threadIdx.x & 31;
-    const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassWarps;
-    const unsigned npair = (unsigned)(P + 1) / 2;
+    double* sR = reinterpret_cast<double*>(pass_raw);
+    const int grp = threadIdx.x / kGroupThreads, g = threadIdx.x % kGroupThreads;
+    double2* sE = reinterpret_cast<double2*>(pass_raw + pass_table_bytes(P) + grp * pass_group_bytes(P));
+    double2* sPart = sE + 4 * P;
+    if (g == 0) abort_grp[grp] = 0;
+    load_real_table(sR, a.tab, P);
+    const int npair = (P + 1) / 2, ns = max(1, kGroupThreads / npair);  // row pairs x slices
+    const int slot = grp * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassGroups;
     int l = a.depth - 1, lbase = 0;
-    int lunits = l >= 2 ? (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * (int)npair : 0;
+    int lunits = l >= 2 ? (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R : 0;
     for (int u = slot;; u += nslots) {
         while (l >= 2 && u >= lbase + lunits) {
             lbase += lunits;
-            if (--l >= 2) lunits = (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R * (int)npair;
+            if (--l >= 2) lunits = (a.nonleaf_start[l + 1] - a.nonleaf_start[l]) * R;
         }
         if (l < 2) break;
-        const int lu = u - lbase;
-        const int vi = lu / (int)npair, j = lu - vi * (int)npair;
-        const int bi = vi / R, r = vi - bi * R;
+        const int vi = u - lbase, bi = vi / R, r = vi - bi * R;
         const int b = a.nonleaf[a.nonleaf_start[l] + bi], c0 = a.child0[b];
         // the non-leaf children's multipoles must be complete (leaf multipoles come from S2M)
-        bool ok = true;
-        if (lane < 4 && a.child0[c0 + lane] >= 0)
-            ok = wait_ready(a.ready + (size_t)(c0 + lane) * R + r, npair, a.err);
-        if (!__all_sync(0xffffffffu, ok)) return;
-        __syncwarp();
-        double2 ra, rb;
-        // the four children are consecutive boxes: position pos is virtual box (c0 + pos) R + r
-        translate_warp(0, sT, a.ex + ((size_t)c0 * R + r) * P, (size_t)R * P, P, j, lane, ra, rb);
-        if (lane == 0) {
-            double2* out = a.ex + ((size_t)b * R + r) * P;
-            out[j] = ra;
-            int e = max(part_exp(ra.x, 2 * j), part_exp(ra.y, 2 * j + 1));
-            if (j != P - 1 - j) {
-                out[P - 1 - j] = rb;
-                e = max(e, max(part_exp(rb.x, 2 * (P - 1 - j)), part_exp(rb.y, 2 * (P - 1 - j) + 1)));
-            }
-            // the M2L operand's level exponent (mixed form), taken as the coefficients are written
-            if (a.glev && e != INT_MIN) atomicMax(a.glev + (size_t)l * R + r, (unsigned)(e + (int)kGexpBias));
-            red_release_add_u32(a.ready + (size_t)b * R + r, 1u);
+        if (g < 4 && a.child0[c0 + g] >= 0 && !wait_ready(a.ready + (size_t)(c0 + g) * R + r, 1u, a.err))
+            abort_grp[grp] = 1;
+        group_sync(grp);
+        if (abort_grp[grp]) return;
+        // E^(c)_n over the (k, n) pairs, the four children read once per pair
+        const double2* x = a.ex + ((size_t)c0 * R + r) * P;
+        const size_t xs = (size_t)R * P;
+        for (int q = g; q < 4 * P; q += kGroupThreads) {
+            const int k = q / P, n = q - k * P;
+            const double2 f = dft4(__ldcg(x + 3 * xs + n), __ldcg(x + 2 * xs + n), __ldcg(x + n),
+                                   __ldcg(x + xs + n), k);
+            sE[((k + n) & 3) * P + n] = mul_rho0(f, n);
         }
+        group_sync(grp);
+        // row pair (j, P-1-j), slice s of the fused loop over both rows' inputs (row oa takes n <= oa)
+        if (g < npair * ns) {
+            const int j = g / ns, s = g - j * ns;
+            const int oa = j, ob = P - 1 - j;
+            const int la = oa + 1, lb = ob != oa ? ob + 1 : 0;
+            const double2* ea = sE + (oa & 3) * P;
+            const double2* eb = sE + (ob & 3) * P;
+            double ar = 0.0, ai = 0.0, br = 0.0, bi2 = 0.0;
+            for (int i = s; i < la + lb; i += ns) {
+                if (i < la) {
+                    const double m = sR[i * P + oa];
+                    const double2 e = ea[i];
+                    ar = fma(m, e.x, ar);
+                    ai = fma(m, e.y, ai);
+                } else {
+                    const int n = i - la;
+                    const double m = sR[n * P + ob];
+                    const double2 e = eb[n];
+                    br = fma(m, e.x, br);
+                    bi2 = fma(m, e.y, bi2);
+                }
+            }
+            sPart[2 * g] = make_double2(ar, ai);
+            sPart[2 * g + 1] = make_double2(br, bi2);
+        }
+        group_sync(grp);
+        // row l: its slices summed in order, rotated by sigma0_l
+        int e = INT_MIN;
+        if (g < P) {
+            const int j = min(g, P - 1 - g), w = g == j ? 0 : 1;
+            double2 acc = sPart[2 * j * ns + w];
+            for (int s = 1; s < ns; ++s) {
+                const double2 t = sPart[2 * (j * ns + s) + w];
+                acc = make_double2(acc.x + t.x, acc.y + t.y);
+            }
+            acc = mul_sigma0(acc, g);
+            a.ex[((size_t)b * R + r) * P + g] = acc;
+            e = max(part_exp(acc.x, 2 * g), part_exp(acc.y, 2 * g + 1));
+            __threadfence();
+        }
+        // the M2L operand's level exponent (mixed form), taken as the coefficients are written
+        if (a.glev && g < ((P + 31) & ~31)) level_exp_max(e, a.glev + (size_t)l * R + r);
+        group_sync(grp);
+        if (g == 0) red_release_add_u32(a.ready + (size_t)b * R + r, 1u);
     }
 }
 
-// Mixed form, all downward levels: level 2 boxes combine their M2L/S2L terms (one warp unit per
-// virtual box); below, each non-leaf parent's local is shifted to its 4 children (L2L) and each
-// child's terms are added (row-pair units).
+// Mixed form, all downward levels. First every box of level >= 2 gets its own terms (the M2L and
+// S2L outputs and coefficient 0) in one warp unit per virtual box, counted 1 on its readiness word
+// (level 2 boxes are then complete). Then, level by level, each non-leaf parent's local is shifted
+// to its 4 children (L2L) and added to their own terms, counted 1 more (complete at 2).
 __global__ void __launch_bounds__(kPassThreads, 1) downward_pass_kernel(PassArgs a, DownArgs d) {
     extern __shared__ __align__(128) unsigned char pass_raw[];
+    __shared__ int abort_grp[kPassGroups];
     const int P = a.P, R = a.R;
-    double2* sT = reinterpret_cast<double2*>(pass_raw);
-    if (!load_tables(sT, a.tab, P, a.err)) return;
-    const int lane = threadIdx.x & 31, pos = lane >> 3;
-    const int slot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassWarps;
-    const unsigned npair = (unsigned)(P + 1) / 2;
-    const int b2 = a.level_start[2], n2 = (a.level_start[3] - b2) * R;  // level-2 units
-    int l = 3, lbase = n2;
-    int lunits = l <= a.depth ? (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * (int)npair : 0;
-    for (int u = slot;; u += nslots) {
-        if (u < n2) {
-            // level 2: no parent term; the whole local at once, published as npair contributions
-            const int64_t vb = (int64_t)b2 * R + u;
-            const int b = (int)(vb / R), r = (int)(vb % R);
-            for (int t = lane; t < P; t += 32) a.ex[(size_t)vb * P + t] = combine_local(d, 2, b, r, t, 0.0, 0.0);
+    double* sR = reinterpret_cast<double*>(pass_raw);
+    const int grp = threadIdx.x / kGroupThreads, g = threadIdx.x % kGroupThreads;
+    double2* sG = reinterpret_cast<double2*>(pass_raw + pass_table_bytes(P) + grp * pass_group_bytes(P));
+    double2* sS = sG + P;
+    if (g == 0) abort_grp[grp] = 0;
+    load_real_table(sR, a.tab, P);
+    // own terms: one warp per virtual box
+    {
+        const int lane = threadIdx.x & 31;
+        const int wslot = (threadIdx.x >> 5) * gridDim.x + blockIdx.x, nw = gridDim.x * kPassWarps;
+        const int64_t vb0 = (int64_t)a.level_start[2] * R, vb1 = (int64_t)a.level_start[a.depth + 1] * R;
+        for (int64_t vb = vb0 + wslot; vb < vb1; vb += nw) {
+            const int b = (int)(vb / R), r = (int)(vb % R), lv = a.level[b];
+            for (int t = lane; t < P; t += 32) a.ex[(size_t)vb * P + t] = combine_local(d, lv, b, r, t, 0.0, 0.0);
             __threadfence();
             __syncwarp();
-            if (lane == 0) red_release_add_u32(a.ready + vb, npair);
-            continue;
+            if (lane == 0) red_release_add_u32(a.ready + vb, 1u);
         }
+    }
+    const int npair = (P + 1) / 2;
+    const int slot = grp * gridDim.x + blockIdx.x, nslots = gridDim.x * kPassGroups;
+    int l = 3, lbase = 0;  // l: the children's level
+    int lunits = l <= a.depth ? (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R : 0;
+    for (int u = slot;; u += nslots) {
         while (l <= a.depth && u >= lbase + lunits) {
             lbase += lunits;
-            if (++l <= a.depth) lunits = (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R * (int)npair;
+            if (++l <= a.depth) lunits = (a.nonleaf_start[l] - a.nonleaf_start[l - 1]) * R;
         }
         if (l > a.depth) break;
-        const int lu = u - lbase;
-        const int vi = lu / (int)npair, j = lu - vi * (int)npair;
-        const int bi = vi / R, r = vi - bi * R;
+        const int vi = u - lbase, bi = vi / R, r = vi - bi * R;
         const int b = a.nonleaf[a.nonleaf_start[l - 1] + bi], c0 = a.child0[b];
-        // the parent's local must be complete
+        // the parent's local must be complete, the children's own terms written
         bool ok = true;
-        if (lane == 0) ok = wait_ready(a.ready + (size_t)b * R + r, npair, a.err);
-        if (!__all_sync(0xffffffffu, ok)) return;
-        __syncwarp();
-        double2 ra, rb;
-        translate_warp(1, sT, a.ex + ((size_t)b * R + r) * P, 0, P, j, lane, ra, rb);
-        if ((lane & 7) == 0) {  // one lane per child position: add the child's own terms
-            const int c = c0 + pos, mb = P - 1 - j;
-            double2* out = a.ex + ((size_t)c * R + r) * P;
-            out[j] = combine_local(d, l, c, r, j, ra.x, ra.y);
-            if (j != mb) out[mb] = combine_local(d, l, c, r, mb, rb.x, rb.y);
-            red_release_add_u32(a.ready + (size_t)c * R + r, 1u);
+        if (g == 4) ok = wait_ready(a.ready + (size_t)b * R + r, l - 1 == 2 ? 1u : 2u, a.err);
+        else if (g < 4) ok = wait_ready(a.ready + (size_t)(c0 + g) * R + r, 1u, a.err);
+        if (!ok) abort_grp[grp] = 1;
+        group_sync(grp);
+        if (abort_grp[grp]) return;
+        const double2* bl = a.ex + ((size_t)b * R + r) * P;
+        for (int t = g; t < P; t += kGroupThreads) sG[t] = mul_sigma0(__ldcg(bl + t), t);
+        group_sync(grp);
+        // S^(c) of the row pair (oa, ob): thread (j, c)
+        for (int q = g; q < 4 * npair; q += kGroupThreads) {
+            const int j = q >> 2, c = q & 3;
+            const int oa = j, ob = P - 1 - j;
+            double ar = 0.0, ai = 0.0;
+            for (int li = oa + c; li < P; li += 4) {
+                const double m = sR[li * P + oa];
+                ar = fma(m, sG[li].x, ar);
+                ai = fma(m, sG[li].y, ai);
+            }
+            sS[c * P + oa] = make_double2(ar, ai);
+            if (ob != oa) {
+                double br = 0.0, bi2 = 0.0;
+                for (int li = ob + c; li < P; li += 4) {
+                    const double m = sR[li * P + ob];
+                    br = fma(m, sG[li].x, br);
+                    bi2 = fma(m, sG[li].y, bi2);
+                }
+                sS[c * P + ob] = make_double2(br, bi2);
+            }
         }
+        group_sync(grp);
+        // child e, coefficient m: own terms + rho0_m sum_c i^(e c) S^(c)_m
+        for (int q = g; q < 4 * P; q += kGroupThreads) {
+            const int e = q / P, m = q - e * P;
+            const double2 h = mul_rho0(dft4(sS[m], sS[P + m], sS[2 * P + m], sS[3 * P + m], e), m);
+            double2* out = a.ex + ((size_t)(c0 + child_of_e(e)) * R + r) * P + m;
+            const double2 own = __ldcg(out);
+            *out = make_double2(own.x + h.x, own.y + h.y);
+        }
+        __threadfence();
+        group_sync(grp);
+        if (g < 4) red_release_add_u32(a.ready + (size_t)(c0 + g) * R + r, 1u);
     }
 }
 
@@ -1330,11 +1377,11 @@ static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, 
     VFMM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPassThreads, smem));
     if (per_sm < 1) return fail(VFMM_ERR_INTERNAL, "tree pass kernel does not fit on an SM");
     // A cooperative launch: a unit may wait for units held by any other CTA, so all CTAs must be
-    // resident. Enough CTAs for one unit per warp at the widest level, at most one per SM and at
-    // most kPassMaxCtas: a smaller grid starts sooner when another stream's kernels still hold SMs
-    // (the launch waits until the whole grid fits).
-    const int units = widest_items * ((P + 1) / 2);
-    const int grid = std::max(1, std::min(std::min(per_sm * sm_count(), kPassMaxCtas), (units + kPassWarps - 1) / kPassWarps));
+    // resident. One CTA per box of the widest level (the first group of each CTA takes a level's
+    // first boxes, so that they run on different SMs), at most one per SM and at most kPassMaxCtas:
+    // a smaller grid starts sooner when another stream's kernels still hold SMs (the launch waits
+    // until the whole grid fits).
+    const int grid = std::max(1, std::min(std::min(per_sm * sm_count(), kPassMaxCtas), widest_items));
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeCooperative;
     attr.val.cooperative = 1;
@@ -1476,7 +1523,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.nonleaf_start = T.nonleaf_start_dev;
         pa.level_start = T.level_start_dev;
         pa.child0 = T.child0;
-        pa.tab = reinterpret_cast<const double2*>(o.m2m_t);
+        pa.tab = o.m2m_r;
         pa.ex = reinterpret_cast<double2*>(w.Mexp);
         pa.parent = T.parent;
         pa.ready = w.ready;
@@ -1558,7 +1605,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.nonleaf_start = T.nonleaf_start_dev;
         pa.level_start = T.level_start_dev;
         pa.child0 = T.child0;
-        pa.tab = reinterpret_cast<const double2*>(o.l2l_t);
+        pa.tab = o.l2l_r;
         pa.ex = reinterpret_cast<double2*>(w.Lexp);
         pa.parent = T.parent;
         pa.ready = w.ready + (size_t)T.n_boxes * R;
