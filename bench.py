@@ -784,7 +784,26 @@ def main():
         fp64_form = {"value": whole_job_rate(n_targets, ms64, world), "unit": UNIT, "ms_per_step": ms64,
                      "steps": len(ms64_list), "ops_create_s": t_ops64,
                      "mixed_over_fp64_speedup": ms64 / ms, "rel_diff_mixed_vs_fp64_all_targets": d}
+        # the same FP64 form with the plane-wave (diagonalised) M2L of Section 3.1 in place of the dense
+        # per-entry translation; the downward stage (M2L + S2L + L2L) of one profiled solve of each form
+        # and the mixed form's split-BF16 M2L contraction beside it
+        flush.fill_(1.0)
+        st_dense, _ = volume_potential_profiled(tree, ops64, f, out64, ws64, stream=stream)
         del ws64, _g64
+        ops64.set_m2l(v.M2L_PLANEWAVE)
+        mspw_list, outpw, wspw, _gpw = time_form(ops64, max(3, min(args.steps, 10)))
+        mspw = max_over_ranks(statistics.mean(mspw_list), dist)
+        flush.fill_(1.0)
+        st_pw, _ = volume_potential_profiled(tree, ops64, f, outpw, wspw, stream=stream)
+        dpw = [torch.max(torch.abs(outpw[q] - out64[q])).item() / torch.max(torch.abs(out64[q])).item()
+               for q in range(3)]
+        fp64_form["planewave_m2l"] = {
+            "value": whole_job_rate(n_targets, mspw, world), "unit": UNIT, "ms_per_step": mspw,
+            "waves_per_side": ops64.m2l[1], "rel_diff_vs_dense_fp64_all_targets": dpw,
+            "down_stage_ms": {"fp64_dense_m2l": st_dense["down"], "fp64_planewave_m2l": st_pw["down"]},
+            "mixed_split_bf16_m2l_ms": stage_ms.get("m2l_tc"),
+            "note": "down stage = M2L + S2L + L2L + per-box sums (profiled solve, one stream)"}
+        del wspw, _gpw, outpw
 
     cpu, cpu1 = None, None
     errs = None

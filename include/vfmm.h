@@ -245,6 +245,28 @@ int vfmm_ops_destroy(vfmm_ops* ops);
 int vfmm_ops_set_slices(vfmm_ops* ops, const int32_t* slices);
 int vfmm_ops_get_slices(const vfmm_ops* ops, int32_t* slices);
 
+/* Form of the M2L translation (the V-list far field of Section 3.1). The paper's box code
+ * diagonalises it with plane waves (Section 3.1, citing [Ethridge] and [Hrycak98]); this library
+ * also keeps the dense (p+1) x (p+1) Laurent-to-Taylor matrix per V offset, which the tensor-core
+ * form needs.
+ *  VFMM_M2L_DENSE      dense translation per V entry (the default; the only form of VFMM_MIXED);
+ *  VFMM_M2L_PLANEWAVE  VFMM_FP64 only: per box, the multipole goes to s exponential (plane-wave)
+ *                      coefficients for each of the four sides (1/u^n as a Laplace integral,
+ *                      discretised by an s-node rule built for the 14 rotated V offsets and
+ *                      every order the translation needs); a V entry is then one complex
+ *                      multiplication per coefficient, and each box turns the sum back into its
+ *                      local expansion. The log term of the multipole is added exactly. s = 57,
+ *                      73, 83, 88 for p <= 10, 20, 30, 60; the result differs from the dense form by
+ *                      about 1e-15 of the potential's scale.
+ * vfmm_ops_set_m2l changes the solve's workspace size (query vfmm_workspace_size again); a graph
+ * keeps the form it captured. Host-only; not while a solve with these operators is being launched.
+ * vfmm_ops_get_m2l returns the form and s (n_waves may be NULL). Errors: INVALID_ARG (null ops,
+ * unknown form, PLANEWAVE on a VFMM_MIXED operator set). */
+#define VFMM_M2L_DENSE 0
+#define VFMM_M2L_PLANEWAVE 1
+int vfmm_ops_set_m2l(vfmm_ops* ops, int32_t form);
+int vfmm_ops_get_m2l(const vfmm_ops* ops, int32_t* form, int32_t* n_waves);
+
 /* Device workspace the solve needs for this tree, operator set and nrhs
  * (multipole and local expansions, near-field partial products). with_io != 0
  * adds room for the device copies vfmm_volume_potential_host stages through.

@@ -11,6 +11,8 @@ from ._lib import c_double_p, c_int32_p, call
 
 FP64 = 0
 MIXED = 1
+M2L_DENSE = 0  # vfmm_ops_set_m2l forms
+M2L_PLANEWAVE = 1
 LISTS = {"U": 0, "V": 1, "W": 2, "X": 3}
 OP_IDS = {"near": 0, "s2m": 1, "s2l": 2, "m2m": 3, "l2l": 4, "m2l": 5}
 
@@ -234,6 +236,17 @@ class Ops:
         cur.update(counts)
         arr = np.array([cur[c] for c in self.CONTRACTIONS], dtype=np.int32)
         call("vfmm_ops_set_slices", self._h, arr.ctypes.data_as(c_int32_p))
+
+    @property
+    def m2l(self):
+        """(form, s): VFMM_M2L_DENSE or VFMM_M2L_PLANEWAVE and the plane-wave rule's length."""
+        form, s = ctypes.c_int32(), ctypes.c_int32()
+        call("vfmm_ops_get_m2l", self._h, ctypes.byref(form), ctypes.byref(s))
+        return form.value, s.value
+
+    def set_m2l(self, form):
+        """vfmm_ops_set_m2l: M2L_DENSE or M2L_PLANEWAVE (FP64 operator sets only)."""
+        call("vfmm_ops_set_m2l", self._h, int(form))
 
     def export(self, name):
         k, p = self.k, self.p

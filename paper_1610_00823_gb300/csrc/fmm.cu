@@ -562,6 +562,7 @@ struct DownArgs {
     const double* m2l_c0;  // Re of local coefficient 0 from the V and X lists, with the log(h) terms
     const double* vslab;   // FP64 form: [n_V][2(p+1)] M2L of every V entry
     const double* xslab;   // FP64 form: [n_X][2(p+1)] S2L of every X entry
+    const double* pwloc;   // FP64 form, plane-wave M2L: [n_boxes][2(p+1)] V-list locals (null: vslab)
     int lw;                 // root width = wm 2^lw, wm in [1, 2)
     double wm;
     const float2* s2l_out; // split-precision S2L rows 2..2p+1, scaled by 2^-(E_f + E_r)
@@ -587,9 +588,15 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
     if (!d.m2l_out && t < P) {
         // FP64 form: M2L and S2L rows from the per-entry slabs of the V and X GEMMs, in list order,
         // with the log(h) a_0 terms of the scaling
+        if (d.pwloc) {
+            re += d.pwloc[(size_t)b * 2 * P + 2 * t];
+            im += d.pwloc[(size_t)b * 2 * P + 2 * t + 1];
+        }
         for (int e = d.vptr[b]; e < d.vptr[b + 1]; ++e) {
-            re += d.vslab[(size_t)e * 2 * P + 2 * t];
-            im += d.vslab[(size_t)e * 2 * P + 2 * t + 1];
+            if (!d.pwloc) {
+                re += d.vslab[(size_t)e * 2 * P + 2 * t];
+                im += d.vslab[(size_t)e * 2 * P + 2 * t + 1];
+            }
             if (t == 0) re += d.Mexp[((size_t)d.vidx[e] * R + r) * 2 * P] * logh;
         }
         for (int e = d.xptr[b]; e < d.xptr[b + 1]; ++e) {
@@ -1137,6 +1144,8 @@ struct Workspace {
     bool fork = false;  // mixed form: run the near field and S2L on the thread's second stream
     double* vslab;      // FP64 form: per V entry M2L rows
     double* xslab;      // FP64 form: per X entry S2L rows
+    double* pwX;        // FP64 form, plane-wave M2L: [n_boxes][4][s] outgoing coefficients (null: dense)
+    double* pwL;        // FP64 form, plane-wave M2L: [n_boxes][2(p+1)] V-list local coefficients
     const PlanSet* ps;  // split-contraction plans for the folded right-hand sides (mixed form)
     unsigned int* ready; // [2][n_boxes * R] readiness counters of the persistent tree passes, then
                          // [(depth + 1) R] biased level exponents (mixed form)
@@ -1188,7 +1197,14 @@ static int layout(const DeviceTree& T, const vfmm_ops& o, int nrhs, bool io, Wor
     }
     take(w ? &w->slab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_U] * 3 * kk);
     take(w ? &w->far : &dummy, mixed ? 1 : (size_t)T.n_leaves * 3 * kk);
-    take(w ? &w->vslab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_V] * P2);
+    const bool pw = !mixed && o.m2l_form == VFMM_M2L_PLANEWAVE;
+    take(w ? &w->vslab : &dummy, mixed || pw ? 1 : (size_t)T.llen[VFMM_LIST_V] * P2);
+    if (pw) {
+        take(w ? &w->pwX : &dummy, planewave_work_doubles(T.n_boxes, o));
+        take(w ? &w->pwL : &dummy, (size_t)T.n_boxes * P2);
+    } else if (w) {
+        w->pwX = w->pwL = nullptr;
+    }
     take(w ? &w->xslab : &dummy, mixed ? 1 : (size_t)T.llen[VFMM_LIST_X] * P2);
     if (mixed) {
         const MixedOps* mo = (const MixedOps*)o.mixed;
@@ -1342,6 +1358,7 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     d.Lexp = w.Lexp;
     d.vslab = w.vslab;
     d.xslab = w.xslab;
+    d.pwloc = w.pwL;
     d.m2l_out = mo ? w.mix.m2l_out : nullptr;
     d.m2l_E = mo ? mo->m2l_E : nullptr;
     d.m2l_G = mo ? w.mix.glev : nullptr;
@@ -1580,7 +1597,15 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
     if (!mixed) {
         // FP64 form: every M2L (V list) and S2L (X list) product as gather GEMMs grouped by
         // configuration, one slab row per list entry; the per-level kernels below sum them
-        if (T.n_v_tiles > 0) {
+        if (w.pwX) {
+            // plane-wave form: outgoing waves of every box, then diagonal translations and the
+            // incoming conversion per target box
+            if (T.depth >= 2) {
+                launches += 2;
+                VFMM_CHECK(planewave_m2l(o, T.level_start[2], T.n_boxes, T.lptr[VFMM_LIST_V],
+                                         T.lidx[VFMM_LIST_V], T.lcfg[VFMM_LIST_V], w.Mexp, w.pwX, w.pwL, st));
+            }
+        } else if (T.n_v_tiles > 0) {
             ++launches;
             dim3 g(T.n_v_tiles, (P2 + GBM - 1) / GBM);
             v_gemm_kernel<<<g, 256, 0, st>>>((const int4*)T.v_tiles, o.m2l_real, P2, T.v_by_cfg,

@@ -25,10 +25,26 @@ struct vfmm_ops {
     double* s2l_real = nullptr;  // [20][2(p+1)][kk]
     // split-precision near-field operands (VFMM_MIXED)
     void* mixed = nullptr;
+    // plane-wave M2L (FP64 form, planewave.cu): rule length s, outgoing [p][s] lambda^(n-1)/(n-1)!,
+    // incoming [s][p+1] omega (-lambda)^l / l!, diagonal [40][s] e^(-lambda U0), log terms [40][p+1],
+    // side q of each V offset [40]
+    int m2l_form = VFMM_M2L_DENSE;
+    int pw_s = 0;
+    double* pw_C = nullptr;
+    double* pw_G = nullptr;
+    double2* pw_E = nullptr;
+    double2* pw_A0 = nullptr;
+    int32_t* pw_side = nullptr;
 };
 
 namespace vfmm {
 int mixed_prepare(vfmm_ops* o, cudaStream_t st);
 void mixed_free(vfmm_ops* o);
 void free_ops(vfmm_ops* o);
+int planewave_prepare(vfmm_ops* o, cudaStream_t st);
+void planewave_free(vfmm_ops* o);
+int pw_stride(int S);
+size_t planewave_work_doubles(int64_t n_boxes, const vfmm_ops& o);
+int planewave_m2l(const vfmm_ops& o, int begin, int n_boxes, const int32_t* vptr, const int32_t* vidx,
+                  const int32_t* vcfg, const double* Mexp, double* X, double* L, cudaStream_t st);
 }  // namespace vfmm

@@ -452,6 +452,7 @@ static int create(int k, int p, int precision, cudaStream_t st, vfmm_ops* o) {
                 }
         VFMM_CHECK(dalloc_copy(&o->m2l_real, mr, st));
         VFMM_CHECK(dalloc_copy(&o->s2l_real, sr, st));
+        VFMM_CHECK(planewave_prepare(o, st));
     }
     VFMM_CUDA(cudaStreamSynchronize(st));
     cudaFree(d_bw);
@@ -470,6 +471,7 @@ void free_ops(vfmm_ops* o) {
     for (double* p : ps)
         if (p) cudaFree(p);
     mixed_free(o);
+    planewave_free(o);
 }
 
 }  // namespace vfmm
