@@ -443,7 +443,11 @@ int vfmm_selftest_wait_timeout(int64_t polls, void* stream);
  * schedule holds both forms of a contraction (targets grouped, or one column per list entry with
  * a per-target sum) times both; keeps the fastest in the tree's schedule (used by every later
  * call with this nrhs) and returns the split-K factors in splits[4] (near, M2L, S2L, far; may be
- * NULL; 1 for the entry-major form, see vfmm_solve_work out[7]). Runs two ordinary solves around the timing, so
+ * NULL; 1 for the entry-major form, see vfmm_solve_work out[7]). Where the near field runs as one
+ * persistent CTA per SM and the tree passes are persistent, it then times the whole forked solve
+ * (near field beside the main chain, as vfmm_volume_potential and its graphs run it) with the near
+ * field capped at 8/8, 7/8, 6/8, 5/8 and 4/8 of the SMs and the tree passes' grids capped to the SMs left
+ * free, and keeps the fastest (out[8], out[9] of vfmm_solve_work). Runs two ordinary solves around the timing, so
  * u, u_x, u_y hold the solution afterwards; synchronises `stream`. Must not overlap other calls
  * on the same tree; graphs captured earlier keep the schedule they captured. No-op (splits = 1)
  * for VFMM_FP64. Errors as vfmm_volume_potential. */
@@ -459,9 +463,22 @@ int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const double* f_dev, i
  * [5] FP64-equivalent FLOPs of the near field, 2 * 3k^2 * k^2 per U-list entry and right-hand side,
  * [6] number of U-list entries, [7] which contractions run in the entry-major form (one column
  *     per list entry, summed per target afterwards): bit 0 near field, 1 M2L, 2 leaf far field,
- *     3 S2L. Host-only; no device work. */
-#define VFMM_N_WORK 8
+ *     3 S2L, [8] the near-field contraction's CTA cap (0: one CTA per work item), [9] the grid cap of
+ *     the persistent tree passes (0: one CTA per box of the widest level, at most one per SM).
+ *     Host-only; no device work. */
+#define VFMM_N_WORK 10
 int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32_t nrhs, double* out);
+
+/* Co-schedule of a VFMM_MIXED solve with nrhs right-hand sides on this tree (no counterpart in the
+ * paper): near_ctas caps the near-field contraction's grid (0: one CTA per work item; a positive
+ * cap makes its CTAs persistent, each walking several work items), pass_ctas caps the grid of the
+ * persistent tree passes (0: one CTA per box of the widest level, at most one per SM). vfmm_tune
+ * picks both by timing the forked solve; these calls read or override its choice (results do not
+ * depend on either: every work item is computed the same way whichever CTA takes it). The set call
+ * applies to later calls and graph captures; not while a solve on this tree is being launched.
+ * Host-only. Errors: INVALID_ARG (null pointers, nrhs < 1, a negative cap). */
+int vfmm_schedule_get(const vfmm_tree* tree, int32_t nrhs, int32_t* near_ctas, int32_t* pass_ctas);
+int vfmm_schedule_set(vfmm_tree* tree, int32_t nrhs, int32_t near_ctas, int32_t pass_ctas);
 
 /* Stage timers (tracing): the same solve as vfmm_volume_potential with CUDA events
  * recorded on `stream` between its stages; synchronises `stream` and returns the

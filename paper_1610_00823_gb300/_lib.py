@@ -66,6 +66,8 @@ EXPORTS = {
     "vfmm_ops_set_slices": [ctypes.c_void_p, c_int32_p],
     "vfmm_ops_get_slices": [ctypes.c_void_p, c_int32_p],
     "vfmm_ops_set_m2l": [ctypes.c_void_p, ctypes.c_int32],
+    "vfmm_schedule_get": [ctypes.c_void_p, ctypes.c_int32, c_int32_p, c_int32_p],
+    "vfmm_schedule_set": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
     "vfmm_ops_get_m2l": [ctypes.c_void_p, c_int32_p, c_int32_p],
     "vfmm_workspace_size": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                             ctypes.POINTER(ctypes.c_size_t)],

@@ -382,7 +382,19 @@ def tune(tree: Tree, ops: Ops, f, out, ws, stream=None):
 
 
 WORK = ("near_tc_flops", "m2l_tc_flops", "far_tc_flops", "s2l_tc_flops", "s2m_tc_flops", "near_fp64eq_flops",
-        "u_entries", "entry_major_mask")
+        "u_entries", "entry_major_mask", "near_ctas", "pass_ctas")
+
+
+def schedule(tree: Tree, nrhs: int = 1):
+    """vfmm_schedule_get: (near-field CTA cap, tree-pass grid cap) of the mixed solve's schedule."""
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    call("vfmm_schedule_get", tree.handle, int(nrhs), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def set_schedule(tree: Tree, near_ctas: int, pass_ctas: int, nrhs: int = 1):
+    """vfmm_schedule_set: override the tuner's co-schedule (0 = uncapped)."""
+    call("vfmm_schedule_set", tree.handle, int(nrhs), int(near_ctas), int(pass_ctas))
 
 
 def solve_work(tree: Tree, ops: Ops, nrhs: int = 1):

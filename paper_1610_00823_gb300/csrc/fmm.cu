@@ -1380,7 +1380,8 @@ static bool use_passes(const DeviceTree& T, int R, int P) {
 }
 
 template <typename... Args>
-static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, cudaStream_t st, Args... args) {
+static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, int cap, cudaStream_t st,
+                       Args... args) {
     const size_t smem = pass_smem_bytes(P);
     static thread_local int attr_dev[2] = {-1, -1};
     const int slot = (void*)kernel == (void*)upward_pass_kernel ? 0 : 1;
@@ -1398,7 +1399,8 @@ static int launch_pass(void (*kernel)(Args...), int R, int P, int widest_items, 
     // first boxes, so that they run on different SMs), at most one per SM and at most kPassMaxCtas:
     // a smaller grid starts sooner when another stream's kernels still hold SMs (the launch waits
     // until the whole grid fits).
-    const int grid = std::max(1, std::min(std::min(per_sm * sm_count(), kPassMaxCtas), widest_items));
+    int grid = std::max(1, std::min(std::min(per_sm * sm_count(), kPassMaxCtas), widest_items));
+    if (cap > 0) grid = std::min(grid, cap);  // any grid works: units wait only on lower-numbered units
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeCooperative;
     attr.val.cooperative = 1;
@@ -1547,7 +1549,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.glev = mixed ? w.mix.glev : nullptr;
         pa.level = T.level;
         pa.err = w.mix.err;
-        VFMM_CHECK(launch_pass(upward_pass_kernel, R, P, widest * R, st, pa));
+        VFMM_CHECK(launch_pass(upward_pass_kernel, R, P, widest * R, mixed ? PS.pass_ctas : 0, st, pa));
         ++launches;
     } else {
         for (int l = T.depth - 1; l >= 2; --l) {
@@ -1637,7 +1639,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         pa.glev = nullptr;
         pa.level = T.level;
         pa.err = w.mix.err;
-        VFMM_CHECK(launch_pass(downward_pass_kernel, R, P, std::max(widest * R, 16 * R), st, pa, d));
+        VFMM_CHECK(launch_pass(downward_pass_kernel, R, P, std::max(widest * R, 16 * R), PS.pass_ctas, st, pa, d));
         ++launches;
     }
     for (int l = 2; l <= T.depth && !(mixed && passes); ++l) {
@@ -2093,6 +2095,46 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
         if (rc == VFMM_OK) time_ctas(jb, jb.P, part);
         if (splits) splits[j] = jb.P->split;
     }
+    // Co-scheduling of the whole step: in a forked solve the near field (low-priority stream) and the
+    // main chain share the SMs, and a near-field CTA leaves no registers for anything else on its SM.
+    // Timed on the forked solve itself: the near field on every SM, or capped at 7/8 ... 4/8 of them,
+    // the cooperative tree passes capped to the SMs it leaves free (they can start only when their
+    // whole grid fits); the fastest is kept (the uncapped schedule unless a cap is faster).
+    if (rc == VFMM_OK && PS->near.n_groups > 0 && PS->near.ctas > 0 && use_passes(T, PS->R, ops->p + 1)) {
+        const int sms = sm_count();
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, upward_pass_kernel, kPassThreads, pass_smem_bytes(ops->p + 1));
+        Workspace wf = w;
+        wf.fork = true;
+        const int near0 = PS->near.ctas, pass0 = PS->pass_ctas;
+        float best = -1.0f;
+        int best_near = near0, best_pass = pass0;
+        const int fracs[5] = {8, 7, 6, 5, 4};  // eighths of the SMs
+        for (int c = 0; c < 5 && rc == VFMM_OK; ++c) {
+            const int ncta = fracs[c] == 8 ? near0 : std::max(1, sms * fracs[c] / 8);
+            PS->near.ctas = ncta;
+            PS->pass_ctas = fracs[c] == 8 ? pass0 : std::max(1, per_sm * (sms - ncta));
+            float total = 0.0f;
+            for (int rep = 0; rep < 6 && rc == VFMM_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                rc = solve_all(T, *ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, wf, st);
+                cudaEventRecord(e1, st);
+                if (rc != VFMM_OK) break;
+                cudaError_t e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) rc = cuda_fail(e, "timing a forked solve");
+                if (rep > 0) total += ms;  // the first run warms up
+            }
+            if (rc == VFMM_OK && (best < 0.0f || total < best)) {
+                best = total;
+                best_near = PS->near.ctas;
+                best_pass = PS->pass_ctas;
+            }
+        }
+        PS->near.ctas = best_near;
+        PS->pass_ctas = best_pass;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     VFMM_CHECK(rc);
@@ -2100,4 +2142,23 @@ extern "C" int vfmm_tune(const vfmm_tree* tree, const vfmm_ops* ops, const doubl
     VFMM_CHECK(solve_all(T, *ops, f_dev, nrhs, u_dev, ux_dev, uy_dev, w, st));
     VFMM_CUDA(cudaStreamSynchronize(st));
     return read_status(w);
+}
+
+extern "C" int vfmm_schedule_get(const vfmm_tree* tree, int32_t nrhs, int32_t* near_ctas, int32_t* pass_ctas) {
+    if (!tree || !near_ctas || !pass_ctas || nrhs < 1) return fail(VFMM_ERR_INVALID_ARG, "bad schedule query");
+    const PlanSet* PS = nullptr;
+    VFMM_CHECK(plans_for(tree->t, nrhs, &PS));
+    *near_ctas = PS->near.ctas;
+    *pass_ctas = PS->pass_ctas;
+    return VFMM_OK;
+}
+
+extern "C" int vfmm_schedule_set(vfmm_tree* tree, int32_t nrhs, int32_t near_ctas, int32_t pass_ctas) {
+    if (!tree || nrhs < 1 || near_ctas < 0 || pass_ctas < 0) return fail(VFMM_ERR_INVALID_ARG, "bad schedule");
+    const PlanSet* PS = nullptr;
+    VFMM_CHECK(plans_for(tree->t, nrhs, &PS));
+    PlanSet* ps = const_cast<PlanSet*>(PS);
+    ps->near.ctas = near_ctas;
+    ps->pass_ctas = pass_ctas;
+    return VFMM_OK;
 }

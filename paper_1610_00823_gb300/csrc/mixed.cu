@@ -85,14 +85,22 @@ __global__ void table_slice_kernel(const double* __restrict__ T, int R, int kk, 
     }
 }
 
-// out[r] = max |f| of right-hand side r (bits of the double; grid.y = r).
-__global__ void fmax_abs_kernel(const double* __restrict__ f, int64_t n, unsigned long long* __restrict__ out) {
+// out[r] = max |f| of right-hand side r (bits of the double; grid.y = r). Warp and CTA maxima first,
+// then one atomic per CTA (the atomics on one address serialise in L2).
+__global__ void __launch_bounds__(256) fmax_abs_kernel(const double* __restrict__ f, int64_t n,
+                                                       unsigned long long* __restrict__ out) {
+    __shared__ double red[8];
     const double* fr = f + (size_t)blockIdx.y * n;
     double m = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         m = fmax(m, fabs(fr[i]));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(m));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        atomicMax(out + blockIdx.y, (unsigned long long)__double_as_longlong(m));
+    }
 }
 
 // fsl[leaf * R + r][i][k] from f_r[leaf][k] / 2^E_f[r]; also stores E_f[r]. One thread per 8
@@ -924,13 +932,26 @@ int plans_for(const DeviceTree& T, int R, const PlanSet** out) {
     return VFMM_OK;
 }
 
+static int fmax_sms() {
+    static thread_local int dev = -1, n = 0;
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d != dev) {
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+        dev = d;
+    }
+    return n > 0 ? n : 1;
+}
+
 int near_slices(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, const MixedWork& w,
                 cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     const int kk = o.k * o.k, R = PS.R;
     VFMM_CUDA(cudaMemsetAsync(w.fmax, 0, (size_t)R * sizeof(unsigned long long), st));
     const int64_t n = (int64_t)T.n_leaves * kk;
-    fmax_abs_kernel<<<dim3((unsigned)std::min<int64_t>(1024, (n + 255) / 256), R), 256, 0, st>>>(f, n, w.fmax);
+    // two CTAs per SM, each thread a few values: a few hundred atomics instead of one per warp
+    const int64_t fm_ctas = std::min<int64_t>(2 * (int64_t)fmax_sms(), (n + 255) / 256);
+    fmax_abs_kernel<<<dim3((unsigned)std::max<int64_t>(1, fm_ctas), R), 256, 0, st>>>(f, n, w.fmax);
     const int64_t nchunk = (int64_t)T.n_leaves * R * (mo->Kp / 8);
     f_slice_kernel<<<(unsigned)((nchunk + 255) / 256), 256, 0, st>>>(f, T.n_leaves, kk, mo->Kp, R, w.fmax, w.Ef,
                                                                      (bf16*)w.fsl);

@@ -556,6 +556,8 @@ extern "C" int vfmm_solve_work(const vfmm_tree* tree, const vfmm_ops* ops, int32
     out[3] = tc(PS->s2l, mo->Kp, mo->Rx, kCtrS2L);
     out[4] = tc(PS->s2m, mo->Kp, mo->Rx, kCtrS2M);
     out[7] = (PS->near.entry ? 1 : 0) + (PS->m2l.entry ? 2 : 0) + (PS->far.entry ? 4 : 0) + (PS->s2l.entry ? 8 : 0);
+    out[8] = PS->near.ctas;
+    out[9] = PS->pass_ctas;
     return VFMM_OK;
 }
 

@@ -66,21 +66,27 @@ __global__ void __launch_bounds__(32 * kPwWarps) pw_out_kernel(int begin, int en
     for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int t = 0; t < 3; ++t) xr[q][t] = xi[q][t] = 0.0;
-    for (int n = 1; n < P; ++n) {
-        const double2 an = a[n];
-        double c[3];
+    // n in steps of 4 from 1, so that every rotation (q n) mod 4 is known at compile time
+    for (int n0 = 1; n0 < P; n0 += 4) {
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int j = lane + 32 * t;
-            c[t] = j < S ? C[(size_t)(n - 1) * S + j] : 0.0;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const double2 r = rot_mi(an, (q * n) & 3);  // d_q^-n = (-i)^(q n)
+        for (int dn = 0; dn < 4; ++dn) {
+            const int n = n0 + dn;
+            if (n >= P) break;
+            const double2 an = a[n];
+            double c[3];
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
-                xr[q][t] = fma(c[t], r.x, xr[q][t]);
-                xi[q][t] = fma(c[t], r.y, xi[q][t]);
+                const int j = lane + 32 * t;
+                c[t] = j < S ? C[(size_t)(n - 1) * S + j] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double2 r = rot_mi(an, (q * (1 + dn)) & 3);  // d_q^-n = (-i)^(q n), n = 1 + dn mod 4
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    xr[q][t] = fma(c[t], r.x, xr[q][t]);
+                    xi[q][t] = fma(c[t], r.y, xi[q][t]);
+                }
             }
         }
     }
@@ -113,46 +119,46 @@ __global__ void __launch_bounds__(32 * kPwWarps) pw_in_kernel(int begin, int end
     if (b >= end) return;
     double2* Z = reinterpret_cast<double2*>(pw_raw) + (size_t)warp * 4 * Sp;
     const int e0 = vptr[b], e1 = vptr[b + 1];
-    double yr[4][3], yi[4][3];
+    // one pass over the V list per side q: Y_q[j] = sum e^(-lambda_j U0) X_q(c)[j] in registers, then
+    // folded into the four phases Z_r[j] = sum_q d_q^-r Y_q[j] (r = l mod 4)
+    double zr[4][3], zi[4][3];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int t = 0; t < 3; ++t) yr[q][t] = yi[q][t] = 0.0;
-    for (int e = e0; e < e1; ++e) {
-        const int c = vidx[e], cf = vcfg[e];
-        const int q = side[cf];
+        for (int t = 0; t < 3; ++t) zr[r][t] = zi[r][t] = 0.0;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int j = lane + 32 * t;
-            if (j < S) {
-                const double2 ex = E[(size_t)cf * S + j];
-                const double2 x = X[((size_t)c * 4 + q) * S + j];
-                const double pr = ex.x * x.x - ex.y * x.y, pi = ex.x * x.y + ex.y * x.x;
+    for (int q = 0; q < 4; ++q) {
+        double yr[3] = {0.0, 0.0, 0.0}, yi[3] = {0.0, 0.0, 0.0};
+        for (int e = e0; e < e1; ++e) {
+            const int cf = vcfg[e];
+            if (side[cf] != q) continue;
+            const size_t xo = ((size_t)vidx[e] * 4 + q) * S;
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq)
-                    if (qq == q) {
-                        yr[qq][t] += pr;
-                        yi[qq][t] += pi;
-                    }
+            for (int t = 0; t < 3; ++t) {
+                const int j = lane + 32 * t;
+                if (j < S) {
+                    const double2 ex = E[(size_t)cf * S + j];
+                    const double2 x = X[xo + j];
+                    yr[t] = fma(ex.x, x.x, fma(-ex.y, x.y, yr[t]));
+                    yi[t] = fma(ex.x, x.y, fma(ex.y, x.x, yi[t]));
+                }
             }
         }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const double2 v = rot_mi(make_double2(yr[t], yi[t]), (q * r) & 3);
+                zr[r][t] += v.x;
+                zi[r][t] += v.y;
+            }
     }
-    // Z_r[j] = sum_q d_q^-r Y_q[j], r = l mod 4
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             const int j = lane + 32 * t;
-            if (j < S) {
-                double zr = 0.0, zi = 0.0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const double2 v = rot_mi(make_double2(yr[q][t], yi[q][t]), (q * r) & 3);
-                    zr += v.x;
-                    zi += v.y;
-                }
-                Z[r * Sp + j] = make_double2(zr, zi);
-            }
+            if (j < S) Z[r * Sp + j] = make_double2(zr[r][t], zi[r][t]);
         }
     __syncwarp();
     for (int l = lane; l < P; l += 32) {

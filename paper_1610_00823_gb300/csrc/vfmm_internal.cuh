@@ -193,6 +193,9 @@ struct PlanSet {
     SplitPlan m2l;   // V list: targets boxes, tables the 40 offsets, A rows boxes
     SplitPlan far;   // L2T + W list: targets leaves, tables 0 (L2T) and 1 + W configuration, A rows far slots
     SplitPlan s2l;   // X list: targets boxes, tables 20 configurations, A rows leaves
+    // grid cap of the persistent tree passes (0: one CTA per box of the widest level, at most one per
+    // SM); with a capped near field the passes then fit on the SMs the near field leaves free
+    int32_t pass_ctas = 0;
     void* arena = nullptr;  // one device allocation holding every index array of the plans above
 };
 

@@ -216,6 +216,39 @@ def test_autotuned_schedule_keeps_results():
         assert rel(again[q].cpu().numpy(), u64[q].cpu().numpy()) < TOL
 
 
+def test_co_schedule_caps_keep_results_bit_identical():
+    """The near-field CTA cap and the tree-pass grid cap (vfmm_schedule_set, chosen by vfmm_tune's
+    whole-step timing) only change which CTA takes which work item: forked solves under any caps,
+    captured or not, equal the uncapped one-stream solve bit for bit."""
+    from paper_1610_00823_gb300.api import SolveGraph, schedule, set_schedule
+    src = W.narrow_gaussians(8, n=2, sigma=0.01, spread=0.4)
+    gt = v.tree_build(0.0, 0.0, 1.0, 16, src, 1e-10, 9)
+    f = v.source_sample(gt, src)
+    ops = v.ops_create(16, 40, v.MIXED)
+    ws = workspace(gt, ops, 1)
+    set_schedule(gt, 0, 0)
+    assert schedule(gt) == (0, 0)
+    ref = tuple(torch.full_like(f, float("nan")) for _ in range(3))
+    volume_potential_profiled(gt, ops, f, ref, ws)
+    torch.cuda.synchronize()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for near, passes in [(sms, 0), (sms * 5 // 8, sms * 3 // 8), (sms // 2, 7), (1, 1)]:
+        set_schedule(gt, near, passes)
+        assert schedule(gt) == (near, passes)
+        got = v.volume_potential(gt, ops, f)
+        stream = torch.cuda.Stream()
+        out = tuple(torch.full_like(f, float("nan")) for _ in range(3))
+        g = SolveGraph(gt, ops, f, out, workspace(gt, ops, 1), stream)
+        g.launch(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        for q in range(3):
+            assert torch.equal(got[q], ref[q]), (near, passes, q)
+            assert torch.equal(out[q], ref[q]), (near, passes, q)
+    with pytest.raises(RuntimeError):
+        set_schedule(gt, -1, 0)
+
+
 def test_bounded_wait_reports_timeout_and_context_survives():
     """The failure path of the tensor-core kernels: a bounded wait that runs out (an mbarrier that
     nothing arrives on) is reported as VFMM_ERR_TIMEOUT, and the GPU context stays usable."""
