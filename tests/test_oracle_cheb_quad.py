@@ -139,6 +139,104 @@ def test_box_integrals_single_basis_vs_adaptive_quadpack():
             assert abs(G[q] - ref) < 1e-10, (x, s, q, G[q], ref)
 
 
+# ---- Green's second identity: an independent route to single-basis box integrals
+def _pmul(a, b):
+    out = {}
+    for (i, j), c in a.items():
+        for (k, l), d in b.items():
+            out[(i + k, j + l)] = out.get((i + k, j + l), 0) + c * d
+    return out
+
+
+def _lagrange_poly(mp, k, i, axis):
+    """Monomial coefficients {(a, b): c} of the 1-D Lagrange basis l_i on first-kind nodes, in y1 or y2."""
+    nodes = [-mp.cos(mp.pi * (2 * m + 1) / (2 * k)) / 2 for m in range(k)]
+    p = {(0, 0): mp.mpf(1)}
+    for m in range(k):
+        if m != i:
+            den = nodes[i] - nodes[m]
+            p = _pmul(p, {((1, 0) if axis == 0 else (0, 1)): 1 / den, (0, 0): -nodes[m] / den})
+    return p
+
+
+def _pdiff(p, axis):
+    out = {}
+    for (a, b), c in p.items():
+        e = a if axis == 0 else b
+        if e > 0:
+            key = (a - 1, b) if axis == 0 else (a, b - 1)
+            out[key] = out.get(key, 0) + e * c
+    return out
+
+
+def _inverse_laplacian(mp, p):
+    """A polynomial q with q_11 + q_22 = p: q = sum_m (-1)^m (d1^-2)^(m+1) d2^(2m) p (the series stops)."""
+    out = {}
+    for (a, b), c in p.items():
+        m = 0
+        while 2 * m <= b:
+            f = mp.factorial(a) / mp.factorial(a + 2 * m + 2) * mp.factorial(b) / mp.factorial(b - 2 * m)
+            key = (a + 2 * m + 2, b - 2 * m)
+            out[key] = out.get(key, 0) + (-1) ** m * f * c
+            m += 1
+    return out
+
+
+def _green_box(mp, p, x):
+    """int_B -(1/2 pi) log|x - y| p(y) dy on B = [-1/2, 1/2]^2 (x off the boundary) by Green's second
+    identity: -q(x) [x in B] + sum over the edges of int (G dq/dn - q dG/dn) ds, Laplacian q = p; the
+    edge integrals by tanh-sinh, split where x projects onto the edge."""
+    q = _inverse_laplacian(mp, p)
+    dq = (_pdiff(q, 0), _pdiff(q, 1))
+    ev = lambda poly, y1, y2: mp.fsum(c * y1 ** a * y2 ** b for (a, b), c in poly.items())  # noqa: E731
+    x1, x2 = mp.mpf(x[0]), mp.mpf(x[1])
+    total = -ev(q, x1, x2) if (abs(x1) < 0.5 and abs(x2) < 0.5) else mp.mpf(0)
+    for ax in (0, 1):
+        for val, sgn in ((mp.mpf(0.5), 1), (mp.mpf(-0.5), -1)):
+            def f(s):
+                y1, y2 = (val, s) if ax == 0 else (s, val)
+                r1, r2 = x1 - y1, x2 - y2
+                rr = r1 * r1 + r2 * r2
+                return (-mp.log(rr) / (4 * mp.pi) * sgn * ev(dq[ax], y1, y2)
+                        - ev(q, y1, y2) * sgn * (r1 if ax == 0 else r2) / (2 * mp.pi * rr))
+            proj = x2 if ax == 0 else x1
+            total += mp.quad(f, [mp.mpf(-0.5)] + ([proj] if abs(proj) < 0.5 else []) + [mp.mpf(0.5)])
+    return total
+
+
+def _green_box_gradient(mp, p, x, axis):
+    """d/dx_axis of the same integral: V[dp/dy_axis](x) - int_dB G p n_axis ds (integration by parts)."""
+    g = _green_box(mp, _pdiff(p, axis), x)
+    ev = lambda poly, y1, y2: mp.fsum(c * y1 ** a * y2 ** b for (a, b), c in poly.items())  # noqa: E731
+    x1, x2 = mp.mpf(x[0]), mp.mpf(x[1])
+    for val, sgn in ((mp.mpf(0.5), 1), (mp.mpf(-0.5), -1)):
+        def f(s):
+            y1, y2 = (val, s) if axis == 0 else (s, val)
+            return -mp.log((x1 - y1) ** 2 + (x2 - y2) ** 2) / (4 * mp.pi) * ev(p, y1, y2) * sgn
+        proj = x2 if axis == 0 else x1
+        g -= mp.quad(f, [mp.mpf(-0.5)] + ([proj] if abs(proj) < 0.5 else []) + [mp.mpf(0.5)])
+    return g
+
+
+def test_box_integrals_single_basis_vs_greens_identity():
+    """Single tensor Lagrange basis functions (k = 6) against Green's second identity in 30-digit
+    arithmetic: the area integral of the log kernel becomes a polynomial value plus edge integrals,
+    an independent route (no area quadrature, no product weights). Targets inside the box (nodes
+    and a non-node point), 0.02 outside an edge, and far; potential and both gradient components."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    k = 6
+    xs = cheb.nodes(k)
+    cases = [(np.array([xs[1], xs[4]]), 7), (np.array([xs[0], xs[0]]), 0), (np.array([0.0, 0.25]), 14),
+             (np.array([0.5 + 0.02, xs[2]]), 20), (np.array([1.3, 0.9]), 35)]
+    for x, s in cases:
+        G = quad.box_integrals(x[None, :], np.array([0.0, 0.0]), 1.0, k)[:, 0, s]
+        p = _pmul(_lagrange_poly(mp, k, s % k, 0), _lagrange_poly(mp, k, s // k, 1))
+        ref = [_green_box(mp, p, x), _green_box_gradient(mp, p, x, 0), _green_box_gradient(mp, p, x, 1)]
+        for q in range(3):
+            assert abs(G[q] - float(ref[q])) < 1e-15, (x, s, q, G[q], float(ref[q]))
+
+
 def test_box_integrals_on_the_boundary_of_the_source_box():
     """Targets on an edge or a corner of the source box (a point on an edge shared by two leaves):
     the potential and its gradient are continuous there; f = 1 against the antiderivative (at the
