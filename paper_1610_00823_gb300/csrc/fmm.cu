@@ -986,8 +986,24 @@ struct LeafMixedArgs {
     const float2* farmix;
     const int* farE;
     const int* Et;
+    // entry-major near field / leaf far field: the slab rows of every leaf's entries, summed here in
+    // entry order (the arithmetic of the separate segmented sum, which these contractions then skip);
+    // null: nearmix / farmix hold the sums
+    const float2* near_slab;
+    const int32_t* near_seg;  // [n_leaves + 1] first entry of each leaf
+    const float2* far_slab;
+    const int32_t* far_seg;
     double *u, *ux, *uy;
 };
+
+// Sum of the slab rows of entries [e0, e1), right-hand side r, row `row` (double-float, entry order).
+__device__ __forceinline__ float2 slab_sum(const float2* __restrict__ slab, int e0, int e1, int R, int r, int Rp,
+                                           int row) {
+    float hi = 0.0f, lo = 0.0f;
+#pragma unroll 4
+    for (int e = e0; e < e1; ++e) df_add(hi, lo, slab[((size_t)e * R + r) * Rp + row]);
+    return df_final(hi, lo);
+}
 
 __global__ void leaf_mixed_kernel(LeafMixedArgs a) {
     // width = wm 2^lw with wm in [1, 2): h = wm 2^(lw - lv), so every power-of-two scale is folded
@@ -1025,8 +1041,27 @@ __global__ void leaf_mixed_kernel(LeafMixedArgs a) {
     const float2* nm = nearmix + (size_t)vl * Rp;
     const float2* fm = farmix + (size_t)vl * Rp;
     const int en = Ef[r] + lw - lv, ef = Et[vl] + lv - lw;  // near scale h 2^E_f, far scale 2^E_t / h
-    const float2 v0 = nm[t], v1 = nm[kk + t], v2 = nm[2 * kk + t];
-    const float2 w0 = fm[t], w1 = fm[kk + t], w2 = fm[2 * kk + t];
+    float2 v0, v1, v2, w0, w1, w2;
+    if (a.near_slab) {
+        const int s0 = a.near_seg[leaf], s1 = a.near_seg[leaf + 1];
+        v0 = slab_sum(a.near_slab, s0, s1, R, r, Rp, t);
+        v1 = slab_sum(a.near_slab, s0, s1, R, r, Rp, kk + t);
+        v2 = slab_sum(a.near_slab, s0, s1, R, r, Rp, 2 * kk + t);
+    } else {
+        v0 = nm[t];
+        v1 = nm[kk + t];
+        v2 = nm[2 * kk + t];
+    }
+    if (a.far_slab) {
+        const int s0 = a.far_seg[leaf], s1 = a.far_seg[leaf + 1];
+        w0 = slab_sum(a.far_slab, s0, s1, R, r, Rp, t);
+        w1 = slab_sum(a.far_slab, s0, s1, R, r, Rp, kk + t);
+        w2 = slab_sum(a.far_slab, s0, s1, R, r, Rp, 2 * kk + t);
+    } else {
+        w0 = fm[t];
+        w1 = fm[kk + t];
+        w2 = fm[2 * kk + t];
+    }
     const int e0 = en + lw - lv + Er[t], e1 = en + Er[kk + t], e2 = en + Er[2 * kk + t];
     double n0 = f2d_scaled(v0.x, e0) + f2d_scaled(v0.y, e0);  // h^2 x near u
     double n1 = f2d_scaled(v1.x, e1) + f2d_scaled(v1.y, e1);  // h x near u_x
@@ -1734,6 +1769,12 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
         la.farmix = w.mix.far_out;
         la.farE = mo->far_E;
         la.Et = w.mix.Et;
+        // an entry-major leaf far field leaves its per-leaf sums (a few entries per leaf) to this kernel;
+        // the near field (about nine entries per leaf, on the side stream) keeps its segmented-sum kernel
+        la.near_slab = nullptr;
+        la.near_seg = nullptr;
+        la.far_slab = PS.far.entry ? w.mix.part : nullptr;
+        la.far_seg = PS.far.entry ? PS.far.seg : nullptr;
         la.u = u;
         la.ux = ux;
         la.uy = uy;

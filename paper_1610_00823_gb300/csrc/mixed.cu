@@ -131,11 +131,6 @@ __device__ __forceinline__ void named_bar_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
 
 struct SplitArgs {
     const bf16* asl;      // A rows [rows][Kp / 32][kSlices][32]; the tables come through the tensor map
@@ -727,19 +722,6 @@ static int launch_split_n(int n, const SplitArgs& a, const CUtensorMap& bmap, in
     return n == kTileNSmall ? launch_split<kTileNSmall>(a, bmap, grid, st) : launch_split<kTileN>(a, bmap, grid, st);
 }
 
-// (hi, lo) += v in double-float with exact two-sums; df_final renormalises.
-__device__ __forceinline__ void df_add(float& hi, float& lo, float2 v) {
-    float s1, e1, s2, e2;
-    two_sum(hi, v.x, s1, e1);
-    two_sum(s1, v.y, s2, e2);
-    hi = s2;
-    lo = __fadd_rn(lo, __fadd_rn(e1, e2));
-}
-
-__device__ __forceinline__ float2 df_final(float hi, float lo) {
-    const float h = __fadd_rn(hi, lo);
-    return make_float2(h, __fsub_rn(lo, __fsub_rn(h, hi)));
-}
 
 // Entry-major contraction: output row of target t (right-hand side r) = sum of the slab rows of
 // its entries, in entry order (double-float); one thread per (target, r, row).
@@ -770,7 +752,7 @@ __global__ void split_reduce_kernel(const float2* __restrict__ part, size_t stri
 }
 
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
-               float2* part, size_t n_out_rows, int slices, cudaStream_t st, cudaEvent_t* ev) {
+               float2* part, size_t n_out_rows, int slices, cudaStream_t st, cudaEvent_t* ev, bool defer_segments) {
     if (slices < kMinSlices || slices > kSlices) return fail(VFMM_ERR_INTERNAL, "slice count out of range");
     if (ev) VFMM_CUDA(cudaEventRecord(ev[0], st));
     if (P.n_groups == 0) {
@@ -805,7 +787,8 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
         a.out = part;
         a.n_items = P.n_groups * a.nchunks;
         VFMM_CHECK(launch_split_n(n_mma, a, bmap, P.ctas > 0 ? std::min(P.ctas, a.n_items) : a.n_items, st));
-        const int64_t n = (int64_t)P.n_seg * P.R * Rp;
+        // with defer_segments the consumer sums each target's slab rows itself (same order)
+        const int64_t n = defer_segments ? 0 : (int64_t)P.n_seg * P.R * Rp;
         if (n > 0)
             segment_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, P.seg, P.seg_out, P.n_seg, P.R,
                                                                                 Rp, out);

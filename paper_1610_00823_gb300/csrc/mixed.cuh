@@ -134,6 +134,19 @@ __device__ __forceinline__ void level_exp_max(int e, unsigned* slot) {
     if ((threadIdx.x & 31) == 0 && e != INT_MIN) atomicMax(slot, (unsigned)(e + (int)kGexpBias));
 }
 
+// Block-wide maximum of e, then one atomicMax by thread 0 (every thread of the block must call it;
+// at most 32 warps).
+__device__ __forceinline__ void level_exp_max_block(int e, unsigned* slot) {
+    __shared__ int wmax[32];
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)((blockDim.x + 31) >> 5); ++w) e = max(e, wmax[w]);
+        if (e != INT_MIN) atomicMax(slot, (unsigned)(e + (int)kGexpBias));
+    }
+}
+
 // Level exponent from its biased form.
 __device__ __forceinline__ int level_exp_value(unsigned g) { return g ? (int)g - (int)kGexpBias : 0; }
 
@@ -176,6 +189,27 @@ struct MixedOps {
     // workloads, 17x below 1e-10 (7 for all: 6e-14)
     int slices[kNumCtr] = {6, 6, 6, 6, 6};
 };
+
+// s + e = a + b exactly (FP32, round to nearest).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += v in double-float with exact two-sums; df_final renormalises.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float2 v) {
+    float s1, e1, s2, e2;
+    two_sum(hi, v.x, s1, e1);
+    two_sum(s1, v.y, s2, e2);
+    hi = s2;
+    lo = __fadd_rn(lo, __fadd_rn(e1, e2));
+}
+
+__device__ __forceinline__ float2 df_final(float hi, float lo) {
+    const float h = __fadd_rn(hi, lo);
+    return make_float2(h, __fsub_rn(lo, __fsub_rn(h, hi)));
+}
 
 struct MixedWork {
     void* fsl = nullptr;                  // bf16 [n_leaves][kSlices][Kp]
@@ -247,7 +281,8 @@ int build_contraction_plan(const PlanItems& I, int n_tables, int n_chunks, int R
 int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtensorMap* out);
 // ev (optional): a (start, stop) event pair recorded around the contraction and its reduction.
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
-               float2* part, size_t n_out_rows, int slices, cudaStream_t st, cudaEvent_t* ev = nullptr);
+               float2* part, size_t n_out_rows, int slices, cudaStream_t st, cudaEvent_t* ev = nullptr,
+               bool defer_segments = false);
 // Partial-sum elements (float2) of the three buffers whose contractions may run at the same time:
 // [0] S2M, M2L and the leaf far field (one after another), [1] the near field, [2] S2L.
 void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t elems[3]);

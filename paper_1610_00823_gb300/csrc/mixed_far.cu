@@ -397,7 +397,8 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
         M[2 + q] = wm == 1.0 ? m : wm * wm * m;
         e = max(e, part_exp(M[2 + q], 2 + q));
     }
-    if (level[b] >= 2) level_exp_max(e, glev + (size_t)level[b] * R + r);
+    // one atomic per CTA (the level slots are few and shared by every leaf of a level)
+    if (level[b] >= 2) level_exp_max_block(e, glev + (size_t)level[b] * R + r);
 }
 
 int s2m_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const double* f, double* Mexp,
@@ -525,7 +526,7 @@ int far_leaf_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, co
                                                           Lexp, w.Et, (bf16*)w.aprep);
     VFMM_CUDA(cudaGetLastError());
     return split_gemm(PS.far, w.aprep, mo->tm_far, mo->Kx, mo->Rp, w.far_out, w.err, w.part,
-                      (size_t)T.n_leaves * PS.R, mo->slices[kCtrFar], st, w.cev ? w.cev + 8 : nullptr);
+                      (size_t)T.n_leaves * PS.R, mo->slices[kCtrFar], st, w.cev ? w.cev + 8 : nullptr, true);
 }
 
 }  // namespace vfmm
