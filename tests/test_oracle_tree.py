@@ -108,6 +108,46 @@ def test_refinement_decisions_follow_tail_test():
     assert info["min_margin"] > 1e-9
 
 
+def _tail_by_vandermonde(vals, k):
+    """Trailing-coefficient indicator by an independent route: the 2-D Chebyshev coefficients as the
+    solution of the interpolation (Vandermonde) system on the nodes, numpy's chebvander, instead of
+    the discrete orthogonality of the oracle's transform."""
+    t = np.sin(0.5 * np.pi / k * np.arange(-k + 1, k + 1, 2))  # first-kind points, ascending
+    Vinv = np.linalg.inv(np.polynomial.chebyshev.chebvander(t, k - 1))  # coefficients = Vinv @ values
+    coef = np.einsum("mj,bji,ni->bmn", Vinv, vals, Vinv)
+    mask = np.zeros((k, k), dtype=bool)
+    mask[k - 2:, :] = True
+    mask[:, k - 2:] = True
+    return np.max(np.abs(coef[:, mask]), axis=-1)
+
+
+@pytest.mark.parametrize("k,tol,depth,min_depth", [(8, 1e-5, 6, 0), (6, 1e-4, 7, 2)])
+def test_refinement_decisions_against_an_independent_tail(k, tol, depth, min_depth):
+    """Every box of the refinement (before balancing) below max_depth was split exactly when its tail,
+    computed by the Vandermonde route and compared with tol times max |f| over the uniform level-5
+    nodes (the F of the tolerance rule, Section 6.1), exceeds the threshold."""
+    src = W.narrow_gaussians(5, n=3, sigma=0.04)
+    t, info = T.build_adaptive(0, 0, 1, k, src, tol, depth, min_depth, return_info=True)
+    assert info["min_margin"] > 1e-9
+    m = min(5, depth)
+    xs = np.sin(0.5 * np.pi / k * np.arange(-k + 1, k + 1, 2)) / 2  # nodes on [-1/2, 1/2]
+    g = ((np.arange(1 << m)[:, None] + 0.5 + xs[None, :]) / (1 << m) - 0.5).reshape(-1)
+    F = np.max(np.abs(source.evaluate_source(src, *np.meshgrid(g, g, indexing="xy"))))
+    assert abs(F - info["F"]) <= 1e-15 * F
+    boxes = sorted(b for b in info["refined"] if min_depth <= b[0] < depth)
+    lv = np.array([b[0] for b in boxes])
+    ix = np.array([b[1] for b in boxes])
+    iy = np.array([b[2] for b in boxes])
+    h = 1.0 / (1 << lv)
+    X = (-0.5 + (ix + 0.5)[:, None, None] * h[:, None, None] + xs[None, None, :] * h[:, None, None])
+    Y = (-0.5 + (iy + 0.5)[:, None, None] * h[:, None, None] + xs[None, :, None] * h[:, None, None])
+    X, Y = np.broadcast_to(X, (len(boxes), k, k)), np.broadcast_to(Y, (len(boxes), k, k))
+    tl = _tail_by_vandermonde(source.evaluate_source(src, X, Y), k)
+    split = np.array([(b[0] + 1, 2 * b[1], 2 * b[2]) in info["refined"] for b in boxes])
+    assert split.any() and (~split).any()
+    assert np.array_equal(split, tl > tol * F)
+
+
 def test_kinked_source_zero_set_is_the_curve():
     wl = W.kinked()
     prm = wl.sources[0].params
