@@ -1016,6 +1016,55 @@ __global__ void leaf_mixed_kernel(LeafMixedArgs a) {
     const unsigned leaf = vl / (unsigned)R, r = vl - leaf * (unsigned)R;
     const int b = a.box_of_leaf[leaf];
     const int lv = a.level[b];
+    // the node values first (their loads overlap the first warp's scalar sums), then the barrier
+    double n0 = 0.0, n1 = 0.0, n2 = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    if (t < kk) {
+        const float2* __restrict__ nearmix = a.nearmix;
+        const float2* __restrict__ farmix = a.farmix;
+        const int* __restrict__ Er = a.Er;
+        const int* __restrict__ farE = a.farE;
+        const int* __restrict__ Et = a.Et;
+        const int* __restrict__ Ef = a.Ef;
+        const float2* nm = nearmix + (size_t)vl * Rp;
+        const float2* fm = farmix + (size_t)vl * Rp;
+        const int en = Ef[r] + lw - lv, ef = Et[vl] + lv - lw;  // near scale h 2^E_f, far scale 2^E_t / h
+        float2 v0, v1, v2, w0, w1, w2;
+        if (a.near_slab) {
+            const int s0 = a.near_seg[leaf], s1 = a.near_seg[leaf + 1];
+            v0 = slab_sum(a.near_slab, s0, s1, R, r, Rp, t);
+            v1 = slab_sum(a.near_slab, s0, s1, R, r, Rp, kk + t);
+            v2 = slab_sum(a.near_slab, s0, s1, R, r, Rp, 2 * kk + t);
+        } else {
+            v0 = nm[t];
+            v1 = nm[kk + t];
+            v2 = nm[2 * kk + t];
+        }
+        if (a.far_slab) {
+            const int s0 = a.far_seg[leaf], s1 = a.far_seg[leaf + 1];
+            w0 = slab_sum(a.far_slab, s0, s1, R, r, Rp, t);
+            w1 = slab_sum(a.far_slab, s0, s1, R, r, Rp, kk + t);
+            w2 = slab_sum(a.far_slab, s0, s1, R, r, Rp, 2 * kk + t);
+        } else {
+            w0 = fm[t];
+            w1 = fm[kk + t];
+            w2 = fm[2 * kk + t];
+        }
+        const int e0 = en + lw - lv + Er[t], e1 = en + Er[kk + t], e2 = en + Er[2 * kk + t];
+        n0 = f2d_scaled(v0.x, e0) + f2d_scaled(v0.y, e0);  // h^2 x near u
+        n1 = f2d_scaled(v1.x, e1) + f2d_scaled(v1.y, e1);  // h x near u_x
+        n2 = f2d_scaled(v2.x, e2) + f2d_scaled(v2.y, e2);
+        const int g0 = Et[vl] + farE[t], g1 = ef + farE[kk + t], g2 = ef + farE[2 * kk + t];
+        f0 = f2d_scaled(w0.x, g0) + f2d_scaled(w0.y, g0);
+        f1 = f2d_scaled(w1.x, g1) + f2d_scaled(w1.y, g1);  // far u_x / h
+        f2 = f2d_scaled(w2.x, g2) + f2d_scaled(w2.y, g2);
+        if (wm != 1.0) {
+            n0 *= wm * wm;
+            n1 *= wm;
+            n2 *= wm;
+            f1 /= wm;
+            f2 /= wm;
+        }
+    }
     if (t < 32) {
         const size_t P2 = 2 * (size_t)a.P;
         const double logh = log(ldexp(a.width, -lv));
@@ -1032,51 +1081,6 @@ __global__ void leaf_mixed_kernel(LeafMixedArgs a) {
     }
     __syncthreads();
     if (t >= kk) return;
-    const float2* __restrict__ nearmix = a.nearmix;
-    const float2* __restrict__ farmix = a.farmix;
-    const int* __restrict__ Er = a.Er;
-    const int* __restrict__ farE = a.farE;
-    const int* __restrict__ Et = a.Et;
-    const int* __restrict__ Ef = a.Ef;
-    const float2* nm = nearmix + (size_t)vl * Rp;
-    const float2* fm = farmix + (size_t)vl * Rp;
-    const int en = Ef[r] + lw - lv, ef = Et[vl] + lv - lw;  // near scale h 2^E_f, far scale 2^E_t / h
-    float2 v0, v1, v2, w0, w1, w2;
-    if (a.near_slab) {
-        const int s0 = a.near_seg[leaf], s1 = a.near_seg[leaf + 1];
-        v0 = slab_sum(a.near_slab, s0, s1, R, r, Rp, t);
-        v1 = slab_sum(a.near_slab, s0, s1, R, r, Rp, kk + t);
-        v2 = slab_sum(a.near_slab, s0, s1, R, r, Rp, 2 * kk + t);
-    } else {
-        v0 = nm[t];
-        v1 = nm[kk + t];
-        v2 = nm[2 * kk + t];
-    }
-    if (a.far_slab) {
-        const int s0 = a.far_seg[leaf], s1 = a.far_seg[leaf + 1];
-        w0 = slab_sum(a.far_slab, s0, s1, R, r, Rp, t);
-        w1 = slab_sum(a.far_slab, s0, s1, R, r, Rp, kk + t);
-        w2 = slab_sum(a.far_slab, s0, s1, R, r, Rp, 2 * kk + t);
-    } else {
-        w0 = fm[t];
-        w1 = fm[kk + t];
-        w2 = fm[2 * kk + t];
-    }
-    const int e0 = en + lw - lv + Er[t], e1 = en + Er[kk + t], e2 = en + Er[2 * kk + t];
-    double n0 = f2d_scaled(v0.x, e0) + f2d_scaled(v0.y, e0);  // h^2 x near u
-    double n1 = f2d_scaled(v1.x, e1) + f2d_scaled(v1.y, e1);  // h x near u_x
-    double n2 = f2d_scaled(v2.x, e2) + f2d_scaled(v2.y, e2);
-    const int g0 = Et[vl] + farE[t], g1 = ef + farE[kk + t], g2 = ef + farE[2 * kk + t];
-    const double f0 = f2d_scaled(w0.x, g0) + f2d_scaled(w0.y, g0);
-    double f1 = f2d_scaled(w1.x, g1) + f2d_scaled(w1.y, g1);  // far u_x / h
-    double f2 = f2d_scaled(w2.x, g2) + f2d_scaled(w2.y, g2);
-    if (wm != 1.0) {
-        n0 *= wm * wm;
-        n1 *= wm;
-        n2 *= wm;
-        f1 /= wm;
-        f2 /= wm;
-    }
     const size_t o = ((size_t)r * nleaf + leaf) * kk + t;
     a.u[o] = n0 + s_scal + f0;
     a.ux[o] = n1 + f1;

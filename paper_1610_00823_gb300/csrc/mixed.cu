@@ -752,7 +752,7 @@ __global__ void split_reduce_kernel(const float2* __restrict__ part, size_t stri
 }
 
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
-               float2* part, size_t n_out_rows, int slices, cudaStream_t st, cudaEvent_t* ev, bool defer_segments) {
+               float2* part, size_t n_out_rows, int slices, cudaStream_t st, cudaEvent_t* ev, int defer) {
     if (slices < kMinSlices || slices > kSlices) return fail(VFMM_ERR_INTERNAL, "slice count out of range");
     if (ev) VFMM_CUDA(cudaEventRecord(ev[0], st));
     if (P.n_groups == 0) {
@@ -787,8 +787,8 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
         a.out = part;
         a.n_items = P.n_groups * a.nchunks;
         VFMM_CHECK(launch_split_n(n_mma, a, bmap, P.ctas > 0 ? std::min(P.ctas, a.n_items) : a.n_items, st));
-        // with defer_segments the consumer sums each target's slab rows itself (same order)
-        const int64_t n = defer_segments ? 0 : (int64_t)P.n_seg * P.R * Rp;
+        // deferred: the consumer sums each target's slab rows itself (same order)
+        const int64_t n = (defer & kDeferSegments) ? 0 : (int64_t)P.n_seg * P.R * Rp;
         if (n > 0)
             segment_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, P.seg, P.seg_out, P.n_seg, P.R,
                                                                                 Rp, out);
@@ -801,7 +801,7 @@ int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int
     a.out = a.split > 1 ? part : out;
     a.n_items = P.n_groups * a.split * a.nchunks;
     VFMM_CHECK(launch_split_n(n_mma, a, bmap, P.ctas > 0 ? std::min(P.ctas, a.n_items) : a.n_items, st));
-    if (a.split > 1) {
+    if (a.split > 1 && !(defer & kDeferSplits)) {
         const int64_t n = (int64_t)P.n_groups * P.group * Rp;
         split_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, a.part_stride, a.split, P.tgt,
                                                                           P.n_groups * P.group, Rp, out);

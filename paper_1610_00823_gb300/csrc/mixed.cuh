@@ -282,7 +282,12 @@ int make_table_map(const void* base, int64_t rows, int Kp, int box_rows, CUtenso
 // ev (optional): a (start, stop) event pair recorded around the contraction and its reduction.
 int split_gemm(const SplitPlan& P, const void* asl, const CUtensorMap& bmap, int Kp, int Rp, float2* out, int* err,
                float2* part, size_t n_out_rows, int slices, cudaStream_t st, cudaEvent_t* ev = nullptr,
-               bool defer_segments = false);
+               int defer = 0);
+// split_gemm's `defer` bits: the consumer of the output sums the entry-major slab rows of each
+// target (kDeferSegments) or the split-K partial sums (kDeferSplits) itself, in the same order and
+// arithmetic as the reduction kernels, which are then not launched
+constexpr int kDeferSegments = 1;
+constexpr int kDeferSplits = 2;
 // Partial-sum elements (float2) of the three buffers whose contractions may run at the same time:
 // [0] S2M, M2L and the leaf far field (one after another), [1] the near field, [2] S2L.
 void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, size_t elems[3]);

@@ -364,9 +364,12 @@ void split_part_elems(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o,
 // ---------------------------------------------------------------- S2M
 // One CTA per virtual leaf (leaf, r): coefficient 0 (the mass) in FP64, the rest from the split
 // contraction scaled back by 2^(E_f[r] + E_row).
+// With split > 1 the contraction's split-K partial sums part[s][row][Rx] are summed here (the
+// reduction kernel's order and arithmetic) instead of read from out.
 __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const int32_t* __restrict__ box_of_leaf,
                                   const int32_t* __restrict__ level, double width, const double* __restrict__ f,
                                   const double* __restrict__ s2m, const float2* __restrict__ out,
+                                  const float2* __restrict__ part, int split, size_t part_stride,
                                   const int* __restrict__ E, const int* __restrict__ Ef, double* __restrict__ Mexp,
                                   unsigned* __restrict__ glev) {
     const int vl = blockIdx.x;
@@ -392,7 +395,14 @@ __global__ void s2m_finish_kernel(int nleaf, int R, int kk, int p, int Rx, const
     const double wm = 2.0 * frexp(width, &lw);
     const int ef = Ef[r] + 2 * (lw - 1 - level[b]);
     for (int q = threadIdx.x; q < 2 * p; q += blockDim.x) {
-        const float2 v = out[(size_t)vl * Rx + q];
+        float2 v;
+        if (split > 1) {
+            float hi = 0.0f, lo = 0.0f;
+            for (int sp = 0; sp < split; ++sp) df_add(hi, lo, part[(size_t)sp * part_stride + (size_t)vl * Rx + q]);
+            v = df_final(hi, lo);
+        } else {
+            v = out[(size_t)vl * Rx + q];
+        }
         const double m = f2d_scaled(v.x, ef + E[q]) + f2d_scaled(v.y, ef + E[q]);
         M[2 + q] = wm == 1.0 ? m : wm * wm * m;
         e = max(e, part_exp(M[2 + q], 2 + q));
@@ -405,10 +415,14 @@ int s2m_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const d
               const MixedWork& w, cudaStream_t st) {
     const MixedOps* mo = (const MixedOps*)o.mixed;
     VFMM_CHECK(split_gemm(PS.s2m, w.fsl, mo->tm_s2m, mo->Kp, mo->Rx, w.s2m_out, w.err, w.part,
-                          (size_t)T.n_leaves * PS.R, mo->slices[kCtrS2M], st, w.cev ? w.cev + 2 : nullptr));
+                          (size_t)T.n_leaves * PS.R, mo->slices[kCtrS2M], st, w.cev ? w.cev + 2 : nullptr,
+                          kDeferSplits));
+    // the split-K partials (when the plan splits) are summed by the finishing kernel
+    const int sp = (!PS.s2m.entry && w.part) ? PS.s2m.split : 1;
+    const size_t stride = (size_t)T.n_leaves * PS.R * mo->Rx;
     s2m_finish_kernel<<<T.n_leaves * PS.R, 128, 0, st>>>(T.n_leaves, PS.R, o.k * o.k, o.p, mo->Rx, T.box_of_leaf,
-                                                         T.level, T.width, f, o.s2m, w.s2m_out, mo->s2m_E, w.Ef,
-                                                         Mexp, w.glev);
+                                                         T.level, T.width, f, o.s2m, w.s2m_out, w.part, sp, stride,
+                                                         mo->s2m_E, w.Ef, Mexp, w.glev);
     VFMM_CUDA(cudaGetLastError());
     return VFMM_OK;
 }
@@ -499,10 +513,21 @@ __global__ void far_operand_kernel(int nleaf, int R, int P2, int Kx, const int32
         if (j == 0) return k >= 2 ? Lexp[((size_t)b * R + r) * P2 + k] : 0.0;
         return Mexp[((size_t)widx[wptr[b] + j - 1] * R + r) * P2 + k];
     };
-    // E_t = exponent bound of the largest value, as the largest exponent bound (integer work)
+    // E_t = exponent bound of the largest value, as the largest exponent bound (integer work). Both
+    // passes walk the same (slot, k < Kx) positions, so the first keeps up to kCache values per thread
+    // in registers for the second (values of k >= P2 are zero).
+    constexpr int kCache = 16;
+    double cache[kCache];
     int em = INT_MIN;
-    for (int q = threadIdx.x; q < ns * P2; q += blockDim.x) {
-        const double v = value(q / P2, q % P2);
+    const int nq = ns * Kx;
+#pragma unroll
+    for (int c = 0; c < kCache; ++c) {
+        const int q = threadIdx.x + c * (int)blockDim.x;
+        cache[c] = q < nq ? value(q / Kx, q % Kx) : 0.0;
+        if (cache[c] != 0.0) em = max(em, exp_bound(cache[c]));
+    }
+    for (int q = threadIdx.x + kCache * (int)blockDim.x; q < nq; q += blockDim.x) {
+        const double v = value(q / Kx, q % Kx);
         if (v != 0.0) em = max(em, exp_bound(v));
     }
     for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
@@ -512,8 +537,13 @@ __global__ void far_operand_kernel(int nleaf, int R, int P2, int Kx, const int32
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) e = max(e, red[w]);
     if (e == INT_MIN) e = 0;  // all zero
     if (threadIdx.x == 0) Et[vl] = e;
-    for (int q = threadIdx.x; q < ns * Kx; q += blockDim.x) {
-        int j = q / Kx, k = q % Kx;
+#pragma unroll
+    for (int c = 0; c < kCache; ++c) {
+        const int q = threadIdx.x + c * (int)blockDim.x;
+        if (q < nq) slice_fixed(cache[c], e, aprep + slice_at((size_t)(s0 + q / Kx) * R + r, Kx, q % Kx), kKBlock);
+    }
+    for (int q = threadIdx.x + kCache * (int)blockDim.x; q < nq; q += blockDim.x) {
+        const int j = q / Kx, k = q % Kx;
         slice_fixed(value(j, k), e, aprep + slice_at((size_t)(s0 + j) * R + r, Kx, k), kKBlock);
     }
 }
@@ -526,7 +556,8 @@ int far_leaf_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, co
                                                           Lexp, w.Et, (bf16*)w.aprep);
     VFMM_CUDA(cudaGetLastError());
     return split_gemm(PS.far, w.aprep, mo->tm_far, mo->Kx, mo->Rp, w.far_out, w.err, w.part,
-                      (size_t)T.n_leaves * PS.R, mo->slices[kCtrFar], st, w.cev ? w.cev + 8 : nullptr, true);
+                      (size_t)T.n_leaves * PS.R, mo->slices[kCtrFar], st, w.cev ? w.cev + 8 : nullptr,
+                      kDeferSegments);
 }
 
 }  // namespace vfmm
