@@ -1496,9 +1496,11 @@ static SideStream* side_stream(cudaStream_t st) {
     return &ss;
 }
 
-// Kernels one split contraction launches: the contraction, and its split-K or segmented reduction.
-static int gemm_launches(const SplitPlan& P) {
-    return P.n_groups > 0 ? 1 + ((P.split > 1 || P.entry) ? 1 : 0) : 0;
+// Kernels one split contraction launches: the contraction, and its split-K or segmented reduction
+// unless the consumer takes that sum over (split_gemm's defer bits).
+static int gemm_launches(const SplitPlan& P, int defer = 0) {
+    const bool reduce = P.entry ? !(defer & kDeferSegments) : (P.split > 1 && !(defer & kDeferSplits));
+    return P.n_groups > 0 ? 1 + (reduce ? 1 : 0) : 0;
 }
 
 // One solve of R right-hand sides (f: [R][n_leaves][k^2]). The mixed form folds them into the
@@ -1561,7 +1563,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
     mark(se, ST_S2M, false, st);
     if (mixed) {
         VFMM_CHECK(s2m_mixed(T, PS, o, f, w.Mexp, w.mix, st));
-        launches += 1 + gemm_launches(PS.s2m);
+        launches += 1 + gemm_launches(PS.s2m, kDeferSplits);
     } else {
         ++launches;
         dim3 g((nleaf + GBN - 1) / GBN, (P2 + GBM - 1) / GBM);
@@ -1716,7 +1718,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
     mark(se, ST_L2T, false, st);
     if (mixed) {
         VFMM_CHECK(far_leaf_mixed(T, PS, o, w.Mexp, w.Lexp, w.mix, st));
-        launches += 1 + gemm_launches(PS.far);
+        launches += 1 + gemm_launches(PS.far, kDeferSegments);
     } else {
         ++launches;
         dim3 g((nleaf + GBN - 1) / GBN, (3 * kk + GBM - 1) / GBM);
