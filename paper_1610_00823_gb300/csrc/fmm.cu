@@ -557,6 +557,11 @@ struct DownArgs {
     double* Lexp;
     // split-precision M2L rows 2..2p+1 (null in the FP64 form): (hi, lo) scaled by 2^-E[level][r]
     const float2* m2l_out;
+    // split-K M2L: its partial sums [split][n_boxes * R][Rx], summed here when m2l_split > 1 (the
+    // reduction kernel's order and arithmetic; that kernel is then not launched)
+    const float2* m2l_part;
+    int m2l_split;
+    size_t m2l_stride;
     const int* m2l_E;   // [Rx] row exponents of the M2L tables
     const unsigned* m2l_G;  // [(depth + 1) R] biased level exponents of the multipole operand
     const double* m2l_c0;  // Re of local coefficient 0 from the V and X lists, with the log(h) terms
@@ -570,6 +575,16 @@ struct DownArgs {
     const int* Ef;
     int Rx;
 };
+
+// M2L output (hi, lo) of virtual box vb, row q: from the split-K partials or the reduced output.
+__device__ __forceinline__ float2 m2l_value(const DownArgs& d, size_t vb, int q) {
+    if (d.m2l_split > 1) {
+        float hi = 0.0f, lo = 0.0f;
+        for (int s = 0; s < d.m2l_split; ++s) df_add(hi, lo, d.m2l_part[(size_t)s * d.m2l_stride + vb * d.Rx + q]);
+        return df_final(hi, lo);
+    }
+    return d.m2l_out[vb * d.Rx + q];
+}
 
 __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
     const int R = d.R;
@@ -616,8 +631,8 @@ __global__ void __launch_bounds__(64) down_kernel(DownArgs d) {
         if (t == 0) {
             re += d.m2l_c0[vb];
         } else if (d.vptr[b + 1] > d.vptr[b]) {
-            const float2 vr = d.m2l_out[vb * d.Rx + 2 * (t - 1)];
-            const float2 vi = d.m2l_out[vb * d.Rx + 2 * (t - 1) + 1];
+            const float2 vr = m2l_value(d, vb, 2 * (t - 1));
+            const float2 vi = m2l_value(d, vb, 2 * (t - 1) + 1);
             const int g = level_exp_value(d.m2l_G[(size_t)d.level * R + r]);
             re += ((double)vr.x + (double)vr.y) * pow2(g + d.m2l_E[2 * (t - 1)]);
             im += ((double)vi.x + (double)vi.y) * pow2(g + d.m2l_E[2 * (t - 1) + 1]);
@@ -656,8 +671,8 @@ __device__ __forceinline__ double2 combine_local(const DownArgs& d, int level, i
         if (t == 0) {
             re += d.m2l_c0[vb];
         } else if (has_v) {
-            const float2 vr = d.m2l_out[vb * d.Rx + 2 * (t - 1)];
-            const float2 vi = d.m2l_out[vb * d.Rx + 2 * (t - 1) + 1];
+            const float2 vr = m2l_value(d, vb, 2 * (t - 1));
+            const float2 vi = m2l_value(d, vb, 2 * (t - 1) + 1);
             const int g = level_exp_value(d.m2l_G[(size_t)level * d.R + r]);
             const int er = g + d.m2l_E[2 * (t - 1)], ei = g + d.m2l_E[2 * (t - 1) + 1];
             re += f2d_scaled(vr.x, er) + f2d_scaled(vr.y, er);
@@ -1399,6 +1414,11 @@ static void fill_down_args(DownArgs& d, const DeviceTree& T, const vfmm_ops& o, 
     d.xslab = w.xslab;
     d.pwloc = w.pwL;
     d.m2l_out = mo ? w.mix.m2l_out : nullptr;
+    // a grouped split-K M2L leaves its partial sums to the downward kernels (m2l_mixed defers them)
+    const bool m2l_parts = mo && !w.ps->m2l.entry && w.ps->m2l.split > 1 && w.mix.part;
+    d.m2l_part = m2l_parts ? w.mix.part : nullptr;
+    d.m2l_split = m2l_parts ? w.ps->m2l.split : 1;
+    d.m2l_stride = (size_t)T.n_boxes * R * (mo ? mo->Rx : 0);
     d.m2l_E = mo ? mo->m2l_E : nullptr;
     d.m2l_G = mo ? w.mix.glev : nullptr;
     d.m2l_c0 = mo ? w.mix.m2l_c0 : nullptr;
@@ -1610,7 +1630,7 @@ static int solve_steps(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o
             c0s = side->aux;
         }
         VFMM_CHECK(m2l_mixed(T, PS, o, w.Mexp, w.mix, passes, st));
-        if (PS.m2l.n_groups > 0) launches += 3 + gemm_launches(PS.m2l);
+        if (PS.m2l.n_groups > 0) launches += 3 + gemm_launches(PS.m2l, kDeferSplits);
         const int begin = T.level_start[2], end = T.level_start[T.depth + 1];
         const int64_t warps = (int64_t)(end - begin) * R;
         const size_t c0_smem = (size_t)kVCfg * P * sizeof(double2) + (size_t)kFarCfg * kk * sizeof(double);

@@ -485,8 +485,9 @@ int m2l_mixed(const DeviceTree& T, const PlanSet& PS, const vfmm_ops& o, const d
     multipole_slice_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(T.level, vb0, vb1, R, P2, mo->Kx, Mexp,
                                                                           w.glev, (bf16*)w.msl);
     VFMM_CUDA(cudaGetLastError());
+    // split-K partials (grouped form) are summed by the downward kernels that read the locals
     return split_gemm(PS.m2l, w.msl, mo->tm_m2l, mo->Kx, mo->Rx, w.m2l_out, w.err, w.part, (size_t)T.n_boxes * R,
-                      mo->slices[kCtrM2L], st, w.cev ? w.cev + 4 : nullptr);
+                      mo->slices[kCtrM2L], st, w.cev ? w.cev + 4 : nullptr, kDeferSplits);
 }
 
 // ---------------------------------------------------------------- S2L
