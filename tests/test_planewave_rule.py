@@ -57,6 +57,19 @@ def test_header_holds_every_bucket_sorted_and_short():
         assert np.all(np.diff(lam) > 0) and lam[0] > 0
 
 
+def test_header_is_what_the_generator_writes():
+    """The committed rules come from the committed script: regenerating the two smaller buckets gives
+    the same nodes, and weights equal to rounding (a differently pivoted QR would change the node
+    set, which the moment pins below would still have to accept)."""
+    pytest.importorskip("scipy")
+    for pm in (10, 20):
+        lam, om = R.make_rule(pm)
+        hl, ho = RULES[pm]
+        assert len(lam) == len(hl)
+        assert np.allclose(lam, hl, rtol=1e-13, atol=0.0)
+        assert np.allclose(om, ho, rtol=1e-9, atol=1e-300)
+
+
 @pytest.mark.parametrize("pmax", [10, 20, 30, 40, 60])
 def test_moments_match_the_laplace_transform(pmax):
     lam, om = RULES[pmax]
