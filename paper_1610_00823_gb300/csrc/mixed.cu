@@ -6,7 +6,7 @@
 //  * f is normalised by a global power of two (|a| < 1) and each table row r by its own power
 //    of two shared by all 33 configurations; each normalised value is written as 8 balanced
 //    base-128 digits a = sum_i m_i 2^(-7 i) (integers |m_1| <= 128, |m_i| <= 64 for i >= 2, exact
-//    in BF16), of which a contraction takes the first S (S = 7: 49 bits).
+//    in BF16), of which a contraction takes the first S (6 by default: 42 bits; up to 8).
 //  * Products (i, j) with i + j <= S + 1 are kept (the dropped terms are below 2^(-7 S - 7)). Per K
 //    value the products of one diagonal d = i + j - 2 sum to at most 2 * 128 * 64 + (d - 1) * 64^2
 //    integer units of 2^(-7(d+2)) (28672 for d = 4), so over a drain group of at most 512 K values
