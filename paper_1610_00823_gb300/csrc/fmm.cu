@@ -1,8 +1,11 @@
-// The FMM passes of the box code (Section 3.1) in FP64, with the gradient from
-// differentiated tables and expansions (Section 3.2).
+// The FMM passes of the box code (Section 3.1), with the gradient from differentiated tables and
+// expansions (Section 3.2), and the solve driver of both forms (FP64 below; the split-BF16
+// contractions of the mixed form are in mixed.cu and mixed_far.cu).
 //
 //   S2M      leaf multipoles  a = h^2 Q f                 (gather GEMM, all leaves)
-//   M2M      per level, finest first, one warp per parent box
+//   M2M      finest parents first: one cooperative persistent pass for small trees (position-DFT
+//            form, readiness counters), else one launch per level
+//   M2L      dense per V entry (gather GEMM per offset) or plane-wave (planewave.cu)
 //   DOWN     per level from 2 down the tree, one CTA per box:
 //            b = L2L(parent) + sum_V M2L a_c (+ a_0(c) log h) + sum_X (2h)^2 R f_c (+ a_0(c) log h)
 //   NEAR     per near configuration, T_cfg f_src for every U-list entry (gather GEMM into
@@ -11,8 +14,9 @@
 //   LEAF     one CTA per leaf: u = h^2 sum_U T f - (1/2pi) log(h) sum_U a_0(src) + L2T + sum_W M2T,
 //            gradient = h sum_U T' f + L2T'/h + sum_W M2T'
 //
-// Workspace (caller-owned, from vfmm_workspace_size): multipoles and locals
-// [n_boxes][2(p+1)], near slabs [n_U][3kk], far values [n_leaves][3kk] (+ I/O copies).
+// Workspace (caller-owned, from vfmm_workspace_size): status word, multipoles and locals
+// [n_boxes][2(p+1)], near slabs [n_U][3kk], far values [n_leaves][3kk], M2L/S2L slabs or
+// plane-waves, the mixed form's operands and outputs (+ I/O copies); see layout().
 #include <algorithm>
 #include <cmath>
 #include <cstring>
