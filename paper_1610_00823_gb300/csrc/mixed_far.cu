@@ -1,7 +1,8 @@
-// Split-BF16 far field (VFMM_MIXED): S2M, M2L and the leaf evaluation of local and W-list
-// multipole expansions (L2T + M2T), all as target-major split contractions on the tensor
-// cores (see mixed.cu for the arithmetic), with FP64 kept for the log(h) terms, the
-// coefficient-0 terms, M2M, L2L, S2L and the final per-target sums.
+// Split-BF16 far field (VFMM_MIXED): S2M, M2L, S2L and the leaf evaluation of local and W-list
+// multipole expansions (L2T + M2T), all as split contractions on the tensor cores (see mixed.cu
+// for the arithmetic), with FP64 kept for the log(h) terms, the coefficient-0 terms, M2M, L2L and
+// the final per-target sums. S2L takes the f slices of the near field (global exponent) and
+// 20 tables of coefficients 1..p; its row 0 and log(h) term are FP64 (m2l_c0_kernel).
 //
 // Normalisation (each product must be exact per diagonal, so every A row and every table row
 // carries a power-of-two scale):

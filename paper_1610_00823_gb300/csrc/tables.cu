@@ -1,5 +1,6 @@
-// Unit-scale operators of the box code, generated on the device (Section 3.1,
-// "precomputed tables ... up to scale"; Section 3.2 for the gradient tables).
+// Unit-scale operators of the box code, generated on the device (Section 3.1: the near-field
+// tables are computed once for a unit box and reused at every level up to scale; Section 3.2 for
+// the gradient tables).
 //
 // Scaling: a box of width h stores its multipole coefficients as a_n / h^n and its
 // local coefficients as b_l h^l; the expansions represent
