@@ -120,7 +120,7 @@ int vfmm_tree_build(const vfmm_tree_params* prm, const vfmm_source* src, void* s
 #define VFMM_REFINE_INTERP_AREA 2   /* interpolation error x (h / width)^2 */
 #define VFMM_REFINE_INTERP_MIXED 3  /* x (h / width)^2 on boxes meeting the boundary, x h / width elsewhere */
 
-/* vfmm_tree_build with the a-priori rules of Section 6.1 ("A note on adaptivity") as the split
+/* vfmm_tree_build with the a-priori rules of Section 6.1 (on adaptivity) as the split
  * test: the interpolation error e = max |f - p| over the nodes of the box's four children, p the
  * interpolant of f on the box's own nodes, compared with tol * F unweighted (INTERP), times the
  * relative area (INTERP_AREA), or times the relative area where the box meets the source's
@@ -213,8 +213,8 @@ int vfmm_source_sample(const vfmm_tree* tree, const vfmm_source* src, double* f_
 
 int vfmm_tree_destroy(vfmm_tree* tree);
 
-/* Unit-scale operators of the box code for (k, p) (Section 3.1, "precomputed
- * tables ... up to scale"; Section 3.2 for the gradient tables), generated on the
+/* Unit-scale operators of the box code for (k, p) (Section 3.1: tables computed once for a unit
+ * box and reused at every level up to scale; Section 3.2 for the gradient tables), generated on the
  * device: 33 near-field tables of the potential and both gradient components,
  * S2M, S2L (20), M2T geometry (20), L2T, M2M (4), M2L (40), L2L (4).
  * 4 <= k <= 16, 1 <= p <= 60. Synchronises. Errors: INVALID_ARG, OOM, CUDA. */

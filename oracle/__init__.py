@@ -14,8 +14,8 @@ Modules:
   cheb    - nodes, Fejer weights, Lagrange basis, values->coefficients (Section 3.1)
   source  - evaluation of the synthetic right-hand sides
   tree    - adaptive refinement, level restriction, U/V/W/X lists (Section 3.1, Fig. 1)
-  quad    - box integrals of the kernel against the Lagrange basis (Section 3.1,
-            "precomputed tables"; Section 3.2 for the gradient kernels)
+  quad    - box integrals of the kernel against the Lagrange basis (Section 3.1: the
+            near-field tables; Section 3.2 for the gradient kernels)
   tables  - unit-scale operators: near tables, S2M, S2L, M2T, L2T, M2M, M2L, L2L
   fmm     - the FMM passes (Section 3.1) producing u, u_x, u_y at leaf nodes
   brute   - direct quadrature of V[f~] without FMM or tables, for small trees
