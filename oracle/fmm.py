@@ -3,8 +3,8 @@
 For every leaf node x_t the box code returns
     V~f~(x_t) = Phi_j(x_t) + sum over near leaves of int_{B_i} G(x_t, y) f~(y) dy,
 where Phi_j collects the far field by expansions (Section 3.1) and the near sum
-is a table apply per neighbour configuration (Section 3.1, "precomputed
-tables"), with the gradient from the differentiated kernels and the
+is a table apply per neighbour configuration (Section 3.1, tables computed once
+for a unit box), with the gradient from the differentiated kernels and the
 differentiated expansions (Section 3.2).
 
 Steps, in the order the FMM takes them:

@@ -8,8 +8,8 @@ for every basis function l_s of S (the tensor Lagrange basis on the nodes of
     G1_s(x) = -(1/2pi) int_S (x1 - y1)/|x-y|^2 l_s(y) dy        (Eq. volumeint3x)
     G2_s(x) = -(1/2pi) int_S (x2 - y2)/|x-y|^2 l_s(y) dy
 
-The paper computes these "up to scale" once, by an adaptive brute-force
-quadrature (Section 1; Section 3.1 on precomputed tables). This oracle uses two
+The paper computes these once for a unit box, to be scaled at every level, by an adaptive
+brute-force quadrature (Section 1; Section 3.1 on precomputed tables). This oracle uses two
 plain rules:
 
 * x inside S: S is cut into four triangles with apex x. On the triangle (x, P0,

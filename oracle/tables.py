@@ -1,4 +1,4 @@
-"""Unit-scale operators of the box code (Section 3.1, "up to scale").
+"""Unit-scale operators of the box code (Section 3.1: the same operators at every level after scaling).
 
 Scaling convention. A box of width h and centre z_b carries a multipole
 expansion Phi(z) = a_0 log(z - z_b) + sum_{n>=1} a_n (z - z_b)^-n stored as

@@ -1,6 +1,6 @@
 // Quadrature of the log kernel and its gradient against the leaf basis over one
-// source box, for the near-field tables of Section 3.1 ("precomputed tables ...
-// up to scale") and the gradient tables of Section 3.2.
+// source box, for the near-field tables of Section 3.1 (computed once for a unit box, reused at
+// every level after scaling) and the gradient tables of Section 3.2.
 //
 // Target x (unit target box [-1/2, 1/2]^2 coordinates), source box S of centre c
 // and width rho. p = the point of the closed box S nearest to x (p = x when x is
